@@ -1,0 +1,659 @@
+/*
+ * wtmd_oracle.c -- plain, slow, FP64 CPU oracle for the well-tempered
+ * metadynamics (WTMD) bias-force path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  It shares no code, header,
+ * constant or table with the CUDA library; the two are written independently
+ * and compared on the same seeded inputs.
+ *
+ * Every function follows the plain definition of what it computes, in the
+ * order the definition states it, in double precision:
+ *   - metadynamics bias as a sum of Gaussians deposited at intervals, fixed
+ *     height (standard) or height scaled by a bias factor (well-tempered):
+ *     PySAGES paper, Sec. 2.1.5 "Metadynamics";
+ *   - optional storage of the bias on a pre-defined grid: Sec. 2.1.5;
+ *   - free energy A(xi) = -kT ln p(xi) + C: Sec. 2.1, Eq. (free-energy);
+ *   - collective variables (Component, DihedralAngle, RadiusofGyration):
+ *     Sec. 2.2; their gradients (the paper obtains them with jax.grad,
+ *     Sec. 2) are written here analytically and pinned by finite differences;
+ *   - the bias force is added to the engine's net force each step: Sec. 2
+ *     ("force-like object ... biasing forces are added to the backend net
+ *     forces"); the step structure (half-step integration, bonded and pair
+ *     forces, CV, bias-force addition, second half-step) is the one named in
+ *     Sec. 3.2.1.
+ * Readings where the paper is silent (WT height formula, coordination
+ * switching function, Philox counter layout, BAOAB splitting, deposition
+ * timing) are stated at each function.
+ *
+ * Parity pins (tests/test_oracle_*.py): Philox known-answer vectors,
+ * Mueller-Brown minima, closed forms of single hills, finite-difference
+ * Jacobians, translation/rotation invariances, the WT fixed-point recursion,
+ * the BAOAB harmonic-oscillator variance, and recovery of the Mueller-Brown
+ * free energy from -(gamma/(gamma-1)) V.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as */
+/* easy as 1, 2, 3", SC'11.  Round: two 32x32->64 products of counter words */
+/* 0 and 2 with the multipliers; outputs mix the high halves with the other */
+/* counter words and the key; the key advances by the Weyl constants        */
+/* between rounds.                                                          */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Noise stream of the Langevin thermostat (reading: the paper fixes no RNG).
+ * key = (seed low word, seed high word); counter = (step low word, global
+ * particle index, step high word, 0).  The four 32-bit outputs become
+ * uniforms u = (x + 1/2) / 2^32 in (0,1) and two Box-Muller pairs; the first
+ * three normals drive x, y, z. */
+void orc_noise3(uint64_t seed, uint64_t step, uint32_t particle, double g[3])
+{
+    uint32_t ctr[4] = {(uint32_t)step, particle, (uint32_t)(step >> 32), 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    double u[4];
+    for (int i = 0; i < 4; ++i) u[i] = ((double)r[i] + 0.5) / 4294967296.0;
+    double rad0 = sqrt(-2.0 * log(u[0]));
+    double rad1 = sqrt(-2.0 * log(u[2]));
+    g[0] = rad0 * cos(2.0 * ORC_PI * u[1]);
+    g[1] = rad0 * sin(2.0 * ORC_PI * u[1]);
+    g[2] = rad1 * cos(2.0 * ORC_PI * u[3]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry helpers                                                          */
+/* ------------------------------------------------------------------------ */
+/* d = a - b, minimum image in each periodic dimension (box[k] > 0). */
+static void orc_delta(const double* a, const double* b, const double* box, double d[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        d[k] = a[k] - b[k];
+        if (box && box[k] > 0.0) d[k] -= box[k] * nearbyint(d[k] / box[k]);
+    }
+}
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Engines (the systems that drive the method; the paper's backends own     */
+/* these).                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Mueller-Brown potential (Mueller & Brown, Theor. Chim. Acta 53, 75 (1979)):
+ * U(x,y) = sum_k A_k exp(a_k (x-x_k)^2 + b_k (x-x_k)(y-y_k) + c_k (y-y_k)^2). */
+static const double MB_A[4] = {-200.0, -100.0, -170.0, 15.0};
+static const double MB_a[4] = {-1.0, -1.0, -6.5, 0.7};
+static const double MB_b[4] = {0.0, 0.0, 11.0, 0.6};
+static const double MB_c[4] = {-10.0, -10.0, -6.5, 0.7};
+static const double MB_x0[4] = {1.0, 0.0, -0.5, -1.0};
+static const double MB_y0[4] = {0.0, 0.5, 1.5, 1.0};
+
+double orc_mb(double x, double y, double* fx, double* fy)
+{
+    double U = 0.0, gx = 0.0, gy = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double dx = x - MB_x0[k], dy = y - MB_y0[k];
+        double e = MB_A[k] * exp(MB_a[k] * dx * dx + MB_b[k] * dx * dy + MB_c[k] * dy * dy);
+        U += e;
+        gx += e * (2.0 * MB_a[k] * dx + MB_b[k] * dy);
+        gy += e * (MB_b[k] * dx + 2.0 * MB_c[k] * dy);
+    }
+    if (fx) *fx = -gx;
+    if (fy) *fy = -gy;
+    return U;
+}
+
+/* 12-6 Lennard-Jones, all pairs, minimum image, truncated at rc, energy
+ * shifted to zero at rc.  f[n][3] is overwritten.  Returns the energy. */
+double orc_lj(int64_t n, const double* x, const double* box, double eps, double sig, double rc, double* f)
+{
+    double rc2 = rc * rc;
+    double sr6c = pow(sig / rc, 6.0);
+    double ushift = 4.0 * eps * (sr6c * sr6c - sr6c);
+    double U = 0.0;
+#pragma omp parallel for reduction(+ : U) schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            orc_delta(&x[3 * i], &x[3 * j], box, d);
+            double r2 = dot3(d, d);
+            if (r2 >= rc2) continue;
+            double sr2 = sig * sig / r2;
+            double sr6 = sr2 * sr2 * sr2;
+            double fr = 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2; /* -dU/dr / r */
+            for (int k = 0; k < 3; ++k) fi[k] += fr * d[k];
+            U += 0.5 * (4.0 * eps * (sr6 * sr6 - sr6) - ushift);
+        }
+        for (int k = 0; k < 3; ++k) f[3 * i + k] = fi[k];
+    }
+    return U;
+}
+
+/* Dihedral angle of four points, IUPAC sign convention:
+ * b1 = p1-p0, b2 = p2-p1, b3 = p3-p2, n1 = b1 x b2, n2 = b2 x b3,
+ * phi = atan2(|b2| b1.n2, n1.n2) in (-pi, pi]; cis = 0, trans = pi.
+ * If g != NULL it receives d phi / d p_k (k = 0..3, 3 components each). */
+static double orc_dihedral_pts(const double* p0, const double* p1, const double* p2, const double* p3,
+                               const double* box, double g[4][3])
+{
+    double b1[3], b2[3], b3[3], n1[3], n2[3];
+    orc_delta(p1, p0, box, b1);
+    orc_delta(p2, p1, box, b2);
+    orc_delta(p3, p2, box, b3);
+    cross3(b1, b2, n1);
+    cross3(b2, b3, n2);
+    double nb2 = sqrt(dot3(b2, b2));
+    double phi = atan2(nb2 * dot3(b1, n2), dot3(n1, n2));
+    if (g) {
+        double n1sq = dot3(n1, n1), n2sq = dot3(n2, n2), b2sq = dot3(b2, b2);
+        double a = dot3(b1, b2) / b2sq, c = dot3(b3, b2) / b2sq;
+        for (int k = 0; k < 3; ++k) {
+            g[0][k] = -nb2 / n1sq * n1[k];
+            g[3][k] = nb2 / n2sq * n2[k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            g[1][k] = -(1.0 + a) * g[0][k] + c * g[3][k];
+            g[2][k] = -(1.0 + c) * g[3][k] + a * g[0][k];
+        }
+    }
+    return phi;
+}
+
+/* Bead-chain force field (per chain of nb consecutive beads):
+ * bonds k_b/2 (r - r0)^2, angles k_a/2 (theta - theta0)^2,
+ * torsions k_t (1 + cos 3 phi).  f is overwritten for the chain's beads. */
+double orc_chain(int64_t nb, const double* x, double kb, double r0, double ka, double th0, double kt, double* f)
+{
+    double U = 0.0;
+    for (int64_t i = 0; i < 3 * nb; ++i) f[i] = 0.0;
+    for (int64_t i = 0; i + 1 < nb; ++i) {
+        double d[3];
+        orc_delta(&x[3 * (i + 1)], &x[3 * i], NULL, d);
+        double r = sqrt(dot3(d, d));
+        U += 0.5 * kb * (r - r0) * (r - r0);
+        double c = -kb * (r - r0) / r; /* force on bead i+1 = c * d */
+        for (int k = 0; k < 3; ++k) {
+            f[3 * (i + 1) + k] += c * d[k];
+            f[3 * i + k] -= c * d[k];
+        }
+    }
+    for (int64_t i = 0; i + 2 < nb; ++i) {
+        double u[3], v[3];
+        orc_delta(&x[3 * i], &x[3 * (i + 1)], NULL, u);      /* bead i   - bead i+1 */
+        orc_delta(&x[3 * (i + 2)], &x[3 * (i + 1)], NULL, v); /* bead i+2 - bead i+1 */
+        double nu = sqrt(dot3(u, u)), nv = sqrt(dot3(v, v));
+        double cs = dot3(u, v) / (nu * nv);
+        double th = acos(cs);
+        U += 0.5 * ka * (th - th0) * (th - th0);
+        /* dtheta/dcos = -1/sin(theta) */
+        double dUdcos = ka * (th - th0) * (-1.0 / sin(th));
+        for (int k = 0; k < 3; ++k) {
+            double dcos_du = v[k] / (nu * nv) - cs * u[k] / (nu * nu);
+            double dcos_dv = u[k] / (nu * nv) - cs * v[k] / (nv * nv);
+            f[3 * i + k] -= dUdcos * dcos_du;
+            f[3 * (i + 2) + k] -= dUdcos * dcos_dv;
+            f[3 * (i + 1) + k] += dUdcos * (dcos_du + dcos_dv);
+        }
+    }
+    for (int64_t i = 0; i + 3 < nb; ++i) {
+        double g[4][3];
+        double phi = orc_dihedral_pts(&x[3 * i], &x[3 * (i + 1)], &x[3 * (i + 2)], &x[3 * (i + 3)], NULL, g);
+        U += kt * (1.0 + cos(3.0 * phi));
+        double dUdphi = -3.0 * kt * sin(3.0 * phi);
+        for (int a = 0; a < 4; ++a)
+            for (int k = 0; k < 3; ++k) f[3 * (i + a) + k] -= dUdphi * g[a][k];
+    }
+    return U;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Collective variables (Sec. 2.2).  Each evaluates xi for one walker whose  */
+/* atoms are x[0..n-1] and writes the dense Jacobian J[n][3] = d xi / d x.   */
+/* ------------------------------------------------------------------------ */
+enum { ORC_CV_COMPONENT = 1, ORC_CV_DIHEDRAL = 2, ORC_CV_COORDINATION = 3, ORC_CV_RG = 4, ORC_CV_QPAIRS = 5 };
+enum { ORC_CV_INTENSIVE = 1 };
+
+typedef struct {
+    int64_t kind;
+    int64_t n_a;        /* size of group a; -1 = all atoms of the walker */
+    const int32_t* a;   /* walker-local indices */
+    int64_t n_b;        /* coordination partner group; -1 = all atoms */
+    const int32_t* b;
+    int64_t axis;       /* Component */
+    double r0;          /* switching-function distance */
+    int64_t nn, mm;     /* switching-function exponents (mm must be 2 nn) */
+    double scale;       /* multiplier; 0 = default (see each CV) */
+    int64_t flags;      /* ORC_CV_INTENSIVE */
+    double period;      /* > 0: periodic CV with this period */
+} orc_cv;
+
+/* Rational switching function s(r) = (1 - x^n) / (1 - x^m), x = r / r0.
+ * With m = 2n this equals 1 / (1 + x^n) exactly (the factor 1 - x^n cancels),
+ * which also removes the 0/0 at r = r0 (s = 1/2).  Returns s and, through
+ * *gr, (ds/dr) / r so that d s / d r_i = gr * (r_i - r_j). */
+static double orc_switch(double r2, double r0, int64_t nn, double* gr)
+{
+    double r = sqrt(r2);
+    double x = r / r0;
+    double xn = pow(x, (double)nn);
+    double s = 1.0 / (1.0 + xn);
+    double dsdr = -(double)nn * pow(x, (double)(nn - 1)) / r0 * s * s;
+    if (gr) *gr = dsdr / r;
+    return s;
+}
+
+static int64_t orc_group(int64_t na, const int32_t* a, int64_t n, int64_t k) { return na < 0 ? k : (int64_t)a[k]; }
+
+/* Evaluate one CV for one walker.  Returns 0 or -1 on bad input. */
+int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box, double* xi, double* J)
+{
+    for (int64_t i = 0; i < 3 * n; ++i) J[i] = 0.0;
+    switch (cv->kind) {
+    case ORC_CV_COMPONENT: {
+        /* Sec. 2.2 AxisCV "Component": one coordinate of one atom. */
+        int64_t i = cv->a[0];
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0;
+        *xi = sc * x[3 * i + cv->axis];
+        J[3 * i + cv->axis] = sc;
+        return 0;
+    }
+    case ORC_CV_DIHEDRAL: {
+        /* Sec. 2.2 FourPointCV "DihedralAngle". */
+        double g[4][3];
+        const int32_t* a = cv->a;
+        *xi = orc_dihedral_pts(&x[3 * a[0]], &x[3 * a[1]], &x[3 * a[2]], &x[3 * a[3]], box, g);
+        for (int p = 0; p < 4; ++p)
+            for (int k = 0; k < 3; ++k) J[3 * a[p] + k] += g[p][k];
+        return 0;
+    }
+    case ORC_CV_COORDINATION: {
+        /* Switching-function coordination number (not defined in the paper):
+         * xi = scale * sum_{i in A} sum_{j in B, j != i} s(r_ij),
+         * default scale = 1/|A| (mean coordination of group A). */
+        int64_t na = cv->n_a < 0 ? n : cv->n_a;
+        int64_t nb = cv->n_b < 0 ? n : cv->n_b;
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0 / (double)na;
+        double sum = 0.0;
+        for (int64_t p = 0; p < na; ++p) {
+            int64_t i = orc_group(cv->n_a, cv->a, n, p);
+            for (int64_t q = 0; q < nb; ++q) {
+                int64_t j = orc_group(cv->n_b, cv->b, n, q);
+                if (j == i) continue;
+                double d[3], gr;
+                orc_delta(&x[3 * i], &x[3 * j], box, d);
+                sum += orc_switch(dot3(d, d), cv->r0, cv->nn, &gr);
+                for (int k = 0; k < 3; ++k) {
+                    J[3 * i + k] += sc * gr * d[k];
+                    J[3 * j + k] -= sc * gr * d[k];
+                }
+            }
+        }
+        *xi = sc * sum;
+        return 0;
+    }
+    case ORC_CV_RG: {
+        /* Sec. 2.2 "RadiusofGyration", equal masses:
+         * Rg = sqrt(1/m sum_k |u_k - c|^2), u_k = positions unwrapped by the
+         * minimum image relative to the group's first atom, c = mean(u).
+         * INTENSIVE divides by m^(1/3). */
+        int64_t m = cv->n_a < 0 ? n : cv->n_a;
+        double* u = (double*)malloc(sizeof(double) * 3 * (size_t)m);
+        int64_t i0 = orc_group(cv->n_a, cv->a, n, 0);
+        double c[3] = {0.0, 0.0, 0.0};
+        for (int64_t p = 0; p < m; ++p) {
+            int64_t i = orc_group(cv->n_a, cv->a, n, p);
+            double d[3];
+            orc_delta(&x[3 * i], &x[3 * i0], box, d);
+            for (int k = 0; k < 3; ++k) {
+                u[3 * p + k] = x[3 * i0 + k] + d[k];
+                c[k] += u[3 * p + k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) c[k] /= (double)m;
+        double s2 = 0.0;
+        for (int64_t p = 0; p < m; ++p)
+            for (int k = 0; k < 3; ++k) s2 += (u[3 * p + k] - c[k]) * (u[3 * p + k] - c[k]);
+        double rg = sqrt(s2 / (double)m);
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0;
+        if (cv->flags & ORC_CV_INTENSIVE) sc /= cbrt((double)m);
+        for (int64_t p = 0; p < m; ++p) {
+            int64_t i = orc_group(cv->n_a, cv->a, n, p);
+            for (int k = 0; k < 3; ++k) J[3 * i + k] += sc * (u[3 * p + k] - c[k]) / ((double)m * rg);
+        }
+        free(u);
+        *xi = sc * rg;
+        return 0;
+    }
+    case ORC_CV_QPAIRS: {
+        /* Q-like pair count (not in the paper): mean switching function over
+         * a fixed list of pairs a[2p], a[2p+1]. */
+        int64_t np = cv->n_a / 2;
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0 / (double)np;
+        double sum = 0.0;
+        for (int64_t p = 0; p < np; ++p) {
+            int64_t i = cv->a[2 * p], j = cv->a[2 * p + 1];
+            double d[3], gr;
+            orc_delta(&x[3 * i], &x[3 * j], box, d);
+            sum += orc_switch(dot3(d, d), cv->r0, cv->nn, &gr);
+            for (int k = 0; k < 3; ++k) {
+                J[3 * i + k] += sc * gr * d[k];
+                J[3 * j + k] -= sc * gr * d[k];
+            }
+        }
+        *xi = sc * sum;
+        return 0;
+    }
+    default:
+        return -1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metadynamics bias (Sec. 2.1.5)                                            */
+/* ------------------------------------------------------------------------ */
+/* V(xi) = sum_k w_k exp(-sum_i D_ki^2 / (2 sigma_i^2)), D_ki = xi_i - s_ki
+ * (minimum image for periodic CVs), and
+ * dV/dxi_i = -sum_k w_k exp(...) D_ki / sigma_i^2.
+ * Hills are summed in deposition order.  xi and dV are [P][d]; hills are
+ * [H][4] = (s_0, s_1, s_2, w). */
+void orc_hills_sum(int64_t d, int64_t P, const double* xi, int64_t H, const double* hills, const double* sigma,
+                   const double* period, double* V, double* dV)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < P; ++p) {
+        double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = 0; k < H; ++k) {
+            double D[3], q = 0.0;
+            for (int64_t i = 0; i < d; ++i) {
+                D[i] = xi[d * p + i] - hills[4 * k + i];
+                if (period && period[i] > 0.0) D[i] -= period[i] * nearbyint(D[i] / period[i]);
+                q += D[i] * D[i] / (2.0 * sigma[i] * sigma[i]);
+            }
+            double e = hills[4 * k + 3] * exp(-q);
+            v += e;
+            for (int64_t i = 0; i < d; ++i) g[i] -= e * D[i] / (sigma[i] * sigma[i]);
+        }
+        V[p] = v;
+        for (int64_t i = 0; i < d; ++i) dV[d * p + i] = g[i];
+    }
+}
+
+/* Hill height.  Standard metadynamics keeps it fixed (Sec. 2.1.5); the
+ * well-tempered variant scales it with the bias factor gamma (Barducci,
+ * Bussi & Parrinello 2008, cited in Sec. 2.1.5; the formula is not printed
+ * in the paper): w = w0 exp(-V(s) / (kT (gamma - 1))), i.e. Delta T =
+ * (gamma - 1) T.  gamma = 0 or infinite selects the standard method. */
+double orc_wt_height(double V, double w0, double kT, double gamma)
+{
+    if (gamma == 0.0 || isinf(gamma)) return w0;
+    return w0 * exp(-V / (kT * (gamma - 1.0)));
+}
+
+/* Grid storage of the bias (Sec. 2.1.5, optional grid): cell-centred grid,
+ * C order (last CV fastest), every cell gets w exp(-sum D^2/(2 sigma^2)). */
+void orc_grid_add(int64_t d, const int64_t* bins, const double* lo, const double* hi, const double* period,
+                  const double* sigma, const double* s, double w, double* grid)
+{
+    int64_t n = 1;
+    for (int64_t i = 0; i < d; ++i) n *= bins[i];
+#pragma omp parallel for schedule(static)
+    for (int64_t cell = 0; cell < n; ++cell) {
+        int64_t rem = cell;
+        double q = 0.0;
+        for (int64_t i = d - 1; i >= 0; --i) {
+            int64_t k = rem % bins[i];
+            rem /= bins[i];
+            double c = lo[i] + ((double)k + 0.5) * (hi[i] - lo[i]) / (double)bins[i];
+            double D = c - s[i];
+            if (period && period[i] > 0.0) D -= period[i] * nearbyint(D / period[i]);
+            q += D * D / (2.0 * sigma[i] * sigma[i]);
+        }
+        grid[cell] += w * exp(-q);
+    }
+}
+
+/* Free-energy estimate from the WT bias: A = -(gamma/(gamma-1)) V + C,
+ * (standard metadynamics: A = -V + C); C puts the minimum at zero.
+ * Meaning of A: Sec. 2.1, Eq. (free-energy). */
+void orc_fes(int64_t n, const double* grid, double gamma, double* out)
+{
+    double f = (gamma == 0.0 || isinf(gamma)) ? -1.0 : -gamma / (gamma - 1.0);
+    double mn = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        out[i] = f * grid[i];
+        if (out[i] < mn) mn = out[i];
+    }
+    for (int64_t i = 0; i < n; ++i) out[i] -= mn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole system: engine + bias + BAOAB + deposition                          */
+/* ------------------------------------------------------------------------ */
+enum { ORC_ENGINE_NONE = 0, ORC_ENGINE_MB = 1, ORC_ENGINE_LJ = 2, ORC_ENGINE_CHAIN = 3, ORC_ENGINE_HARMONIC = 4 };
+
+typedef struct {
+    int64_t engine;
+    int64_t dims;             /* integrated spatial dimensions: 2 (MB) or 3 */
+    int64_t n_walkers;
+    const int64_t* walker_off;
+    const int64_t* walker_n;
+    double box[3];            /* > 0: periodic */
+    double dt, friction, mass, kT;
+    uint64_t seed;
+    double lj_eps, lj_sig, lj_rc;
+    double bond_k, bond_r0, angle_k, angle_t0, tors_k;
+    double harm_k;
+    int64_t n_cv;
+    const orc_cv* cv;
+    double sigma[3];
+    double w0, gamma;
+    int64_t stride;
+    int64_t hill_cap;
+    int64_t grid_bins[3];     /* all zero: no grid */
+    double grid_lo[3], grid_hi[3];
+    int64_t bias_on;
+} orc_sys;
+
+typedef struct {
+    double* x;      /* [N][3] */
+    double* v;      /* [N][3] */
+    double* f;      /* [N][3] total force at x */
+    double* hills;  /* [hill_cap][4] */
+    int64_t n_hills;
+    double* grid;   /* [prod bins] or NULL */
+    int64_t step;
+    double* xi;     /* [W][3] CVs at x */
+    double* V;      /* [W] bias at x (hills before any deposit at this step) */
+    double* dV;     /* [W][3] */
+} orc_state;
+
+static int64_t orc_total_atoms(const orc_sys* s)
+{
+    int64_t w = s->n_walkers - 1;
+    return s->walker_off[w] + s->walker_n[w];
+}
+
+static void orc_periods(const orc_sys* s, double* period)
+{
+    for (int i = 0; i < 3; ++i) period[i] = (i < s->n_cv) ? s->cv[i].period : 0.0;
+}
+
+/* Engine force for every walker into f (overwritten). */
+static void orc_engine(const orc_sys* s, const double* x, double* f)
+{
+    int64_t N = orc_total_atoms(s);
+    for (int64_t i = 0; i < 3 * N; ++i) f[i] = 0.0;
+    for (int64_t w = 0; w < s->n_walkers; ++w) {
+        int64_t o = s->walker_off[w], n = s->walker_n[w];
+        const double* xw = &x[3 * o];
+        double* fw = &f[3 * o];
+        switch (s->engine) {
+        case ORC_ENGINE_MB:
+            for (int64_t i = 0; i < n; ++i) orc_mb(xw[3 * i], xw[3 * i + 1], &fw[3 * i], &fw[3 * i + 1]);
+            break;
+        case ORC_ENGINE_LJ:
+            orc_lj(n, xw, s->box, s->lj_eps, s->lj_sig, s->lj_rc, fw);
+            break;
+        case ORC_ENGINE_CHAIN:
+            orc_chain(n, xw, s->bond_k, s->bond_r0, s->angle_k, s->angle_t0, s->tors_k, fw);
+            break;
+        case ORC_ENGINE_HARMONIC:
+            for (int64_t i = 0; i < 3 * n; ++i) fw[i] = -s->harm_k * xw[i];
+            break;
+        default:
+            break;
+        }
+    }
+}
+
+/* Bias at x: CVs, hills sum over the first H hills, and f -= J^T dV/dxi
+ * for every walker.  xi, V, dV receive the per-walker values. */
+int orc_bias(const orc_sys* s, const double* x, const double* hills, int64_t H, double* f, double* xi, double* V,
+             double* dV)
+{
+    double period[3];
+    orc_periods(s, period);
+    int64_t d = s->n_cv;
+    for (int64_t w = 0; w < s->n_walkers; ++w) {
+        int64_t o = s->walker_off[w], n = s->walker_n[w];
+        double* J = (double*)malloc(sizeof(double) * 3 * (size_t)n * (size_t)d);
+        double xw[3] = {0.0, 0.0, 0.0}, vw, gw[3] = {0.0, 0.0, 0.0};
+        for (int64_t c = 0; c < d; ++c)
+            if (orc_cv_eval(&s->cv[c], n, &x[3 * o], s->box, &xw[c], &J[3 * n * c]) != 0) {
+                free(J);
+                return -1;
+            }
+        orc_hills_sum(d, 1, xw, H, hills, s->sigma, period, &vw, gw);
+        for (int64_t c = 0; c < d; ++c)
+            for (int64_t i = 0; i < 3 * n; ++i) f[3 * o + i] -= gw[c] * J[3 * n * c + i];
+        for (int64_t c = 0; c < 3; ++c) {
+            xi[3 * w + c] = xw[c];
+            dV[3 * w + c] = c < d ? gw[c] : 0.0;
+        }
+        V[w] = vw;
+        free(J);
+    }
+    return 0;
+}
+
+/* Total force (engine + bias) at the current positions; fills xi, V, dV. */
+int orc_forces(const orc_sys* s, orc_state* st)
+{
+    orc_engine(s, st->x, st->f);
+    if (!s->bias_on) return 0;
+    return orc_bias(s, st->x, st->hills, st->n_hills, st->f, st->xi, st->V, st->dV);
+}
+
+/* n steps of BAOAB Langevin dynamics (Leimkuhler & Matthews 2013):
+ *   B: v += dt/2 F/m;  A: x += dt/2 v;  O: v = c1 v + sqrt((1-c1^2) kT/m) R;
+ *   A: x += dt/2 v;  forces at the new x (engine + bias);  B: v += dt/2 F/m;
+ * c1 = exp(-friction dt).  After a step t (counted from 0) with
+ * (t+1) % stride == 0 every walker deposits one hill at s = xi(x_{t+1}) with
+ * the height from the bias V(s) of the hills that existed before this step's
+ * deposits (walkers in index order); the grid, when present, gets the same
+ * Gaussian.  Positions are not wrapped into the box; every distance uses the
+ * minimum image.  Returns 0, or -3 when the hill capacity is exceeded. */
+int orc_run(const orc_sys* s, orc_state* st, int64_t nsteps)
+{
+    int64_t N = orc_total_atoms(s);
+    double c1 = exp(-s->friction * s->dt);
+    double c2 = sqrt((1.0 - c1 * c1) * s->kT / s->mass);
+    double half = 0.5 * s->dt;
+    double period[3];
+    orc_periods(s, period);
+    int has_grid = s->grid_bins[0] > 0;
+    int rc = 0;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        int64_t t = st->step;
+        for (int64_t i = 0; i < N; ++i) {
+            double g[3];
+            orc_noise3(s->seed, (uint64_t)t, (uint32_t)i, g);
+            for (int64_t k = 0; k < s->dims; ++k) {
+                double* x = &st->x[3 * i + k];
+                double* v = &st->v[3 * i + k];
+                *v += half * st->f[3 * i + k] / s->mass;
+                *x += half * (*v);
+                *v = c1 * (*v) + c2 * g[k];
+                *x += half * (*v);
+            }
+        }
+        if (orc_forces(s, st) != 0) return -1;
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t k = 0; k < s->dims; ++k) st->v[3 * i + k] += half * st->f[3 * i + k] / s->mass;
+        st->step = t + 1;
+        if (s->bias_on && s->stride > 0 && (t + 1) % s->stride == 0) {
+            if (st->n_hills + s->n_walkers > s->hill_cap) {
+                rc = -3;
+                continue;
+            }
+            for (int64_t w = 0; w < s->n_walkers; ++w) {
+                double* h = &st->hills[4 * st->n_hills];
+                for (int c = 0; c < 3; ++c) h[c] = c < s->n_cv ? st->xi[3 * w + c] : 0.0;
+                h[3] = orc_wt_height(st->V[w], s->w0, s->kT, s->gamma);
+                st->n_hills += 1;
+                if (has_grid) {
+                    int64_t bins[3] = {s->grid_bins[0], s->grid_bins[1], s->grid_bins[2]};
+                    orc_grid_add(s->n_cv, bins, s->grid_lo, s->grid_hi, period, s->sigma, h, h[3], st->grid);
+                }
+            }
+        }
+    }
+    return rc;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
