@@ -150,7 +150,7 @@ double orc_lj(int64_t n, const double* x, const double* box, double eps, double 
     double U = 0.0;
 #pragma omp parallel for reduction(+ : U) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        double fi[3] = {0.0, 0.0, 0.0};
+        long double fi[3] = {0.0L, 0.0L, 0.0L}; /* terms of both signs cancel: extended precision */
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];
@@ -163,7 +163,7 @@ double orc_lj(int64_t n, const double* x, const double* box, double eps, double 
             for (int k = 0; k < 3; ++k) fi[k] += fr * d[k];
             U += 0.5 * (4.0 * eps * (sr6 * sr6 - sr6) - ushift);
         }
-        for (int k = 0; k < 3; ++k) f[3 * i + k] = fi[k];
+        for (int k = 0; k < 3; ++k) f[3 * i + k] = (double)fi[k];
     }
     return U;
 }
@@ -312,7 +312,11 @@ int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box,
         int64_t na = cv->n_a < 0 ? n : cv->n_a;
         int64_t nb = cv->n_b < 0 ? n : cv->n_b;
         double sc = cv->scale != 0.0 ? cv->scale : 1.0 / (double)na;
-        double sum = 0.0;
+        /* sums over up to ~1e7 pair terms accumulate in extended precision
+         * so that the reference's own rounding stays far below the parity
+         * tolerances */
+        long double sum = 0.0L;
+        long double* Jl = (long double*)calloc(3 * (size_t)n, sizeof(long double));
         for (int64_t p = 0; p < na; ++p) {
             int64_t i = orc_group(cv->n_a, cv->a, n, p);
             for (int64_t q = 0; q < nb; ++q) {
@@ -322,12 +326,14 @@ int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box,
                 orc_delta(&x[3 * i], &x[3 * j], box, d);
                 sum += orc_switch(dot3(d, d), cv->r0, cv->nn, &gr);
                 for (int k = 0; k < 3; ++k) {
-                    J[3 * i + k] += sc * gr * d[k];
-                    J[3 * j + k] -= sc * gr * d[k];
+                    Jl[3 * i + k] += gr * d[k];
+                    Jl[3 * j + k] -= gr * d[k];
                 }
             }
         }
-        *xi = sc * sum;
+        for (int64_t i = 0; i < 3 * n; ++i) J[i] = (double)(sc * Jl[i]);
+        free(Jl);
+        *xi = (double)(sc * sum);
         return 0;
     }
     case ORC_CV_RG: {
@@ -338,21 +344,22 @@ int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box,
         int64_t m = cv->n_a < 0 ? n : cv->n_a;
         double* u = (double*)malloc(sizeof(double) * 3 * (size_t)m);
         int64_t i0 = orc_group(cv->n_a, cv->a, n, 0);
-        double c[3] = {0.0, 0.0, 0.0};
+        long double cl[3] = {0.0L, 0.0L, 0.0L};
         for (int64_t p = 0; p < m; ++p) {
             int64_t i = orc_group(cv->n_a, cv->a, n, p);
             double d[3];
             orc_delta(&x[3 * i], &x[3 * i0], box, d);
             for (int k = 0; k < 3; ++k) {
                 u[3 * p + k] = x[3 * i0 + k] + d[k];
-                c[k] += u[3 * p + k];
+                cl[k] += u[3 * p + k];
             }
         }
-        for (int k = 0; k < 3; ++k) c[k] /= (double)m;
-        double s2 = 0.0;
+        double c[3];
+        for (int k = 0; k < 3; ++k) c[k] = (double)(cl[k] / (long double)m);
+        long double s2 = 0.0L;
         for (int64_t p = 0; p < m; ++p)
             for (int k = 0; k < 3; ++k) s2 += (u[3 * p + k] - c[k]) * (u[3 * p + k] - c[k]);
-        double rg = sqrt(s2 / (double)m);
+        double rg = sqrt((double)(s2 / (long double)m));
         double sc = cv->scale != 0.0 ? cv->scale : 1.0;
         if (cv->flags & ORC_CV_INTENSIVE) sc /= cbrt((double)m);
         for (int64_t p = 0; p < m; ++p) {
@@ -368,18 +375,21 @@ int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box,
          * a fixed list of pairs a[2p], a[2p+1]. */
         int64_t np = cv->n_a / 2;
         double sc = cv->scale != 0.0 ? cv->scale : 1.0 / (double)np;
-        double sum = 0.0;
+        long double sum = 0.0L;
+        long double* Jl = (long double*)calloc(3 * (size_t)n, sizeof(long double));
         for (int64_t p = 0; p < np; ++p) {
             int64_t i = cv->a[2 * p], j = cv->a[2 * p + 1];
             double d[3], gr;
             orc_delta(&x[3 * i], &x[3 * j], box, d);
             sum += orc_switch(dot3(d, d), cv->r0, cv->nn, &gr);
             for (int k = 0; k < 3; ++k) {
-                J[3 * i + k] += sc * gr * d[k];
-                J[3 * j + k] -= sc * gr * d[k];
+                Jl[3 * i + k] += gr * d[k];
+                Jl[3 * j + k] -= gr * d[k];
             }
         }
-        *xi = sc * sum;
+        for (int64_t i = 0; i < 3 * n; ++i) J[i] = (double)(sc * Jl[i]);
+        free(Jl);
+        *xi = (double)(sc * sum);
         return 0;
     }
     default:
@@ -400,7 +410,8 @@ void orc_hills_sum(int64_t d, int64_t P, const double* xi, int64_t H, const doub
 {
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < P; ++p) {
-        double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+        /* extended-precision accumulators: up to 1e6 terms per point */
+        long double v = 0.0L, g[3] = {0.0L, 0.0L, 0.0L};
         for (int64_t k = 0; k < H; ++k) {
             double D[3], q = 0.0;
             for (int64_t i = 0; i < d; ++i) {
@@ -412,8 +423,8 @@ void orc_hills_sum(int64_t d, int64_t P, const double* xi, int64_t H, const doub
             v += e;
             for (int64_t i = 0; i < d; ++i) g[i] -= e * D[i] / (sigma[i] * sigma[i]);
         }
-        V[p] = v;
-        for (int64_t i = 0; i < d; ++i) dV[d * p + i] = g[i];
+        V[p] = (double)v;
+        for (int64_t i = 0; i < d; ++i) dV[d * p + i] = (double)g[i];
     }
 }
 

@@ -32,6 +32,25 @@ def fcc_lattice(n: int, rho: float, seed: int = 0, jitter: float = 0.0):
     return x.astype(np.float64), float(L)
 
 
+def lattice(n: int, rho: float, seed: int = 0, jitter: float = 0.0):
+    """n atoms on a cubic lattice at density rho: FCC when n = 4 k^3, simple
+    cubic when n = k^3 (e.g. 4096 = 16^3), with optional Gaussian jitter.
+    Returns (positions [n][3], box edge L)."""
+    k4 = int(round((n / 4) ** (1.0 / 3.0)))
+    if 4 * k4 ** 3 == n:
+        return fcc_lattice(n, rho, seed, jitter)
+    k = int(round(n ** (1.0 / 3.0)))
+    if k ** 3 != n:
+        raise ValueError("lattice needs n = 4 k^3 or k^3")
+    L = (n / rho) ** (1.0 / 3.0)
+    a = L / k
+    g = np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), -1).reshape(-1, 3)
+    x = (g + 0.5) * a
+    if jitter > 0:
+        x = x + rng(seed).normal(scale=jitter, size=x.shape)
+    return x.astype(np.float64), float(L)
+
+
 def random_liquid(n: int, L: float, seed: int, min_dist: float = 0.9, max_tries: int = 200):
     """n points in a cubic periodic box of edge L drawn one by one from a
     seeded uniform distribution, rejecting any closer than min_dist to an
