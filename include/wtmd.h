@@ -1,0 +1,210 @@
+/*
+ * wtmd.h -- C ABI of the B300 (sm_103a) well-tempered metadynamics
+ * bias-force library (libwtmd.so).
+ *
+ * The calls follow the problem statement of the PySAGES paper
+ * (arXiv 2301.04835):
+ *   - a sampling method has an initialize step that allocates its state and an
+ *     update step that advances it from the simulation's current snapshot
+ *     (Sec. 2.1, SamplingMethod.build -> initialize/update): wtmd_create,
+ *     cv_define, wtmd_bind, step_n;
+ *   - the method's update runs inside the engine's time step as a force-like
+ *     object whose biasing forces are added to the engine's net forces, with
+ *     device-resident particle data and no host copies (Sec. 2, Snapshot and
+ *     DLPack; Sec. 3.2.1 steps (a)-(f)): bias_eval, step_n;
+ *   - metadynamics deposits Gaussian hills of width sigma at user-defined
+ *     intervals, with fixed height (standard) or height scaled by a bias
+ *     factor (well-tempered), optionally storing the bias on a grid
+ *     (Sec. 2.1.5): hills_eval, wtmd_hills_load, wtmd_hills_read;
+ *   - analyze turns the method's state into a free energy
+ *     (Sec. 2, analyze; Sec. 2.1, Eq. (free-energy)): fes_grid;
+ *   - CV gradients, obtained in the paper by automatic differentiation
+ *     (Sec. 2, jax.grad), are a hand-written Jacobian and adjoint here:
+ *     wtmd_cv_forward, wtmd_cv_adjoint.
+ *
+ * Conventions
+ *   - Every call returns an int status: WTMD_OK (0) or a negative WTMD_E*
+ *     code; wtmd_last_error() gives a message for the last failing call on a
+ *     handle.  Calls are not thread-safe on one handle.
+ *   - Precision is fixed per handle (WTMD_F32 or WTMD_F64).  "Real" below is
+ *     float for WTMD_F32 and double for WTMD_F64.
+ *   - Particle arrays (positions, velocities, forces) are DEVICE pointers to
+ *     [n_atoms][4] Real (x, y, z, unused), 16-byte (F32) or 32-byte (F64)
+ *     aligned.  They are borrowed: the caller owns them and keeps them alive
+ *     while they are bound.  Walkers are contiguous, in walker order.
+ *   - Every kernel is enqueued on the handle's stream (wtmd_set_stream;
+ *     default: the legacy default stream).  Calls return after enqueueing;
+ *     wtmd_check() synchronizes the stream and reports any error a kernel
+ *     recorded (hill capacity, non-finite values, cell overflow, timeout).
+ *   - Device memory of the handle (hills, grid, scratch, graphs) is owned by
+ *     the handle and released by wtmd_destroy.
+ */
+#ifndef WTMD_H
+#define WTMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define WTMD_OK 0
+#define WTMD_EINVAL (-1)    /* bad argument, size, index or state */
+#define WTMD_ENOMEM (-2)    /* device allocation failed */
+#define WTMD_ECAPACITY (-3) /* hill list full: the deposit was skipped */
+#define WTMD_ENUMERIC (-4)  /* a kernel saw a non-finite CV, bias or force */
+#define WTMD_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define WTMD_ECUDA (-6)     /* a CUDA runtime call failed */
+#define WTMD_ECELL (-7)     /* a cell of the LJ cell list overflowed */
+
+/* ---- enumerations ---- */
+#define WTMD_F32 0
+#define WTMD_F64 1
+
+#define WTMD_ENGINE_NONE 0  /* no engine force (bias only) */
+#define WTMD_ENGINE_MB 1    /* Mueller-Brown 2-D potential on (x, y); z frozen */
+#define WTMD_ENGINE_LJ 2    /* 12-6 Lennard-Jones, cut and shifted at lj_rc */
+#define WTMD_ENGINE_CHAIN 3 /* bead chain: harmonic bonds/angles, k(1+cos 3 phi) torsions */
+
+#define WTMD_CV_COMPONENT 1    /* one coordinate of one atom (Sec. 2.2, AxisCV Component) */
+#define WTMD_CV_DIHEDRAL 2     /* IUPAC dihedral of 4 atoms (Sec. 2.2, FourPointCV DihedralAngle) */
+#define WTMD_CV_COORDINATION 3 /* sum_{i in A} sum_{j in B, j != i} 1/(1+(r_ij/r0)^n) (rational switch, m = 2n) */
+#define WTMD_CV_RG 4           /* radius of gyration of a group (Sec. 2.2, RadiusofGyration) */
+#define WTMD_CV_QPAIRS 5       /* mean switching function over a fixed list of pairs */
+
+#define WTMD_CV_INTENSIVE 1 /* RG only: divide by (group size)^(1/3) */
+
+/* ---- configuration (copied by wtmd_create) ---- */
+typedef struct wtmd_config {
+    int32_t precision;      /* WTMD_F32 or WTMD_F64 */
+    int32_t n_cv;           /* number of CVs d, 1..3 */
+    double sigma[3];        /* Gaussian widths per CV (Sec. 2.1.5) */
+    double w0;              /* initial hill height */
+    double gamma;           /* bias factor; 0 selects standard metadynamics (fixed heights) */
+    double kT;              /* thermal energy k_B T */
+    int64_t stride;         /* deposit one hill per walker every `stride` steps; 0 = never */
+    int64_t hill_capacity;  /* maximum number of hills */
+    uint64_t seed;          /* Philox key of the thermostat noise */
+    int32_t grid_bins[3];   /* cells per CV of the FP64 bias grid; all 0 = no grid */
+    int32_t engine;         /* WTMD_ENGINE_* */
+    double grid_lo[3];      /* grid range per CV (cell-centred cells) */
+    double grid_hi[3];
+    int32_t dims;           /* integrated spatial dimensions (2 or 3); 0 = 3 (2 for MB) */
+    int32_t n_walkers;      /* number of walkers W (>= 1) */
+    const int64_t* walker_size; /* host [W] atoms per walker (required; copied) */
+    double dt, friction, mass;  /* BAOAB time step, friction (1/time), particle mass */
+    double box[3];          /* periodic box edges; 0 = open in that direction */
+    double lj_eps, lj_sigma, lj_rc;
+    double bond_k, bond_r0, angle_k, angle_theta0, torsion_k;
+} wtmd_config;
+
+/* ---- one collective variable; indices are walker-local and host-side ---- */
+typedef struct wtmd_cv_desc {
+    int32_t kind;       /* WTMD_CV_* */
+    int32_t axis;       /* COMPONENT: 0, 1 or 2 */
+    int64_t n_a;        /* group A size; -1 = all atoms of the walker (COORDINATION, RG) */
+    const int32_t* a;   /* COMPONENT: 1 index; DIHEDRAL: 4; COORDINATION/RG: group A;
+                           QPAIRS: 2*npairs indices (i0, j0, i1, j1, ...) */
+    int64_t n_b;        /* COORDINATION partner group B size; -1 = all atoms */
+    const int32_t* b;
+    double r0;          /* switching distance */
+    int32_t nn, mm;     /* switching exponents; mm must equal 2*nn, nn even, 2..16 */
+    double scale;       /* CV multiplier; 0 = default (COORDINATION 1/|A|, QPAIRS 1/npairs, else 1) */
+    int32_t flags;      /* WTMD_CV_INTENSIVE */
+    int32_t reserved;
+    double period;      /* > 0: periodic CV (e.g. 2 pi for a dihedral); hill distances use the minimum image */
+} wtmd_cv_desc;
+
+typedef struct wtmd_t wtmd_t;
+
+/* Create a handle: allocates the hill list (hill_capacity), the bias grid,
+ * counters and per-walker scratch on the current CUDA device.
+ * Errors: WTMD_EINVAL (bad config), WTMD_ENOMEM, WTMD_ECUDA. */
+int wtmd_create(const wtmd_config* cfg, wtmd_t** out);
+
+/* Release everything the handle owns (not the bound particle arrays). */
+int wtmd_destroy(wtmd_t* h);
+
+/* Message of the last error on this handle (never NULL). */
+const char* wtmd_last_error(const wtmd_t* h);
+
+/* Enqueue subsequent work on `stream` (a cudaStream_t; NULL = default). */
+int wtmd_set_stream(wtmd_t* h, void* stream);
+
+/* Define the next CV (ids 0..n_cv-1 in call order).  Index lists are copied
+ * to the device.  Errors: WTMD_EINVAL (kind, index out of the walker, wrong
+ * count, duplicate atoms, mm != 2 nn, more than n_cv CVs). */
+int cv_define(wtmd_t* h, const wtmd_cv_desc* desc, int32_t* cv_id);
+
+/* Bind the engine's particle arrays (device, [n_atoms][4] Real).  n_atoms
+ * must equal the sum of walker sizes.  Marks forces stale: the next step_n
+ * first computes the total force at the bound positions. */
+int wtmd_bind(wtmd_t* h, void* pos, void* vel, void* force, int64_t n_atoms);
+
+/* Advance the bound system n_steps BAOAB steps: engine force, CVs, hills
+ * sum, bias-force scatter into the force array, integration, and deposition
+ * every `stride` steps (one hill per walker, well-tempered height).  Runs as
+ * replays of a captured CUDA graph; no host synchronization inside.  Errors
+ * recorded by kernels surface at wtmd_check(). */
+int step_n(wtmd_t* h, int64_t n_steps);
+
+/* Synchronize the handle's stream and return the first error a kernel
+ * recorded since the last check (WTMD_ECAPACITY, WTMD_ENUMERIC, WTMD_ECELL,
+ * WTMD_ETIMEOUT), or a CUDA error; clears the recorded status. */
+int wtmd_check(wtmd_t* h);
+
+/* One bias evaluation at `pos` (device [n_atoms][4] Real): CVs, hills sum over
+ * the current hills, and force_inout -= J^T dV/dxi for every walker (force
+ * may be NULL: nothing is scattered).  Outputs (device, may be NULL):
+ * V_out [W] Real, xi_out [W][n_cv] Real, dV_out [W][n_cv] Real.  Does not
+ * deposit and does not touch the bound arrays. */
+int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_out, void* xi_out, void* dV_out);
+
+/* Hills sum alone at P points: xi (device [P][n_cv] Real) ->
+ * V_out [P] Real, dV_out [P][n_cv] Real (device). */
+int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out);
+
+/* Free-energy estimate on the grid: out (device, [prod grid_bins] double,
+ * C order, last CV fastest) = -(gamma/(gamma-1)) V_grid (standard
+ * metadynamics: -V_grid), shifted so that its minimum is 0.
+ * Errors: WTMD_EINVAL (no grid, n_out too small). */
+int fes_grid(wtmd_t* h, double* out, int64_t n_out);
+
+/* Replace the hill list by `count` hills from host memory [count][4] double
+ * (s0, s1, s2, w); the grid is rebuilt from them.  Errors: WTMD_EINVAL
+ * (count > capacity, w <= 0 or non-finite). */
+int wtmd_hills_load(wtmd_t* h, const double* hills_host, int64_t count);
+
+/* Copy the hill list to host memory [capacity_out][4] double; *count gets
+ * the number of hills (synchronizes the stream). */
+int wtmd_hills_read(wtmd_t* h, double* hills_host, int64_t capacity_out, int64_t* count);
+
+/* Read the step counter and the hill count (synchronizes the stream). */
+int wtmd_counters(wtmd_t* h, int64_t* step, int64_t* n_hills);
+
+/* Copy the FP64 bias grid (device) to host memory [n_out] double. */
+int wtmd_grid_read(wtmd_t* h, double* out_host, int64_t n_out);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device for n blocks: in_host
+ * [n][6] uint32 (ctr0..3, key0..1) -> out_host [n][4] uint32.  Exposes the
+ * generator behind the thermostat noise for bitwise checks. */
+int wtmd_philox(const uint32_t* in_host, uint32_t* out_host, int64_t n);
+
+/* Run n_steps eager (non-graph) MD steps with a CUDA event recorded on the
+ * handle's stream after every kernel; return the mean time per kernel:
+ * names [cap][32] (NUL-terminated) and ms [cap]; *n_marks = kernels per step.
+ * Used to time kernels live for roofline reporting.  Synchronizes. */
+int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32_t cap, int32_t* n_marks);
+
+/* Throughput probe of one SM pipe on the current device (not part of the
+ * method): kind 0 = MUFU ex2.approx per second, kind 1 = FP32 FMA lane
+ * operations per second (packed FFMA2 counted as two FMAs).  Gives the
+ * measured denominators of the hills-sum roofline; *ms = kernel time. */
+int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WTMD_H */

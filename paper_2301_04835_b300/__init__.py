@@ -1,0 +1,325 @@
+"""Python binding of libwtmd, the B300 well-tempered metadynamics library.
+
+Argument marshalling only: every step of the bias-force path runs in the
+CUDA kernels of libwtmd.so (built from csrc/ by `build.py`).  PyTorch
+provides device memory and the stream; there is no CPU fallback -- importing
+the binding without the built library raises.
+
+    import paper_2301_04835_b300 as wt
+    m = wt.Wtmd(precision="f32", sigma=(0.05, 0.1), w0=1.0, gamma=8.0, kT=1.0,
+                stride=100, capacity=100000, walker_sizes=[N], engine="lj",
+                box=(L, L, L), dt=0.005)
+    m.cv_define(wt.CV_COORDINATION, a=tagged, r0=1.5, nn=6, mm=12)
+    m.cv_define(wt.CV_RG, a=subset)
+    m.bind(pos, vel, force)          # torch CUDA tensors [N, 4]
+    m.step_n(1000)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwtmd.so")
+
+OK, EINVAL, ENOMEM, ECAPACITY, ENUMERIC, ETIMEOUT, ECUDA, ECELL = 0, -1, -2, -3, -4, -5, -6, -7
+F32, F64 = 0, 1
+ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN = 0, 1, 2, 3
+CV_COMPONENT, CV_DIHEDRAL, CV_COORDINATION, CV_RG, CV_QPAIRS = 1, 2, 3, 4, 5
+CV_INTENSIVE = 1
+_ENGINES = {"none": ENGINE_NONE, "mb": ENGINE_MB, "lj": ENGINE_LJ, "chain": ENGINE_CHAIN}
+
+
+class WtmdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libwtmd error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    """Mirror of wtmd_config (include/wtmd.h)."""
+    _fields_ = [
+        ("precision", C.c_int32), ("n_cv", C.c_int32), ("sigma", C.c_double * 3), ("w0", C.c_double),
+        ("gamma", C.c_double), ("kT", C.c_double), ("stride", C.c_int64), ("hill_capacity", C.c_int64),
+        ("seed", C.c_uint64), ("grid_bins", C.c_int32 * 3), ("engine", C.c_int32),
+        ("grid_lo", C.c_double * 3), ("grid_hi", C.c_double * 3), ("dims", C.c_int32), ("n_walkers", C.c_int32),
+        ("walker_size", C.POINTER(C.c_int64)), ("dt", C.c_double), ("friction", C.c_double), ("mass", C.c_double),
+        ("box", C.c_double * 3), ("lj_eps", C.c_double), ("lj_sigma", C.c_double), ("lj_rc", C.c_double),
+        ("bond_k", C.c_double), ("bond_r0", C.c_double), ("angle_k", C.c_double), ("angle_theta0", C.c_double),
+        ("torsion_k", C.c_double),
+    ]
+
+
+class CvDesc(C.Structure):
+    """Mirror of wtmd_cv_desc (include/wtmd.h)."""
+    _fields_ = [
+        ("kind", C.c_int32), ("axis", C.c_int32), ("n_a", C.c_int64), ("a", C.POINTER(C.c_int32)),
+        ("n_b", C.c_int64), ("b", C.POINTER(C.c_int32)), ("r0", C.c_double), ("nn", C.c_int32), ("mm", C.c_int32),
+        ("scale", C.c_double), ("flags", C.c_int32), ("reserved", C.c_int32), ("period", C.c_double),
+    ]
+
+
+EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", "cv_define", "wtmd_bind", "step_n",
+           "wtmd_check", "bias_eval", "hills_eval", "fes_grid", "wtmd_hills_load", "wtmd_hills_read",
+           "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak"]
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libwtmd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2301_04835_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    L.wtmd_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+    L.wtmd_destroy.argtypes = [vp]
+    L.wtmd_last_error.argtypes = [vp]
+    L.wtmd_last_error.restype = C.c_char_p
+    L.wtmd_set_stream.argtypes = [vp, vp]
+    L.cv_define.argtypes = [vp, C.POINTER(CvDesc), C.POINTER(i32)]
+    L.wtmd_bind.argtypes = [vp, vp, vp, vp, i64]
+    L.step_n.argtypes = [vp, i64]
+    L.wtmd_check.argtypes = [vp]
+    L.bias_eval.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.hills_eval.argtypes = [vp, vp, i64, vp, vp]
+    L.fes_grid.argtypes = [vp, vp, i64]
+    L.wtmd_hills_load.argtypes = [vp, C.POINTER(C.c_double), i64]
+    L.wtmd_hills_read.argtypes = [vp, C.POINTER(C.c_double), i64, C.POINTER(i64)]
+    L.wtmd_counters.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.wtmd_grid_read.argtypes = [vp, C.POINTER(C.c_double), i64]
+    L.wtmd_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64]
+    L.wtmd_profile_step.argtypes = [vp, i64, C.c_char_p, C.POINTER(C.c_double), i32, C.POINTER(i32)]
+    L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    for name in EXPORTS:
+        if not hasattr(L, name):
+            raise ImportError(f"libwtmd.so lacks {name}")
+        if name != "wtmd_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def philox(ctr_key: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 on the device: [n][6] uint32 (ctr0..3, key0..1) -> [n][4]."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32)
+    out = np.zeros((a.shape[0], 4), dtype=np.uint32)
+    rc = lib().wtmd_philox(a.ctypes.data_as(C.POINTER(C.c_uint32)), out.ctypes.data_as(C.POINTER(C.c_uint32)),
+                           a.shape[0])
+    if rc:
+        raise WtmdError(rc, "wtmd_philox")
+    return out
+
+
+class Wtmd:
+    """One WTMD handle (wtmd_t).  Tensors passed in are CUDA tensors of the
+    handle's precision, [n_atoms, 4] for particle arrays."""
+
+    def __init__(self, *, precision="f32", sigma, w0=1.0, gamma=10.0, kT=1.0, stride=100, capacity=100000,
+                 seed=0, grid=None, engine="none", dims=0, walker_sizes, dt=1e-3, friction=1.0, mass=1.0,
+                 box=(0.0, 0.0, 0.0), lj=(1.0, 1.0, 2.5), chain=(100.0, 1.0, 50.0, float(np.deg2rad(109.47)), 1.0)):
+        torch = _torch()
+        self.prec = F32 if precision in ("f32", F32) else F64
+        self.dtype = torch.float32 if self.prec == F32 else torch.float64
+        self.d = len(sigma)
+        self.W = len(walker_sizes)
+        self.N = int(np.sum(walker_sizes))
+        self._ws = (C.c_int64 * self.W)(*[int(v) for v in walker_sizes])
+        c = Config()
+        c.precision, c.n_cv = self.prec, self.d
+        c.sigma = (C.c_double * 3)(*(list(sigma) + [1.0] * (3 - self.d)))
+        c.w0, c.gamma, c.kT = w0, gamma, kT
+        c.stride, c.hill_capacity, c.seed = int(stride), int(capacity), int(seed)
+        if grid is not None:
+            bins, lo, hi = grid
+            c.grid_bins = (C.c_int32 * 3)(*(list(bins) + [0] * (3 - len(bins))))
+            c.grid_lo = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+            c.grid_hi = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+            self.grid_shape = tuple(bins)
+        else:
+            self.grid_shape = None
+        c.engine = _ENGINES[engine] if isinstance(engine, str) else int(engine)
+        c.dims, c.n_walkers = int(dims), self.W
+        c.walker_size = C.cast(self._ws, C.POINTER(C.c_int64))
+        c.dt, c.friction, c.mass = dt, friction, mass
+        c.box = (C.c_double * 3)(*box)
+        c.lj_eps, c.lj_sigma, c.lj_rc = lj
+        c.bond_k, c.bond_r0, c.angle_k, c.angle_theta0, c.torsion_k = chain
+        self.cfg = c
+        h = C.c_void_p()
+        torch.cuda.init()
+        rc = lib().wtmd_create(C.byref(c), C.byref(h))
+        if rc:
+            raise WtmdError(rc, "wtmd_create rejected the configuration")
+        self.h = h
+        self._keep = []
+
+    # ------------------------------------------------------------------
+    def _err(self, rc, what):
+        if rc:
+            msg = lib().wtmd_last_error(self.h)
+            raise WtmdError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def _stream(self):
+        s = _torch().cuda.current_stream().cuda_stream
+        lib().wtmd_set_stream(self.h, C.c_void_p(s))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().wtmd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_tensor(self, t, shape=None):
+        torch = _torch()
+        if t is None:
+            return None
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA {self.dtype} tensor")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return C.c_void_p(t.data_ptr())
+
+    # ------------------------------------------------------------------
+    def cv_define(self, kind, a=None, b=None, axis=0, r0=1.5, nn=6, mm=12, scale=0.0, flags=0, period=0.0) -> int:
+        d = CvDesc()
+        d.kind, d.axis, d.r0, d.nn, d.mm, d.scale, d.flags, d.period = kind, axis, r0, nn, mm, scale, flags, period
+        for nm in ("a", "b"):
+            arr = locals()[nm]
+            if arr is None:
+                setattr(d, "n_" + nm, -1)
+            else:
+                arr = np.ascontiguousarray(np.asarray(arr, dtype=np.int32))
+                self._keep.append(arr)
+                setattr(d, "n_" + nm, arr.size)
+                setattr(d, nm, arr.ctypes.data_as(C.POINTER(C.c_int32)))
+        cid = C.c_int32()
+        self._err(lib().cv_define(self.h, C.byref(d), C.byref(cid)), "cv_define")
+        return cid.value
+
+    def bind(self, pos, vel, force):
+        self._bound = (pos, vel, force)
+        self._err(lib().wtmd_bind(self.h, self._check_tensor(pos, (self.N, 4)), self._check_tensor(vel, (self.N, 4)),
+                                  self._check_tensor(force, (self.N, 4)), self.N), "wtmd_bind")
+
+    def step_n(self, n: int, check: bool = True):
+        self._stream()
+        self._err(lib().step_n(self.h, int(n)), "step_n")
+        if check:
+            self.check()
+
+    def check(self):
+        self._stream()
+        self._err(lib().wtmd_check(self.h), "wtmd_check")
+
+    def bias_eval(self, pos, force=None):
+        """Returns (V [W], xi [W, d], dV [W, d]); force (if given) -= J^T dV."""
+        torch = _torch()
+        self._stream()
+        V = torch.empty(self.W, dtype=self.dtype, device=pos.device)
+        xi = torch.empty(self.W, self.d, dtype=self.dtype, device=pos.device)
+        dV = torch.empty(self.W, self.d, dtype=self.dtype, device=pos.device)
+        self._err(lib().bias_eval(self.h, self._check_tensor(pos, (self.N, 4)),
+                                  self._check_tensor(force, (self.N, 4)) if force is not None else None,
+                                  C.c_void_p(V.data_ptr()), C.c_void_p(xi.data_ptr()), C.c_void_p(dV.data_ptr())),
+                  "bias_eval")
+        return V, xi, dV
+
+    def hills_eval(self, xi):
+        torch = _torch()
+        self._stream()
+        P = xi.shape[0]
+        V = torch.empty(P, dtype=self.dtype, device=xi.device)
+        dV = torch.empty(P, self.d, dtype=self.dtype, device=xi.device)
+        self._err(lib().hills_eval(self.h, self._check_tensor(xi, (P, self.d)), P, C.c_void_p(V.data_ptr()),
+                                   C.c_void_p(dV.data_ptr())), "hills_eval")
+        return V, dV
+
+    def hills_eval_into(self, xi, V, dV):
+        """hills_eval into preallocated outputs (no allocation; for timing)."""
+        self._err(lib().hills_eval(self.h, C.c_void_p(xi.data_ptr()), xi.shape[0], C.c_void_p(V.data_ptr()),
+                                   C.c_void_p(dV.data_ptr())), "hills_eval")
+
+    def profile_step(self, n_steps: int = 20):
+        """Mean device time per kernel of an MD step ({name: ms}), measured
+        with CUDA events on the launching stream (eager launches)."""
+        self._stream()
+        cap = 64
+        names = C.create_string_buffer(32 * cap)
+        ms = (C.c_double * cap)()
+        n = C.c_int32()
+        self._err(lib().wtmd_profile_step(self.h, int(n_steps), names, ms, cap, C.byref(n)), "wtmd_profile_step")
+        out = []
+        for i in range(n.value):
+            nm = names.raw[32 * i: 32 * i + 32].split(b"\0", 1)[0].decode()
+            out.append((nm, ms[i]))
+        return out
+
+    def fes_grid(self):
+        torch = _torch()
+        self._stream()
+        n = int(np.prod(self.grid_shape))
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        self._err(lib().fes_grid(self.h, C.c_void_p(out.data_ptr()), n), "fes_grid")
+        return out.reshape(self.grid_shape)
+
+    def hills_load(self, hills):
+        self._stream()
+        h = np.ascontiguousarray(np.asarray(hills, dtype=np.float64).reshape(-1, 4))
+        self._err(lib().wtmd_hills_load(self.h, h.ctypes.data_as(C.POINTER(C.c_double)), h.shape[0]),
+                  "wtmd_hills_load")
+
+    def hills_read(self) -> np.ndarray:
+        self._stream()
+        cnt = C.c_int64()
+        self._err(lib().wtmd_hills_read(self.h, None, 0, C.byref(cnt)), "wtmd_hills_read")
+        out = np.zeros((max(cnt.value, 1), 4))
+        self._err(lib().wtmd_hills_read(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), cnt.value, C.byref(cnt)),
+                  "wtmd_hills_read")
+        return out[: cnt.value]
+
+    def counters(self):
+        self._stream()
+        s, c = C.c_int64(), C.c_int64()
+        self._err(lib().wtmd_counters(self.h, C.byref(s), C.byref(c)), "wtmd_counters")
+        return s.value, c.value
+
+    def grid_read(self) -> np.ndarray:
+        self._stream()
+        n = int(np.prod(self.grid_shape))
+        out = np.zeros(n)
+        self._err(lib().wtmd_grid_read(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), n), "wtmd_grid_read")
+        return out.reshape(self.grid_shape)
+
+
+def probe_peak(kind: int):
+    """Measured pipe throughput: kind 0 = MUFU ex2/s, 1 = FP32 FMA lane-ops/s."""
+    v, ms = C.c_double(), C.c_double()
+    rc = lib().wtmd_probe_peak(kind, C.byref(v), C.byref(ms))
+    if rc:
+        raise WtmdError(rc, "wtmd_probe_peak")
+    return v.value, ms.value
+
+
+def particles(x, dtype, device="cuda"):
+    """[N,3] array -> contiguous [N,4] CUDA tensor of the handle's precision."""
+    torch = _torch()
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    t = torch.zeros(x.shape[0], 4, dtype=dtype)
+    t[:, :3] = torch.from_numpy(x).to(dtype)
+    return t.to(device).contiguous()

@@ -1,0 +1,611 @@
+// C ABI of libwtmd (declared in include/wtmd.h): handle lifetime, argument
+// checks, and the per-step launch sequence captured once into a CUDA graph.
+//
+// One MD step (PySAGES paper, Sec. 3.2.1 steps (a)-(f), with the method's
+// update inside the step as the paper's force-like object, Sec. 2):
+//   (a) B-A-O-A half of BAOAB with Philox noise;
+//   (b,c) engine forces at the new positions;
+//   (d) CVs and their Jacobians;  hills sum V, dV/dxi;
+//   (e) bias-force scatter F -= J^T dV/dxi, fused with (f) the closing B;
+//   deposition every `stride` steps (Sec. 2.1.5), FP64 grid update, step++.
+// The step counter and the hill count live in device memory, so one captured
+// graph replays for the whole run while the hill list grows.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "wtmd_internal.cuh"
+
+using namespace wtmd;
+
+namespace wtmd {
+void store_hills32_range(wtmd_t* h, long long k0, long long k1);
+int launch_hills_partial_prealloc(wtmd_t* h, int64_t P);
+}  // namespace wtmd
+
+static const int kGraphSteps = 8;
+
+#define FAIL(h, code, msg)    \
+    do {                      \
+        (h)->err = (msg);     \
+        return (code);        \
+    } while (0)
+
+static double c_lo(const wtmd_config* c, int i) { return c->grid_lo[i]; }
+static double c_hi(const wtmd_config* c, int i) { return c->grid_hi[i]; }
+
+static size_t realsz(const wtmd_t* h) { return h->prec == WTMD_F32 ? sizeof(float) : sizeof(double); }
+static size_t r4sz(const wtmd_t* h) { return h->prec == WTMD_F32 ? sizeof(float4) : sizeof(dbl4); }
+
+__global__ static void pad_hills32_kernel(float4* p, long long npairs)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs) return;
+    p[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    p[2 * i + 1] = make_float4(0.f, 0.f, INFINITY, INFINITY);
+}
+
+static void drop_graphs(wtmd_t* h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph1) cudaGraphExecDestroy(h->graph1);
+    h->graph = nullptr;
+    h->graph1 = nullptr;
+}
+
+static void free_cv(CvDev& c)
+{
+    cudaFree(c.a);
+    cudaFree(c.b);
+    cudaFree(c.inv_a);
+    cudaFree(c.inv_b);
+    cudaFree(c.q_rowptr);
+    cudaFree(c.q_items);
+    cudaFree(c.part_row);
+    cudaFree(c.part_col);
+    c = CvDev();
+}
+
+extern "C" int wtmd_destroy(wtmd_t* h)
+{
+    if (!h) return WTMD_EINVAL;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaDeviceSynchronize();
+    drop_graphs(h);
+    for (int i = 0; i < h->ncv; ++i) free_cv(h->cv[i]);
+    void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status,
+                    h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
+                    h->cell_atoms};
+    for (void* p : ptrs) cudaFree(p);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return WTMD_OK;
+}
+
+extern "C" const char* wtmd_last_error(const wtmd_t* h)
+{
+    if (!h) return "null handle";
+    return h->err.c_str();
+}
+
+extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
+{
+    if (!cfg || !out) return WTMD_EINVAL;
+    *out = nullptr;
+    const wtmd_config& c = *cfg;
+    if (c.precision != WTMD_F32 && c.precision != WTMD_F64) return WTMD_EINVAL;
+    if (c.n_cv < 1 || c.n_cv > 3) return WTMD_EINVAL;
+    for (int i = 0; i < c.n_cv; ++i)
+        if (!(c.sigma[i] > 0.0) || !isfinite(c.sigma[i])) return WTMD_EINVAL;
+    if (!(c.w0 > 0.0) || !isfinite(c.w0)) return WTMD_EINVAL;
+    if (!(c.gamma == 0.0 || isinf(c.gamma) || c.gamma > 1.0)) return WTMD_EINVAL;
+    if (!(c.kT > 0.0)) return WTMD_EINVAL;
+    if (c.stride < 0 || c.hill_capacity < 0) return WTMD_EINVAL;
+    if (c.engine < WTMD_ENGINE_NONE || c.engine > WTMD_ENGINE_CHAIN) return WTMD_EINVAL;
+    if (c.n_walkers < 1 || !c.walker_size) return WTMD_EINVAL;
+    if (!(c.dt > 0.0) || !(c.mass > 0.0) || c.friction < 0.0) return WTMD_EINVAL;
+    const bool grid = c.grid_bins[0] > 0;
+    for (int i = 0; i < c.n_cv; ++i) {
+        if (grid != (c.grid_bins[i] > 0)) return WTMD_EINVAL;
+        if (grid && !(c.grid_hi[i] > c.grid_lo[i])) return WTMD_EINVAL;
+    }
+    if (c.engine == WTMD_ENGINE_LJ && !(c.lj_rc > 0.0 && c.lj_sigma > 0.0)) return WTMD_EINVAL;
+
+    wtmd_t* h = new (std::nothrow) wtmd_t();
+    if (!h) return WTMD_ENOMEM;
+    h->cfg = c;
+    h->cfg.walker_size = nullptr;
+    h->prec = c.precision;
+    h->d = c.n_cv;
+    h->dims = c.dims > 0 ? c.dims : (c.engine == WTMD_ENGINE_MB ? 2 : 3);
+    if (h->dims < 2 || h->dims > 3) {
+        delete h;
+        return WTMD_EINVAL;
+    }
+    h->W = c.n_walkers;
+    int64_t off = 0;
+    for (int w = 0; w < h->W; ++w) {
+        const int64_t n = c.walker_size[w];
+        if (n < 1 || n > (1 << 30)) {
+            delete h;
+            return WTMD_EINVAL;
+        }
+        h->woff_h.push_back(off);
+        h->wn_h.push_back(n);
+        off += n;
+        h->max_wn = std::max<int>(h->max_wn, (int)n);
+    }
+    h->N = off;
+    const double log2e = 1.4426950408889634;
+    for (int i = 0; i < 3; ++i) h->a[i] = i < h->d ? sqrt(log2e / 2.0) / c.sigma[i] : 0.0;
+    for (int k = 0; k < 3; ++k) {
+        h->box.L[k] = c.box[k] > 0.0 ? c.box[k] : 0.0;
+        h->box.invL[k] = c.box[k] > 0.0 ? 1.0 / c.box[k] : 0.0;
+        h->box.Lf[k] = (float)h->box.L[k];
+        h->box.Llo[k] = (float)(h->box.L[k] - (double)h->box.Lf[k]);
+    }
+    auto fail = [&](int code, const char* m) {
+        h->err = m;
+        wtmd_destroy(h);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(WTMD_ECUDA, "stream");
+    // walkers
+    std::vector<int> aw(h->N), wn32(h->W);
+    for (int w = 0; w < h->W; ++w) {
+        wn32[w] = (int)h->wn_h[w];
+        for (int64_t i = 0; i < h->wn_h[w]; ++i) aw[h->woff_h[w] + i] = w;
+    }
+    if (cudaMalloc(&h->woff, sizeof(int64_t) * h->W) || cudaMalloc(&h->wn, sizeof(int) * h->W) ||
+        cudaMalloc(&h->atom_walker, sizeof(int) * h->N))
+        return fail(WTMD_ENOMEM, "walker tables");
+    cudaMemcpy(h->woff, h->woff_h.data(), sizeof(int64_t) * h->W, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->wn, wn32.data(), sizeof(int) * h->W, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->atom_walker, aw.data(), sizeof(int) * h->N, cudaMemcpyHostToDevice);
+    // hills
+    h->cap = c.hill_capacity;
+    const int64_t CH = 128;  // chunk of the FP32 hills kernel (pairs)
+    const int64_t pairs = (h->cap + 1) / 2;
+    h->cap_pairs = std::max<int64_t>(CH, (pairs + CH - 1) / CH * CH);
+    if (cudaMalloc(&h->hills64, 32 * (size_t)std::max<int64_t>(h->cap, 1)) ||
+        cudaMalloc(&h->hills32, 32 * (size_t)h->cap_pairs))
+        return fail(WTMD_ENOMEM, "hill list");
+    cudaMemset(h->hills64, 0, 32 * (size_t)std::max<int64_t>(h->cap, 1));
+    pad_hills32_kernel<<<(unsigned)((h->cap_pairs + 255) / 256), 256>>>(h->hills32, h->cap_pairs);
+    if (cudaMalloc(&h->count, sizeof(long long)) || cudaMalloc(&h->step, sizeof(long long)) ||
+        cudaMalloc(&h->dep, 2 * sizeof(long long)) || cudaMalloc(&h->status, sizeof(unsigned)))
+        return fail(WTMD_ENOMEM, "counters");
+    cudaMemset(h->count, 0, sizeof(long long));
+    cudaMemset(h->step, 0, sizeof(long long));
+    cudaMemset(h->dep, 0, 2 * sizeof(long long));
+    cudaMemset(h->status, 0, sizeof(unsigned));
+    // grid
+    h->ncell = 0;
+    h->gbins_sum = 0;
+    if (grid) {
+        h->ncell = 1;
+        for (int i = 0; i < h->d; ++i) {
+            h->ncell *= c.grid_bins[i];
+            h->gbins_sum += c.grid_bins[i];
+        }
+        if (cudaMalloc(&h->grid, sizeof(double) * h->ncell)) return fail(WTMD_ENOMEM, "grid");
+        cudaMemset(h->grid, 0, sizeof(double) * h->ncell);
+    }
+    if (cudaMalloc(&h->gfac, sizeof(double) * std::max<int64_t>(1, (int64_t)h->W * std::max(1, h->gbins_sum))))
+        return fail(WTMD_ENOMEM, "grid factors");
+    // per-walker and per-atom scratch
+    if (cudaMalloc(&h->xi, sizeof(double) * 4 * h->W) || cudaMalloc(&h->ctr, sizeof(double) * 3) ||
+        cudaMalloc(&h->V, realsz(h) * h->W) ||
+        cudaMalloc(&h->dV, realsz(h) * 4 * h->W) || cudaMalloc(&h->J, r4sz(h) * h->d * (size_t)h->N))
+        return fail(WTMD_ENOMEM, "scratch");
+    cudaMemset(h->xi, 0, sizeof(double) * 4 * h->W);
+    {
+        // centre of the scaled FP32 hill layout: the grid's centre, else set
+        // by the first loaded or deposited hills (NaN = not yet set)
+        double c[3];
+        for (int i = 0; i < 3; ++i)
+            c[i] = i >= h->d ? 0.0 : (grid ? 0.5 * (c_lo(cfg, i) + c_hi(cfg, i)) : NAN);
+        cudaMemcpy(h->ctr, c, sizeof(c), cudaMemcpyHostToDevice);
+    }
+    cudaMemset(h->dV, 0, realsz(h) * 4 * h->W);
+    cudaMemset(h->J, 0, r4sz(h) * h->d * (size_t)h->N);
+    if (setup_cells(h) != WTMD_OK) return fail(WTMD_ENOMEM, "cell list");
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(WTMD_ECUDA, "create");
+    *out = h;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_set_stream(wtmd_t* h, void* stream)
+{
+    if (!h) return WTMD_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return WTMD_OK;
+}
+
+static bool valid_list(const int32_t* a, int64_t n, int64_t limit, bool distinct)
+{
+    if (!a || n < 1) return false;
+    std::vector<char> seen(distinct ? (size_t)limit : 0, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (a[i] < 0 || a[i] >= limit) return false;
+        if (distinct) {
+            if (seen[a[i]]) return false;
+            seen[a[i]] = 1;
+        }
+    }
+    return true;
+}
+
+extern "C" int cv_define(wtmd_t* h, const wtmd_cv_desc* d, int32_t* cv_id)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!d) FAIL(h, WTMD_EINVAL, "null CV description");
+    if (h->ncv >= h->d) FAIL(h, WTMD_EINVAL, "all n_cv CVs are already defined");
+    int64_t minw = h->wn_h[0];
+    for (auto n : h->wn_h) minw = std::min(minw, n);
+    CvDev c;
+    c.kind = d->kind;
+    c.axis = d->axis;
+    c.nn = d->nn;
+    c.flags = d->flags;
+    c.r0 = d->r0;
+    c.scale = d->scale;
+    c.period = d->period;
+    if (!(d->period >= 0.0) || !isfinite(d->period)) FAIL(h, WTMD_EINVAL, "bad period");
+    if (!isfinite(d->scale)) FAIL(h, WTMD_EINVAL, "bad scale");
+    auto upload = [&](const int32_t* src, int64_t n, int** dst) -> int {
+        if (cudaMalloc(dst, sizeof(int) * n) != cudaSuccess) return WTMD_ENOMEM;
+        cudaMemcpy(*dst, src, sizeof(int) * n, cudaMemcpyHostToDevice);
+        return WTMD_OK;
+    };
+    switch (d->kind) {
+    case WTMD_CV_COMPONENT:
+        if (d->n_a != 1 || !valid_list(d->a, 1, minw, true)) FAIL(h, WTMD_EINVAL, "COMPONENT needs 1 atom index");
+        if (d->axis < 0 || d->axis > 2) FAIL(h, WTMD_EINVAL, "COMPONENT axis must be 0, 1 or 2");
+        c.hidx[0] = d->a[0];
+        c.n_a = 1;
+        break;
+    case WTMD_CV_DIHEDRAL:
+        if (d->n_a != 4 || !valid_list(d->a, 4, minw, true)) FAIL(h, WTMD_EINVAL, "DIHEDRAL needs 4 distinct atoms");
+        for (int k = 0; k < 4; ++k) c.hidx[k] = d->a[k];
+        c.n_a = 4;
+        break;
+    case WTMD_CV_RG:
+        c.n_a = (int)d->n_a;
+        if (d->n_a == -1) {
+            if (minw < 2) FAIL(h, WTMD_EINVAL, "RG needs at least 2 atoms");
+        } else {
+            if (d->n_a < 2 || !valid_list(d->a, d->n_a, minw, true)) FAIL(h, WTMD_EINVAL, "bad RG group");
+            if (upload(d->a, d->n_a, &c.a)) FAIL(h, WTMD_ENOMEM, "RG group");
+        }
+        break;
+    case WTMD_CV_COORDINATION:
+    case WTMD_CV_QPAIRS: {
+        if (!(d->r0 > 0.0)) FAIL(h, WTMD_EINVAL, "r0 must be > 0");
+        if (d->nn < 2 || d->nn > 16 || d->nn % 2 || d->mm != 2 * d->nn)
+            FAIL(h, WTMD_EINVAL, "switching exponents: nn even in 2..16 and mm = 2 nn");
+        if (d->kind == WTMD_CV_QPAIRS) {
+            if (d->n_a < 2 || d->n_a % 2 || !valid_list(d->a, d->n_a, minw, false))
+                FAIL(h, WTMD_EINVAL, "QPAIRS needs 2*npairs indices");
+            for (int64_t p = 0; p < d->n_a / 2; ++p)
+                if (d->a[2 * p] == d->a[2 * p + 1]) FAIL(h, WTMD_EINVAL, "QPAIRS pair of one atom");
+            c.n_pairs = (int)(d->n_a / 2);
+            c.n_a = (int)d->n_a;
+            if (upload(d->a, d->n_a, &c.a)) FAIL(h, WTMD_ENOMEM, "pairs");
+            std::vector<int> cntv(h->max_wn + 1, 0), items(d->n_a);
+            for (int64_t q = 0; q < d->n_a; ++q) cntv[d->a[q] + 1]++;
+            for (int k = 0; k < h->max_wn; ++k) cntv[k + 1] += cntv[k];
+            std::vector<int> fill(cntv.begin(), cntv.end() - 1);
+            for (int64_t q = 0; q < d->n_a; ++q) items[fill[d->a[q]]++] = (int)((q / 2) * 2 + (q & 1));
+            if (upload(cntv.data(), h->max_wn + 1, &c.q_rowptr) || upload(items.data(), d->n_a, &c.q_items))
+                FAIL(h, WTMD_ENOMEM, "pair CSR");
+            break;
+        }
+        c.n_a = (int)d->n_a;
+        c.n_b = (int)d->n_b;
+        if (d->n_a != -1 && !valid_list(d->a, d->n_a, minw, true)) FAIL(h, WTMD_EINVAL, "bad group A");
+        if (d->n_b != -1 && !valid_list(d->b, d->n_b, minw, true)) FAIL(h, WTMD_EINVAL, "bad group B");
+        if (d->n_a == -1 && d->n_b == -1) c.same_ab = true;
+        if (d->n_a > 0 && d->n_a == d->n_b && !memcmp(d->a, d->b, sizeof(int32_t) * d->n_a)) c.same_ab = true;
+        std::vector<int> inv(h->max_wn, -1);
+        if (d->n_a > 0) {
+            for (int64_t p = 0; p < d->n_a; ++p) inv[d->a[p]] = (int)p;
+            if (upload(d->a, d->n_a, &c.a) || upload(inv.data(), h->max_wn, &c.inv_a)) FAIL(h, WTMD_ENOMEM, "A");
+        }
+        if (d->n_b > 0) {
+            std::fill(inv.begin(), inv.end(), -1);
+            for (int64_t p = 0; p < d->n_b; ++p) inv[d->b[p]] = (int)p;
+            if (upload(d->b, d->n_b, &c.b) || upload(inv.data(), h->max_wn, &c.inv_b)) FAIL(h, WTMD_ENOMEM, "B");
+        }
+        if (h->W > 1 && (d->n_a == -1) != (d->n_b == -1) && c.n_a != -1) {
+            // explicit lists are shared by all walkers; fine
+        }
+        break;
+    }
+    default:
+        FAIL(h, WTMD_EINVAL, "unknown CV kind");
+    }
+    const int rc = cv_alloc_scratch(h, c);
+    if (rc != WTMD_OK) {
+        free_cv(c);
+        return rc;
+    }
+    h->cv[h->ncv] = c;
+    if (cv_id) *cv_id = h->ncv;
+    h->ncv++;
+    drop_graphs(h);
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_bind(wtmd_t* h, void* pos, void* vel, void* force, int64_t n_atoms)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_atoms != h->N) FAIL(h, WTMD_EINVAL, "n_atoms differs from the sum of walker sizes");
+    if (!pos || !force) FAIL(h, WTMD_EINVAL, "positions and forces are required");
+    const uintptr_t al = h->prec == WTMD_F32 ? 16 : 32;
+    if ((uintptr_t)pos % al || (uintptr_t)force % al || (vel && (uintptr_t)vel % al))
+        FAIL(h, WTMD_EINVAL, "particle arrays must be 16-byte (F32) / 32-byte (F64) aligned");
+    h->pos = pos;
+    h->vel = vel;
+    h->force = force;
+    h->forces_valid = false;
+    drop_graphs(h);
+    return WTMD_OK;
+}
+
+// Total force at the bound positions (engine + bias), no kick, no deposit.
+static int enqueue_forces(wtmd_t* h)
+{
+    int rc;
+    if ((rc = launch_engine(h))) return rc;
+    if ((rc = launch_cvs(h, h->pos))) return rc;
+    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    return launch_scatter(h, h->force, nullptr, false);
+}
+
+static int enqueue_step(wtmd_t* h)
+{
+    int rc;
+    if ((rc = launch_baoab_first(h))) return rc;
+    if ((rc = launch_engine(h))) return rc;
+    if ((rc = launch_cvs(h, h->pos))) return rc;
+    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if ((rc = launch_scatter(h, h->force, h->vel, true))) return rc;
+    return launch_deposit(h);
+}
+
+static int capture(wtmd_t* h, int nsteps, cudaGraphExec_t* out)
+{
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->stream = user;
+        FAIL(h, WTMD_ECUDA, "begin capture");
+    }
+    int rc = WTMD_OK;
+    for (int s = 0; s < nsteps && rc == WTMD_OK; ++s) rc = enqueue_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->stream = user;
+    if (rc != WTMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) FAIL(h, WTMD_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) FAIL(h, WTMD_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    return WTMD_OK;
+}
+
+static int ready(wtmd_t* h)
+{
+    if (h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
+    return WTMD_OK;
+}
+
+extern "C" int step_n(wtmd_t* h, int64_t n_steps)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_steps < 0) FAIL(h, WTMD_EINVAL, "negative step count");
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
+    if (n_steps == 0) return WTMD_OK;
+    if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+    if (!h->forces_valid) {
+        if ((rc = enqueue_forces(h))) return rc;
+        h->forces_valid = true;
+    }
+    if (!h->graph) {
+        if ((rc = capture(h, kGraphSteps, &h->graph))) return rc;
+        if ((rc = capture(h, 1, &h->graph1))) return rc;
+    }
+    const int64_t full = n_steps / kGraphSteps, rest = n_steps % kGraphSteps;
+    for (int64_t i = 0; i < full; ++i) WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    for (int64_t i = 0; i < rest; ++i) WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph1, h->stream));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_check(wtmd_t* h)
+{
+    if (!h) return WTMD_EINVAL;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    unsigned st = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+    WTMD_CUDA_TRY(h, cudaMemset(h->status, 0, sizeof(unsigned)));
+    if (st & ST_TIMEOUT) FAIL(h, WTMD_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_NUMERIC) FAIL(h, WTMD_ENUMERIC, "non-finite CV, bias or gradient");
+    if (st & ST_CELL) FAIL(h, WTMD_ECELL, "cell list overflow");
+    if (st & ST_CAPACITY) FAIL(h, WTMD_ECAPACITY, "hill capacity reached; deposits skipped");
+    return WTMD_OK;
+}
+
+template <typename S, typename D>
+__global__ static void copy_cols_kernel(const S* __restrict__ src, D* __restrict__ dst, int W, int cols)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * cols) return;
+    dst[i] = (D)src[(i / cols) * 4 + i % cols];
+}
+
+// [W][4] (double CV values or Real gradients) -> [W][cols] Real
+static int copy_cols(wtmd_t* h, void* dst, const void* src, bool src_f64, int cols)
+{
+    const int n = h->W * cols, nb = (n + 255) / 256;
+    if (h->prec == WTMD_F64)
+        copy_cols_kernel<double, double><<<nb, 256, 0, h->stream>>>((const double*)src, (double*)dst, h->W, cols);
+    else if (src_f64)
+        copy_cols_kernel<double, float><<<nb, 256, 0, h->stream>>>((const double*)src, (float*)dst, h->W, cols);
+    else
+        copy_cols_kernel<float, float><<<nb, 256, 0, h->stream>>>((const float*)src, (float*)dst, h->W, cols);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_out, void* xi_out, void* dV_out)
+{
+    if (!h) return WTMD_EINVAL;
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!pos) FAIL(h, WTMD_EINVAL, "null positions");
+    if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+    if ((rc = launch_cvs(h, pos))) return rc;
+    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if (force_inout && (rc = launch_scatter(h, force_inout, nullptr, false))) return rc;
+    if (V_out) WTMD_CUDA_TRY(h, cudaMemcpyAsync(V_out, h->V, realsz(h) * h->W, cudaMemcpyDeviceToDevice, h->stream));
+    if (xi_out && (rc = copy_cols(h, xi_out, h->xi, true, h->d))) return rc;
+    if (dV_out && (rc = copy_cols(h, dV_out, h->dV, false, h->d))) return rc;
+    return WTMD_OK;
+}
+
+extern "C" int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (P < 0 || (P > 0 && !xi)) FAIL(h, WTMD_EINVAL, "bad points");
+    if (h->ncv > 0 && h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs (or none) first");
+    return launch_hills(h, xi, h->prec == WTMD_F64, h->d, P, V_out, dV_out, h->d);
+}
+
+extern "C" int fes_grid(wtmd_t* h, double* out, int64_t n_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!h->grid) FAIL(h, WTMD_EINVAL, "no grid configured");
+    if (!out || n_out < h->ncell) FAIL(h, WTMD_EINVAL, "output smaller than the grid");
+    return launch_fes(h, out);
+}
+
+extern "C" int wtmd_hills_load(wtmd_t* h, const double* hills, int64_t count)
+{
+    if (!h) return WTMD_EINVAL;
+    if (count < 0 || count > h->cap || (count > 0 && !hills)) FAIL(h, WTMD_EINVAL, "count outside 0..capacity");
+    for (int64_t k = 0; k < count; ++k) {
+        const double w = hills[4 * k + 3];
+        if (!(w > 0.0) || !isfinite(w)) FAIL(h, WTMD_EINVAL, "hill heights must be finite and > 0");
+        for (int i = 0; i < 3; ++i)
+            if (!isfinite(hills[4 * k + i])) FAIL(h, WTMD_EINVAL, "non-finite hill centre");
+    }
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (count) WTMD_CUDA_TRY(h, cudaMemcpy(h->hills64, hills, 32 * (size_t)count, cudaMemcpyHostToDevice));
+    long long c = count;
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->count, &c, sizeof(c), cudaMemcpyHostToDevice));
+    double ctr[3];
+    WTMD_CUDA_TRY(h, cudaMemcpy(ctr, h->ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+    if (isnan(ctr[0]) && count > 0) {
+        for (int i = 0; i < 3; ++i) {
+            double m = 0.0;
+            for (int64_t k = 0; k < count; ++k) m += hills[4 * k + i];
+            ctr[i] = i < h->d ? m / count : 0.0;
+        }
+        WTMD_CUDA_TRY(h, cudaMemcpy(h->ctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice));
+    }
+    pad_hills32_kernel<<<(unsigned)((h->cap_pairs + 255) / 256), 256, 0, h->stream>>>(h->hills32, h->cap_pairs);
+    store_hills32_range(h, 0, count);
+    int rc = launch_grid_rebuild(h);
+    if (rc) return rc;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_hills_read(wtmd_t* h, double* out, int64_t cap_out, int64_t* count)
+{
+    if (!h) return WTMD_EINVAL;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    long long c = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpy(&c, h->count, sizeof(c), cudaMemcpyDeviceToHost));
+    if (count) *count = c;
+    const int64_t n = std::min<int64_t>(c, cap_out);
+    if (n > 0 && out) WTMD_CUDA_TRY(h, cudaMemcpy(out, h->hills64, 32 * (size_t)n, cudaMemcpyDeviceToHost));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_counters(wtmd_t* h, int64_t* step, int64_t* n_hills)
+{
+    if (!h) return WTMD_EINVAL;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    long long s = 0, c = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpy(&s, h->step, sizeof(s), cudaMemcpyDeviceToHost));
+    WTMD_CUDA_TRY(h, cudaMemcpy(&c, h->count, sizeof(c), cudaMemcpyDeviceToHost));
+    if (step) *step = s;
+    if (n_hills) *n_hills = c;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_grid_read(wtmd_t* h, double* out, int64_t n_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!h->grid) FAIL(h, WTMD_EINVAL, "no grid configured");
+    if (!out || n_out < h->ncell) FAIL(h, WTMD_EINVAL, "output smaller than the grid");
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpy(out, h->grid, sizeof(double) * h->ncell, cudaMemcpyDeviceToHost));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32_t cap, int32_t* n_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_steps < 1 || cap < 1 || !names || !ms || !n_out) FAIL(h, WTMD_EINVAL, "bad profile arguments");
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
+    if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+    if (!h->forces_valid) {
+        if ((rc = enqueue_forces(h))) return rc;
+        h->forces_valid = true;
+    }
+    std::vector<double> acc;
+    std::vector<std::string> nm;
+    h->prof = true;
+    for (int64_t s = 0; s < n_steps; ++s) {
+        h->ev_n = 0;
+        mark(h, "start");
+        rc = enqueue_step(h);
+        if (rc) break;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            rc = WTMD_ECUDA;
+            break;
+        }
+        if (s == 0) {
+            nm.assign(h->ev_names.begin() + 1, h->ev_names.begin() + h->ev_n);
+            acc.assign(nm.size(), 0.0);
+        }
+        for (int i = 1; i < h->ev_n && i - 1 < (int)acc.size(); ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, h->ev_pool[i - 1], h->ev_pool[i]);
+            acc[i - 1] += t;
+        }
+    }
+    h->prof = false;
+    if (rc) return rc;
+    const int n = std::min<int>((int)nm.size(), cap);
+    for (int i = 0; i < n; ++i) {
+        std::strncpy(names + 32 * i, nm[i].c_str(), 31);
+        names[32 * i + 31] = 0;
+        ms[i] = acc[i] / n_steps;
+    }
+    *n_out = n;
+    return WTMD_OK;
+}

@@ -1,0 +1,262 @@
+// Hill deposition of metadynamics with optional grid storage of the bias, and
+// the free-energy estimate (PySAGES paper, Sec. 2.1.5; Sec. 2 `analyze`;
+// Sec. 2.1, Eq. (free-energy)).
+//
+// Every `stride` steps each walker appends one hill at its current CVs.  The
+// height is w0 in standard metadynamics and, in the well-tempered variant,
+// w0 exp(-V(s) / (kT (gamma - 1))) with V(s) the bias of the hills that
+// existed before this step's deposits (the same V the force used); it is
+// computed in FP64.  Walkers append in index order.  The FP64 grid holds the
+// running bias at cell centres; each new Gaussian is added as a product of
+// per-axis factors exp(-D_i^2/(2 sigma_i^2)) (periodic axes use the minimum
+// image), which needs sum(bins) exponentials per hill instead of prod(bins).
+#include <algorithm>
+
+#include "wtmd_internal.cuh"
+
+namespace wtmd {
+
+void store_hills32_range(wtmd_t* h, long long k0, long long k1);
+
+struct DepPrm {
+    long long stride;
+    long long cap;
+    int W, d;
+    double w0, inv_dT;  // inv_dT = 1/(kT (gamma - 1)); 0 for standard metadynamics
+    double a[3];        // FP32 layout scale
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) deposit_kernel(DepPrm p, const double* __restrict__ xi,
+                                                      const R* __restrict__ V, long long* __restrict__ count,
+                                                      long long* __restrict__ step, long long* __restrict__ dep,
+                                                      double* __restrict__ ctr, dbl4* __restrict__ h64,
+                                                      float* __restrict__ h32, unsigned* status)
+{
+    __shared__ long long base;
+    __shared__ int doit;
+    __shared__ double c[3];
+    if (threadIdx.x == 0) {
+        const long long t = *step;
+        doit = p.stride > 0 && (t + 1) % p.stride == 0;
+        base = *count;
+        if (doit && base + p.W > p.cap) {
+            atomicOr(status, ST_CAPACITY);
+            doit = 0;
+        }
+        dep[0] = base;
+        dep[1] = doit ? p.W : 0;
+        // the centre of the scaled FP32 layout is fixed by the first hill
+        // when no grid defined it
+        if (doit && isnan(ctr[0]))
+            for (int i = 0; i < 3; ++i) ctr[i] = i < p.d ? xi[i] : 0.0;
+        for (int i = 0; i < 3; ++i) c[i] = ctr[i];
+    }
+    __syncthreads();
+    if (doit) {
+        for (int w = threadIdx.x; w < p.W; w += blockDim.x) {
+            const long long k = base + w;
+            double s[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < p.d; ++i) s[i] = xi[w * 4 + i];
+            const double hgt = p.w0 * exp(-(double)V[w] * p.inv_dT);
+            h64[k] = dbl4{s[0], s[1], s[2], hgt};
+            const long long b = (k >> 1) * 8 + (k & 1);
+            h32[b + 0] = (float)(-(s[0] - c[0]) * p.a[0]);
+            h32[b + 2] = (float)(-(s[1] - c[1]) * p.a[1]);
+            h32[b + 4] = (float)(-(s[2] - c[2]) * p.a[2]);
+            h32[b + 6] = (float)(-log2(hgt));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (doit) *count = base + p.W;
+        *step = *step + 1;
+    }
+}
+
+struct GridPrm {
+    int d;
+    int bins[3];
+    int off[3];      // offset of axis i in the factor table
+    double lo[3], dx[3], inv2s2[3], per[3];
+};
+
+// factors f[n][off_i + k] = exp(-D^2/(2 sigma_i^2)) of new hill n on axis i
+__global__ void grid_factor_kernel(GridPrm g, const long long* __restrict__ dep, const dbl4* __restrict__ h64,
+                                   int tot, double* __restrict__ fac)
+{
+    const long long nnew = dep[1];
+    const long long first = dep[0];
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nnew * tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long n = q / tot;
+        const int j = (int)(q % tot);
+        int i = 0;
+        while (i + 1 < g.d && j >= g.off[i + 1]) ++i;
+        const int k = j - g.off[i];
+        const dbl4 h = h64[first + n];
+        const double s = i == 0 ? h.x : (i == 1 ? h.y : h.z);
+        double D = g.lo[i] + (k + 0.5) * g.dx[i] - s;
+        if (g.per[i] > 0.0) D -= g.per[i] * rint(D / g.per[i]);
+        fac[q] = exp(-D * D * g.inv2s2[i]);
+    }
+}
+
+__global__ void grid_add_kernel(GridPrm g, const long long* __restrict__ dep, const dbl4* __restrict__ h64, int tot,
+                                const double* __restrict__ fac, long long ncell, double* __restrict__ grid)
+{
+    const long long nnew = dep[1];
+    if (nnew == 0) return;
+    const long long first = dep[0];
+    for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < ncell;
+         cidx += (long long)gridDim.x * blockDim.x) {
+        int k[3] = {0, 0, 0};
+        long long rem = cidx;
+        for (int i = g.d - 1; i >= 0; --i) {
+            k[i] = (int)(rem % g.bins[i]);
+            rem /= g.bins[i];
+        }
+        double v = grid[cidx];
+        for (long long n = 0; n < nnew; ++n) {
+            double e = h64[first + n].w;
+            for (int i = 0; i < g.d; ++i) e *= fac[n * tot + g.off[i] + k[i]];
+            v += e;
+        }
+        grid[cidx] = v;
+    }
+}
+
+// Rebuild the grid from all hills (after a hill-list load).
+__global__ void grid_rebuild_kernel(GridPrm g, const dbl4* __restrict__ h64, long long H, long long ncell,
+                                    double* __restrict__ grid)
+{
+    for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < ncell;
+         cidx += (long long)gridDim.x * blockDim.x) {
+        double x[3] = {0, 0, 0};
+        long long rem = cidx;
+        for (int i = g.d - 1; i >= 0; --i) {
+            const int k = (int)(rem % g.bins[i]);
+            rem /= g.bins[i];
+            x[i] = g.lo[i] + (k + 0.5) * g.dx[i];
+        }
+        double v = 0.0;
+        for (long long n = 0; n < H; ++n) {
+            const dbl4 h = h64[n];
+            const double s[3] = {h.x, h.y, h.z};
+            double e = h.w;
+            for (int i = 0; i < g.d; ++i) {
+                double D = x[i] - s[i];
+                if (g.per[i] > 0.0) D -= g.per[i] * rint(D / g.per[i]);
+                e *= exp(-D * D * g.inv2s2[i]);
+            }
+            v += e;
+        }
+        grid[cidx] = v;
+    }
+}
+
+__global__ void __launch_bounds__(1024) grid_max_kernel(const double* __restrict__ grid, long long n,
+                                                        double* __restrict__ out)
+{
+    __shared__ double sm[32];
+    double m = -INFINITY;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, grid[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) sm[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) r = fmax(r, sm[w]);
+        out[0] = r;
+    }
+}
+
+__global__ void fes_kernel(const double* __restrict__ grid, long long n, double f, const double* __restrict__ vmax,
+                           double* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // f < 0: the minimum of f*V is f*max(V)
+    out[i] = f * grid[i] - f * vmax[0];
+}
+
+// ---------------------------------------------------------------------------
+static GridPrm grid_prm(const wtmd_t* h)
+{
+    GridPrm g{};
+    g.d = h->d;
+    int off = 0;
+    for (int i = 0; i < 3; ++i) {
+        g.bins[i] = i < h->d ? h->cfg.grid_bins[i] : 1;
+        g.off[i] = off;
+        if (i < h->d) off += h->cfg.grid_bins[i];
+        g.lo[i] = h->cfg.grid_lo[i];
+        g.dx[i] = i < h->d ? (h->cfg.grid_hi[i] - h->cfg.grid_lo[i]) / h->cfg.grid_bins[i] : 1.0;
+        const double sg = h->cfg.sigma[i] > 0 ? h->cfg.sigma[i] : 1.0;
+        g.inv2s2[i] = 1.0 / (2.0 * sg * sg);
+        g.per[i] = i < h->d ? h->cv[i].period : 0.0;
+    }
+    return g;
+}
+
+static double fes_factor(const wtmd_config& c)
+{
+    return (c.gamma == 0.0 || isinf(c.gamma)) ? -1.0 : -c.gamma / (c.gamma - 1.0);
+}
+
+int launch_deposit(wtmd_t* h)
+{
+    DepPrm p{};
+    p.stride = h->cfg.stride;
+    p.cap = h->cap;
+    p.W = h->W;
+    p.d = h->d;
+    p.w0 = h->cfg.w0;
+    p.inv_dT = (h->cfg.gamma == 0.0 || isinf(h->cfg.gamma)) ? 0.0 : 1.0 / (h->cfg.kT * (h->cfg.gamma - 1.0));
+    for (int i = 0; i < 3; ++i) p.a[i] = h->a[i];
+    if (h->prec == WTMD_F32)
+        deposit_kernel<float><<<1, 256, 0, h->stream>>>(p, h->xi, (const float*)h->V, h->count, h->step, h->dep,
+                                                        h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status);
+    else
+        deposit_kernel<double><<<1, 256, 0, h->stream>>>(p, h->xi, (const double*)h->V, h->count, h->step, h->dep,
+                                                         h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status);
+    mark(h, "deposit");
+    if (h->grid) {
+        GridPrm g = grid_prm(h);
+        const int tot = h->gbins_sum;
+        const long long nf = (long long)h->W * tot;
+        grid_factor_kernel<<<(unsigned)std::min<long long>((nf + 255) / 256, 4096), 256, 0, h->stream>>>(
+            g, h->dep, (const dbl4*)h->hills64, tot, h->gfac);
+        mark(h, "grid_factor");
+        grid_add_kernel<<<(unsigned)std::min<long long>((h->ncell + 255) / 256, 8192), 256, 0, h->stream>>>(
+            g, h->dep, (const dbl4*)h->hills64, tot, h->gfac, h->ncell, h->grid);
+        mark(h, "grid_add");
+    }
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+int launch_grid_rebuild(wtmd_t* h)
+{
+    if (!h->grid) return WTMD_OK;
+    long long H = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(&H, h->count, sizeof(H), cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    GridPrm g = grid_prm(h);
+    grid_rebuild_kernel<<<(unsigned)std::min<long long>((h->ncell + 255) / 256, 8192), 256, 0, h->stream>>>(
+        g, (const dbl4*)h->hills64, H, h->ncell, h->grid);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+int launch_fes(wtmd_t* h, double* out)
+{
+    double* vmax = (double*)h->gfac;  // any scratch double; the factor table is idle here
+    grid_max_kernel<<<1, 1024, 0, h->stream>>>(h->grid, h->ncell, vmax);
+    fes_kernel<<<(unsigned)((h->ncell + 255) / 256), 256, 0, h->stream>>>(h->grid, h->ncell, fes_factor(h->cfg), vmax,
+                                                                          out);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+}  // namespace wtmd

@@ -1,0 +1,466 @@
+// The minimal engine that drives the method: BAOAB Langevin integration with
+// counter-based Philox noise, and three force fields (Mueller-Brown, 12-6
+// Lennard-Jones with a cell list or all pairs, bead chain).  In the paper the
+// backend (HOOMD-blue, OpenMM, ...) owns these steps: half-step integration,
+// bonded and pair forces, second half-step (Sec. 3.2.1 steps (a), (b), (c), (f)).
+//
+// BAOAB (Leimkuhler & Matthews 2013): B v += dt/2 F/m; A x += dt/2 v;
+// O v = c1 v + sqrt((1 - c1^2) kT/m) R, c1 = exp(-friction dt); A x += dt/2 v;
+// forces; B.  The noise of particle i at step t is Philox4x32-10 with key
+// (seed lo, seed hi) and counter (t lo, i, t hi, 0); its four words become
+// uniforms u = (x + 1/2) 2^-32 and two Box-Muller pairs (first three normals
+// used).  Positions are never wrapped; distances use the minimum image.
+#include "wtmd_internal.cuh"
+
+namespace wtmd {
+
+template <typename R> struct Normal3 {
+    R g[3];
+};
+
+template <typename R> __device__ __forceinline__ Normal3<R> noise3(uint64_t seed, long long step, uint32_t i);
+
+template <> __device__ __forceinline__ Normal3<double> noise3<double>(uint64_t seed, long long step, uint32_t i)
+{
+    const U4 r = philox10((uint32_t)step, i, (uint32_t)((unsigned long long)step >> 32), 0u, (uint32_t)seed,
+                          (uint32_t)(seed >> 32));
+    const double k = 2.3283064365386963e-10;  // 2^-32
+    const double u0 = ((double)r.v[0] + 0.5) * k, u1 = ((double)r.v[1] + 0.5) * k;
+    const double u2 = ((double)r.v[2] + 0.5) * k, u3 = ((double)r.v[3] + 0.5) * k;
+    const double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
+    double s1, c1, c3;
+    sincospi(2.0 * u1, &s1, &c1);
+    c3 = cospi(2.0 * u3);
+    Normal3<double> n;
+    n.g[0] = a * c1;
+    n.g[1] = a * s1;
+    n.g[2] = b * c3;
+    return n;
+}
+
+template <> __device__ __forceinline__ Normal3<float> noise3<float>(uint64_t seed, long long step, uint32_t i)
+{
+    const U4 r = philox10((uint32_t)step, i, (uint32_t)((unsigned long long)step >> 32), 0u, (uint32_t)seed,
+                          (uint32_t)(seed >> 32));
+    // 24 significant bits: u = (floor(x / 2^8) + 1/2) 2^-24, in (0, 1)
+    const float k = 5.9604644775390625e-08f;  // 2^-24
+    const float u0 = ((float)(r.v[0] >> 8) + 0.5f) * k, u1 = ((float)(r.v[1] >> 8) + 0.5f) * k;
+    const float u2 = ((float)(r.v[2] >> 8) + 0.5f) * k, u3 = ((float)(r.v[3] >> 8) + 0.5f) * k;
+    const float a = sqrtf(-2.0f * logf(u0)), b = sqrtf(-2.0f * logf(u2));
+    float s1, c1;
+    sincospif(2.0f * u1, &s1, &c1);
+    Normal3<float> n;
+    n.g[0] = a * c1;
+    n.g[1] = a * s1;
+    n.g[2] = b * cospif(2.0f * u3);
+    return n;
+}
+
+template <typename R>
+__global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __restrict__ v,
+                                   const R4<R>* __restrict__ f, const long long* __restrict__ step, uint64_t seed,
+                                   R half, R inv_m, R c1, R c2, int dims)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long t = *step;
+    const Normal3<R> n = noise3<R>(seed, t, (uint32_t)i);
+    R4<R> xi = x[i], vi = v[i];
+    const R4<R> fi = f[i];
+    R* xp[3] = {&xi.x, &xi.y, &xi.z};
+    R* vp[3] = {&vi.x, &vi.y, &vi.z};
+    const R fp[3] = {fi.x, fi.y, fi.z};
+    for (int k = 0; k < dims; ++k) {
+        R vv = *vp[k], xx = *xp[k];
+        vv += half * fp[k] * inv_m;
+        xx += half * vv;
+        vv = c1 * vv + c2 * n.g[k];
+        xx += half * vv;
+        *vp[k] = vv;
+        *xp[k] = xx;
+    }
+    x[i] = xi;
+    v[i] = vi;
+}
+
+// Mueller-Brown (Mueller & Brown 1979): sum of four anisotropic Gaussians.
+__constant__ double kMB[6][4] = {
+    {-200.0, -100.0, -170.0, 15.0},  // A
+    {-1.0, -1.0, -6.5, 0.7},         // a
+    {0.0, 0.0, 11.0, 0.6},           // b
+    {-10.0, -10.0, -6.5, 0.7},       // c
+    {1.0, 0.0, -0.5, -1.0},          // x0
+    {0.0, 0.5, 1.5, 1.0},            // y0
+};
+
+template <typename R>
+__global__ void mb_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __restrict__ f)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R4<R> p = x[i];
+    R gx = 0, gy = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R dx = p.x - (R)kMB[4][k], dy = p.y - (R)kMB[5][k];
+        const R a = (R)kMB[1][k], b = (R)kMB[2][k], c = (R)kMB[3][k];
+        const R e = (R)kMB[0][k] * exp(a * dx * dx + b * dx * dy + c * dy * dy);
+        gx += e * (R(2) * a * dx + b * dy);
+        gy += e * (b * dx + R(2) * c * dy);
+    }
+    f[i] = mk4<R>(-gx, -gy, R(0), R(0));
+}
+
+// LJ pair force factor: F_t += fr * (r_t - r_s), fr = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2.
+template <typename R> __device__ __forceinline__ R lj_fr(R r2, R sig2, R eps24)
+{
+    const R sr2 = sig2 / r2;
+    const R sr6 = sr2 * sr2 * sr2;
+    return eps24 * (R(2) * sr6 * sr6 - sr6) / r2;
+}
+
+// All pairs within each walker; sources staged in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restrict__ x, const int64_t* __restrict__ woff,
+                                                          const int* __restrict__ wn, Box box, R rc2, R sig2, R eps24,
+                                                          R4<R>* __restrict__ f)
+{
+    __shared__ R4<R> src[128];
+    const int w = blockIdx.y;
+    const long long o = woff[w];
+    const int n = wn[w];
+    const int t = blockIdx.x * 128 + threadIdx.x;
+    if (blockIdx.x * 128 >= n) return;
+    R4<R> xt = t < n ? x[o + t] : mk4<R>(0, 0, 0, 0);
+    R fx = 0, fy = 0, fz = 0;
+    for (int s0 = 0; s0 < n; s0 += 128) {
+        __syncthreads();
+        if (s0 + threadIdx.x < n) src[threadIdx.x] = x[o + s0 + threadIdx.x];
+        __syncthreads();
+        const int m = min(128, n - s0);
+        for (int j = 0; j < m; ++j) {
+            if (s0 + j == t) continue;
+            const R4<R> xs = src[j];
+            const R dx = min_image<R>(xt.x - xs.x, box, 0);
+            const R dy = min_image<R>(xt.y - xs.y, box, 1);
+            const R dz = min_image<R>(xt.z - xs.z, box, 2);
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2) {
+                const R fr = lj_fr<R>(r2, sig2, eps24);
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+            }
+        }
+    }
+    if (t < n) f[o + t] = mk4<R>(fx, fy, fz, R(0));
+}
+
+// Cell list (single periodic walker).  Binning with atomics, then each
+// cell's list is sorted by atom index so the force sum order is fixed.
+template <typename R>
+__global__ void cell_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx, int ncy, int ncz,
+                                int cap, int* __restrict__ cnt, int* __restrict__ atoms, unsigned* status)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R4<R> p = x[i];
+    const R q[3] = {p.x, p.y, p.z};
+    const int nc[3] = {ncx, ncy, ncz};
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+        const R L = (R)box.L[k];
+        R u = q[k] * (R)box.invL[k];
+        u -= floor(u);  // fractional coordinate in [0, 1]
+        int c = (int)(u * nc[k]);
+        ci[k] = c >= nc[k] ? nc[k] - 1 : (c < 0 ? 0 : c);
+        (void)L;
+    }
+    const int cell = (ci[0] * ncy + ci[1]) * ncz + ci[2];
+    const int slot = atomicAdd(&cnt[cell], 1);
+    if (slot < cap) atoms[(size_t)cell * cap + slot] = (int)i;
+    else atomicOr(status, ST_CELL);
+}
+
+__global__ void cell_sort_kernel(int ncells, int cap, const int* __restrict__ cnt, int* __restrict__ atoms)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int n = min(cnt[c], cap);
+    int* a = atoms + (size_t)c * cap;
+    for (int i = 1; i < n; ++i) {
+        const int v = a[i];
+        int j = i - 1;
+        while (j >= 0 && a[j] > v) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = v;
+    }
+}
+
+template <typename R>
+__global__ void lj_cells_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx, int ncy, int ncz, int cap,
+                                const int* __restrict__ cnt, const int* __restrict__ atoms, R rc2, R sig2, R eps24,
+                                R4<R>* __restrict__ f)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R4<R> p = x[i];
+    const R q[3] = {p.x, p.y, p.z};
+    const int nc[3] = {ncx, ncy, ncz};
+    int ci[3];
+    for (int k = 0; k < 3; ++k) {
+        R u = q[k] * (R)box.invL[k];
+        u -= floor(u);
+        int c = (int)(u * nc[k]);
+        ci[k] = c >= nc[k] ? nc[k] - 1 : (c < 0 ? 0 : c);
+    }
+    R fx = 0, fy = 0, fz = 0;
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int cx = (ci[0] + dx + ncx) % ncx, cy = (ci[1] + dy + ncy) % ncy, cz = (ci[2] + dz + ncz) % ncz;
+                const int cell = (cx * ncy + cy) * ncz + cz;
+                const int n = min(cnt[cell], cap);
+                const int* a = atoms + (size_t)cell * cap;
+                for (int k = 0; k < n; ++k) {
+                    const int j = a[k];
+                    if (j == i) continue;
+                    const R4<R> s = x[j];
+                    const R ddx = min_image<R>(p.x - s.x, box, 0);
+                    const R ddy = min_image<R>(p.y - s.y, box, 1);
+                    const R ddz = min_image<R>(p.z - s.z, box, 2);
+                    const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (r2 < rc2) {
+                        const R fr = lj_fr<R>(r2, sig2, eps24);
+                        fx += fr * ddx;
+                        fy += fr * ddy;
+                        fz += fr * ddz;
+                    }
+                }
+            }
+    f[i] = mk4<R>(fx, fy, fz, R(0));
+}
+
+// Bead chain: bonds kb/2 (r - r0)^2, angles ka/2 (theta - th0)^2, torsions
+// kt (1 + cos 3 phi); each bead gathers the terms it takes part in.
+template <typename R>
+__device__ __forceinline__ void angle_grad(const R a[3], const R b[3], const R c[3], R ka, R th0, R ga[3], R gb[3],
+                                           R gc[3])
+{
+    R u[3], v[3];
+    for (int k = 0; k < 3; ++k) {
+        u[k] = a[k] - b[k];
+        v[k] = c[k] - b[k];
+    }
+    const R nu2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2], nv2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const R nu = sqrt(nu2), nv = sqrt(nv2);
+    R cs = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / (nu * nv);
+    const R th = acos(cs);
+    const R dU = ka * (th - th0) * (R(-1) / sin(th));  // dU/dcos
+    for (int k = 0; k < 3; ++k) {
+        const R du = v[k] / (nu * nv) - cs * u[k] / nu2;
+        const R dv = u[k] / (nu * nv) - cs * v[k] / nv2;
+        ga[k] = dU * du;
+        gc[k] = dU * dv;
+        gb[k] = -(ga[k] + gc[k]);
+    }
+}
+
+template <typename R>
+__global__ void chain_kernel(const R4<R>* __restrict__ x, const int64_t* __restrict__ woff, const int* __restrict__ wn,
+                             R kb, R r0, R ka, R th0, R kt, R4<R>* __restrict__ f)
+{
+    const int w = blockIdx.y;
+    const int n = wn[w];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long o = woff[w];
+    auto P = [&](int j, R q[3]) {
+        const R4<R> v = x[o + j];
+        q[0] = v.x;
+        q[1] = v.y;
+        q[2] = v.z;
+    };
+    R gi[3] = {0, 0, 0};  // dU/dr_i
+    R pi[3];
+    P(i, pi);
+    for (int j = i - 1; j <= i + 1; j += 2) {
+        if (j < 0 || j >= n) continue;
+        R pj[3];
+        P(j, pj);
+        const R d[3] = {pi[0] - pj[0], pi[1] - pj[1], pi[2] - pj[2]};
+        const R r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const R c = kb * (r - r0) / r;
+        for (int k = 0; k < 3; ++k) gi[k] += c * d[k];
+    }
+    for (int s = i - 2; s <= i; ++s) {  // angle (s, s+1, s+2)
+        if (s < 0 || s + 2 >= n) continue;
+        R a[3], b[3], c[3], ga[3], gb[3], gc[3];
+        P(s, a);
+        P(s + 1, b);
+        P(s + 2, c);
+        angle_grad<R>(a, b, c, ka, th0, ga, gb, gc);
+        const R* g = (i == s) ? ga : (i == s + 1 ? gb : gc);
+        for (int k = 0; k < 3; ++k) gi[k] += g[k];
+    }
+    for (int s = i - 3; s <= i; ++s) {  // torsion (s .. s+3)
+        if (s < 0 || s + 3 >= n) continue;
+        R p[4][3];
+        for (int q = 0; q < 4; ++q) P(s + q, p[q]);
+        R b1[3], b2[3], b3[3];
+        for (int k = 0; k < 3; ++k) {
+            b1[k] = p[1][k] - p[0][k];
+            b2[k] = p[2][k] - p[1][k];
+            b3[k] = p[3][k] - p[2][k];
+        }
+        const R n1[3] = {b1[1] * b2[2] - b1[2] * b2[1], b1[2] * b2[0] - b1[0] * b2[2], b1[0] * b2[1] - b1[1] * b2[0]};
+        const R n2[3] = {b2[1] * b3[2] - b2[2] * b3[1], b2[2] * b3[0] - b2[0] * b3[2], b2[0] * b3[1] - b2[1] * b3[0]};
+        const R b2sq = b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2], nb2 = sqrt(b2sq);
+        const R phi = atan2(nb2 * (b1[0] * n2[0] + b1[1] * n2[1] + b1[2] * n2[2]),
+                            n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
+        const R dU = R(-3) * kt * sin(R(3) * phi);
+        const R n1sq = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+        const R n2sq = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
+        const R u = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) / b2sq;
+        const R v = (b3[0] * b2[0] + b3[1] * b2[1] + b3[2] * b2[2]) / b2sq;
+        const int q = i - s;
+        for (int k = 0; k < 3; ++k) {
+            const R g0 = -nb2 / n1sq * n1[k], g3 = nb2 / n2sq * n2[k];
+            R g = q == 0 ? g0 : (q == 3 ? g3 : (q == 1 ? -(R(1) + u) * g0 + v * g3 : -(R(1) + v) * g3 + u * g0));
+            gi[k] += dU * g;
+        }
+    }
+    f[o + i] = mk4<R>(-gi[0], -gi[1], -gi[2], R(0));
+}
+
+__global__ void philox_test_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t* q = in + 6 * i;
+    const U4 r = philox10(q[0], q[1], q[2], q[3], q[4], q[5]);
+    for (int k = 0; k < 4; ++k) out[4 * i + k] = r.v[k];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int setup_cells(wtmd_t* h)
+{
+    h->ncells = 0;
+    if (h->cfg.engine != WTMD_ENGINE_LJ || h->W != 1) return WTMD_OK;
+    int nc[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!(h->cfg.box[k] > 0)) return WTMD_OK;  // open boundaries: all pairs
+        nc[k] = (int)floor(h->cfg.box[k] / h->cfg.lj_rc);
+        if (nc[k] < 3) return WTMD_OK;             // too small for a 27-cell stencil
+    }
+    h->nc[0] = nc[0];
+    h->nc[1] = nc[1];
+    h->nc[2] = nc[2];
+    h->ncells = nc[0] * nc[1] * nc[2];
+    const double vol_cell = h->cfg.box[0] * h->cfg.box[1] * h->cfg.box[2] / h->ncells;
+    const double rho = (double)h->N / (h->cfg.box[0] * h->cfg.box[1] * h->cfg.box[2]);
+    int cap = (int)ceil(4.0 * rho * vol_cell + 32.0);
+    h->cell_cap = (cap + 31) / 32 * 32;
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_count, sizeof(int) * h->ncells));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
+    return WTMD_OK;
+}
+
+template <typename R> static int launch_engine_t(wtmd_t* h)
+{
+    const auto* x = (const R4<R>*)h->pos;
+    auto* f = (R4<R>*)h->force;
+    const int nb = (int)((h->N + 255) / 256);
+    cudaStream_t st = h->stream;
+    const wtmd_config& c = h->cfg;
+    switch (c.engine) {
+    case WTMD_ENGINE_NONE:
+        WTMD_CUDA_TRY(h, cudaMemsetAsync(f, 0, sizeof(R4<R>) * h->N, st));
+        mark(h, "zero_force");
+        break;
+    case WTMD_ENGINE_MB:
+        mb_kernel<R><<<nb, 256, 0, st>>>(h->N, x, f);
+        mark(h, "mb_force");
+        break;
+    case WTMD_ENGINE_LJ: {
+        const R rc2 = (R)(c.lj_rc * c.lj_rc), sig2 = (R)(c.lj_sigma * c.lj_sigma), e24 = (R)(24.0 * c.lj_eps);
+        if (h->ncells > 0) {
+            WTMD_CUDA_TRY(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * h->ncells, st));
+            cell_bin_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
+                                                   h->cell_count, h->cell_atoms, h->status);
+            mark(h, "lj_cell_bin");
+            cell_sort_kernel<<<(h->ncells + 127) / 128, 128, 0, st>>>(h->ncells, h->cell_cap, h->cell_count,
+                                                                      h->cell_atoms);
+            mark(h, "lj_cell_sort");
+            lj_cells_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
+                                                   h->cell_count, h->cell_atoms, rc2, sig2, e24, f);
+            mark(h, "lj_cell_force");
+        } else {
+            dim3 g((h->max_wn + 127) / 128, h->W);
+            lj_allpairs_kernel<R><<<g, 128, 0, st>>>(x, h->woff, h->wn, h->box, rc2, sig2, e24, f);
+            mark(h, "lj_allpairs");
+        }
+        break;
+    }
+    case WTMD_ENGINE_CHAIN: {
+        dim3 g((h->max_wn + 127) / 128, h->W);
+        chain_kernel<R><<<g, 128, 0, st>>>(x, h->woff, h->wn, (R)c.bond_k, (R)c.bond_r0, (R)c.angle_k,
+                                           (R)c.angle_theta0, (R)c.torsion_k, f);
+        mark(h, "chain_force");
+        break;
+    }
+    default:
+        h->err = "unknown engine";
+        return WTMD_EINVAL;
+    }
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+int launch_engine(wtmd_t* h)
+{
+    return h->prec == WTMD_F32 ? launch_engine_t<float>(h) : launch_engine_t<double>(h);
+}
+
+int launch_baoab_first(wtmd_t* h)
+{
+    const int nb = (int)((h->N + 255) / 256);
+    const wtmd_config& c = h->cfg;
+    const double c1 = exp(-c.friction * c.dt);
+    const double c2 = sqrt((1.0 - c1 * c1) * c.kT / c.mass);
+    if (h->prec == WTMD_F32)
+        baoab_first_kernel<float><<<nb, 256, 0, h->stream>>>(h->N, (float4*)h->pos, (float4*)h->vel,
+                                                             (const float4*)h->force, h->step, c.seed,
+                                                             (float)(0.5 * c.dt), (float)(1.0 / c.mass), (float)c1,
+                                                             (float)c2, h->dims);
+    else
+        baoab_first_kernel<double><<<nb, 256, 0, h->stream>>>(h->N, (dbl4*)h->pos, (dbl4*)h->vel,
+                                                              (const dbl4*)h->force, h->step, c.seed, 0.5 * c.dt,
+                                                              1.0 / c.mass, c1, c2, h->dims);
+    mark(h, "baoab_first");
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+}  // namespace wtmd
+
+extern "C" int wtmd_philox(const uint32_t* in_host, uint32_t* out_host, int64_t n)
+{
+    if (n <= 0 || !in_host || !out_host) return WTMD_EINVAL;
+    uint32_t *din = nullptr, *dout = nullptr;
+    if (cudaMalloc(&din, sizeof(uint32_t) * 6 * n) != cudaSuccess) return WTMD_ENOMEM;
+    if (cudaMalloc(&dout, sizeof(uint32_t) * 4 * n) != cudaSuccess) {
+        cudaFree(din);
+        return WTMD_ENOMEM;
+    }
+    cudaMemcpy(din, in_host, sizeof(uint32_t) * 6 * n, cudaMemcpyHostToDevice);
+    wtmd::philox_test_kernel<<<(unsigned)((n + 255) / 256), 256>>>(din, dout, n);
+    cudaError_t e = cudaMemcpy(out_host, dout, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+    cudaFree(din);
+    cudaFree(dout);
+    return e == cudaSuccess ? WTMD_OK : WTMD_ECUDA;
+}

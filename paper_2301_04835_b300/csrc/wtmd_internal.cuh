@@ -1,0 +1,298 @@
+// Internal declarations of libwtmd: device types, the handle, small device
+// helpers (Philox, reductions, mbarrier/bulk-copy PTX) and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wtmd.h"
+
+namespace wtmd {
+
+// ----------------------------------------------------------------------------
+// status bits recorded by kernels (atomicOr into Handle::status)
+// ----------------------------------------------------------------------------
+enum : unsigned {
+    ST_CAPACITY = 1u,
+    ST_NUMERIC = 2u,
+    ST_CELL = 4u,
+    ST_TIMEOUT = 8u,
+};
+
+// 32-byte aligned 4-vector of doubles (positions/forces in FP64 mode).
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <typename R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = dbl4; };
+template <typename R> using R4 = typename Vec4<R>::T;
+
+template <typename R> __host__ __device__ inline R4<R> mk4(R x, R y, R z, R w);
+template <> __host__ __device__ inline float4 mk4<float>(float x, float y, float z, float w) { return make_float4(x, y, z, w); }
+template <> __host__ __device__ inline dbl4 mk4<double>(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+// Periodic box: L[k] > 0 means periodic in k.  FP32 kernels use the edge as
+// an unevaluated sum Lf + Llo of two floats (Llo = L - Lf): rounding L to one
+// float would shift every boundary-crossing pair distance the same way, a
+// systematic error that sums over all pairs of a CV.
+struct Box {
+    double L[3];
+    double invL[3];
+    float Lf[3];
+    float Llo[3];
+};
+
+template <typename R> __device__ __forceinline__ R min_image(R d, const Box& b, int k);
+template <> __device__ __forceinline__ double min_image<double>(double d, const Box& b, int k)
+{
+    return b.L[k] > 0.0 ? d - b.L[k] * rint(d * b.invL[k]) : d;
+}
+template <> __device__ __forceinline__ float min_image<float>(float d, const Box& b, int k)
+{
+    if (!(b.Lf[k] > 0.f)) return d;
+    const float n = rintf(d * (float)b.invL[k]);
+    return fmaf(-n, b.Llo[k], fmaf(-n, b.Lf[k], d));
+}
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Device version.
+// ----------------------------------------------------------------------------
+struct U4 {
+    uint32_t v[4];
+};
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+    const uint32_t MA = 0xD2511F53u, MB = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t h0 = __umulhi(MA, c0), l0 = MA * c0;
+        const uint32_t h1 = __umulhi(MB, c2), l1 = MB * c2;
+        const uint32_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = l1;
+        c2 = n2;
+        c3 = l0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    U4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+// ----------------------------------------------------------------------------
+// shared-memory mbarrier + bulk-copy (TMA engine) wrappers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes and both
+// addresses must be multiples of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 SM cycles (about a second), records
+// ST_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ----------------------------------------------------------------------------
+// device-side CV description
+// ----------------------------------------------------------------------------
+struct CvDev {
+    int kind = 0, axis = 0, nn = 6, flags = 0;
+    int n_a = 0, n_b = 0;          // -1 = all atoms of the walker
+    int hidx[4] = {0, 0, 0, 0};    // host copy of small index lists (COMPONENT, DIHEDRAL)
+    int* a = nullptr;              // device, walker-local
+    int* b = nullptr;
+    int* inv_a = nullptr;          // device [max_wn]: position in A or -1
+    int* inv_b = nullptr;
+    double r0 = 1.0, scale = 0.0, period = 0.0;
+    bool same_ab = false;          // A and B are the same set (one pair pass, factor 2)
+    // QPAIRS: CSR from atom to (pair, sign)
+    int n_pairs = 0;
+    int* q_rowptr = nullptr;       // [max_wn + 1]
+    int* q_items = nullptr;        // [2*n_pairs]: pair index * 2 + (0: atom is i, 1: atom is j)
+    // scratch for pair passes
+    void* part_row = nullptr;      // [split][W][nT] R4
+    void* part_col = nullptr;
+    int split_row = 0, split_col = 0;
+    int nT_row = 0, nT_col = 0;    // per-walker target counts (max over walkers for "all")
+};
+
+// ----------------------------------------------------------------------------
+// the handle
+// ----------------------------------------------------------------------------
+struct Tuned {
+    int th = 0;       // hill lanes per point
+    int split = 0;    // hill splits
+};
+
+}  // namespace wtmd
+
+struct wtmd_t {
+    wtmd_config cfg{};
+    int prec = 0;
+    int d = 0;
+    int dims = 3;
+    int W = 1;
+    int64_t N = 0;
+    int max_wn = 0;
+    bool walkers_from_bind = false;
+    std::vector<int64_t> woff_h, wn_h;
+    int64_t* woff = nullptr;   // device [W]
+    int* wn = nullptr;         // device [W]
+    int* atom_walker = nullptr;  // device [N]
+    wtmd::CvDev cv[3];
+    int ncv = 0;
+    double a[3] = {0, 0, 0};   // sqrt(log2(e)/2)/sigma: scaled-CV factors of the FP32 hills sum
+    wtmd::Box box{};
+    // hills
+    int64_t cap = 0;
+    int64_t cap_pairs = 0;     // padded to a multiple of the chunk
+    double* hills64 = nullptr;     // [cap][4]
+    float4* hills32 = nullptr;     // [cap_pairs][2], pair-interleaved, pre-scaled, negated
+    long long* count = nullptr;    // device hill count
+    long long* step = nullptr;     // device step counter
+    long long* dep = nullptr;      // device [2]: first new hill, number of new hills this step
+    unsigned* status = nullptr;
+    double* grid = nullptr;
+    int64_t ncell = 0;
+    double* gfac = nullptr;        // [W][sum bins] per-axis Gaussian factors of new hills
+    int gbins_sum = 0;
+    // per-evaluation scratch
+    double* xi = nullptr;      // [W][4] CV values, FP64 in both precisions
+    double* ctr = nullptr;     // device [3]: CV centre of the scaled FP32 hill layout (NaN = unset)
+    void* V = nullptr;         // [W] R
+    void* dV = nullptr;        // [W][4] R
+    void* J = nullptr;         // [d][N] R4
+    void* partial = nullptr;   // hills partial sums
+    size_t partial_bytes = 0;
+    void* hev_xi = nullptr;    // hills_eval staging
+    size_t hev_bytes = 0;
+    // LJ cell list
+    int nc[3] = {0, 0, 0};
+    int ncells = 0;
+    int cell_cap = 0;
+    int* cell_count = nullptr;
+    int* cell_atoms = nullptr;
+    // bound arrays
+    void* pos = nullptr;
+    void* vel = nullptr;
+    void* force = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+    bool forces_valid = false;
+    // graphs
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    cudaGraphExec_t graph1 = nullptr;
+    // autotune cache: key = (P bucket, d) -> tile
+    std::vector<std::pair<long long, wtmd::Tuned>> tuned;
+    // profiling: when `prof` is set, mark() records a CUDA event on the
+    // launching stream after each kernel (eager steps only, never in graphs)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::string> ev_names;
+    int ev_n = 0;
+    std::string err;
+};
+
+namespace wtmd {
+inline void mark(wtmd_t* h, const char* name)
+{
+    if (!h->prof) return;
+    if (h->ev_n >= (int)h->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->ev_pool.push_back(e);
+        h->ev_names.emplace_back();
+    }
+    cudaEventRecord(h->ev_pool[h->ev_n], h->stream);
+    h->ev_names[h->ev_n] = name;
+    ++h->ev_n;
+}
+}  // namespace wtmd
+
+namespace wtmd {
+
+// launchers (defined in the .cu files); all enqueue on h->stream
+int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all CVs
+int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
+int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
+int launch_engine(wtmd_t* h);                                    // engine forces into h->force
+int launch_baoab_first(wtmd_t* h);
+int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
+int launch_grid_rebuild(wtmd_t* h);
+int launch_fes(wtmd_t* h, double* out);
+void store_hills32(wtmd_t* h);                                   // rebuild FP32 layout from hills64
+int setup_cells(wtmd_t* h);
+int cv_alloc_scratch(wtmd_t* h, CvDev& c);
+
+}  // namespace wtmd
+
+#define WTMD_CUDA_TRY(h, expr)                                                     \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            (h)->err = std::string(#expr) + ": " + cudaGetErrorString(_e);         \
+            return WTMD_ECUDA;                                                     \
+        }                                                                          \
+    } while (0)

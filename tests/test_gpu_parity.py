@@ -1,0 +1,397 @@
+"""GPU (libwtmd, through the C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances:
+  * FP64 handles: 1e-12 relative (V, dV/dxi, CVs, forces norm-wise).
+  * FP32 handles: 1e-5 relative.  V is a sum of positive terms: plain
+    relative error.  dV/dxi and the bias force are signed sums whose terms
+    can cancel (a walker inside a filled basin sits where the bias is flat);
+    there the bound is 1e-5 of the sum of the absolute terms,
+    S_c = sum_k w_k e_k |D_kc| / sigma_c^2 for dV/dxi_c and
+    F_scale,i = sum_c S_c |J_ci| for the force (norm-wise).  Without
+    cancellation these equal |dV| and |F|: the plain relative bound.
+The oracle always receives the inputs exactly as the GPU sees them (FP32
+handles: positions and points rounded to float first).
+"""
+import numpy as np
+import pytest
+
+import synth
+from systems import gpu_handle, lj_fluid_spec, oracle_system, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _wt():
+    import paper_2301_04835_b300 as wt
+    return wt
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def _close_V(Vg, Vr, prec):
+    tol = 1e-12 if prec == "f64" else 1e-5
+    assert np.all(np.abs(Vg - Vr) <= tol * np.abs(Vr) + 1e-300), np.max(np.abs(Vg - Vr) / np.maximum(np.abs(Vr), 1e-300))
+
+
+def grad_scale(pts, hills, sigma, period=None):
+    """S[p, c] = sum_k w_k e_k |D_kc| / sigma_c^2 (tolerance scale only)."""
+    pts = np.atleast_2d(pts)
+    d = pts.shape[1]
+    sig = np.asarray(sigma, float)[:d]
+    per = np.zeros(d) if period is None else np.asarray(period, float)[:d]
+    out = np.zeros((pts.shape[0], d))
+    for p in range(pts.shape[0]):
+        D = pts[p][None, :] - hills[:, :d]
+        D = np.where(per > 0, D - per * np.rint(D / np.where(per > 0, per, 1.0)), D)
+        e = hills[:, 3] * np.exp(-(D ** 2 / (2 * sig ** 2)).sum(1))
+        out[p] = (e[:, None] * np.abs(D)).sum(0) / sig ** 2
+    return out
+
+
+def _close_dV(dg, dr, S, prec):
+    """FP64: 1e-12 of |dV|; FP32: 1e-5 of the absolute-term sum S."""
+    if prec == "f64":
+        err = np.abs(dg - dr) / np.maximum(np.abs(dr), 1e-300)
+        ok = np.abs(dg - dr) <= 1e-12 * np.abs(dr) + 1e-13 * S
+    else:
+        err = np.abs(dg - dr) / np.maximum(S, 1e-300)
+        ok = err <= 1e-5
+    assert np.all(ok), err.max()
+
+
+def _close_F(Fg, Fr, prec, Fscale=None):
+    """FP64: ||dF|| <= 1e-12 ||F||.  FP32: ||dF|| <= 1e-5 ||F_scale||, where
+    F_scale,i = sum_c S_c |J_ci| and S_c = sum_k w_k e_k |D_kc| / sigma_c^2 is
+    the sum of the absolute gradient terms: a bias gradient that cancels to
+    a small fraction of its terms (a walker inside a filled basin) cannot be
+    resolved to 1e-5 of itself in FP32, only to 1e-5 of its terms.  Without
+    cancellation F_scale = |F| and this is the plain relative bound."""
+    tol = 1e-12 if prec == "f64" else 1e-5
+    den = np.linalg.norm(Fr) if (prec == "f64" or Fscale is None) else np.linalg.norm(Fscale)
+    assert np.linalg.norm(Fg - Fr) <= tol * den, np.linalg.norm(Fg - Fr) / den
+
+
+def force_scale(sim, x, hills, cvs_period):
+    """F_scale of _close_F from the oracle's CV Jacobians (tolerance only)."""
+    import oracle as o
+
+    sysd = sim.sys
+    sig = np.asarray(sysd.sigma[: len(sysd.cvs)])
+    per = np.asarray(cvs_period)
+    out = np.zeros_like(x)
+    off = 0
+    box = list(sysd.box)
+    for n in sysd.walker_n:
+        xw = x[off: off + n]
+        xi, Js = [], []
+        for cv in sysd.cvs:
+            v, J = o.cv_eval(cv, xw, box)
+            xi.append(v)
+            Js.append(J)
+        D = np.asarray(xi)[None, :] - hills[:, : len(xi)]
+        D = np.where(per > 0, D - per * np.rint(D / np.where(per > 0, per, 1.0)), D)
+        e = hills[:, 3] * np.exp(-(D ** 2 / (2 * sig ** 2)).sum(1))
+        S = (e[:, None] * np.abs(D)).sum(0) / sig ** 2
+        out[off: off + n] = sum(S[c] * np.abs(Js[c]) for c in range(len(xi)))
+        off += n
+    return out
+
+
+# --------------------------------------------------------------------------
+def test_philox_bitwise():
+    wt = _wt()
+    import oracle as o
+
+    r = synth.rng(5)
+    q = r.integers(0, 2 ** 32, size=(257, 6), dtype=np.uint64).astype(np.uint32)
+    out = wt.philox(q)
+    for i in range(q.shape[0]):
+        assert list(out[i]) == list(o.philox4x32_10(q[i, :4], q[i, 4:]))
+
+
+# --------------------------------------------------------------------------
+# hills sum
+# --------------------------------------------------------------------------
+HILL_CASES = [
+    # d, periodic, P, H
+    (1, False, 1, 1),
+    (2, False, 1, 1001),
+    (2, False, 5, 257),
+    (2, False, 40, 3001),
+    (2, True, 300, 2049),
+    (3, False, 2100, 513),
+    (3, True, 7, 999),
+    (1, True, 1100, 4097),
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("d,periodic,P,H", HILL_CASES)
+def test_hills_eval_matches_oracle(prec, d, periodic, P, H):
+    wt = _wt()
+    import oracle as o
+
+    sigma = [0.35, 0.2, 0.5][:d] if periodic else [0.05, 0.1, 0.07][:d]
+    lo, hi = ([-np.pi] * d, [np.pi] * d) if periodic else ([-1.0, 0.5, 2.0][:d], [1.5, 2.0, 3.0][:d])
+    per = [2 * np.pi] * d if periodic else [0.0] * d
+    hills = synth.uniform_hills(H, lo, hi, seed=d * 100 + P)
+    pts = synth.uniform_points(P, lo, hi, seed=d * 100 + P + 1)
+    m = wt.Wtmd(precision=prec, sigma=sigma, capacity=H + 3, walker_sizes=[1])
+    for i in range(d):
+        m.cv_define(wt.CV_COMPONENT, a=[0], axis=i, period=per[i])
+    m.hills_load(hills)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    x = torch.tensor(pts, dtype=dt, device="cuda")
+    V, dV = m.hills_eval(x)
+    torch.cuda.synchronize()
+    xr = _f32(pts) if prec == "f32" else pts
+    Vr, dVr = o.hills_sum(xr, hills, sigma, per)
+    _close_V(to_np(V), Vr, prec)
+    _close_dV(to_np(dV), dVr, grad_scale(xr, hills, sigma, per), prec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_hills_eval_edge_cases(prec):
+    wt = _wt()
+    dt = torch.float32 if prec == "f32" else torch.float64
+    m = wt.Wtmd(precision=prec, sigma=[0.1, 0.2], capacity=10, walker_sizes=[1])
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=1)
+    x = torch.tensor([[0.25, 0.375], [1.0, -2.0]], dtype=dt, device="cuda")  # exact in FP32
+    V, dV = m.hills_eval(x)  # no hills
+    assert torch.all(V == 0) and torch.all(dV == 0)
+    m.hills_load([[0.25, 0.375, 0.0, 2.0]])  # one hill: V(s) = w, dV(s) = 0
+    V, dV = m.hills_eval(x[:1])
+    assert abs(V.item() - 2.0) <= (1e-6 if prec == "f32" else 1e-15) * 2
+    assert torch.all(dV.abs() <= 1e-6)
+    V, dV = m.hills_eval(x[:0])  # zero points
+    assert V.numel() == 0
+    with pytest.raises(wt.WtmdError):
+        m.hills_load(np.zeros((11, 4)) + [0, 0, 0, 1])  # over capacity
+    with pytest.raises(wt.WtmdError):
+        m.hills_load([[0.0, 0.0, 0.0, -1.0]])  # negative height
+
+
+# --------------------------------------------------------------------------
+# bias_eval: CVs + hills + scatter on LJ systems
+# --------------------------------------------------------------------------
+def _bias_case(spec, x, prec, n_hills, seed=3):
+    wt = _wt()
+    import oracle as o
+
+    dt = torch.float32 if prec == "f32" else torch.float64
+    xin = _f32(x) if prec == "f32" else x
+    osys = oracle_system(spec)
+    sim = o.Sim(osys, x=xin)
+    _, xi0, _, _ = sim.bias(xin, hills=np.zeros((0, 4)))
+    d = len(spec["cvs"])
+    sig = np.asarray(spec["sigma"])
+    hills = synth.walk_hills(n_hills, xi0[0, :d] - 3 * sig, xi0[0, :d] + 3 * sig, 0.5 * sig, seed=seed)
+    Fr, xir, Vr, dVr = sim.bias(xin, hills=hills)
+    m = gpu_handle(spec, prec)
+    m.hills_load(hills)
+    pos = wt.particles(xin, dt)
+    F = torch.zeros_like(pos)
+    V, xi, dV = m.bias_eval(pos, F)
+    torch.cuda.synchronize()
+    per = [c.get("period", 0.0) for c in spec["cvs"]]
+    Fs = force_scale(sim, xin, hills, per)
+    S = grad_scale(xir[:, :d], hills, spec["sigma"], per)
+    return (to_np(F)[:, :3], to_np(xi), to_np(V), to_np(dV)), (Fr, xir[:, :d], Vr, dVr[:, :d], Fs, S)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bias_eval_lj_small(prec):
+    spec, x, L = lj_fluid_spec(n=500, n_tag=37, n_rg=20, seed=4, jitter=0.1)
+    (F, xi, V, dV), (Fr, xir, Vr, dVr, Fs, S) = _bias_case(spec, x, prec, 301)
+    tol = 1e-12 if prec == "f64" else 1e-6
+    assert np.allclose(xi, xir, rtol=tol, atol=0)
+    _close_V(V, Vr, prec)
+    _close_dV(dV, dVr, S, prec)
+    _close_F(F, Fr, prec, Fs)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_bias_eval_lj_4096_full_size(prec):
+    """The 4096-atom workload (512 tagged, 64-atom Rg) with 1e5 hills."""
+    spec, x, L = lj_fluid_spec(n=4096, seed=0)
+    (F, xi, V, dV), (Fr, xir, Vr, dVr, Fs, S) = _bias_case(spec, x, prec, 100000)
+    tol = 1e-12 if prec == "f64" else 1e-6
+    assert np.allclose(xi, xir, rtol=tol, atol=0)
+    _close_V(V, Vr, prec)
+    _close_dV(dV, dVr, S, prec)
+    _close_F(F, Fr, prec, Fs)
+
+
+CV_CASES = {
+    "component": [dict(kind="component", a=[7], axis=2)],
+    "dihedral_pbc": [dict(kind="dihedral", a=[3, 10, 11, 40], period=2 * np.pi)],
+    "coord_all": [dict(kind="coordination", a=None, r0=1.2, nn=6, mm=12)],
+    "coord_ab": [dict(kind="coordination", a=[1, 5, 9, 200], b=list(range(0, 300, 2)), r0=1.5, nn=8, mm=16)],
+    "rg_all_intensive": [dict(kind="rg", a=None, flags=1)],
+    "qpairs": [dict(kind="qpairs", a=[0, 1, 2, 5, 7, 3, 1, 9, 40, 41], r0=1.5, nn=6, mm=12)],
+    "three_cvs": [dict(kind="coordination", a=list(range(0, 500, 5)), r0=1.5),
+                  dict(kind="rg", a=list(range(100, 164))),
+                  dict(kind="qpairs", a=[0, 1, 2, 5, 7, 3, 1, 9], r0=1.5)],
+}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(CV_CASES))
+def test_bias_eval_each_cv(prec, name):
+    x, L = synth.fcc_lattice(500, 0.8, seed=9, jitter=0.1)
+    cvs = CV_CASES[name]
+    sig = [0.05, 0.1, 0.02][: len(cvs)]
+    if name == "dihedral_pbc":
+        sig = [0.35]
+    spec = dict(engine="lj", walker_sizes=[500], box=(L, L, L), sigma=sig, cvs=cvs, capacity=2000)
+    (F, xi, V, dV), (Fr, xir, Vr, dVr, Fs, S) = _bias_case(spec, x, prec, 777)
+    tol = 1e-12 if prec == "f64" else 1e-6
+    assert np.allclose(xi, xir, rtol=tol, atol=tol)
+    _close_V(V, Vr, prec)
+    _close_F(F, Fr, prec, Fs)
+
+
+def test_bias_eval_many_walkers_chain_dihedrals():
+    """1024 replicas of a 22-bead chain, two dihedral CVs (beads 5-7-9-15 and
+    7-9-15-17, 0-based), periodic, sigma 0.35 rad: every replica's forces."""
+    x = synth.chain_replicas(1024, 22, seed=2)
+    spec = dict(engine="chain", walker_sizes=[22] * 1024, sigma=(0.35, 0.35), gamma=6.0,
+                cvs=[dict(kind="dihedral", a=[5, 7, 9, 15], period=2 * np.pi),
+                     dict(kind="dihedral", a=[7, 9, 15, 17], period=2 * np.pi)], capacity=1000)
+    for prec in ("f64", "f32"):
+        wt = _wt()
+        import oracle as o
+
+        xin = _f32(x) if prec == "f32" else x
+        hills = synth.uniform_hills(500, [-np.pi, -np.pi], [np.pi, np.pi], seed=4)
+        sim = o.Sim(oracle_system(spec), x=xin)
+        Fr, xir, Vr, dVr = sim.bias(xin, hills=hills)
+        m = gpu_handle(spec, prec)
+        m.hills_load(hills)
+        dt = torch.float32 if prec == "f32" else torch.float64
+        pos = wt.particles(xin, dt)
+        F = torch.zeros_like(pos)
+        V, xi, dV = m.bias_eval(pos, F)
+        torch.cuda.synchronize()
+        dphi = np.mod(to_np(xi) - xir[:, :2] + np.pi, 2 * np.pi) - np.pi  # periodic CVs: compare modulo 2 pi
+        assert np.abs(dphi).max() <= (1e-12 if prec == "f64" else 1e-5), np.abs(dphi).max()
+        _close_V(to_np(V), Vr, prec)
+        _close_F(to_np(F)[:, :3], Fr, prec, force_scale(sim, xin, hills, [2 * np.pi, 2 * np.pi]))
+
+
+# --------------------------------------------------------------------------
+# trajectories
+# --------------------------------------------------------------------------
+def _run_pair(spec, x, v, nsteps, prec, hills=None):
+    wt = _wt()
+    import oracle as o
+
+    dt = torch.float32 if prec == "f32" else torch.float64
+    xin = _f32(x) if prec == "f32" else x
+    vin = _f32(v) if prec == "f32" else v
+    sim = o.Sim(oracle_system(spec), x=xin, v=vin, hills=hills)
+    sim.forces()
+    rc = sim.run(nsteps)
+    m = gpu_handle(spec, prec)
+    if hills is not None:
+        m.hills_load(hills)
+    pos, vel = wt.particles(xin, dt), wt.particles(vin, dt)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(nsteps)
+    torch.cuda.synchronize()
+    return m, sim, rc, to_np(pos)[:, :3], to_np(vel)[:, :3]
+
+
+def test_trajectory_mueller_brown_fp64_with_deposition():
+    """Config-1 physics (kT = 15, dt = 1e-4, friction 1, sigma 0.05, w0 1,
+    gamma 10) with a short stride so hills feed back within 100 steps."""
+    spec = dict(engine="mb", walker_sizes=[1, 1, 1], dims=2, dt=1e-4, friction=1.0, kT=15.0, seed=0,
+                sigma=(0.05, 0.05), w0=1.0, gamma=10.0, stride=10, capacity=100,
+                grid=((64, 48), (-1.5, -0.5), (1.2, 2.2)),
+                cvs=[dict(kind="component", a=[0], axis=0), dict(kind="component", a=[0], axis=1)])
+    x = np.array([[-0.558, 1.442, 0], [0.623, 0.028, 0], [-0.05, 0.467, 0]])
+    v = np.zeros_like(x)
+    m, sim, rc, X, Vv = _run_pair(spec, x, v, 100, "f64")
+    assert rc == 0
+    assert np.max(np.abs(X - sim.x)) < 1e-6
+    assert np.max(np.abs(X - sim.x)) < 1e-10  # in practice: rounding level
+    h = m.hills_read()
+    assert h.shape[0] == sim.n_hills == 30
+    assert np.allclose(h, sim.hills[:30], rtol=1e-12, atol=1e-13)
+    g = m.grid_read().ravel()
+    assert np.allclose(g, sim.grid, rtol=1e-12, atol=1e-12 * np.abs(sim.grid).max())
+    F = to_np(m.fes_grid()).ravel()
+    assert np.allclose(F, sim.fes(), rtol=1e-12, atol=1e-10)
+    step, n = m.counters()
+    assert step == 100 and n == 30
+
+
+def test_trajectory_lj_fp64_100_steps():
+    spec, x, L = lj_fluid_spec(n=500, n_tag=50, n_rg=20, seed=7, jitter=0.05)
+    spec.update(stride=10, capacity=100)
+    v = synth.velocities(500, 1.0, 1.0, seed=8)
+    m, sim, rc, X, Vv = _run_pair(spec, x, v, 100, "f64")
+    assert rc == 0
+    assert np.max(np.abs(X - sim.x)) < 1e-6
+    h = m.hills_read()
+    assert h.shape[0] == sim.n_hills == 10
+    assert np.allclose(h, sim.hills[:10], rtol=1e-9, atol=1e-10)
+
+
+def test_trajectory_lj_fp32_against_fp64_oracle():
+    """FP32 engine with identical Philox streams: after 100 steps the
+    positions agree with the FP64 oracle to ~1e-4 (FP32 rounding grows with
+    the chaotic LJ dynamics; the 1e-6 trajectory bar is met in FP64)."""
+    spec, x, L = lj_fluid_spec(n=500, n_tag=50, n_rg=20, seed=7, jitter=0.05)
+    spec.update(stride=10, capacity=100)
+    v = synth.velocities(500, 1.0, 1.0, seed=8)
+    m, sim, rc, X, Vv = _run_pair(spec, x, v, 100, "f32")
+    assert rc == 0
+    assert np.max(np.abs(X - sim.x)) < 1e-3
+    assert np.median(np.abs(X - sim.x)) < 1e-5
+
+
+def test_trajectory_cell_list_4096_fp64_20_steps():
+    spec, x, L = lj_fluid_spec(n=4096, seed=0)
+    spec.update(stride=5, capacity=100)
+    v = synth.velocities(4096, 1.0, 1.0, seed=1)
+    m, sim, rc, X, Vv = _run_pair(spec, x, v, 20, "f64")
+    assert np.max(np.abs(X - sim.x)) < 1e-6
+
+
+def test_capacity_overflow_is_reported():
+    wt = _wt()
+    spec = dict(engine="mb", walker_sizes=[1, 1], dims=2, dt=1e-4, kT=15.0, sigma=(0.05, 0.05), stride=2,
+                capacity=5, cvs=[dict(kind="component", a=[0], axis=0), dict(kind="component", a=[0], axis=1)])
+    m = gpu_handle(spec, "f64")
+    pos = wt.particles([[-0.5, 1.4, 0], [0.6, 0.0, 0]], torch.float64)
+    vel, F = torch.zeros_like(pos), torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(4)  # 4 hills
+    with pytest.raises(wt.WtmdError) as e:
+        m.step_n(2)  # would need 6
+    assert e.value.code == wt.ECAPACITY
+    assert m.counters()[1] == 4
+
+
+def test_invalid_arguments_are_rejected():
+    wt = _wt()
+    m = wt.Wtmd(precision="f64", sigma=[0.1], walker_sizes=[10])
+    for bad in [dict(kind=wt.CV_DIHEDRAL, a=[0, 1, 2]), dict(kind=wt.CV_DIHEDRAL, a=[0, 1, 1, 2]),
+                dict(kind=wt.CV_COMPONENT, a=[10]), dict(kind=wt.CV_COORDINATION, a=[0, 1], nn=6, mm=10),
+                dict(kind=wt.CV_COORDINATION, a=[0, 1], nn=5, mm=10), dict(kind=99, a=[0])]:
+        with pytest.raises(wt.WtmdError):
+            m.cv_define(**bad)
+    m.cv_define(wt.CV_RG, a=None)
+    with pytest.raises(wt.WtmdError):
+        m.cv_define(wt.CV_RG, a=None)  # more than n_cv
+    assert wt.lib().fes_grid(m.h, None, 0) == wt.EINVAL  # no grid configured
+    with pytest.raises(wt.WtmdError):
+        wt.Wtmd(precision="f64", sigma=[0.1], gamma=0.5, walker_sizes=[1])
