@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the WTMD bias-force pipeline on one B300 (or N replicas).
+
+Workload (the 4096-atom Lennard-Jones configuration): LJ fluid N = 4096,
+rho* = 0.8, T* = 1.0, rc = 2.5 sigma with a cell list, BAOAB dt = 0.005,
+friction 1; two CVs -- the mean coordination of 512 tagged atoms (rational
+switch r0 = 1.5, n = 6, m = 12) and the radius of gyration of a 64-atom
+subset; well-tempered metadynamics sigma = (0.05, 0.1), gamma = 8, w0 = 1,
+kT = 1, one hill every 100 steps, on top of 1e5 pre-deposited hills; FP32.
+A bench step is one full MD step: engine forces, CVs + Jacobians, hills sum,
+bias-force scatter, integration and deposition.  Inputs are synthetic and
+seeded (no dataset).  The L2 cache (126 MB) is flushed between timed steps.
+
+Extra figures on the same line: the hills-sum kernel at 1e6 hills and
+P = 1 ... 4096 evaluation points against the measured MUFU/FP32 pipe peaks,
+per-kernel times, the end-to-end rate with host buffers, the FP64 oracle on
+the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bias-force evals/s and hill-evals/s (10⁶ hills), % MUFU roofline, MD steps/s"
+N_ATOMS, RHO, N_TAG, N_RG, H_PRE = 4096, 0.8, 512, 64, 100000
+SIGMA = (0.05, 0.1)
+WORKLOAD = dict(workload="LJ fluid N=4096 rho*=0.8 T*=1 rc=2.5 cell list dt=0.005; CVs: mean coordination "
+                         "of 512 tagged atoms (r0=1.5, n=6, m=12) + Rg of 64 atoms; WTMD sigma=(0.05,0.1) "
+                         "gamma=8 w0=1 stride=100 on 1e5 pre-deposited hills; FP32",
+                n_atoms=N_ATOMS, n_cv=2, hills=H_PRE, precision="f32", l2="flushed between timed steps")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-micro", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# workload construction (shared by both arms; inputs from synth only)
+# --------------------------------------------------------------------------
+def workload_inputs(seed: int):
+    import synth
+
+    x, L = synth.lattice(N_ATOMS, RHO, seed=seed, jitter=0.05)
+    tag = synth.permutation_subset(N_ATOMS, N_TAG, seed + 1)
+    rg = synth.nearest_subset(x, L, N_RG, seed + 2)
+    v = synth.velocities(N_ATOMS, 1.0, 1.0, seed=seed + 3)
+    return x, v, L, tag, rg
+
+
+def hills_around(xi0, seed):
+    import synth
+
+    sig = np.asarray(SIGMA)
+    return synth.walk_hills(H_PRE, xi0 - 3 * sig, xi0 + 3 * sig, 0.5 * sig, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines()[1:] if l.strip()]
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0]))
+                mx = max(mx, float(r[2].split()[0]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# roofline bookkeeping
+# --------------------------------------------------------------------------
+def peaks():
+    p = {}
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    return p.get("hbm_gbs", 6400.0), ("measured" if "hbm_gbs" in p else "fallback")
+
+
+def src_sha(*names):
+    h = hashlib.sha1()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_2301_04835_b300", "csrc", n), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(kernel: str, sha: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else null)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        c = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(c) >= 3 and c[0] == kernel and c[1] == sha:
+            try:
+                return float(c[2])
+            except ValueError:
+                return None
+    return None
+
+
+KERNEL_SRC = {"lj_cell_force": "engine.cu", "lj_cell_bin": "engine.cu", "lj_cell_sort": "engine.cu",
+              "baoab_first": "engine.cu", "coord_pair_row": "cv.cu", "coord_pair_col": "cv.cu",
+              "coord_finalize": "cv.cu", "coord_value": "cv.cu", "cv_rg": "cv.cu", "scatter_kick": "cv.cu",
+              "hills_partial_f32": "hills.cu", "hills_finalize": "hills.cu", "deposit": "deposit.cu"}
+
+
+def algorithmic(kernel: str, n_hills: int):
+    """Algorithmic (compulsory) DRAM bytes of one launch in the 4096-atom step."""
+    r4 = 16
+    table = {
+        "baoab_first": N_ATOMS * r4 * 5,           # read x, v, f; write x, v
+        "lj_cell_bin": N_ATOMS * (r4 + 4),         # read x, write cell slots
+        "lj_cell_force": N_ATOMS * (r4 + r4 + 4),  # read x (once), cell lists, write f
+        "coord_pair_row": N_ATOMS * r4 + N_TAG * r4,
+        "coord_pair_col": N_ATOMS * r4 + N_TAG * r4,
+        "coord_finalize": N_ATOMS * r4,
+        "cv_rg": N_RG * r4 * 2,
+        "hills_partial_f32": ((n_hills + 1) // 2) * 32,  # hill-pair records read once
+        "scatter_kick": N_ATOMS * r4 * 6,           # f, 2 J rows, v in; f, v out
+    }
+    return table.get(kernel)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2301_04835_b300 as wt
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    x, v, L, tag, rg = workload_inputs(seed=rank)
+    m = wt.Wtmd(precision="f32", sigma=SIGMA, w0=1.0, gamma=8.0, kT=1.0, stride=100,
+                capacity=H_PRE + 100000, seed=rank, engine="lj", walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005,
+                friction=1.0)
+    m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+    m.cv_define(wt.CV_RG, a=rg)
+    pos = wt.particles(x, torch.float32)
+    vel = wt.particles(v, torch.float32)
+    F = torch.zeros_like(pos)
+    _, xi0, _ = m.bias_eval(pos)
+    m.hills_load(hills_around(xi0[0].double().cpu().numpy(), seed=100 + rank))
+    m.bind(pos, vel, F)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (graph capture happens on the first call)
+    m.step_n(max(args.warmup, 3), check=True)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev.index) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict L2 between timed steps (not timed)
+            ev[i][0].record(stream)
+            m.step_n(1, check=False)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    m.check()
+    dev_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    ms_tensor = torch.tensor([dev_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_tensor, op=torch.distributed.ReduceOp.MAX)
+    dev_ms_max = float(ms_tensor.item())
+
+    # steady state: K steps as one step_n call (graph replays), no flush
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.step_n(args.steps, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    steady_ms = e0.elapsed_time(e1)
+
+    # per-kernel device times (events between kernels, eager launches)
+    prof = m.profile_step(20)
+    kernels_per_step = len(prof)
+    n_hills = m.counters()[1]
+
+    # end to end through the public API with host buffers
+    hx = torch.empty_like(pos, device="cpu").pin_memory()
+    hv = torch.empty_like(pos, device="cpu").pin_memory()
+    hf = torch.empty_like(pos, device="cpu").pin_memory()
+    hx.copy_(pos.cpu())
+    hv.copy_(vel.cpu())
+    hf.copy_(F.cpu())
+    ox, ov, of = (torch.empty_like(hx).pin_memory() for _ in range(3))
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ee[i][0].record(stream)
+        pos.copy_(hx, non_blocking=True)
+        vel.copy_(hv, non_blocking=True)
+        F.copy_(hf, non_blocking=True)
+        m.step_n(1, check=False)
+        ox.copy_(pos, non_blocking=True)
+        ov.copy_(vel, non_blocking=True)
+        of.copy_(F, non_blocking=True)
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    m.check()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in ee))
+    bytes_step = 3 * N_ATOMS * 16
+
+    micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
+    return dict(dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+                kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
+                micro=micro)
+
+
+def hills_micro(wt, torch, dev, flush):
+    """Hills sum alone: 1e6 hills, P points, d = 2 and 3, against the
+    measured MUFU ex2 and FP32 FMA rates (taken right before)."""
+    import synth
+
+    ex2, _ = wt.probe_peak(0)
+    fma, _ = wt.probe_peak(1)
+    out = {"ex2_per_s_measured": ex2, "fp32_lane_ops_per_s_measured": fma, "cases": []}
+    stream = torch.cuda.current_stream()
+    H = 1_000_000
+    for d, sig in ((2, (0.05, 0.1)), (3, (0.05, 0.1, 0.02))):
+        lo, hi = [0.0] * d, [1.0] * d
+        m = wt.Wtmd(precision="f32", sigma=sig, capacity=H, walker_sizes=[1])
+        for i in range(d):
+            m.cv_define(wt.CV_COMPONENT, a=[0], axis=i)
+        m.hills_load(synth.uniform_hills(H, lo, hi, seed=11 + d))
+        ops = {2: 7, 3: 10}[d]
+        for P in (1, 256, 1024, 4096):
+            pts = torch.tensor(synth.uniform_points(P, lo, hi, seed=P + d), dtype=torch.float32, device=dev)
+            V = torch.empty(P, dtype=torch.float32, device=dev)
+            dV = torch.empty(P, d, dtype=torch.float32, device=dev)
+            for _ in range(3):
+                m.hills_eval_into(pts, V, dV)
+            reps = 5 if P >= 1024 else 20
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in evs:
+                flush.fill_(1.0)
+                a.record(stream)
+                m.hills_eval_into(pts, V, dV)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+            rate = P * H / (ms * 1e-3)
+            peak = min(ex2, fma / ops)
+            out["cases"].append(dict(d=d, P=P, hills=H, ms=ms, hill_evals_per_s=rate,
+                                     bound="mufu" if ex2 <= fma / ops else "fp32",
+                                     frac_of_measured_pipe_peak=rate / peak,
+                                     hbm_gbs=(H * 16) / (ms * 1e-3) / 1e9))
+        m.close()
+    return out
+
+
+def cpu_baseline_oracle(seconds: float, max_steps: int | None = None):
+    """The FP64 oracle on the host cores, same workload, bounded sample."""
+    import oracle as o
+
+    x, v, L, tag, rg = workload_inputs(seed=0)
+    cvs = [o.CV(o.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12), o.CV(o.CV_RG, a=rg)]
+    s = o.System(engine=o.ENGINE_LJ, walker_n=[N_ATOMS], cvs=cvs, box=(L, L, L), dt=0.005, friction=1.0, kT=1.0,
+                 sigma=SIGMA, w0=1.0, gamma=8.0, stride=100, hill_cap=H_PRE + 10000)
+    sim = o.Sim(s, x=x, v=v)
+    _, xi0, _, _ = sim.bias(x, hills=np.zeros((0, 4)))
+    h = hills_around(xi0[0, :2], seed=100)
+    sim = o.Sim(s, x=x, v=v, hills=h)
+    sim.forces()
+    n, t0 = 0, time.perf_counter()
+    times = []
+    while True:
+        a = time.perf_counter()
+        sim.run(1)
+        times.append(time.perf_counter() - a)
+        n += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and n >= max_steps) or (max_steps is None and el >= seconds):
+            break
+    return n, times, o.num_threads()
+
+
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    K = args.steps
+    value = world * K / (r["dev_ms"] * 1e-3)
+    prof = r["prof"]
+    dom_name, dom_ms = max(prof, key=lambda t: t[1])
+    hbm, peak_kind = peaks()
+    alg = algorithmic(dom_name, r["n_hills"])
+    roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+            "traffic": None, "peak_source": peak_kind}
+    if alg is not None:
+        ach = alg / (dom_ms * 1e-3) / 1e9
+        roof.update(achieved=ach, frac=ach / hbm, algorithmic_bytes=alg, ms=dom_ms)
+    sha = src_sha(KERNEL_SRC.get(dom_name, "api.cu"))
+    roof["traffic"] = traffic_for(dom_name, sha)
+    roof["source_sha"] = sha
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": r["dev_ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}"),
+        "roofline": roof, "gpu_launches": K * r["kernels_per_step"], "clocks": r["clocks"],
+        "e2e": {"value": world * K / (r["e2e_ms"] * 1e-3), "unit": "steps/s",
+                "h2d_bytes_per_step": r["e2e_bytes"], "d2h_bytes_per_step": r["e2e_bytes"]},
+        "steady_state_steps_per_s": world * K / (r["steady_ms"] * 1e-3),
+        "wall_s": r["wall"],
+        "kernels_ms": {k: round(v, 5) for k, v in prof},
+        "hills_sum_1e6": r["micro"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        n, times, cores = cpu_baseline_oracle(seconds=15.0)
+        line["cpu_baseline"] = {"value": n / float(np.sum(times)), "unit": "steps/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{n} full MD steps of the same workload (FP64 oracle, all-pairs LJ)"}
+    print(json.dumps(line))
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle timed as it stands on the host
+    cores, on this workload (rank 0 only)."""
+    if rank != 0:
+        return
+    n_total = args.warmup + args.steps
+    n, times, cores = cpu_baseline_oracle(seconds=0.0, max_steps=n_total)
+    timed = float(np.sum(times[args.warmup:]))
+    val = args.steps / timed
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * timed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, precision="f64", parallelism="host cores"),
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed full MD steps after {args.warmup} warm-up"},
+            "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
