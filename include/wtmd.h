@@ -203,6 +203,28 @@ int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32
  * measured denominators of the hills-sum roofline; *ms = kernel time. */
 int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
 
+/* Hills sum for callers that cannot allocate device memory (the paper has no
+ * counterpart: it is an interface for hosts such as an engine plugin that may
+ * only touch the buffers it is given, or a caller whose memory footprint
+ * must stay fixed after start-up).  Same quantity as hills_eval on a WTMD_F64
+ * handle, without a handle: V_out[p] and dV_out[p][i] for P points xi
+ * (device [P][n_cv] double) over n_hills hills (device [n_hills][4] double =
+ * (s0, s1, s2, w), 32-byte aligned), widths sigma and periods period (host
+ * [n_cv] double; period NULL or 0 = not periodic).  Calls no cudaMalloc,
+ * cudaFree or other allocating routine: its partial sums use a fixed
+ * library-owned device array of WTMD_STATIC_MAX_POINTS x 32 bytes (1 MiB)
+ * that every GPU loading the library keeps until exit.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * kernels overlap on the GPU race, so serialize them.  Work is enqueued on
+ * `stream` (cudaStream_t, NULL = default).  Errors: WTMD_EINVAL when
+ * P > WTMD_STATIC_MAX_POINTS, for bad sizes, sigma <= 0, negative periods,
+ * null or misaligned pointers; WTMD_ECUDA if a CUDA call fails. */
+#define WTMD_STATIC_MAX_POINTS 32768
+int wtmd_hills_eval_static(int32_t n_cv, const double* sigma, const double* period, const double* hills,
+                           int64_t n_hills, const double* xi, int64_t P, double* V_out, double* dV_out,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,7 +63,8 @@ class CvDesc(C.Structure):
 
 EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", "cv_define", "wtmd_bind", "step_n",
            "wtmd_check", "bias_eval", "hills_eval", "fes_grid", "wtmd_hills_load", "wtmd_hills_read",
-           "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak"]
+           "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
+           "wtmd_hills_eval_static"]
 
 _lib = None
 
@@ -96,6 +97,8 @@ def lib() -> C.CDLL:
     L.wtmd_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64]
     L.wtmd_profile_step.argtypes = [vp, i64, C.c_char_p, C.POINTER(C.c_double), i32, C.POINTER(i32)]
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
+                                         vp, vp]
     for name in EXPORTS:
         if not hasattr(L, name):
             raise ImportError(f"libwtmd.so lacks {name}")
