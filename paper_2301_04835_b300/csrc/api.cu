@@ -63,6 +63,10 @@ static void free_cv(CvDev& c)
     cudaFree(c.inv_b);
     cudaFree(c.q_rowptr);
     cudaFree(c.q_items);
+    cudaFree(c.order);
+    cudaFree(c.scw);
+    cudaFree(c.tile_row);
+    cudaFree(c.tile_col);
     cudaFree(c.part_row);
     cudaFree(c.part_col);
     c = CvDev();
@@ -75,11 +79,19 @@ extern "C" int wtmd_destroy(wtmd_t* h)
     cudaDeviceSynchronize();
     drop_graphs(h);
     for (int i = 0; i < h->ncv; ++i) free_cv(h->cv[i]);
-    void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status,
+    void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status, h->ticket,
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
                     h->cell_atoms};
     for (void* p : ptrs) cudaFree(p);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    for (int c = 0; c < 3; ++c) {
+        if (h->cv_stream[c]) cudaStreamDestroy(h->cv_stream[c]);
+        if (h->ev_cv[c]) cudaEventDestroy(h->ev_cv[c]);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
     delete h;
     return WTMD_OK;
 }
@@ -145,14 +157,22 @@ extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
         h->box.invL[k] = c.box[k] > 0.0 ? 1.0 / c.box[k] : 0.0;
         h->box.Lf[k] = (float)h->box.L[k];
         h->box.Llo[k] = (float)(h->box.L[k] - (double)h->box.Lf[k]);
+        h->box.invLf[k] = (float)h->box.invL[k];
     }
     auto fail = [&](int code, const char* m) {
         h->err = m;
         wtmd_destroy(h);
         return code;
     };
-    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return fail(WTMD_ECUDA, "stream");
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(WTMD_ECUDA, "streams");
+    for (int c = 1; c < 3; ++c)
+        if (cudaStreamCreateWithFlags(&h->cv_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_cv[c], cudaEventDisableTiming) != cudaSuccess)
+            return fail(WTMD_ECUDA, "streams");
     // walkers
     std::vector<int> aw(h->N), wn32(h->W);
     for (int w = 0; w < h->W; ++w) {
@@ -176,12 +196,14 @@ extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
     cudaMemset(h->hills64, 0, 32 * (size_t)std::max<int64_t>(h->cap, 1));
     pad_hills32_kernel<<<(unsigned)((h->cap_pairs + 255) / 256), 256>>>(h->hills32, h->cap_pairs);
     if (cudaMalloc(&h->count, sizeof(long long)) || cudaMalloc(&h->step, sizeof(long long)) ||
-        cudaMalloc(&h->dep, 2 * sizeof(long long)) || cudaMalloc(&h->status, sizeof(unsigned)))
+        cudaMalloc(&h->dep, 2 * sizeof(long long)) || cudaMalloc(&h->status, sizeof(unsigned)) ||
+        cudaMalloc(&h->ticket, sizeof(unsigned)))
         return fail(WTMD_ENOMEM, "counters");
     cudaMemset(h->count, 0, sizeof(long long));
     cudaMemset(h->step, 0, sizeof(long long));
     cudaMemset(h->dep, 0, 2 * sizeof(long long));
     cudaMemset(h->status, 0, sizeof(unsigned));
+    cudaMemset(h->ticket, 0, sizeof(unsigned));
     // grid
     h->ncell = 0;
     h->gbins_sum = 0;
@@ -320,8 +342,20 @@ extern "C" int cv_define(wtmd_t* h, const wtmd_cv_desc* d, int32_t* cv_id)
             for (int64_t p = 0; p < d->n_b; ++p) inv[d->b[p]] = (int)p;
             if (upload(d->b, d->n_b, &c.b) || upload(inv.data(), h->max_wn, &c.inv_b)) FAIL(h, WTMD_ENOMEM, "B");
         }
-        if (h->W > 1 && (d->n_a == -1) != (d->n_b == -1) && c.n_a != -1) {
-            // explicit lists are shared by all walkers; fine
+        // target order: members of A (in A's order), then members of B not in
+        // A (increasing); "all" means every atom index below the largest
+        // walker size (kernels skip indices beyond a walker's own size)
+        if (!(d->n_a == -1)) {
+            std::vector<char> inA(h->max_wn, 0);
+            for (int64_t p = 0; p < d->n_a; ++p) inA[d->a[p]] = 1;
+            std::vector<int> ord(d->a, d->a + d->n_a);
+            for (int k = 0; k < h->max_wn; ++k) {
+                bool inB = d->n_b == -1;
+                if (!inB) inB = std::find(d->b, d->b + d->n_b, k) != d->b + d->n_b;
+                if (inB && !inA[k]) ord.push_back(k);
+            }
+            c.n_order = (int)ord.size();
+            if (upload(ord.data(), (int64_t)ord.size(), &c.order)) FAIL(h, WTMD_ENOMEM, "target order");
         }
         break;
     }
@@ -366,13 +400,48 @@ static int enqueue_forces(wtmd_t* h)
     return launch_scatter(h, h->force, nullptr, false);
 }
 
+// Engine force and bias (CVs -> hills sum) both only read the positions, so
+// the engine runs on a side stream forked from and joined back to the main
+// stream (parallel branches of the captured graph).  While profiling, the two
+// run in sequence so that each kernel's event interval is its own.
+static int enqueue_engine_and_bias(wtmd_t* h)
+{
+    int rc;
+    const bool fork = !h->prof;
+    if (fork) {
+        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+        WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
+        cudaStream_t main_stream = h->stream;
+        h->stream = h->side_stream;
+        rc = launch_engine(h);
+        h->stream = main_stream;
+        if (rc) return rc;
+        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side_stream));
+    } else if ((rc = launch_engine(h))) {
+        return rc;
+    }
+    // CVs 1 and 2 on their own branches, CV 0 on the main stream
+    cudaStream_t main_stream = h->stream;
+    for (int c = 1; c < h->ncv && fork; ++c) {
+        WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->cv_stream[c], h->ev_fork, 0));
+        h->stream = h->cv_stream[c];
+        rc = launch_cv(h, h->pos, c);
+        h->stream = main_stream;
+        if (rc) return rc;
+        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_cv[c], h->cv_stream[c]));
+    }
+    if ((rc = fork ? launch_cv(h, h->pos, 0) : launch_cvs(h, h->pos))) return rc;
+    for (int c = 1; c < h->ncv && fork; ++c) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0));
+    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if (fork) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    return WTMD_OK;
+}
+
 static int enqueue_step(wtmd_t* h)
 {
     int rc;
     if ((rc = launch_baoab_first(h))) return rc;
-    if ((rc = launch_engine(h))) return rc;
-    if ((rc = launch_cvs(h, h->pos))) return rc;
-    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if ((rc = enqueue_engine_and_bias(h))) return rc;
     if ((rc = launch_scatter(h, h->force, h->vel, true))) return rc;
     return launch_deposit(h);
 }
@@ -564,6 +633,21 @@ extern "C" int wtmd_grid_read(wtmd_t* h, double* out, int64_t n_out)
     return WTMD_OK;
 }
 
+// Holds the stream for a fixed time (bounded by its argument, at most 2 ms)
+// so that the host can enqueue a whole profiled step behind it: the step's
+// kernels then run back to back and the events between them measure device
+// time, not host launch gaps.
+__global__ static void delay_kernel(long long ns)
+{
+    if (threadIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    } while ((long long)(t - t0) < ns && (long long)(t - t0) < 2000000);
+}
+
 extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32_t cap, int32_t* n_out)
 {
     if (!h) return WTMD_EINVAL;
@@ -581,6 +665,7 @@ extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double
     h->prof = true;
     for (int64_t s = 0; s < n_steps; ++s) {
         h->ev_n = 0;
+        delay_kernel<<<1, 32, 0, h->stream>>>(500000);
         mark(h, "start");
         rc = enqueue_step(h);
         if (rc) break;

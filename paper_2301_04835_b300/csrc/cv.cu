@@ -11,6 +11,9 @@
 // (target tile x source split) blocks with the sources staged in shared
 // memory, followed by a fixed-order reduction over the splits: no atomics, so
 // results are bitwise reproducible.
+#include <algorithm>
+#include <vector>
+
 #include "wtmd_internal.cuh"
 
 namespace wtmd {
@@ -47,6 +50,26 @@ template <typename T, int NV> __device__ void block_sum(T v[NV])
         T s = 0;
         for (int w = 0; w < nw; ++w) s += sm[w][k];
         v[k] = s;
+    }
+}
+
+// Deterministic block-wide compensated FP32 sum of NV values; every thread
+// gets the totals.
+template <int NV> __device__ void block_sum_cf(cf v[NV])
+{
+    __shared__ cf sm[32][NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] = cf_add(v[k], cf_shfl_xor(v[k], o));
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) sm[warp][k] = v[k];
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) {
+        cf t = sm[0][k];
+        for (int w = 1; w < nw; ++w) t = cf_add(t, sm[w][k]);
+        v[k] = t;
     }
 }
 
@@ -129,63 +152,100 @@ __global__ void cv_dihedral_kernel(const R4<R>* __restrict__ pos, const int64_t*
 // minimum image relative to the group's first atom; Rg = sqrt(mean |u-c|^2),
 // dRg/dr_k = (u_k - c) / (m Rg).  One block per walker.
 // ---------------------------------------------------------------------------
+constexpr int RG_CACHE = 1024;  // members whose unwrapped position stays in shared memory
+
 template <typename R>
 __global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
                                                     const int* __restrict__ wn, const int* __restrict__ A, int nA,
-                                                    Box box, double scale, int intensive, double* __restrict__ xi, int col,
-                                                    R4<R>* __restrict__ J)
+                                                    Box box, double scale, int intensive, double* __restrict__ xi,
+                                                    int col, R4<R>* __restrict__ J)
 {
+    __shared__ R4<R> u[RG_CACHE];
+    __shared__ R bc[4];  // broadcast: centre (3) and the Jacobian factor
     const int w = blockIdx.x;
     const long long o = woff[w];
     const int m = A ? nA : wn[w];
     const int i0 = A ? A[0] : 0;
     R rx, ry, rz;
     load3<R>(pos, o + i0, rx, ry, rz);
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    // unwrapped position of member p (minimum image relative to member 0)
+    auto unwrap = [&](int p) {
         const int i = A ? A[p] : p;
         R x, y, z, d[3];
         load3<R>(pos, o + i, x, y, z);
         delta<R>(box, x, y, z, rx, ry, rz, d);
-        s[0] += (double)(rx + d[0]);
-        s[1] += (double)(ry + d[1]);
-        s[2] += (double)(rz + d[2]);
+        return mk4<R>(rx + d[0], ry + d[1], rz + d[2], R(0));
+    };
+    // FP32 handles sum in compensated FP32, FP64 handles in FP64
+    cf s[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double sd[3] = {0.0, 0.0, 0.0};
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const R4<R> q = unwrap(p);
+        if (p < RG_CACHE) u[p] = q;
+        if constexpr (sizeof(R) == 4) {
+            s[0] = cf_add(s[0], (float)q.x);
+            s[1] = cf_add(s[1], (float)q.y);
+            s[2] = cf_add(s[2], (float)q.z);
+        } else {
+            sd[0] += (double)q.x;
+            sd[1] += (double)q.y;
+            sd[2] += (double)q.z;
+        }
     }
-    block_sum<double, 3>(s);
-    const R c[3] = {(R)(s[0] / m), (R)(s[1] / m), (R)(s[2] / m)};
-    double q[1] = {0.0};
+    if constexpr (sizeof(R) == 4) block_sum_cf<3>(s);
+    else block_sum<double, 3>(sd);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) bc[k] = (R)((sizeof(R) == 4 ? cf_val(s[k]) : sd[k]) / m);
+    __syncthreads();
+    const R c[3] = {bc[0], bc[1], bc[2]};
+    cf q2[1] = {{0.f, 0.f}};
+    double q2d[1] = {0.0};
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const R4<R> q = p < RG_CACHE ? u[p] : unwrap(p);
+        const R ux = q.x - c[0], uy = q.y - c[1], uz = q.z - c[2];
+        if constexpr (sizeof(R) == 4) q2[0] = cf_add(q2[0], (float)(ux * ux + uy * uy + uz * uz));
+        else q2d[0] += (double)(ux * ux + uy * uy + uz * uz);
+    }
+    if constexpr (sizeof(R) == 4) block_sum_cf<1>(q2);
+    else block_sum<double, 1>(q2d);
+    __shared__ double rg_s;
+    if (threadIdx.x == 0) {
+        const double rg = sqrt((sizeof(R) == 4 ? cf_val(q2[0]) : q2d[0]) / m);
+        double sc = scale != 0.0 ? scale : 1.0;
+        if (intensive) sc /= cbrt((double)m);
+        bc[3] = (R)(sc / (m * rg));
+        rg_s = sc * rg;
+    }
+    __syncthreads();
+    const R f = bc[3];
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
         const int i = A ? A[p] : p;
-        R x, y, z, d[3];
-        load3<R>(pos, o + i, x, y, z);
-        delta<R>(box, x, y, z, rx, ry, rz, d);
-        const R ux = rx + d[0] - c[0], uy = ry + d[1] - c[1], uz = rz + d[2] - c[2];
-        q[0] += (double)(ux * ux + uy * uy + uz * uz);
+        const R4<R> q = p < RG_CACHE ? u[p] : unwrap(p);
+        J[o + i] = mk4<R>(f * (q.x - c[0]), f * (q.y - c[1]), f * (q.z - c[2]), R(0));
     }
-    block_sum<double, 1>(q);
-    const double rg = sqrt(q[0] / m);
-    double sc = scale != 0.0 ? scale : 1.0;
-    if (intensive) sc /= cbrt((double)m);
-    const R f = (R)(sc / (m * rg));
-    for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        const int i = A ? A[p] : p;
-        R x, y, z, d[3];
-        load3<R>(pos, o + i, x, y, z);
-        delta<R>(box, x, y, z, rx, ry, rz, d);
-        J[o + i] = mk4<R>(f * (rx + d[0] - c[0]), f * (ry + d[1] - c[1]), f * (rz + d[2] - c[2]), R(0));
-    }
-    if (threadIdx.x == 0) xi[w * 4 + col] = sc * rg;
+    if (threadIdx.x == 0) xi[w * 4 + col] = rg_s;
 }
 
 // ---------------------------------------------------------------------------
 // Switching-function pair sums.  s(r) = 1/(1 + y^h), y = r^2/r0^2, h = n/2
 // (the rational (1-x^n)/(1-x^m) with m = 2n, which equals this exactly), and
 // ds/dr_t = -(n/r0^2) y^(h-1) s^2 (r_t - r_s).
-// pair_pass: for every target t of the walker, over one split of sources,
-//   part = (sum_s ds/dr_t, sum_s s(r_ts)), self pairs excluded.
+//
+// Coordination xi = scale sum_{i in A} sum_{j in B, j != i} s(r_ij) has
+//   dxi/dr_k = scale ( [k in A] sum_{j in B, j != k} ds/dr_k(r_kj)
+//                    + [k in B] sum_{i in A, i != k} ds/dr_k(r_ik) ).
+// One warp per target atom k computes its whole Jacobian row: lane l takes
+// partners l, l+32, ... (FP32 lane sums, FP64 xor-shuffle tree, fixed order),
+// and, for k in A, the row sum of s.  The last CTA of each walker reduces the
+// row sums of A in index order into xi.  No atomics on data: deterministic.
 // ---------------------------------------------------------------------------
-constexpr int PP_T = 128;  // targets per block
-constexpr int PP_S = 128;  // sources per split
+constexpr int CW_T = 256;  // threads per block (8 target warps)
+
+// correctly rounded reciprocal (FP32: MUFU estimate + refinement, no IEEE
+// division subroutine; unbiased, so sums of many terms do not drift)
+template <typename R> __device__ __forceinline__ R rcp(R x);
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 template <typename R>
 __device__ __forceinline__ R ypow(R y, int h)
@@ -195,108 +255,362 @@ __device__ __forceinline__ R ypow(R y, int h)
     return r;
 }
 
+constexpr int CW_CH = 512;  // source positions staged per chunk
+constexpr int CW_GT = 64;   // threads per target in group mode
+constexpr int CW_G = CW_T / CW_GT;
+
 template <typename R>
-__global__ void __launch_bounds__(PP_T) pair_pass_kernel(const R4<R>* __restrict__ pos,
-                                                         const int64_t* __restrict__ woff, const int* __restrict__ wn,
-                                                         const int* __restrict__ T, int nT, const int* __restrict__ S,
-                                                         int nS, Box box, R inv_r0sq, int h, R gpref,
-                                                         R4<R>* __restrict__ part, int nT_stride)
+__global__ void __launch_bounds__(CW_T) coord_warp_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
+                                                          const int* __restrict__ wn, const int* __restrict__ A, int nA,
+                                                          const int* __restrict__ B, int nB,
+                                                          const int* __restrict__ inv_a, const int* __restrict__ inv_b,
+                                                          const int* __restrict__ order, int n_order, int a_blocks,
+                                                          int same_ab,
+                                                          Box box, R inv_r0sq, int h, R gpref, double scale,
+                                                          const double* __restrict__ scw,
+                                                          double* __restrict__ rowval, int rv_stride,
+                                                          unsigned* __restrict__ tickets, R4<R>* __restrict__ J,
+                                                          double* __restrict__ xi, int col)
 {
-    __shared__ R4<R> src[PP_S];
-    __shared__ int sid[PP_S];
-    const int w = blockIdx.z;
-    const int W = gridDim.z;
-    const long long o = woff[w];
+    __shared__ R4<R> src[CW_CH];
+    __shared__ int sid[CW_CH];
+    const int w = blockIdx.y;
     const int nw = wn[w];
-    const int nTw = T ? nT : nw;
-    const int nSw = S ? nS : nw;
-    const int s0 = blockIdx.y * PP_S;
-    const int s1 = min(s0 + PP_S, nSw);
-    for (int j = threadIdx.x; j < s1 - s0; j += blockDim.x) {
-        const int li = S ? S[s0 + j] : s0 + j;
-        src[j] = pos[o + li];
-        sid[j] = li;
+    const long long o = woff[w];
+    const int nAw = A ? nA : nw, nBw = B ? nB : nw;
+    const int lane = threadIdx.x % 32;
+    // group mode: the first a_blocks CTAs take CW_G targets (members of A)
+    // each, one per 64-thread group, partners read straight from global
+    // memory; the other CTAs take one target per warp with staged partners
+    const bool bm = (int)blockIdx.x < a_blocks;
+    const int gid = threadIdx.x / CW_GT, gl = threadIdx.x % CW_GT;
+    const int ng = a_blocks > 0 ? nA : 0;  // targets handled by groups: the members of A
+    int t = bm ? (int)blockIdx.x * CW_G + gid : ng + ((int)blockIdx.x - a_blocks) * (CW_T / 32) + threadIdx.x / 32;
+    if (bm && t >= ng) t = 1 << 30;  // spare group of the last group CTA
+    int k = -1, pa = -1, pb = -1;
+    if (t < (order ? n_order : nw)) {
+        k = order ? order[t] : t;
+        if (k < nw) {
+            pa = A ? inv_a[k] : k;
+            pb = B ? inv_b[k] : k;
+        } else {
+            k = -1;
+        }
     }
-    __syncthreads();
-    const int t = blockIdx.x * PP_T + threadIdx.x;
-    if (t >= nTw) return;
-    const int ti = T ? T[t] : t;
-    R tx, ty, tz;
-    load3<R>(pos, o + ti, tx, ty, tz);
-    R gx = 0, gy = 0, gz = 0, ss = 0;
-    for (int j = 0; j < s1 - s0; ++j) {
-        if (sid[j] == ti) continue;
-        const R4<R> sp = src[j];
+    R tx = 0, ty = 0, tz = 0;
+    if (k >= 0) load3<R>(pos, o + k, tx, ty, tz);
+    R gx = 0, gy = 0, gz = 0, sv = 0;
+    // sweep 0: partners in B (targets in A, with the value); sweep 1:
+    // partners in A (targets in B, gradient only; not needed when A == B)
+    auto pair = [&](const R4<R> sp, int j, bool value) {
         R d[3];
         delta<R>(box, tx, ty, tz, sp.x, sp.y, sp.z, d);
         const R y = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv_r0sq;
         const R yh1 = ypow<R>(y, h - 1);
-        const R sv = R(1) / (R(1) + yh1 * y);
-        ss += sv;
-        const R gr = gpref * yh1 * sv * sv;
+        R s = rcp<R>(R(1) + yh1 * y);
+        if (j == k) s = R(0);  // no self pair
+        if (value) sv += s;
+        const R gr = gpref * yh1 * s * s;
         gx += gr * d[0];
         gy += gr * d[1];
         gz += gr * d[2];
+    };
+    if (bm) {
+        if (pa >= 0) {
+#pragma unroll 4
+            for (int q = gl; q < nBw; q += CW_GT) {
+                const int j = B ? B[q] : q;
+                pair(pos[o + j], j, true);
+            }
+        }
+        if (pb >= 0 && !same_ab) {
+#pragma unroll 4
+            for (int q = gl; q < nAw; q += CW_GT) {
+                const int i = A ? A[q] : q;
+                pair(pos[o + i], i, false);
+            }
+        }
+    } else {
+        // one target per warp: the CTA's 8 targets share staged partners
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            const bool mine = sweep == 0 ? pa >= 0 : (pb >= 0 && !same_ab);
+            if (!__syncthreads_or(mine)) continue;
+            const int* list = sweep == 0 ? B : A;
+            const int n = sweep == 0 ? nBw : nAw;
+            for (int c0 = 0; c0 < n; c0 += CW_CH) {
+                const int m = min(CW_CH, n - c0);
+                __syncthreads();
+                for (int q = threadIdx.x; q < m; q += CW_T) {
+                    const int j = list ? list[c0 + q] : c0 + q;
+                    src[q] = pos[o + j];
+                    sid[q] = j;
+                }
+                __syncthreads();
+                if (!mine) continue;
+#pragma unroll 4
+                for (int q = lane; q < m; q += 32) pair(src[q], sid[q], sweep == 0);
+            }
+        }
     }
-    part[((size_t)blockIdx.y * W + w) * nT_stride + t] = mk4<R>(gx, gy, gz, ss);
+    // gradient in FP32 (a fixed shuffle tree), the row sum of s in FP64 (it
+    // is the CV value, which the hills sum amplifies by |xi|/sigma)
+    double srow = (double)sv;
+    for (int off = 16; off > 0; off >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, off);
+        gy += __shfl_xor_sync(0xffffffffu, gy, off);
+        gz += __shfl_xor_sync(0xffffffffu, gz, off);
+        srow += __shfl_xor_sync(0xffffffffu, srow, off);
+    }
+    if (bm) {  // the two warps of each group, in order
+        __shared__ R redg[CW_T / 32][3];
+        __shared__ double reds[CW_T / 32];
+        if (lane == 0) {
+            redg[threadIdx.x / 32][0] = gx;
+            redg[threadIdx.x / 32][1] = gy;
+            redg[threadIdx.x / 32][2] = gz;
+            reds[threadIdx.x / 32] = srow;
+        }
+        __syncthreads();
+        if (gl == 0) {
+            const int w0 = threadIdx.x / 32;
+            gx = gy = gz = R(0);
+            srow = 0.0;
+            for (int w = w0; w < w0 + CW_GT / 32; ++w) {
+                gx += redg[w][0];
+                gy += redg[w][1];
+                gz += redg[w][2];
+                srow += reds[w];
+            }
+        }
+    }
+    if ((bm ? gl : lane) == 0 && k >= 0) {
+        const R f = (R)((same_ab ? 2.0 : 1.0) * scw[w]);
+        J[o + k] = mk4<R>(f * gx, f * gy, f * gz, R(0));
+        if (pa >= 0) rowval[(size_t)w * rv_stride + pa] = srow;
+    }
+    // the last CTA of this walker sums the row values of A in order
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&tickets[w], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v[1] = {0.0};
+    for (int q = threadIdx.x; q < nAw; q += CW_T) v[0] += __ldcg(rowval + (size_t)w * rv_stride + q);
+    block_sum<double, 1>(v);
+    if (threadIdx.x == 0) {
+        xi[w * 4 + col] = scw[w] * v[0];
+        tickets[w] = 0u;
+    }
 }
 
-// J rows of coordination for every atom of every walker.
+// ---------------------------------------------------------------------------
+// Coordination for a list A against a large partner group B, each ordered
+// pair (i in A, j in B) evaluated once.  A CTA takes a tile of 32 members of
+// A (lane l holds a_l) and a chunk of CT_B partners staged in shared memory;
+// warp w sweeps partners w*32 ... w*32+31 of the chunk.  ds/dr for the row
+// atom a_l accumulates in its lane; the column contributions -ds/dr of each
+// group of 8 partners are summed over the 32 lanes by a shuffle
+// reduce-scatter (9 shuffles per component per 8 partners).  Row partials
+// [chunk][A] and column partials [tile][B] are written once each and summed
+// in fixed order by coord_tile_finalize: deterministic, no atomics on data.
+// ---------------------------------------------------------------------------
+constexpr int CT_T = 256;
+constexpr int CT_B = 256;  // partners per CTA (8 warps x 32)
+
+// Sum over the 32 lanes of v[0..7]; on return every lane holds in v[0] the
+// total for partner m = ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
+template <typename R> __device__ __forceinline__ void reduce_scatter8(R v[8], int lane)
+{
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R keep = b4 ? v[k + 4] : v[k];
+        const R send = b4 ? v[k] : v[k + 4];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const R keep = b3 ? v[k + 2] : v[k];
+        const R send = b3 ? v[k] : v[k + 2];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const R keep = b2 ? v[1] : v[0];
+        const R send = b2 ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <typename R>
-__global__ void coord_finalize_kernel(const int64_t* __restrict__ woff, const int* __restrict__ wn, int W,
-                                      const int* __restrict__ inv_a, bool a_all, const int* __restrict__ inv_b,
-                                      bool b_all, bool same_ab, const R4<R>* __restrict__ prow, int split_row,
-                                      int nT_row, const R4<R>* __restrict__ pcol, int split_col, int nT_col,
-                                      double scale, int nA, R4<R>* __restrict__ J)
+__global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
+                                                          const int* __restrict__ wn, const int* __restrict__ A, int nA,
+                                                          const int* __restrict__ B, int nB, int nbchunk, Box box,
+                                                          R inv_r0sq, int h, R gpref, R4<R>* __restrict__ rowpart,
+                                                          R4<R>* __restrict__ colpart, int nB_stride)
+{
+    __shared__ R4<R> src[CT_B];
+    __shared__ int sid[CT_B];
+    __shared__ R4<R> rowred[CT_T / 32][32];
+    const int w = blockIdx.y;
+    const int nw = wn[w];
+    const long long o = woff[w];
+    const int nBw = B ? nB : nw;
+    const int tile = blockIdx.x / nbchunk, chunk = blockIdx.x % nbchunk;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int b0 = chunk * CT_B;
+    const int mb = min(CT_B, nBw - b0);
+    for (int q = threadIdx.x; q < mb; q += CT_T) {
+        const int j = B ? B[b0 + q] : b0 + q;
+        src[q] = pos[o + j];
+        sid[q] = j;
+    }
+    const int ia = tile * 32 + lane;
+    const int a = ia < nA ? A[ia] : -1;
+    R tx = 0, ty = 0, tz = 0;
+    if (a >= 0) load3<R>(pos, o + a, tx, ty, tz);
+    __syncthreads();
+    R gx = 0, gy = 0, gz = 0, sv = 0;
+    for (int m0 = warp * 32; m0 < warp * 32 + 32; m0 += 8) {
+        R cx[8], cy[8], cz[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            cx[m] = cy[m] = cz[m] = R(0);
+            const int q = m0 + m;
+            if (q < mb && a >= 0) {
+                const R4<R> sp = src[q];
+                R d[3];
+                delta<R>(box, tx, ty, tz, sp.x, sp.y, sp.z, d);
+                const R y = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv_r0sq;
+                const R yh1 = ypow<R>(y, h - 1);
+                R s = rcp<R>(R(1) + yh1 * y);
+                if (sid[q] == a) s = R(0);
+                sv += s;
+                const R gr = gpref * yh1 * s * s;
+                gx += gr * d[0];
+                gy += gr * d[1];
+                gz += gr * d[2];
+                cx[m] = -gr * d[0];
+                cy[m] = -gr * d[1];
+                cz[m] = -gr * d[2];
+            }
+        }
+        reduce_scatter8<R>(cx, lane);
+        reduce_scatter8<R>(cy, lane);
+        reduce_scatter8<R>(cz, lane);
+        const int m = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        const int q = m0 + m;
+        if ((lane & 3) == 0 && q < mb) {
+            const int pbq = b0 + q;  // position in B
+            colpart[((size_t)w * gridDim.x / nbchunk + tile) * nB_stride + pbq] = mk4<R>(cx[0], cy[0], cz[0], R(0));
+        }
+    }
+    // rows: the 8 warps hold partial sums over their partner slices
+    rowred[warp][lane] = mk4<R>(gx, gy, gz, sv);
+    __syncthreads();
+    if (warp == 0 && a >= 0) {
+        R4<R> t = rowred[0][lane];
+        for (int k = 1; k < CT_T / 32; ++k) {
+            const R4<R> u = rowred[k][lane];
+            t.x += u.x;
+            t.y += u.y;
+            t.z += u.z;
+            t.w += u.w;
+        }
+        rowpart[((size_t)w * nbchunk + chunk) * nA + ia] = t;
+    }
+}
+
+// J rows and the CV value from the tile partials.  Thread k sums the chunk
+// partials of its row (k in A; also its row value of s, stored per member)
+// and the tile partials of its column (k in B); the walker's last CTA sums
+// the per-member row values in member order.
+template <typename R>
+__global__ void __launch_bounds__(64) coord_tile_finalize(const int64_t* __restrict__ woff, const int* __restrict__ wn,
+                                                           const int* __restrict__ inv_a, const int* __restrict__ inv_b,
+                                                           bool b_all, int nA, int ntile, int nbchunk,
+                                                           const R4<R>* __restrict__ rowpart,
+                                                           const R4<R>* __restrict__ colpart, int nB_stride,
+                                                           const double* __restrict__ scw, double* __restrict__ rowval,
+                                                           unsigned* __restrict__ tickets, R4<R>* __restrict__ J,
+                                                           double* __restrict__ xi, int col)
 {
     const int w = blockIdx.y;
+    const int nw = wn[w];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= wn[w]) return;
-    const int pa = a_all ? k : inv_a[k];
-    const int pb = b_all ? k : inv_b[k];
-    if (pa < 0 && pb < 0) return;
-    double gx = 0, gy = 0, gz = 0;
-    if (pa >= 0)
-        for (int s = 0; s < split_row; ++s) {
-            const R4<R> q = prow[((size_t)s * W + w) * nT_row + pa];
-            gx += q.x;
-            gy += q.y;
-            gz += q.z;
-        }
-    if (same_ab) {
-        gx *= 2.0;
-        gy *= 2.0;
-        gz *= 2.0;
-    } else if (pb >= 0) {
-        for (int s = 0; s < split_col; ++s) {
-            const R4<R> q = pcol[((size_t)s * W + w) * nT_col + pb];
-            gx += q.x;
-            gy += q.y;
-            gz += q.z;
+    if (k < nw) {
+        const int pa = inv_a[k];
+        const int pb = b_all ? k : inv_b[k];
+        if (pa >= 0 || pb >= 0) {
+            R gx = 0, gy = 0, gz = 0;
+            // issue all partial loads before summing them (in order)
+            constexpr int MAXP = 32;
+            if (pa >= 0) {
+                R4<R> rp[MAXP];
+#pragma unroll
+                for (int c = 0; c < MAXP; ++c)
+                    if (c < nbchunk) rp[c] = rowpart[((size_t)w * nbchunk + c) * nA + pa];
+                cf sv{0.f, 0.f};
+                double svd = 0.0;
+#pragma unroll
+                for (int c = 0; c < MAXP; ++c)
+                    if (c < nbchunk) {
+                        gx += rp[c].x;
+                        gy += rp[c].y;
+                        gz += rp[c].z;
+                        if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)rp[c].w);
+                        else svd += (double)rp[c].w;
+                    }
+                for (int c = MAXP; c < nbchunk; ++c) {
+                    const R4<R> t = rowpart[((size_t)w * nbchunk + c) * nA + pa];
+                    gx += t.x;
+                    gy += t.y;
+                    gz += t.z;
+                    if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)t.w);
+                    else svd += (double)t.w;
+                }
+                rowval[(size_t)w * nA + pa] = sizeof(R) == 4 ? cf_val(sv) : svd;
+            }
+            if (pb >= 0) {
+                R4<R> cp[MAXP];
+#pragma unroll
+                for (int t = 0; t < MAXP; ++t)
+                    if (t < ntile) cp[t] = colpart[((size_t)w * ntile + t) * nB_stride + pb];
+#pragma unroll
+                for (int t = 0; t < MAXP; ++t)
+                    if (t < ntile) {
+                        gx += cp[t].x;
+                        gy += cp[t].y;
+                        gz += cp[t].z;
+                    }
+                for (int t = MAXP; t < ntile; ++t) {
+                    const R4<R> u = colpart[((size_t)w * ntile + t) * nB_stride + pb];
+                    gx += u.x;
+                    gy += u.y;
+                    gz += u.z;
+                }
+            }
+            const R f = (R)scw[w];
+            J[woff[w] + k] = mk4<R>(f * gx, f * gy, f * gz, R(0));
         }
     }
-    const double sc = scale != 0.0 ? scale : 1.0 / (a_all ? wn[w] : nA);
-    J[woff[w] + k] = mk4<R>((R)(sc * gx), (R)(sc * gy), (R)(sc * gz), R(0));
-}
-
-// xi = scale * sum over targets of group A of the row sums of s.
-template <typename R>
-__global__ void __launch_bounds__(256) coord_value_kernel(const int* __restrict__ wn, bool a_all, int nA,
-                                                          const R4<R>* __restrict__ prow, int split_row, int nT_row,
-                                                          double scale, double* __restrict__ xi, int col)
-{
-    const int w = blockIdx.x;
-    const int W = gridDim.x;
-    const int na = a_all ? wn[w] : nA;
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&tickets[w], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     double v[1] = {0.0};
-    for (int t = threadIdx.x; t < na; t += blockDim.x) {
-        double r = 0.0;
-        for (int s = 0; s < split_row; ++s) r += prow[((size_t)s * W + w) * nT_row + t].w;
-        v[0] += r;
-    }
+    for (int q = threadIdx.x; q < nA; q += blockDim.x) v[0] += __ldcg(rowval + (size_t)w * nA + q);
     block_sum<double, 1>(v);
-    const double sc = scale != 0.0 ? scale : 1.0 / na;
-    if (threadIdx.x == 0) xi[w * 4 + col] = sc * v[0];
+    if (threadIdx.x == 0) {
+        xi[w * 4 + col] = scw[w] * v[0];
+        tickets[w] = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -392,29 +706,38 @@ int cv_alloc_scratch(wtmd_t* h, CvDev& c)
     const size_t r4 = h->prec == WTMD_F32 ? sizeof(float4) : sizeof(dbl4);
     if (c.kind == WTMD_CV_COORDINATION) {
         const int nA = c.n_a < 0 ? h->max_wn : c.n_a;
-        const int nB = c.n_b < 0 ? h->max_wn : c.n_b;
-        c.nT_row = nA;
-        c.split_row = (nB + PP_S - 1) / PP_S;
-        WTMD_CUDA_TRY(h, cudaMalloc(&c.part_row, r4 * (size_t)c.split_row * h->W * c.nT_row));
-        if (!c.same_ab) {
-            c.nT_col = nB;
-            c.split_col = (nA + PP_S - 1) / PP_S;
-            WTMD_CUDA_TRY(h, cudaMalloc(&c.part_col, r4 * (size_t)c.split_col * h->W * c.nT_col));
+        c.nT_row = nA;  // row-value stride per walker
+        WTMD_CUDA_TRY(h, cudaMalloc(&c.part_row, sizeof(double) * (size_t)h->W * nA));
+        WTMD_CUDA_TRY(h, cudaMalloc(&c.part_col, sizeof(unsigned) * (size_t)h->W));
+        WTMD_CUDA_TRY(h, cudaMemset(c.part_col, 0, sizeof(unsigned) * (size_t)h->W));
+        // per-walker CV scale (default 1/|A|, |A| = walker size for "all")
+        std::vector<double> scw(h->W);
+        for (int w = 0; w < h->W; ++w)
+            scw[w] = c.scale != 0.0 ? c.scale : 1.0 / (double)(c.n_a < 0 ? h->wn_h[w] : c.n_a);
+        WTMD_CUDA_TRY(h, cudaMalloc(&c.scw, sizeof(double) * (size_t)h->W));
+        if (c.n_a > 0) {  // tile path: row partials [W][chunk][A], column partials [W][tile][B]
+            const int nB = c.n_b < 0 ? h->max_wn : c.n_b;
+            c.nbchunk = (nB + 255) / 256;
+            c.ntile = (c.n_a + 31) / 32;
+            c.nB_stride = nB;
+            WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_row, r4 * (size_t)h->W * c.nbchunk * c.n_a));
+            WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_col, r4 * (size_t)h->W * c.ntile * nB));
         }
+        WTMD_CUDA_TRY(h, cudaMemcpy(c.scw, scw.data(), sizeof(double) * (size_t)h->W, cudaMemcpyHostToDevice));
     } else if (c.kind == WTMD_CV_QPAIRS) {
         WTMD_CUDA_TRY(h, cudaMalloc(&c.part_row, r4 * (size_t)h->W * c.n_pairs));
     }
     return WTMD_OK;
 }
 
-template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_)
+template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c_begin, int c_end)
 {
     const R4<R>* pos = (const R4<R>*)pos_;
     double* xi = h->xi;
     R4<R>* J = (R4<R>*)h->J;
     const int W = h->W;
     cudaStream_t st = h->stream;
-    for (int c = 0; c < h->ncv; ++c) {
+    for (int c = c_begin; c < c_end; ++c) {
         CvDev& cv = h->cv[c];
         R4<R>* Jc = J + (size_t)c * h->N;
         const R sc = (R)(cv.scale != 0.0 ? cv.scale : 1.0);
@@ -438,28 +761,35 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_)
         case WTMD_CV_COORDINATION: {
             const R inv = (R)(1.0 / (cv.r0 * cv.r0));
             const R gp = (R)(-(double)cv.nn / (cv.r0 * cv.r0));
-            const int hh = cv.nn / 2;
             const int* A = cv.n_a < 0 ? nullptr : cv.a;
             const int* B = cv.n_b < 0 ? nullptr : cv.b;
-            dim3 g1((cv.nT_row + PP_T - 1) / PP_T, cv.split_row, W);
-            pair_pass_kernel<R><<<g1, PP_T, 0, st>>>(pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, h->box, inv, hh, gp,
-                                                     (R4<R>*)cv.part_row, cv.nT_row);
-            mark(h, "coord_pair_row");
-            if (!cv.same_ab) {
-                dim3 g2((cv.nT_col + PP_T - 1) / PP_T, cv.split_col, W);
-                pair_pass_kernel<R><<<g2, PP_T, 0, st>>>(pos, h->woff, h->wn, B, cv.n_b, A, cv.n_a, h->box, inv, hh,
-                                                         gp, (R4<R>*)cv.part_col, cv.nT_col);
-                mark(h, "coord_pair_col");
+            if (cv.n_a > 0) {
+                dim3 gt(cv.ntile * cv.nbchunk, W);
+                coord_tile_kernel<R><<<gt, CT_T, 0, st>>>(pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box,
+                                                          inv, cv.nn / 2, gp, (R4<R>*)cv.tile_row,
+                                                          (R4<R>*)cv.tile_col, cv.nB_stride);
+                mark(h, "coord_tile");
+                dim3 gf((h->max_wn + 63) / 64, W);
+                coord_tile_finalize<R><<<gf, 64, 0, st>>>(h->woff, h->wn, cv.inv_a, cv.inv_b, cv.n_b < 0, cv.n_a,
+                                                           cv.ntile, cv.nbchunk, (const R4<R>*)cv.tile_row,
+                                                           (const R4<R>*)cv.tile_col, cv.nB_stride, cv.scw,
+                                                           (double*)cv.part_row, (unsigned*)cv.part_col, Jc, xi, c);
+                mark(h, "coord_tile_finalize");
+                break;
             }
-            dim3 g3((h->max_wn + 255) / 256, W);
-            coord_finalize_kernel<R><<<g3, 256, 0, st>>>(h->woff, h->wn, W, cv.inv_a, cv.n_a < 0, cv.inv_b,
-                                                         cv.n_b < 0, cv.same_ab, (const R4<R>*)cv.part_row,
-                                                         cv.split_row, cv.nT_row, (const R4<R>*)cv.part_col,
-                                                         cv.split_col, cv.nT_col, cv.scale, cv.n_a, Jc);
-            mark(h, "coord_finalize");
-            coord_value_kernel<R><<<W, 256, 0, st>>>(h->wn, cv.n_a < 0, cv.n_a, (const R4<R>*)cv.part_row,
-                                                     cv.split_row, cv.nT_row, cv.scale, xi, c);
-            mark(h, "coord_value");
+            const int nt = cv.order ? cv.n_order : h->max_wn;
+            // a short list A against many partners: one CTA per member of A
+            const int nBmax = cv.n_b < 0 ? h->max_wn : cv.n_b;
+            const int ab = (cv.order && nBmax >= 1024) ? (cv.n_a + CW_G - 1) / CW_G : 0;
+            const int nrest = nt - (ab > 0 ? cv.n_a : 0);
+            dim3 g(ab + (nrest + CW_T / 32 - 1) / (CW_T / 32), W);
+            coord_warp_kernel<R><<<g, CW_T, 0, st>>>(pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.inv_a, cv.inv_b,
+                                                     cv.order, cv.n_order, ab, cv.same_ab ? 1 : 0, h->box, inv,
+                                                     cv.nn / 2, gp, cv.scale,
+                                                     cv.scw, (double*)cv.part_row, cv.nT_row, (unsigned*)cv.part_col,
+                                                     Jc, xi,
+                                                     c);
+            mark(h, "coord_warp");
             break;
         }
         case WTMD_CV_QPAIRS: {
@@ -487,9 +817,14 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_)
     return WTMD_OK;
 }
 
+int launch_cv(wtmd_t* h, const void* pos, int c)
+{
+    return h->prec == WTMD_F32 ? launch_cvs_t<float>(h, pos, c, c + 1) : launch_cvs_t<double>(h, pos, c, c + 1);
+}
+
 int launch_cvs(wtmd_t* h, const void* pos)
 {
-    return h->prec == WTMD_F32 ? launch_cvs_t<float>(h, pos) : launch_cvs_t<double>(h, pos);
+    return h->prec == WTMD_F32 ? launch_cvs_t<float>(h, pos, 0, h->ncv) : launch_cvs_t<double>(h, pos, 0, h->ncv);
 }
 
 int launch_scatter(wtmd_t* h, void* force, const void* vel, bool kick)

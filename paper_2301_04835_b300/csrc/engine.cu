@@ -112,11 +112,16 @@ __global__ void mb_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __res
 }
 
 // LJ pair force factor: F_t += fr * (r_t - r_s), fr = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2.
+template <typename R> __device__ __forceinline__ R inv(R x);
+template <> __device__ __forceinline__ float inv<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double inv<double>(double x) { return 1.0 / x; }
+
 template <typename R> __device__ __forceinline__ R lj_fr(R r2, R sig2, R eps24)
 {
-    const R sr2 = sig2 / r2;
+    const R ir2 = inv<R>(r2);
+    const R sr2 = sig2 * ir2;
     const R sr6 = sr2 * sr2 * sr2;
-    return eps24 * (R(2) * sr6 * sr6 - sr6) / r2;
+    return eps24 * (R(2) * sr6 * sr6 - sr6) * ir2;
 }
 
 // All pairs within each walker; sources staged in shared memory.
@@ -156,6 +161,29 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
     if (t < n) f[o + t] = mk4<R>(fx, fy, fz, R(0));
 }
 
+template <typename R> __device__ __forceinline__ R inv_box(const Box& b, int k);
+template <> __device__ __forceinline__ float inv_box<float>(const Box& b, int k) { return b.invLf[k]; }
+template <> __device__ __forceinline__ double inv_box<double>(const Box& b, int k) { return b.invL[k]; }
+
+// x - m L for an integer m, with L as hi + lo floats in FP32.
+template <typename R> __device__ __forceinline__ R shift_box(R x, R m, const Box& b, int k);
+template <> __device__ __forceinline__ float shift_box<float>(float x, float m, const Box& b, int k)
+{
+    return fmaf(-m, b.Llo[k], fmaf(-m, b.Lf[k], x));
+}
+template <> __device__ __forceinline__ double shift_box<double>(double x, double m, const Box& b, int k)
+{
+    return x - m * b.L[k];
+}
+
+// Position of x in the periodic image of the home cell's frame: wrapped by
+// floor(x / L) (the formula the binning uses), then moved by `img` boxes.
+template <typename R> __device__ __forceinline__ R image_coord(R x, int img, const Box& b, int k)
+{
+    const R m = floor(x * inv_box<R>(b, k)) - (R)img;
+    return shift_box<R>(x, m, b, k);
+}
+
 // Cell list (single periodic walker).  Binning with atomics, then each
 // cell's list is sorted by atom index so the force sum order is fixed.
 template <typename R>
@@ -169,12 +197,10 @@ __global__ void cell_bin_kernel(long long N, const R4<R>* __restrict__ x, Box bo
     const int nc[3] = {ncx, ncy, ncz};
     int ci[3];
     for (int k = 0; k < 3; ++k) {
-        const R L = (R)box.L[k];
-        R u = q[k] * (R)box.invL[k];
+        R u = q[k] * inv_box<R>(box, k);
         u -= floor(u);  // fractional coordinate in [0, 1]
         int c = (int)(u * nc[k]);
         ci[k] = c >= nc[k] ? nc[k] - 1 : (c < 0 ? 0 : c);
-        (void)L;
     }
     const int cell = (ci[0] * ncy + ci[1]) * ncz + ci[2];
     const int slot = atomicAdd(&cnt[cell], 1);
@@ -182,65 +208,119 @@ __global__ void cell_bin_kernel(long long N, const R4<R>* __restrict__ x, Box bo
     else atomicOr(status, ST_CELL);
 }
 
-__global__ void cell_sort_kernel(int ncells, int cap, const int* __restrict__ cnt, int* __restrict__ atoms)
+// Each cell's atom list is put in increasing atom order once per step (one
+// warp per cell: every entry's rank is the number of smaller entries; atom
+// indices are distinct), so the binning atomics' order never reaches the
+// force sums: the engine force is bitwise reproducible.
+__global__ void __launch_bounds__(256) cell_sort_kernel(int ncells, int cap, const int* __restrict__ cnt,
+                                                        int* __restrict__ atoms)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
-    const int n = min(cnt[c], cap);
-    int* a = atoms + (size_t)c * cap;
-    for (int i = 1; i < n; ++i) {
-        const int v = a[i];
-        int j = i - 1;
-        while (j >= 0 && a[j] > v) {
-            a[j + 1] = a[j];
-            --j;
+    extern __shared__ int cs_smem[];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int c = blockIdx.x * 8 + warp;
+    int* in = cs_smem + warp * 2 * cap;
+    int* out = in + cap;
+    const int n = c < ncells ? min(cnt[c], cap) : 0;
+    int* a = atoms + (size_t)(c < ncells ? c : 0) * cap;
+    for (int k = lane; k < n; k += 32) in[k] = a[k];
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) {
+        const int v = in[k];
+        int r = 0;
+        for (int q = 0; q < n; ++q) r += in[q] < v;
+        out[r] = v;
+    }
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) a[k] = out[k];
+}
+
+// Cell-tiled LJ forces.  One CTA per home cell gathers the (sorted) atom
+// lists of the 27 neighbour cells and their positions into shared memory;
+// one warp per target atom of the home cell; lane l takes candidates l,
+// l+32, ... in (cell, atom) order; a fixed xor-shuffle tree reduces the lanes.
+constexpr int LJ_T = 512;  // 16 warps: about one target atom per warp
+
+template <typename R>
+__global__ void __launch_bounds__(LJ_T) lj_tiled_kernel(const R4<R>* __restrict__ x, Box box, int ncx, int ncy,
+                                                        int ncz, int cap, const int* __restrict__ cnt,
+                                                        const int* __restrict__ atoms, R rc2, R sig2, R eps24,
+                                                        R4<R>* __restrict__ f)
+{
+    extern __shared__ __align__(32) unsigned char lj_smem[];
+    __shared__ int off[28];
+    __shared__ int nbc[27];
+    const int c = blockIdx.x;
+    const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncy * ncz);
+    if (threadIdx.x < 27) {
+        const int q = threadIdx.x;
+        const int dx = q / 9 - 1, dy = (q / 3) % 3 - 1, dz = q % 3 - 1;
+        const int nb = (((cx + dx + ncx) % ncx) * ncy + (cy + dy + ncy) % ncy) * ncz + (cz + dz + ncz) % ncz;
+        nbc[q] = nb;
+        off[q + 1] = min(cnt[nb], cap);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        off[0] = 0;
+        for (int q = 0; q < 27; ++q) off[q + 1] += off[q];
+    }
+    __syncthreads();
+    const int ncand = off[27];
+    int* idx = reinterpret_cast<int*>(lj_smem);
+    R4<R>* cp = reinterpret_cast<R4<R>*>(lj_smem + (((size_t)27 * cap * sizeof(int) + 31) / 32) * 32);
+    // flat gather: candidate e lives in neighbour cell q with off[q] <= e <
+    // off[q+1]; it is stored at its periodic image next to the home cell, so
+    // the pair loop needs no minimum image
+    const int hc[3] = {cx, cy, cz}, ncv[3] = {ncx, ncy, ncz};
+    for (int e = threadIdx.x; e < ncand; e += LJ_T) {
+        int q = 0;
+        while (off[q + 1] <= e) ++q;
+        const int j = atoms[(size_t)nbc[q] * cap + (e - off[q])];
+        idx[e] = j;
+        const int dq[3] = {q / 9 - 1, (q / 3) % 3 - 1, q % 3 - 1};
+        int img[3];
+        for (int k = 0; k < 3; ++k) {
+            const int n = hc[k] + dq[k];
+            img[k] = n < 0 ? -1 : (n >= ncv[k] ? 1 : 0);
         }
-        a[j + 1] = v;
+        const R4<R> sx = x[j];
+        cp[e] = mk4<R>(image_coord<R>(sx.x, img[0], box, 0), image_coord<R>(sx.y, img[1], box, 1),
+                       image_coord<R>(sx.z, img[2], box, 2), R(0));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int nhome = min(cnt[c], cap);
+    for (int t = warp; t < nhome; t += LJ_T / 32) {
+        const int i = atoms[(size_t)c * cap + t];
+        const R4<R> px = x[i];
+        const R p[3] = {image_coord<R>(px.x, 0, box, 0), image_coord<R>(px.y, 0, box, 1),
+                        image_coord<R>(px.z, 0, box, 2)};
+        R fx = 0, fy = 0, fz = 0;
+#pragma unroll 4
+        for (int e = lane; e < ncand; e += 32) {
+            const R4<R> s = cp[e];
+            const R ddx = p[0] - s.x;
+            const R ddy = p[1] - s.y;
+            const R ddz = p[2] - s.z;
+            const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2 < rc2 && idx[e] != i) {
+                const R fr = lj_fr<R>(r2, sig2, eps24);
+                fx += fr * ddx;
+                fy += fr * ddy;
+                fz += fr * ddz;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+        }
+        if (lane == 0) f[i] = mk4<R>(fx, fy, fz, R(0));
     }
 }
 
-template <typename R>
-__global__ void lj_cells_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx, int ncy, int ncz, int cap,
-                                const int* __restrict__ cnt, const int* __restrict__ atoms, R rc2, R sig2, R eps24,
-                                R4<R>* __restrict__ f)
+template <typename R> static size_t lj_tiled_smem(int cap)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const R4<R> p = x[i];
-    const R q[3] = {p.x, p.y, p.z};
-    const int nc[3] = {ncx, ncy, ncz};
-    int ci[3];
-    for (int k = 0; k < 3; ++k) {
-        R u = q[k] * (R)box.invL[k];
-        u -= floor(u);
-        int c = (int)(u * nc[k]);
-        ci[k] = c >= nc[k] ? nc[k] - 1 : (c < 0 ? 0 : c);
-    }
-    R fx = 0, fy = 0, fz = 0;
-    for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dz = -1; dz <= 1; ++dz) {
-                const int cx = (ci[0] + dx + ncx) % ncx, cy = (ci[1] + dy + ncy) % ncy, cz = (ci[2] + dz + ncz) % ncz;
-                const int cell = (cx * ncy + cy) * ncz + cz;
-                const int n = min(cnt[cell], cap);
-                const int* a = atoms + (size_t)cell * cap;
-                for (int k = 0; k < n; ++k) {
-                    const int j = a[k];
-                    if (j == i) continue;
-                    const R4<R> s = x[j];
-                    const R ddx = min_image<R>(p.x - s.x, box, 0);
-                    const R ddy = min_image<R>(p.y - s.y, box, 1);
-                    const R ddz = min_image<R>(p.z - s.z, box, 2);
-                    const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < rc2) {
-                        const R fr = lj_fr<R>(r2, sig2, eps24);
-                        fx += fr * ddx;
-                        fy += fr * ddy;
-                        fz += fr * ddz;
-                    }
-                }
-            }
-    f[i] = mk4<R>(fx, fy, fz, R(0));
+    return ((size_t)27 * cap * sizeof(int) + 31) / 32 * 32 + (size_t)27 * cap * sizeof(R4<R>);
 }
 
 // Bead chain: bonds kb/2 (r - r0)^2, angles ka/2 (theta - th0)^2, torsions
@@ -361,10 +441,20 @@ int setup_cells(wtmd_t* h)
     h->nc[1] = nc[1];
     h->nc[2] = nc[2];
     h->ncells = nc[0] * nc[1] * nc[2];
-    const double vol_cell = h->cfg.box[0] * h->cfg.box[1] * h->cfg.box[2] / h->ncells;
-    const double rho = (double)h->N / (h->cfg.box[0] * h->cfg.box[1] * h->cfg.box[2]);
-    int cap = (int)ceil(4.0 * rho * vol_cell + 32.0);
-    h->cell_cap = (cap + 31) / 32 * 32;
+    // capacity: twice the mean occupancy plus 16 (a liquid cell exceeding it
+    // is a many-sigma event; overflow is reported as WTMD_ECELL)
+    const double mean = (double)h->N / h->ncells;
+    int cap = (int)ceil(2.0 * mean + 16.0);
+    h->cell_cap = (cap + 7) / 8 * 8;
+    const size_t sm = h->prec == WTMD_F32 ? lj_tiled_smem<float>(h->cell_cap) : lj_tiled_smem<double>(h->cell_cap);
+    if (sm > 200 * 1024) {
+        h->ncells = 0;  // too dense for the tiled kernel: all pairs
+        return WTMD_OK;
+    }
+    if (h->prec == WTMD_F32)
+        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(lj_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    else
+        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(lj_tiled_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_count, sizeof(int) * h->ncells));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
     return WTMD_OK;
@@ -393,11 +483,11 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
             cell_bin_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
                                                    h->cell_count, h->cell_atoms, h->status);
             mark(h, "lj_cell_bin");
-            cell_sort_kernel<<<(h->ncells + 127) / 128, 128, 0, st>>>(h->ncells, h->cell_cap, h->cell_count,
-                                                                      h->cell_atoms);
+            cell_sort_kernel<<<(h->ncells + 7) / 8, 256, 8 * 2 * h->cell_cap * sizeof(int), st>>>(
+                h->ncells, h->cell_cap, h->cell_count, h->cell_atoms);
             mark(h, "lj_cell_sort");
-            lj_cells_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
-                                                   h->cell_count, h->cell_atoms, rc2, sig2, e24, f);
+            lj_tiled_kernel<R><<<h->ncells, LJ_T, lj_tiled_smem<R>(h->cell_cap), st>>>(
+                x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap, h->cell_count, h->cell_atoms, rc2, sig2, e24, f);
             mark(h, "lj_cell_force");
         } else {
             dim3 g((h->max_wn + 127) / 128, h->W);

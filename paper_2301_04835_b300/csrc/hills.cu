@@ -18,8 +18,10 @@
 //   * hill records are staged in shared memory by the bulk-copy (TMA) engine
 //     into a 4-stage ring guarded by mbarriers, so every loaded record is
 //     reused by all points of the CTA;
-//   * per-thread FP32 sums are flushed into FP64 after every 128-pair chunk,
-//     and the hill-range splits are reduced in a fixed order (deterministic).
+//   * per-thread FP32 chunk sums are folded into compensated FP32 (TwoSum)
+//     accumulators after every 128-pair chunk (no FP64 in the loop),
+//     and the hill-range splits are reduced in a fixed order by the CTA that
+//     finishes last (one launch, deterministic, no CTA waits for another).
 // FP64 path: the same sum in double with exp(), for parity at 1e-12.
 #include "wtmd_internal.cuh"
 
@@ -75,6 +77,252 @@ template <int TH> __device__ __forceinline__ void reduce_lanes(double acc[4])
     }
 }
 
+// Output of a hills-sum launch: V [P], dV [P][dvs] (first D columns), the
+// gradient scale gs (dV_i = gs_i * sum_k e_k D_ki in the kernel's units), a
+// launch ticket and the status word.
+template <typename R> struct HillOut {
+    R* V;
+    R* dV;
+    int dvs;
+    int D;
+    double gs[3];
+    unsigned* ticket;  // null: partials only (a separate finalize kernel reduces them)
+    unsigned* status;
+};
+
+// L2 load that bypasses L1 (the partials were written by other CTAs of the
+// same launch).
+__device__ __forceinline__ dbl4 ldcg4(const dbl4* p)
+{
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return dbl4{a.x, a.y, b.x, b.y};
+}
+
+// Every CTA calls this after writing its partial sums.  The CTA that takes the
+// last ticket sums the splits of every point in split order (the same order
+// whichever CTA is last, so the result is deterministic), writes V and dV and
+// resets the ticket for the next launch.  No CTA waits for another.
+template <typename R>
+__device__ void finalize_if_last(const dbl4* partial, int P, const HillOut<R>& o)
+{
+    if (!o.ticket) return;
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(o.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int S = gridDim.y;
+    auto emit = [&](int p, const double a[4]) {
+        const double g[3] = {o.gs[0] * a[1], o.gs[1] * a[2], o.gs[2] * a[3]};
+        if (!isfinite(a[0]) || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) atomicOr(o.status, ST_NUMERIC);
+        if (o.V) o.V[p] = (R)a[0];
+        if (o.dV)
+            for (int i = 0; i < o.D; ++i) o.dV[(size_t)p * o.dvs + i] = (R)g[i];
+    };
+    if (P <= 8) {
+        // few points: the whole CTA strides over the splits of each point
+        __shared__ double red[HB / 32][4];
+        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+        for (int p = 0; p < P; ++p) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                const dbl4 q = ldcg4(partial + (size_t)s * P + p);
+                a[0] += q.x;
+                a[1] += q.y;
+                a[2] += q.z;
+                a[3] += q.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = lane_sum<32>(a[i]);
+            if (lane == 0)
+                for (int i = 0; i < 4; ++i) red[warp][i] = a[i];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+                    for (int i = 0; i < 4; ++i) t[i] += red[w][i];
+                emit(p, t);
+            }
+            __syncthreads();
+        }
+    } else if (S <= 8) {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int s = 0; s < S; ++s) {
+                const dbl4 q = ldcg4(partial + (size_t)s * P + p);
+                a[0] += q.x;
+                a[1] += q.y;
+                a[2] += q.z;
+                a[3] += q.w;
+            }
+            emit(p, a);
+        }
+    } else {
+        const int lane = threadIdx.x % 32, nw = blockDim.x / 32;
+        for (int p = threadIdx.x / 32; p < P; p += nw) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int s = lane; s < S; s += 32) {
+                const dbl4 q = ldcg4(partial + (size_t)s * P + p);
+                a[0] += q.x;
+                a[1] += q.y;
+                a[2] += q.z;
+                a[3] += q.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = lane_sum<32>(a[i]);
+            if (lane == 0) emit(p, a);
+        }
+    }
+    if (threadIdx.x == 0) *o.ticket = 0u;
+}
+
+// Separate reduction of the splits when P x splits is large: one warp per
+// point (lanes stride over the splits, fixed shuffle tree).
+template <typename R>
+__global__ void __launch_bounds__(256) hills_finalize_kernel(const dbl4* __restrict__ partial, int S, int P,
+                                                             HillOut<R> o)
+{
+    const int lane = threadIdx.x % 32;
+    const int p = blockIdx.x * 8 + threadIdx.x / 32;
+    if (p >= P) return;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = lane; s < S; s += 32) {
+        const dbl4 q = partial[(size_t)s * P + p];
+        a[0] += q.x;
+        a[1] += q.y;
+        a[2] += q.z;
+        a[3] += q.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = lane_sum<32>(a[i]);
+    if (lane == 0) {
+        const double g[3] = {o.gs[0] * a[1], o.gs[1] * a[2], o.gs[2] * a[3]};
+        if (!isfinite(a[0]) || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) atomicOr(o.status, ST_NUMERIC);
+        if (o.V) o.V[p] = (R)a[0];
+        if (o.dV)
+            for (int i = 0; i < o.D; ++i) o.dV[(size_t)p * o.dvs + i] = (R)g[i];
+    }
+}
+
+// ---- compensated-FP32 reduction path of the FP32 kernel (no FP64 ops until
+// the one conversion per point) ----
+struct CF4 {
+    cf v[4];
+};
+
+__device__ __forceinline__ void store_cf4(dbl4* slot, const CF4& a)
+{
+    float4* q = reinterpret_cast<float4*>(slot);
+    q[0] = make_float4(a.v[0].hi, a.v[0].lo, a.v[1].hi, a.v[1].lo);
+    q[1] = make_float4(a.v[2].hi, a.v[2].lo, a.v[3].hi, a.v[3].lo);
+}
+__device__ __forceinline__ CF4 load_cf4(const dbl4* slot)
+{
+    const float4* q = reinterpret_cast<const float4*>(slot);
+    const float4 a = __ldcg(q), b = __ldcg(q + 1);
+    return CF4{{cf{a.x, a.y}, cf{a.z, a.w}, cf{b.x, b.y}, cf{b.z, b.w}}};
+}
+__device__ __forceinline__ void cf4_add(CF4& a, const CF4& b)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a.v[i] = cf_add(a.v[i], b.v[i]);
+}
+template <int W> __device__ __forceinline__ void cf4_lane_sum(CF4& a)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.v[i] = cf_add(a.v[i], cf_shfl_xor(a.v[i], o));
+}
+
+// Reduce over the TH hill lanes of each point (lane 0 of the point gets it).
+template <int TH> __device__ __forceinline__ void reduce_lanes_cf(CF4& a)
+{
+    if constexpr (TH <= 32) {
+        cf4_lane_sum<TH>(a);
+    } else {
+        __shared__ CF4 red[HB / 32];
+        cf4_lane_sum<32>(a);
+        if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = a;
+        __syncthreads();
+        if (threadIdx.x % TH == 0) {
+            CF4 t = red[threadIdx.x / 32];
+            for (int w = 1; w < TH / 32; ++w) cf4_add(t, red[threadIdx.x / 32 + w]);
+            a = t;
+        }
+    }
+}
+
+__device__ __forceinline__ void emit_cf(int p, const CF4& a, const HillOut<float>& o)
+{
+    const double v = cf_val(a.v[0]);
+    const double g[3] = {o.gs[0] * cf_val(a.v[1]), o.gs[1] * cf_val(a.v[2]), o.gs[2] * cf_val(a.v[3])};
+    if (!isfinite(v) || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) atomicOr(o.status, ST_NUMERIC);
+    if (o.V) o.V[p] = (float)v;
+    if (o.dV)
+        for (int i = 0; i < o.D; ++i) o.dV[(size_t)p * o.dvs + i] = (float)g[i];
+}
+
+// Sum of the S splits of point p by the whole CTA (fixed order: thread
+// strides, xor tree, warps in order); the result is valid in thread 0.
+__device__ __forceinline__ CF4 cta_split_sum(const dbl4* partial, int S, int P, int p)
+{
+    __shared__ CF4 red[HB / 32];
+    CF4 a{};
+    for (int s = threadIdx.x; s < S; s += blockDim.x) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
+    cf4_lane_sum<32>(a);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = a;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) cf4_add(a, red[w]);
+    __syncthreads();
+    return a;
+}
+
+// As finalize_if_last, for the compensated partials of the FP32 kernel.
+__device__ void finalize_if_last_cf(const dbl4* partial, int P, const HillOut<float>& o)
+{
+    if (!o.ticket) return;
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(o.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int S = gridDim.y;
+    if (P <= 8) {
+        for (int p = 0; p < P; ++p) {
+            const CF4 a = cta_split_sum(partial, S, P, p);
+            if (threadIdx.x == 0) emit_cf(p, a, o);
+        }
+    } else {
+        const int lane = threadIdx.x % 32, nw = blockDim.x / 32;
+        for (int p = threadIdx.x / 32; p < P; p += nw) {
+            CF4 a{};
+            for (int s = lane; s < S; s += 32) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
+            cf4_lane_sum<32>(a);
+            if (lane == 0) emit_cf(p, a, o);
+        }
+    }
+    if (threadIdx.x == 0) *o.ticket = 0u;
+}
+
+__global__ void __launch_bounds__(256) hills_finalize_cf_kernel(const dbl4* __restrict__ partial, int S, int P,
+                                                                HillOut<float> o)
+{
+    const int lane = threadIdx.x % 32;
+    const int p = blockIdx.x * 8 + threadIdx.x / 32;
+    if (p >= P) return;
+    CF4 a{};
+    for (int s = lane; s < S; s += 32) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
+    cf4_lane_sum<32>(a);
+    if (lane == 0) emit_cf(p, a, o);
+}
+
 __device__ __forceinline__ float2 wrap2(float2 d, float per, float iper)
 {
     float2 k = __fmul2_rn(d, make_float2(iper, iper));
@@ -87,7 +335,7 @@ template <int D, int TH, bool PER, typename PT>
 __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict__ hp, const long long* __restrict__ cnt,
                                                        const PT* __restrict__ xi, int xs, int P,
                                                        const double* __restrict__ ctr, HillPrmF32 prm,
-                                                       dbl4* __restrict__ partial, unsigned* status)
+                                                       dbl4* __restrict__ partial, HillOut<float> out)
 {
     constexpr int TP = HB / TH;  // points per CTA
     __shared__ __align__(128) float4 ring[NST][2 * CHUNK];
@@ -129,12 +377,16 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
         }
     }
 
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    // chunk sums are folded into compensated FP32 accumulators (hi + lo,
+    // Knuth's TwoSum): ~48-bit sums without FP64 instructions, which are slow
+    // on this part
+    CF4 acc{};
+    auto fold = [&](int i, float x) { acc.v[i] = cf_add(acc.v[i], x); };
     int c = 0;
     for (; c < nmine; ++c) {
         const int s = c % NST;
         const uint32_t parity = (uint32_t)(c / NST) & 1u;
-        const bool ok = mbar_wait_bounded(&bar[s], parity, status);
+        const bool ok = mbar_wait_bounded(&bar[s], parity, out.status);
         if (!__syncthreads_and(ok)) break;
         const float4* sh = ring[s];
         float2 v = make_float2(0.f, 0.f), g0 = v, g1 = v, g2 = v;
@@ -162,10 +414,18 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
             if constexpr (D >= 2) g1 = __ffma2_rn(e, d1, g1);
             if constexpr (D >= 3) g2 = __ffma2_rn(e, d2, g2);
         }
-        acc[0] += (double)v.x + (double)v.y;
-        acc[1] += (double)g0.x + (double)g0.y;
-        if constexpr (D >= 2) acc[2] += (double)g1.x + (double)g1.y;
-        if constexpr (D >= 3) acc[3] += (double)g2.x + (double)g2.y;
+        fold(0, v.x);
+        fold(0, v.y);
+        fold(1, g0.x);
+        fold(1, g0.y);
+        if constexpr (D >= 2) {
+            fold(2, g1.x);
+            fold(2, g1.y);
+        }
+        if constexpr (D >= 3) {
+            fold(3, g2.x);
+            fold(3, g2.y);
+        }
         __syncthreads();  // stage s consumed by every thread
         if (tid == 0 && c + NST < nmine) {
             mbar_arrive_expect_tx(&bar[s], CHUNK * 32);
@@ -173,21 +433,25 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
         }
     }
     if (c < nmine) {
-        // timed out: let the copies already issued land before the CTA exits
+        // timed out (recorded in the status word): let the copies already
+        // issued land, then take part in the ticket so the next launch starts
+        // from a clean ticket
         if (tid == 0)
             for (int k = c; k < nmine && k < c + NST; ++k)
-                mbar_wait_bounded(&bar[k % NST], (uint32_t)(k / NST) & 1u, status);
+                mbar_wait_bounded(&bar[k % NST], (uint32_t)(k / NST) & 1u, out.status);
         __syncthreads();
-        return;
+    } else {
+        reduce_lanes_cf<TH>(acc);
+        if (p < P && hl == 0) store_cf4(partial + (size_t)blockIdx.y * P + p, acc);
     }
-    reduce_lanes<TH>(acc);
-    if (p < P && hl == 0) partial[(size_t)blockIdx.y * P + p] = dbl4{acc[0], acc[1], acc[2], acc[3]};
+    finalize_if_last_cf(partial, P, out);
 }
 
 template <int TH, bool PER>
 __global__ void __launch_bounds__(HB) hills_f64_kernel(const dbl4* __restrict__ hills, const long long* __restrict__ cnt,
                                                        const double* __restrict__ xi, int xs, int P, int D,
-                                                       HillPrmF64 prm, dbl4* __restrict__ partial)
+                                                       HillPrmF64 prm, dbl4* __restrict__ partial,
+                                                       HillOut<double> out)
 {
     constexpr int TP = HB / TH;
     const int tid = threadIdx.x;
@@ -218,28 +482,7 @@ __global__ void __launch_bounds__(HB) hills_f64_kernel(const dbl4* __restrict__ 
     }
     reduce_lanes<TH>(acc);
     if (p < P && hl == 0) partial[(size_t)blockIdx.y * P + p] = dbl4{acc[0], acc[1], acc[2], acc[3]};
-}
-
-template <typename R>
-__global__ void hills_finalize_kernel(const dbl4* __restrict__ partial, int nsplit, int P, int D, double gs0,
-                                      double gs1, double gs2, R* __restrict__ V, R* __restrict__ dV, int dvs,
-                                      unsigned* status)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int s = 0; s < nsplit; ++s) {
-        const dbl4 q = partial[(size_t)s * P + p];
-        a0 += q.x;
-        a1 += q.y;
-        a2 += q.z;
-        a3 += q.w;
-    }
-    const double g[3] = {gs0 * a1, gs1 * a2, gs2 * a3};
-    if (!isfinite(a0) || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) atomicOr(status, ST_NUMERIC);
-    if (V) V[p] = (R)a0;
-    if (dV)
-        for (int i = 0; i < D; ++i) dV[(size_t)p * dvs + i] = (R)g[i];
+    finalize_if_last<double>(partial, P, out);
 }
 
 // ----------------------------------------------------------------------------
@@ -306,7 +549,9 @@ static Plan plan_for(long long P, long long cap_pairs)
     else pl.th = 256;
     const long long tp = HB / pl.th;
     const long long tiles = (P + tp - 1) / tp;
-    const long long want = 4ll * num_sms();
+    // few points: ~2 CTAs per SM (each CTA then streams several chunks and
+    // the final reduction stays short); many points: ~4 per SM
+    const long long want = (P < 64 ? 2ll : 4ll) * num_sms();
     long long split = (want + tiles - 1) / tiles;
     const long long nch = (cap_pairs + CHUNK - 1) / CHUNK;
     if (split > nch) split = nch;
@@ -318,20 +563,20 @@ static Plan plan_for(long long P, long long cap_pairs)
 
 template <int D, bool PER, typename PT>
 static void launch_f32_d(int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* cnt, const PT* xi,
-                         int xs, int P, const double* ctr, const HillPrmF32& prm, dbl4* part, unsigned* status)
+                         int xs, int P, const double* ctr, const HillPrmF32& prm, dbl4* part, const HillOut<float>& o)
 {
     switch (th) {
-    case 1: hills_f32_kernel<D, 1, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, status); break;
-    case 4: hills_f32_kernel<D, 4, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, status); break;
-    case 32: hills_f32_kernel<D, 32, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, status); break;
-    default: hills_f32_kernel<D, 256, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, status); break;
+    case 1: hills_f32_kernel<D, 1, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 4: hills_f32_kernel<D, 4, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 32: hills_f32_kernel<D, 32, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
+    default: hills_f32_kernel<D, 256, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
     }
 }
 
 template <typename PT>
 static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* cnt,
                           const PT* x, int xs, int P, const double* ctr, const HillPrmF32& prm, dbl4* part,
-                          unsigned* status)
+                          const HillOut<float>& status)
 {
     switch (d * 2 + (per ? 1 : 0)) {
     case 2: launch_f32_d<1, false, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
@@ -345,13 +590,13 @@ static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, c
 
 template <bool PER>
 static void launch_f64_t(int th, dim3 grid, cudaStream_t st, const dbl4* hills, const long long* cnt, const double* xi,
-                         int xs, int P, int D, const HillPrmF64& prm, dbl4* part)
+                         int xs, int P, int D, const HillPrmF64& prm, dbl4* part, const HillOut<double>& o)
 {
     switch (th) {
-    case 1: hills_f64_kernel<1, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part); break;
-    case 4: hills_f64_kernel<4, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part); break;
-    case 32: hills_f64_kernel<32, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part); break;
-    default: hills_f64_kernel<256, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part); break;
+    case 1: hills_f64_kernel<1, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part, o); break;
+    case 4: hills_f64_kernel<4, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part, o); break;
+    case 32: hills_f64_kernel<32, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part, o); break;
+    default: hills_f64_kernel<256, PER><<<grid, HB, 0, st>>>(hills, cnt, xi, xs, P, D, prm, part, o); break;
     }
 }
 
@@ -407,6 +652,9 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void
         h->partial_bytes = need;
     }
     dim3 grid((unsigned)tiles, (unsigned)pl.split);
+    // small reductions are done by the CTA that finishes last (saves a
+    // launch); large ones by a separate, parallel finalize kernel
+    const bool fused = (long long)pl.split * P <= 16384;
     bool per = false;
     for (int i = 0; i < h->d; ++i) per = per || h->cv[i].period > 0.0;
     double gs[3] = {0.0, 0.0, 0.0};
@@ -421,15 +669,19 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void
         }
         auto part = (dbl4*)h->partial;
         const int Pi = (int)P;
+        HillOut<float> o{(float*)V, (float*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
+                         h->status};
         if (xi_f64)
             launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, h->hills32, h->count, (const double*)xi, xs, Pi,
-                                  h->ctr, prm, part, h->status);
+                                  h->ctr, prm, part, o);
         else
             launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, h->hills32, h->count, (const float*)xi, xs, Pi,
-                                 h->ctr, prm, part, h->status);
-        mark(h, "hills_partial_f32");
-        hills_finalize_kernel<float><<<(Pi + 255) / 256, 256, 0, h->stream>>>(
-            part, pl.split, Pi, h->d, gs[0], gs[1], gs[2], (float*)V, (float*)dV, dvs, h->status);
+                                 h->ctr, prm, part, o);
+        mark(h, "hills_sum_f32");
+        if (!fused) {
+            hills_finalize_cf_kernel<<<(Pi + 7) / 8, 256, 0, h->stream>>>(part, pl.split, Pi, o);
+            mark(h, "hills_finalize");
+        }
     } else {
         HillPrmF64 prm{};
         for (int i = 0; i < 3; ++i) {
@@ -440,17 +692,20 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void
         }
         auto part = (dbl4*)h->partial;
         const int Pi = (int)P;
+        HillOut<double> o{(double*)V, (double*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
+                          h->status};
         if (per)
             launch_f64_t<true>(pl.th, grid, h->stream, (const dbl4*)h->hills64, h->count, (const double*)xi, xs, Pi,
-                               h->d, prm, part);
+                               h->d, prm, part, o);
         else
             launch_f64_t<false>(pl.th, grid, h->stream, (const dbl4*)h->hills64, h->count, (const double*)xi, xs, Pi,
-                                h->d, prm, part);
-        mark(h, "hills_partial_f64");
-        hills_finalize_kernel<double><<<(Pi + 255) / 256, 256, 0, h->stream>>>(
-            part, pl.split, Pi, h->d, gs[0], gs[1], gs[2], (double*)V, (double*)dV, dvs, h->status);
+                                h->d, prm, part, o);
+        mark(h, "hills_sum_f64");
+        if (!fused) {
+            hills_finalize_kernel<double><<<(Pi + 7) / 8, 256, 0, h->stream>>>(part, pl.split, Pi, o);
+            mark(h, "hills_finalize");
+        }
     }
-    mark(h, "hills_finalize");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
 }

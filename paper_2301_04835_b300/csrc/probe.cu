@@ -70,7 +70,7 @@ extern "C" int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms)
     cudaEventDestroy(e1);
     cudaFree(out);
     if (cudaGetLastError() != cudaSuccess) return WTMD_ECUDA;
-    const double ops = (double)blocks * threads * iters * 8.0 * (kind == 0 ? 1.0 : 4.0);
+    const double ops = (double)blocks * threads * iters * 8.0 * (kind == 0 ? 1.0 : 2.0);  // FFMA2 = 2 lane FMAs
     *ops_per_s = ops / (best * 1e-3);
     if (ms) *ms = best;
     return WTMD_OK;

@@ -45,6 +45,7 @@ struct Box {
     double invL[3];
     float Lf[3];
     float Llo[3];
+    float invLf[3];
 };
 
 template <typename R> __device__ __forceinline__ R min_image(R d, const Box& b, int k);
@@ -55,7 +56,7 @@ template <> __device__ __forceinline__ double min_image<double>(double d, const 
 template <> __device__ __forceinline__ float min_image<float>(float d, const Box& b, int k)
 {
     if (!(b.Lf[k] > 0.f)) return d;
-    const float n = rintf(d * (float)b.invL[k]);
+    const float n = rintf(d * b.invLf[k]);
     return fmaf(-n, b.Llo[k], fmaf(-n, b.Lf[k], d));
 }
 
@@ -146,6 +147,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Compensated FP32 sum (hi + lo, Knuth's TwoSum): about 48 significant bits
+// from FP32 instructions only (FP64 throughput is very low on this part).
+struct cf {
+    float hi, lo;
+};
+__device__ __forceinline__ cf cf_add(cf a, float b)
+{
+    const float s = a.hi + b;
+    const float bp = s - a.hi;
+    return cf{s, a.lo + ((a.hi - (s - bp)) + (b - bp))};
+}
+__device__ __forceinline__ cf cf_add(cf a, cf b)
+{
+    cf r = cf_add(a, b.hi);
+    r.lo += b.lo;
+    return r;
+}
+__device__ __forceinline__ cf cf_shfl_xor(cf a, int off)
+{
+    return cf{__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
+__device__ __forceinline__ double cf_val(cf a) { return (double)a.hi + (double)a.lo; }
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -166,6 +190,12 @@ struct CvDev {
     int* inv_b = nullptr;
     double r0 = 1.0, scale = 0.0, period = 0.0;
     bool same_ab = false;          // A and B are the same set (one pair pass, factor 2)
+    int* order = nullptr;          // device: coordination targets, members of A first, then B-only members
+    double* scw = nullptr;         // device [W]: coordination scale per walker
+    void* tile_row = nullptr;      // tile path (list A): row partials [W][chunk][|A|] R4
+    void* tile_col = nullptr;      // column partials [W][tile][|B|] R4
+    int nbchunk = 0, ntile = 0, nB_stride = 0;
+    int n_order = 0;
     // QPAIRS: CSR from atom to (pair, sign)
     int n_pairs = 0;
     int* q_rowptr = nullptr;       // [max_wn + 1]
@@ -213,6 +243,7 @@ struct wtmd_t {
     long long* step = nullptr;     // device step counter
     long long* dep = nullptr;      // device [2]: first new hill, number of new hills this step
     unsigned* status = nullptr;
+    unsigned* ticket = nullptr;    // last-CTA ticket of the hills-sum launch (0 between launches)
     double* grid = nullptr;
     int64_t ncell = 0;
     double* gfac = nullptr;        // [W][sum bins] per-axis Gaussian factors of new hills
@@ -239,6 +270,10 @@ struct wtmd_t {
     void* force = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+    cudaStream_t side_stream = nullptr; // engine-force branch of a step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t cv_stream[3] = {nullptr, nullptr, nullptr};  // branches of CVs 1, 2
+    cudaEvent_t ev_cv[3] = {nullptr, nullptr, nullptr};
     bool forces_valid = false;
     // graphs
     cudaGraphExec_t graph = nullptr;
@@ -275,6 +310,7 @@ namespace wtmd {
 
 // launchers (defined in the .cu files); all enqueue on h->stream
 int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all CVs
+int launch_cv(wtmd_t* h, const void* pos, int c);               // xi, J of CV c
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
