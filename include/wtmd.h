@@ -161,6 +161,19 @@ int wtmd_check(wtmd_t* h);
  * deposit and does not touch the bound arrays. */
 int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_out, void* xi_out, void* dV_out);
 
+/* CV values and Jacobians at `pos` (device [n_atoms][4] Real) for every
+ * walker: xi_out (device [W][n_cv] Real).  The Jacobians are kept in the
+ * handle for wtmd_cv_adjoint.  The paper obtains CV gradients with jax.grad
+ * (Sec. 2); here they are written by hand. */
+int wtmd_cv_forward(wtmd_t* h, const void* pos, void* xi_out);
+
+/* Adjoint (vector-Jacobian product) of the CV map of the most recent
+ * wtmd_cv_forward or bias_eval on this handle: grad_pos[i] =
+ * sum_c grad_xi[w(i)][c] d xi_c / d r_i.  grad_xi: device [W][n_cv] Real;
+ * grad_pos: device [n_atoms][4] Real, overwritten (w = 0).  With grad_xi =
+ * -dV/dxi this is the bias force. */
+int wtmd_cv_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos);
+
 /* Hills sum alone at P points: xi (device [P][n_cv] Real) ->
  * V_out [P] Real, dV_out [P][n_cv] Real (device). */
 int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out);

@@ -64,7 +64,7 @@ class CvDesc(C.Structure):
 EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", "cv_define", "wtmd_bind", "step_n",
            "wtmd_check", "bias_eval", "hills_eval", "fes_grid", "wtmd_hills_load", "wtmd_hills_read",
            "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
-           "wtmd_hills_eval_static"]
+           "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint"]
 
 _lib = None
 
@@ -97,6 +97,8 @@ def lib() -> C.CDLL:
     L.wtmd_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64]
     L.wtmd_profile_step.argtypes = [vp, i64, C.c_char_p, C.POINTER(C.c_double), i32, C.POINTER(i32)]
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wtmd_cv_forward.argtypes = [vp, vp, vp]
+    L.wtmd_cv_adjoint.argtypes = [vp, vp, vp]
     L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
                                          vp, vp]
     for name in EXPORTS:
@@ -243,6 +245,26 @@ class Wtmd:
                   "bias_eval")
         return V, xi, dV
 
+    def cv_forward(self, pos):
+        """CV values [W, d] at pos; keeps the Jacobians for cv_adjoint."""
+        torch = _torch()
+        self._stream()
+        xi = torch.empty(self.W, self.d, dtype=self.dtype, device=pos.device)
+        self._err(lib().wtmd_cv_forward(self.h, self._check_tensor(pos, (self.N, 4)), C.c_void_p(xi.data_ptr())),
+                  "wtmd_cv_forward")
+        self._gen = getattr(self, "_gen", 0) + 1
+        return xi
+
+    def cv_adjoint(self, grad_xi):
+        """J^T grad_xi of the latest forward: [N, 4] (last column 0)."""
+        torch = _torch()
+        self._stream()
+        g = grad_xi.to(self.dtype).contiguous()
+        out = torch.empty(self.N, 4, dtype=self.dtype, device=g.device)
+        self._err(lib().wtmd_cv_adjoint(self.h, self._check_tensor(g, (self.W, self.d)), C.c_void_p(out.data_ptr())),
+                  "wtmd_cv_adjoint")
+        return out
+
     def hills_eval(self, xi):
         torch = _torch()
         self._stream()
@@ -308,6 +330,44 @@ class Wtmd:
         out = np.zeros(n)
         self._err(lib().wtmd_grid_read(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), n), "wtmd_grid_read")
         return out.reshape(self.grid_shape)
+
+
+def _cv_function():
+    import torch
+
+    class CVFunction(torch.autograd.Function):
+        """xi = CVs(positions) with the hand-written adjoint as backward.
+
+        Forward: pos [N, 3] (or [N, 4]) -> xi [W, d] through wtmd_cv_forward;
+        backward: grad_pos = J^T grad_xi through the wtmd_cv_adjoint kernel.
+        If another forward ran on the handle in between, the forward is
+        recomputed at the saved positions first (the adjoint uses the
+        handle's latest Jacobians)."""
+
+        @staticmethod
+        def forward(ctx, pos, handle):
+            p4 = pos if pos.shape[-1] == 4 else torch.nn.functional.pad(pos, (0, 1))
+            p4 = p4.detach().to(handle.dtype).contiguous()
+            xi = handle.cv_forward(p4)
+            ctx.handle, ctx.gen, ctx.ncol = handle, handle._gen, pos.shape[-1]
+            ctx.save_for_backward(p4)
+            return xi
+
+        @staticmethod
+        def backward(ctx, grad_xi):
+            h = ctx.handle
+            (p4,) = ctx.saved_tensors
+            if h._gen != ctx.gen:
+                h.cv_forward(p4)
+            g = h.cv_adjoint(grad_xi)
+            return g[:, : ctx.ncol].to(grad_xi.dtype), None
+
+    return CVFunction
+
+
+def cv_apply(pos, handle):
+    """Differentiable CV evaluation: xi = cv_apply(pos, handle)."""
+    return _cv_function().apply(pos, handle)
 
 
 def probe_peak(kind: int):

@@ -551,6 +551,25 @@ extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_
     return WTMD_OK;
 }
 
+extern "C" int wtmd_cv_forward(wtmd_t* h, const void* pos, void* xi_out)
+{
+    if (!h) return WTMD_EINVAL;
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!pos || !xi_out) FAIL(h, WTMD_EINVAL, "null positions or output");
+    if ((rc = launch_cvs(h, pos))) return rc;
+    return copy_cols(h, xi_out, h->xi, true, h->d);
+}
+
+extern "C" int wtmd_cv_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos)
+{
+    if (!h) return WTMD_EINVAL;
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!grad_xi || !grad_pos) FAIL(h, WTMD_EINVAL, "null gradient");
+    return launch_adjoint(h, grad_xi, grad_pos);
+}
+
 extern "C" int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out)
 {
     if (!h) return WTMD_EINVAL;

@@ -699,6 +699,43 @@ __global__ void scatter_kernel(long long N, int d, const int* __restrict__ aw, c
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of the CV map (the paper differentiates CVs with jax.grad, Sec. 2):
+// grad_r[i] = sum_c grad_xi[w(i)][c] J_c[i] for an arbitrary upstream
+// grad_xi [W][d]; with grad_xi = -dV/dxi this is the bias force.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void cv_adjoint_kernel(long long N, int d, const int* __restrict__ aw, const R* __restrict__ gxi,
+                                  const R4<R>* __restrict__ J, R4<R>* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int w = aw[i];
+    R gx = 0, gy = 0, gz = 0;
+    for (int c = 0; c < d; ++c) {
+        const R g = gxi[(size_t)w * d + c];
+        const R4<R> j = J[(size_t)c * N + i];
+        gx += g * j.x;
+        gy += g * j.y;
+        gz += g * j.z;
+    }
+    out[i] = mk4<R>(gx, gy, gz, R(0));
+}
+
+int launch_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos)
+{
+    const int nb = (int)((h->N + 255) / 256);
+    if (h->prec == WTMD_F32)
+        cv_adjoint_kernel<float><<<nb, 256, 0, h->stream>>>(h->N, h->d, h->atom_walker, (const float*)grad_xi,
+                                                            (const float4*)h->J, (float4*)grad_pos);
+    else
+        cv_adjoint_kernel<double><<<nb, 256, 0, h->stream>>>(h->N, h->d, h->atom_walker, (const double*)grad_xi,
+                                                             (const dbl4*)h->J, (dbl4*)grad_pos);
+    mark(h, "cv_adjoint");
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int cv_alloc_scratch(wtmd_t* h, CvDev& c)

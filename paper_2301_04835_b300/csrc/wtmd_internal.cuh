@@ -311,6 +311,7 @@ namespace wtmd {
 // launchers (defined in the .cu files); all enqueue on h->stream
 int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all CVs
 int launch_cv(wtmd_t* h, const void* pos, int c);               // xi, J of CV c
+int launch_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos);  // J^T grad_xi
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
