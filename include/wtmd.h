@@ -216,6 +216,25 @@ int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32
  * measured denominators of the hills-sum roofline; *ms = kernel time. */
 int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
 
+/* Run each MD step of a multi-walker handle as one persistent (cooperative)
+ * kernel launch: BAOAB, all-pairs LJ, coordination and Rg CVs, hills sum over
+ * the shared hill list, bias force and deposition for every walker, with
+ * bounded grid barriers between the phases.  The paper runs replicas as
+ * separate simulations (Sec. 2, concurrent.futures / MPI); here walkers of
+ * uneven size share one GPU launch and one hill list.  Requirements: FP32,
+ * LJ engine with open boundaries, 1-2 CVs among COORDINATION (A = B = all)
+ * and RG (all atoms), walkers of at most 8192 atoms; else WTMD_EINVAL.
+ * enable = 0 returns to the per-kernel step. */
+int wtmd_walkers_persistent(wtmd_t* h, int32_t enable);
+
+/* Autotuner of the persistent walker step: times every candidate (targets
+ * per pair task 32/64/128/256, CTAs per SM 1/2/4, hill splits per CTA 1/2)
+ * over `steps` steps from the same saved state, keeps the fastest, and
+ * restores the state (positions, velocities, forces, hill count, step, grid),
+ * so tuning does not advance the run.  choice (host [3], may be NULL)
+ * receives the chosen (T, CTAs per SM, split factor).  Synchronizes. */
+int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice);
+
 /* Hills sum for callers that cannot allocate device memory (the paper has no
  * counterpart: it is an interface for hosts such as an engine plugin that may
  * only touch the buffers it is given, or a caller whose memory footprint

@@ -64,7 +64,8 @@ class CvDesc(C.Structure):
 EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", "cv_define", "wtmd_bind", "step_n",
            "wtmd_check", "bias_eval", "hills_eval", "fes_grid", "wtmd_hills_load", "wtmd_hills_read",
            "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
-           "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint"]
+           "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint", "wtmd_walkers_persistent",
+           "wtmd_autotune"]
 
 _lib = None
 
@@ -97,6 +98,8 @@ def lib() -> C.CDLL:
     L.wtmd_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), i64]
     L.wtmd_profile_step.argtypes = [vp, i64, C.c_char_p, C.POINTER(C.c_double), i32, C.POINTER(i32)]
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wtmd_walkers_persistent.argtypes = [vp, i32]
+    L.wtmd_autotune.argtypes = [vp, i64, C.POINTER(i32)]
     L.wtmd_cv_forward.argtypes = [vp, vp, vp]
     L.wtmd_cv_adjoint.argtypes = [vp, vp, vp]
     L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
@@ -244,6 +247,17 @@ class Wtmd:
                                   C.c_void_p(V.data_ptr()), C.c_void_p(xi.data_ptr()), C.c_void_p(dV.data_ptr())),
                   "bias_eval")
         return V, xi, dV
+
+    def walkers_persistent(self, enable: bool = True):
+        """Run each step as one persistent launch over all walkers."""
+        self._err(lib().wtmd_walkers_persistent(self.h, 1 if enable else 0), "wtmd_walkers_persistent")
+
+    def autotune(self, steps: int = 5):
+        """Pick the persistent step's tiles by timing; returns (T, CTAs/SM, split factor)."""
+        self._stream()
+        ch = (C.c_int32 * 3)()
+        self._err(lib().wtmd_autotune(self.h, int(steps), ch), "wtmd_autotune")
+        return tuple(ch)
 
     def cv_forward(self, pos):
         """CV values [W, d] at pos; keeps the Jacobians for cv_adjoint."""

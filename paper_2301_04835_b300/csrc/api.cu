@@ -83,6 +83,11 @@ extern "C" int wtmd_destroy(wtmd_t* h)
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
                     h->cell_atoms};
     for (void* p : ptrs) cudaFree(p);
+    {
+        WalkerPlan& k = h->wk;
+        void* wp[] = {k.tasks, k.tbase, k.tcount, k.tpart, k.ticket, k.rgc, k.bar};
+        for (void* p : wp) cudaFree(p);
+    }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -393,6 +398,7 @@ extern "C" int wtmd_bind(wtmd_t* h, void* pos, void* vel, void* force, int64_t n
 // Total force at the bound positions (engine + bias), no kick, no deposit.
 static int enqueue_forces(wtmd_t* h)
 {
+    if (h->persistent) return launch_walkers_step(h, 1);
     int rc;
     if ((rc = launch_engine(h))) return rc;
     if ((rc = launch_cvs(h, h->pos))) return rc;
@@ -439,6 +445,7 @@ static int enqueue_engine_and_bias(wtmd_t* h)
 
 static int enqueue_step(wtmd_t* h)
 {
+    if (h->persistent) return launch_walkers_step(h, 0);
     int rc;
     if ((rc = launch_baoab_first(h))) return rc;
     if ((rc = enqueue_engine_and_bias(h))) return rc;
@@ -489,9 +496,18 @@ extern "C" int step_n(wtmd_t* h, int64_t n_steps)
         if ((rc = enqueue_forces(h))) return rc;
         h->forces_valid = true;
     }
-    if (!h->graph) {
-        if ((rc = capture(h, kGraphSteps, &h->graph))) return rc;
-        if ((rc = capture(h, 1, &h->graph1))) return rc;
+    if (!h->graph && !h->no_graph) {
+        if (capture(h, kGraphSteps, &h->graph) != WTMD_OK || capture(h, 1, &h->graph1) != WTMD_OK) {
+            // this launch sequence cannot be captured here: replay eagerly
+            cudaGetLastError();
+            drop_graphs(h);
+            h->no_graph = true;
+        }
+    }
+    if (h->no_graph) {
+        for (int64_t i = 0; i < n_steps; ++i)
+            if ((rc = enqueue_step(h))) return rc;
+        return WTMD_OK;
     }
     const int64_t full = n_steps / kGraphSteps, rest = n_steps % kGraphSteps;
     for (int64_t i = 0; i < full; ++i) WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
@@ -712,4 +728,115 @@ extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double
     }
     *n_out = n;
     return WTMD_OK;
+}
+
+extern "C" int wtmd_walkers_persistent(wtmd_t* h, int32_t enable)
+{
+    if (!h) return WTMD_EINVAL;
+    drop_graphs(h);
+    h->no_graph = false;
+    if (!enable) {
+        h->persistent = false;
+        return WTMD_OK;
+    }
+    return walkers_enable(h);
+}
+
+// Times each tile candidate over `steps` eager steps from the same saved
+// state (positions, velocities, forces, hill count, step, grid), keeps the
+// fastest and restores the state: tuning does not advance the simulation.
+extern "C" int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!h->persistent) FAIL(h, WTMD_EINVAL, "autotuning applies to the persistent walker step");
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind particle arrays first");
+    if (steps < 1) FAIL(h, WTMD_EINVAL, "steps must be >= 1");
+    int rc;
+    if (!h->forces_valid) {
+        if ((rc = enqueue_forces(h))) return rc;
+        h->forces_valid = true;
+    }
+    const size_t pb = sizeof(float4) * (size_t)h->N;
+    void *sx = nullptr, *sv = nullptr, *sf = nullptr, *sg = nullptr;
+    long long counters[2];
+    double centre[3];
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    WTMD_CUDA_TRY(h, cudaMalloc(&sx, pb));
+    WTMD_CUDA_TRY(h, cudaMalloc(&sv, pb));
+    WTMD_CUDA_TRY(h, cudaMalloc(&sf, pb));
+    if (h->grid) WTMD_CUDA_TRY(h, cudaMalloc(&sg, sizeof(double) * h->ncell));
+    auto save = [&]() {
+        cudaMemcpy(sx, h->pos, pb, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(sv, h->vel, pb, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(sf, h->force, pb, cudaMemcpyDeviceToDevice);
+        if (sg) cudaMemcpy(sg, h->grid, sizeof(double) * h->ncell, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(&counters[0], h->count, sizeof(long long), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&counters[1], h->step, sizeof(long long), cudaMemcpyDeviceToHost);
+        cudaMemcpy(centre, h->ctr, sizeof(centre), cudaMemcpyDeviceToHost);
+    };
+    auto restore = [&]() {
+        cudaStreamSynchronize(h->stream);
+        cudaMemcpy(h->pos, sx, pb, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(h->vel, sv, pb, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(h->force, sf, pb, cudaMemcpyDeviceToDevice);
+        if (sg) cudaMemcpy(h->grid, sg, sizeof(double) * h->ncell, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(h->count, &counters[0], sizeof(long long), cudaMemcpyHostToDevice);
+        cudaMemcpy(h->step, &counters[1], sizeof(long long), cudaMemcpyHostToDevice);
+        cudaMemcpy(h->ctr, centre, sizeof(centre), cudaMemcpyHostToDevice);
+    };
+    save();
+    const int Ts[] = {32, 64, 128, 256}, Bs[] = {1, 2, 4}, Hs[] = {1, 2};
+    float best = 1e30f;
+    int bT = 128, bB = 2, bH = 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    rc = WTMD_OK;
+    for (int T : Ts)
+        for (int B : Bs)
+            for (int Hm : Hs) {
+                if ((rc = walkers_retile(h, T, B, Hm))) goto done;
+                if ((rc = launch_walkers_step(h, 0))) goto done;  // warm-up
+                cudaEventRecord(e0, h->stream);
+                for (int64_t s = 0; s < steps && rc == WTMD_OK; ++s) rc = launch_walkers_step(h, 0);
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                if (rc) goto done;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best && h->wk.T == T && h->wk.bps == B) {
+                    best = ms;
+                    bT = T;
+                    bB = B;
+                    bH = Hm;
+                }
+                restore();
+            }
+done:
+    restore();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rc2 = walkers_retile(h, bT, bB, bH);
+    // hills deposited during the trials lie beyond the restored count: put the
+    // FP32 layout back to padding there
+    pad_hills32_kernel<<<(unsigned)((h->cap_pairs + 255) / 256), 256, 0, h->stream>>>(h->hills32, h->cap_pairs);
+    store_hills32_range(h, 0, counters[0]);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(sx);
+    cudaFree(sv);
+    cudaFree(sf);
+    cudaFree(sg);
+    unsigned st = 0;
+    cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
+    st &= ~ST_CAPACITY;  // trial deposits may have hit capacity
+    cudaMemcpy(h->status, &st, sizeof(st), cudaMemcpyHostToDevice);
+    drop_graphs(h);
+    h->no_graph = false;
+    if (choice) {
+        choice[0] = bT;
+        choice[1] = h->wk.bps;
+        choice[2] = bH;
+    }
+    if (rc) return rc;
+    return rc2;
 }

@@ -12,19 +12,11 @@
 // image), which needs sum(bins) exponentials per hill instead of prod(bins).
 #include <algorithm>
 
-#include "wtmd_internal.cuh"
+#include "step_dev.cuh"
 
 namespace wtmd {
 
 void store_hills32_range(wtmd_t* h, long long k0, long long k1);
-
-struct DepPrm {
-    long long stride;
-    long long cap;
-    int W, d;
-    double w0, inv_dT;  // inv_dT = 1/(kT (gamma - 1)); 0 for standard metadynamics
-    double a[3];        // FP32 layout scale
-};
 
 template <typename R>
 __global__ void __launch_bounds__(256) deposit_kernel(DepPrm p, const double* __restrict__ xi,
@@ -33,45 +25,7 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepPrm p, const double* __
                                                       double* __restrict__ ctr, dbl4* __restrict__ h64,
                                                       float* __restrict__ h32, unsigned* status)
 {
-    __shared__ long long base;
-    __shared__ int doit;
-    __shared__ double c[3];
-    if (threadIdx.x == 0) {
-        const long long t = *step;
-        doit = p.stride > 0 && (t + 1) % p.stride == 0;
-        base = *count;
-        if (doit && base + p.W > p.cap) {
-            atomicOr(status, ST_CAPACITY);
-            doit = 0;
-        }
-        dep[0] = base;
-        dep[1] = doit ? p.W : 0;
-        // the centre of the scaled FP32 layout is fixed by the first hill
-        // when no grid defined it
-        if (doit && isnan(ctr[0]))
-            for (int i = 0; i < 3; ++i) ctr[i] = i < p.d ? xi[i] : 0.0;
-        for (int i = 0; i < 3; ++i) c[i] = ctr[i];
-    }
-    __syncthreads();
-    if (doit) {
-        for (int w = threadIdx.x; w < p.W; w += blockDim.x) {
-            const long long k = base + w;
-            double s[3] = {0.0, 0.0, 0.0};
-            for (int i = 0; i < p.d; ++i) s[i] = xi[w * 4 + i];
-            const double hgt = p.w0 * exp(-(double)V[w] * p.inv_dT);
-            h64[k] = dbl4{s[0], s[1], s[2], hgt};
-            const long long b = (k >> 1) * 8 + (k & 1);
-            h32[b + 0] = (float)(-(s[0] - c[0]) * p.a[0]);
-            h32[b + 2] = (float)(-(s[1] - c[1]) * p.a[1]);
-            h32[b + 4] = (float)(-(s[2] - c[2]) * p.a[2]);
-            h32[b + 6] = (float)(-log2(hgt));
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (doit) *count = base + p.W;
-        *step = *step + 1;
-    }
+    deposit_block<R>(p, xi, V, count, step, dep, ctr, h64, h32, status);
 }
 
 struct GridPrm {
@@ -221,6 +175,11 @@ int launch_deposit(wtmd_t* h)
         deposit_kernel<double><<<1, 256, 0, h->stream>>>(p, h->xi, (const double*)h->V, h->count, h->step, h->dep,
                                                          h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status);
     mark(h, "deposit");
+    return launch_grid_update(h);
+}
+
+int launch_grid_update(wtmd_t* h)
+{
     if (h->grid) {
         GridPrm g = grid_prm(h);
         const int tot = h->gbins_sum;

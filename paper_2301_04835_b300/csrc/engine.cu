@@ -10,51 +10,9 @@
 // (seed lo, seed hi) and counter (t lo, i, t hi, 0); its four words become
 // uniforms u = (x + 1/2) 2^-32 and two Box-Muller pairs (first three normals
 // used).  Positions are never wrapped; distances use the minimum image.
-#include "wtmd_internal.cuh"
+#include "step_dev.cuh"
 
 namespace wtmd {
-
-template <typename R> struct Normal3 {
-    R g[3];
-};
-
-template <typename R> __device__ __forceinline__ Normal3<R> noise3(uint64_t seed, long long step, uint32_t i);
-
-template <> __device__ __forceinline__ Normal3<double> noise3<double>(uint64_t seed, long long step, uint32_t i)
-{
-    const U4 r = philox10((uint32_t)step, i, (uint32_t)((unsigned long long)step >> 32), 0u, (uint32_t)seed,
-                          (uint32_t)(seed >> 32));
-    const double k = 2.3283064365386963e-10;  // 2^-32
-    const double u0 = ((double)r.v[0] + 0.5) * k, u1 = ((double)r.v[1] + 0.5) * k;
-    const double u2 = ((double)r.v[2] + 0.5) * k, u3 = ((double)r.v[3] + 0.5) * k;
-    const double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
-    double s1, c1, c3;
-    sincospi(2.0 * u1, &s1, &c1);
-    c3 = cospi(2.0 * u3);
-    Normal3<double> n;
-    n.g[0] = a * c1;
-    n.g[1] = a * s1;
-    n.g[2] = b * c3;
-    return n;
-}
-
-template <> __device__ __forceinline__ Normal3<float> noise3<float>(uint64_t seed, long long step, uint32_t i)
-{
-    const U4 r = philox10((uint32_t)step, i, (uint32_t)((unsigned long long)step >> 32), 0u, (uint32_t)seed,
-                          (uint32_t)(seed >> 32));
-    // 24 significant bits: u = (floor(x / 2^8) + 1/2) 2^-24, in (0, 1)
-    const float k = 5.9604644775390625e-08f;  // 2^-24
-    const float u0 = ((float)(r.v[0] >> 8) + 0.5f) * k, u1 = ((float)(r.v[1] >> 8) + 0.5f) * k;
-    const float u2 = ((float)(r.v[2] >> 8) + 0.5f) * k, u3 = ((float)(r.v[3] >> 8) + 0.5f) * k;
-    const float a = sqrtf(-2.0f * logf(u0)), b = sqrtf(-2.0f * logf(u2));
-    float s1, c1;
-    sincospif(2.0f * u1, &s1, &c1);
-    Normal3<float> n;
-    n.g[0] = a * c1;
-    n.g[1] = a * s1;
-    n.g[2] = b * cospif(2.0f * u3);
-    return n;
-}
 
 template <typename R>
 __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __restrict__ v,
@@ -63,24 +21,7 @@ __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const long long t = *step;
-    const Normal3<R> n = noise3<R>(seed, t, (uint32_t)i);
-    R4<R> xi = x[i], vi = v[i];
-    const R4<R> fi = f[i];
-    R* xp[3] = {&xi.x, &xi.y, &xi.z};
-    R* vp[3] = {&vi.x, &vi.y, &vi.z};
-    const R fp[3] = {fi.x, fi.y, fi.z};
-    for (int k = 0; k < dims; ++k) {
-        R vv = *vp[k], xx = *xp[k];
-        vv += half * fp[k] * inv_m;
-        xx += half * vv;
-        vv = c1 * vv + c2 * n.g[k];
-        xx += half * vv;
-        *vp[k] = vv;
-        *xp[k] = xx;
-    }
-    x[i] = xi;
-    v[i] = vi;
+    baoab_first_atom<R>(i, *step, x, v, f, seed, half, inv_m, c1, c2, dims);
 }
 
 // Mueller-Brown (Mueller & Brown 1979): sum of four anisotropic Gaussians.

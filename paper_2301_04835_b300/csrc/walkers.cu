@@ -1,0 +1,568 @@
+// Many walkers of uneven size in one persistent launch per MD step.
+//
+// Walkers are independent systems (here: Lennard-Jones clusters in open
+// space) that share one hill list; the paper runs replicas as separate
+// simulations (Sec. 2, replicas through concurrent.futures / MPI).  One
+// cooperative kernel does a whole step for all walkers, with bounded grid
+// barriers between the phases:
+//   P0  first half of BAOAB for every atom;
+//   P1  (walker, target tile) tasks, sorted by cost: the walker's positions
+//       are staged in shared memory and one all-pairs loop gives the LJ force,
+//       the coordination row sum and its gradient (A = B = all atoms) and the
+//       Rg moment of each target; the walker's last task finishes its CVs;
+//   P2a hills sum for all walker points over the shared hill list (the FP32
+//       bulk-copy ring task of hills.cu), one partial per hill split;
+//   P2b fixed-order reduction of the splits -> V, dV/dxi per walker;
+//   P3  deposition (CTA 0) and, for every atom, the bias force -J^T dV/dxi
+//       added to the LJ force and the closing half kick.
+// The FP64 bias grid, when configured, is updated by the two grid kernels
+// that follow (they exit at once on steps without a deposit).
+// Tile sizes, CTAs per SM and the hill split count come from the autotuner
+// (wtmd_autotune).  Every reduction has a fixed order: deterministic.
+#include <algorithm>
+#include <vector>
+
+#include "hills_dev.cuh"
+#include "step_dev.cuh"
+
+namespace wtmd {
+
+int launch_grid_update(wtmd_t* h);
+
+constexpr int WK_T = 256;
+
+struct WkArgs {
+    int W;
+    long long N;
+    const int64_t* woff;
+    const int* wn;
+    const int* aw;
+    const int4* tasks;  // (walker, first target, end target, task index within walker), by decreasing cost
+    int ntasks;
+    int T;              // targets per task
+    const int* tbase;   // [W] first partial slot of the walker's tasks
+    const int* tcount;  // [W]
+    double* tpart;      // [ntasks][2]
+    unsigned* ticket;   // [W]
+    float4* rgc;        // [W] Rg centre and Jacobian factor
+    float4* x;
+    float4* v;
+    float4* f;
+    float rc2, sig2, eps24, half, inv_m, c1, c2;
+    uint64_t seed;
+    long long* step;
+    int d, cv_coord, cv_rg;
+    float inv_r0sq, gpref;
+    int hpow;
+    const double* coord_scw;  // [W]
+    double rg_scale;
+    int rg_intensive;
+    float4* J;  // [d][N]
+    double* xi;
+    // hills
+    const float4* hp;
+    const long long* cnt;
+    const double* ctr;
+    HillPrmF32 hprm;
+    dbl4* hpart;
+    int hsplit;
+    HillOut<float> hout;
+    // deposition
+    DepPrm dep;
+    long long* count;
+    long long* depw;
+    double* ctrw;
+    dbl4* h64;
+    float* h32;
+    unsigned* bar;
+    unsigned* status;
+    int max_wn;
+};
+
+// Sense-reversing grid barrier for a cooperative launch.  Waits are bounded
+// (~2^31 cycles); on a timeout the status word records it and false is
+// returned, after which the CTA leaves the kernel.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == gen) {
+                if (clock64() - t0 > (1ll << 31)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int D>
+__global__ void __launch_bounds__(WK_T) walkers_step_kernel(WkArgs a, int mode)
+{
+    extern __shared__ __align__(128) unsigned char wk_smem[];
+    float4 (*ring)[2 * CHUNK] = reinterpret_cast<float4 (*)[2 * CHUNK]>(wk_smem);
+    uint64_t* hbar = reinterpret_cast<uint64_t*>(wk_smem + sizeof(float4) * NST * 2 * CHUNK);
+    float4* wpos = reinterpret_cast<float4*>(wk_smem + sizeof(float4) * NST * 2 * CHUNK + 128);
+    const unsigned G = gridDim.x;
+    const int tid = threadIdx.x;
+
+    // ---- P0: B-A-O-A
+    if (mode == 0) {
+        const long long t = *a.step;
+        for (long long i = (long long)blockIdx.x * WK_T + tid; i < a.N; i += (long long)G * WK_T)
+            baoab_first_atom<float>(i, t, a.x, a.v, a.f, a.seed, a.half, a.inv_m, a.c1, a.c2, 3);
+        if (!grid_barrier(a.bar, G, a.status)) return;
+    }
+
+    // ---- P1: pair tasks
+    {
+        __shared__ float red[WK_T][7];
+        __shared__ float cshare[3];
+        const int T = a.T, Gs = WK_T / a.T;
+        const int ti = tid % T, sl = tid / T;
+        for (int task = blockIdx.x; task < a.ntasks; task += G) {
+            const int4 tk = a.tasks[task];
+            const int w = tk.x, t0 = tk.y, t1 = tk.z;
+            const int n = a.wn[w];
+            const long long o = a.woff[w];
+            __syncthreads();
+            for (int q = tid; q < n; q += WK_T) wpos[q] = a.x[o + q];
+            __syncthreads();
+            // centre of the walker (Rg), identical in every task of the walker
+            if (a.cv_rg >= 0) {
+                cf s3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                for (int q = tid; q < n; q += WK_T) {
+                    s3[0] = cf_add(s3[0], wpos[q].x);
+                    s3[1] = cf_add(s3[1], wpos[q].y);
+                    s3[2] = cf_add(s3[2], wpos[q].z);
+                }
+                for (int k = 0; k < 3; ++k)
+                    for (int off = 16; off > 0; off >>= 1) s3[k] = cf_add(s3[k], cf_shfl_xor(s3[k], off));
+                __shared__ cf cw[WK_T / 32][3];
+                if (tid % 32 == 0)
+                    for (int k = 0; k < 3; ++k) cw[tid / 32][k] = s3[k];
+                __syncthreads();
+                if (tid == 0)
+                    for (int k = 0; k < 3; ++k) {
+                        cf t = cw[0][k];
+                        for (int q = 1; q < WK_T / 32; ++q) t = cf_add(t, cw[q][k]);
+                        cshare[k] = (float)(cf_val(t) / n);
+                    }
+                __syncthreads();
+            }
+            const int i = t0 + ti;
+            const bool act = i < t1;
+            float fx = 0.f, fy = 0.f, fz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, sv = 0.f;
+            if (act) {
+                const float4 p = wpos[i];
+                const int j0 = (int)((long long)n * sl / Gs), j1 = (int)((long long)n * (sl + 1) / Gs);
+#pragma unroll 4
+                for (int j = j0; j < j1; ++j) {
+                    const float4 s = wpos[j];
+                    const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (j == i) continue;
+                    if (a.cv_coord >= 0) {
+                        const float y = r2 * a.inv_r0sq;
+                        float yh1 = y;
+                        for (int k = 2; k < a.hpow; ++k) yh1 *= y;
+                        const float sw = __frcp_rn(1.f + yh1 * y);
+                        sv += sw;
+                        const float gr = a.gpref * yh1 * sw * sw;
+                        gx += gr * dx;
+                        gy += gr * dy;
+                        gz += gr * dz;
+                    }
+                    if (r2 < a.rc2) {
+                        const float ir2 = __frcp_rn(r2);
+                        const float sr2 = a.sig2 * ir2;
+                        const float sr6 = sr2 * sr2 * sr2;
+                        const float fr = a.eps24 * (2.f * sr6 * sr6 - sr6) * ir2;
+                        fx += fr * dx;
+                        fy += fr * dy;
+                        fz += fr * dz;
+                    }
+                }
+            }
+            // sum the source slices of each target in slice order
+            red[tid][0] = fx;
+            red[tid][1] = fy;
+            red[tid][2] = fz;
+            red[tid][3] = gx;
+            red[tid][4] = gy;
+            red[tid][5] = gz;
+            red[tid][6] = sv;
+            __syncthreads();
+            cf tsv{0.f, 0.f}, tq{0.f, 0.f};
+            if (sl == 0 && act) {
+                float acc[7];
+                for (int k = 0; k < 7; ++k) acc[k] = red[ti][k];
+                for (int g = 1; g < Gs; ++g)
+                    for (int k = 0; k < 7; ++k) acc[k] += red[g * T + ti][k];
+                const float4 p = wpos[i];
+                a.f[o + i] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                if (a.cv_coord >= 0) {
+                    const float jf = (float)(2.0 * a.coord_scw[w]);  // A = B: both orderings of each pair
+                    a.J[(size_t)a.cv_coord * a.N + o + i] = make_float4(jf * acc[3], jf * acc[4], jf * acc[5], 0.f);
+                    tsv = cf{acc[6], 0.f};
+                }
+                if (a.cv_rg >= 0) {
+                    const float ux = p.x - cshare[0], uy = p.y - cshare[1], uz = p.z - cshare[2];
+                    tq = cf{ux * ux + uy * uy + uz * uz, 0.f};
+                }
+            }
+            // task partials (fixed order), then the walker's last task finishes its CVs
+            for (int off = 16; off > 0; off >>= 1) {
+                tsv = cf_add(tsv, cf_shfl_xor(tsv, off));
+                tq = cf_add(tq, cf_shfl_xor(tq, off));
+            }
+            __shared__ cf tw[WK_T / 32][2];
+            __shared__ int last;
+            if (tid % 32 == 0) {
+                tw[tid / 32][0] = tsv;
+                tw[tid / 32][1] = tq;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                cf s0 = tw[0][0], s1 = tw[0][1];
+                for (int q = 1; q < WK_T / 32; ++q) {
+                    s0 = cf_add(s0, tw[q][0]);
+                    s1 = cf_add(s1, tw[q][1]);
+                }
+                double* slot = a.tpart + 2 * (size_t)(a.tbase[w] + tk.w);
+                slot[0] = cf_val(s0);
+                slot[1] = cf_val(s1);
+                __threadfence();
+                last = atomicAdd(&a.ticket[w], 1u) == (unsigned)a.tcount[w] - 1;
+                if (last) {
+                    __threadfence();
+                    double S = 0.0, Q = 0.0;
+                    const double* base = a.tpart + 2 * (size_t)a.tbase[w];
+                    for (int k = 0; k < a.tcount[w]; ++k) {
+                        S += __ldcg(base + 2 * k);
+                        Q += __ldcg(base + 2 * k + 1);
+                    }
+                    if (a.cv_coord >= 0) a.xi[w * 4 + a.cv_coord] = a.coord_scw[w] * S;
+                    if (a.cv_rg >= 0) {
+                        const double rg = sqrt(Q / n);
+                        double sc = a.rg_scale != 0.0 ? a.rg_scale : 1.0;
+                        if (a.rg_intensive) sc /= cbrt((double)n);
+                        a.xi[w * 4 + a.cv_rg] = sc * rg;
+                        a.rgc[w] = make_float4(cshare[0], cshare[1], cshare[2], (float)(sc / (n * rg)));
+                    }
+                    a.ticket[w] = 0u;
+                }
+            }
+        }
+    }
+    if (!grid_barrier(a.bar, G, a.status)) return;
+
+    // ---- P2a: hills partials for all walker points
+    {
+        const int tiles = (a.W + WK_T - 1) / WK_T;
+        bool fresh = true;
+        for (int task = blockIdx.x; task < tiles * a.hsplit; task += G) {
+            if (!hills_f32_task<D, 1, false, double>(a.hp, a.cnt, a.xi, 4, a.W, a.ctr, a.hprm, a.hpart, a.status,
+                                                     task / a.hsplit, task % a.hsplit, a.hsplit, ring, hbar, fresh))
+                return;
+            fresh = false;
+        }
+        if (!fresh) {
+            __syncthreads();
+            if (tid == 0)
+                for (int s = 0; s < NST; ++s) mbar_inval(&hbar[s]);
+        }
+    }
+    if (!grid_barrier(a.bar, G, a.status)) return;
+
+    // ---- P2b: V and dV/dxi per walker (one warp per point)
+    {
+        const int lane = tid % 32;
+        for (int p = blockIdx.x * (WK_T / 32) + tid / 32; p < a.W; p += G * (WK_T / 32)) {
+            CF4 acc{};
+            for (int s = lane; s < a.hsplit; s += 32) cf4_add(acc, load_cf4(a.hpart + (size_t)s * a.W + p));
+            cf4_lane_sum<32>(acc);
+            if (lane == 0) emit_cf(p, acc, a.hout);
+        }
+    }
+    if (!grid_barrier(a.bar, G, a.status)) return;
+
+    // ---- P3: deposition (CTA 0), bias force and closing kick
+    if (mode == 0 && blockIdx.x == 0)
+        deposit_block<float>(a.dep, a.xi, a.hout.V, a.count, a.step, a.depw, a.ctrw, a.h64, a.h32, a.status);
+    for (long long i = (long long)blockIdx.x * WK_T + tid; i < a.N; i += (long long)G * WK_T) {
+        const int w = a.aw[i];
+        float4 F = a.f[i];
+        if (a.cv_coord >= 0) {
+            const float g = a.hout.dV[w * 4 + a.cv_coord];
+            const float4 j = a.J[(size_t)a.cv_coord * a.N + i];
+            F.x -= g * j.x;
+            F.y -= g * j.y;
+            F.z -= g * j.z;
+        }
+        if (a.cv_rg >= 0) {
+            const float g = a.hout.dV[w * 4 + a.cv_rg];
+            const float4 c = a.rgc[w];
+            const float4 p = a.x[i];
+            F.x -= g * c.w * (p.x - c.x);
+            F.y -= g * c.w * (p.y - c.y);
+            F.z -= g * c.w * (p.z - c.z);
+        }
+        a.f[i] = F;
+        if (mode == 0) {
+            float4 v = a.v[i];
+            v.x += a.half * a.inv_m * F.x;
+            v.y += a.half * a.inv_m * F.y;
+            v.z += a.half * a.inv_m * F.z;
+            a.v[i] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t wk_smem_bytes(const wtmd_t* h)
+{
+    return sizeof(float4) * NST * 2 * CHUNK + 128 + sizeof(float4) * (size_t)h->max_wn;
+}
+
+static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
+{
+    WalkerPlan& k = h->wk;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t sm = wk_smem_bytes(h);
+    auto fn = h->d == 1 ? (const void*)walkers_step_kernel<1> : (const void*)walkers_step_kernel<2>;
+    WTMD_CUDA_TRY(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int occ = 0;
+    WTMD_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, WK_T, sm));
+    if (occ < 1) {
+        h->err = "persistent walker kernel does not fit on an SM";
+        return WTMD_EINVAL;
+    }
+    bps = std::max(1, std::min(bps, occ));
+    // tasks, sorted by cost
+    std::vector<int4> tasks;
+    std::vector<int> tbase(h->W), tcount(h->W);
+    int slot = 0;
+    for (int w = 0; w < h->W; ++w) {
+        const int n = (int)h->wn_h[w];
+        tbase[w] = slot;
+        tcount[w] = (n + T - 1) / T;
+        for (int q = 0; q < tcount[w]; ++q) tasks.push_back(make_int4(w, q * T, std::min(n, (q + 1) * T), q));
+        slot += tcount[w];
+    }
+    std::stable_sort(tasks.begin(), tasks.end(), [&](const int4& x, const int4& y) {
+        return (long long)(x.z - x.y) * h->wn_h[x.x] > (long long)(y.z - y.y) * h->wn_h[y.x];
+    });
+    cudaFree(k.tasks);
+    cudaFree(k.tbase);
+    cudaFree(k.tcount);
+    cudaFree(k.tpart);
+    k.tasks = nullptr;
+    k.tbase = k.tcount = nullptr;
+    k.tpart = nullptr;
+    WTMD_CUDA_TRY(h, cudaMalloc(&k.tasks, sizeof(int4) * tasks.size()));
+    WTMD_CUDA_TRY(h, cudaMalloc(&k.tbase, sizeof(int) * h->W));
+    WTMD_CUDA_TRY(h, cudaMalloc(&k.tcount, sizeof(int) * h->W));
+    WTMD_CUDA_TRY(h, cudaMalloc(&k.tpart, sizeof(double) * 2 * slot));
+    WTMD_CUDA_TRY(h, cudaMemcpy(k.tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemcpy(k.tbase, tbase.data(), sizeof(int) * h->W, cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemcpy(k.tcount, tcount.data(), sizeof(int) * h->W, cudaMemcpyHostToDevice));
+    if (!k.ticket) {
+        WTMD_CUDA_TRY(h, cudaMalloc(&k.ticket, sizeof(unsigned) * h->W));
+        WTMD_CUDA_TRY(h, cudaMemset(k.ticket, 0, sizeof(unsigned) * h->W));
+        WTMD_CUDA_TRY(h, cudaMalloc(&k.rgc, sizeof(float4) * h->W));
+        WTMD_CUDA_TRY(h, cudaMalloc(&k.bar, sizeof(unsigned) * 2));
+        WTMD_CUDA_TRY(h, cudaMemset(k.bar, 0, sizeof(unsigned) * 2));
+    }
+    k.T = T;
+    k.bps = bps;
+    k.grid = bps * sms;
+    k.ntasks = (int)tasks.size();
+    k.hsplit = std::max(1, std::min(hsplit_mult * k.grid, (int)((h->cap_pairs + CHUNK - 1) / CHUNK)));
+    const size_t need = (size_t)k.hsplit * h->W * sizeof(dbl4);
+    if (need > h->partial_bytes) {
+        cudaFree(h->partial);
+        h->partial = nullptr;
+        h->partial_bytes = 0;
+        WTMD_CUDA_TRY(h, cudaMalloc(&h->partial, need));
+        h->partial_bytes = need;
+    }
+    k.smem = wk_smem_bytes(h);
+    return WTMD_OK;
+}
+
+int walkers_enable(wtmd_t* h)
+{
+    if (h->prec != WTMD_F32 || h->cfg.engine != WTMD_ENGINE_LJ) {
+        h->err = "persistent walkers need an FP32 handle with the LJ engine";
+        return WTMD_EINVAL;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (h->cfg.box[k] > 0.0) {
+            h->err = "persistent walkers run open (non-periodic) clusters";
+            return WTMD_EINVAL;
+        }
+    if (h->ncv != h->d || h->d > 2) {
+        h->err = "persistent walkers need 1 or 2 CVs, all defined";
+        return WTMD_EINVAL;
+    }
+    int nco = 0, nrg = 0;
+    for (int c = 0; c < h->d; ++c) {
+        const CvDev& cv = h->cv[c];
+        const bool co = cv.kind == WTMD_CV_COORDINATION && cv.n_a < 0 && cv.n_b < 0;
+        const bool rg = cv.kind == WTMD_CV_RG && cv.n_a < 0;
+        if (!(co || rg) || cv.period > 0.0) {
+            h->err = "persistent walkers support coordination (all atoms) and Rg (all atoms)";
+            return WTMD_EINVAL;
+        }
+        nco += co;
+        nrg += rg;
+    }
+    if (nco > 1 || nrg > 1) {
+        h->err = "at most one coordination and one Rg CV";
+        return WTMD_EINVAL;
+    }
+    if (h->max_wn > 8192) {
+        h->err = "walkers above 8192 atoms do not fit the staged-positions design";
+        return WTMD_EINVAL;
+    }
+    const int T = h->wk.T ? h->wk.T : 128, bps = h->wk.bps ? h->wk.bps : 2, hm = h->wk.hsplit_mult ? h->wk.hsplit_mult : 1;
+    h->wk.hsplit_mult = hm;
+    const int rc = wk_build(h, T, bps, hm);
+    if (rc) return rc;
+    h->persistent = true;
+    return WTMD_OK;
+}
+
+int launch_walkers_step(wtmd_t* h, int mode)
+{
+    const WalkerPlan& k = h->wk;
+    WkArgs a{};
+    a.W = h->W;
+    a.N = h->N;
+    a.woff = h->woff;
+    a.wn = h->wn;
+    a.aw = h->atom_walker;
+    a.tasks = k.tasks;
+    a.ntasks = k.ntasks;
+    a.T = k.T;
+    a.tbase = k.tbase;
+    a.tcount = k.tcount;
+    a.tpart = k.tpart;
+    a.ticket = k.ticket;
+    a.rgc = k.rgc;
+    a.x = (float4*)h->pos;
+    a.v = (float4*)h->vel;
+    a.f = (float4*)h->force;
+    const wtmd_config& c = h->cfg;
+    a.rc2 = (float)(c.lj_rc * c.lj_rc);
+    a.sig2 = (float)(c.lj_sigma * c.lj_sigma);
+    a.eps24 = (float)(24.0 * c.lj_eps);
+    const double c1 = exp(-c.friction * c.dt);
+    a.half = (float)(0.5 * c.dt);
+    a.inv_m = (float)(1.0 / c.mass);
+    a.c1 = (float)c1;
+    a.c2 = (float)sqrt((1.0 - c1 * c1) * c.kT / c.mass);
+    a.seed = c.seed;
+    a.step = h->step;
+    a.d = h->d;
+    a.cv_coord = a.cv_rg = -1;
+    for (int q = 0; q < h->d; ++q) {
+        const CvDev& cv = h->cv[q];
+        if (cv.kind == WTMD_CV_COORDINATION) {
+            a.cv_coord = q;
+            a.inv_r0sq = (float)(1.0 / (cv.r0 * cv.r0));
+            a.gpref = (float)(-(double)cv.nn / (cv.r0 * cv.r0));
+            a.hpow = cv.nn / 2;
+            a.coord_scw = cv.scw;
+        } else {
+            a.cv_rg = q;
+            a.rg_scale = cv.scale;
+            a.rg_intensive = cv.flags & WTMD_CV_INTENSIVE;
+        }
+    }
+    a.J = (float4*)h->J;
+    a.xi = h->xi;
+    a.hp = h->hills32;
+    a.cnt = h->count;
+    a.ctr = h->ctr;
+    for (int q = 0; q < 3; ++q) {
+        a.hprm.a[q] = h->a[q];
+        a.hprm.per[q] = 0.f;
+        a.hprm.iper[q] = 0.f;
+    }
+    a.hpart = (dbl4*)h->partial;
+    a.hsplit = k.hsplit;
+    a.hout.V = (float*)h->V;
+    a.hout.dV = (float*)h->dV;
+    a.hout.dvs = 4;
+    a.hout.D = h->d;
+    for (int q = 0; q < 3; ++q) a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
+    a.hout.ticket = nullptr;
+    a.hout.status = h->status;
+    a.dep.stride = c.stride;
+    a.dep.cap = h->cap;
+    a.dep.W = h->W;
+    a.dep.d = h->d;
+    a.dep.w0 = c.w0;
+    a.dep.inv_dT = (c.gamma == 0.0 || isinf(c.gamma)) ? 0.0 : 1.0 / (c.kT * (c.gamma - 1.0));
+    for (int q = 0; q < 3; ++q) a.dep.a[q] = h->a[q];
+    a.count = h->count;
+    a.depw = h->dep;
+    a.ctrw = h->ctr;
+    a.h64 = (dbl4*)h->hills64;
+    a.h32 = (float*)h->hills32;
+    a.bar = k.bar;
+    a.status = h->status;
+    a.max_wn = h->max_wn;
+    // a timed-out barrier would leave its counter dirty: start every launch clean
+    WTMD_CUDA_TRY(h, cudaMemsetAsync(k.bar, 0, sizeof(unsigned), h->stream));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(k.grid);
+    cfg.blockDim = dim3(WK_T);
+    cfg.dynamicSmemBytes = k.smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = h->d == 1 ? cudaLaunchKernelEx(&cfg, walkers_step_kernel<1>, a, mode)
+                              : cudaLaunchKernelEx(&cfg, walkers_step_kernel<2>, a, mode);
+    if (e != cudaSuccess) {
+        h->err = std::string("persistent walker launch: ") + cudaGetErrorString(e);
+        return WTMD_ECUDA;
+    }
+    mark(h, "walkers_step");
+    if (mode == 0 && h->grid) return launch_grid_update(h);
+    return WTMD_OK;
+}
+
+int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult)
+{
+    h->wk.hsplit_mult = hsplit_mult;
+    return wk_build(h, T, bps, hsplit_mult);
+}
+
+}  // namespace wtmd

@@ -101,6 +101,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_mbar_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -215,6 +219,22 @@ struct Tuned {
     int split = 0;    // hill splits
 };
 
+// Plan of the persistent multi-walker step (walkers.cu).
+struct WalkerPlan {
+    int T = 0;             // targets per pair task
+    int bps = 0;           // CTAs per SM
+    int hsplit_mult = 0;   // hill splits per CTA
+    int grid = 0, ntasks = 0, hsplit = 0;
+    size_t smem = 0;
+    int4* tasks = nullptr;
+    int* tbase = nullptr;
+    int* tcount = nullptr;
+    double* tpart = nullptr;
+    unsigned* ticket = nullptr;
+    float4* rgc = nullptr;
+    unsigned* bar = nullptr;
+};
+
 }  // namespace wtmd
 
 struct wtmd_t {
@@ -279,6 +299,9 @@ struct wtmd_t {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     cudaGraphExec_t graph1 = nullptr;
+    bool persistent = false;        // multi-walker step as one persistent launch
+    wtmd::WalkerPlan wk;
+    bool no_graph = false;          // capture failed: replay eagerly
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
     // profiling: when `prof` is set, mark() records a CUDA event on the
@@ -312,6 +335,10 @@ namespace wtmd {
 int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all CVs
 int launch_cv(wtmd_t* h, const void* pos, int c);               // xi, J of CV c
 int launch_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos);  // J^T grad_xi
+int launch_grid_update(wtmd_t* h);                              // FP64 grid += this step's new hills
+int walkers_enable(wtmd_t* h);
+int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult);
+int launch_walkers_step(wtmd_t* h, int mode);                   // 0: full step, 1: forces only
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
