@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
+    ap.add_argument("--no-walkers", action="store_true")
     return ap.parse_args()
 
 
@@ -72,6 +73,94 @@ def hills_around(xi0, seed):
 
     sig = np.asarray(SIGMA)
     return synth.walk_hills(H_PRE, xi0 - 3 * sig, xi0 + 3 * sig, 0.5 * sig, seed=seed)
+
+
+# batched walkers: 256 LJ clusters of log-uniform size 38..2048 atoms at
+# T* = 0.3, CVs (mean coordination over all atoms, Rg / n^(1/3)), a shared
+# list of 2e5 hills, FP32 with an FP64 bias grid
+W_CL, CL_LO, CL_HI, H_CL = 256, 38, 2048, 200000
+CL_SIGMA = (0.2, 0.01)
+CL_WORKLOAD = ("256 LJ clusters, sizes log-uniform 38-2048 atoms, rho*=0.9 FCC-site start, T*=0.3, dt=0.005; "
+               "CVs: mean coordination (all atoms, r0=1.5, n=6, m=12), Rg/n^(1/3); shared list of 2e5 hills "
+               "(random walk over the walkers' CV range), sigma=(0.2,0.01), gamma=8, stride 100; FP32 with "
+               "FP64 256x256 bias grid")
+
+
+def cluster_handle(wt, sizes, grid=None, capacity=H_CL + 16384):
+    m = wt.Wtmd(precision="f32", sigma=CL_SIGMA, w0=0.3, gamma=8.0, kT=0.3, stride=100, capacity=capacity,
+                seed=0, grid=grid, engine="lj", walker_sizes=[int(n) for n in sizes], dt=0.005, friction=1.0)
+    m.cv_define(wt.CV_COORDINATION, r0=1.5, nn=6, mm=12)
+    m.cv_define(wt.CV_RG, flags=wt.CV_INTENSIVE)
+    return m
+
+
+def cluster_inputs(wt, torch):
+    """Sizes, positions, velocities, hills and grid of the cluster workload."""
+    import synth
+
+    sizes, x = synth.lj_clusters(W_CL, CL_LO, CL_HI, 0.9, seed=0)
+    v = synth.velocities(x.shape[0], 0.3, 1.0, seed=7)
+    m0 = cluster_handle(wt, sizes, capacity=16)
+    _, xi, _ = m0.bias_eval(wt.particles(x, torch.float32))
+    xi = xi.double().cpu().numpy()
+    m0.close()
+    sig = np.asarray(CL_SIGMA)
+    lo, hi = xi.min(0) - 3 * sig, xi.max(0) + 3 * sig
+    hills = synth.walk_hills(H_CL, lo, hi, 0.5 * sig, seed=8, w_range=(0.01, 0.3))
+    grid = ((256, 256), tuple(lo - 10 * sig), tuple(hi + 10 * sig))
+    return sizes, x, v, hills, grid
+
+
+def walkers_bench(wt, torch, dev, flush, steps):
+    """The cluster workload three ways: the per-kernel step (CUDA graph of
+    ~13 launches), the persistent step with the default plan, and the
+    persistent step with the autotuned plan."""
+    sizes, x, v, hills, grid = cluster_inputs(wt, torch)
+    N = int(sizes.sum())
+    stream = torch.cuda.current_stream()
+    out = {"workload": CL_WORKLOAD, "walkers": W_CL, "atoms": N, "hills": H_CL,
+           "pair_terms_per_step": int((sizes.astype(np.int64) ** 2).sum())}
+
+    def timed(m, K, flushed):
+        m.step_n(5, check=True)
+        torch.cuda.synchronize()
+        if flushed:
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            for i, (a, b) in enumerate(evs):
+                flush.fill_(float(i))
+                a.record(stream)
+                m.step_n(1, check=False)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = float(sum(a.elapsed_time(b) for a, b in evs))
+        else:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.step_n(K, check=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+        m.check()
+        return K / (ms * 1e-3)
+
+    for mode in ("per_kernel", "persistent_default", "persistent_tuned"):
+        m = cluster_handle(wt, sizes, grid=grid)
+        m.hills_load(hills)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        r = {}
+        if mode != "per_kernel":
+            m.walkers_persistent(True)
+        if mode == "persistent_tuned":
+            r["plan"] = dict(zip(("targets_per_task", "ctas_per_sm", "hill_split_factor"), m.autotune(steps=3)))
+        sps = timed(m, steps, flushed=False)
+        r.update(steps_per_s=sps, atom_steps_per_s=sps * N, bias_force_evals_per_s=sps * W_CL,
+                 hill_evals_per_s=sps * W_CL * m.counters()[1])
+        r["steps_per_s_l2_flushed"] = timed(m, max(steps // 4, 10), flushed=True)
+        out[mode] = r
+        m.close()
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -273,7 +362,8 @@ def run_ours(args, rank, world):
     bytes_step = 3 * N_ATOMS * 16
 
     micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
-    return dict(dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
+    return dict(walkers=walkers, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
 
@@ -387,6 +477,7 @@ def main():
         "wall_s": r["wall"],
         "kernels_ms": {k: round(v, 5) for k, v in prof},
         "hills_sum_1e6": r["micro"],
+        "walkers_256_clusters": r["walkers"],
     }
     if not args.no_cpu_baseline and world == 1:
         n, times, cores = cpu_baseline_oracle(seconds=15.0)

@@ -175,3 +175,11 @@ def fcc_cluster(n: int, rho: float, seed: int):
 def velocities(n: int, kT: float, mass: float, seed: int) -> np.ndarray:
     """Maxwell-Boltzmann velocities (std sqrt(kT/m)) from `seed`."""
     return rng(seed).normal(scale=np.sqrt(kT / mass), size=(n, 3))
+
+
+def lj_clusters(W: int, lo: int, hi: int, rho: float, seed: int):
+    """W compact LJ clusters (fcc_cluster) of log-uniform sizes in [lo, hi],
+    concatenated walker after walker; returns (sizes, positions [sum n, 3])."""
+    sizes = log_uniform_sizes(W, lo, hi, seed)
+    x = np.concatenate([fcc_cluster(int(n), rho, seed=1000 * (seed + 1) + w) for w, n in enumerate(sizes)])
+    return sizes, x

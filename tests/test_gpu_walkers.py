@@ -181,3 +181,55 @@ def test_persistent_rejects_unsupported_handles():
     m = gpu_handle(spec, "f32")
     with pytest.raises(wt.WtmdError):
         m.autotune()
+
+
+def test_full_size_cluster_workload_sampled_against_oracle():
+    """The 256-cluster workload at full size (sizes 38..2048 atoms, 2e5
+    shared hills, FP64 grid) in the benchmark's launch configuration
+    (persistent step, autotuned plan), one step with a deposit: for sampled
+    walkers (smallest, largest and four seeded others) the deposited CVs, the
+    well-tempered heights and the total forces agree with the FP64 oracle
+    evaluated at the GPU's own positions."""
+    import oracle as o
+    from test_gpu_parity import force_scale
+
+    wt = _wt()
+    sizes, x = synth.lj_clusters(256, 38, 2048, 0.9, seed=0)
+    sizes = [int(n) for n in sizes]
+    v = synth.velocities(x.shape[0], 0.3, 1.0, seed=7)
+    sig = np.array([0.2, 0.01])
+    spec = dict(engine="lj", walker_sizes=sizes, box=(0, 0, 0), dt=0.005, kT=0.3, friction=1.0, sigma=tuple(sig),
+                gamma=8.0, w0=0.3, stride=1, capacity=200000 + 4096, seed=0,
+                cvs=[dict(kind="coordination", r0=1.5, nn=6, mm=12), dict(kind="rg", flags=wt.CV_INTENSIVE)])
+    m0 = gpu_handle(dict(spec, capacity=16), "f32")
+    _, xi0, _ = m0.bias_eval(wt.particles(x, torch.float32))
+    xi0 = to_np(xi0)
+    lo, hi = xi0.min(0) - 3 * sig, xi0.max(0) + 3 * sig
+    hills = synth.walk_hills(200000, lo, hi, 0.5 * sig, seed=8, w_range=(0.01, 0.3))
+    grid = ((256, 256), tuple(lo - 10 * sig), tuple(hi + 10 * sig))
+    m, pos, vel, F = _setup(dict(spec, grid=grid), x, v, hills, True)
+    m.autotune(steps=2)
+    m.step_n(1)
+    torch.cuda.synchronize()
+    X, Fg = to_np(pos)[:, :3], to_np(F)[:, :3]
+    h = m.hills_read()
+    assert h.shape[0] == 200000 + 256
+    dep = h[200000:]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    r = np.random.default_rng(3)
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), *r.choice(256, 4, replace=False).tolist()})
+    inv_dT = 1.0 / (0.3 * 7.0)
+    for w in sample:
+        n = sizes[w]
+        xw = X[off[w]: off[w + 1]]
+        sub = dict(spec, walker_sizes=[n])
+        sim = o.Sim(oracle_system(sub), x=xw, hills=hills)
+        Fr = sim.forces()
+        _, xi_r, _, _ = sim.bias(xw)
+        assert np.all(np.abs(dep[w, :2] - xi_r[0, :2]) <= 1e-5 * np.abs(xi_r[0, :2])), (w, dep[w], xi_r[0])
+        Vr, _ = o.hills_sum(dep[w, :2][None, :], hills, tuple(sig))
+        h_r = 0.3 * np.exp(-Vr[0] * inv_dT)
+        assert abs(dep[w, 3] - h_r) <= h_r * 2e-5 * Vr[0] * inv_dT + 1e-12, (w, dep[w, 3], h_r)
+        Fs = force_scale(sim, xw, hills, [0.0, 0.0])
+        dF = np.linalg.norm(Fg[off[w]: off[w + 1]] - Fr)
+        assert dF <= 1e-5 * (np.linalg.norm(Fr) + np.linalg.norm(Fs)), (w, n, dF / np.linalg.norm(Fr))
