@@ -6,10 +6,12 @@
 // cooperative kernel does a whole step for all walkers, with bounded grid
 // barriers between the phases:
 //   P0  first half of BAOAB for every atom;
-//   P1  (walker, target tile) tasks, sorted by cost: the walker's positions
-//       are staged in shared memory and one all-pairs loop gives the LJ force,
-//       the coordination row sum and its gradient (A = B = all atoms) and the
-//       Rg moment of each target; the walker's last task finishes its CVs;
+//   P1  (walker, target tile) tasks, handed out by an atomic queue in order
+//       of decreasing cost: the walker's positions are staged in shared
+//       memory and one all-pairs loop gives the LJ force, the coordination
+//       row sum and its gradient (A = B = all atoms) of each target, plus the
+//       targets' first and second moments for Rg; the walker's last task
+//       finishes its CVs;
 //   P2a hills sum for all walker points over the shared hill list (the FP32
 //       bulk-copy ring task of hills.cu), one partial per hill split;
 //   P2b fixed-order reduction of the splits -> V, dV/dxi per walker;
@@ -52,7 +54,7 @@ struct WkArgs {
     uint64_t seed;
     long long* step;
     int d, cv_coord, cv_rg;
-    float inv_r0sq, gpref;
+    float inv_r0sq;
     int hpow;
     const double* coord_scw;  // [W]
     double rg_scale;
@@ -113,8 +115,64 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status)
     return ok != 0;
 }
 
-template <int D>
-__global__ void __launch_bounds__(WK_T) walkers_step_kernel(WkArgs a, int mode)
+// Targets per pair task of an n-atom walker: the plan's T, or for a smaller
+// walker the least power of two >= n (>= 32), so that its threads split the
+// sources instead of idling.
+__host__ __device__ inline int wk_targets(int n, int T)
+{
+    int t = 32;
+    while (t < n && t < T) t <<= 1;
+    return t;
+}
+
+struct PairAcc {
+    float fx, fy, fz, gx, gy, gz, sv;
+};
+
+// LJ force and coordination terms of target p against sources [j0, j1).
+// One approximate reciprocal of r^2 serves both: with y = r^2/r0^2 and
+// s = 1/(1 + y^h), ds/dx = -n y^h s^2 dx / r^2 (n = 2h).  H > 0 fixes the
+// exponent h at compile time, H = 0 reads it from the arguments.
+template <int H>
+__device__ __forceinline__ void pair_range(const float4* __restrict__ wpos, float4 p, int j0, int j1,
+                                           const WkArgs& a, PairAcc& c)
+{
+    const bool co = a.cv_coord >= 0;
+    const float nneg = -2.f * (float)a.hpow;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const float4 s = wpos[j];
+        const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float ir2 = rcp_approx(r2);
+        if (co) {
+            const float y = r2 * a.inv_r0sq;
+            float yh = y;
+            if constexpr (H > 0) {
+#pragma unroll
+                for (int k = 1; k < H; ++k) yh *= y;
+            } else {
+                for (int k = 1; k < a.hpow; ++k) yh *= y;
+            }
+            const float sw = rcp_approx(1.f + yh);
+            c.sv += sw;
+            const float gr = nneg * yh * sw * sw * ir2;
+            c.gx = fmaf(gr, dx, c.gx);
+            c.gy = fmaf(gr, dy, c.gy);
+            c.gz = fmaf(gr, dz, c.gz);
+        }
+        const float sr2 = a.sig2 * ir2;
+        const float sr6 = sr2 * sr2 * sr2;
+        float fr = a.eps24 * fmaf(2.f * sr6, sr6, -sr6) * ir2;
+        fr = r2 < a.rc2 ? fr : 0.f;
+        c.fx = fmaf(fr, dx, c.fx);
+        c.fy = fmaf(fr, dy, c.fy);
+        c.fz = fmaf(fr, dz, c.fz);
+    }
+}
+
+template <int D, int H>
+__global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mode)
 {
     extern __shared__ __align__(128) unsigned char wk_smem[];
     float4 (*ring)[2 * CHUNK] = reinterpret_cast<float4 (*)[2 * CHUNK]>(wk_smem);
@@ -131,141 +189,102 @@ __global__ void __launch_bounds__(WK_T) walkers_step_kernel(WkArgs a, int mode)
         if (!grid_barrier(a.bar, G, a.status)) return;
     }
 
-    // ---- P1: pair tasks
+    // ---- P1: pair tasks, taken from a queue in decreasing cost (greedy
+    // balance); the walker's last task finishes its CVs
     {
         __shared__ float red[WK_T][7];
-        __shared__ float cshare[3];
-        const int T = a.T, Gs = WK_T / a.T;
-        const int ti = tid % T, sl = tid / T;
-        for (int task = blockIdx.x; task < a.ntasks; task += G) {
+        __shared__ cf tw[WK_T / 32][5];
+        __shared__ int next, last;
+        for (;;) {
+            __syncthreads();  // the previous task is done with wpos, red, tw
+            if (tid == 0) next = (int)atomicAdd(a.bar + 2, 1u);
+            __syncthreads();
+            const int task = next;
+            if (task >= a.ntasks) break;
             const int4 tk = a.tasks[task];
             const int w = tk.x, t0 = tk.y, t1 = tk.z;
             const int n = a.wn[w];
             const long long o = a.woff[w];
-            __syncthreads();
+            const int T = wk_targets(n, a.T), Gs = WK_T / T;
+            const int ti = tid % T, sl = tid / T;
             for (int q = tid; q < n; q += WK_T) wpos[q] = a.x[o + q];
             __syncthreads();
-            // centre of the walker (Rg), identical in every task of the walker
-            if (a.cv_rg >= 0) {
-                cf s3[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                for (int q = tid; q < n; q += WK_T) {
-                    s3[0] = cf_add(s3[0], wpos[q].x);
-                    s3[1] = cf_add(s3[1], wpos[q].y);
-                    s3[2] = cf_add(s3[2], wpos[q].z);
-                }
-                for (int k = 0; k < 3; ++k)
-                    for (int off = 16; off > 0; off >>= 1) s3[k] = cf_add(s3[k], cf_shfl_xor(s3[k], off));
-                __shared__ cf cw[WK_T / 32][3];
-                if (tid % 32 == 0)
-                    for (int k = 0; k < 3; ++k) cw[tid / 32][k] = s3[k];
-                __syncthreads();
-                if (tid == 0)
-                    for (int k = 0; k < 3; ++k) {
-                        cf t = cw[0][k];
-                        for (int q = 1; q < WK_T / 32; ++q) t = cf_add(t, cw[q][k]);
-                        cshare[k] = (float)(cf_val(t) / n);
-                    }
-                __syncthreads();
-            }
             const int i = t0 + ti;
             const bool act = i < t1;
-            float fx = 0.f, fy = 0.f, fz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, sv = 0.f;
+            PairAcc acc{};
             if (act) {
                 const float4 p = wpos[i];
                 const int j0 = (int)((long long)n * sl / Gs), j1 = (int)((long long)n * (sl + 1) / Gs);
-#pragma unroll 4
-                for (int j = j0; j < j1; ++j) {
-                    const float4 s = wpos[j];
-                    const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (j == i) continue;
-                    if (a.cv_coord >= 0) {
-                        const float y = r2 * a.inv_r0sq;
-                        float yh1 = y;
-                        for (int k = 2; k < a.hpow; ++k) yh1 *= y;
-                        const float sw = __frcp_rn(1.f + yh1 * y);
-                        sv += sw;
-                        const float gr = a.gpref * yh1 * sw * sw;
-                        gx += gr * dx;
-                        gy += gr * dy;
-                        gz += gr * dz;
-                    }
-                    if (r2 < a.rc2) {
-                        const float ir2 = __frcp_rn(r2);
-                        const float sr2 = a.sig2 * ir2;
-                        const float sr6 = sr2 * sr2 * sr2;
-                        const float fr = a.eps24 * (2.f * sr6 * sr6 - sr6) * ir2;
-                        fx += fr * dx;
-                        fy += fr * dy;
-                        fz += fr * dz;
-                    }
-                }
+                // the self pair is left out by splitting the source range at i
+                const int m0 = i >= j0 && i < j1 ? i : j1;
+                const int m1 = i >= j0 && i < j1 ? i + 1 : j1;
+                pair_range<H>(wpos, p, j0, m0, a, acc);
+                pair_range<H>(wpos, p, m1, j1, a, acc);
             }
             // sum the source slices of each target in slice order
-            red[tid][0] = fx;
-            red[tid][1] = fy;
-            red[tid][2] = fz;
-            red[tid][3] = gx;
-            red[tid][4] = gy;
-            red[tid][5] = gz;
-            red[tid][6] = sv;
+            red[tid][0] = acc.fx;
+            red[tid][1] = acc.fy;
+            red[tid][2] = acc.fz;
+            red[tid][3] = acc.gx;
+            red[tid][4] = acc.gy;
+            red[tid][5] = acc.gz;
+            red[tid][6] = acc.sv;
             __syncthreads();
-            cf tsv{0.f, 0.f}, tq{0.f, 0.f};
+            // task moments: coordination row sum, and for Rg the sums of
+            // u = x - x_0 and |u|^2 (x_0 = the walker's first atom, which
+            // keeps the shifted second moment well conditioned)
+            cf mom[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
             if (sl == 0 && act) {
-                float acc[7];
-                for (int k = 0; k < 7; ++k) acc[k] = red[ti][k];
+                float v[7];
+                for (int k = 0; k < 7; ++k) v[k] = red[ti][k];
                 for (int g = 1; g < Gs; ++g)
-                    for (int k = 0; k < 7; ++k) acc[k] += red[g * T + ti][k];
-                const float4 p = wpos[i];
-                a.f[o + i] = make_float4(acc[0], acc[1], acc[2], 0.f);
+                    for (int k = 0; k < 7; ++k) v[k] += red[g * T + ti][k];
+                a.f[o + i] = make_float4(v[0], v[1], v[2], 0.f);
                 if (a.cv_coord >= 0) {
                     const float jf = (float)(2.0 * a.coord_scw[w]);  // A = B: both orderings of each pair
-                    a.J[(size_t)a.cv_coord * a.N + o + i] = make_float4(jf * acc[3], jf * acc[4], jf * acc[5], 0.f);
-                    tsv = cf{acc[6], 0.f};
+                    a.J[(size_t)a.cv_coord * a.N + o + i] = make_float4(jf * v[3], jf * v[4], jf * v[5], 0.f);
+                    mom[0] = cf{v[6], 0.f};
                 }
                 if (a.cv_rg >= 0) {
-                    const float ux = p.x - cshare[0], uy = p.y - cshare[1], uz = p.z - cshare[2];
-                    tq = cf{ux * ux + uy * uy + uz * uz, 0.f};
+                    const float4 p = wpos[i], p0 = wpos[0];
+                    const float ux = p.x - p0.x, uy = p.y - p0.y, uz = p.z - p0.z;
+                    mom[1] = cf{ux, 0.f};
+                    mom[2] = cf{uy, 0.f};
+                    mom[3] = cf{uz, 0.f};
+                    mom[4] = cf{fmaf(ux, ux, fmaf(uy, uy, uz * uz)), 0.f};
                 }
             }
-            // task partials (fixed order), then the walker's last task finishes its CVs
-            for (int off = 16; off > 0; off >>= 1) {
-                tsv = cf_add(tsv, cf_shfl_xor(tsv, off));
-                tq = cf_add(tq, cf_shfl_xor(tq, off));
-            }
-            __shared__ cf tw[WK_T / 32][2];
-            __shared__ int last;
-            if (tid % 32 == 0) {
-                tw[tid / 32][0] = tsv;
-                tw[tid / 32][1] = tq;
-            }
+            for (int k = 0; k < 5; ++k)
+                for (int off = 16; off > 0; off >>= 1) mom[k] = cf_add(mom[k], cf_shfl_xor(mom[k], off));
+            if (tid % 32 == 0)
+                for (int k = 0; k < 5; ++k) tw[tid / 32][k] = mom[k];
             __syncthreads();
             if (tid == 0) {
-                cf s0 = tw[0][0], s1 = tw[0][1];
-                for (int q = 1; q < WK_T / 32; ++q) {
-                    s0 = cf_add(s0, tw[q][0]);
-                    s1 = cf_add(s1, tw[q][1]);
+                double* slot = a.tpart + 5 * (size_t)(a.tbase[w] + tk.w);
+                for (int k = 0; k < 5; ++k) {
+                    cf t = tw[0][k];
+                    for (int q = 1; q < WK_T / 32; ++q) t = cf_add(t, tw[q][k]);
+                    slot[k] = cf_val(t);
                 }
-                double* slot = a.tpart + 2 * (size_t)(a.tbase[w] + tk.w);
-                slot[0] = cf_val(s0);
-                slot[1] = cf_val(s1);
                 __threadfence();
                 last = atomicAdd(&a.ticket[w], 1u) == (unsigned)a.tcount[w] - 1;
                 if (last) {
                     __threadfence();
-                    double S = 0.0, Q = 0.0;
-                    const double* base = a.tpart + 2 * (size_t)a.tbase[w];
-                    for (int k = 0; k < a.tcount[w]; ++k) {
-                        S += __ldcg(base + 2 * k);
-                        Q += __ldcg(base + 2 * k + 1);
-                    }
-                    if (a.cv_coord >= 0) a.xi[w * 4 + a.cv_coord] = a.coord_scw[w] * S;
+                    double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                    const double* base = a.tpart + 5 * (size_t)a.tbase[w];
+                    for (int k = 0; k < a.tcount[w]; ++k)
+                        for (int q = 0; q < 5; ++q) m[q] += __ldcg(base + 5 * k + q);
+                    if (a.cv_coord >= 0) a.xi[w * 4 + a.cv_coord] = a.coord_scw[w] * m[0];
                     if (a.cv_rg >= 0) {
+                        const double cx = m[1] / n, cy = m[2] / n, cz = m[3] / n;
+                        const double Q = fmax(m[4] - n * (cx * cx + cy * cy + cz * cz), 0.0);
                         const double rg = sqrt(Q / n);
                         double sc = a.rg_scale != 0.0 ? a.rg_scale : 1.0;
                         if (a.rg_intensive) sc /= cbrt((double)n);
                         a.xi[w * 4 + a.cv_rg] = sc * rg;
-                        a.rgc[w] = make_float4(cshare[0], cshare[1], cshare[2], (float)(sc / (n * rg)));
+                        const float4 p0 = wpos[0];
+                        a.rgc[w] = make_float4((float)(p0.x + cx), (float)(p0.y + cy), (float)(p0.z + cz),
+                                               (float)(sc / (n * rg)));
                     }
                     a.ticket[w] = 0u;
                 }
@@ -339,6 +358,18 @@ __global__ void __launch_bounds__(WK_T) walkers_step_kernel(WkArgs a, int mode)
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+using WkKernel = void (*)(WkArgs, int);
+
+// n = 6 (h = 3) gets a kernel with the exponent fixed at compile time
+static WkKernel wk_kernel(const wtmd_t* h)
+{
+    int hp = 3;
+    for (int c = 0; c < h->d; ++c)
+        if (h->cv[c].kind == WTMD_CV_COORDINATION) hp = h->cv[c].nn / 2;
+    if (h->d == 1) return hp == 3 ? walkers_step_kernel<1, 3> : walkers_step_kernel<1, 0>;
+    return hp == 3 ? walkers_step_kernel<2, 3> : walkers_step_kernel<2, 0>;
+}
+
 static size_t wk_smem_bytes(const wtmd_t* h)
 {
     return sizeof(float4) * NST * 2 * CHUNK + 128 + sizeof(float4) * (size_t)h->max_wn;
@@ -351,7 +382,7 @@ static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t sm = wk_smem_bytes(h);
-    auto fn = h->d == 1 ? (const void*)walkers_step_kernel<1> : (const void*)walkers_step_kernel<2>;
+    const void* fn = (const void*)wk_kernel(h);
     WTMD_CUDA_TRY(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int occ = 0;
     WTMD_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, WK_T, sm));
@@ -367,8 +398,9 @@ static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
     for (int w = 0; w < h->W; ++w) {
         const int n = (int)h->wn_h[w];
         tbase[w] = slot;
-        tcount[w] = (n + T - 1) / T;
-        for (int q = 0; q < tcount[w]; ++q) tasks.push_back(make_int4(w, q * T, std::min(n, (q + 1) * T), q));
+        const int tw = wk_targets(n, T);
+        tcount[w] = (n + tw - 1) / tw;
+        for (int q = 0; q < tcount[w]; ++q) tasks.push_back(make_int4(w, q * tw, std::min(n, (q + 1) * tw), q));
         slot += tcount[w];
     }
     std::stable_sort(tasks.begin(), tasks.end(), [&](const int4& x, const int4& y) {
@@ -384,7 +416,7 @@ static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
     WTMD_CUDA_TRY(h, cudaMalloc(&k.tasks, sizeof(int4) * tasks.size()));
     WTMD_CUDA_TRY(h, cudaMalloc(&k.tbase, sizeof(int) * h->W));
     WTMD_CUDA_TRY(h, cudaMalloc(&k.tcount, sizeof(int) * h->W));
-    WTMD_CUDA_TRY(h, cudaMalloc(&k.tpart, sizeof(double) * 2 * slot));
+    WTMD_CUDA_TRY(h, cudaMalloc(&k.tpart, sizeof(double) * 5 * slot));
     WTMD_CUDA_TRY(h, cudaMemcpy(k.tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice));
     WTMD_CUDA_TRY(h, cudaMemcpy(k.tbase, tbase.data(), sizeof(int) * h->W, cudaMemcpyHostToDevice));
     WTMD_CUDA_TRY(h, cudaMemcpy(k.tcount, tcount.data(), sizeof(int) * h->W, cudaMemcpyHostToDevice));
@@ -392,8 +424,8 @@ static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
         WTMD_CUDA_TRY(h, cudaMalloc(&k.ticket, sizeof(unsigned) * h->W));
         WTMD_CUDA_TRY(h, cudaMemset(k.ticket, 0, sizeof(unsigned) * h->W));
         WTMD_CUDA_TRY(h, cudaMalloc(&k.rgc, sizeof(float4) * h->W));
-        WTMD_CUDA_TRY(h, cudaMalloc(&k.bar, sizeof(unsigned) * 2));
-        WTMD_CUDA_TRY(h, cudaMemset(k.bar, 0, sizeof(unsigned) * 2));
+        WTMD_CUDA_TRY(h, cudaMalloc(&k.bar, sizeof(unsigned) * 4));  // count, generation, task queue, spare
+        WTMD_CUDA_TRY(h, cudaMemset(k.bar, 0, sizeof(unsigned) * 4));
     }
     k.T = T;
     k.bps = bps;
@@ -493,7 +525,6 @@ int launch_walkers_step(wtmd_t* h, int mode)
         if (cv.kind == WTMD_CV_COORDINATION) {
             a.cv_coord = q;
             a.inv_r0sq = (float)(1.0 / (cv.r0 * cv.r0));
-            a.gpref = (float)(-(double)cv.nn / (cv.r0 * cv.r0));
             a.hpow = cv.nn / 2;
             a.coord_scw = cv.scw;
         } else {
@@ -536,8 +567,9 @@ int launch_walkers_step(wtmd_t* h, int mode)
     a.bar = k.bar;
     a.status = h->status;
     a.max_wn = h->max_wn;
-    // a timed-out barrier would leave its counter dirty: start every launch clean
-    WTMD_CUDA_TRY(h, cudaMemsetAsync(k.bar, 0, sizeof(unsigned), h->stream));
+    // barrier counter, generation and task queue start clean on every launch
+    // (a timed-out barrier would leave its counter dirty)
+    WTMD_CUDA_TRY(h, cudaMemsetAsync(k.bar, 0, sizeof(unsigned) * 4, h->stream));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(k.grid);
     cfg.blockDim = dim3(WK_T);
@@ -548,8 +580,7 @@ int launch_walkers_step(wtmd_t* h, int mode)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = h->d == 1 ? cudaLaunchKernelEx(&cfg, walkers_step_kernel<1>, a, mode)
-                              : cudaLaunchKernelEx(&cfg, walkers_step_kernel<2>, a, mode);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, wk_kernel(h), a, mode);
     if (e != cudaSuccess) {
         h->err = std::string("persistent walker launch: ") + cudaGetErrorString(e);
         return WTMD_ECUDA;

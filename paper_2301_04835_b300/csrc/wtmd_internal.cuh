@@ -181,6 +181,15 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// 1/x from the PTX approximate reciprocal (max error 1 ulp; +-0 -> +-inf,
+// +-inf -> +-0)
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ----------------------------------------------------------------------------
 // device-side CV description
 // ----------------------------------------------------------------------------
