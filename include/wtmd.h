@@ -66,6 +66,11 @@ extern "C" {
 #define WTMD_ENGINE_MB 1    /* Mueller-Brown 2-D potential on (x, y); z frozen */
 #define WTMD_ENGINE_LJ 2    /* 12-6 Lennard-Jones, cut and shifted at lj_rc */
 #define WTMD_ENGINE_CHAIN 3 /* bead chain: harmonic bonds/angles, k(1+cos 3 phi) torsions */
+#define WTMD_ENGINE_WELLS3 5 /* 3-D test landscape per particle: three Gaussian wells, depths
+                              * (8, 6, 7), widths (0.45, 0.40, 0.50), centres (-1,0,0),
+                              * (1,0.2,-0.3), (0.1,1.3,0.6), in a harmonic confinement
+                              * (1.5/2)|r|^2 (a synthetic free-energy surface for CV-space
+                              * runs that generate long hill lists) */
 
 #define WTMD_CV_COMPONENT 1    /* one coordinate of one atom (Sec. 2.2, AxisCV Component) */
 #define WTMD_CV_DIHEDRAL 2     /* IUPAC dihedral of 4 atoms (Sec. 2.2, FourPointCV DihedralAngle) */
@@ -256,6 +261,81 @@ int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice);
 int wtmd_hills_eval_static(int32_t n_cv, const double* sigma, const double* period, const double* hills,
                            int64_t n_hills, const double* xi, int64_t P, double* V_out, double* dV_out,
                            void* stream);
+
+/* ---- MLP surrogate of the hills sum ----------------------------------------
+ * The paper represents biases by neural networks in its ANN and FUNN methods
+ * (Sec. 2.1.6); for metadynamics the hills sum (Sec. 2.1.5) is kept and a
+ * network V_nn stands in for its older part only:
+ *     V(xi) = V_nn(xi) + sum_{k >= K} w_k exp(-sum_i (xi_i - s_ki)^2 / (2 sigma_i^2)),
+ * where V_nn approximates the sum over hills [0, K), K a multiple of 256.
+ * V_nn(xi) = Vs * y((xi - mu) * inv_s) + Vm, y a 3 -> 64 -> 64 -> 1
+ * perceptron with SiLU activations (z * sigmoid(z)); unused inputs (n_cv < 3)
+ * are 0.  Parameters: 4481 FP32 numbers in the order W1 [64][3] (row j =
+ * hidden unit j), b1 [64], W2 [64][64] (row i = output unit i), b2 [64],
+ * w3 [64], b3; the kernels use them rounded to bfloat16 (nearest, ties to
+ * even) with FP32 arithmetic.  Normalisation: norm[8] = mu[3], inv_s[3],
+ * Vm, Vs.  FP32 handles only (else WTMD_EINVAL); not with the persistent
+ * walker step. */
+#define WTMD_MLP_PARAMS 4481
+
+/* Enable (1) or disable (0) the surrogate in step_n and bias_eval.  When on,
+ * the network is fitted at the next step_n (and again every `retrain_every`
+ * new hills; 0 = only when asked by wtmd_surrogate_fit) on samples the run
+ * generates: jittered copies (one sigma) of the most recent hill centres,
+ * labelled by the exact FP32 hills sum over [0, K) (V and dV/dxi).  A tenth
+ * of the samples is held out; the network part is used while the held-out
+ * RMS error of V, after removing the mean offset, is <= tol_kT * kT, else the
+ * exact sum over all hills is used (the fallback).  Synchronizes. */
+int wtmd_surrogate(wtmd_t* h, int32_t enable, double tol_kT, int64_t retrain_every);
+
+/* Training settings of later fits: samples per fit (rounded up to a multiple
+ * of 10, >= 20), Adam iterations, batch size, learning rate (cosine decay to
+ * lr/100 over the iterations of a fit) and the weight lambda of
+ * the gradient term of the Sobolev loss
+ *     L = mean_b (y_b - V_b)^2 + lambda * mean_b |grad_x y_b - G_b|^2
+ * (targets scaled into the network's units). */
+int wtmd_surrogate_config(wtmd_t* h, int64_t n_samples, int64_t iters, int64_t batch, double lr, double lambda);
+
+/* Fit now (synchronous).  stats (host [8], may be NULL): K, held-out RMS
+ * error of V in kT (after offset removal), its maximum in kT, relative RMS
+ * error of dV/dxi, last training loss, 1 if the network part is in use,
+ * number of fits so far, total Adam iterations.  With fewer than 512 hills
+ * nothing is fitted and the exact sum stays in use. */
+int wtmd_surrogate_fit(wtmd_t* h, double* stats);
+
+/* The statistics of the last fit (host [8], as wtmd_surrogate_fit). */
+int wtmd_surrogate_status(wtmd_t* h, double* stats);
+
+/* Use the current network for hills [0, k0) (k0 a multiple of 256, within
+ * capacity) without fitting, active = 1; active = 0 returns to the exact sum.
+ * Turns the surrogate on with refits disabled. */
+int wtmd_surrogate_set(wtmd_t* h, int64_t k0, int32_t active);
+
+/* Load and/or read the network: in (host [4481] FP32, may be NULL) replaces
+ * the master weights and resets the Adam state; norm_in (host [8], may be
+ * NULL; Vs != 0) replaces the normalisation; out / norm_out (host, may be
+ * NULL) receive the current master weights / normalisation.  Synchronizes. */
+int wtmd_mlp_params(wtmd_t* h, const float* in, float* out, const double* norm_in, double* norm_out);
+
+/* The network alone at P points: xi device [P][n_cv] double; V device [P]
+ * float and dV device [P][n_cv] float (either may be NULL) receive V_nn and
+ * dV_nn/dxi. */
+int wtmd_mlp_eval(wtmd_t* h, const double* xi, int64_t P, float* V, float* dV);
+
+/* Gradient of the Sobolev loss (wtmd_surrogate_config) over one batch of B
+ * samples with respect to the 4481 parameters, at the bfloat16-rounded
+ * weights: xi device [B][3] double (unused CVs 0), V device [B] float, dV
+ * device [B][3] float (in CV units, unused 0); grad_out device [4482] float:
+ * the gradient, then the loss.  Deterministic for a given GPU. */
+int wtmd_mlp_grad(wtmd_t* h, const double* xi, const float* V, const float* dV, int64_t B, double lambda,
+                  float* grad_out);
+
+/* `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on
+ * the master weights; step t uses the batch of samples (t*B + b) mod n,
+ * b < B, of the device arrays (layout as wtmd_mlp_grad).  loss_out (device
+ * float, may be NULL) receives the last step's loss. */
+int wtmd_mlp_train(wtmd_t* h, const double* xi, const float* V, const float* dV, int64_t n, int64_t B,
+                   int64_t iters, double lr, double lambda, float* loss_out);
 
 #ifdef __cplusplus
 }

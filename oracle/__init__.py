@@ -26,7 +26,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 CV_COMPONENT, CV_DIHEDRAL, CV_COORDINATION, CV_RG, CV_QPAIRS = 1, 2, 3, 4, 5
 CV_INTENSIVE = 1
-ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN, ENGINE_HARMONIC = 0, 1, 2, 3, 4
+ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN, ENGINE_HARMONIC, ENGINE_WELLS3 = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -84,6 +84,8 @@ def lib():
         _lib.orc_noise3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, dp]
         _lib.orc_mb.argtypes = [d, d, dp, dp]
         _lib.orc_mb.restype = d
+        _lib.orc_wells3.argtypes = [dp, dp]
+        _lib.orc_wells3.restype = d
         _lib.orc_lj.argtypes = [i64, dp, dp, d, d, d, dp]
         _lib.orc_lj.restype = d
         _lib.orc_chain.argtypes = [i64, dp, d, d, d, d, d, dp]
@@ -134,6 +136,14 @@ def mb(x: float, y: float):
     fx, fy = C.c_double(), C.c_double()
     u = lib().orc_mb(x, y, C.byref(fx), C.byref(fy))
     return u, np.array([fx.value, fy.value])
+
+
+def wells3(r):
+    """Three-well test landscape: energy and force [3] at r [3]."""
+    r = _f64(np.asarray(r, float).reshape(3))
+    f = np.zeros(3)
+    u = lib().orc_wells3(_dp(r), _dp(f))
+    return u, f
 
 
 def lj(x, box, eps=1.0, sig=1.0, rc=2.5):

@@ -155,7 +155,10 @@ def adam(theta, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 def bias(theta, norm, xi):
     """Surrogate bias V_nn and dV_nn/dxi at CV points xi [P][d] (d <= 3),
-    norm = (mu[3], inv_s[3], Vm, Vs); unused inputs are 0."""
+    norm = (mu[3], inv_s[3], Vm, Vs), or the same 8 numbers flat; unused
+    inputs are 0."""
+    if np.ndim(norm[0]) == 0:
+        norm = (norm[0:3], norm[3:6], norm[6], norm[7])
     mu, inv_s, Vm, Vs = np.asarray(norm[0], float), np.asarray(norm[1], float), float(norm[2]), float(norm[3])
     xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
     d = xi.shape[1]

@@ -140,6 +140,33 @@ double orc_mb(double x, double y, double* fx, double* fy)
     return U;
 }
 
+/* Three-well test landscape in 3-D (a synthetic free-energy surface for the
+ * CV-space metadynamics runs that generate long hill lists): three Gaussian
+ * wells in a harmonic confinement,
+ *   U(r) = -sum_m A_m exp(-|r - c_m|^2 / (2 s_m^2)) + (k/2) |r|^2,
+ * A = (8, 6, 7), s = (0.45, 0.40, 0.50), c_1 = (-1, 0, 0),
+ * c_2 = (1, 0.2, -0.3), c_3 = (0.1, 1.3, 0.6), k = 1.5.  f[3] = -grad U. */
+static const double W3_A[3] = {8.0, 6.0, 7.0};
+static const double W3_S[3] = {0.45, 0.40, 0.50};
+static const double W3_C[3][3] = {{-1.0, 0.0, 0.0}, {1.0, 0.2, -0.3}, {0.1, 1.3, 0.6}};
+static const double W3_K = 1.5;
+
+double orc_wells3(const double* r, double* f)
+{
+    double U = 0.5 * W3_K * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double g[3] = {W3_K * r[0], W3_K * r[1], W3_K * r[2]};
+    for (int m = 0; m < 3; ++m) {
+        double d[3] = {r[0] - W3_C[m][0], r[1] - W3_C[m][1], r[2] - W3_C[m][2]};
+        double q = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) / (2.0 * W3_S[m] * W3_S[m]);
+        double e = W3_A[m] * exp(-q);
+        U -= e;
+        for (int k = 0; k < 3; ++k) g[k] += e * d[k] / (W3_S[m] * W3_S[m]);
+    }
+    if (f)
+        for (int k = 0; k < 3; ++k) f[k] = -g[k];
+    return U;
+}
+
 /* 12-6 Lennard-Jones, all pairs, minimum image, truncated at rc, energy
  * shifted to zero at rc.  f[n][3] is overwritten.  Returns the energy. */
 double orc_lj(int64_t n, const double* x, const double* box, double eps, double sig, double rc, double* f)
@@ -479,7 +506,14 @@ void orc_fes(int64_t n, const double* grid, double gamma, double* out)
 /* ------------------------------------------------------------------------ */
 /* Whole system: engine + bias + BAOAB + deposition                          */
 /* ------------------------------------------------------------------------ */
-enum { ORC_ENGINE_NONE = 0, ORC_ENGINE_MB = 1, ORC_ENGINE_LJ = 2, ORC_ENGINE_CHAIN = 3, ORC_ENGINE_HARMONIC = 4 };
+enum {
+    ORC_ENGINE_NONE = 0,
+    ORC_ENGINE_MB = 1,
+    ORC_ENGINE_LJ = 2,
+    ORC_ENGINE_CHAIN = 3,
+    ORC_ENGINE_HARMONIC = 4,
+    ORC_ENGINE_WELLS3 = 5
+};
 
 typedef struct {
     int64_t engine;
@@ -549,6 +583,9 @@ static void orc_engine(const orc_sys* s, const double* x, double* f)
             break;
         case ORC_ENGINE_HARMONIC:
             for (int64_t i = 0; i < 3 * n; ++i) fw[i] = -s->harm_k * xw[i];
+            break;
+        case ORC_ENGINE_WELLS3:
+            for (int64_t i = 0; i < n; ++i) orc_wells3(&xw[3 * i], &fw[3 * i]);
             break;
         default:
             break;

@@ -29,7 +29,8 @@ F32, F64 = 0, 1
 ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN = 0, 1, 2, 3
 CV_COMPONENT, CV_DIHEDRAL, CV_COORDINATION, CV_RG, CV_QPAIRS = 1, 2, 3, 4, 5
 CV_INTENSIVE = 1
-_ENGINES = {"none": ENGINE_NONE, "mb": ENGINE_MB, "lj": ENGINE_LJ, "chain": ENGINE_CHAIN}
+ENGINE_WELLS3 = 5
+_ENGINES = {"none": ENGINE_NONE, "mb": ENGINE_MB, "lj": ENGINE_LJ, "chain": ENGINE_CHAIN, "wells3": ENGINE_WELLS3}
 
 
 class WtmdError(RuntimeError):
@@ -65,7 +66,10 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_check", "bias_eval", "hills_eval", "fes_grid", "wtmd_hills_load", "wtmd_hills_read",
            "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
            "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint", "wtmd_walkers_persistent",
-           "wtmd_autotune"]
+           "wtmd_autotune", "wtmd_surrogate", "wtmd_surrogate_config", "wtmd_surrogate_fit", "wtmd_surrogate_status",
+           "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train"]
+
+MLP_PARAMS = 4481
 
 _lib = None
 
@@ -100,6 +104,16 @@ def lib() -> C.CDLL:
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wtmd_walkers_persistent.argtypes = [vp, i32]
     L.wtmd_autotune.argtypes = [vp, i64, C.POINTER(i32)]
+    dp, fp = C.POINTER(C.c_double), C.POINTER(C.c_float)
+    L.wtmd_surrogate.argtypes = [vp, i32, C.c_double, i64]
+    L.wtmd_surrogate_config.argtypes = [vp, i64, i64, i64, C.c_double, C.c_double]
+    L.wtmd_surrogate_fit.argtypes = [vp, dp]
+    L.wtmd_surrogate_status.argtypes = [vp, dp]
+    L.wtmd_surrogate_set.argtypes = [vp, i64, i32]
+    L.wtmd_mlp_params.argtypes = [vp, fp, fp, dp, dp]
+    L.wtmd_mlp_eval.argtypes = [vp, vp, i64, vp, vp]
+    L.wtmd_mlp_grad.argtypes = [vp, vp, vp, vp, i64, C.c_double, vp]
+    L.wtmd_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i64, C.c_double, C.c_double, vp]
     L.wtmd_cv_forward.argtypes = [vp, vp, vp]
     L.wtmd_cv_adjoint.argtypes = [vp, vp, vp]
     L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
@@ -203,6 +217,16 @@ class Wtmd:
             raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
         return C.c_void_p(t.data_ptr())
 
+    @staticmethod
+    def _dev(t, shape, dtype):
+        """Validate a contiguous CUDA tensor of `dtype`; None in `shape` matches any size."""
+        torch = _torch()
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA {dtype} tensor")
+        if len(t.shape) != len(shape) or any(w is not None and w != g for w, g in zip(shape, t.shape)):
+            raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return t
+
     # ------------------------------------------------------------------
     def cv_define(self, kind, a=None, b=None, axis=0, r0=1.5, nn=6, mm=12, scale=0.0, flags=0, period=0.0) -> int:
         d = CvDesc()
@@ -258,6 +282,89 @@ class Wtmd:
         ch = (C.c_int32 * 3)()
         self._err(lib().wtmd_autotune(self.h, int(steps), ch), "wtmd_autotune")
         return tuple(ch)
+
+    # ---- MLP surrogate of the hills sum ----
+    _STATS = ("K", "rms_kT", "max_kT", "grad_rel_rms", "loss", "active", "fits", "iters")
+
+    def surrogate(self, enable: bool = True, tol_kT: float = 0.05, retrain_every: int = 10000):
+        """Network for the older hills + exact tail, refitted every `retrain_every` hills."""
+        self._stream()
+        self._err(lib().wtmd_surrogate(self.h, 1 if enable else 0, float(tol_kT), int(retrain_every)),
+                  "wtmd_surrogate")
+
+    def surrogate_config(self, n_samples=65540, iters=80000, batch=4096, lr=6e-3, lam=0.1):
+        self._err(lib().wtmd_surrogate_config(self.h, int(n_samples), int(iters), int(batch), float(lr), float(lam)),
+                  "wtmd_surrogate_config")
+
+    def surrogate_fit(self) -> dict:
+        self._stream()
+        st = (C.c_double * 8)()
+        self._err(lib().wtmd_surrogate_fit(self.h, st), "wtmd_surrogate_fit")
+        return dict(zip(self._STATS, list(st)))
+
+    def surrogate_status(self) -> dict:
+        st = (C.c_double * 8)()
+        self._err(lib().wtmd_surrogate_status(self.h, st), "wtmd_surrogate_status")
+        return dict(zip(self._STATS, list(st)))
+
+    def surrogate_set(self, k0: int, active: bool = True):
+        self._stream()
+        self._err(lib().wtmd_surrogate_set(self.h, int(k0), 1 if active else 0), "wtmd_surrogate_set")
+
+    def mlp_params(self, params=None, norm=None):
+        """Load (if given) and return (FP32 master weights [4481], norm [8])."""
+        self._stream()
+        fp, dp = C.POINTER(C.c_float), C.POINTER(C.c_double)
+        pin = None
+        if params is not None:
+            pin = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(MLP_PARAMS))
+        nin = None if norm is None else np.ascontiguousarray(np.asarray(norm, dtype=np.float64).reshape(8))
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        nout = np.zeros(8)
+        self._err(lib().wtmd_mlp_params(self.h, pin.ctypes.data_as(fp) if pin is not None else None,
+                                        out.ctypes.data_as(fp), nin.ctypes.data_as(dp) if nin is not None else None,
+                                        nout.ctypes.data_as(dp)), "wtmd_mlp_params")
+        return out, nout
+
+    def mlp_eval(self, xi):
+        """V_nn [P] and dV_nn/dxi [P][d] (float32) at CV points xi (CUDA FP64 [P][d])."""
+        torch = _torch()
+        self._stream()
+        xi = self._dev(xi, (None, self.d), torch.float64)
+        P = xi.shape[0]
+        V = torch.empty(P, dtype=torch.float32, device=xi.device)
+        dV = torch.empty(P, self.d, dtype=torch.float32, device=xi.device)
+        self._err(lib().wtmd_mlp_eval(self.h, C.c_void_p(xi.data_ptr()), P, C.c_void_p(V.data_ptr()),
+                                      C.c_void_p(dV.data_ptr())), "wtmd_mlp_eval")
+        return V, dV
+
+    def mlp_grad(self, x, V, G, lam):
+        """Sobolev-loss gradient [4481] and loss over one batch (x FP64 [B][3], V [B], G [B][3] FP32)."""
+        torch = _torch()
+        self._stream()
+        x = self._dev(x, (None, 3), torch.float64)
+        B = x.shape[0]
+        V = self._dev(V, (B,), torch.float32)
+        G = self._dev(G, (B, 3), torch.float32)
+        out = torch.empty(MLP_PARAMS + 1, dtype=torch.float32, device=x.device)
+        self._err(lib().wtmd_mlp_grad(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(V.data_ptr()),
+                                      C.c_void_p(G.data_ptr()), B, float(lam), C.c_void_p(out.data_ptr())),
+                  "wtmd_mlp_grad")
+        return out[:MLP_PARAMS], out[MLP_PARAMS]
+
+    def mlp_train(self, x, V, G, batch, iters, lr, lam):
+        """`iters` Adam steps over cyclic batches of the given samples; returns the last loss (tensor)."""
+        torch = _torch()
+        self._stream()
+        x = self._dev(x, (None, 3), torch.float64)
+        n = x.shape[0]
+        V = self._dev(V, (n,), torch.float32)
+        G = self._dev(G, (n, 3), torch.float32)
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        self._err(lib().wtmd_mlp_train(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(V.data_ptr()),
+                                       C.c_void_p(G.data_ptr()), n, int(batch), int(iters), float(lr), float(lam),
+                                       C.c_void_p(loss.data_ptr())), "wtmd_mlp_train")
+        return loss
 
     def cv_forward(self, pos):
         """CV values [W, d] at pos; keeps the Jacobians for cv_adjoint."""

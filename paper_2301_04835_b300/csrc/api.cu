@@ -55,6 +55,19 @@ static void drop_graphs(wtmd_t* h)
     h->graph1 = nullptr;
 }
 
+namespace wtmd {
+void drop_step_graphs(wtmd_t* h) { drop_graphs(h); }
+}  // namespace wtmd
+
+// Bias at the walkers' CVs: the exact hills sum, over [k0, count) plus the
+// network's part when the surrogate is active.
+static int launch_bias_sum(wtmd_t* h)
+{
+    int rc = launch_hills_range(h, h->xi, true, 4, h->W, h->V, h->dV, 4, surrogate_k0(h), h->count);
+    if (rc) return rc;
+    return launch_mlp_add(h);
+}
+
 static void free_cv(CvDev& c)
 {
     cudaFree(c.a);
@@ -83,6 +96,7 @@ extern "C" int wtmd_destroy(wtmd_t* h)
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
                     h->cell_atoms};
     for (void* p : ptrs) cudaFree(p);
+    surrogate_free(h->sur);
     {
         WalkerPlan& k = h->wk;
         void* wp[] = {k.tasks, k.tbase, k.tcount, k.tpart, k.ticket, k.rgc, k.bar};
@@ -120,7 +134,8 @@ extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
     if (!(c.gamma == 0.0 || isinf(c.gamma) || c.gamma > 1.0)) return WTMD_EINVAL;
     if (!(c.kT > 0.0)) return WTMD_EINVAL;
     if (c.stride < 0 || c.hill_capacity < 0) return WTMD_EINVAL;
-    if (c.engine < WTMD_ENGINE_NONE || c.engine > WTMD_ENGINE_CHAIN) return WTMD_EINVAL;
+    if (!(c.engine >= WTMD_ENGINE_NONE && c.engine <= WTMD_ENGINE_CHAIN) && c.engine != WTMD_ENGINE_WELLS3)
+        return WTMD_EINVAL;
     if (c.n_walkers < 1 || !c.walker_size) return WTMD_EINVAL;
     if (!(c.dt > 0.0) || !(c.mass > 0.0) || c.friction < 0.0) return WTMD_EINVAL;
     const bool grid = c.grid_bins[0] > 0;
@@ -402,7 +417,7 @@ static int enqueue_forces(wtmd_t* h)
     int rc;
     if ((rc = launch_engine(h))) return rc;
     if ((rc = launch_cvs(h, h->pos))) return rc;
-    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if ((rc = launch_bias_sum(h))) return rc;
     return launch_scatter(h, h->force, nullptr, false);
 }
 
@@ -438,7 +453,7 @@ static int enqueue_engine_and_bias(wtmd_t* h)
     }
     if ((rc = fork ? launch_cv(h, h->pos, 0) : launch_cvs(h, h->pos))) return rc;
     for (int c = 1; c < h->ncv && fork; ++c) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0));
-    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if ((rc = launch_bias_sum(h))) return rc;
     if (fork) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return WTMD_OK;
 }
@@ -483,19 +498,9 @@ static int ready(wtmd_t* h)
     return WTMD_OK;
 }
 
-extern "C" int step_n(wtmd_t* h, int64_t n_steps)
+static int run_steps(wtmd_t* h, int64_t n_steps)
 {
-    if (!h) return WTMD_EINVAL;
-    if (n_steps < 0) FAIL(h, WTMD_EINVAL, "negative step count");
-    int rc = ready(h);
-    if (rc) return rc;
-    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
-    if (n_steps == 0) return WTMD_OK;
-    if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
-    if (!h->forces_valid) {
-        if ((rc = enqueue_forces(h))) return rc;
-        h->forces_valid = true;
-    }
+    int rc;
     if (!h->graph && !h->no_graph) {
         if (capture(h, kGraphSteps, &h->graph) != WTMD_OK || capture(h, 1, &h->graph1) != WTMD_OK) {
             // this launch sequence cannot be captured here: replay eagerly
@@ -512,6 +517,30 @@ extern "C" int step_n(wtmd_t* h, int64_t n_steps)
     const int64_t full = n_steps / kGraphSteps, rest = n_steps % kGraphSteps;
     for (int64_t i = 0; i < full; ++i) WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
     for (int64_t i = 0; i < rest; ++i) WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph1, h->stream));
+    return WTMD_OK;
+}
+
+extern "C" int step_n(wtmd_t* h, int64_t n_steps)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_steps < 0) FAIL(h, WTMD_EINVAL, "negative step count");
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
+    if (n_steps == 0) return WTMD_OK;
+    if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+    if (!h->forces_valid) {
+        if ((rc = enqueue_forces(h))) return rc;
+        h->forces_valid = true;
+    }
+    // with the surrogate on, the run is cut where a refit is due
+    for (int64_t left = n_steps; left > 0;) {
+        int64_t seg = left;
+        if ((rc = surrogate_segment(h, left, &seg))) return rc;
+        if ((rc = run_steps(h, seg))) return rc;
+        surrogate_advanced(h, seg);
+        left -= seg;
+    }
     return WTMD_OK;
 }
 
@@ -559,7 +588,7 @@ extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_
     if (!pos) FAIL(h, WTMD_EINVAL, "null positions");
     if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
     if ((rc = launch_cvs(h, pos))) return rc;
-    if ((rc = launch_hills(h, h->xi, true, 4, h->W, h->V, h->dV, 4))) return rc;
+    if ((rc = launch_bias_sum(h))) return rc;
     if (force_inout && (rc = launch_scatter(h, force_inout, nullptr, false))) return rc;
     if (V_out) WTMD_CUDA_TRY(h, cudaMemcpyAsync(V_out, h->V, realsz(h) * h->W, cudaMemcpyDeviceToDevice, h->stream));
     if (xi_out && (rc = copy_cols(h, xi_out, h->xi, true, h->d))) return rc;
@@ -630,6 +659,7 @@ extern "C" int wtmd_hills_load(wtmd_t* h, const double* hills, int64_t count)
     store_hills32_range(h, 0, count);
     int rc = launch_grid_rebuild(h);
     if (rc) return rc;
+    if ((rc = surrogate_invalidate(h))) return rc;
     WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return WTMD_OK;
 }

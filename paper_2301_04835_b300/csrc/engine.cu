@@ -34,6 +34,35 @@ __constant__ double kMB[6][4] = {
     {0.0, 0.5, 1.5, 1.0},            // y0
 };
 
+// Three Gaussian wells in a harmonic confinement (3-D test landscape):
+// U = -sum_m A_m exp(-|r - c_m|^2 / (2 s_m^2)) + (k/2) |r|^2, F = -grad U.
+__constant__ double kW3[3][5] = {
+    // A, s, c_x, c_y, c_z
+    {8.0, 0.45, -1.0, 0.0, 0.0},
+    {6.0, 0.40, 1.0, 0.2, -0.3},
+    {7.0, 0.50, 0.1, 1.3, 0.6},
+};
+constexpr double kW3Conf = 1.5;
+
+template <typename R>
+__global__ void wells3_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __restrict__ f)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R4<R> p = x[i];
+    R fx = -(R)kW3Conf * p.x, fy = -(R)kW3Conf * p.y, fz = -(R)kW3Conf * p.z;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const R dx = p.x - (R)kW3[m][2], dy = p.y - (R)kW3[m][3], dz = p.z - (R)kW3[m][4];
+        const R is2 = (R)(1.0 / (kW3[m][1] * kW3[m][1]));
+        const R e = (R)kW3[m][0] * exp(-(R)0.5 * (dx * dx + dy * dy + dz * dz) * is2);
+        fx -= e * dx * is2;
+        fy -= e * dy * is2;
+        fz -= e * dz * is2;
+    }
+    f[i] = mk4<R>(fx, fy, fz, R(0));
+}
+
 template <typename R>
 __global__ void mb_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __restrict__ f)
 {
@@ -416,6 +445,10 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
     case WTMD_ENGINE_MB:
         mb_kernel<R><<<nb, 256, 0, st>>>(h->N, x, f);
         mark(h, "mb_force");
+        break;
+    case WTMD_ENGINE_WELLS3:
+        wells3_kernel<R><<<nb, 256, 0, st>>>(h->N, x, f);
+        mark(h, "wells3_force");
         break;
     case WTMD_ENGINE_LJ: {
         const R rc2 = (R)(c.lj_rc * c.lj_rc), sig2 = (R)(c.lj_sigma * c.lj_sigma), e24 = (R)(24.0 * c.lj_eps);

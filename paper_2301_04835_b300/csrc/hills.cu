@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256) hills_finalize_cf_kernel(const dbl4* __re
 }
 
 template <int D, int TH, bool PER, typename PT>
-__global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict__ hp, const long long* __restrict__ cnt,
+__global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict__ hp, const long long* __restrict__ k0p,
+                                                       const long long* __restrict__ cnt,
                                                        const PT* __restrict__ xi, int xs, int P,
                                                        const double* __restrict__ ctr, HillPrmF32 prm,
                                                        dbl4* __restrict__ partial, HillOut<float> out)
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
     __shared__ __align__(8) uint64_t bar[NST];
     // on a timeout the CTA still takes part in the ticket so that the next
     // launch starts from a clean ticket (the status word reports the error)
-    hills_f32_task<D, TH, PER, PT>(hp, cnt, xi, xs, P, ctr, prm, partial, out.status, blockIdx.x, blockIdx.y,
+    hills_f32_task<D, TH, PER, PT>(hp, k0p, cnt, xi, xs, P, ctr, prm, partial, out.status, blockIdx.x, blockIdx.y,
                                    gridDim.y, ring, bar, true);
     finalize_if_last_cf(partial, P, out);
 }
@@ -194,29 +195,30 @@ static Plan plan_for(long long P, long long cap_pairs)
 }
 
 template <int D, bool PER, typename PT>
-static void launch_f32_d(int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* cnt, const PT* xi,
-                         int xs, int P, const double* ctr, const HillPrmF32& prm, dbl4* part, const HillOut<float>& o)
+static void launch_f32_d(int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* k0p,
+                         const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
+                         dbl4* part, const HillOut<float>& o)
 {
     switch (th) {
-    case 1: hills_f32_kernel<D, 1, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
-    case 4: hills_f32_kernel<D, 4, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
-    case 32: hills_f32_kernel<D, 32, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
-    default: hills_f32_kernel<D, 256, PER, PT><<<grid, HB, 0, st>>>(hp, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 1: hills_f32_kernel<D, 1, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 4: hills_f32_kernel<D, 4, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 32: hills_f32_kernel<D, 32, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    default: hills_f32_kernel<D, 256, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
     }
 }
 
 template <typename PT>
-static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* cnt,
-                          const PT* x, int xs, int P, const double* ctr, const HillPrmF32& prm, dbl4* part,
-                          const HillOut<float>& status)
+static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, const float4* hp,
+                          const long long* k0p, const long long* cnt, const PT* x, int xs, int P, const double* ctr,
+                          const HillPrmF32& prm, dbl4* part, const HillOut<float>& status)
 {
     switch (d * 2 + (per ? 1 : 0)) {
-    case 2: launch_f32_d<1, false, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 3: launch_f32_d<1, true, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 4: launch_f32_d<2, false, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 5: launch_f32_d<2, true, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 6: launch_f32_d<3, false, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
-    default: launch_f32_d<3, true, PT>(th, grid, st, hp, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 2: launch_f32_d<1, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 3: launch_f32_d<1, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 4: launch_f32_d<2, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 5: launch_f32_d<2, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 6: launch_f32_d<3, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    default: launch_f32_d<3, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
     }
 }
 
@@ -255,6 +257,12 @@ int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
 }
 
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs)
+{
+    return launch_hills_range(h, xi, xi_f64, xs, P, V, dV, dvs, nullptr, h->count);
+}
+
+int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs,
+                       const long long* k0p, const long long* k1p)
 {
     if (P <= 0) return WTMD_OK;
     if (P > (1ll << 30)) {
@@ -304,10 +312,10 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void
         HillOut<float> o{(float*)V, (float*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
                          h->status};
         if (xi_f64)
-            launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, h->hills32, h->count, (const double*)xi, xs, Pi,
-                                  h->ctr, prm, part, o);
+            launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, h->hills32, k0p, k1p, (const double*)xi, xs,
+                                  Pi, h->ctr, prm, part, o);
         else
-            launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, h->hills32, h->count, (const float*)xi, xs, Pi,
+            launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, h->hills32, k0p, k1p, (const float*)xi, xs, Pi,
                                  h->ctr, prm, part, o);
         mark(h, "hills_sum_f32");
         if (!fused) {
@@ -327,10 +335,10 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void
         HillOut<double> o{(double*)V, (double*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
                           h->status};
         if (per)
-            launch_f64_t<true>(pl.th, grid, h->stream, (const dbl4*)h->hills64, h->count, (const double*)xi, xs, Pi,
+            launch_f64_t<true>(pl.th, grid, h->stream, (const dbl4*)h->hills64, k1p, (const double*)xi, xs, Pi,
                                h->d, prm, part, o);
         else
-            launch_f64_t<false>(pl.th, grid, h->stream, (const dbl4*)h->hills64, h->count, (const double*)xi, xs, Pi,
+            launch_f64_t<false>(pl.th, grid, h->stream, (const dbl4*)h->hills64, k1p, (const double*)xi, xs, Pi,
                                 h->d, prm, part, o);
         mark(h, "hills_sum_f64");
         if (!fused) {

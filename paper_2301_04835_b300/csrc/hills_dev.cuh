@@ -281,10 +281,11 @@ __device__ __forceinline__ float2 wrap2(float2 d, float per, float iper)
 // the mbarriers are new (false: they served an earlier task of this CTA and
 // are invalidated and re-initialized first).  Returns false on a timeout.
 template <int D, int TH, bool PER, typename PT>
-__device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* __restrict__ cnt,
-                               const PT* __restrict__ xi, int xs, int P, const double* __restrict__ ctr,
-                               const HillPrmF32& prm, dbl4* __restrict__ partial, unsigned* status, int tile,
-                               int split, int nsplit, float4 (*ring)[2 * CHUNK], uint64_t* bar, bool fresh)
+__device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* __restrict__ k0p,
+                               const long long* __restrict__ cnt, const PT* __restrict__ xi, int xs, int P,
+                               const double* __restrict__ ctr, const HillPrmF32& prm, dbl4* __restrict__ partial,
+                               unsigned* status, int tile, int split, int nsplit, float4 (*ring)[2 * CHUNK],
+                               uint64_t* bar, bool fresh)
 {
     constexpr int TP = HB / TH;  // points per CTA
     const int tid = threadIdx.x;
@@ -302,8 +303,12 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     const float2 X1 = make_float2(xh[1], xh[1]);
     const float2 X2 = make_float2(xh[2], xh[2]);
 
+    // hills [k0, count): k0 is a multiple of 2 * CHUNK, so the range starts
+    // on a chunk boundary of the pair layout
+    const long long k0 = k0p ? *k0p : 0;
     const long long count = *cnt;
-    const long long npairs = (count + 1) >> 1;
+    const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
+    hp += (size_t)(k0 >> 1) * 2;
     const long long nch = (npairs + CHUNK - 1) / CHUNK;
     const long long per = (nch + nsplit - 1) / nsplit;
     const long long c0 = (long long)split * per;

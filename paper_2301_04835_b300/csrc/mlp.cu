@@ -1,0 +1,984 @@
+// MLP surrogate of the hills sum.
+//
+// Once the hill list is long, the bias V(xi) = sum_k w_k exp(...) costs one
+// exponential per hill per step.  The paper represents biases by neural
+// networks in its ANN and FUNN methods (Sec. 2.1.6); here a small network
+// stands in for the older part of the hill list:
+//     V(xi) = V_nn(xi) + sum_{k >= K} w_k exp(...),
+// where V_nn approximates the sum over hills [0, K) and the exact sum covers
+// the hills deposited since (K is a multiple of 256 so that the FP32 hill
+// layout's range starts on a chunk boundary).  The network is
+//     z1 = W1 x + b1, a1 = silu(z1), z2 = W2 a1 + b2, a2 = silu(z2),
+//     y = w3 . a2 + b3,   silu(z) = z sigmoid(z),
+// 3 -> 64 -> 64 -> 1 (4481 parameters), with x = (xi - mu) inv_s and
+// V_nn = Vs y + Vm.  Weights are used in bfloat16 (an FP32 master copy is
+// trained); activations and sums are FP32.
+//
+// Kernels (all hand-written, one warp per point or sample; lane l owns the
+// hidden units l and l + 32 of both layers):
+//   mlp_eval_kernel   V_nn and dV_nn/dxi at P points (inference; the step
+//                     path adds them to the exact tail sum);
+//   mlp_grad_kernel   Sobolev loss sum_b (y - V)^2 + lam |grad_x y - G|^2 and
+//                     its weight gradient: forward, input gradient and the
+//                     double backward through it, accumulated per lane in
+//                     registers, reduced per block in a fixed order;
+//   mlp_adam_kernel   fixed-order sum of the block partials and the Adam
+//                     update (Kingma & Ba 2015) of the FP32 master, which is
+//                     re-rounded to bfloat16 (nearest, ties to even).
+// Training data come from the run: jittered copies of the most recent hill
+// centres, labelled by the exact hills sum over [0, K).  A tenth of them is
+// held out; the surrogate is used only while its held-out RMS error (after
+// removing the mean offset) is at most the tolerance, else the exact sum
+// over all hills is used.
+//
+// The layer-2 products have 64-long reductions per output and FP32 inputs:
+// the tensor-core MMA needs both operands in one 16-bit type, and bfloat16
+// activations would put errors of order 1e-2 kT into V.  The work is a few
+// microseconds per step, so the FP32 pipe is used.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "step_dev.cuh"
+
+namespace wtmd {
+
+constexpr int MH = 64;      // hidden width
+constexpr int MP = 4481;    // parameters
+constexpr int O_W1 = 0, O_B1 = 192, O_W2 = 256, O_B2 = 4352, O_W3 = 4416, O_B3 = 4480;
+constexpr int W2P = 68;     // shared row pitch of W2: 16-byte rows, conflict-free quad loads
+constexpr int MLP_T = 128;  // threads per block
+constexpr int MLP_W = MLP_T / 32;
+constexpr int RW2P = 65;    // pitch of the transposed W2 gradient in the block reduction
+constexpr int RED_N = O_W2 + MH * RW2P + (MP - O_B2) + 1;  // + loss
+
+struct Surrogate {
+    float* master = nullptr;        // [MP] FP32 master weights
+    unsigned short* wb = nullptr;   // [MP] bfloat16 bits used by the kernels
+    float* m = nullptr;             // Adam moments [MP]
+    float* v = nullptr;
+    double* norm = nullptr;         // device [8]: mu[3], inv_s[3], Vm, Vs
+    long long* k0 = nullptr;        // device: first hill of the exact tail (0 while inactive)
+    long long* kend = nullptr;      // device: end of the fitted hill range
+    int* active = nullptr;          // device flag read by the step path
+    long long* ctr = nullptr;       // device [2]: Adam step t, batch iteration
+    unsigned* ticket = nullptr;
+    float* partial = nullptr;       // [pblocks][MP + 1]
+    int pblocks = 0;
+    float* loss = nullptr;          // device: loss of the last training step
+    float* grad = nullptr;          // device [MP + 1] scratch of wtmd_mlp_grad
+    double* sx = nullptr;           // training set [S][3] CV points
+    float* sV = nullptr;            // [S]
+    float* sG = nullptr;            // [S][3]
+    float* hV = nullptr;            // held-out predictions [S/10]
+    float* hG = nullptr;            // [S/10][3]
+    int64_t S = 0;
+    double norm_h[8] = {0, 0, 0, 1, 1, 1, 0, 1};
+    bool have_norm = false;
+    bool enabled = false;
+    double tol = 0.05;
+    int64_t every = 10000;
+    int64_t next_fit = 0;
+    int64_t fit_samples = 65540, fit_iters = 80000, batch = 4096;
+    double lr = 6e-3, lam = 0.1;
+    double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long host_step = 0, host_count = 0;
+    uint64_t seed = 0x5eedULL;
+    long long round = 0;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16_bits_to_f(unsigned short b) { return __uint_as_float((unsigned)b << 16); }
+
+// FP32 -> bfloat16, round to nearest, ties to even (finite inputs)
+__device__ __forceinline__ unsigned short f_to_bf16_bits(float x)
+{
+    unsigned u = __float_as_uint(x);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
+}
+
+__device__ __forceinline__ float sigm(float z) { return rcp_approx(1.f + ex2_approx(-1.4426950408889634f * z)); }
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+struct MlpW {
+    float W2[MH][W2P];
+    float W1[MH][4];
+    float b1[MH], b2[MH], w3[MH];
+    float b3;
+};
+
+__device__ void mlp_stage(const unsigned short* __restrict__ wb, MlpW& s)
+{
+    for (int q = threadIdx.x; q < MP; q += blockDim.x) {
+        const float v = bf16_bits_to_f(wb[q]);
+        if (q < O_B1) {
+            s.W1[q / 3][q % 3] = v;
+        } else if (q < O_W2) {
+            s.b1[q - O_B1] = v;
+        } else if (q < O_B2) {
+            const int r = q - O_W2;
+            s.W2[r / MH][r % MH] = v;
+        } else if (q < O_W3) {
+            s.b2[q - O_B2] = v;
+        } else if (q < O_B3) {
+            s.w3[q - O_W3] = v;
+        } else {
+            s.b3 = v;
+        }
+    }
+    for (int j = threadIdx.x; j < MH; j += blockDim.x) s.W1[j][3] = 0.f;
+}
+
+struct Fwd {
+    float z1[2], d1[2], z2[2], a2[2], d2[2], g2[2], h1[2];
+    float y, u[3];
+};
+
+// Forward pass and input gradient of one point by one warp.  A1 and G2 are
+// the warp's shared vectors of 64.
+__device__ __forceinline__ void warp_forward(const MlpW& s, const float x[3], float* A1, float* G2, Fwd& f)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int j = lane + 32 * r;
+        const float z = fmaf(s.W1[j][0], x[0], fmaf(s.W1[j][1], x[1], fmaf(s.W1[j][2], x[2], s.b1[j])));
+        const float sg = sigm(z);
+        f.z1[r] = z;
+        f.d1[r] = sg * fmaf(z, 1.f - sg, 1.f);
+        A1[j] = z * sg;
+    }
+    __syncwarp();
+    float ys = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = lane + 32 * r;
+        const float4* wr = reinterpret_cast<const float4*>(&s.W2[i][0]);
+        const float4* av = reinterpret_cast<const float4*>(A1);
+        float z = s.b2[i];
+#pragma unroll 4
+        for (int q = 0; q < MH / 4; ++q) {
+            const float4 w = wr[q], a = av[q];
+            z = fmaf(w.x, a.x, z);
+            z = fmaf(w.y, a.y, z);
+            z = fmaf(w.z, a.z, z);
+            z = fmaf(w.w, a.w, z);
+        }
+        const float sg = sigm(z);
+        f.z2[r] = z;
+        f.a2[r] = z * sg;
+        f.d2[r] = sg * fmaf(z, 1.f - sg, 1.f);
+        f.g2[r] = f.d2[r] * s.w3[i];
+        G2[i] = f.g2[r];
+        ys = fmaf(s.w3[i], f.a2[r], ys);
+    }
+    __syncwarp();
+    f.y = warp_sum(ys) + s.b3;
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int j = lane + 32 * r;
+        float hs = 0.f;
+#pragma unroll 8
+        for (int i = 0; i < MH; ++i) hs = fmaf(s.W2[i][j], G2[i], hs);
+        f.h1[r] = hs;
+        const float g1 = f.d1[r] * hs;
+        u0 = fmaf(s.W1[j][0], g1, u0);
+        u1 = fmaf(s.W1[j][1], g1, u1);
+        u2 = fmaf(s.W1[j][2], g1, u2);
+    }
+    f.u[0] = warp_sum(u0);
+    f.u[1] = warp_sum(u1);
+    f.u[2] = warp_sum(u2);
+}
+
+// silu''(z) = s (1 - s) (2 + z (1 - 2 s))
+__device__ __forceinline__ float silu_dd(float z)
+{
+    const float sg = sigm(z);
+    return sg * (1.f - sg) * fmaf(z, 1.f - 2.f * sg, 2.f);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const unsigned short* __restrict__ wb,
+                                                         const double* __restrict__ norm, const int* __restrict__ active,
+                                                         const double* __restrict__ xi, int xs, int d, int P,
+                                                         float* __restrict__ V, float* __restrict__ dV, int dvs,
+                                                         int add)
+{
+    if (active && *active == 0) return;
+    __shared__ MlpW s;
+    __shared__ __align__(16) float A1[MLP_W][MH];
+    __shared__ __align__(16) float G2[MLP_W][MH];
+    mlp_stage(wb, s);
+    __syncthreads();
+    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+    for (int p = blockIdx.x * MLP_W + w; p < P; p += gridDim.x * MLP_W) {
+        float x[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < d; ++k) x[k] = (float)((xi[(size_t)p * xs + k] - norm[k]) * norm[3 + k]);
+        Fwd f;
+        warp_forward(s, x, A1[w], G2[w], f);
+        if (lane == 0) {
+            const float Vn = (float)(norm[7] * (double)f.y + norm[6]);
+            if (V) V[p] = add ? V[p] + Vn : Vn;
+            if (dV)
+                for (int k = 0; k < d; ++k) {
+                    const float g = (float)(norm[7] * norm[3 + k]) * f.u[k];
+                    dV[(size_t)p * dvs + k] = add ? dV[(size_t)p * dvs + k] + g : g;
+                }
+        }
+        __syncwarp();
+    }
+}
+
+struct TrainArgs {
+    const unsigned short* wb;
+    const double* norm;
+    const double* x;        // samples [n][3] (CV units; unused dimensions 0)
+    const float* V;         // [n]
+    const float* G;         // [n][3]
+    long long n;
+    int B;                  // batch size
+    const long long* iter;  // batch counter (null: batch = samples [0, B))
+    long long perm;         // sample order: index (q * perm) mod n, perm coprime with n
+    int d;
+    float lam;
+    float* partial;         // [gridDim.x][MP + 1]
+};
+
+__global__ void __launch_bounds__(MLP_T, 2) mlp_grad_kernel(TrainArgs a)
+{
+    __shared__ MlpW s;
+    __shared__ __align__(16) float A1[MLP_W][MH];
+    __shared__ __align__(16) float G2[MLP_W][MH];
+    __shared__ __align__(16) float HB[MLP_W][MH];
+    __shared__ __align__(16) float Z2[MLP_W][MH];
+    mlp_stage(a.wb, s);
+    __syncthreads();
+    const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * MLP_W + w, nw = gridDim.x * MLP_W;
+    const long long it = a.iter ? *a.iter : 0;
+    float gsc[3];
+    for (int k = 0; k < 3; ++k) gsc[k] = (float)(1.0 / (a.norm[7] * a.norm[3 + k]));
+    const double Vm = a.norm[6], iVs = 1.0 / a.norm[7];
+    const float invB = 1.f / (float)a.B;
+
+    float acc2[2][MH];
+    float acc1[2][3], ab1[2], ab2[2], aw3[2];
+    float ab3 = 0.f, aloss = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int j = 0; j < MH; ++j) acc2[r][j] = 0.f;
+        acc1[r][0] = acc1[r][1] = acc1[r][2] = 0.f;
+        ab1[r] = ab2[r] = aw3[r] = 0.f;
+    }
+
+    for (int sm = gw; sm < a.B; sm += nw) {
+        const long long q = (it * a.B + sm) % a.n;
+        const long long idx = (q * a.perm) % a.n;
+        float x[3] = {0.f, 0.f, 0.f}, Gt[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < a.d; ++k) {
+            x[k] = (float)((a.x[idx * 3 + k] - a.norm[k]) * a.norm[3 + k]);
+            Gt[k] = a.G[idx * 3 + k] * gsc[k];
+        }
+        const float Vt = (float)(((double)a.V[idx] - Vm) * iVs);
+        Fwd f;
+        warp_forward(s, x, A1[w], G2[w], f);
+        const float r = f.y - Vt;
+        float e[3], du[3];
+        for (int k = 0; k < 3; ++k) {
+            e[k] = f.u[k] - Gt[k];
+            du[k] = 2.f * a.lam * e[k] * invB;
+        }
+        const float dy = 2.f * r * invB;
+        if (lane == 0) aloss += r * r + a.lam * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        // upstream of g1 = silu'(z1) * h1 through u = W1^T g1
+        float gb1[2];
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int j = lane + 32 * rr;
+            gb1[rr] = fmaf(s.W1[j][0], du[0], fmaf(s.W1[j][1], du[1], s.W1[j][2] * du[2]));
+            HB[w][j] = gb1[rr] * f.d1[rr];  // upstream of h1
+        }
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int i = lane + 32 * rr;
+            const float4* wr = reinterpret_cast<const float4*>(&s.W2[i][0]);
+            const float4* hb = reinterpret_cast<const float4*>(HB[w]);
+            float gb2 = 0.f;  // upstream of g2 = W2 hb1
+#pragma unroll 4
+            for (int qq = 0; qq < MH / 4; ++qq) {
+                const float4 ww = wr[qq], hh = hb[qq];
+                gb2 = fmaf(ww.x, hh.x, gb2);
+                gb2 = fmaf(ww.y, hh.y, gb2);
+                gb2 = fmaf(ww.z, hh.z, gb2);
+                gb2 = fmaf(ww.w, hh.w, gb2);
+            }
+            const float w3 = s.w3[i];
+            const float zb2 = fmaf(dy * w3, f.d2[rr], gb2 * w3 * silu_dd(f.z2[rr]));
+            aw3[rr] = fmaf(dy, f.a2[rr], fmaf(gb2, f.d2[rr], aw3[rr]));
+            ab2[rr] += zb2;
+            const float g2 = f.g2[rr];
+            const float4* av = reinterpret_cast<const float4*>(A1[w]);
+#pragma unroll
+            for (int qq = 0; qq < MH / 4; ++qq) {
+                const float4 aa = av[qq], hh = hb[qq];
+                acc2[rr][4 * qq + 0] = fmaf(zb2, aa.x, fmaf(g2, hh.x, acc2[rr][4 * qq + 0]));
+                acc2[rr][4 * qq + 1] = fmaf(zb2, aa.y, fmaf(g2, hh.y, acc2[rr][4 * qq + 1]));
+                acc2[rr][4 * qq + 2] = fmaf(zb2, aa.z, fmaf(g2, hh.z, acc2[rr][4 * qq + 2]));
+                acc2[rr][4 * qq + 3] = fmaf(zb2, aa.w, fmaf(g2, hh.w, acc2[rr][4 * qq + 3]));
+            }
+            Z2[w][i] = zb2;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int j = lane + 32 * rr;
+            float ab = 0.f;  // upstream of a1 = W2^T zb2
+#pragma unroll 8
+            for (int i = 0; i < MH; ++i) ab = fmaf(s.W2[i][j], Z2[w][i], ab);
+            const float zb1 = fmaf(ab, f.d1[rr], gb1[rr] * f.h1[rr] * silu_dd(f.z1[rr]));
+            const float g1 = f.d1[rr] * f.h1[rr];
+            for (int k = 0; k < 3; ++k) acc1[rr][k] = fmaf(zb1, x[k], fmaf(g1, du[k], acc1[rr][k]));
+            ab1[rr] += zb1;
+        }
+        if (lane == 0) ab3 += dy;
+        __syncwarp();
+    }
+
+    // block sum in warp order; W2's gradient is kept transposed (pitch 65)
+    // so that both the per-lane adds and the final copy are conflict-free
+    __shared__ float red[RED_N];
+    for (int q = threadIdx.x; q < RED_N; q += MLP_T) red[q] = 0.f;
+    __syncthreads();
+    for (int ww = 0; ww < MLP_W; ++ww) {
+        if (w == ww) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int i = lane + 32 * rr;
+#pragma unroll
+                for (int j = 0; j < MH; ++j) red[O_W2 + j * RW2P + i] += acc2[rr][j];
+                red[O_W2 + MH * RW2P + (i)] += ab2[rr];               // b2
+                red[O_W2 + MH * RW2P + MH + i] += aw3[rr];            // w3
+                for (int k = 0; k < 3; ++k) red[i * 3 + k] += acc1[rr][k];  // W1 row j = i
+                red[O_B1 + i] += ab1[rr];
+            }
+            if (lane == 0) {
+                red[O_W2 + MH * RW2P + 2 * MH] += ab3;
+                red[RED_N - 1] += aloss;
+            }
+        }
+        __syncthreads();
+    }
+    float* out = a.partial + (size_t)blockIdx.x * (MP + 1);
+    for (int q = threadIdx.x; q < MP + 1; q += MLP_T) {
+        float v;
+        if (q < O_W2) {
+            v = red[q];
+        } else if (q < O_B2) {
+            const int rq = q - O_W2;
+            v = red[O_W2 + (rq % MH) * RW2P + rq / MH];
+        } else if (q < MP) {
+            v = red[O_W2 + MH * RW2P + (q - O_B2)];
+        } else {
+            v = red[RED_N - 1];
+        }
+        out[q] = v;
+    }
+}
+
+// Fixed-order sum of the block partials: gradient and mean loss only.
+__global__ void mlp_reduce_kernel(const float* __restrict__ partial, int nblk, float invB, float* __restrict__ out)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > MP) return;
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * (MP + 1) + q];
+    out[q] = q == MP ? g * invB : g;
+}
+
+struct AdamPrm {
+    float lr, b1, b2, eps, invB;
+};
+
+__global__ void mlp_adam_kernel(const float* __restrict__ partial, int nblk, float* __restrict__ master,
+                                float* __restrict__ m, float* __restrict__ v, unsigned short* __restrict__ wb,
+                                AdamPrm p, long long* __restrict__ ctr, unsigned* __restrict__ ticket,
+                                float* __restrict__ loss_out)
+{
+    const long long t = ctr[0] + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < MP) {
+        float g = 0.f;
+        for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * (MP + 1) + q];
+        const float mm = fmaf(p.b1, m[q], (1.f - p.b1) * g);
+        const float vv = fmaf(p.b2, v[q], (1.f - p.b2) * g * g);
+        const float bc1 = (float)(1.0 - pow((double)p.b1, (double)t));
+        const float bc2 = (float)(1.0 - pow((double)p.b2, (double)t));
+        const float th = master[q] - p.lr * (mm / bc1) / (sqrtf(vv / bc2) + p.eps);
+        master[q] = th;
+        m[q] = mm;
+        v[q] = vv;
+        wb[q] = f_to_bf16_bits(th);
+    }
+    // the last block advances the counters (every block has read them)
+    __shared__ int lastb;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        lastb = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (lastb && threadIdx.x == 0) {
+        float L = 0.f;
+        for (int b = 0; b < nblk; ++b) L += partial[(size_t)b * (MP + 1) + MP];
+        if (loss_out) *loss_out = L * p.invB;
+        ctr[0] = t;
+        ctr[1] += 1;
+        *ticket = 0u;
+    }
+}
+
+__global__ void mlp_round_kernel(const float* __restrict__ master, unsigned short* __restrict__ wb)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < MP) wb[q] = f_to_bf16_bits(master[q]);
+}
+
+// Training points: jittered copies of the most recent M hill centres of
+// [0, K); every tenth sample goes to the held-out part at the end.
+__global__ void mlp_samples_kernel(const dbl4* __restrict__ h64, long long K, long long M, long long S, double j0,
+                                   double j1, double j2, int d, uint64_t seed, long long round, double* __restrict__ out)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const long long k = K - M + s % M;
+    const Normal3<double> n = noise3<double>(seed, round, (uint32_t)s);
+    const dbl4 c = h64[k];
+    const long long Str = S - S / 10;
+    const long long dst = (s % 10 == 9) ? Str + s / 10 : s - s / 10;
+    const double cc[3] = {c.x, c.y, c.z}, jj[3] = {j0, j1, j2};
+    for (int i = 0; i < 3; ++i) out[dst * 3 + i] = i < d ? cc[i] + jj[i] * n.g[i] : 0.0;
+}
+
+__global__ void set_ll_kernel(long long* p, long long v) { *p = v; }
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int grad_blocks()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        n = 2 * (sms > 0 ? sms : 148);
+    }
+    return n;
+}
+
+static uint64_t splitmix(uint64_t& s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void surrogate_free(Surrogate* s)
+{
+    if (!s) return;
+    void* p[] = {s->master, s->wb, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr, s->ticket,
+                 s->partial, s->loss, s->grad, s->sx, s->sV, s->sG, s->hV, s->hG};
+    for (void* q : p) cudaFree(q);
+    delete s;
+}
+
+// Allocate the surrogate state with a seeded Glorot-uniform initialisation.
+static int sur_get(wtmd_t* h, Surrogate** out)
+{
+    if (h->sur) {
+        *out = h->sur;
+        return WTMD_OK;
+    }
+    if (h->prec != WTMD_F32) {
+        h->err = "the surrogate runs on FP32 handles";
+        return WTMD_EINVAL;
+    }
+    Surrogate* s = new Surrogate();
+    h->sur = s;
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->master, sizeof(float) * MP));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->wb, sizeof(unsigned short) * MP));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->m, sizeof(float) * MP));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->v, sizeof(float) * MP));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->norm, sizeof(double) * 8));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->k0, sizeof(long long)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->kend, sizeof(long long)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->active, sizeof(int)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->ctr, sizeof(long long) * 2));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->ticket, sizeof(unsigned)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->loss, sizeof(float)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->grad, sizeof(float) * (MP + 1)));
+    s->pblocks = grad_blocks();
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->partial, sizeof(float) * (MP + 1) * (size_t)s->pblocks));
+    std::vector<float> w(MP, 0.f);
+    uint64_t st = s->seed;
+    auto uni = [&](float lim) { return (float)(((splitmix(st) >> 11) * 0x1.0p-53 * 2.0 - 1.0) * lim); };
+    const float l1 = std::sqrt(6.f / (3 + MH)), l2 = std::sqrt(6.f / (MH + MH)), l3 = std::sqrt(6.f / (MH + 1));
+    for (int q = O_W1; q < O_B1; ++q) w[q] = uni(l1);
+    for (int q = O_W2; q < O_B2; ++q) w[q] = uni(l2);
+    for (int q = O_W3; q < O_B3; ++q) w[q] = uni(l3);
+    WTMD_CUDA_TRY(h, cudaMemcpy(s->master, w.data(), sizeof(float) * MP, cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemset(s->m, 0, sizeof(float) * MP));
+    WTMD_CUDA_TRY(h, cudaMemset(s->v, 0, sizeof(float) * MP));
+    WTMD_CUDA_TRY(h, cudaMemset(s->ctr, 0, sizeof(long long) * 2));
+    WTMD_CUDA_TRY(h, cudaMemset(s->ticket, 0, sizeof(unsigned)));
+    WTMD_CUDA_TRY(h, cudaMemset(s->k0, 0, sizeof(long long)));
+    WTMD_CUDA_TRY(h, cudaMemset(s->active, 0, sizeof(int)));
+    WTMD_CUDA_TRY(h, cudaMemcpy(s->norm, s->norm_h, sizeof(double) * 8, cudaMemcpyHostToDevice));
+    mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb);
+    WTMD_CUDA_TRY(h, cudaDeviceSynchronize());
+    *out = s;
+    return WTMD_OK;
+}
+
+const long long* surrogate_k0(const wtmd_t* h) { return h->sur && h->sur->enabled ? h->sur->k0 : nullptr; }
+
+// Step path: V += V_nn, dV += dV_nn at the walkers' CVs when the surrogate
+// is active (the kernel returns at once otherwise).
+int launch_mlp_add(wtmd_t* h)
+{
+    if (!h->sur || !h->sur->enabled) return WTMD_OK;
+    Surrogate& s = *h->sur;
+    const int nb = std::max(1, std::min((h->W + MLP_W - 1) / MLP_W, 2 * grad_blocks()));
+    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s.wb, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
+                                                 (float*)h->dV, 4, 1);
+    mark(h, "mlp_surrogate");
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+static int launch_train(wtmd_t* h, const double* x, const float* V, const float* G, long long n, int B,
+                        const long long* iter, long long perm, double lam, bool adam, double lr, float* grad_out)
+{
+    Surrogate& s = *h->sur;
+    TrainArgs a{s.wb, s.norm, x, V, G, n, B, iter, perm, h->d, (float)lam, s.partial};
+    const int nb = std::max(1, std::min(s.pblocks, (B + MLP_W - 1) / MLP_W));
+    mlp_grad_kernel<<<nb, MLP_T, 0, h->stream>>>(a);
+    mark(h, "mlp_grad");
+    if (adam) {
+        AdamPrm p{(float)lr, 0.9f, 0.999f, 1e-8f, 1.f / (float)B};
+        mlp_adam_kernel<<<(MP + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, s.master, s.m, s.v, s.wb, p, s.ctr,
+                                                                 s.ticket, s.loss);
+        mark(h, "mlp_adam");
+    } else {
+        mlp_reduce_kernel<<<(MP + 1 + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, 1.f / (float)B, grad_out);
+    }
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+static long long coprime_step(long long n)
+{
+    long long a = (long long)(0.6180339887498949 * (double)n) | 1;
+    auto gcd = [](long long x, long long y) {
+        while (y) {
+            const long long t = x % y;
+            x = y;
+            y = t;
+        }
+        return x;
+    };
+    while (a > 1 && gcd(a, n) != 1) a += 2;
+    return a < 1 ? 1 : a;
+}
+
+static int sur_ensure_samples(wtmd_t* h, int64_t S)
+{
+    Surrogate& s = *h->sur;
+    if (S <= s.S) return WTMD_OK;
+    cudaFree(s.sx);
+    cudaFree(s.sV);
+    cudaFree(s.sG);
+    cudaFree(s.hV);
+    cudaFree(s.hG);
+    s.sx = nullptr;
+    s.sV = s.sG = s.hV = s.hG = nullptr;
+    s.S = 0;
+    WTMD_CUDA_TRY(h, cudaMalloc(&s.sx, sizeof(double) * 3 * S));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s.sV, sizeof(float) * S));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s.sG, sizeof(float) * 3 * S));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s.hV, sizeof(float) * (S / 10 + 1)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s.hG, sizeof(float) * 3 * (S / 10 + 1)));
+    s.S = S;
+    return WTMD_OK;
+}
+
+// Fit the network to the hills [0, K), K = count rounded down to a multiple
+// of 256, and switch the step path to network + exact tail if the held-out
+// error is within the tolerance (else to the exact sum).  Synchronizes.
+static int sur_fit(wtmd_t* h)
+{
+    Surrogate& s = *h->sur;
+    int rc;
+    long long count = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(&count, h->count, sizeof(count), cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const long long K = count / 256 * 256;
+    s.stats[0] = (double)K;
+    if (K < 512) {  // too few hills to be worth a network
+        s.stats[5] = 0.0;
+        set_int_kernel<<<1, 1, 0, h->stream>>>(s.active, 0);
+        set_ll_kernel<<<1, 1, 0, h->stream>>>(s.k0, 0);
+        s.next_fit = K + 512;
+        return WTMD_OK;
+    }
+    const int64_t S = std::max<int64_t>(10 * ((s.fit_samples + 9) / 10), 20);
+    if ((rc = sur_ensure_samples(h, S))) return rc;
+    const long long M = std::min<long long>(K, S);
+    set_ll_kernel<<<1, 1, 0, h->stream>>>(s.kend, K);
+    mlp_samples_kernel<<<(unsigned)((S + 255) / 256), 256, 0, h->stream>>>(
+        (const dbl4*)h->hills64, K, M, S, h->cfg.sigma[0], h->cfg.sigma[1], h->cfg.sigma[2], h->d, s.seed, s.round++,
+        s.sx);
+    WTMD_CUDA_TRY(h, cudaMemsetAsync(s.sG, 0, sizeof(float) * 3 * S, h->stream));
+    if ((rc = launch_hills_range(h, s.sx, true, 3, S, s.sV, s.sG, 3, nullptr, s.kend))) return rc;
+    const int64_t Str = S - S / 10, Sho = S / 10;
+    if (!s.have_norm) {
+        // input and output scales from the first training set; kept fixed
+        // afterwards so that later fits continue from the current weights
+        std::vector<double> hx(3 * S);
+        std::vector<float> hv(S);
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(hx.data(), s.sx, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(hv.data(), s.sV, sizeof(float) * S, cudaMemcpyDeviceToHost, h->stream));
+        WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        double nm[8] = {0, 0, 0, 1, 1, 1, 0, 1};
+        for (int k = 0; k < h->d; ++k) {
+            double m1 = 0.0, m2 = 0.0;
+            for (int64_t i = 0; i < S; ++i) m1 += hx[3 * i + k];
+            m1 /= (double)S;
+            for (int64_t i = 0; i < S; ++i) m2 += (hx[3 * i + k] - m1) * (hx[3 * i + k] - m1);
+            const double sd = std::sqrt(m2 / (double)S);
+            nm[k] = m1;
+            nm[3 + k] = sd > 0.0 ? 1.0 / sd : 1.0;
+        }
+        double v1 = 0.0, v2 = 0.0;
+        for (int64_t i = 0; i < S; ++i) v1 += hv[i];
+        v1 /= (double)S;
+        for (int64_t i = 0; i < S; ++i) v2 += (hv[i] - v1) * (hv[i] - v1);
+        nm[6] = v1;
+        nm[7] = v2 > 0.0 ? std::sqrt(v2 / (double)S) : 1.0;
+        std::memcpy(s.norm_h, nm, sizeof(nm));
+        WTMD_CUDA_TRY(h, cudaMemcpy(s.norm, nm, sizeof(nm), cudaMemcpyHostToDevice));
+        s.have_norm = true;
+    }
+    // Adam over batches of the training part, in a fixed pseudo-random order
+    const int B = (int)std::min<int64_t>(s.batch, Str);
+    const long long perm = coprime_step(Str);
+    WTMD_CUDA_TRY(h, cudaMemsetAsync(s.ctr + 1, 0, sizeof(long long), h->stream));
+    for (int64_t it = 0; it < s.fit_iters; ++it) {
+        // cosine decay from lr to lr/100 over the fit
+        const double c = 0.5 * (1.0 + std::cos(3.141592653589793 * (double)it / (double)s.fit_iters));
+        const double lr = s.lr * (0.01 + 0.99 * c);
+        if ((rc = launch_train(h, s.sx, s.sV, s.sG, Str, B, s.ctr + 1, perm, s.lam, true, lr, nullptr))) return rc;
+    }
+    // held-out error
+    const int nbe = (int)std::min<int64_t>((Sho + MLP_W - 1) / MLP_W, 4 * grad_blocks());
+    mlp_eval_kernel<<<std::max(nbe, 1), MLP_T, 0, h->stream>>>(s.wb, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
+                                                                (int)Sho, s.hV, s.hG, 3, 0);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    std::vector<float> pv(Sho), tv(Sho), pg(3 * Sho), tg(3 * Sho);
+    float L = 0.f;
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(pv.data(), s.hV, sizeof(float) * Sho, cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(tv.data(), s.sV + Str, sizeof(float) * Sho, cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(pg.data(), s.hG, sizeof(float) * 3 * Sho, cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(tg.data(), s.sG + 3 * Str, sizeof(float) * 3 * Sho, cudaMemcpyDeviceToHost,
+                                     h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(&L, s.loss, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double off = 0.0;
+    for (int64_t i = 0; i < Sho; ++i) off += (double)pv[i] - (double)tv[i];
+    off /= (double)std::max<int64_t>(Sho, 1);
+    double se = 0.0, mx = 0.0, ge = 0.0, gn = 0.0;
+    for (int64_t i = 0; i < Sho; ++i) {
+        const double e = (double)pv[i] - (double)tv[i] - off;
+        se += e * e;
+        mx = std::max(mx, std::fabs(e));
+        for (int k = 0; k < h->d; ++k) {
+            const double g = (double)pg[3 * i + k] - (double)tg[3 * i + k];
+            ge += g * g;
+            gn += (double)tg[3 * i + k] * (double)tg[3 * i + k];
+        }
+    }
+    const double kT = h->cfg.kT;
+    const double rms = std::sqrt(se / (double)std::max<int64_t>(Sho, 1)) / kT;
+    const bool ok = std::isfinite(rms) && rms <= s.tol;
+    s.stats[1] = rms;
+    s.stats[2] = mx / kT;
+    s.stats[3] = gn > 0.0 ? std::sqrt(ge / gn) : 0.0;
+    s.stats[4] = L;
+    s.stats[5] = ok ? 1.0 : 0.0;
+    s.stats[6] += 1.0;
+    s.stats[7] += (double)s.fit_iters;
+    set_int_kernel<<<1, 1, 0, h->stream>>>(s.active, ok ? 1 : 0);
+    set_ll_kernel<<<1, 1, 0, h->stream>>>(s.k0, ok ? K : 0);
+    s.next_fit = K + std::max<int64_t>(s.every, 256);
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return WTMD_OK;
+}
+
+// Host mirrors of the step and hill counters, used to schedule refits
+// without reading the device every step.
+static int sur_sync_counters(wtmd_t* h)
+{
+    Surrogate& s = *h->sur;
+    long long c[2];
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(&c[0], h->step, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaMemcpyAsync(&c[1], h->count, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    s.host_step = c[0];
+    s.host_count = c[1];
+    return WTMD_OK;
+}
+
+// Steps (>= 1) until the hill count reaches `target`, given the deposit
+// schedule (after step t when (t + 1) % stride == 0, W hills each time).
+static int64_t steps_until(const wtmd_t* h, long long target)
+{
+    const Surrogate& s = *h->sur;
+    const long long st = h->cfg.stride;
+    if (st <= 0 || target <= s.host_count) return 1;
+    const long long q = (target - s.host_count + h->W - 1) / h->W;  // deposits needed
+    const long long m0 = s.host_step / st + 1;                     // first deposit event index ahead
+    return (int64_t)(st * (m0 + q - 1) - s.host_step);
+}
+
+static void advance_counters(wtmd_t* h, int64_t n)
+{
+    Surrogate& s = *h->sur;
+    const long long st = h->cfg.stride;
+    if (st > 0) {
+        const long long ev = (s.host_step + n) / st - s.host_step / st;
+        s.host_count = std::min<long long>(s.host_count + ev * h->W, h->cap);
+    }
+    s.host_step += n;
+}
+
+// Called by step_n: how many of the n steps to run before the next refit
+// (refitting first when one is due).
+int surrogate_segment(wtmd_t* h, int64_t n, int64_t* seg)
+{
+    *seg = n;
+    if (!h->sur || !h->sur->enabled || h->sur->every <= 0) return WTMD_OK;
+    Surrogate& s = *h->sur;
+    if (s.host_count >= s.next_fit) {
+        int rc = sur_fit(h);
+        if (rc) return rc;
+        if ((rc = sur_sync_counters(h))) return rc;
+    }
+    *seg = std::max<int64_t>(1, std::min<int64_t>(n, steps_until(h, s.next_fit)));
+    return WTMD_OK;
+}
+
+void surrogate_advanced(wtmd_t* h, int64_t n)
+{
+    if (h->sur && h->sur->enabled) advance_counters(h, n);
+}
+
+// The hill list was replaced: the fitted range no longer applies.
+int surrogate_invalidate(wtmd_t* h)
+{
+    if (!h->sur) return WTMD_OK;
+    Surrogate& s = *h->sur;
+    set_int_kernel<<<1, 1, 0, h->stream>>>(s.active, 0);
+    set_ll_kernel<<<1, 1, 0, h->stream>>>(s.k0, 0);
+    s.stats[5] = 0.0;
+    if (!s.enabled) return WTMD_OK;
+    int rc = sur_sync_counters(h);
+    if (rc) return rc;
+    s.next_fit = s.every > 0 ? s.host_count : (1ll << 62);
+    return WTMD_OK;
+}
+
+}  // namespace wtmd
+
+using namespace wtmd;
+
+#define SFAIL(h, code, msg) \
+    do {                    \
+        (h)->err = (msg);   \
+        return (code);      \
+    } while (0)
+
+extern "C" int wtmd_surrogate(wtmd_t* h, int32_t enable, double tol_kT, int64_t retrain_every)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!enable) {
+        if (h->sur && h->sur->enabled) {
+            h->sur->enabled = false;
+            set_int_kernel<<<1, 1, 0, h->stream>>>(h->sur->active, 0);
+            set_ll_kernel<<<1, 1, 0, h->stream>>>(h->sur->k0, 0);
+            drop_step_graphs(h);
+        }
+        return WTMD_OK;
+    }
+    if (!(tol_kT > 0.0) || retrain_every < 0) SFAIL(h, WTMD_EINVAL, "tolerance must be > 0, retrain_every >= 0");
+    if (h->persistent) SFAIL(h, WTMD_EINVAL, "the surrogate is not available with the persistent walker step");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    s->tol = tol_kT;
+    s->every = retrain_every;
+    if (!s->enabled) {
+        s->enabled = true;
+        drop_step_graphs(h);
+    }
+    if ((rc = sur_sync_counters(h))) return rc;
+    s->next_fit = s->host_count;  // fit at the next step_n (or now, by wtmd_surrogate_fit)
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_surrogate_config(wtmd_t* h, int64_t n_samples, int64_t iters, int64_t batch, double lr,
+                                     double lambda)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_samples < 20 || iters < 0 || batch < 1 || !(lr > 0.0) || !(lambda >= 0.0))
+        SFAIL(h, WTMD_EINVAL, "bad surrogate training parameters");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    s->fit_samples = n_samples;
+    s->fit_iters = iters;
+    s->batch = batch;
+    s->lr = lr;
+    s->lam = lambda;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_surrogate_fit(wtmd_t* h, double* stats)
+{
+    if (!h) return WTMD_EINVAL;
+    if (h->ncv != h->d) SFAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    if ((rc = sur_fit(h))) return rc;
+    if (s->enabled && (rc = sur_sync_counters(h))) return rc;
+    if (stats) std::memcpy(stats, s->stats, sizeof(s->stats));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_surrogate_status(wtmd_t* h, double* stats)
+{
+    if (!h || !stats) return WTMD_EINVAL;
+    if (!h->sur) {
+        for (int i = 0; i < 8; ++i) stats[i] = 0.0;
+        return WTMD_OK;
+    }
+    std::memcpy(stats, h->sur->stats, sizeof(h->sur->stats));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_surrogate_set(wtmd_t* h, int64_t k0, int32_t active)
+{
+    if (!h) return WTMD_EINVAL;
+    if (k0 < 0 || k0 % 256 || k0 > h->cap) SFAIL(h, WTMD_EINVAL, "k0 must be a multiple of 256 within capacity");
+    if (h->persistent) SFAIL(h, WTMD_EINVAL, "the surrogate is not available with the persistent walker step");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    if (!s->enabled) {
+        s->enabled = true;
+        drop_step_graphs(h);
+    }
+    s->every = 0;  // no refits: the caller owns the network
+    set_int_kernel<<<1, 1, 0, h->stream>>>(s->active, active ? 1 : 0);
+    set_ll_kernel<<<1, 1, 0, h->stream>>>(s->k0, active ? k0 : 0);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_mlp_params(wtmd_t* h, const float* in, float* out, const double* norm_in, double* norm_out)
+{
+    if (!h) return WTMD_EINVAL;
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (in) {
+        WTMD_CUDA_TRY(h, cudaMemcpy(s->master, in, sizeof(float) * MP, cudaMemcpyHostToDevice));
+        WTMD_CUDA_TRY(h, cudaMemset(s->m, 0, sizeof(float) * MP));
+        WTMD_CUDA_TRY(h, cudaMemset(s->v, 0, sizeof(float) * MP));
+        WTMD_CUDA_TRY(h, cudaMemset(s->ctr, 0, sizeof(long long) * 2));
+        mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb);
+        WTMD_CUDA_TRY(h, cudaDeviceSynchronize());
+    }
+    if (norm_in) {
+        if (!(norm_in[7] != 0.0) || !std::isfinite(norm_in[7])) SFAIL(h, WTMD_EINVAL, "Vs must be finite and nonzero");
+        std::memcpy(s->norm_h, norm_in, sizeof(s->norm_h));
+        s->have_norm = true;
+        WTMD_CUDA_TRY(h, cudaMemcpy(s->norm, norm_in, sizeof(double) * 8, cudaMemcpyHostToDevice));
+    }
+    if (out) WTMD_CUDA_TRY(h, cudaMemcpy(out, s->master, sizeof(float) * MP, cudaMemcpyDeviceToHost));
+    if (norm_out) std::memcpy(norm_out, s->norm_h, sizeof(s->norm_h));
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_mlp_eval(wtmd_t* h, const double* xi, int64_t P, float* V, float* dV)
+{
+    if (!h) return WTMD_EINVAL;
+    if (P < 0 || P > (1 << 30) || (P > 0 && !xi)) SFAIL(h, WTMD_EINVAL, "bad points");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    if (P == 0) return WTMD_OK;
+    // each block stages the network once: a few blocks per SM, points by grid stride
+    const int nb = (int)std::min<int64_t>((P + MLP_W - 1) / MLP_W, grad_blocks());
+    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s->wb, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_mlp_grad(wtmd_t* h, const double* xi, const float* V, const float* dV, int64_t B, double lambda,
+                             float* grad_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (B < 1 || B > (1 << 30) || !xi || !V || !dV || !grad_out || !(lambda >= 0.0))
+        SFAIL(h, WTMD_EINVAL, "bad batch");
+    if (h->d != 3 && h->d != 2 && h->d != 1) SFAIL(h, WTMD_EINVAL, "bad CV count");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    return launch_train(h, xi, V, dV, B, (int)B, nullptr, 1, lambda, false, 0.0, grad_out);
+}
+
+extern "C" int wtmd_mlp_train(wtmd_t* h, const double* xi, const float* V, const float* dV, int64_t n, int64_t B,
+                              int64_t iters, double lr, double lambda, float* loss_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n < 1 || B < 1 || B > n || iters < 0 || !xi || !V || !dV || !(lr > 0.0) || !(lambda >= 0.0))
+        SFAIL(h, WTMD_EINVAL, "bad training arguments");
+    Surrogate* s = nullptr;
+    int rc = sur_get(h, &s);
+    if (rc) return rc;
+    WTMD_CUDA_TRY(h, cudaMemsetAsync(s->ctr + 1, 0, sizeof(long long), h->stream));
+    for (int64_t it = 0; it < iters; ++it)
+        if ((rc = launch_train(h, xi, V, dV, n, (int)B, s->ctr + 1, 1, lambda, true, lr, nullptr))) return rc;
+    if (loss_out) WTMD_CUDA_TRY(h, cudaMemcpyAsync(loss_out, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return WTMD_OK;
+}

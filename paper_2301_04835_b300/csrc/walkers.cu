@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
         const int tiles = (a.W + WK_T - 1) / WK_T;
         bool fresh = true;
         for (int task = blockIdx.x; task < tiles * a.hsplit; task += G) {
-            if (!hills_f32_task<D, 1, false, double>(a.hp, a.cnt, a.xi, 4, a.W, a.ctr, a.hprm, a.hpart, a.status,
+            if (!hills_f32_task<D, 1, false, double>(a.hp, nullptr, a.cnt, a.xi, 4, a.W, a.ctr, a.hprm, a.hpart, a.status,
                                                      task / a.hsplit, task % a.hsplit, a.hsplit, ring, hbar, fresh))
                 return;
             fresh = false;

@@ -228,6 +228,8 @@ struct Tuned {
     int split = 0;    // hill splits
 };
 
+struct Surrogate;  // MLP surrogate of the hills sum (mlp.cu)
+
 // Plan of the persistent multi-walker step (walkers.cu).
 struct WalkerPlan {
     int T = 0;             // targets per pair task
@@ -311,6 +313,7 @@ struct wtmd_t {
     bool persistent = false;        // multi-walker step as one persistent launch
     wtmd::WalkerPlan wk;
     bool no_graph = false;          // capture failed: replay eagerly
+    wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
     // profiling: when `prof` is set, mark() records a CUDA event on the
@@ -349,7 +352,18 @@ int walkers_enable(wtmd_t* h);
 int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult);
 int launch_walkers_step(wtmd_t* h, int mode);                   // 0: full step, 1: forces only
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
+// hills [*k0p, *k1p) (k0p may be null: 0; *k0p a multiple of 256; FP32 handles)
+int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
+                       int dV_stride, const long long* k0p, const long long* k1p);
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
+// surrogate (mlp.cu)
+void surrogate_free(Surrogate* s);
+const long long* surrogate_k0(const wtmd_t* h);                 // first hill of the exact tail, or null
+int launch_mlp_add(wtmd_t* h);                                   // V, dV += network part (if active)
+int surrogate_segment(wtmd_t* h, int64_t n, int64_t* seg);       // refit if due; steps until the next refit
+void surrogate_advanced(wtmd_t* h, int64_t n);
+int surrogate_invalidate(wtmd_t* h);
+void drop_step_graphs(wtmd_t* h);                                // api.cu
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
 int launch_baoab_first(wtmd_t* h);
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++

@@ -16,7 +16,7 @@ def oracle_system(spec):
                 nn=c.get("nn", 6), mm=c.get("mm", 12), scale=c.get("scale", 0.0), flags=c.get("flags", 0),
                 period=c.get("period", 0.0)) for c in spec["cvs"]]
     grid = spec.get("grid")
-    kw = dict(engine={"none": 0, "mb": 1, "lj": 2, "chain": 3}[spec.get("engine", "none")],
+    kw = dict(engine={"none": 0, "mb": 1, "lj": 2, "chain": 3, "wells3": 5}[spec.get("engine", "none")],
               walker_n=list(spec["walker_sizes"]), cvs=cvs, dims=spec.get("dims", 3), box=tuple(spec.get("box", (0, 0, 0))),
               dt=spec.get("dt", 1e-3), friction=spec.get("friction", 1.0), mass=spec.get("mass", 1.0),
               kT=spec.get("kT", 1.0), seed=spec.get("seed", 0), sigma=tuple(spec["sigma"]), w0=spec.get("w0", 1.0),

@@ -425,3 +425,25 @@ def test_mueller_brown_free_energy_recovered_within_half_kT():
     d -= d.mean()
     assert np.abs(d).max() < 0.5 * kT
     assert np.sqrt(np.mean(d ** 2)) < 0.25 * kT
+
+
+def test_three_well_landscape_force_and_minima():
+    """The three-well landscape: force = -grad U by central differences, and
+    a local minimum near each well centre, lower than the saddle region."""
+    import oracle as o
+
+    r = np.array([0.3, -0.2, 0.4])
+    h = 1e-6
+    u, f = o.wells3(r)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = -(o.wells3(r + e)[0] - o.wells3(r - e)[0]) / (2 * h)
+        assert abs(fd - f[k]) < 1e-7 * max(1.0, abs(f[k]))
+    for c in ([-1.0, 0.0, 0.0], [1.0, 0.2, -0.3], [0.1, 1.3, 0.6]):
+        x = np.array(c, float)
+        for _ in range(2000):  # steepest descent
+            x = x + 0.01 * o.wells3(x)[1]
+        assert np.linalg.norm(o.wells3(x)[1]) < 1e-6
+        assert np.linalg.norm(x - np.array(c)) < 0.5
+        assert o.wells3(x)[0] < o.wells3((x + np.zeros(3)) * 0.0 + np.array([0.0, 0.5, 0.0]))[0]
