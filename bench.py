@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-walkers", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -160,6 +161,151 @@ def walkers_bench(wt, torch, dev, flush, steps):
         r["steps_per_s_l2_flushed"] = timed(m, max(steps // 4, 10), flushed=True)
         out[mode] = r
         m.close()
+    return out
+
+
+# learned surrogate: LJ N=32768 (rho*=0.8) with three CVs (coordination of
+# 512 tagged atoms, Rg of 64 atoms, fraction of native pairs of a 1024-atom
+# subset), 1e6 hills from a well-tempered run of 2048 walkers on the
+# three-well landscape, mapped affinely into the CV space around the
+# system's CVs
+N_SU, SU_SIGMA, H_SU = 32768, (0.05, 0.1, 0.02), 1_000_000
+SU_WORKLOAD = ("LJ N=32768 rho*=0.8 T*=1 cell list dt=0.005; CVs: coordination of 512 tagged atoms (r0=1.5, "
+               "n=6, m=12), Rg of 64 atoms, fraction of native pairs (r<1.5 at t=0) of a 1024-atom subset; "
+               "sigma=(0.05,0.1,0.02); 1e6 hills from a well-tempered run (2048 walkers, gamma=3, w0=0.05 kT) "
+               "on a three-well landscape, mapped into the CV space; FP32; MLP 3-64-64-1 SiLU, bf16 weights")
+
+
+def wells3_hills(wt, torch, H=H_SU, W=2048, sigma=0.4, w0=0.05, gamma=3.0, seed=5):
+    """H hills of a well-tempered run of W walkers on the three-well
+    landscape (CVs x, y, z), made by the library; returns [H][4] host."""
+    import synth
+
+    m = wt.Wtmd(precision="f32", sigma=(sigma,) * 3, w0=w0, gamma=gamma, kT=1.0, stride=10, capacity=H + W,
+                seed=seed, engine="wells3", walker_sizes=[1] * W, dims=3, dt=5e-3, friction=1.0)
+    for k in range(3):
+        m.cv_define(wt.CV_COMPONENT, a=[0], axis=k)
+    centres = np.array([[-1, 0, 0], [1, 0.2, -0.3], [0.1, 1.3, 0.6]])
+    x = synth.rng(1).normal(scale=0.3, size=(W, 3)) + centres[np.arange(W) % 3]
+    pos, vel = wt.particles(x, torch.float32), wt.particles(np.zeros_like(x), torch.float32)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(((H + W - 1) // W) * 10)
+    h = m.hills_read()[:H]
+    m.close()
+    return h, sigma
+
+
+def surrogate_bench(wt, torch, dev, flush, steps):
+    """Exact hills sum vs network + exact tail at 1e6 hills: bias-force
+    evaluations and MD steps of the 32768-atom system, and the batched form
+    (4096 points)."""
+    import synth
+
+    x, L = synth.lattice(N_SU, 0.8, seed=3, jitter=0.05)
+    v = synth.velocities(N_SU, 1.0, 1.0, seed=4)
+    tag = synth.permutation_subset(N_SU, 512, 5)
+    rg = synth.nearest_subset(x, L, 64, 6)
+    sub = synth.nearest_subset(x, L, 1024, 7)
+    pairs = synth.native_pairs(x, L, sub, 1.5)
+    stream = torch.cuda.current_stream()
+
+    def handle(cap):
+        m = wt.Wtmd(precision="f32", sigma=SU_SIGMA, w0=0.05, gamma=3.0, kT=1.0, stride=100, capacity=cap, seed=0,
+                    engine="lj", walker_sizes=[N_SU], box=(L, L, L), dt=0.005, friction=1.0)
+        m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+        m.cv_define(wt.CV_RG, a=rg)
+        m.cv_define(wt.CV_QPAIRS, a=pairs, r0=1.5, nn=6, mm=12)
+        return m
+
+    m = handle(16)
+    _, xi0, _ = m.bias_eval(wt.particles(x, torch.float32))
+    xi0 = xi0[0].double().cpu().numpy()
+    m.close()
+    t0 = time.perf_counter()
+    hw, sw = wells3_hills(wt, torch)
+    gen_s = time.perf_counter() - t0
+    hills = hw.copy()
+    hills[:, :3] = xi0[None, :] + hw[:, :3] * (np.asarray(SU_SIGMA) / sw)[None, :]
+    out = {"workload": SU_WORKLOAD, "atoms": N_SU, "hills": int(hills.shape[0]), "native_pairs": int(len(pairs) // 2),
+           "hill_generation_s": gen_s}
+
+    def evals_per_s(m, pos, reps):
+        for _ in range(3):
+            m.bias_eval(pos)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            m.bias_eval(pos)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return reps / (a.elapsed_time(b) * 1e-3)
+
+    def steps_per_s(m, K):
+        m.step_n(5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.step_n(K, check=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        return K / (a.elapsed_time(b) * 1e-3)
+
+    res = {}
+    for mode in ("exact", "surrogate"):
+        m = handle(hills.shape[0] + 4096)
+        m.hills_load(hills)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        r = {}
+        if mode == "surrogate":
+            m.surrogate(True, tol_kT=0.05, retrain_every=10000)
+            t0 = time.perf_counter()
+            st = m.surrogate_fit()
+            r["fit_s"] = time.perf_counter() - t0
+            r["fit"] = st
+        r["bias_force_evals_per_s"] = evals_per_s(m, pos, 200)
+        r["steps_per_s"] = steps_per_s(m, steps)
+        res[mode] = r
+        if mode == "surrogate":
+            # batched form: 4096 CV points, exact sum vs network
+            rr = synth.rng(9)
+            P = 4096
+            pts = hills[rr.integers(0, hills.shape[0], P), :3] + np.asarray(SU_SIGMA) * rr.normal(size=(P, 3))
+            x64 = torch.tensor(pts, device=dev)
+            x32 = x64.float()
+            Ve = torch.empty(P, dtype=torch.float32, device=dev)
+            dVe = torch.empty(P, 3, dtype=torch.float32, device=dev)
+
+            def tm(fn, reps=20):
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                return a.elapsed_time(b) / reps
+
+            te = tm(lambda: m.hills_eval_into(x32, Ve, dVe))
+            tn = tm(lambda: m.mlp_eval(x64))
+            Vn, _ = m.mlp_eval(x64)
+            e = (Vn.double() - Ve.double()).cpu().numpy()
+            e -= e.mean()
+            out["batched_4096"] = {"exact_ms": te, "mlp_ms": tn, "exact_bias_evals_per_s": P / (te * 1e-3),
+                                   "mlp_bias_evals_per_s": P / (tn * 1e-3), "speedup": te / tn,
+                                   "exact_hill_evals_per_s": P * hills.shape[0] / (te * 1e-3),
+                                   "rms_err_kT_fresh_points": float(np.sqrt(np.mean(e ** 2))),
+                                   "max_err_kT_fresh_points": float(np.abs(e).max())}
+        m.close()
+    out.update(res)
+    out["bias_force_speedup"] = res["surrogate"]["bias_force_evals_per_s"] / res["exact"]["bias_force_evals_per_s"]
+    out["step_speedup"] = res["surrogate"]["steps_per_s"] / res["exact"]["steps_per_s"]
     return out
 
 
@@ -363,7 +509,8 @@ def run_ours(args, rank, world):
 
     micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
     walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
-    return dict(walkers=walkers, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    sur = None if args.no_surrogate else surrogate_bench(wt, torch, dev, flush, args.steps)
+    return dict(walkers=walkers, surrogate=sur, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
 
@@ -478,6 +625,7 @@ def main():
         "kernels_ms": {k: round(v, 5) for k, v in prof},
         "hills_sum_1e6": r["micro"],
         "walkers_256_clusters": r["walkers"],
+        "surrogate_1e6_hills": r["surrogate"],
     }
     if not args.no_cpu_baseline and world == 1:
         n, times, cores = cpu_baseline_oracle(seconds=15.0)

@@ -63,7 +63,8 @@ void drop_step_graphs(wtmd_t* h) { drop_graphs(h); }
 // network's part when the surrogate is active.
 static int launch_bias_sum(wtmd_t* h)
 {
-    int rc = launch_hills_range(h, h->xi, true, 4, h->W, h->V, h->dV, 4, surrogate_k0(h), h->count);
+    int rc = launch_hills_range(h, h->xi, true, 4, h->W, h->V, h->dV, 4, surrogate_k0(h), h->count,
+                                surrogate_tail_bound(h));
     if (rc) return rc;
     return launch_mlp_add(h);
 }

@@ -23,6 +23,8 @@
 //     and the hill-range splits are reduced in a fixed order by the CTA that
 //     finishes last (one launch, deterministic, no CTA waits for another).
 // FP64 path: the same sum in double with exp(), for parity at 1e-12.
+#include <algorithm>
+
 #include "hills_dev.cuh"
 
 namespace wtmd {
@@ -258,20 +260,22 @@ int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
 
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs)
 {
-    return launch_hills_range(h, xi, xi_f64, xs, P, V, dV, dvs, nullptr, h->count);
+    return launch_hills_range(h, xi, xi_f64, xs, P, V, dV, dvs, nullptr, h->count, 0);
 }
 
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs,
-                       const long long* k0p, const long long* k1p)
+                       const long long* k0p, const long long* k1p, long long max_hills)
 {
+    // the plan's split covers at most max_hills hills (0: the capacity)
+    const long long cap_pairs = max_hills > 0 ? std::min<long long>(h->cap_pairs, (max_hills + 1) / 2) : h->cap_pairs;
     if (P <= 0) return WTMD_OK;
     if (P > (1ll << 30)) {
         h->err = "hills: too many points";
         return WTMD_EINVAL;
     }
-    Plan pl = plan_for(P, h->cap_pairs);
+    Plan pl = plan_for(P, cap_pairs);
     for (auto& t : h->tuned)
-        if (t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
+        if (max_hills <= 0 && t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
     if (hills_plan_override_th) pl.th = hills_plan_override_th;
     if (hills_plan_override_split) pl.split = hills_plan_override_split;
     const int tp = HB / pl.th;

@@ -53,9 +53,12 @@ constexpr int MLP_W = MLP_T / 32;
 constexpr int RW2P = 65;    // pitch of the transposed W2 gradient in the block reduction
 constexpr int RED_N = O_W2 + MH * RW2P + (MP - O_B2) + 1;  // + loss
 
+struct MlpW;
+
 struct Surrogate {
     float* master = nullptr;        // [MP] FP32 master weights
-    unsigned short* wb = nullptr;   // [MP] bfloat16 bits used by the kernels
+    unsigned short* wb = nullptr;   // [MP] bfloat16 bits of the weights
+    MlpW* img = nullptr;            // the same weights as the kernels' FP32 image
     float* m = nullptr;             // Adam moments [MP]
     float* v = nullptr;
     double* norm = nullptr;         // device [8]: mu[3], inv_s[3], Vm, Vs
@@ -110,33 +113,34 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// The network as the kernels read it: FP32 values of the bfloat16 weights
+// in a padded layout.  A copy of this image lives in global memory (kept in
+// step with the weights) so that a block stages it with plain 16-byte loads.
 struct MlpW {
     float W2[MH][W2P];
-    float W1[MH][4];
+    float W1[MH][4];  // column 3 is 0
     float b1[MH], b2[MH], w3[MH];
     float b3;
+    float pad[3];
 };
+static_assert(sizeof(MlpW) % 16 == 0, "image copied in 16-byte pieces");
 
-__device__ void mlp_stage(const unsigned short* __restrict__ wb, MlpW& s)
+// Parameter q (flat order W1, b1, W2, b2, w3, b3) -> its slot in the image.
+__device__ __forceinline__ float* img_slot(MlpW* s, int q)
 {
-    for (int q = threadIdx.x; q < MP; q += blockDim.x) {
-        const float v = bf16_bits_to_f(wb[q]);
-        if (q < O_B1) {
-            s.W1[q / 3][q % 3] = v;
-        } else if (q < O_W2) {
-            s.b1[q - O_B1] = v;
-        } else if (q < O_B2) {
-            const int r = q - O_W2;
-            s.W2[r / MH][r % MH] = v;
-        } else if (q < O_W3) {
-            s.b2[q - O_B2] = v;
-        } else if (q < O_B3) {
-            s.w3[q - O_W3] = v;
-        } else {
-            s.b3 = v;
-        }
-    }
-    for (int j = threadIdx.x; j < MH; j += blockDim.x) s.W1[j][3] = 0.f;
+    if (q < O_B1) return &s->W1[q / 3][q % 3];
+    if (q < O_W2) return &s->b1[q - O_B1];
+    if (q < O_B2) return &s->W2[(q - O_W2) / MH][(q - O_W2) % MH];
+    if (q < O_W3) return &s->b2[q - O_B2];
+    if (q < O_B3) return &s->w3[q - O_W3];
+    return &s->b3;
+}
+
+__device__ void mlp_stage(const MlpW* __restrict__ img, MlpW& s)
+{
+    const float4* src = reinterpret_cast<const float4*>(img);
+    float4* dst = reinterpret_cast<float4*>(&s);
+    for (int q = threadIdx.x; q < (int)(sizeof(MlpW) / 16); q += blockDim.x) dst[q] = src[q];
 }
 
 struct Fwd {
@@ -212,17 +216,17 @@ __device__ __forceinline__ float silu_dd(float z)
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const unsigned short* __restrict__ wb,
+__global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const MlpW* __restrict__ img,
                                                          const double* __restrict__ norm, const int* __restrict__ active,
                                                          const double* __restrict__ xi, int xs, int d, int P,
                                                          float* __restrict__ V, float* __restrict__ dV, int dvs,
                                                          int add)
 {
     if (active && *active == 0) return;
-    __shared__ MlpW s;
+    __shared__ __align__(16) MlpW s;
     __shared__ __align__(16) float A1[MLP_W][MH];
     __shared__ __align__(16) float G2[MLP_W][MH];
-    mlp_stage(wb, s);
+    mlp_stage(img, s);
     __syncthreads();
     const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
     for (int p = blockIdx.x * MLP_W + w; p < P; p += gridDim.x * MLP_W) {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const unsigned short* _
 }
 
 struct TrainArgs {
-    const unsigned short* wb;
+    const MlpW* img;
     const double* norm;
     const double* x;        // samples [n][3] (CV units; unused dimensions 0)
     const float* V;         // [n]
@@ -260,12 +264,12 @@ struct TrainArgs {
 
 __global__ void __launch_bounds__(MLP_T, 2) mlp_grad_kernel(TrainArgs a)
 {
-    __shared__ MlpW s;
+    __shared__ __align__(16) MlpW s;
     __shared__ __align__(16) float A1[MLP_W][MH];
     __shared__ __align__(16) float G2[MLP_W][MH];
     __shared__ __align__(16) float HB[MLP_W][MH];
     __shared__ __align__(16) float Z2[MLP_W][MH];
-    mlp_stage(a.wb, s);
+    mlp_stage(a.img, s);
     __syncthreads();
     const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * MLP_W + w, nw = gridDim.x * MLP_W;
@@ -417,7 +421,7 @@ struct AdamPrm {
 
 __global__ void mlp_adam_kernel(const float* __restrict__ partial, int nblk, float* __restrict__ master,
                                 float* __restrict__ m, float* __restrict__ v, unsigned short* __restrict__ wb,
-                                AdamPrm p, long long* __restrict__ ctr, unsigned* __restrict__ ticket,
+                                MlpW* __restrict__ img, AdamPrm p, long long* __restrict__ ctr, unsigned* __restrict__ ticket,
                                 float* __restrict__ loss_out)
 {
     const long long t = ctr[0] + 1;
@@ -433,7 +437,9 @@ __global__ void mlp_adam_kernel(const float* __restrict__ partial, int nblk, flo
         master[q] = th;
         m[q] = mm;
         v[q] = vv;
-        wb[q] = f_to_bf16_bits(th);
+        const unsigned short b = f_to_bf16_bits(th);
+        wb[q] = b;
+        *img_slot(img, q) = bf16_bits_to_f(b);
     }
     // the last block advances the counters (every block has read them)
     __shared__ int lastb;
@@ -453,10 +459,15 @@ __global__ void mlp_adam_kernel(const float* __restrict__ partial, int nblk, flo
     }
 }
 
-__global__ void mlp_round_kernel(const float* __restrict__ master, unsigned short* __restrict__ wb)
+__global__ void mlp_round_kernel(const float* __restrict__ master, unsigned short* __restrict__ wb,
+                                 MlpW* __restrict__ img)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < MP) wb[q] = f_to_bf16_bits(master[q]);
+    if (q < MP) {
+        const unsigned short b = f_to_bf16_bits(master[q]);
+        wb[q] = b;
+        *img_slot(img, q) = bf16_bits_to_f(b);
+    }
 }
 
 // Training points: jittered copies of the most recent M hill centres of
@@ -504,7 +515,7 @@ static uint64_t splitmix(uint64_t& s)
 void surrogate_free(Surrogate* s)
 {
     if (!s) return;
-    void* p[] = {s->master, s->wb, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr, s->ticket,
+    void* p[] = {s->master, s->wb, s->img, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr, s->ticket,
                  s->partial, s->loss, s->grad, s->sx, s->sV, s->sG, s->hV, s->hG};
     for (void* q : p) cudaFree(q);
     delete s;
@@ -525,6 +536,8 @@ static int sur_get(wtmd_t* h, Surrogate** out)
     h->sur = s;
     WTMD_CUDA_TRY(h, cudaMalloc(&s->master, sizeof(float) * MP));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->wb, sizeof(unsigned short) * MP));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->img, sizeof(MlpW)));
+    WTMD_CUDA_TRY(h, cudaMemset(s->img, 0, sizeof(MlpW)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->m, sizeof(float) * MP));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->v, sizeof(float) * MP));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->norm, sizeof(double) * 8));
@@ -552,13 +565,23 @@ static int sur_get(wtmd_t* h, Surrogate** out)
     WTMD_CUDA_TRY(h, cudaMemset(s->k0, 0, sizeof(long long)));
     WTMD_CUDA_TRY(h, cudaMemset(s->active, 0, sizeof(int)));
     WTMD_CUDA_TRY(h, cudaMemcpy(s->norm, s->norm_h, sizeof(double) * 8, cudaMemcpyHostToDevice));
-    mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb);
+    mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb, s->img);
     WTMD_CUDA_TRY(h, cudaDeviceSynchronize());
     *out = s;
     return WTMD_OK;
 }
 
 const long long* surrogate_k0(const wtmd_t* h) { return h->sur && h->sur->enabled ? h->sur->k0 : nullptr; }
+
+// With refits every `every` hills the exact tail never exceeds every + W
+// hills (+ one deposit of slack); while the network is inactive k0 = 0 and
+// the whole list is summed, which the plan must also cover, so the bound
+// applies only once a fit made the network active.
+long long surrogate_tail_bound(const wtmd_t* h)
+{
+    if (!h->sur || !h->sur->enabled || h->sur->every <= 0 || h->sur->stats[5] == 0.0) return 0;
+    return h->sur->every + 2ll * h->W + 256;
+}
 
 // Step path: V += V_nn, dV += dV_nn at the walkers' CVs when the surrogate
 // is active (the kernel returns at once otherwise).
@@ -567,7 +590,7 @@ int launch_mlp_add(wtmd_t* h)
     if (!h->sur || !h->sur->enabled) return WTMD_OK;
     Surrogate& s = *h->sur;
     const int nb = std::max(1, std::min((h->W + MLP_W - 1) / MLP_W, 2 * grad_blocks()));
-    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s.wb, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
+    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s.img, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
                                                  (float*)h->dV, 4, 1);
     mark(h, "mlp_surrogate");
     WTMD_CUDA_TRY(h, cudaGetLastError());
@@ -578,14 +601,14 @@ static int launch_train(wtmd_t* h, const double* x, const float* V, const float*
                         const long long* iter, long long perm, double lam, bool adam, double lr, float* grad_out)
 {
     Surrogate& s = *h->sur;
-    TrainArgs a{s.wb, s.norm, x, V, G, n, B, iter, perm, h->d, (float)lam, s.partial};
+    TrainArgs a{s.img, s.norm, x, V, G, n, B, iter, perm, h->d, (float)lam, s.partial};
     const int nb = std::max(1, std::min(s.pblocks, (B + MLP_W - 1) / MLP_W));
     mlp_grad_kernel<<<nb, MLP_T, 0, h->stream>>>(a);
     mark(h, "mlp_grad");
     if (adam) {
         AdamPrm p{(float)lr, 0.9f, 0.999f, 1e-8f, 1.f / (float)B};
-        mlp_adam_kernel<<<(MP + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, s.master, s.m, s.v, s.wb, p, s.ctr,
-                                                                 s.ticket, s.loss);
+        mlp_adam_kernel<<<(MP + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, s.master, s.m, s.v, s.wb, s.img, p,
+                                                                 s.ctr, s.ticket, s.loss);
         mark(h, "mlp_adam");
     } else {
         mlp_reduce_kernel<<<(MP + 1 + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, 1.f / (float)B, grad_out);
@@ -657,7 +680,7 @@ static int sur_fit(wtmd_t* h)
         (const dbl4*)h->hills64, K, M, S, h->cfg.sigma[0], h->cfg.sigma[1], h->cfg.sigma[2], h->d, s.seed, s.round++,
         s.sx);
     WTMD_CUDA_TRY(h, cudaMemsetAsync(s.sG, 0, sizeof(float) * 3 * S, h->stream));
-    if ((rc = launch_hills_range(h, s.sx, true, 3, S, s.sV, s.sG, 3, nullptr, s.kend))) return rc;
+    if ((rc = launch_hills_range(h, s.sx, true, 3, S, s.sV, s.sG, 3, nullptr, s.kend, 0))) return rc;
     const int64_t Str = S - S / 10, Sho = S / 10;
     if (!s.have_norm) {
         // input and output scales from the first training set; kept fixed
@@ -699,7 +722,7 @@ static int sur_fit(wtmd_t* h)
     }
     // held-out error
     const int nbe = (int)std::min<int64_t>((Sho + MLP_W - 1) / MLP_W, 4 * grad_blocks());
-    mlp_eval_kernel<<<std::max(nbe, 1), MLP_T, 0, h->stream>>>(s.wb, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
+    mlp_eval_kernel<<<std::max(nbe, 1), MLP_T, 0, h->stream>>>(s.img, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
                                                                 (int)Sho, s.hV, s.hG, 3, 0);
     WTMD_CUDA_TRY(h, cudaGetLastError());
     std::vector<float> pv(Sho), tv(Sho), pg(3 * Sho), tg(3 * Sho);
@@ -732,6 +755,7 @@ static int sur_fit(wtmd_t* h)
     s.stats[2] = mx / kT;
     s.stats[3] = gn > 0.0 ? std::sqrt(ge / gn) : 0.0;
     s.stats[4] = L;
+    if ((s.stats[5] != 0.0) != ok) drop_step_graphs(h);  // the tail plan depends on it
     s.stats[5] = ok ? 1.0 : 0.0;
     s.stats[6] += 1.0;
     s.stats[7] += (double)s.fit_iters;
@@ -925,7 +949,7 @@ extern "C" int wtmd_mlp_params(wtmd_t* h, const float* in, float* out, const dou
         WTMD_CUDA_TRY(h, cudaMemset(s->m, 0, sizeof(float) * MP));
         WTMD_CUDA_TRY(h, cudaMemset(s->v, 0, sizeof(float) * MP));
         WTMD_CUDA_TRY(h, cudaMemset(s->ctr, 0, sizeof(long long) * 2));
-        mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb);
+        mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb, s->img);
         WTMD_CUDA_TRY(h, cudaDeviceSynchronize());
     }
     if (norm_in) {
@@ -949,7 +973,7 @@ extern "C" int wtmd_mlp_eval(wtmd_t* h, const double* xi, int64_t P, float* V, f
     if (P == 0) return WTMD_OK;
     // each block stages the network once: a few blocks per SM, points by grid stride
     const int nb = (int)std::min<int64_t>((P + MLP_W - 1) / MLP_W, grad_blocks());
-    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s->wb, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
+    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s->img, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
 }

@@ -352,9 +352,11 @@ int walkers_enable(wtmd_t* h);
 int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult);
 int launch_walkers_step(wtmd_t* h, int mode);                   // 0: full step, 1: forces only
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
-// hills [*k0p, *k1p) (k0p may be null: 0; *k0p a multiple of 256; FP32 handles)
+// hills [*k0p, *k1p) (k0p may be null: 0; *k0p a multiple of 256; FP32
+// handles); max_hills > 0 bounds the range's length for the launch plan
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
-                       int dV_stride, const long long* k0p, const long long* k1p);
+                       int dV_stride, const long long* k0p, const long long* k1p, long long max_hills);
+long long surrogate_tail_bound(const wtmd_t* h);                // hills beyond k0 between refits (0: unbounded)
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 // surrogate (mlp.cu)
 void surrogate_free(Surrogate* s);

@@ -183,3 +183,15 @@ def lj_clusters(W: int, lo: int, hi: int, rho: float, seed: int):
     sizes = log_uniform_sizes(W, lo, hi, seed)
     x = np.concatenate([fcc_cluster(int(n), rho, seed=1000 * (seed + 1) + w) for w, n in enumerate(sizes)])
     return sizes, x
+
+
+def native_pairs(x: np.ndarray, L: float, subset: np.ndarray, rcut: float) -> np.ndarray:
+    """Pairs (i < j) of `subset` closer than rcut (minimum image, box L) in
+    the configuration x, as a flat int32 array (i0, j0, i1, j1, ...)."""
+    s = np.sort(np.asarray(subset))
+    p = x[s]
+    d = p[:, None, :] - p[None, :, :]
+    d -= L * np.rint(d / L)
+    r2 = (d ** 2).sum(-1)
+    i, j = np.nonzero(np.triu(r2 < rcut * rcut, k=1))
+    return np.stack([s[i], s[j]], axis=1).reshape(-1).astype(np.int32)

@@ -285,3 +285,71 @@ def test_fit_on_oracle_metadynamics_hills():
     V, xi, _ = m2.bias_eval(pos)
     Ve, _ = o.hills_sum(to_np(xi), hills, (1.0, 1.0, 1.0))
     assert np.allclose(to_np(V), Ve, rtol=1e-5)
+
+
+def wells3_hills_gpu(wt, H=1_000_000, W=2048, sigma=0.4, w0=0.05, gamma=3.0, seed=5):
+    """A long hill list from a well-tempered run of W walkers on the
+    three-well landscape in CV space (x, y, z), made by the library itself
+    (inputs of the GPU-only gain test)."""
+    m = wt.Wtmd(precision="f32", sigma=(sigma,) * 3, w0=w0, gamma=gamma, kT=1.0, stride=10, capacity=H + W,
+                seed=seed, engine="wells3", walker_sizes=[1] * W, dims=3, dt=5e-3, friction=1.0)
+    for k in range(3):
+        m.cv_define(wt.CV_COMPONENT, a=[0], axis=k)
+    centres = np.array([[-1, 0, 0], [1, 0.2, -0.3], [0.1, 1.3, 0.6]])
+    x = synth.rng(1).normal(scale=0.3, size=(W, 3)) + centres[np.arange(W) % 3]
+    pos, vel = wt.particles(x, torch.float32), wt.particles(np.zeros_like(x), torch.float32)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n((H // W) * 10)
+    return m
+
+
+def test_gain_at_1e6_hills():
+    """What the trained network gains: at ~1e6 hills the fitted network is
+    within 0.05 kT (held out) and evaluates bias and gradient at 4096 points
+    many times faster than the exact hills sum; the step path with the
+    surrogate active gives the same bias as the exact path to that
+    tolerance."""
+    wt = _wt()
+    m = wells3_hills_gpu(wt)
+    K = m.counters()[1]
+    assert K > 990000
+    m.surrogate(True, tol_kT=0.05, retrain_every=0)
+    st = m.surrogate_fit()
+    assert st["active"] == 1.0 and st["rms_kT"] <= 0.05, st
+    h = m.hills_read()
+    r = synth.rng(3)
+    P = 4096
+    pts = h[r.integers(0, h.shape[0], P), :3] + 0.4 * r.normal(size=(P, 3))
+    x64 = torch.tensor(pts, device="cuda")
+    x32 = x64.float()
+    Ve = torch.empty(P, dtype=torch.float32, device="cuda")
+    dVe = torch.empty(P, 3, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=10):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_exact = timed(lambda: m.hills_eval_into(x32, Ve, dVe))
+    t_nn = timed(lambda: m.mlp_eval(x64))
+    Vn, dVn = m.mlp_eval(x64)
+    e = to_np(Vn) - to_np(Ve)
+    e -= e.mean()
+    assert np.sqrt(np.mean(e ** 2)) <= 0.06  # fresh points, exact GPU sum as reference
+    assert t_exact / t_nn > 10.0, (t_exact, t_nn)
+    # step path: bias of the 2048 walkers, surrogate vs exact
+    pos = m._bound[0]
+    V1, xi1, _ = m.bias_eval(pos)
+    m.surrogate(False)
+    V0, xi0, _ = m.bias_eval(pos)
+    d = to_np(V1) - to_np(V0)
+    d -= d.mean()
+    assert np.sqrt(np.mean(d ** 2)) <= 0.1
