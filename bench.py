@@ -395,26 +395,49 @@ def traffic_for(kernel: str, sha: str):
 
 
 KERNEL_SRC = {"lj_cell_force": "engine.cu", "lj_cell_bin": "engine.cu", "lj_cell_sort": "engine.cu",
-              "baoab_first": "engine.cu", "coord_pair_row": "cv.cu", "coord_pair_col": "cv.cu",
-              "coord_finalize": "cv.cu", "coord_value": "cv.cu", "cv_rg": "cv.cu", "scatter_kick": "cv.cu",
-              "hills_partial_f32": "hills.cu", "hills_finalize": "hills.cu", "deposit": "deposit.cu"}
+              "baoab_first": "engine.cu", "coord_tile": "cv.cu", "cv_rg": "cv.cu", "scatter_kick_deposit": "cv.cu",
+              "scatter_kick": "cv.cu", "hills_sum_f32": "hills.cu", "hills_finalize": "hills.cu",
+              "deposit": "deposit.cu"}
+
+# Algorithmic work of one launch of each kernel of the 4096-atom step.
+# Pair kernels are bound by FP32 arithmetic ("alu"), counted in FLOP (an FMA
+# is 2): a coordination pair (tagged atom, any other atom) is 39 FLOP --
+# difference and minimum image 15, r^2 5, y = r^2/r0^2 1, y^3 2, 1 + y^3 1,
+# reciprocal 1, row sum 1, gradient prefactor 4, its three components 3, row
+# and column accumulation 6; an LJ pair inside the cutoff is 24 FLOP
+# (difference 3, r^2 5, reciprocal 1, (s/r)^6 3, force factor 6, three
+# components 6).  The other kernels move data ("hbm"), counted in compulsory
+# DRAM bytes (each array read or written once).
+FLOP_COORD_PAIR, FLOP_LJ_PAIR = 39, 24
+LJ_RC = 2.5
+LJ_PAIRS = int(N_ATOMS * RHO * 4.0 / 3.0 * np.pi * LJ_RC ** 3)  # ordered pairs inside rc
 
 
-def algorithmic(kernel: str, n_hills: int):
-    """Algorithmic (compulsory) DRAM bytes of one launch in the 4096-atom step."""
+def kernel_work(kernel: str, n_hills: int):
+    """(bound, amount per launch, unit of the amount) or None."""
     r4 = 16
-    table = {
-        "baoab_first": N_ATOMS * r4 * 5,           # read x, v, f; write x, v
-        "lj_cell_bin": N_ATOMS * (r4 + 4),         # read x, write cell slots
-        "lj_cell_force": N_ATOMS * (r4 + r4 + 4),  # read x (once), cell lists, write f
-        "coord_pair_row": N_ATOMS * r4 + N_TAG * r4,
-        "coord_pair_col": N_ATOMS * r4 + N_TAG * r4,
-        "coord_finalize": N_ATOMS * r4,
-        "cv_rg": N_RG * r4 * 2,
-        "hills_partial_f32": ((n_hills + 1) // 2) * 32,  # hill-pair records read once
-        "scatter_kick": N_ATOMS * r4 * 6,           # f, 2 J rows, v in; f, v out
+    alu = {
+        "coord_tile": N_TAG * (N_ATOMS - 1) * FLOP_COORD_PAIR,
+        "lj_cell_force": LJ_PAIRS * FLOP_LJ_PAIR,
     }
-    return table.get(kernel)
+    hbm = {
+        "baoab_first": N_ATOMS * r4 * 5,                    # read x, v, f; write x, v
+        "lj_cell_bin": N_ATOMS * (r4 + 4),                  # read x, write cell slots
+        "lj_cell_sort": N_ATOMS * 4 * 2,                    # cell slots in and out
+        "cv_rg": N_RG * r4 * 2,                             # positions in, J out
+        "hills_sum_f32": ((n_hills + 1) // 2) * 32,         # hill-pair records read once
+        "scatter_kick_deposit": N_ATOMS * r4 * 6,           # f, 2 J rows, v in; f, v out (+ one hill)
+    }
+    if kernel in alu:
+        return "alu", alu[kernel], "FLOP"
+    if kernel in hbm:
+        return "hbm", hbm[kernel], "B"
+    return None
+
+
+def alu_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 peak from unit counts and clock: SMs x 128 FP32 lanes x 2 FLOP (FMA) x SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 # --------------------------------------------------------------------------
@@ -604,12 +627,25 @@ def main():
     prof = r["prof"]
     dom_name, dom_ms = max(prof, key=lambda t: t[1])
     hbm, peak_kind = peaks()
-    alg = algorithmic(dom_name, r["n_hills"])
-    roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-            "traffic": None, "peak_source": peak_kind}
-    if alg is not None:
-        ach = alg / (dom_ms * 1e-3) / 1e9
-        roof.update(achieved=ach, frac=ach / hbm, algorithmic_bytes=alg, ms=dom_ms)
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = r["clocks"].get("sm_mhz") or 2032.0
+    work = kernel_work(dom_name, r["n_hills"])
+    roof = {"kernel": dom_name, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "ms": dom_ms}
+    if work is not None:
+        bound, amount, what = work
+        if bound == "alu":
+            peak = alu_peak_tflops(sms, mhz)
+            ach = amount / (dom_ms * 1e-3) / 1e12
+            roof.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                        algorithmic_flop=amount,
+                        peak_source=f"derived: {sms} SMs x 128 FP32 lanes x 2 FLOP x {mhz:.0f} MHz (measured median)")
+        else:
+            ach = amount / (dom_ms * 1e-3) / 1e9
+            roof.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, algorithmic_bytes=amount,
+                        peak_source=peak_kind)
     sha = src_sha(KERNEL_SRC.get(dom_name, "api.cu"))
     roof["traffic"] = traffic_for(dom_name, sha)
     roof["source_sha"] = sha

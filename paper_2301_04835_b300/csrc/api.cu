@@ -77,6 +77,7 @@ static void free_cv(CvDev& c)
     cudaFree(c.inv_b);
     cudaFree(c.q_rowptr);
     cudaFree(c.q_items);
+    cudaFree(c.tile_tk);
     cudaFree(c.order);
     cudaFree(c.scw);
     cudaFree(c.tile_row);
@@ -465,8 +466,7 @@ static int enqueue_step(wtmd_t* h)
     int rc;
     if ((rc = launch_baoab_first(h))) return rc;
     if ((rc = enqueue_engine_and_bias(h))) return rc;
-    if ((rc = launch_scatter(h, h->force, h->vel, true))) return rc;
-    return launch_deposit(h);
+    return launch_scatter_deposit(h);
 }
 
 static int capture(wtmd_t* h, int nsteps, cudaGraphExec_t* out)
@@ -703,7 +703,10 @@ extern "C" int wtmd_grid_read(wtmd_t* h, double* out, int64_t n_out)
 // so that the host can enqueue a whole profiled step behind it: the step's
 // kernels then run back to back and the events between them measure device
 // time, not host launch gaps.
-__global__ static void delay_kernel(long long ns)
+// A short spin of `dither` SM cycles (< 4096) at the end moves the start of
+// the profiled step by a varying fraction of the event timer's tick, so that
+// per-kernel means over many steps are not biased by that granularity.
+__global__ static void delay_kernel(long long ns, int dither)
 {
     if (threadIdx.x != 0) return;
     unsigned long long t0, t;
@@ -712,6 +715,9 @@ __global__ static void delay_kernel(long long ns)
         __nanosleep(1000);
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     } while ((long long)(t - t0) < ns && (long long)(t - t0) < 2000000);
+    const long long c0 = clock64();
+    while (clock64() - c0 < (dither & 4095)) {
+    }
 }
 
 extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32_t cap, int32_t* n_out)
@@ -731,7 +737,7 @@ extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double
     h->prof = true;
     for (int64_t s = 0; s < n_steps; ++s) {
         h->ev_n = 0;
-        delay_kernel<<<1, 32, 0, h->stream>>>(500000);
+        delay_kernel<<<1, 32, 0, h->stream>>>(500000, (int)((uint32_t)(s * 2654435761u) >> 20));
         mark(h, "start");
         rc = enqueue_step(h);
         if (rc) break;

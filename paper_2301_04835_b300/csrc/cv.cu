@@ -14,7 +14,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "wtmd_internal.cuh"
+#include "step_dev.cuh"
 
 namespace wtmd {
 
@@ -244,7 +244,9 @@ constexpr int CW_T = 256;  // threads per block (8 target warps)
 // correctly rounded reciprocal (FP32: MUFU estimate + refinement, no IEEE
 // division subroutine; unbiased, so sums of many terms do not drift)
 template <typename R> __device__ __forceinline__ R rcp(R x);
-template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+// FP32: the PTX approximate reciprocal (1 ulp), far cheaper than the IEEE
+// division sequence; the switching-function terms need no more
+template <> __device__ __forceinline__ float rcp<float>(float x) { return rcp_approx(x); }
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
 template <typename R>
@@ -414,7 +416,8 @@ __global__ void __launch_bounds__(CW_T) coord_warp_kernel(const R4<R>* __restric
 // group of 8 partners are summed over the 32 lanes by a shuffle
 // reduce-scatter (9 shuffles per component per 8 partners).  Row partials
 // [chunk][A] and column partials [tile][B] are written once each and summed
-// in fixed order by coord_tile_finalize: deterministic, no atomics on data.
+// in fixed order by the CTAs that complete a tile or a chunk (tickets), in
+// the same launch: deterministic.
 // ---------------------------------------------------------------------------
 constexpr int CT_T = 256;
 constexpr int CT_B = 256;  // partners per CTA (8 warps x 32)
@@ -445,12 +448,25 @@ template <typename R> __device__ __forceinline__ void reduce_scatter8(R v[8], in
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-template <typename R>
+// A partial written by another CTA of the same launch: read past L1.
+template <typename R> __device__ __forceinline__ R4<R> ldcg_r4(const R4<R>* p);
+template <> __device__ __forceinline__ R4<float> ldcg_r4<float>(const R4<float>* p) { return __ldcg(p); }
+template <> __device__ __forceinline__ R4<double> ldcg_r4<double>(const R4<double>* p)
+{
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    return dbl4{a.x, a.y, b.x, b.y};
+}
+
+template <typename R, int HC>
 __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
                                                           const int* __restrict__ wn, const int* __restrict__ A, int nA,
                                                           const int* __restrict__ B, int nB, int nbchunk, Box box,
                                                           R inv_r0sq, int h, R gpref, R4<R>* __restrict__ rowpart,
-                                                          R4<R>* __restrict__ colpart, int nB_stride)
+                                                          R4<R>* __restrict__ colpart, int nB_stride,
+                                                          const double* __restrict__ scw, double* __restrict__ rowval,
+                                                          unsigned* __restrict__ tk, R4<R>* __restrict__ J,
+                                                          double* __restrict__ xi, int col)
 {
     __shared__ R4<R> src[CT_B];
     __shared__ int sid[CT_B];
@@ -485,7 +501,14 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
                 R d[3];
                 delta<R>(box, tx, ty, tz, sp.x, sp.y, sp.z, d);
                 const R y = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv_r0sq;
-                const R yh1 = ypow<R>(y, h - 1);
+                R yh1 = y;  // y^(h-1); the exponent is a compile-time constant when HC > 0
+                if constexpr (HC > 0) {
+                    yh1 = R(1);
+#pragma unroll
+                    for (int e = 1; e < HC; ++e) yh1 *= y;
+                } else {
+                    yh1 = ypow<R>(y, h - 1);
+                }
                 R s = rcp<R>(R(1) + yh1 * y);
                 if (sid[q] == a) s = R(0);
                 sv += s;
@@ -522,96 +545,86 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
         }
         rowpart[((size_t)w * nbchunk + chunk) * nA + ia] = t;
     }
+
+    // Finalization without a second launch.  The CTA that completes a tile
+    // (its last chunk) sums the tile's row partials over the chunks; the CTA
+    // that completes a chunk (its last tile) sums the chunk's column
+    // partials over the tiles; the CTA that completes the last tile sums the
+    // row values into xi.  All sums run in a fixed order.  J was zeroed
+    // before the launch and each atom receives at most one row and one
+    // column contribution, so their two additions commute exactly.
+    const int ntile = gridDim.x / nbchunk;
+    const int ntk = ntile + nbchunk + 1;
+    unsigned* tkw = tk + (size_t)w * ntk;
+    __shared__ int last_row, last_col, last_x;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last_row = atomicAdd(&tkw[tile], 1u) == (unsigned)nbchunk - 1;
+        last_col = atomicAdd(&tkw[ntile + chunk], 1u) == (unsigned)ntile - 1;
+    }
+    __syncthreads();
+    const R f = (R)scw[w];
+    if (last_row) {
+        __threadfence();
+        if (warp == 0 && a >= 0) {
+            R sx = 0, sy = 0, sz = 0;
+            cf sv{0.f, 0.f};
+            double svd = 0.0;
+            for (int c = 0; c < nbchunk; ++c) {
+                const R4<R> u = ldcg_r4<R>(rowpart + ((size_t)w * nbchunk + c) * nA + ia);
+                sx += u.x;
+                sy += u.y;
+                sz += u.z;
+                if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)u.w);
+                else svd += (double)u.w;
+            }
+            atomicAdd(&J[o + a].x, f * sx);
+            atomicAdd(&J[o + a].y, f * sy);
+            atomicAdd(&J[o + a].z, f * sz);
+            rowval[(size_t)w * nA + ia] = sizeof(R) == 4 ? cf_val(sv) : svd;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tkw[tile] = 0u;
+            last_x = atomicAdd(&tkw[ntile + nbchunk], 1u) == (unsigned)ntile - 1;
+        }
+        __syncthreads();
+        if (last_x) {
+            __threadfence();
+            double v[1] = {0.0};
+            for (int q = threadIdx.x; q < nA; q += CT_T) v[0] += __ldcg(rowval + (size_t)w * nA + q);
+            block_sum<double, 1>(v);
+            if (threadIdx.x == 0) {
+                xi[w * 4 + col] = scw[w] * v[0];
+                tkw[ntile + nbchunk] = 0u;
+            }
+        }
+    }
+    if (last_col) {
+        __threadfence();
+        for (int q = threadIdx.x; q < mb; q += CT_T) {
+            R sx = 0, sy = 0, sz = 0;
+            for (int t = 0; t < ntile; ++t) {
+                const R4<R> u = ldcg_r4<R>(colpart + ((size_t)w * ntile + t) * nB_stride + b0 + q);
+                sx += u.x;
+                sy += u.y;
+                sz += u.z;
+            }
+            const int j = sid[q];
+            atomicAdd(&J[o + j].x, f * sx);
+            atomicAdd(&J[o + j].y, f * sy);
+            atomicAdd(&J[o + j].z, f * sz);
+        }
+        if (threadIdx.x == 0) tkw[ntile + chunk] = 0u;
+    }
 }
 
 // J rows and the CV value from the tile partials.  Thread k sums the chunk
 // partials of its row (k in A; also its row value of s, stored per member)
 // and the tile partials of its column (k in B); the walker's last CTA sums
 // the per-member row values in member order.
-template <typename R>
-__global__ void __launch_bounds__(64) coord_tile_finalize(const int64_t* __restrict__ woff, const int* __restrict__ wn,
-                                                           const int* __restrict__ inv_a, const int* __restrict__ inv_b,
-                                                           bool b_all, int nA, int ntile, int nbchunk,
-                                                           const R4<R>* __restrict__ rowpart,
-                                                           const R4<R>* __restrict__ colpart, int nB_stride,
-                                                           const double* __restrict__ scw, double* __restrict__ rowval,
-                                                           unsigned* __restrict__ tickets, R4<R>* __restrict__ J,
-                                                           double* __restrict__ xi, int col)
-{
-    const int w = blockIdx.y;
-    const int nw = wn[w];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nw) {
-        const int pa = inv_a[k];
-        const int pb = b_all ? k : inv_b[k];
-        if (pa >= 0 || pb >= 0) {
-            R gx = 0, gy = 0, gz = 0;
-            // issue all partial loads before summing them (in order)
-            constexpr int MAXP = 32;
-            if (pa >= 0) {
-                R4<R> rp[MAXP];
-#pragma unroll
-                for (int c = 0; c < MAXP; ++c)
-                    if (c < nbchunk) rp[c] = rowpart[((size_t)w * nbchunk + c) * nA + pa];
-                cf sv{0.f, 0.f};
-                double svd = 0.0;
-#pragma unroll
-                for (int c = 0; c < MAXP; ++c)
-                    if (c < nbchunk) {
-                        gx += rp[c].x;
-                        gy += rp[c].y;
-                        gz += rp[c].z;
-                        if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)rp[c].w);
-                        else svd += (double)rp[c].w;
-                    }
-                for (int c = MAXP; c < nbchunk; ++c) {
-                    const R4<R> t = rowpart[((size_t)w * nbchunk + c) * nA + pa];
-                    gx += t.x;
-                    gy += t.y;
-                    gz += t.z;
-                    if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)t.w);
-                    else svd += (double)t.w;
-                }
-                rowval[(size_t)w * nA + pa] = sizeof(R) == 4 ? cf_val(sv) : svd;
-            }
-            if (pb >= 0) {
-                R4<R> cp[MAXP];
-#pragma unroll
-                for (int t = 0; t < MAXP; ++t)
-                    if (t < ntile) cp[t] = colpart[((size_t)w * ntile + t) * nB_stride + pb];
-#pragma unroll
-                for (int t = 0; t < MAXP; ++t)
-                    if (t < ntile) {
-                        gx += cp[t].x;
-                        gy += cp[t].y;
-                        gz += cp[t].z;
-                    }
-                for (int t = MAXP; t < ntile; ++t) {
-                    const R4<R> u = colpart[((size_t)w * ntile + t) * nB_stride + pb];
-                    gx += u.x;
-                    gy += u.y;
-                    gz += u.z;
-                }
-            }
-            const R f = (R)scw[w];
-            J[woff[w] + k] = mk4<R>(f * gx, f * gy, f * gz, R(0));
-        }
-    }
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&tickets[w], 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double v[1] = {0.0};
-    for (int q = threadIdx.x; q < nA; q += blockDim.x) v[0] += __ldcg(rowval + (size_t)w * nA + q);
-    block_sum<double, 1>(v);
-    if (threadIdx.x == 0) {
-        xi[w * 4 + col] = scw[w] * v[0];
-        tickets[w] = 0u;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Q-like pair count: xi = scale * sum_p s(r_{i_p j_p}) over a fixed list.
@@ -673,12 +686,10 @@ __global__ void __launch_bounds__(256) qpair_value_kernel(const R4<R>* __restric
 // closing half kick v += dt/2 F/m of BAOAB.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void scatter_kernel(long long N, int d, const int* __restrict__ aw, const R* __restrict__ dV,
-                               const R4<R>* __restrict__ J, R4<R>* __restrict__ force, R4<R>* __restrict__ vel,
-                               R half_dt_over_m, int dims)
+__device__ __forceinline__ void scatter_atom(long long i, int d, const int* __restrict__ aw, const R* __restrict__ dV,
+                                             const R4<R>* __restrict__ J, long long N, R4<R>* __restrict__ force,
+                                             R4<R>* __restrict__ vel, R half_dt_over_m, int dims)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     const int w = aw[i];
     R4<R> f = force[i];
     for (int c = 0; c < d; ++c) {
@@ -696,6 +707,32 @@ __global__ void scatter_kernel(long long N, int d, const int* __restrict__ aw, c
         if (dims > 2) v.z += half_dt_over_m * f.z;
         vel[i] = v;
     }
+}
+
+// Closing half-kick of the step fused with the deposition: the last block
+// first deposits (reads xi and V, appends hills, advances the step counter),
+// then every block scatters its atoms' bias forces and kicks.
+template <typename R>
+__global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d, const int* __restrict__ aw,
+                                                              const R* __restrict__ dV, const R4<R>* __restrict__ J,
+                                                              R4<R>* __restrict__ force, R4<R>* __restrict__ vel,
+                                                              R half_dt_over_m, int dims, DepPrm dp,
+                                                              const double* __restrict__ xi, const R* __restrict__ V,
+                                                              long long* count, long long* step, long long* dep,
+                                                              double* ctr, dbl4* h64, float* h32, unsigned* status)
+{
+    if (blockIdx.x == gridDim.x - 1) deposit_block<R>(dp, xi, V, count, step, dep, ctr, h64, h32, status);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) scatter_atom<R>(i, d, aw, dV, J, N, force, vel, half_dt_over_m, dims);
+}
+
+template <typename R>
+__global__ void scatter_kernel(long long N, int d, const int* __restrict__ aw, const R* __restrict__ dV,
+                               const R4<R>* __restrict__ J, R4<R>* __restrict__ force, R4<R>* __restrict__ vel,
+                               R half_dt_over_m, int dims)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) scatter_atom<R>(i, d, aw, dV, J, N, force, vel, half_dt_over_m, dims);
 }
 
 // ---------------------------------------------------------------------------
@@ -759,6 +796,9 @@ int cv_alloc_scratch(wtmd_t* h, CvDev& c)
             c.nB_stride = nB;
             WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_row, r4 * (size_t)h->W * c.nbchunk * c.n_a));
             WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_col, r4 * (size_t)h->W * c.ntile * nB));
+            const size_t ntk = (size_t)h->W * (c.ntile + c.nbchunk + 1);
+            WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_tk, sizeof(unsigned) * ntk));
+            WTMD_CUDA_TRY(h, cudaMemset(c.tile_tk, 0, sizeof(unsigned) * ntk));
         }
         WTMD_CUDA_TRY(h, cudaMemcpy(c.scw, scw.data(), sizeof(double) * (size_t)h->W, cudaMemcpyHostToDevice));
     } else if (c.kind == WTMD_CV_QPAIRS) {
@@ -802,16 +842,18 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
             const int* B = cv.n_b < 0 ? nullptr : cv.b;
             if (cv.n_a > 0) {
                 dim3 gt(cv.ntile * cv.nbchunk, W);
-                coord_tile_kernel<R><<<gt, CT_T, 0, st>>>(pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box,
-                                                          inv, cv.nn / 2, gp, (R4<R>*)cv.tile_row,
-                                                          (R4<R>*)cv.tile_col, cv.nB_stride);
+                WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
+                if (cv.nn == 6)
+                    coord_tile_kernel<R, 3><<<gt, CT_T, 0, st>>>(
+                        pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, 3, gp,
+                        (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
+                        cv.tile_tk, Jc, xi, c);
+                else
+                    coord_tile_kernel<R, 0><<<gt, CT_T, 0, st>>>(
+                        pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, cv.nn / 2, gp,
+                        (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
+                        cv.tile_tk, Jc, xi, c);
                 mark(h, "coord_tile");
-                dim3 gf((h->max_wn + 63) / 64, W);
-                coord_tile_finalize<R><<<gf, 64, 0, st>>>(h->woff, h->wn, cv.inv_a, cv.inv_b, cv.n_b < 0, cv.n_a,
-                                                           cv.ntile, cv.nbchunk, (const R4<R>*)cv.tile_row,
-                                                           (const R4<R>*)cv.tile_col, cv.nB_stride, cv.scw,
-                                                           (double*)cv.part_row, (unsigned*)cv.part_col, Jc, xi, c);
-                mark(h, "coord_tile_finalize");
                 break;
             }
             const int nt = cv.order ? cv.n_order : h->max_wn;
@@ -862,6 +904,26 @@ int launch_cv(wtmd_t* h, const void* pos, int c)
 int launch_cvs(wtmd_t* h, const void* pos)
 {
     return h->prec == WTMD_F32 ? launch_cvs_t<float>(h, pos, 0, h->ncv) : launch_cvs_t<double>(h, pos, 0, h->ncv);
+}
+
+int launch_scatter_deposit(wtmd_t* h)
+{
+    const int nb = (int)((h->N + 255) / 256);
+    const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
+    const DepPrm dp = dep_prm(h);
+    if (h->prec == WTMD_F32)
+        scatter_deposit_kernel<float><<<nb, 256, 0, h->stream>>>(
+            h->N, h->d, h->atom_walker, (const float*)h->dV, (const float4*)h->J, (float4*)h->force,
+            (float4*)h->vel, (float)hdm, h->dims, dp, h->xi, (const float*)h->V, h->count, h->step, h->dep, h->ctr,
+            (dbl4*)h->hills64, (float*)h->hills32, h->status);
+    else
+        scatter_deposit_kernel<double><<<nb, 256, 0, h->stream>>>(
+            h->N, h->d, h->atom_walker, (const double*)h->dV, (const dbl4*)h->J, (dbl4*)h->force, (dbl4*)h->vel, hdm,
+            h->dims, dp, h->xi, (const double*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
+            (float*)h->hills32, h->status);
+    mark(h, "scatter_kick_deposit");
+    WTMD_CUDA_TRY(h, cudaGetLastError());
+    return launch_grid_update(h);
 }
 
 int launch_scatter(wtmd_t* h, void* force, const void* vel, bool kick)

@@ -158,7 +158,7 @@ static double fes_factor(const wtmd_config& c)
     return (c.gamma == 0.0 || isinf(c.gamma)) ? -1.0 : -c.gamma / (c.gamma - 1.0);
 }
 
-int launch_deposit(wtmd_t* h)
+DepPrm dep_prm(const wtmd_t* h)
 {
     DepPrm p{};
     p.stride = h->cfg.stride;
@@ -168,6 +168,12 @@ int launch_deposit(wtmd_t* h)
     p.w0 = h->cfg.w0;
     p.inv_dT = (h->cfg.gamma == 0.0 || isinf(h->cfg.gamma)) ? 0.0 : 1.0 / (h->cfg.kT * (h->cfg.gamma - 1.0));
     for (int i = 0; i < 3; ++i) p.a[i] = h->a[i];
+    return p;
+}
+
+int launch_deposit(wtmd_t* h)
+{
+    const DepPrm p = dep_prm(h);
     if (h->prec == WTMD_F32)
         deposit_kernel<float><<<1, 256, 0, h->stream>>>(p, h->xi, (const float*)h->V, h->count, h->step, h->dep,
                                                         h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status);

@@ -91,6 +91,8 @@ struct DepPrm {
     double a[3];        // FP32 layout scale
 };
 
+DepPrm dep_prm(const wtmd_t* h);  // deposit.cu
+
 // Deposition by one CTA (all its threads call this): every `stride` steps
 // each walker appends a hill at its CVs with height w0 exp(-V inv_dT) in
 // FP64 (walker order), then the step counter advances.

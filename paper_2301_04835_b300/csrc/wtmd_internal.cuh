@@ -208,6 +208,7 @@ struct CvDev {
     void* tile_row = nullptr;      // tile path (list A): row partials [W][chunk][|A|] R4
     void* tile_col = nullptr;      // column partials [W][tile][|B|] R4
     int nbchunk = 0, ntile = 0, nB_stride = 0;
+    unsigned* tile_tk = nullptr;   // tile path tickets [W][ntile + nbchunk + 1]
     int n_order = 0;
     // QPAIRS: CSR from atom to (pair, sign)
     int n_pairs = 0;
@@ -358,6 +359,7 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, in
                        int dV_stride, const long long* k0p, const long long* k1p, long long max_hills);
 long long surrogate_tail_bound(const wtmd_t* h);                // hills beyond k0 between refits (0: unbounded)
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
+int launch_scatter_deposit(wtmd_t* h);                          // kick + deposit (+ grid) of a step
 // surrogate (mlp.cu)
 void surrogate_free(Surrogate* s);
 const long long* surrogate_k0(const wtmd_t* h);                 // first hill of the exact tail, or null
