@@ -353,3 +353,32 @@ def test_gain_at_1e6_hills():
     d = to_np(V1) - to_np(V0)
     d -= d.mean()
     assert np.sqrt(np.mean(d ** 2)) <= 0.1
+
+
+def test_refits_are_scheduled_inside_step_n():
+    """With retrain_every = 512 the network is refitted inside step_n each
+    time 512 more hills exist (64 walkers deposit every step), continuing
+    from the current weights, and the step counters stay consistent."""
+    wt = _wt()
+    W = 64
+    spec = dict(engine="wells3", walker_sizes=[1] * W, dims=3, dt=5e-3, kT=1.0, sigma=(0.5, 0.5, 0.5), w0=0.05,
+                gamma=3.0, stride=1, capacity=8192, cvs=[dict(kind="component", a=[0], axis=k) for k in range(3)])
+    m = gpu_handle(spec, "f32")
+    x = synth.rng(2).normal(scale=0.5, size=(W, 3))
+    pos, vel = wt.particles(x, torch.float32), wt.particles(np.zeros_like(x), torch.float32)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.surrogate_config(n_samples=4000, iters=300, batch=512, lr=3e-3, lam=0.1)
+    m.surrogate(True, tol_kT=10.0, retrain_every=512)
+    m.step_n(40)  # 2560 hills: fits at 512 (first chance), 1024, 1536, 2048, 2560
+    st = m.surrogate_status()
+    assert m.counters() == (40, 2560)
+    assert st["fits"] >= 4 and st["K"] % 256 == 0 and st["K"] >= 2048, st
+    assert st["active"] == 1.0 and st["iters"] == 300 * st["fits"]
+    # the bias the step path uses agrees with the exact sum to the fit's error
+    V1, xi, _ = m.bias_eval(pos)
+    m.surrogate(False)
+    V0, _, _ = m.bias_eval(pos)
+    d = to_np(V1) - to_np(V0)
+    d -= d.mean()
+    assert np.sqrt(np.mean(d ** 2)) <= 3 * st["rms_kT"] + 0.05
