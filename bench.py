@@ -469,6 +469,7 @@ def run_ours(args, rank, world):
     F = torch.zeros_like(pos)
     _, xi0, _ = m.bias_eval(pos)
     m.hills_load(hills_around(xi0[0].double().cpu().numpy(), seed=100 + rank))
+    hills_plan = m.hills_tune(1)  # one walker: one evaluation point per step
     m.bind(pos, vel, F)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -542,7 +543,7 @@ def run_ours(args, rank, world):
     micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
     walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
     sur = None if args.no_surrogate else surrogate_bench(wt, torch, dev, flush, args.steps)
-    return dict(walkers=walkers, surrogate=sur, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    return dict(hills_plan=hills_plan, walkers=walkers, surrogate=sur, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
 
@@ -669,6 +670,8 @@ def main():
         "steady_state_steps_per_s": world * K / (r["steady_ms"] * 1e-3),
         "wall_s": r["wall"],
         "kernels_ms": {k: round(v, 5) for k, v in prof},
+        "hills_plan": {"lanes_per_point": r["hills_plan"][0], "splits": r["hills_plan"][1],
+                       "tuned_ms": r["hills_plan"][2]},
         "hills_sum_1e6": r["micro"],
         "walkers_256_clusters": r["walkers"],
         "surrogate_1e6_hills": r["surrogate"],

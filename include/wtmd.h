@@ -240,6 +240,16 @@ int wtmd_walkers_persistent(wtmd_t* h, int32_t enable);
  * receives the chosen (T, CTAs per SM, split factor).  Synchronizes. */
 int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice);
 
+/* Autotuner of the hills-sum launch plan (Sec. 2.1.5 sum; the plan splits the
+ * hill list over CTAs and sets the hill lanes per point) for P evaluation
+ * points: times every (lanes per point 1/4/32/256, splits 1 ... 1184)
+ * candidate on the handle's current hills at P points placed at the CV
+ * centre, and keeps the fastest for later sums with P points (step_n with
+ * W = P walkers, bias_eval, hills_eval).  choice (host [2], may be NULL)
+ * receives (lanes per point, splits); ms (host, may be NULL) the time of one
+ * sum.  Synchronizes; drops captured step graphs. */
+int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms);
+
 /* Hills sum for callers that cannot allocate device memory (the paper has no
  * counterpart: it is an interface for hosts such as an engine plugin that may
  * only touch the buffers it is given, or a caller whose memory footprint

@@ -67,7 +67,7 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
            "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint", "wtmd_walkers_persistent",
            "wtmd_autotune", "wtmd_surrogate", "wtmd_surrogate_config", "wtmd_surrogate_fit", "wtmd_surrogate_status",
-           "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train"]
+           "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune"]
 
 MLP_PARAMS = 4481
 
@@ -114,6 +114,7 @@ def lib() -> C.CDLL:
     L.wtmd_mlp_eval.argtypes = [vp, vp, i64, vp, vp]
     L.wtmd_mlp_grad.argtypes = [vp, vp, vp, vp, i64, C.c_double, vp]
     L.wtmd_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i64, C.c_double, C.c_double, vp]
+    L.wtmd_hills_tune.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(C.c_double)]
     L.wtmd_cv_forward.argtypes = [vp, vp, vp]
     L.wtmd_cv_adjoint.argtypes = [vp, vp, vp]
     L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
@@ -271,6 +272,15 @@ class Wtmd:
                                   C.c_void_p(V.data_ptr()), C.c_void_p(xi.data_ptr()), C.c_void_p(dV.data_ptr())),
                   "bias_eval")
         return V, xi, dV
+
+    def hills_tune(self, P: int):
+        """Time the hills-sum plans for P points and keep the fastest; returns
+        (lanes per point, splits, ms per sum)."""
+        self._stream()
+        ch = (C.c_int32 * 2)()
+        ms = C.c_double()
+        self._err(lib().wtmd_hills_tune(self.h, int(P), ch, C.byref(ms)), "wtmd_hills_tune")
+        return ch[0], ch[1], ms.value
 
     def walkers_persistent(self, enable: bool = True):
         """Run each step as one persistent launch over all walkers."""

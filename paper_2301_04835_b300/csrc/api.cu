@@ -624,6 +624,22 @@ extern "C" int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, voi
     return launch_hills(h, xi, h->prec == WTMD_F64, h->d, P, V_out, dV_out, h->d);
 }
 
+extern "C" int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms)
+{
+    if (!h) return WTMD_EINVAL;
+    if (h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
+    int th = 0, sp = 0;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const int rc = hills_tune(h, P, &th, &sp, ms);
+    if (rc) return rc;
+    drop_graphs(h);  // recapture with the tuned plan
+    if (choice) {
+        choice[0] = th;
+        choice[1] = sp;
+    }
+    return WTMD_OK;
+}
+
 extern "C" int fes_grid(wtmd_t* h, double* out, int64_t n_out)
 {
     if (!h) return WTMD_EINVAL;

@@ -412,41 +412,16 @@ __global__ void __launch_bounds__(CW_T) coord_warp_kernel(const R4<R>* __restric
 // pair (i in A, j in B) evaluated once.  A CTA takes a tile of 32 members of
 // A (lane l holds a_l) and a chunk of CT_B partners staged in shared memory;
 // warp w sweeps partners w*32 ... w*32+31 of the chunk.  ds/dr for the row
-// atom a_l accumulates in its lane; the column contributions -ds/dr of each
-// group of 8 partners are summed over the 32 lanes by a shuffle
-// reduce-scatter (9 shuffles per component per 8 partners).  Row partials
+// atom a_l accumulates in its lane; each partner's column sum -ds/dr travels
+// once around the warp (one shuffle per component per pair).  Row partials
 // [chunk][A] and column partials [tile][B] are written once each and summed
 // in fixed order by the CTAs that complete a tile or a chunk (tickets), in
 // the same launch: deterministic.
 // ---------------------------------------------------------------------------
 constexpr int CT_T = 256;
 constexpr int CT_B = 256;  // partners per CTA (8 warps x 32)
+constexpr int FB = 4;      // partial sums loaded per batch in the finalization
 
-// Sum over the 32 lanes of v[0..7]; on return every lane holds in v[0] the
-// total for partner m = ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1).
-template <typename R> __device__ __forceinline__ void reduce_scatter8(R v[8], int lane)
-{
-    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const R keep = b4 ? v[k + 4] : v[k];
-        const R send = b4 ? v[k] : v[k + 4];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const R keep = b3 ? v[k + 2] : v[k];
-        const R send = b3 ? v[k] : v[k + 2];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    {
-        const R keep = b2 ? v[1] : v[0];
-        const R send = b2 ? v[0] : v[1];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-}
 
 // A partial written by another CTA of the same launch: read past L1.
 template <typename R> __device__ __forceinline__ R4<R> ldcg_r4(const R4<R>* p);
@@ -466,7 +441,8 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
                                                           R4<R>* __restrict__ colpart, int nB_stride,
                                                           const double* __restrict__ scw, double* __restrict__ rowval,
                                                           unsigned* __restrict__ tk, R4<R>* __restrict__ J,
-                                                          double* __restrict__ xi, int col)
+                                                          double* __restrict__ xi, int col,
+                                                          const int* __restrict__ inv_b)
 {
     __shared__ R4<R> src[CT_B];
     __shared__ int sid[CT_B];
@@ -479,57 +455,64 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const int b0 = chunk * CT_B;
     const int mb = min(CT_B, nBw - b0);
-    for (int q = threadIdx.x; q < mb; q += CT_T) {
-        const int j = B ? B[b0 + q] : b0 + q;
-        src[q] = pos[o + j];
-        sid[q] = j;
+    // partners of the chunk; padding slots carry weight 0 (.w) so that they
+    // contribute nothing without a branch in the pair loop
+    for (int q = threadIdx.x; q < CT_B; q += CT_T) {
+        if (q < mb) {
+            const int j = B ? B[b0 + q] : b0 + q;
+            const R4<R> p = pos[o + j];
+            src[q] = mk4<R>(p.x, p.y, p.z, R(1));
+            sid[q] = j;
+        } else {
+            src[q] = mk4<R>(R(0), R(0), R(0), R(0));
+            sid[q] = -1;
+        }
     }
     const int ia = tile * 32 + lane;
     const int a = ia < nA ? A[ia] : -1;
     R tx = 0, ty = 0, tz = 0;
     if (a >= 0) load3<R>(pos, o + a, tx, ty, tz);
+    const R gpl = a >= 0 ? gpref : R(0);  // an empty target lane adds nothing to the columns
     __syncthreads();
+    // Warp `warp` sweeps partners warp*32 ... warp*32+31 in 32 rotation
+    // steps: at step k lane l pairs its target with partner (l + k) mod 32
+    // and carries that partner's column sum, which then moves to lane l - 1.
+    // After the 32 steps lane l holds the full column sum of partner l.  The
+    // pair of an atom with itself (d = 0) adds s(0) = 1 to the row sum and
+    // nothing to the gradients; the row finalization removes it.
     R gx = 0, gy = 0, gz = 0, sv = 0;
-    for (int m0 = warp * 32; m0 < warp * 32 + 32; m0 += 8) {
-        R cx[8], cy[8], cz[8];
+    R cx = 0, cy = 0, cz = 0;
+    const int base = warp * 32, from = (lane + 1) & 31;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        const R4<R> sp = src[base + ((lane + k) & 31)];
+        R d[3];
+        delta<R>(box, tx, ty, tz, sp.x, sp.y, sp.z, d);
+        const R y = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv_r0sq;
+        R yh1;  // y^(h-1); the exponent is a compile-time constant when HC > 0
+        if constexpr (HC > 0) {
+            yh1 = R(1);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            cx[m] = cy[m] = cz[m] = R(0);
-            const int q = m0 + m;
-            if (q < mb && a >= 0) {
-                const R4<R> sp = src[q];
-                R d[3];
-                delta<R>(box, tx, ty, tz, sp.x, sp.y, sp.z, d);
-                const R y = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * inv_r0sq;
-                R yh1 = y;  // y^(h-1); the exponent is a compile-time constant when HC > 0
-                if constexpr (HC > 0) {
-                    yh1 = R(1);
-#pragma unroll
-                    for (int e = 1; e < HC; ++e) yh1 *= y;
-                } else {
-                    yh1 = ypow<R>(y, h - 1);
-                }
-                R s = rcp<R>(R(1) + yh1 * y);
-                if (sid[q] == a) s = R(0);
-                sv += s;
-                const R gr = gpref * yh1 * s * s;
-                gx += gr * d[0];
-                gy += gr * d[1];
-                gz += gr * d[2];
-                cx[m] = -gr * d[0];
-                cy[m] = -gr * d[1];
-                cz[m] = -gr * d[2];
-            }
+            for (int e = 1; e < HC; ++e) yh1 *= y;
+        } else {
+            yh1 = ypow<R>(y, h - 1);
         }
-        reduce_scatter8<R>(cx, lane);
-        reduce_scatter8<R>(cy, lane);
-        reduce_scatter8<R>(cz, lane);
-        const int m = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        const int q = m0 + m;
-        if ((lane & 3) == 0 && q < mb) {
-            const int pbq = b0 + q;  // position in B
-            colpart[((size_t)w * gridDim.x / nbchunk + tile) * nB_stride + pbq] = mk4<R>(cx[0], cy[0], cz[0], R(0));
-        }
+        const R s = rcp<R>(R(1) + yh1 * y) * sp.w;
+        sv += s;
+        const R gr = gpl * yh1 * s * s;
+        gx += gr * d[0];
+        gy += gr * d[1];
+        gz += gr * d[2];
+        cx -= gr * d[0];
+        cy -= gr * d[1];
+        cz -= gr * d[2];
+        cx = __shfl_sync(0xffffffffu, cx, from);
+        cy = __shfl_sync(0xffffffffu, cy, from);
+        cz = __shfl_sync(0xffffffffu, cz, from);
+    }
+    {
+        const int q = base + lane;
+        if (q < mb) colpart[((size_t)w * gridDim.x / nbchunk + tile) * nB_stride + b0 + q] = mk4<R>(cx, cy, cz, R(0));
     }
     // rows: the 8 warps hold partial sums over their partner slices
     rowred[warp][lane] = mk4<R>(gx, gy, gz, sv);
@@ -571,17 +554,31 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
             R sx = 0, sy = 0, sz = 0;
             cf sv{0.f, 0.f};
             double svd = 0.0;
-            for (int c = 0; c < nbchunk; ++c) {
-                const R4<R> u = ldcg_r4<R>(rowpart + ((size_t)w * nbchunk + c) * nA + ia);
-                sx += u.x;
-                sy += u.y;
-                sz += u.z;
-                if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)u.w);
-                else svd += (double)u.w;
+            // loads issued in batches of FB before they are summed (in order):
+            // a dependent load per partial would serialize L2 round trips
+            for (int c0 = 0; c0 < nbchunk; c0 += FB) {
+                R4<R> u[FB];
+#pragma unroll
+                for (int k = 0; k < FB; ++k)
+                    if (c0 + k < nbchunk) u[k] = ldcg_r4<R>(rowpart + ((size_t)w * nbchunk + c0 + k) * nA + ia);
+#pragma unroll
+                for (int k = 0; k < FB; ++k)
+                    if (c0 + k < nbchunk) {
+                        sx += u[k].x;
+                        sy += u[k].y;
+                        sz += u[k].z;
+                        if constexpr (sizeof(R) == 4) sv = cf_add(sv, (float)u[k].w);
+                        else svd += (double)u[k].w;
+                    }
             }
             atomicAdd(&J[o + a].x, f * sx);
             atomicAdd(&J[o + a].y, f * sy);
             atomicAdd(&J[o + a].z, f * sz);
+            // the target's pair with itself, if it is a partner, added s(0)
+            const bool self = inv_b ? inv_b[a] >= 0 : a < nw;
+            const R s0 = self ? rcp<R>(R(1)) : R(0);
+            if constexpr (sizeof(R) == 4) sv = cf_add(sv, -(float)s0);
+            else svd -= (double)s0;
             rowval[(size_t)w * nA + ia] = sizeof(R) == 4 ? cf_val(sv) : svd;
         }
         __threadfence();
@@ -606,11 +603,18 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
         __threadfence();
         for (int q = threadIdx.x; q < mb; q += CT_T) {
             R sx = 0, sy = 0, sz = 0;
-            for (int t = 0; t < ntile; ++t) {
-                const R4<R> u = ldcg_r4<R>(colpart + ((size_t)w * ntile + t) * nB_stride + b0 + q);
-                sx += u.x;
-                sy += u.y;
-                sz += u.z;
+            for (int t0 = 0; t0 < ntile; t0 += FB) {
+                R4<R> u[FB];
+#pragma unroll
+                for (int k = 0; k < FB; ++k)
+                    if (t0 + k < ntile) u[k] = ldcg_r4<R>(colpart + ((size_t)w * ntile + t0 + k) * nB_stride + b0 + q);
+#pragma unroll
+                for (int k = 0; k < FB; ++k)
+                    if (t0 + k < ntile) {
+                        sx += u[k].x;
+                        sy += u[k].y;
+                        sz += u[k].z;
+                    }
             }
             const int j = sid[q];
             atomicAdd(&J[o + j].x, f * sx);
@@ -847,12 +851,12 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                     coord_tile_kernel<R, 3><<<gt, CT_T, 0, st>>>(
                         pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, 3, gp,
                         (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
-                        cv.tile_tk, Jc, xi, c);
+                        cv.tile_tk, Jc, xi, c, cv.n_b < 0 ? nullptr : cv.inv_b);
                 else
                     coord_tile_kernel<R, 0><<<gt, CT_T, 0, st>>>(
                         pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, cv.nn / 2, gp,
                         (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
-                        cv.tile_tk, Jc, xi, c);
+                        cv.tile_tk, Jc, xi, c, cv.n_b < 0 ? nullptr : cv.inv_b);
                 mark(h, "coord_tile");
                 break;
             }

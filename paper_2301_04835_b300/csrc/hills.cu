@@ -24,6 +24,8 @@
 //     finishes last (one launch, deterministic, no CTA waits for another).
 // FP64 path: the same sum in double with exp(), for parity at 1e-12.
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "hills_dev.cuh"
 
@@ -236,9 +238,6 @@ static void launch_f64_t(int th, dim3 grid, cudaStream_t st, const dbl4* hills, 
     }
 }
 
-int hills_plan_override_th = 0;     // autotuner / benchmark hooks (0 = heuristic)
-int hills_plan_override_split = 0;
-
 // Make sure the split-partials scratch is large enough for P points with the
 // plan launch_hills will pick (call outside graph capture).
 int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
@@ -246,7 +245,6 @@ int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
     Plan pl = plan_for(P, h->cap_pairs);
     for (auto& t : h->tuned)
         if (t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
-    if (hills_plan_override_split) pl.split = hills_plan_override_split;
     const size_t need = (size_t)pl.split * (size_t)P * sizeof(dbl4);
     if (need > h->partial_bytes) {
         cudaFree(h->partial);
@@ -276,8 +274,6 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
     Plan pl = plan_for(P, cap_pairs);
     for (auto& t : h->tuned)
         if (max_hills <= 0 && t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
-    if (hills_plan_override_th) pl.th = hills_plan_override_th;
-    if (hills_plan_override_split) pl.split = hills_plan_override_split;
     const int tp = HB / pl.th;
     const long long tiles = (P + tp - 1) / tp;
     if (tiles > 0x7fffffff) return WTMD_EINVAL;
@@ -351,6 +347,79 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         }
     }
     WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+// Plan autotuner for P points: times every (hill lanes per point, hill
+// splits) candidate on the handle's current hill list and keeps the fastest
+// for later launches with P points (step path, bias_eval, hills_eval).
+int hills_tune(wtmd_t* h, int64_t P, int* th_out, int* split_out, double* ms_out)
+{
+    if (P < 1 || P > (1 << 24)) {
+        h->err = "hills_tune: P out of range";
+        return WTMD_EINVAL;
+    }
+    const int d = h->d;
+    const size_t rs = h->prec == WTMD_F32 ? sizeof(float) : sizeof(double);
+    double c[3] = {0.0, 0.0, 0.0};
+    WTMD_CUDA_TRY(h, cudaMemcpy(c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    std::vector<char> host((size_t)P * d * rs);
+    for (int64_t p = 0; p < P; ++p)
+        for (int i = 0; i < d; ++i) {
+            const double v = std::isnan(c[i]) ? 0.0 : c[i];
+            if (h->prec == WTMD_F32) reinterpret_cast<float*>(host.data())[p * d + i] = (float)v;
+            else reinterpret_cast<double*>(host.data())[p * d + i] = v;
+        }
+    void *xi = nullptr, *V = nullptr, *dV = nullptr;
+    WTMD_CUDA_TRY(h, cudaMalloc(&xi, host.size()));
+    WTMD_CUDA_TRY(h, cudaMalloc(&V, (size_t)P * rs));
+    WTMD_CUDA_TRY(h, cudaMalloc(&dV, (size_t)P * d * rs));
+    WTMD_CUDA_TRY(h, cudaMemcpy(xi, host.data(), host.size(), cudaMemcpyHostToDevice));
+    const long long key = (P << 2) | d;
+    h->tuned.erase(std::remove_if(h->tuned.begin(), h->tuned.end(), [&](const std::pair<long long, Tuned>& t) {
+                       return t.first == key;
+                   }),
+                   h->tuned.end());
+    const long long nch = (h->cap_pairs + CHUNK - 1) / CHUNK;
+    const int ths[] = {1, 4, 32, 256};
+    const int splits[] = {1, 2, 4, 8, 16, 32, 64, 96, 128, 148, 192, 296, 444, 592, 888, 1184};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    Tuned bt = {plan_for(P, h->cap_pairs).th, plan_for(P, h->cap_pairs).split};
+    int rc = WTMD_OK;
+    for (int th : ths) {
+        const long long tiles = (P + HB / th - 1) / (HB / th);
+        for (int sp : splits) {
+            if (sp > nch || tiles * sp > (1ll << 20) || (size_t)sp * P * sizeof(dbl4) > (256ull << 20)) continue;
+            h->tuned.push_back({key, Tuned{th, sp}});
+            for (int r = 0; r < 2 && rc == WTMD_OK; ++r) rc = launch_hills(h, xi, h->prec == WTMD_F64, d, P, V, dV, d);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 10 && rc == WTMD_OK; ++r) rc = launch_hills(h, xi, h->prec == WTMD_F64, d, P, V, dV, d);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            h->tuned.pop_back();
+            if (rc) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = Tuned{th, sp};
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(xi);
+    cudaFree(V);
+    cudaFree(dV);
+    if (rc) return rc;
+    h->tuned.push_back({key, bt});
+    if (th_out) *th_out = bt.th;
+    if (split_out) *split_out = bt.split;
+    if (ms_out) *ms_out = best / 10.0;
     return WTMD_OK;
 }
 

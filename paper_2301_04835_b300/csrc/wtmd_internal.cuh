@@ -357,7 +357,8 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t 
 // handles); max_hills > 0 bounds the range's length for the launch plan
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
                        int dV_stride, const long long* k0p, const long long* k1p, long long max_hills);
-long long surrogate_tail_bound(const wtmd_t* h);                // hills beyond k0 between refits (0: unbounded)
+long long surrogate_tail_bound(const wtmd_t* h);
+int hills_tune(wtmd_t* h, int64_t P, int* th, int* split, double* ms);  // hills.cu                // hills beyond k0 between refits (0: unbounded)
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 int launch_scatter_deposit(wtmd_t* h);                          // kick + deposit (+ grid) of a step
 // surrogate (mlp.cu)

@@ -395,3 +395,25 @@ def test_invalid_arguments_are_rejected():
     assert wt.lib().fes_grid(m.h, None, 0) == wt.EINVAL  # no grid configured
     with pytest.raises(wt.WtmdError):
         wt.Wtmd(precision="f64", sigma=[0.1], gamma=0.5, walker_sizes=[1])
+
+
+def test_hills_tune_keeps_results():
+    """The plan autotuner changes only the launch shape: V and dV/dxi after
+    tuning agree with the oracle as before (FP32 bound), and the choice is a
+    valid plan."""
+    wt = _wt()
+    import oracle as o
+
+    spec, x, L = lj_fluid_spec(n=500, n_tag=50, n_rg=20, seed=3, jitter=0.05)
+    m = gpu_handle(spec, "f32")
+    pos = wt.particles(_f32(x), torch.float32)
+    _, xi0, _ = m.bias_eval(pos)
+    c = to_np(xi0)[0]
+    hills = synth.walk_hills(3000, c - 0.3, c + 0.3, 0.05, seed=4)
+    m.hills_load(hills)
+    th, sp, ms = m.hills_tune(1)
+    assert th in (1, 4, 32, 256) and sp >= 1 and ms > 0
+    V, xi, dV = m.bias_eval(pos)
+    Vr, dVr = o.hills_sum(to_np(xi), hills, spec["sigma"])
+    _close_V(to_np(V), Vr, "f32")
+    _close_dV(to_np(dV), dVr, grad_scale(to_np(xi), hills, spec["sigma"]), "f32")
