@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-walkers", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--case", choices=["hills", "walkers", "mlp"], default=None,
+                    help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
     return ap.parse_args()
 
 
@@ -618,8 +620,59 @@ def cpu_baseline_oracle(seconds: float, max_steps: int | None = None):
 
 
 # --------------------------------------------------------------------------
+def run_case(name: str):
+    """One representative launch configuration of a hot kernel, repeated a
+    few times: `hills` = FP32 hills sum, 1e6 hills, 4096 points, d = 2;
+    `walkers` = the 256-cluster persistent step; `mlp` = network inference at
+    4096 points and training steps on 4096 samples."""
+    import torch
+
+    import paper_2301_04835_b300 as wt
+    import synth
+
+    dev = torch.device("cuda", 0)
+    if name == "hills":
+        H, P = 1_000_000, 4096
+        m = wt.Wtmd(precision="f32", sigma=(0.05, 0.1), capacity=H, walker_sizes=[1])
+        for i in range(2):
+            m.cv_define(wt.CV_COMPONENT, a=[0], axis=i)
+        m.hills_load(synth.uniform_hills(H, [0, 0], [1, 1], seed=13))
+        pts = torch.tensor(synth.uniform_points(P, [0, 0], [1, 1], seed=P + 2), dtype=torch.float32, device=dev)
+        V = torch.empty(P, dtype=torch.float32, device=dev)
+        dV = torch.empty(P, 2, dtype=torch.float32, device=dev)
+        for _ in range(5):
+            m.hills_eval_into(pts, V, dV)
+    elif name == "walkers":
+        sizes, x, v, hills, grid = cluster_inputs(wt, torch)
+        m = cluster_handle(wt, sizes, grid=grid)
+        m.hills_load(hills)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        m.walkers_persistent(True)
+        m.step_n(8)
+    else:
+        m = wt.Wtmd(precision="f32", sigma=(0.4, 0.4, 0.4), capacity=16, walker_sizes=[1])
+        for i in range(3):
+            m.cv_define(wt.CV_COMPONENT, a=[0], axis=i)
+        r = synth.rng(5)
+        m.mlp_params(r.normal(scale=0.3, size=4481), np.array([0, 0, 0, 1, 1, 1, 0, 1.0]))
+        P = 4096
+        x = torch.tensor(r.normal(size=(P, 3)), device=dev)
+        Vt = torch.tensor(r.normal(size=P), dtype=torch.float32, device=dev)
+        Gt = torch.tensor(r.normal(size=(P, 3)), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            m.mlp_eval(x)
+        m.mlp_train(x, Vt, Gt, P, 5, 1e-3, 0.1)
+    torch.cuda.synchronize()
+    m.check()
+    print(f"case {name}: ok")
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args.case)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

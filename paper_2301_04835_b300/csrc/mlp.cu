@@ -20,8 +20,10 @@
 //                     path adds them to the exact tail sum);
 //   mlp_grad_kernel   Sobolev loss sum_b (y - V)^2 + lam |grad_x y - G|^2 and
 //                     its weight gradient: forward, input gradient and the
-//                     double backward through it, accumulated per lane in
-//                     registers, reduced per block in a fixed order;
+//                     double backward through it per warp; W2's gradient (a
+//                     sum of outer products) accumulated block-wide, 16
+//                     entries per thread, the rest per lane and reduced per
+//                     block in a fixed order;
 //   mlp_adam_kernel   fixed-order sum of the block partials and the Adam
 //                     update (Kingma & Ba 2015) of the FP32 master, which is
 //                     re-rounded to bfloat16 (nearest, ties to even).
@@ -46,12 +48,15 @@ namespace wtmd {
 
 constexpr int MH = 64;      // hidden width
 constexpr int MP = 4481;    // parameters
+constexpr int PSTRIDE = (MP + 1 + 3) / 4 * 4;  // floats per block partial (gradient + loss), 16-byte rows
 constexpr int O_W1 = 0, O_B1 = 192, O_W2 = 256, O_B2 = 4352, O_W3 = 4416, O_B3 = 4480;
 constexpr int W2P = 68;     // shared row pitch of W2: 16-byte rows, conflict-free quad loads
-constexpr int MLP_T = 128;  // threads per block
+constexpr int MLP_T = 256;  // threads per block of the training kernel
 constexpr int MLP_W = MLP_T / 32;
-constexpr int RW2P = 65;    // pitch of the transposed W2 gradient in the block reduction
-constexpr int RED_N = O_W2 + MH * RW2P + (MP - O_B2) + 1;  // + loss
+constexpr int EV_T = 256;   // threads per block of the inference kernel (one network staging per 8 warps)
+constexpr int EV_W = EV_T / 32;
+// block-reduction slots of the parameters other than W2 (+ the loss)
+constexpr int RB_B2 = O_W2, RB_W3 = RB_B2 + MH, RB_B3 = RB_W3 + MH, RB_LOSS = RB_B3 + 1, RED_N = RB_LOSS + 1;
 
 struct MlpW;
 
@@ -65,9 +70,9 @@ struct Surrogate {
     long long* k0 = nullptr;        // device: first hill of the exact tail (0 while inactive)
     long long* kend = nullptr;      // device: end of the fitted hill range
     int* active = nullptr;          // device flag read by the step path
-    long long* ctr = nullptr;       // device [2]: Adam step t, batch iteration
-    unsigned* ticket = nullptr;
-    float* partial = nullptr;       // [pblocks][MP + 1]
+    long long* ctr = nullptr;       // device [2]: (unused), batch iteration of the training launches
+    long long adam_t = 0;           // Adam steps taken (host copy; bias corrections)
+    float* partial = nullptr;       // [pblocks][PSTRIDE]
     int pblocks = 0;
     float* loss = nullptr;          // device: loss of the last training step
     float* grad = nullptr;          // device [MP + 1] scratch of wtmd_mlp_grad
@@ -169,15 +174,17 @@ __device__ __forceinline__ void warp_forward(const MlpW& s, const float x[3], fl
         const int i = lane + 32 * r;
         const float4* wr = reinterpret_cast<const float4*>(&s.W2[i][0]);
         const float4* av = reinterpret_cast<const float4*>(A1);
-        float z = s.b2[i];
-#pragma unroll 4
+        // four partial sums (by column mod 4): four short dependency chains
+        float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll 8
         for (int q = 0; q < MH / 4; ++q) {
             const float4 w = wr[q], a = av[q];
-            z = fmaf(w.x, a.x, z);
-            z = fmaf(w.y, a.y, z);
-            z = fmaf(w.z, a.z, z);
-            z = fmaf(w.w, a.w, z);
+            z0 = fmaf(w.x, a.x, z0);
+            z1 = fmaf(w.y, a.y, z1);
+            z2 = fmaf(w.z, a.z, z2);
+            z3 = fmaf(w.w, a.w, z3);
         }
+        const float z = s.b2[i] + ((z0 + z1) + (z2 + z3));
         const float sg = sigm(z);
         f.z2[r] = z;
         f.a2[r] = z * sg;
@@ -192,9 +199,15 @@ __device__ __forceinline__ void warp_forward(const MlpW& s, const float x[3], fl
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int j = lane + 32 * r;
-        float hs = 0.f;
+        float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f;
 #pragma unroll 8
-        for (int i = 0; i < MH; ++i) hs = fmaf(s.W2[i][j], G2[i], hs);
+        for (int i = 0; i < MH; i += 4) {
+            h0 = fmaf(s.W2[i][j], G2[i], h0);
+            h1 = fmaf(s.W2[i + 1][j], G2[i + 1], h1);
+            h2 = fmaf(s.W2[i + 2][j], G2[i + 2], h2);
+            h3 = fmaf(s.W2[i + 3][j], G2[i + 3], h3);
+        }
+        const float hs = (h0 + h1) + (h2 + h3);
         f.h1[r] = hs;
         const float g1 = f.d1[r] * hs;
         u0 = fmaf(s.W1[j][0], g1, u0);
@@ -216,7 +229,7 @@ __device__ __forceinline__ float silu_dd(float z)
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const MlpW* __restrict__ img,
+__global__ void __launch_bounds__(EV_T) mlp_eval_kernel(const MlpW* __restrict__ img,
                                                          const double* __restrict__ norm, const int* __restrict__ active,
                                                          const double* __restrict__ xi, int xs, int d, int P,
                                                          float* __restrict__ V, float* __restrict__ dV, int dvs,
@@ -224,24 +237,29 @@ __global__ void __launch_bounds__(MLP_T) mlp_eval_kernel(const MlpW* __restrict_
 {
     if (active && *active == 0) return;
     __shared__ __align__(16) MlpW s;
-    __shared__ __align__(16) float A1[MLP_W][MH];
-    __shared__ __align__(16) float G2[MLP_W][MH];
+    __shared__ __align__(16) float A1[EV_W][MH];
+    __shared__ __align__(16) float G2[EV_W][MH];
     mlp_stage(img, s);
     __syncthreads();
     const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
-    for (int p = blockIdx.x * MLP_W + w; p < P; p += gridDim.x * MLP_W) {
+    for (int p = blockIdx.x * EV_W + w; p < P; p += gridDim.x * EV_W) {
         float x[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < d; ++k) x[k] = (float)((xi[(size_t)p * xs + k] - norm[k]) * norm[3 + k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (k < d) x[k] = (float)((xi[(size_t)p * xs + k] - norm[k]) * norm[3 + k]);
         Fwd f;
         warp_forward(s, x, A1[w], G2[w], f);
         if (lane == 0) {
             const float Vn = (float)(norm[7] * (double)f.y + norm[6]);
             if (V) V[p] = add ? V[p] + Vn : Vn;
-            if (dV)
-                for (int k = 0; k < d; ++k) {
-                    const float g = (float)(norm[7] * norm[3 + k]) * f.u[k];
-                    dV[(size_t)p * dvs + k] = add ? dV[(size_t)p * dvs + k] + g : g;
-                }
+            if (dV) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (k < d) {
+                        const float g = (float)(norm[7] * norm[3 + k]) * f.u[k];
+                        dV[(size_t)p * dvs + k] = add ? dV[(size_t)p * dvs + k] + g : g;
+                    }
+            }
         }
         __syncwarp();
     }
@@ -259,16 +277,19 @@ struct TrainArgs {
     long long perm;         // sample order: index (q * perm) mod n, perm coprime with n
     int d;
     float lam;
-    float* partial;         // [gridDim.x][MP + 1]
+    float* partial;         // [gridDim.x][PSTRIDE]
 };
 
-__global__ void __launch_bounds__(MLP_T, 2) mlp_grad_kernel(TrainArgs a)
+static_assert(MH * MH % MLP_T == 0 && (MH * MH / MLP_T) % 4 == 0, "outer-product ownership");
+
+__global__ void __launch_bounds__(MLP_T) mlp_grad_kernel(TrainArgs a)
 {
     __shared__ __align__(16) MlpW s;
     __shared__ __align__(16) float A1[MLP_W][MH];
     __shared__ __align__(16) float G2[MLP_W][MH];
     __shared__ __align__(16) float HB[MLP_W][MH];
     __shared__ __align__(16) float Z2[MLP_W][MH];
+    __shared__ int has[MLP_W];
     mlp_stage(a.img, s);
     __syncthreads();
     const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -279,93 +300,119 @@ __global__ void __launch_bounds__(MLP_T, 2) mlp_grad_kernel(TrainArgs a)
     const double Vm = a.norm[6], iVs = 1.0 / a.norm[7];
     const float invB = 1.f / (float)a.B;
 
-    float acc2[2][MH];
+    // W2's gradient sum_b (zb2 a1^T + g2 hb1^T) is accumulated by the whole
+    // block: thread t owns OCOL consecutive entries of row t / (64 / OCOL)
+    // and adds the outer products of the samples of all warps after each
+    // round
+    constexpr int OCOL = MH * MH / MLP_T;
+    const int oi = threadIdx.x / (MH / OCOL), oj = (threadIdx.x % (MH / OCOL)) * OCOL;
+    float acc2[OCOL];
+#pragma unroll
+    for (int k = 0; k < OCOL; ++k) acc2[k] = 0.f;
     float acc1[2][3], ab1[2], ab2[2], aw3[2];
     float ab3 = 0.f, aloss = 0.f;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-#pragma unroll
-        for (int j = 0; j < MH; ++j) acc2[r][j] = 0.f;
         acc1[r][0] = acc1[r][1] = acc1[r][2] = 0.f;
         ab1[r] = ab2[r] = aw3[r] = 0.f;
     }
 
-    for (int sm = gw; sm < a.B; sm += nw) {
-        const long long q = (it * a.B + sm) % a.n;
-        const long long idx = (q * a.perm) % a.n;
-        float x[3] = {0.f, 0.f, 0.f}, Gt[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < a.d; ++k) {
-            x[k] = (float)((a.x[idx * 3 + k] - a.norm[k]) * a.norm[3 + k]);
-            Gt[k] = a.G[idx * 3 + k] * gsc[k];
-        }
-        const float Vt = (float)(((double)a.V[idx] - Vm) * iVs);
-        Fwd f;
-        warp_forward(s, x, A1[w], G2[w], f);
-        const float r = f.y - Vt;
-        float e[3], du[3];
-        for (int k = 0; k < 3; ++k) {
-            e[k] = f.u[k] - Gt[k];
-            du[k] = 2.f * a.lam * e[k] * invB;
-        }
-        const float dy = 2.f * r * invB;
-        if (lane == 0) aloss += r * r + a.lam * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-        // upstream of g1 = silu'(z1) * h1 through u = W1^T g1
-        float gb1[2];
+    const int rounds = (a.B + nw - 1) / nw;
+    for (int rd = 0; rd < rounds; ++rd) {
+        const int sm = gw + rd * nw;
+        if (lane == 0) has[w] = sm < a.B;
+        if (sm < a.B) {
+            const long long q = (it * a.B + sm) % a.n;
+            const long long idx = (q * a.perm) % a.n;
+            float x[3] = {0.f, 0.f, 0.f}, Gt[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int j = lane + 32 * rr;
-            gb1[rr] = fmaf(s.W1[j][0], du[0], fmaf(s.W1[j][1], du[1], s.W1[j][2] * du[2]));
-            HB[w][j] = gb1[rr] * f.d1[rr];  // upstream of h1
-        }
-        __syncwarp();
+            for (int k = 0; k < 3; ++k)
+                if (k < a.d) {
+                    x[k] = (float)((a.x[idx * 3 + k] - a.norm[k]) * a.norm[3 + k]);
+                    Gt[k] = a.G[idx * 3 + k] * gsc[k];
+                }
+            const float Vt = (float)(((double)a.V[idx] - Vm) * iVs);
+            Fwd f;
+            warp_forward(s, x, A1[w], G2[w], f);
+            const float r = f.y - Vt;
+            float e[3], du[3];
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int i = lane + 32 * rr;
-            const float4* wr = reinterpret_cast<const float4*>(&s.W2[i][0]);
-            const float4* hb = reinterpret_cast<const float4*>(HB[w]);
-            float gb2 = 0.f;  // upstream of g2 = W2 hb1
-#pragma unroll 4
-            for (int qq = 0; qq < MH / 4; ++qq) {
-                const float4 ww = wr[qq], hh = hb[qq];
-                gb2 = fmaf(ww.x, hh.x, gb2);
-                gb2 = fmaf(ww.y, hh.y, gb2);
-                gb2 = fmaf(ww.z, hh.z, gb2);
-                gb2 = fmaf(ww.w, hh.w, gb2);
+            for (int k = 0; k < 3; ++k) {
+                e[k] = f.u[k] - Gt[k];
+                du[k] = 2.f * a.lam * e[k] * invB;
             }
-            const float w3 = s.w3[i];
-            const float zb2 = fmaf(dy * w3, f.d2[rr], gb2 * w3 * silu_dd(f.z2[rr]));
-            aw3[rr] = fmaf(dy, f.a2[rr], fmaf(gb2, f.d2[rr], aw3[rr]));
-            ab2[rr] += zb2;
-            const float g2 = f.g2[rr];
-            const float4* av = reinterpret_cast<const float4*>(A1[w]);
+            const float dy = 2.f * r * invB;
+            if (lane == 0) aloss += r * r + a.lam * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            // upstream of g1 = silu'(z1) * h1 through u = W1^T g1
+            float gb1[2];
 #pragma unroll
-            for (int qq = 0; qq < MH / 4; ++qq) {
-                const float4 aa = av[qq], hh = hb[qq];
-                acc2[rr][4 * qq + 0] = fmaf(zb2, aa.x, fmaf(g2, hh.x, acc2[rr][4 * qq + 0]));
-                acc2[rr][4 * qq + 1] = fmaf(zb2, aa.y, fmaf(g2, hh.y, acc2[rr][4 * qq + 1]));
-                acc2[rr][4 * qq + 2] = fmaf(zb2, aa.z, fmaf(g2, hh.z, acc2[rr][4 * qq + 2]));
-                acc2[rr][4 * qq + 3] = fmaf(zb2, aa.w, fmaf(g2, hh.w, acc2[rr][4 * qq + 3]));
+            for (int rr = 0; rr < 2; ++rr) {
+                const int j = lane + 32 * rr;
+                gb1[rr] = fmaf(s.W1[j][0], du[0], fmaf(s.W1[j][1], du[1], s.W1[j][2] * du[2]));
+                HB[w][j] = gb1[rr] * f.d1[rr];  // upstream of h1
             }
-            Z2[w][i] = zb2;
-        }
-        __syncwarp();
+            __syncwarp();
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int j = lane + 32 * rr;
-            float ab = 0.f;  // upstream of a1 = W2^T zb2
+            for (int rr = 0; rr < 2; ++rr) {
+                const int i = lane + 32 * rr;
+                const float4* wr = reinterpret_cast<const float4*>(&s.W2[i][0]);
+                const float4* hb = reinterpret_cast<const float4*>(HB[w]);
+                float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;  // upstream of g2 = W2 hb1
 #pragma unroll 8
-            for (int i = 0; i < MH; ++i) ab = fmaf(s.W2[i][j], Z2[w][i], ab);
-            const float zb1 = fmaf(ab, f.d1[rr], gb1[rr] * f.h1[rr] * silu_dd(f.z1[rr]));
-            const float g1 = f.d1[rr] * f.h1[rr];
-            for (int k = 0; k < 3; ++k) acc1[rr][k] = fmaf(zb1, x[k], fmaf(g1, du[k], acc1[rr][k]));
-            ab1[rr] += zb1;
+                for (int qq = 0; qq < MH / 4; ++qq) {
+                    const float4 ww = wr[qq], hh = hb[qq];
+                    q0 = fmaf(ww.x, hh.x, q0);
+                    q1 = fmaf(ww.y, hh.y, q1);
+                    q2 = fmaf(ww.z, hh.z, q2);
+                    q3 = fmaf(ww.w, hh.w, q3);
+                }
+                const float gb2 = (q0 + q1) + (q2 + q3);
+                const float w3 = s.w3[i];
+                const float zb2 = fmaf(dy * w3, f.d2[rr], gb2 * w3 * silu_dd(f.z2[rr]));
+                aw3[rr] = fmaf(dy, f.a2[rr], fmaf(gb2, f.d2[rr], aw3[rr]));
+                ab2[rr] += zb2;
+                Z2[w][i] = zb2;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int j = lane + 32 * rr;
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;  // upstream of a1 = W2^T zb2
+#pragma unroll 8
+                for (int i = 0; i < MH; i += 4) {
+                    c0 = fmaf(s.W2[i][j], Z2[w][i], c0);
+                    c1 = fmaf(s.W2[i + 1][j], Z2[w][i + 1], c1);
+                    c2 = fmaf(s.W2[i + 2][j], Z2[w][i + 2], c2);
+                    c3 = fmaf(s.W2[i + 3][j], Z2[w][i + 3], c3);
+                }
+                const float ab = (c0 + c1) + (c2 + c3);
+                const float zb1 = fmaf(ab, f.d1[rr], gb1[rr] * f.h1[rr] * silu_dd(f.z1[rr]));
+                const float g1 = f.d1[rr] * f.h1[rr];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc1[rr][k] = fmaf(zb1, x[k], fmaf(g1, du[k], acc1[rr][k]));
+                ab1[rr] += zb1;
+            }
+            if (lane == 0) ab3 += dy;
         }
-        if (lane == 0) ab3 += dy;
-        __syncwarp();
+        __syncthreads();  // every warp's a1, g2, hb1, zb2 of this round are in shared memory
+        for (int ww = 0; ww < MLP_W; ++ww) {
+            if (!has[ww]) continue;
+            const float zi = Z2[ww][oi], gi = G2[ww][oi];
+            const float4* av = reinterpret_cast<const float4*>(&A1[ww][oj]);
+            const float4* hv = reinterpret_cast<const float4*>(&HB[ww][oj]);
+#pragma unroll
+            for (int qq = 0; qq < OCOL / 4; ++qq) {
+                const float4 aa = av[qq], hh = hv[qq];
+                acc2[4 * qq + 0] = fmaf(zi, aa.x, fmaf(gi, hh.x, acc2[4 * qq + 0]));
+                acc2[4 * qq + 1] = fmaf(zi, aa.y, fmaf(gi, hh.y, acc2[4 * qq + 1]));
+                acc2[4 * qq + 2] = fmaf(zi, aa.z, fmaf(gi, hh.z, acc2[4 * qq + 2]));
+                acc2[4 * qq + 3] = fmaf(zi, aa.w, fmaf(gi, hh.w, acc2[4 * qq + 3]));
+            }
+        }
+        __syncthreads();  // before the next round overwrites the vectors
     }
 
-    // block sum in warp order; W2's gradient is kept transposed (pitch 65)
-    // so that both the per-lane adds and the final copy are conflict-free
+    // the other parameters: block sum in warp order
     __shared__ float red[RED_N];
     for (int q = threadIdx.x; q < RED_N; q += MLP_T) red[q] = 0.f;
     __syncthreads();
@@ -374,89 +421,100 @@ __global__ void __launch_bounds__(MLP_T, 2) mlp_grad_kernel(TrainArgs a)
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
                 const int i = lane + 32 * rr;
-#pragma unroll
-                for (int j = 0; j < MH; ++j) red[O_W2 + j * RW2P + i] += acc2[rr][j];
-                red[O_W2 + MH * RW2P + (i)] += ab2[rr];               // b2
-                red[O_W2 + MH * RW2P + MH + i] += aw3[rr];            // w3
-                for (int k = 0; k < 3; ++k) red[i * 3 + k] += acc1[rr][k];  // W1 row j = i
+                red[RB_B2 + i] += ab2[rr];
+                red[RB_W3 + i] += aw3[rr];
+                for (int k = 0; k < 3; ++k) red[i * 3 + k] += acc1[rr][k];  // W1 row i
                 red[O_B1 + i] += ab1[rr];
             }
             if (lane == 0) {
-                red[O_W2 + MH * RW2P + 2 * MH] += ab3;
-                red[RED_N - 1] += aloss;
+                red[RB_B3] += ab3;
+                red[RB_LOSS] += aloss;
             }
         }
         __syncthreads();
     }
-    float* out = a.partial + (size_t)blockIdx.x * (MP + 1);
+    float* out = a.partial + (size_t)blockIdx.x * PSTRIDE;
+    float4* o2 = reinterpret_cast<float4*>(out + O_W2 + oi * MH + oj);
+#pragma unroll
+    for (int qq = 0; qq < OCOL / 4; ++qq)
+        o2[qq] = make_float4(acc2[4 * qq], acc2[4 * qq + 1], acc2[4 * qq + 2], acc2[4 * qq + 3]);
     for (int q = threadIdx.x; q < MP + 1; q += MLP_T) {
-        float v;
-        if (q < O_W2) {
-            v = red[q];
-        } else if (q < O_B2) {
-            const int rq = q - O_W2;
-            v = red[O_W2 + (rq % MH) * RW2P + rq / MH];
-        } else if (q < MP) {
-            v = red[O_W2 + MH * RW2P + (q - O_B2)];
-        } else {
-            v = red[RED_N - 1];
-        }
-        out[q] = v;
+        if (q < O_W2) out[q] = red[q];
+        else if (q >= O_B2 && q < O_W3) out[q] = red[RB_B2 + (q - O_B2)];
+        else if (q >= O_W3 && q < O_B3) out[q] = red[RB_W3 + (q - O_W3)];
+        else if (q == O_B3) out[q] = red[RB_B3];
+        else if (q == MP) out[q] = red[RB_LOSS];
     }
 }
 
-// Fixed-order sum of the block partials: gradient and mean loss only.
-__global__ void mlp_reduce_kernel(const float* __restrict__ partial, int nblk, float invB, float* __restrict__ out)
+// Block sums of the training partials: a block of AD_T threads covers AD_Q
+// consecutive entries (the 4481 parameters, then the loss); warp w adds the
+// partials b = w, w + 8, ... of its lane's entry (eight loads in flight),
+// then the eight warp sums are added in warp order: a fixed order.
+constexpr int AD_T = 256, AD_Q = 32;
+
+__device__ __forceinline__ float block_partial_sum(const float* __restrict__ partial, int nblk, int q)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q > MP) return;
+    __shared__ float ps[AD_T / 32][AD_Q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float g = 0.f;
-    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * (MP + 1) + q];
-    out[q] = q == MP ? g * invB : g;
+    if (q <= MP)
+        for (int b0 = warp; b0 < nblk; b0 += 64) {
+            float t[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = b0 + 8 * k;
+                t[k] = b < nblk ? partial[(size_t)b * PSTRIDE + q] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) g += t[k];
+        }
+    ps[warp][lane] = g;
+    __syncthreads();
+    float tot = ps[0][lane];
+    for (int w = 1; w < AD_T / 32; ++w) tot += ps[w][lane];
+    return tot;  // valid in every warp
+}
+
+// Gradient and mean loss only.
+__global__ void __launch_bounds__(AD_T) mlp_reduce_kernel(const float* __restrict__ partial, int nblk, float invB,
+                                                          float* __restrict__ out)
+{
+    const int q = blockIdx.x * AD_Q + (threadIdx.x & 31);
+    const float g = block_partial_sum(partial, nblk, q);
+    if (threadIdx.x < 32 && q <= MP) out[q] = q == MP ? g * invB : g;
 }
 
 struct AdamPrm {
     float lr, b1, b2, eps, invB;
+    float bc1, bc2;  // bias corrections 1 - b1^t, 1 - b2^t of this step
 };
 
-__global__ void mlp_adam_kernel(const float* __restrict__ partial, int nblk, float* __restrict__ master,
-                                float* __restrict__ m, float* __restrict__ v, unsigned short* __restrict__ wb,
-                                MlpW* __restrict__ img, AdamPrm p, long long* __restrict__ ctr, unsigned* __restrict__ ticket,
-                                float* __restrict__ loss_out)
+__global__ void __launch_bounds__(AD_T) mlp_adam_kernel(const float* __restrict__ partial, int nblk,
+                                                        float* __restrict__ master, float* __restrict__ m,
+                                                        float* __restrict__ v, unsigned short* __restrict__ wb,
+                                                        MlpW* __restrict__ img, AdamPrm p, long long* __restrict__ ctr,
+                                                        float* __restrict__ loss_out)
 {
-    const long long t = ctr[0] + 1;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < MP) {
-        float g = 0.f;
-        for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * (MP + 1) + q];
-        const float mm = fmaf(p.b1, m[q], (1.f - p.b1) * g);
-        const float vv = fmaf(p.b2, v[q], (1.f - p.b2) * g * g);
-        const float bc1 = (float)(1.0 - pow((double)p.b1, (double)t));
-        const float bc2 = (float)(1.0 - pow((double)p.b2, (double)t));
-        const float th = master[q] - p.lr * (mm / bc1) / (sqrtf(vv / bc2) + p.eps);
-        master[q] = th;
-        m[q] = mm;
-        v[q] = vv;
-        const unsigned short b = f_to_bf16_bits(th);
-        wb[q] = b;
-        *img_slot(img, q) = bf16_bits_to_f(b);
+    const int q = blockIdx.x * AD_Q + (threadIdx.x & 31);
+    const float g = block_partial_sum(partial, nblk, q);
+    if (threadIdx.x < 32) {
+        if (q < MP) {
+            const float mm = fmaf(p.b1, m[q], (1.f - p.b1) * g);
+            const float vv = fmaf(p.b2, v[q], (1.f - p.b2) * g * g);
+            const float th = master[q] - p.lr * (mm / p.bc1) / (sqrtf(vv / p.bc2) + p.eps);
+            master[q] = th;
+            m[q] = mm;
+            v[q] = vv;
+            const unsigned short b = f_to_bf16_bits(th);
+            wb[q] = b;
+            *img_slot(img, q) = bf16_bits_to_f(b);
+        } else if (q == MP && loss_out) {
+            *loss_out = g * p.invB;
+        }
     }
-    // the last block advances the counters (every block has read them)
-    __shared__ int lastb;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        lastb = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (lastb && threadIdx.x == 0) {
-        float L = 0.f;
-        for (int b = 0; b < nblk; ++b) L += partial[(size_t)b * (MP + 1) + MP];
-        if (loss_out) *loss_out = L * p.invB;
-        ctr[0] = t;
-        ctr[1] += 1;
-        *ticket = 0u;
-    }
+    // the next training launch reads the batch counter after this kernel
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[1] += 1;
 }
 
 __global__ void mlp_round_kernel(const float* __restrict__ master, unsigned short* __restrict__ wb,
@@ -515,7 +573,7 @@ static uint64_t splitmix(uint64_t& s)
 void surrogate_free(Surrogate* s)
 {
     if (!s) return;
-    void* p[] = {s->master, s->wb, s->img, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr, s->ticket,
+    void* p[] = {s->master, s->wb, s->img, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr,
                  s->partial, s->loss, s->grad, s->sx, s->sV, s->sG, s->hV, s->hG};
     for (void* q : p) cudaFree(q);
     delete s;
@@ -545,11 +603,10 @@ static int sur_get(wtmd_t* h, Surrogate** out)
     WTMD_CUDA_TRY(h, cudaMalloc(&s->kend, sizeof(long long)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->active, sizeof(int)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->ctr, sizeof(long long) * 2));
-    WTMD_CUDA_TRY(h, cudaMalloc(&s->ticket, sizeof(unsigned)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->loss, sizeof(float)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->grad, sizeof(float) * (MP + 1)));
     s->pblocks = grad_blocks();
-    WTMD_CUDA_TRY(h, cudaMalloc(&s->partial, sizeof(float) * (MP + 1) * (size_t)s->pblocks));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->partial, sizeof(float) * PSTRIDE * (size_t)s->pblocks));
     std::vector<float> w(MP, 0.f);
     uint64_t st = s->seed;
     auto uni = [&](float lim) { return (float)(((splitmix(st) >> 11) * 0x1.0p-53 * 2.0 - 1.0) * lim); };
@@ -561,7 +618,6 @@ static int sur_get(wtmd_t* h, Surrogate** out)
     WTMD_CUDA_TRY(h, cudaMemset(s->m, 0, sizeof(float) * MP));
     WTMD_CUDA_TRY(h, cudaMemset(s->v, 0, sizeof(float) * MP));
     WTMD_CUDA_TRY(h, cudaMemset(s->ctr, 0, sizeof(long long) * 2));
-    WTMD_CUDA_TRY(h, cudaMemset(s->ticket, 0, sizeof(unsigned)));
     WTMD_CUDA_TRY(h, cudaMemset(s->k0, 0, sizeof(long long)));
     WTMD_CUDA_TRY(h, cudaMemset(s->active, 0, sizeof(int)));
     WTMD_CUDA_TRY(h, cudaMemcpy(s->norm, s->norm_h, sizeof(double) * 8, cudaMemcpyHostToDevice));
@@ -589,8 +645,8 @@ int launch_mlp_add(wtmd_t* h)
 {
     if (!h->sur || !h->sur->enabled) return WTMD_OK;
     Surrogate& s = *h->sur;
-    const int nb = std::max(1, std::min((h->W + MLP_W - 1) / MLP_W, 2 * grad_blocks()));
-    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s.img, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
+    const int nb = std::max(1, std::min((h->W + EV_W - 1) / EV_W, grad_blocks()));
+    mlp_eval_kernel<<<nb, EV_T, 0, h->stream>>>(s.img, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
                                                  (float*)h->dV, 4, 1);
     mark(h, "mlp_surrogate");
     WTMD_CUDA_TRY(h, cudaGetLastError());
@@ -606,12 +662,14 @@ static int launch_train(wtmd_t* h, const double* x, const float* V, const float*
     mlp_grad_kernel<<<nb, MLP_T, 0, h->stream>>>(a);
     mark(h, "mlp_grad");
     if (adam) {
-        AdamPrm p{(float)lr, 0.9f, 0.999f, 1e-8f, 1.f / (float)B};
-        mlp_adam_kernel<<<(MP + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, s.master, s.m, s.v, s.wb, s.img, p,
-                                                                 s.ctr, s.ticket, s.loss);
+        const long long t = ++s.adam_t;
+        AdamPrm p{(float)lr, 0.9f, 0.999f, 1e-8f, 1.f / (float)B, (float)(1.0 - std::pow(0.9, (double)t)),
+                  (float)(1.0 - std::pow(0.999, (double)t))};
+        mlp_adam_kernel<<<(MP + 1 + AD_Q - 1) / AD_Q, AD_T, 0, h->stream>>>(s.partial, nb, s.master, s.m, s.v, s.wb,
+                                                                            s.img, p, s.ctr, s.loss);
         mark(h, "mlp_adam");
     } else {
-        mlp_reduce_kernel<<<(MP + 1 + 255) / 256, 256, 0, h->stream>>>(s.partial, nb, 1.f / (float)B, grad_out);
+        mlp_reduce_kernel<<<(MP + 1 + AD_Q - 1) / AD_Q, AD_T, 0, h->stream>>>(s.partial, nb, 1.f / (float)B, grad_out);
     }
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
@@ -721,8 +779,8 @@ static int sur_fit(wtmd_t* h)
         if ((rc = launch_train(h, s.sx, s.sV, s.sG, Str, B, s.ctr + 1, perm, s.lam, true, lr, nullptr))) return rc;
     }
     // held-out error
-    const int nbe = (int)std::min<int64_t>((Sho + MLP_W - 1) / MLP_W, 4 * grad_blocks());
-    mlp_eval_kernel<<<std::max(nbe, 1), MLP_T, 0, h->stream>>>(s.img, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
+    const int nbe = (int)std::min<int64_t>((Sho + EV_W - 1) / EV_W, grad_blocks());
+    mlp_eval_kernel<<<std::max(nbe, 1), EV_T, 0, h->stream>>>(s.img, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
                                                                 (int)Sho, s.hV, s.hG, 3, 0);
     WTMD_CUDA_TRY(h, cudaGetLastError());
     std::vector<float> pv(Sho), tv(Sho), pg(3 * Sho), tg(3 * Sho);
@@ -949,6 +1007,7 @@ extern "C" int wtmd_mlp_params(wtmd_t* h, const float* in, float* out, const dou
         WTMD_CUDA_TRY(h, cudaMemset(s->m, 0, sizeof(float) * MP));
         WTMD_CUDA_TRY(h, cudaMemset(s->v, 0, sizeof(float) * MP));
         WTMD_CUDA_TRY(h, cudaMemset(s->ctr, 0, sizeof(long long) * 2));
+        s->adam_t = 0;
         mlp_round_kernel<<<(MP + 255) / 256, 256>>>(s->master, s->wb, s->img);
         WTMD_CUDA_TRY(h, cudaDeviceSynchronize());
     }
@@ -972,8 +1031,8 @@ extern "C" int wtmd_mlp_eval(wtmd_t* h, const double* xi, int64_t P, float* V, f
     if (rc) return rc;
     if (P == 0) return WTMD_OK;
     // each block stages the network once: a few blocks per SM, points by grid stride
-    const int nb = (int)std::min<int64_t>((P + MLP_W - 1) / MLP_W, grad_blocks());
-    mlp_eval_kernel<<<nb, MLP_T, 0, h->stream>>>(s->img, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
+    const int nb = (int)std::min<int64_t>((P + EV_W - 1) / EV_W, grad_blocks());
+    mlp_eval_kernel<<<nb, EV_T, 0, h->stream>>>(s->img, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
 }
