@@ -417,3 +417,62 @@ def test_hills_tune_keeps_results():
     Vr, dVr = o.hills_sum(to_np(xi), hills, spec["sigma"])
     _close_V(to_np(V), Vr, "f32")
     _close_dV(to_np(dV), dVr, grad_scale(to_np(xi), hills, spec["sigma"]), "f32")
+
+
+def test_frozen_walker_heights_follow_the_well_tempered_recursion():
+    """A walker that cannot move (no engine, no noise, zero velocity; the
+    bias gradient vanishes at a hill's own centre) deposits every stride
+    steps at the same point, so the heights obey the scalar recursion
+    V_{k+1} = V_k + w_k, w_k = w0 exp(-V_k / (kT (gamma - 1))) of Sec. 2.1.5
+    exactly (FP64 handle)."""
+    wt = _wt()
+    spec = dict(engine="none", walker_sizes=[1], dims=3, dt=1e-3, kT=2.0, friction=0.0, sigma=(0.3, 0.2),
+                w0=1.5, gamma=6.0, stride=3, capacity=64,
+                cvs=[dict(kind="component", a=[0], axis=0), dict(kind="component", a=[0], axis=1)])
+    m = gpu_handle(spec, "f64")
+    pos = wt.particles([[0.4, -0.7, 0.0]], torch.float64)
+    vel, F = torch.zeros_like(pos), torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(60)
+    h = m.hills_read()
+    assert h.shape[0] == 20
+    assert np.all(h[:, 0] == 0.4) and np.all(h[:, 1] == -0.7)
+    V, ref = 0.0, []
+    for _ in range(20):
+        w = 1.5 * np.exp(-V / (2.0 * 5.0))
+        ref.append(w)
+        V += w
+    assert np.allclose(h[:, 3], ref, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_standard_metadynamics_and_no_deposition(prec):
+    """gamma = 0 deposits fixed heights w0 (standard metadynamics); stride = 0
+    never deposits; both against the oracle's trajectory."""
+    import oracle as o
+
+    wt = _wt()
+    dt = torch.float32 if prec == "f32" else torch.float64
+    base = dict(engine="mb", walker_sizes=[1, 1], dims=2, dt=1e-4, friction=1.0, kT=15.0, seed=2,
+                sigma=(0.05, 0.05), w0=0.7, capacity=100,
+                cvs=[dict(kind="component", a=[0], axis=0), dict(kind="component", a=[0], axis=1)])
+    x = np.array([[-0.558, 1.442, 0], [0.623, 0.028, 0]])
+    for extra, nh in ((dict(gamma=0.0, stride=5), 2 * 8), (dict(gamma=10.0, stride=0), 0)):
+        spec = dict(base, **extra)
+        xin = _f32(x) if prec == "f32" else x
+        sim = o.Sim(oracle_system(spec), x=xin, v=np.zeros_like(x))
+        sim.forces()
+        assert sim.run(40) == 0
+        m = gpu_handle(spec, prec)
+        pos, vel = wt.particles(xin, dt), wt.particles(np.zeros_like(x), dt)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        m.step_n(40)
+        torch.cuda.synchronize()
+        assert m.counters() == (40, nh) and sim.n_hills == nh
+        if nh:
+            h = m.hills_read()
+            assert np.all(h[:, 3] == 0.7)
+            assert np.allclose(h[:, :2], sim.hills[:nh, :2], rtol=0, atol=1e-5 if prec == "f32" else 1e-12)
+        tol = 1e-4 if prec == "f32" else 1e-12
+        assert np.max(np.abs(to_np(pos)[:, :3] - sim.x)) < tol
