@@ -479,6 +479,10 @@ int walkers_enable(wtmd_t* h)
         h->err = "walkers above 8192 atoms do not fit the staged-positions design";
         return WTMD_EINVAL;
     }
+    if (surrogate_k0(h)) {
+        h->err = "turn the surrogate off before the persistent walker step";
+        return WTMD_EINVAL;
+    }
     const int T = h->wk.T ? h->wk.T : 128, bps = h->wk.bps ? h->wk.bps : 2, hm = h->wk.hsplit_mult ? h->wk.hsplit_mult : 1;
     h->wk.hsplit_mult = hm;
     const int rc = wk_build(h, T, bps, hm);

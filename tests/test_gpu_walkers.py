@@ -181,6 +181,13 @@ def test_persistent_rejects_unsupported_handles():
     m = gpu_handle(spec, "f32")
     with pytest.raises(wt.WtmdError):
         m.autotune()
+    m.surrogate_set(0, False)  # surrogate on (network inactive): the persistent step refuses
+    with pytest.raises(wt.WtmdError):
+        m.walkers_persistent(True)
+    m.surrogate(False)
+    m.walkers_persistent(True)
+    with pytest.raises(wt.WtmdError):
+        m.surrogate(True)
 
 
 def test_full_size_cluster_workload_sampled_against_oracle():
