@@ -63,8 +63,9 @@ void drop_step_graphs(wtmd_t* h) { drop_graphs(h); }
 // network's part when the surrogate is active.
 static int launch_bias_sum(wtmd_t* h)
 {
+    // the preceding kernel on this stream computes CVs (it writes xi only)
     int rc = launch_hills_range(h, h->xi, true, 4, h->W, h->V, h->dV, 4, surrogate_k0(h), h->count,
-                                surrogate_tail_bound(h));
+                                surrogate_tail_bound(h), true);
     if (rc) return rc;
     return launch_mlp_add(h);
 }

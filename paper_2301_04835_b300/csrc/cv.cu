@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
     __shared__ R4<R> src[CT_B];
     __shared__ int sid[CT_B];
     __shared__ R4<R> rowred[CT_T / 32][32];
+    pdl_trigger();  // the hills sum that follows may start its hill copies now
     const int w = blockIdx.y;
     const int nw = wn[w];
     const long long o = woff[w];

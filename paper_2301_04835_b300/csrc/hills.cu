@@ -198,31 +198,51 @@ static Plan plan_for(long long P, long long cap_pairs)
     return pl;
 }
 
+// pdl: launch with programmatic stream serialization, so that the kernel's
+// CTAs start (and issue their first hill copies) while the preceding kernel
+// finishes; the task waits for that kernel before it reads the points.
+template <int D, int TH, bool PER, typename PT>
+static void launch_f32_k(dim3 grid, cudaStream_t st, bool pdl, const float4* hp, const long long* k0p,
+                         const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
+                         dbl4* part, const HillOut<float>& o)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(HB);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, hills_f32_kernel<D, TH, PER, PT>, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+}
+
 template <int D, bool PER, typename PT>
-static void launch_f32_d(int th, dim3 grid, cudaStream_t st, const float4* hp, const long long* k0p,
+static void launch_f32_d(int th, dim3 grid, cudaStream_t st, bool pdl, const float4* hp, const long long* k0p,
                          const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
                          dbl4* part, const HillOut<float>& o)
 {
     switch (th) {
-    case 1: hills_f32_kernel<D, 1, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
-    case 4: hills_f32_kernel<D, 4, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
-    case 32: hills_f32_kernel<D, 32, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
-    default: hills_f32_kernel<D, 256, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 1: launch_f32_k<D, 1, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 4: launch_f32_k<D, 4, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    case 32: launch_f32_k<D, 32, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
+    default: launch_f32_k<D, 256, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
     }
 }
 
 template <typename PT>
-static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, const float4* hp,
+static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, bool pdl, const float4* hp,
                           const long long* k0p, const long long* cnt, const PT* x, int xs, int P, const double* ctr,
-                          const HillPrmF32& prm, dbl4* part, const HillOut<float>& status)
+                          const HillPrmF32& prm, dbl4* part, const HillOut<float>& o)
 {
     switch (d * 2 + (per ? 1 : 0)) {
-    case 2: launch_f32_d<1, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 3: launch_f32_d<1, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 4: launch_f32_d<2, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 5: launch_f32_d<2, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
-    case 6: launch_f32_d<3, false, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
-    default: launch_f32_d<3, true, PT>(th, grid, st, hp, k0p, cnt, x, xs, P, ctr, prm, part, status); break;
+    case 2: launch_f32_d<1, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    case 3: launch_f32_d<1, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    case 4: launch_f32_d<2, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    case 5: launch_f32_d<2, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    case 6: launch_f32_d<3, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    default: launch_f32_d<3, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
     }
 }
 
@@ -258,11 +278,11 @@ int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
 
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs)
 {
-    return launch_hills_range(h, xi, xi_f64, xs, P, V, dV, dvs, nullptr, h->count, 0);
+    return launch_hills_range(h, xi, xi_f64, xs, P, V, dV, dvs, nullptr, h->count, 0, false);
 }
 
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs,
-                       const long long* k0p, const long long* k1p, long long max_hills)
+                       const long long* k0p, const long long* k1p, long long max_hills, bool pdl)
 {
     // the plan's split covers at most max_hills hills (0: the capacity)
     const long long cap_pairs = max_hills > 0 ? std::min<long long>(h->cap_pairs, (max_hills + 1) / 2) : h->cap_pairs;
@@ -312,11 +332,11 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         HillOut<float> o{(float*)V, (float*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
                          h->status};
         if (xi_f64)
-            launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, h->hills32, k0p, k1p, (const double*)xi, xs,
-                                  Pi, h->ctr, prm, part, o);
+            launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, pdl, h->hills32, k0p, k1p, (const double*)xi,
+                                  xs, Pi, h->ctr, prm, part, o);
         else
-            launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, h->hills32, k0p, k1p, (const float*)xi, xs, Pi,
-                                 h->ctr, prm, part, o);
+            launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, pdl, h->hills32, k0p, k1p, (const float*)xi, xs,
+                                 Pi, h->ctr, prm, part, o);
         mark(h, "hills_sum_f32");
         if (!fused) {
             hills_finalize_cf_kernel<<<(Pi + 7) / 8, 256, 0, h->stream>>>(part, pl.split, Pi, o);

@@ -292,17 +292,6 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     const int hl = tid % TH;
     const int p = tile * TP + tid / TH;
 
-    // scaled, centred point: the subtraction of the centre is done in FP64 so
-    // that the FP32 coordinate keeps its relative precision near the hills
-    float xh[3] = {0.f, 0.f, 0.f};
-    if (p < P) {
-#pragma unroll
-        for (int i = 0; i < D; ++i) xh[i] = (float)(((double)xi[(size_t)p * xs + i] - ctr[i]) * prm.a[i]);
-    }
-    const float2 X0 = make_float2(xh[0], xh[0]);
-    const float2 X1 = make_float2(xh[1], xh[1]);
-    const float2 X2 = make_float2(xh[2], xh[2]);
-
     // hills [k0, count): k0 is a multiple of 2 * CHUNK, so the range starts
     // on a chunk boundary of the pair layout
     const long long k0 = k0p ? *k0p : 0;
@@ -330,6 +319,21 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
             bulk_g2s(ring[s], hp + (size_t)(c0 + s) * CHUNK * 2, CHUNK * 32, &bar[s]);
         }
     }
+    // The hill records and counts were written before the preceding kernel
+    // started; the points may come from it (its CVs).  Under a programmatic
+    // dependent launch the first copies above overlap that kernel's tail.
+    pdl_wait();
+
+    // scaled, centred point: the subtraction of the centre is done in FP64 so
+    // that the FP32 coordinate keeps its relative precision near the hills
+    float xh[3] = {0.f, 0.f, 0.f};
+    if (p < P) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) xh[i] = (float)(((double)xi[(size_t)p * xs + i] - ctr[i]) * prm.a[i]);
+    }
+    const float2 X0 = make_float2(xh[0], xh[0]);
+    const float2 X1 = make_float2(xh[1], xh[1]);
+    const float2 X2 = make_float2(xh[2], xh[2]);
 
     // chunk sums are folded into compensated FP32 accumulators (hi + lo,
     // Knuth's TwoSum): ~48-bit sums without FP64 instructions, which are slow

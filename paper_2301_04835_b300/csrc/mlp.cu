@@ -738,7 +738,7 @@ static int sur_fit(wtmd_t* h)
         (const dbl4*)h->hills64, K, M, S, h->cfg.sigma[0], h->cfg.sigma[1], h->cfg.sigma[2], h->d, s.seed, s.round++,
         s.sx);
     WTMD_CUDA_TRY(h, cudaMemsetAsync(s.sG, 0, sizeof(float) * 3 * S, h->stream));
-    if ((rc = launch_hills_range(h, s.sx, true, 3, S, s.sV, s.sG, 3, nullptr, s.kend, 0))) return rc;
+    if ((rc = launch_hills_range(h, s.sx, true, 3, S, s.sV, s.sG, 3, nullptr, s.kend, 0, false))) return rc;
     const int64_t Str = S - S / 10, Sho = S / 10;
     if (!s.have_norm) {
         // input and output scales from the first training set; kept fixed

@@ -181,6 +181,13 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor runs; pdl_wait() blocks until
+// the predecessor grid has completed and its writes are visible (a no-op in
+// a normal launch).  pdl_trigger() lets the dependent grid start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // 1/x from the PTX approximate reciprocal (max error 1 ulp; +-0 -> +-inf,
 // +-inf -> +-0)
 __device__ __forceinline__ float rcp_approx(float x)
@@ -354,9 +361,11 @@ int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult);
 int launch_walkers_step(wtmd_t* h, int mode);                   // 0: full step, 1: forces only
 int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV, int dV_stride);
 // hills [*k0p, *k1p) (k0p may be null: 0; *k0p a multiple of 256; FP32
-// handles); max_hills > 0 bounds the range's length for the launch plan
+// handles); max_hills > 0 bounds the range's length for the launch plan;
+// pdl: programmatic dependent launch on the preceding kernel (which must not
+// write the hill list, the counts or the centre; only the points)
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
-                       int dV_stride, const long long* k0p, const long long* k1p, long long max_hills);
+                       int dV_stride, const long long* k0p, const long long* k1p, long long max_hills, bool pdl);
 long long surrogate_tail_bound(const wtmd_t* h);
 int hills_tune(wtmd_t* h, int64_t P, int* th, int* split, double* ms);  // hills.cu                // hills beyond k0 between refits (0: unbounded)
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
