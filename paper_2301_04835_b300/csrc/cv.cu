@@ -726,9 +726,33 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
                                                               long long* count, long long* step, long long* dep,
                                                               double* ctr, dbl4* h64, float* h32, unsigned* status)
 {
-    if (blockIdx.x == gridDim.x - 1) deposit_block<R>(dp, xi, V, count, step, dep, ctr, h64, h32, status);
+    // Launched as a programmatic dependent of the hills sum: the atom's
+    // force, velocity and Jacobian rows (written before the hills sum
+    // started) are loaded first; dV/dxi, V and xi only after the wait.
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) scatter_atom<R>(i, d, aw, dV, J, N, force, vel, half_dt_over_m, dims);
+    const bool act = i < N;
+    int w = 0;
+    R4<R> f = mk4<R>(0, 0, 0, 0), v = f, jr[3] = {f, f, f};
+    if (act) {
+        w = aw[i];
+        f = force[i];
+        v = vel[i];
+        for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
+    }
+    pdl_wait();
+    if (blockIdx.x == gridDim.x - 1) deposit_block<R>(dp, xi, V, count, step, dep, ctr, h64, h32, status);
+    if (!act) return;
+    for (int c = 0; c < d && c < 3; ++c) {
+        const R g = dV[w * 4 + c];
+        f.x -= g * jr[c].x;
+        f.y -= g * jr[c].y;
+        f.z -= g * jr[c].z;
+    }
+    force[i] = f;
+    v.x += half_dt_over_m * f.x;
+    v.y += half_dt_over_m * f.y;
+    if (dims > 2) v.z += half_dt_over_m * f.z;
+    vel[i] = v;
 }
 
 template <typename R>
@@ -916,16 +940,28 @@ int launch_scatter_deposit(wtmd_t* h)
     const int nb = (int)((h->N + 255) / 256);
     const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
     const DepPrm dp = dep_prm(h);
+    // programmatic dependent of the hills sum (or of the network's part)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(256);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     if (h->prec == WTMD_F32)
-        scatter_deposit_kernel<float><<<nb, 256, 0, h->stream>>>(
-            h->N, h->d, h->atom_walker, (const float*)h->dV, (const float4*)h->J, (float4*)h->force,
-            (float4*)h->vel, (float)hdm, h->dims, dp, h->xi, (const float*)h->V, h->count, h->step, h->dep, h->ctr,
-            (dbl4*)h->hills64, (float*)h->hills32, h->status);
+        WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, scatter_deposit_kernel<float>, h->N, h->d,
+                                            (const int*)h->atom_walker, (const float*)h->dV, (const float4*)h->J,
+                                            (float4*)h->force, (float4*)h->vel, (float)hdm, h->dims, dp,
+                                            (const double*)h->xi, (const float*)h->V, h->count, h->step, h->dep,
+                                            h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status));
     else
-        scatter_deposit_kernel<double><<<nb, 256, 0, h->stream>>>(
-            h->N, h->d, h->atom_walker, (const double*)h->dV, (const dbl4*)h->J, (dbl4*)h->force, (dbl4*)h->vel, hdm,
-            h->dims, dp, h->xi, (const double*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
-            (float*)h->hills32, h->status);
+        WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, scatter_deposit_kernel<double>, h->N, h->d,
+                                            (const int*)h->atom_walker, (const double*)h->dV, (const dbl4*)h->J,
+                                            (dbl4*)h->force, (dbl4*)h->vel, hdm, h->dims, dp, (const double*)h->xi,
+                                            (const double*)h->V, h->count, h->step, h->dep, h->ctr,
+                                            (dbl4*)h->hills64, (float*)h->hills32, h->status));
     mark(h, "scatter_kick_deposit");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return launch_grid_update(h);

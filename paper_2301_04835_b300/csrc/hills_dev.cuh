@@ -323,6 +323,7 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     // started; the points may come from it (its CVs).  Under a programmatic
     // dependent launch the first copies above overlap that kernel's tail.
     pdl_wait();
+    pdl_trigger();  // a kernel launched after this one may start its loads
 
     // scaled, centred point: the subtraction of the centre is done in FP64 so
     // that the FP32 coordinate keeps its relative precision near the hills
