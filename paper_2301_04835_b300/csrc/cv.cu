@@ -457,20 +457,29 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
     const int b0 = chunk * CT_B;
     const int mb = min(CT_B, nBw - b0);
     // partners of the chunk; padding slots carry weight 0 (.w) so that they
-    // contribute nothing without a branch in the pair loop
-    for (int q = threadIdx.x; q < CT_B; q += CT_T) {
-        if (q < mb) {
-            const int j = B ? B[b0 + q] : b0 + q;
-            const R4<R> p = pos[o + j];
-            src[q] = mk4<R>(p.x, p.y, p.z, R(1));
-            sid[q] = j;
-        } else {
-            src[q] = mk4<R>(R(0), R(0), R(0), R(0));
-            sid[q] = -1;
-        }
-    }
+    // contribute nothing without a branch in the pair loop.  The index lists
+    // are constant: they are read before waiting for the kernel that wrote
+    // the positions (programmatic dependent launch), the positions after.
     const int ia = tile * 32 + lane;
     const int a = ia < nA ? A[ia] : -1;
+    int jq[CT_B / CT_T];
+#pragma unroll
+    for (int k = 0; k < CT_B / CT_T; ++k) {
+        const int q = threadIdx.x + k * CT_T;
+        jq[k] = q < mb ? (B ? B[b0 + q] : b0 + q) : -1;
+    }
+    pdl_wait();
+#pragma unroll
+    for (int k = 0; k < CT_B / CT_T; ++k) {
+        const int q = threadIdx.x + k * CT_T;
+        if (jq[k] >= 0) {
+            const R4<R> p = pos[o + jq[k]];
+            src[q] = mk4<R>(p.x, p.y, p.z, R(1));
+        } else {
+            src[q] = mk4<R>(R(0), R(0), R(0), R(0));
+        }
+        sid[q] = jq[k];
+    }
     R tx = 0, ty = 0, tz = 0;
     if (a >= 0) load3<R>(pos, o + a, tx, ty, tz);
     const R gpl = a >= 0 ? gpref : R(0);  // an empty target lane adds nothing to the columns
@@ -871,17 +880,23 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
             const int* B = cv.n_b < 0 ? nullptr : cv.b;
             if (cv.n_a > 0) {
                 dim3 gt(cv.ntile * cv.nbchunk, W);
-                WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
-                if (cv.nn == 6)
-                    coord_tile_kernel<R, 3><<<gt, CT_T, 0, st>>>(
-                        pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, 3, gp,
-                        (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
-                        cv.tile_tk, Jc, xi, c, cv.n_b < 0 ? nullptr : cv.inv_b);
-                else
-                    coord_tile_kernel<R, 0><<<gt, CT_T, 0, st>>>(
-                        pos, h->woff, h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, cv.nn / 2, gp,
-                        (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride, cv.scw, (double*)cv.part_row,
-                        cv.tile_tk, Jc, xi, c, cv.n_b < 0 ? nullptr : cv.inv_b);
+                if (!h->jz_pre) WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
+                // programmatic dependent of the kernel that moved the positions
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = gt;
+                cfg.blockDim = dim3(CT_T);
+                cfg.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                at[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                auto kern = cv.nn == 6 ? coord_tile_kernel<R, 3> : coord_tile_kernel<R, 0>;
+                WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, kern, pos, (const int64_t*)h->woff, (const int*)h->wn, A,
+                                                    cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, cv.nn / 2, gp,
+                                                    (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride,
+                                                    (const double*)cv.scw, (double*)cv.part_row, cv.tile_tk, Jc, xi,
+                                                    c, (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b)));
                 mark(h, "coord_tile");
                 break;
             }

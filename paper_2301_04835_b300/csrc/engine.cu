@@ -19,6 +19,7 @@ __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __
                                    const R4<R>* __restrict__ f, const long long* __restrict__ step, uint64_t seed,
                                    R half, R inv_m, R c1, R c2, int dims)
 {
+    pdl_trigger();  // the CV kernels that follow may launch; they wait for these positions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     baoab_first_atom<R>(i, *step, x, v, f, seed, half, inv_m, c1, c2, dims);

@@ -321,6 +321,7 @@ struct wtmd_t {
     bool persistent = false;        // multi-walker step as one persistent launch
     wtmd::WalkerPlan wk;
     bool no_graph = false;          // capture failed: replay eagerly
+    bool jz_pre = false;            // the step zeroed the tile-path coordination J rows before BAOAB
     wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
