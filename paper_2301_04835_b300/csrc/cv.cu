@@ -882,21 +882,12 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                 dim3 gt(cv.ntile * cv.nbchunk, W);
                 if (!h->jz_pre) WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
                 // programmatic dependent of the kernel that moved the positions
-                cudaLaunchConfig_t cfg{};
-                cfg.gridDim = gt;
-                cfg.blockDim = dim3(CT_T);
-                cfg.stream = st;
-                cudaLaunchAttribute at[1];
-                at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-                at[0].val.programmaticStreamSerializationAllowed = 1;
-                cfg.attrs = at;
-                cfg.numAttrs = 1;
                 auto kern = cv.nn == 6 ? coord_tile_kernel<R, 3> : coord_tile_kernel<R, 0>;
-                WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, kern, pos, (const int64_t*)h->woff, (const int*)h->wn, A,
-                                                    cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv, cv.nn / 2, gp,
-                                                    (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride,
-                                                    (const double*)cv.scw, (double*)cv.part_row, cv.tile_tk, Jc, xi,
-                                                    c, (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b)));
+                WTMD_CUDA_TRY(h, launch_pdl(kern, gt, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
+                                            (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
+                                            cv.nn / 2, gp, (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride,
+                                            (const double*)cv.scw, (double*)cv.part_row, cv.tile_tk, Jc, xi, c,
+                                            (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b)));
                 mark(h, "coord_tile");
                 break;
             }
@@ -956,27 +947,18 @@ int launch_scatter_deposit(wtmd_t* h)
     const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
     const DepPrm dp = dep_prm(h);
     // programmatic dependent of the hills sum (or of the network's part)
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(nb);
-    cfg.blockDim = dim3(256);
-    cfg.stream = h->stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
     if (h->prec == WTMD_F32)
-        WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, scatter_deposit_kernel<float>, h->N, h->d,
-                                            (const int*)h->atom_walker, (const float*)h->dV, (const float4*)h->J,
-                                            (float4*)h->force, (float4*)h->vel, (float)hdm, h->dims, dp,
-                                            (const double*)h->xi, (const float*)h->V, h->count, h->step, h->dep,
-                                            h->ctr, (dbl4*)h->hills64, (float*)h->hills32, h->status));
+        WTMD_CUDA_TRY(h, launch_pdl(scatter_deposit_kernel<float>, dim3(nb), dim3(256), 0, h->stream, h->N, h->d,
+                                    (const int*)h->atom_walker, (const float*)h->dV, (const float4*)h->J,
+                                    (float4*)h->force, (float4*)h->vel, (float)hdm, h->dims, dp, (const double*)h->xi,
+                                    (const float*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
+                                    (float*)h->hills32, h->status));
     else
-        WTMD_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, scatter_deposit_kernel<double>, h->N, h->d,
-                                            (const int*)h->atom_walker, (const double*)h->dV, (const dbl4*)h->J,
-                                            (dbl4*)h->force, (dbl4*)h->vel, hdm, h->dims, dp, (const double*)h->xi,
-                                            (const double*)h->V, h->count, h->step, h->dep, h->ctr,
-                                            (dbl4*)h->hills64, (float*)h->hills32, h->status));
+        WTMD_CUDA_TRY(h, launch_pdl(scatter_deposit_kernel<double>, dim3(nb), dim3(256), 0, h->stream, h->N, h->d,
+                                    (const int*)h->atom_walker, (const double*)h->dV, (const dbl4*)h->J,
+                                    (dbl4*)h->force, (dbl4*)h->vel, hdm, h->dims, dp, (const double*)h->xi,
+                                    (const double*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
+                                    (float*)h->hills32, h->status));
     mark(h, "scatter_kick_deposit");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return launch_grid_update(h);

@@ -206,16 +206,10 @@ static void launch_f32_k(dim3 grid, cudaStream_t st, bool pdl, const float4* hp,
                          const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
                          dbl4* part, const HillOut<float>& o)
 {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(HB);
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, hills_f32_kernel<D, TH, PER, PT>, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+    if (pdl)
+        launch_pdl(hills_f32_kernel<D, TH, PER, PT>, grid, dim3(HB), 0, st, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+    else
+        hills_f32_kernel<D, TH, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
 }
 
 template <int D, bool PER, typename PT>

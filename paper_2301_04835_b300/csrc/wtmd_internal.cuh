@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/wtmd.h"
@@ -388,6 +389,28 @@ void store_hills32(wtmd_t* h);                                   // rebuild FP32
 int setup_cells(wtmd_t* h);
 int cv_alloc_scratch(wtmd_t* h, CvDev& c);
 
+}  // namespace wtmd
+
+namespace wtmd {
+// Launch with programmatic stream serialization: the kernel may start while
+// the preceding kernel on the stream runs; it must call pdl_wait() before it
+// reads anything that kernel writes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 }  // namespace wtmd
 
 #define WTMD_CUDA_TRY(h, expr)                                                     \
