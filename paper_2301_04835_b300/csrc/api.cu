@@ -465,13 +465,13 @@ static int enqueue_step(wtmd_t* h)
 {
     if (h->persistent) return launch_walkers_step(h, 0);
     int rc;
-    // zero the tile-path coordination Jacobians first, so that the CV kernels
-    // directly follow BAOAB (programmatic dependent launch)
-    const size_t r4 = h->prec == WTMD_F32 ? sizeof(float4) : sizeof(dbl4);
+    // BAOAB zeroes the Jacobian rows that the coordination tile kernel
+    // accumulates, so that the CV kernels directly follow it (programmatic
+    // dependent launches: previous step -> BAOAB -> CVs)
+    int jmask = 0;
     for (int c = 0; c < h->ncv; ++c)
-        if (h->cv[c].kind == WTMD_CV_COORDINATION && h->cv[c].n_a > 0)
-            WTMD_CUDA_TRY(h, cudaMemsetAsync((char*)h->J + r4 * (size_t)c * h->N, 0, r4 * (size_t)h->N, h->stream));
-    if ((rc = launch_baoab_first(h))) return rc;
+        if (h->cv[c].kind == WTMD_CV_COORDINATION && h->cv[c].n_a > 0) jmask |= 1 << c;
+    if ((rc = launch_baoab_first(h, jmask))) return rc;
     h->jz_pre = true;
     rc = enqueue_engine_and_bias(h);
     h->jz_pre = false;

@@ -14,14 +14,21 @@
 
 namespace wtmd {
 
+// First half of the step for every atom.  Launched as a programmatic
+// dependent of the previous step's last kernel: it waits for that kernel,
+// then lets the CV kernels launch.  It also zeroes the Jacobian rows given
+// by jmask (CVs whose kernel accumulates its Jacobian).
 template <typename R>
 __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __restrict__ v,
                                    const R4<R>* __restrict__ f, const long long* __restrict__ step, uint64_t seed,
-                                   R half, R inv_m, R c1, R c2, int dims)
+                                   R half, R inv_m, R c1, R c2, int dims, R4<R>* __restrict__ J, int jmask)
 {
+    pdl_wait();
     pdl_trigger();  // the CV kernels that follow may launch; they wait for these positions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    for (int c = 0; c < 3; ++c)
+        if (jmask >> c & 1) J[(size_t)c * N + i] = mk4<R>(R(0), R(0), R(0), R(0));
     baoab_first_atom<R>(i, *step, x, v, f, seed, half, inv_m, c1, c2, dims);
 }
 
@@ -491,21 +498,21 @@ int launch_engine(wtmd_t* h)
     return h->prec == WTMD_F32 ? launch_engine_t<float>(h) : launch_engine_t<double>(h);
 }
 
-int launch_baoab_first(wtmd_t* h)
+int launch_baoab_first(wtmd_t* h, int jmask)
 {
     const int nb = (int)((h->N + 255) / 256);
     const wtmd_config& c = h->cfg;
     const double c1 = exp(-c.friction * c.dt);
     const double c2 = sqrt((1.0 - c1 * c1) * c.kT / c.mass);
     if (h->prec == WTMD_F32)
-        baoab_first_kernel<float><<<nb, 256, 0, h->stream>>>(h->N, (float4*)h->pos, (float4*)h->vel,
-                                                             (const float4*)h->force, h->step, c.seed,
-                                                             (float)(0.5 * c.dt), (float)(1.0 / c.mass), (float)c1,
-                                                             (float)c2, h->dims);
+        WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<float>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
+                                    (float4*)h->pos, (float4*)h->vel, (const float4*)h->force,
+                                    (const long long*)h->step, c.seed, (float)(0.5 * c.dt), (float)(1.0 / c.mass),
+                                    (float)c1, (float)c2, h->dims, (float4*)h->J, jmask));
     else
-        baoab_first_kernel<double><<<nb, 256, 0, h->stream>>>(h->N, (dbl4*)h->pos, (dbl4*)h->vel,
-                                                              (const dbl4*)h->force, h->step, c.seed, 0.5 * c.dt,
-                                                              1.0 / c.mass, c1, c2, h->dims);
+        WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<double>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
+                                    (dbl4*)h->pos, (dbl4*)h->vel, (const dbl4*)h->force, (const long long*)h->step,
+                                    c.seed, 0.5 * c.dt, 1.0 / c.mass, c1, c2, h->dims, (dbl4*)h->J, jmask));
     mark(h, "baoab_first");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;

@@ -381,7 +381,7 @@ void surrogate_advanced(wtmd_t* h, int64_t n);
 int surrogate_invalidate(wtmd_t* h);
 void drop_step_graphs(wtmd_t* h);                                // api.cu
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
-int launch_baoab_first(wtmd_t* h);
+int launch_baoab_first(wtmd_t* h, int jmask);                    // jmask: Jacobian rows to zero
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
 int launch_grid_rebuild(wtmd_t* h);
 int launch_fes(wtmd_t* h, double* out);
