@@ -268,12 +268,19 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                 }
                 __threadfence();
                 last = atomicAdd(&a.ticket[w], 1u) == (unsigned)a.tcount[w] - 1;
-                if (last) {
-                    __threadfence();
-                    double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-                    const double* base = a.tpart + 5 * (size_t)a.tbase[w];
-                    for (int k = 0; k < a.tcount[w]; ++k)
-                        for (int q = 0; q < 5; ++q) m[q] += __ldcg(base + 5 * k + q);
+            }
+            __syncthreads();
+            // the walker's last task sums the task moments: warp 0, lanes
+            // over tasks, then a fixed xor tree
+            if (last && tid < 32) {
+                __threadfence();
+                double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                const double* base = a.tpart + 5 * (size_t)a.tbase[w];
+                for (int k = tid; k < a.tcount[w]; k += 32)
+                    for (int q = 0; q < 5; ++q) m[q] += __ldcg(base + 5 * k + q);
+                for (int q = 0; q < 5; ++q)
+                    for (int off = 16; off > 0; off >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], off);
+                if (tid == 0) {
                     if (a.cv_coord >= 0) a.xi[w * 4 + a.cv_coord] = a.coord_scw[w] * m[0];
                     if (a.cv_rg >= 0) {
                         const double cx = m[1] / n, cy = m[2] / n, cz = m[3] / n;
