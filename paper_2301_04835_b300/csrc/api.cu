@@ -112,6 +112,9 @@ extern "C" int wtmd_destroy(wtmd_t* h)
     for (int c = 0; c < 3; ++c) {
         if (h->cv_stream[c]) cudaStreamDestroy(h->cv_stream[c]);
         if (h->ev_cv[c]) cudaEventDestroy(h->ev_cv[c]);
+        if (h->jf_stream[c]) cudaStreamDestroy(h->jf_stream[c]);
+        if (h->ev_jfork[c]) cudaEventDestroy(h->ev_jfork[c]);
+        if (h->ev_jjoin[c]) cudaEventDestroy(h->ev_jjoin[c]);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -195,6 +198,11 @@ extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
     for (int c = 1; c < 3; ++c)
         if (cudaStreamCreateWithFlags(&h->cv_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->ev_cv[c], cudaEventDisableTiming) != cudaSuccess)
+            return fail(WTMD_ECUDA, "streams");
+    for (int c = 0; c < 3; ++c)
+        if (cudaStreamCreateWithFlags(&h->jf_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_jfork[c], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->ev_jjoin[c], cudaEventDisableTiming) != cudaSuccess)
             return fail(WTMD_ECUDA, "streams");
     // walkers
     std::vector<int> aw(h->N), wn32(h->W);
@@ -465,13 +473,17 @@ static int enqueue_step(wtmd_t* h)
 {
     if (h->persistent) return launch_walkers_step(h, 0);
     int rc;
-    // BAOAB zeroes the Jacobian rows that the coordination tile kernel
-    // accumulates, so that the CV kernels directly follow it (programmatic
-    // dependent launches: previous step -> BAOAB -> CVs)
-    int jmask = 0;
-    for (int c = 0; c < h->ncv; ++c)
-        if (h->cv[c].kind == WTMD_CV_COORDINATION && h->cv[c].n_a > 0) jmask |= 1 << c;
-    if ((rc = launch_baoab_first(h, jmask))) return rc;
+    h->jf_pending = 0;
+    // BAOAB zeroes what the coordination tile kernels accumulate (the FP64
+    // kernel's Jacobian rows, the FP32 kernel's CV value), so that the CV
+    // kernels directly follow it (programmatic dependent launches: previous
+    // step -> BAOAB -> CVs)
+    int jmask = 0, xmask = 0;
+    for (int c = 0; c < h->ncv; ++c) {
+        if (coord_factored(h, c)) xmask |= 1 << c;
+        else if (h->cv[c].kind == WTMD_CV_COORDINATION && h->cv[c].n_a > 0) jmask |= 1 << c;
+    }
+    if ((rc = launch_baoab_first(h, jmask, xmask))) return rc;
     h->jz_pre = true;
     rc = enqueue_engine_and_bias(h);
     h->jz_pre = false;

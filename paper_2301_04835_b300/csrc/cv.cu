@@ -12,6 +12,7 @@
 // memory, followed by a fixed-order reduction over the splits: no atomics, so
 // results are bitwise reproducible.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "step_dev.cuh"
@@ -635,6 +636,230 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 form of the tile kernel.  A CTA takes 64 members of A, two per lane
+// (tile members lane and lane + 32), and a chunk of CT_B partners, so that
+// every arithmetic instruction of the pair loop serves two pairs through the
+// packed f32x2 operations.  Partners are staged pre-negated and duplicated
+// into both halves, (-x,-x,-y,-y) and (-z,-z,w,w), so a difference is one
+// packed add.  The minimum image rounds d/L by the 1.5 * 2^23 shift
+// (exact for |d/L| < 2^22) instead of a conversion instruction.
+//
+// The kernel ends with its partials: nothing waits on another CTA.  The CV
+// value needs no second pass: each CTA rounds its share
+// scale * (sum of s over its pairs, its self pairs removed) to a multiple of
+// 2^-q and adds it to xi with a double atomic.  q is chosen on the host so
+// that every partial sum of such shares is a double exactly; the additions
+// are then exact and the result does not depend on their order.  J stays in
+// factored form, row partials [W][chunk][A] and column partials
+// [W][tile][B], contracted per atom in a fixed order by `coord_jfin_kernel`,
+// which in a step runs beside the hills sum (that needs xi only).
+// ---------------------------------------------------------------------------
+constexpr int C2_A = 64;   // targets per CTA (two per lane)
+
+// Factored J of an FP32 tile coordination CV (see coord_j_parts).
+struct CoordParts {
+    const float4* rowpart = nullptr;  // [W][nbchunk][nA]
+    const float4* colpart = nullptr;  // [W][ntile][nB_stride]
+    const int* inv_a = nullptr;       // [max_wn]: position in A or -1
+    const int* inv_b = nullptr;       // [max_wn]: position in B or -1; null: B = all atoms
+    const double* scw = nullptr;      // [W] scale
+    int nA = 0, nbchunk = 0, ntile = 0, nB_stride = 0;
+};
+constexpr int C2_U = 8;    // rotation steps whose pair terms are computed together
+static_assert(CT_B == CT_T, "one staged partner per thread");
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// d - L rint(d / L) for two pairs along one axis (L = hi + lo in two floats);
+// iL = hi = lo = 0 on an open axis leaves d unchanged.
+__device__ __forceinline__ float2 min_image2(float2 d, float2 iL, float2 nhi, float2 nlo)
+{
+    float2 n = __ffma2_rn(d, iL, f2(12582912.f));
+    n = __fadd2_rn(n, f2(-12582912.f));
+    d = __ffma2_rn(n, nhi, d);
+    return __ffma2_rn(n, nlo, d);
+}
+
+template <int HC>
+__global__ void __launch_bounds__(CT_T) coord_tile2_kernel(const float4* __restrict__ pos,
+                                                           const int64_t* __restrict__ woff,
+                                                           const int* __restrict__ wn, const int* __restrict__ A,
+                                                           int nA, const int* __restrict__ B, int nB, int nbchunk,
+                                                           Box box, float inv_r0sq, int h, float gpref,
+                                                           float4* __restrict__ rowpart, float4* __restrict__ colpart,
+                                                           int nB_stride, const double* __restrict__ scw,
+                                                           double* __restrict__ xi, int col,
+                                                           const int* __restrict__ inv_b, double xq, double ixq)
+{
+    __shared__ float4 srcA[CT_B], srcB[CT_B];
+    __shared__ float4 rowred[CT_T / 32][C2_A];
+    __shared__ double xred[2];
+    pdl_trigger();  // the hills sum that follows may start its hill copies now
+    const int w = blockIdx.y;
+    const int nw = wn[w];
+    const long long o = woff[w];
+    const int nBw = B ? nB : nw;
+    const int tile = blockIdx.x / nbchunk, chunk = blockIdx.x % nbchunk;
+    const int ntile = gridDim.x / nbchunk;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int b0 = chunk * CT_B;
+    const int mb = min(CT_B, nBw - b0);
+    // index lists are constant: read before waiting for the positions
+    const int ia0 = tile * C2_A + lane, ia1 = ia0 + 32;
+    const int a0 = ia0 < nA ? A[ia0] : -1, a1 = ia1 < nA ? A[ia1] : -1;
+    const int q = threadIdx.x;
+    const int jq = q < mb ? (B ? B[b0 + q] : b0 + q) : -1;
+    pdl_wait();
+    if (jq >= 0) {
+        const float4 p = pos[o + jq];
+        srcA[q] = make_float4(-p.x, -p.x, -p.y, -p.y);
+        srcB[q] = make_float4(-p.z, -p.z, 1.f, 1.f);
+    } else {  // padding: weight 0
+        srcA[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        srcB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
+    if (a0 >= 0) t0 = pos[o + a0];
+    if (a1 >= 0) t1 = pos[o + a1];
+    const float2 tx = make_float2(t0.x, t1.x), ty = make_float2(t0.y, t1.y), tz = make_float2(t0.z, t1.z);
+    // an empty target lane adds nothing to the columns
+    const float2 gpl = make_float2(a0 >= 0 ? gpref : 0.f, a1 >= 0 ? gpref : 0.f);
+    float2 iL[3], nhi[3], nlo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool per = box.Lf[k] > 0.f;
+        iL[k] = f2(per ? box.invLf[k] : 0.f);
+        nhi[k] = f2(per ? -box.Lf[k] : 0.f);
+        nlo[k] = f2(per ? -box.Llo[k] : 0.f);
+    }
+    __syncthreads();
+    // rotation over the warp's 32 partners as in the generic kernel: the
+    // column sum of a partner (both targets of the lane added) moves one
+    // lane down per step and ends in the partner's own lane.  A shuffle
+    // orders the code around it, so the pair terms of C2_U steps are
+    // computed first (independent, interleaved) and then passed along.
+    float2 gx = f2(0.f), gy = gx, gz = gx, sv = gx;
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    const int base = warp * 32, from = (lane + 1) & 31;
+    const float2 inv2 = f2(inv_r0sq), one2 = f2(1.f);
+#pragma unroll 1
+    for (int k0 = 0; k0 < 32; k0 += C2_U) {
+        float hx[C2_U], hy[C2_U], hz[C2_U];
+#pragma unroll
+        for (int u = 0; u < C2_U; ++u) {
+            const int m = base + ((lane + k0 + u) & 31);
+            const float4 pa = srcA[m], pb = srcB[m];
+            const float2 dx = min_image2(__fadd2_rn(tx, make_float2(pa.x, pa.y)), iL[0], nhi[0], nlo[0]);
+            const float2 dy = min_image2(__fadd2_rn(ty, make_float2(pa.z, pa.w)), iL[1], nhi[1], nlo[1]);
+            const float2 dz = min_image2(__fadd2_rn(tz, make_float2(pb.x, pb.y)), iL[2], nhi[2], nlo[2]);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 y = __fmul2_rn(r2, inv2);
+            float2 yh1;  // y^(h-1)
+            if constexpr (HC == 1) {
+                yh1 = one2;
+            } else if constexpr (HC > 1) {
+                yh1 = y;
+#pragma unroll
+                for (int e = 2; e < HC; ++e) yh1 = __fmul2_rn(yh1, y);
+            } else {
+                yh1 = one2;
+                for (int e = 1; e < h; ++e) yh1 = __fmul2_rn(yh1, y);
+            }
+            const float2 den = __ffma2_rn(yh1, y, one2);
+            const float2 s = __fmul2_rn(make_float2(rcp_approx(den.x), rcp_approx(den.y)), make_float2(pb.z, pb.w));
+            sv = __fadd2_rn(sv, s);
+            const float2 gr = __fmul2_rn(__fmul2_rn(s, s), __fmul2_rn(yh1, gpl));
+            const float2 px = __fmul2_rn(gr, dx), py = __fmul2_rn(gr, dy), pz = __fmul2_rn(gr, dz);
+            gx = __fadd2_rn(gx, px);
+            gy = __fadd2_rn(gy, py);
+            gz = __fadd2_rn(gz, pz);
+            hx[u] = px.x + px.y;
+            hy[u] = py.x + py.y;
+            hz[u] = pz.x + pz.y;
+        }
+#pragma unroll
+        for (int u = 0; u < C2_U; ++u) {
+            cx = __shfl_sync(0xffffffffu, cx + hx[u], from);
+            cy = __shfl_sync(0xffffffffu, cy + hy[u], from);
+            cz = __shfl_sync(0xffffffffu, cz + hz[u], from);
+        }
+    }
+    if (base + lane < mb)
+        colpart[((size_t)w * ntile + tile) * nB_stride + b0 + base + lane] = make_float4(-cx, -cy, -cz, 0.f);
+    rowred[warp][lane] = make_float4(gx.x, gy.x, gz.x, sv.x);
+    rowred[warp][lane + 32] = make_float4(gx.y, gy.y, gz.y, sv.y);
+    __syncthreads();
+    // rows of the chunk (threads 0..63, warps in order) and this CTA's share
+    // of the CV value; the pair of a target with itself added s(0) in the
+    // chunk that holds it as a partner
+    if (warp < 2) {
+        const int r = threadIdx.x, ia = tile * C2_A + r;
+        double xs = 0.0;
+        if (ia < nA) {
+            float4 t = rowred[0][r];
+            for (int k = 1; k < CT_T / 32; ++k) {
+                const float4 u = rowred[k][r];
+                t.x += u.x;
+                t.y += u.y;
+                t.z += u.z;
+                t.w += u.w;
+            }
+            rowpart[((size_t)w * nbchunk + chunk) * nA + ia] = t;
+            const int a = warp == 0 ? a0 : a1;
+            const int pb = inv_b ? inv_b[a] : (a < nw ? a : -1);
+            if (pb >= b0 && pb < b0 + mb) t.w -= rcp_approx(1.f);
+            xs = (double)t.w;
+        }
+        for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+        if (lane == 0) xred[warp] = xs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&xi[w * 4 + col], rint(scw[w] * (xred[0] + xred[1]) * xq) * ixq);
+}
+
+// J of one atom of walker w (local index li) from the FP32 tile partials:
+// its column sums over the tiles, then its row sums over the chunks, each
+// in increasing order, times the walker's scale.
+__device__ __forceinline__ float4 coord_j_parts(const CoordParts& p, int w, int li)
+{
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    const int pb = p.inv_b ? p.inv_b[li] : li;
+    if (pb >= 0) {
+#pragma unroll 8
+        for (int t = 0; t < p.ntile; ++t) {
+            const float4 u = __ldcg(p.colpart + ((size_t)w * p.ntile + t) * p.nB_stride + pb);
+            sx += u.x;
+            sy += u.y;
+            sz += u.z;
+        }
+    }
+    const int ia = p.inv_a[li];
+    if (ia >= 0) {
+#pragma unroll 8
+        for (int c = 0; c < p.nbchunk; ++c) {
+            const float4 u = __ldcg(p.rowpart + ((size_t)w * p.nbchunk + c) * p.nA + ia);
+            sx += u.x;
+            sy += u.y;
+            sz += u.z;
+        }
+    }
+    const float f = (float)p.scw[w];
+    return make_float4(f * sx, f * sy, f * sz, 0.f);
+}
+
+// J rows of an FP32 tile coordination CV for every atom (0 for atoms in
+// neither group).
+__global__ void coord_jfin_kernel(long long N, const int* __restrict__ aw, const int64_t* __restrict__ woff,
+                                  CoordParts p, float4* __restrict__ J)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int w = aw[i];
+    const int li = (int)(i - woff[w]);
+    J[i] = coord_j_parts(p, w, li);
+}
+
 // J rows and the CV value from the tile partials.  Thread k sums the chunk
 // partials of its row (k in A; also its row value of s, stored per member)
 // and the tile partials of its column (k in B); the walker's last CTA sums
@@ -832,6 +1057,10 @@ int cv_alloc_scratch(wtmd_t* h, CvDev& c)
             c.nbchunk = (nB + 255) / 256;
             c.ntile = (c.n_a + 31) / 32;
             c.nB_stride = nB;
+            // bound of |xi| over the walkers (every s <= 1)
+            c.xi_bound = 0.0;
+            for (int w = 0; w < h->W; ++w)
+                c.xi_bound = std::max(c.xi_bound, std::fabs(scw[w]) * c.n_a * (c.n_b < 0 ? h->wn_h[w] : c.n_b));
             WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_row, r4 * (size_t)h->W * c.nbchunk * c.n_a));
             WTMD_CUDA_TRY(h, cudaMalloc(&c.tile_col, r4 * (size_t)h->W * c.ntile * nB));
             const size_t ntk = (size_t)h->W * (c.ntile + c.nbchunk + 1);
@@ -843,6 +1072,26 @@ int cv_alloc_scratch(wtmd_t* h, CvDev& c)
         WTMD_CUDA_TRY(h, cudaMalloc(&c.part_row, r4 * (size_t)h->W * c.n_pairs));
     }
     return WTMD_OK;
+}
+
+static CoordParts coord_parts(const wtmd_t* h, const CvDev& cv)
+{
+    CoordParts p;
+    p.rowpart = (const float4*)cv.tile_row;
+    p.colpart = (const float4*)cv.tile_col;
+    p.inv_a = cv.inv_a;
+    p.inv_b = cv.n_b < 0 ? nullptr : cv.inv_b;
+    p.scw = cv.scw;
+    p.nA = cv.n_a;
+    p.nbchunk = cv.nbchunk;
+    p.ntile = (cv.n_a + C2_A - 1) / C2_A;
+    p.nB_stride = cv.nB_stride;
+    return p;
+}
+
+bool coord_factored(const wtmd_t* h, int c)
+{
+    return h->prec == WTMD_F32 && h->cv[c].kind == WTMD_CV_COORDINATION && h->cv[c].n_a > 0;
 }
 
 template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c_begin, int c_end)
@@ -879,8 +1128,43 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
             const int* A = cv.n_a < 0 ? nullptr : cv.a;
             const int* B = cv.n_b < 0 ? nullptr : cv.b;
             if (cv.n_a > 0) {
-                dim3 gt(cv.ntile * cv.nbchunk, W);
+                if constexpr (sizeof(R) == 4) {
+                    // FP32: the CV value accumulates in xi, which starts at 0
+                    // (the step's BAOAB kernel zeroes it)
+                    if (!h->jz_pre)
+                        WTMD_CUDA_TRY(h, cudaMemset2DAsync(xi + c, 4 * sizeof(double), 0, sizeof(double), W, st));
+                    // shares are multiples of 2^-q with |xi| < 2^(53-q) for every walker
+                    const int q = 50 - std::max(0, (int)std::ceil(std::log2(std::max(cv.xi_bound, 1.0))));
+                    dim3 g2(((cv.n_a + C2_A - 1) / C2_A) * cv.nbchunk, W);
+                    auto k2 = cv.nn == 6 ? coord_tile2_kernel<3> : coord_tile2_kernel<0>;
+                    WTMD_CUDA_TRY(h, launch_pdl(k2, g2, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
+                                                (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
+                                                cv.nn / 2, gp, (float4*)cv.tile_row, (float4*)cv.tile_col,
+                                                cv.nB_stride, (const double*)cv.scw, xi, c,
+                                                (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b), std::ldexp(1.0, q),
+                                                std::ldexp(1.0, -q)));
+                    mark(h, "coord_tile");
+                    // J rows from the partials.  In a captured step this is
+                    // a graph branch of its own beside the hills sum, which
+                    // needs only xi; the closing kick joins it.
+                    cudaStream_t js = st;
+                    const bool branch = h->jz_pre && !h->prof;
+                    if (branch) {
+                        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_jfork[c], st));
+                        WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->jf_stream[c], h->ev_jfork[c], 0));
+                        js = h->jf_stream[c];
+                    }
+                    coord_jfin_kernel<<<(unsigned)((h->N + 255) / 256), 256, 0, js>>>(
+                        h->N, h->atom_walker, (const int64_t*)h->woff, coord_parts(h, cv), (float4*)Jc);
+                    mark(h, "coord_jfin");
+                    if (branch) {
+                        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_jjoin[c], js));
+                        h->jf_pending |= 1 << c;
+                    }
+                    break;
+                }
                 if (!h->jz_pre) WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
+                dim3 gt(cv.ntile * cv.nbchunk, W);
                 // programmatic dependent of the kernel that moved the positions
                 auto kern = cv.nn == 6 ? coord_tile_kernel<R, 3> : coord_tile_kernel<R, 0>;
                 WTMD_CUDA_TRY(h, launch_pdl(kern, gt, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
@@ -944,6 +1228,10 @@ int launch_cvs(wtmd_t* h, const void* pos)
 int launch_scatter_deposit(wtmd_t* h)
 {
     const int nb = (int)((h->N + 255) / 256);
+    // join the J branches of the FP32 coordination CVs
+    for (int c = 0; c < 3; ++c)
+        if (h->jf_pending >> c & 1) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_jjoin[c], 0));
+    h->jf_pending = 0;
     const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
     const DepPrm dp = dep_prm(h);
     // programmatic dependent of the hills sum (or of the network's part)

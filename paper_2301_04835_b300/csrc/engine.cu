@@ -17,15 +17,20 @@ namespace wtmd {
 // First half of the step for every atom.  Launched as a programmatic
 // dependent of the previous step's last kernel: it waits for that kernel,
 // then lets the CV kernels launch.  It also zeroes the Jacobian rows given
-// by jmask (CVs whose kernel accumulates its Jacobian).
+// by jmask and the CV values given by xmask (CVs whose kernel accumulates
+// them).
 template <typename R>
 __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __restrict__ v,
                                    const R4<R>* __restrict__ f, const long long* __restrict__ step, uint64_t seed,
-                                   R half, R inv_m, R c1, R c2, int dims, R4<R>* __restrict__ J, int jmask)
+                                   R half, R inv_m, R c1, R c2, int dims, R4<R>* __restrict__ J, int jmask,
+                                   double* __restrict__ xi, int xmask, int W)
 {
     pdl_wait();
     pdl_trigger();  // the CV kernels that follow may launch; they wait for these positions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < W)
+        for (int c = 0; c < 3; ++c)
+            if (xmask >> c & 1) xi[i * 4 + c] = 0.0;
     if (i >= N) return;
     for (int c = 0; c < 3; ++c)
         if (jmask >> c & 1) J[(size_t)c * N + i] = mk4<R>(R(0), R(0), R(0), R(0));
@@ -498,9 +503,9 @@ int launch_engine(wtmd_t* h)
     return h->prec == WTMD_F32 ? launch_engine_t<float>(h) : launch_engine_t<double>(h);
 }
 
-int launch_baoab_first(wtmd_t* h, int jmask)
+int launch_baoab_first(wtmd_t* h, int jmask, int xmask)
 {
-    const int nb = (int)((h->N + 255) / 256);
+    const int nb = (int)((std::max<long long>(h->N, h->W) + 255) / 256);
     const wtmd_config& c = h->cfg;
     const double c1 = exp(-c.friction * c.dt);
     const double c2 = sqrt((1.0 - c1 * c1) * c.kT / c.mass);
@@ -508,11 +513,12 @@ int launch_baoab_first(wtmd_t* h, int jmask)
         WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<float>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
                                     (float4*)h->pos, (float4*)h->vel, (const float4*)h->force,
                                     (const long long*)h->step, c.seed, (float)(0.5 * c.dt), (float)(1.0 / c.mass),
-                                    (float)c1, (float)c2, h->dims, (float4*)h->J, jmask));
+                                    (float)c1, (float)c2, h->dims, (float4*)h->J, jmask, h->xi, xmask, h->W));
     else
         WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<double>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
                                     (dbl4*)h->pos, (dbl4*)h->vel, (const dbl4*)h->force, (const long long*)h->step,
-                                    c.seed, 0.5 * c.dt, 1.0 / c.mass, c1, c2, h->dims, (dbl4*)h->J, jmask));
+                                    c.seed, 0.5 * c.dt, 1.0 / c.mass, c1, c2, h->dims, (dbl4*)h->J, jmask,
+                                    h->xi, xmask, h->W));
     mark(h, "baoab_first");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;

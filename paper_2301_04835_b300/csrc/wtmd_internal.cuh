@@ -216,6 +216,7 @@ struct CvDev {
     void* tile_row = nullptr;      // tile path (list A): row partials [W][chunk][|A|] R4
     void* tile_col = nullptr;      // column partials [W][tile][|B|] R4
     int nbchunk = 0, ntile = 0, nB_stride = 0;
+    double xi_bound = 0.0;         // tile path: bound of |xi| (sets the FP32 share quantum)
     unsigned* tile_tk = nullptr;   // tile path tickets [W][ntile + nbchunk + 1]
     int n_order = 0;
     // QPAIRS: CSR from atom to (pair, sign)
@@ -314,6 +315,9 @@ struct wtmd_t {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t cv_stream[3] = {nullptr, nullptr, nullptr};  // branches of CVs 1, 2
     cudaEvent_t ev_cv[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t jf_stream[3] = {nullptr, nullptr, nullptr};  // J branches of FP32 coordination CVs
+    cudaEvent_t ev_jfork[3] = {nullptr, nullptr, nullptr}, ev_jjoin[3] = {nullptr, nullptr, nullptr};
+    int jf_pending = 0;             // J branches the closing kick must join
     bool forces_valid = false;
     // graphs
     cudaGraphExec_t graph = nullptr;
@@ -381,7 +385,8 @@ void surrogate_advanced(wtmd_t* h, int64_t n);
 int surrogate_invalidate(wtmd_t* h);
 void drop_step_graphs(wtmd_t* h);                                // api.cu
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
-int launch_baoab_first(wtmd_t* h, int jmask);                    // jmask: Jacobian rows to zero
+int launch_baoab_first(wtmd_t* h, int jmask, int xmask);         // Jacobian rows / CV values to zero
+bool coord_factored(const wtmd_t* h, int c);  // CV c keeps J as FP32 tile partials (contracted by the kick)
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
 int launch_grid_rebuild(wtmd_t* h);
 int launch_fes(wtmd_t* h, double* out);
