@@ -403,7 +403,7 @@ def traffic_for(kernel: str, sha: str):
     return None
 
 
-KERNEL_SRC = {"lj_cell_force": "engine.cu", "lj_cell_bin": "engine.cu", "lj_cell_sort": "engine.cu",
+KERNEL_SRC = {"lj_list": "engine.cu", "nl_bin": "engine.cu", "nl_build": "engine.cu", "coord_jfin": "cv.cu",
               "baoab_first": "engine.cu", "coord_tile": "cv.cu", "cv_rg": "cv.cu", "scatter_kick_deposit": "cv.cu",
               "scatter_kick": "cv.cu", "hills_sum_f32": "hills.cu", "hills_finalize": "hills.cu",
               "deposit": "deposit.cu"}
@@ -427,12 +427,13 @@ def kernel_work(kernel: str, n_hills: int):
     r4 = 16
     alu = {
         "coord_tile": N_TAG * (N_ATOMS - 1) * FLOP_COORD_PAIR,
-        "lj_cell_force": LJ_PAIRS * FLOP_LJ_PAIR,
+        "lj_list": LJ_PAIRS * FLOP_LJ_PAIR,
     }
     hbm = {
         "baoab_first": N_ATOMS * r4 * 5,                    # read x, v, f; write x, v
-        "lj_cell_bin": N_ATOMS * (r4 + 4),                  # read x, write cell slots
-        "lj_cell_sort": N_ATOMS * 4 * 2,                    # cell slots in and out
+        # J rows of the coordination CV from its partials: 8 column partials
+        # per atom, 16 row partials per tagged atom, one J row out
+        "coord_jfin": (8 * N_ATOMS + 16 * N_TAG + N_ATOMS) * r4,
         "cv_rg": N_RG * r4 * 2,                             # positions in, J out
         "hills_sum_f32": ((n_hills + 1) // 2) * 32,         # hill-pair records read once
         "scatter_kick_deposit": N_ATOMS * r4 * 6,           # f, 2 J rows, v in; f, v out (+ one hill)

@@ -97,7 +97,7 @@ extern "C" int wtmd_destroy(wtmd_t* h)
     for (int i = 0; i < h->ncv; ++i) free_cv(h->cv[i]);
     void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status, h->ticket,
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
-                    h->cell_atoms};
+                    h->cell_atoms, h->nl_nbr, h->nl_cnt, h->nl_xref, h->nl_ctl};
     for (void* p : ptrs) cudaFree(p);
     surrogate_free(h->sur);
     {
@@ -426,7 +426,7 @@ static int enqueue_forces(wtmd_t* h)
 {
     if (h->persistent) return launch_walkers_step(h, 1);
     int rc;
-    if ((rc = launch_engine(h))) return rc;
+    if ((rc = nl_request(h)) || (rc = launch_engine(h)) || (rc = nl_reset(h))) return rc;
     if ((rc = launch_cvs(h, h->pos))) return rc;
     if ((rc = launch_bias_sum(h))) return rc;
     return launch_scatter(h, h->force, nullptr, false);

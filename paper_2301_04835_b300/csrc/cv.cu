@@ -958,12 +958,18 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
                                                               R half_dt_over_m, int dims, DepPrm dp,
                                                               const double* __restrict__ xi, const R* __restrict__ V,
                                                               long long* count, long long* step, long long* dep,
-                                                              double* ctr, dbl4* h64, float* h32, unsigned* status)
+                                                              double* ctr, dbl4* h64, float* h32, unsigned* status,
+                                                              int* __restrict__ ccount, int ncells,
+                                                              unsigned* __restrict__ nl_ctl)
 {
     // Launched as a programmatic dependent of the hills sum: the atom's
     // force, velocity and Jacobian rows (written before the hills sum
     // started) are loaded first; dV/dxi, V and xi only after the wait.
+    // It also resets the engine's cell counts and neighbour-list rebuild
+    // flag (the engine branch has joined).
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long c = i; c < ncells; c += (long long)gridDim.x * blockDim.x) ccount[c] = 0;
+    if (nl_ctl && i == 0) *nl_ctl = 0u;
     const bool act = i < N;
     int w = 0;
     R4<R> f = mk4<R>(0, 0, 0, 0), v = f, jr[3] = {f, f, f};
@@ -1240,13 +1246,13 @@ int launch_scatter_deposit(wtmd_t* h)
                                     (const int*)h->atom_walker, (const float*)h->dV, (const float4*)h->J,
                                     (float4*)h->force, (float4*)h->vel, (float)hdm, h->dims, dp, (const double*)h->xi,
                                     (const float*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
-                                    (float*)h->hills32, h->status));
+                                    (float*)h->hills32, h->status, h->cell_count, h->ncells, h->nl_ctl));
     else
         WTMD_CUDA_TRY(h, launch_pdl(scatter_deposit_kernel<double>, dim3(nb), dim3(256), 0, h->stream, h->N, h->d,
                                     (const int*)h->atom_walker, (const double*)h->dV, (const dbl4*)h->J,
                                     (dbl4*)h->force, (dbl4*)h->vel, hdm, h->dims, dp, (const double*)h->xi,
                                     (const double*)h->V, h->count, h->step, h->dep, h->ctr, (dbl4*)h->hills64,
-                                    (float*)h->hills32, h->status));
+                                    (float*)h->hills32, h->status, h->cell_count, h->ncells, h->nl_ctl));
     mark(h, "scatter_kick_deposit");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return launch_grid_update(h);

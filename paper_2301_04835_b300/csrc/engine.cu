@@ -23,7 +23,8 @@ template <typename R>
 __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __restrict__ v,
                                    const R4<R>* __restrict__ f, const long long* __restrict__ step, uint64_t seed,
                                    R half, R inv_m, R c1, R c2, int dims, R4<R>* __restrict__ J, int jmask,
-                                   double* __restrict__ xi, int xmask, int W)
+                                   double* __restrict__ xi, int xmask, int W, const R4<R>* __restrict__ xref,
+                                   R half_skin2, unsigned* nl_flag)
 {
     pdl_wait();
     pdl_trigger();  // the CV kernels that follow may launch; they wait for these positions
@@ -35,6 +36,11 @@ __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __
     for (int c = 0; c < 3; ++c)
         if (jmask >> c & 1) J[(size_t)c * N + i] = mk4<R>(R(0), R(0), R(0), R(0));
     baoab_first_atom<R>(i, *step, x, v, f, seed, half, inv_m, c1, c2, dims);
+    if (nl_flag) {  // moved more than half the skin since the neighbour lists were built
+        const R4<R> p = x[i], q = xref[i];
+        const R dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        if (dx * dx + dy * dy + dz * dz > half_skin2) atomicOr(nl_flag, 1u);
+    }
 }
 
 // Mueller-Brown (Mueller & Brown 1979): sum of four anisotropic Gaussians.
@@ -144,102 +150,93 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
     if (t < n) f[o + t] = mk4<R>(fx, fy, fz, R(0));
 }
 
-template <typename R> __device__ __forceinline__ R inv_box(const Box& b, int k);
-template <> __device__ __forceinline__ float inv_box<float>(const Box& b, int k) { return b.invLf[k]; }
-template <> __device__ __forceinline__ double inv_box<double>(const Box& b, int k) { return b.invL[k]; }
+// Verlet neighbour lists on a cell list (single periodic walker).
+//
+// A list holds every partner within rl = rc + skin at its build; while no
+// atom is further than skin / 2 from where it was then, every pair within
+// rc is in it, so a step normally evaluates forces from the list alone.
+// BAOAB compares each atom's new position with its build position and
+// raises the rebuild flag past skin / 2 (whoever moved the atom); a force
+// evaluation that no BAOAB precedes requests a rebuild.
+//
+// Each atom's partners are stored as NL_S sub-lists by j mod NL_S, each in
+// increasing j.  Lane s of the atom's NL_S lanes sums the pairs of sub-list
+// s within rc in that order and a fixed xor tree adds the lanes, so the force
+// depends only on the pairs within rc, never on when the list was built.
+// Entry k of sub-list u = NL_S i + s is nbr[k * NL_S N + u], so that the
+// lanes of a warp read consecutive words.
+//
+// Three launches per evaluation: binning and the list build return at once
+// unless the rebuild flag is set; the force kernel always runs, and zeroes
+// the cell counts and the flag for the next rebuild.
+constexpr int NL_S = 8;     // sub-lists (lanes) per atom
+constexpr int NL_T = 256;   // threads per CTA of the build and force kernels
+constexpr int NL_B = 12;    // list entries a force lane loads together
 
-// x - m L for an integer m, with L as hi + lo floats in FP32.
-template <typename R> __device__ __forceinline__ R shift_box(R x, R m, const Box& b, int k);
-template <> __device__ __forceinline__ float shift_box<float>(float x, float m, const Box& b, int k)
+template <typename R> __device__ __forceinline__ int cell_coord(R q, R invL, int nc)
 {
-    return fmaf(-m, b.Llo[k], fmaf(-m, b.Lf[k], x));
-}
-template <> __device__ __forceinline__ double shift_box<double>(double x, double m, const Box& b, int k)
-{
-    return x - m * b.L[k];
+    R u = q * invL;
+    u -= floor(u);  // fractional coordinate in [0, 1]
+    const int c = (int)(u * (R)nc);
+    return c >= nc ? nc - 1 : (c < 0 ? 0 : c);
 }
 
-// Position of x in the periodic image of the home cell's frame: wrapped by
-// floor(x / L) (the formula the binning uses), then moved by `img` boxes.
-template <typename R> __device__ __forceinline__ R image_coord(R x, int img, const Box& b, int k)
+template <typename R> __device__ __forceinline__ R box_inv(const Box& b, int k)
 {
-    const R m = floor(x * inv_box<R>(b, k)) - (R)img;
-    return shift_box<R>(x, m, b, k);
+    return sizeof(R) == 4 ? (R)b.invLf[k] : (R)b.invL[k];
 }
 
-// Cell list (single periodic walker).  Binning with atomics, then each
-// cell's list is sorted by atom index so the force sum order is fixed.
+// Binning (atomics: the slot order within a cell is arbitrary and harmless,
+// since the sub-lists are sorted).  Cell counts are zero on entry.
 template <typename R>
-__global__ void cell_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx, int ncy, int ncz,
-                                int cap, int* __restrict__ cnt, int* __restrict__ atoms, unsigned* status)
+__global__ void nl_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx, int ncy, int ncz, int ccap,
+                              int* __restrict__ ccount, int* __restrict__ catoms, const unsigned* __restrict__ ctl,
+                              unsigned* status)
 {
+    pdl_trigger();  // the list build may launch; it waits for the binning only on a rebuild
+    if (*ctl == 0u) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const R4<R> p = x[i];
-    const R q[3] = {p.x, p.y, p.z};
-    const int nc[3] = {ncx, ncy, ncz};
-    int ci[3];
-    for (int k = 0; k < 3; ++k) {
-        R u = q[k] * inv_box<R>(box, k);
-        u -= floor(u);  // fractional coordinate in [0, 1]
-        int c = (int)(u * nc[k]);
-        ci[k] = c >= nc[k] ? nc[k] - 1 : (c < 0 ? 0 : c);
-    }
-    const int cell = (ci[0] * ncy + ci[1]) * ncz + ci[2];
-    const int slot = atomicAdd(&cnt[cell], 1);
-    if (slot < cap) atoms[(size_t)cell * cap + slot] = (int)i;
+    const int cell = (cell_coord<R>(p.x, box_inv<R>(box, 0), ncx) * ncy + cell_coord<R>(p.y, box_inv<R>(box, 1), ncy)) *
+                         ncz + cell_coord<R>(p.z, box_inv<R>(box, 2), ncz);
+    const int slot = atomicAdd(&ccount[cell], 1);
+    if (slot < ccap) catoms[(size_t)cell * ccap + slot] = (int)i;
     else atomicOr(status, ST_CELL);
 }
 
-// Each cell's atom list is put in increasing atom order once per step (one
-// warp per cell: every entry's rank is the number of smaller entries; atom
-// indices are distinct), so the binning atomics' order never reaches the
-// force sums: the engine force is bitwise reproducible.
-__global__ void __launch_bounds__(256) cell_sort_kernel(int ncells, int cap, const int* __restrict__ cnt,
-                                                        int* __restrict__ atoms)
-{
-    extern __shared__ int cs_smem[];
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int c = blockIdx.x * 8 + warp;
-    int* in = cs_smem + warp * 2 * cap;
-    int* out = in + cap;
-    const int n = c < ncells ? min(cnt[c], cap) : 0;
-    int* a = atoms + (size_t)(c < ncells ? c : 0) * cap;
-    for (int k = lane; k < n; k += 32) in[k] = a[k];
-    __syncwarp();
-    for (int k = lane; k < n; k += 32) {
-        const int v = in[k];
-        int r = 0;
-        for (int q = 0; q < n; ++q) r += in[q] < v;
-        out[r] = v;
-    }
-    __syncwarp();
-    for (int k = lane; k < n; k += 32) a[k] = out[k];
-}
-
-// Cell-tiled LJ forces.  One CTA per home cell gathers the (sorted) atom
-// lists of the 27 neighbour cells and their positions into shared memory;
-// one warp per target atom of the home cell; lane l takes candidates l,
-// l+32, ... in (cell, atom) order; a fixed xor-shuffle tree reduces the lanes.
-constexpr int LJ_T = 512;  // 16 warps: about one target atom per warp
-
+// List build, one CTA per home cell: the 27 neighbour cells' atoms are
+// staged in shared memory, every (home atom, candidate) pair is tested,
+// partners within rl go to the home atom's sub-list by j mod NL_S, and each
+// sub-list is sorted.  Sub-lists in shared memory have an odd stride.
 template <typename R>
-__global__ void __launch_bounds__(LJ_T) lj_tiled_kernel(const R4<R>* __restrict__ x, Box box, int ncx, int ncy,
-                                                        int ncz, int cap, const int* __restrict__ cnt,
-                                                        const int* __restrict__ atoms, R rc2, R sig2, R eps24,
-                                                        R4<R>* __restrict__ f)
+__global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx,
+                                                        int ncy, int ncz, int ccap, const int* __restrict__ ccount,
+                                                        const int* __restrict__ catoms, int* __restrict__ nbr,
+                                                        int* __restrict__ ncnt, R4<R>* __restrict__ xref,
+                                                        const unsigned* __restrict__ ctl, int cap8, R rl2,
+                                                        unsigned* status)
 {
-    extern __shared__ __align__(32) unsigned char lj_smem[];
-    __shared__ int off[28];
-    __shared__ int nbc[27];
+    pdl_trigger();
+    if (*ctl == 0u) return;
+    pdl_wait();  // the binning
+    extern __shared__ __align__(32) unsigned char nl_smem[];
+    const int ls = cap8 + 1;
+    R4<R>* cpos = reinterpret_cast<R4<R>*>(nl_smem);
+    R4<R>* hpos = cpos + 27 * ccap;
+    int* cidx = reinterpret_cast<int*>(hpos + ccap);
+    int* hidx = cidx + 27 * ccap;
+    int* hcnt = hidx + ccap;
+    int* hlist = hcnt + ccap * NL_S;
+    __shared__ int off[28], nbc[27];
     const int c = blockIdx.x;
-    const int cz = c % ncz, cy = (c / ncz) % ncy, cx = c / (ncy * ncz);
+    const int hz = c % ncz, hy = (c / ncz) % ncy, hx = c / (ncy * ncz);
     if (threadIdx.x < 27) {
         const int q = threadIdx.x;
-        const int dx = q / 9 - 1, dy = (q / 3) % 3 - 1, dz = q % 3 - 1;
-        const int nb = (((cx + dx + ncx) % ncx) * ncy + (cy + dy + ncy) % ncy) * ncz + (cz + dz + ncz) % ncz;
+        const int nb = (((hx + q / 9 - 1 + ncx) % ncx) * ncy + (hy + (q / 3) % 3 - 1 + ncy) % ncy) * ncz +
+                       (hz + q % 3 - 1 + ncz) % ncz;
         nbc[q] = nb;
-        off[q + 1] = min(cnt[nb], cap);
+        off[q + 1] = min(ccount[nb], ccap);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -247,63 +244,107 @@ __global__ void __launch_bounds__(LJ_T) lj_tiled_kernel(const R4<R>* __restrict_
         for (int q = 0; q < 27; ++q) off[q + 1] += off[q];
     }
     __syncthreads();
-    const int ncand = off[27];
-    int* idx = reinterpret_cast<int*>(lj_smem);
-    R4<R>* cp = reinterpret_cast<R4<R>*>(lj_smem + (((size_t)27 * cap * sizeof(int) + 31) / 32) * 32);
-    // flat gather: candidate e lives in neighbour cell q with off[q] <= e <
-    // off[q+1]; it is stored at its periodic image next to the home cell, so
-    // the pair loop needs no minimum image
-    const int hc[3] = {cx, cy, cz}, ncv[3] = {ncx, ncy, ncz};
-    for (int e = threadIdx.x; e < ncand; e += LJ_T) {
+    const int ncand = off[27], nh = min(ccount[c], ccap);
+    for (int e = threadIdx.x; e < ncand; e += NL_T) {
         int q = 0;
         while (off[q + 1] <= e) ++q;
-        const int j = atoms[(size_t)nbc[q] * cap + (e - off[q])];
-        idx[e] = j;
-        const int dq[3] = {q / 9 - 1, (q / 3) % 3 - 1, q % 3 - 1};
-        int img[3];
-        for (int k = 0; k < 3; ++k) {
-            const int n = hc[k] + dq[k];
-            img[k] = n < 0 ? -1 : (n >= ncv[k] ? 1 : 0);
-        }
-        const R4<R> sx = x[j];
-        cp[e] = mk4<R>(image_coord<R>(sx.x, img[0], box, 0), image_coord<R>(sx.y, img[1], box, 1),
-                       image_coord<R>(sx.z, img[2], box, 2), R(0));
+        const int j = catoms[(size_t)nbc[q] * ccap + (e - off[q])];
+        cidx[e] = j;
+        cpos[e] = x[j];
     }
+    for (int t = threadIdx.x; t < nh; t += NL_T) {
+        const int i = catoms[(size_t)c * ccap + t];
+        hidx[t] = i;
+        hpos[t] = x[i];
+    }
+    for (int k = threadIdx.x; k < nh * NL_S; k += NL_T) hcnt[k] = 0;
     __syncthreads();
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    const int nhome = min(cnt[c], cap);
-    for (int t = warp; t < nhome; t += LJ_T / 32) {
-        const int i = atoms[(size_t)c * cap + t];
-        const R4<R> px = x[i];
-        const R p[3] = {image_coord<R>(px.x, 0, box, 0), image_coord<R>(px.y, 0, box, 1),
-                        image_coord<R>(px.z, 0, box, 2)};
-        R fx = 0, fy = 0, fz = 0;
-#pragma unroll 4
-        for (int e = lane; e < ncand; e += 32) {
-            const R4<R> s = cp[e];
-            const R ddx = p[0] - s.x;
-            const R ddy = p[1] - s.y;
-            const R ddz = p[2] - s.z;
-            const R r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < rc2 && idx[e] != i) {
-                const R fr = lj_fr<R>(r2, sig2, eps24);
-                fx += fr * ddx;
-                fy += fr * ddy;
-                fz += fr * ddz;
+    for (int t = 0; t < nh; ++t) {
+        const int i = hidx[t];
+        const R4<R> p = hpos[t];
+        for (int e = threadIdx.x; e < ncand; e += NL_T) {
+            const int j = cidx[e];
+            const R4<R> o = cpos[e];
+            const R dx = min_image<R>(p.x - o.x, box, 0), dy = min_image<R>(p.y - o.y, box, 1),
+                    dz = min_image<R>(p.z - o.z, box, 2);
+            if (j != i && dx * dx + dy * dy + dz * dz < rl2) {
+                const int k = t * NL_S + j % NL_S;
+                const int slot = atomicAdd(&hcnt[k], 1);
+                if (slot < cap8) hlist[k * ls + slot] = j;
+                else atomicOr(status, ST_CELL);
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            fx += __shfl_xor_sync(0xffffffffu, fx, o);
-            fy += __shfl_xor_sync(0xffffffffu, fy, o);
-            fz += __shfl_xor_sync(0xffffffffu, fz, o);
-        }
-        if (lane == 0) f[i] = mk4<R>(fx, fy, fz, R(0));
     }
+    __syncthreads();
+    const long long NS = N * NL_S;
+    for (int k = threadIdx.x; k < nh * NL_S; k += NL_T) {
+        const int n = min(hcnt[k], cap8);
+        int* l = hlist + k * ls;
+        for (int a = 1; a < n; ++a) {  // insertion sort: increasing j
+            const int v = l[a];
+            int b = a;
+            while (b > 0 && l[b - 1] > v) {
+                l[b] = l[b - 1];
+                --b;
+            }
+            l[b] = v;
+        }
+        const long long u = (long long)hidx[k / NL_S] * NL_S + k % NL_S;
+        for (int a = 0; a < n; ++a) nbr[a * NS + u] = l[a];
+        ncnt[u] = n;
+    }
+    for (int t = threadIdx.x; t < nh; t += NL_T) xref[hidx[t]] = hpos[t];
 }
 
-template <typename R> static size_t lj_tiled_smem(int cap)
+// Forces from the lists: NL_S lanes per atom, a fixed xor tree over them.
+// The cell counts and the rebuild flag are reset after the step's join
+// (the closing kick), or by nl_reset.
+template <typename R>
+__global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>* __restrict__ x, Box box,
+                                                       const int* __restrict__ nbr, const int* __restrict__ ncnt,
+                                                       const unsigned* __restrict__ ctl, R rc2, R sig2, R eps24,
+                                                       R4<R>* __restrict__ f)
 {
-    return ((size_t)27 * cap * sizeof(int) + 31) / 32 * 32 + (size_t)27 * cap * sizeof(R4<R>);
+    const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
+    // the flag was set (or not) before the chain started and is cleared
+    // after it; without a rebuild the lists are those of an earlier step and
+    // nothing is waited for
+    if (*ctl != 0u) pdl_wait();  // the list build
+    const long long NS = N * NL_S;
+    const long long i = u / NL_S;
+    R fx = 0, fy = 0, fz = 0;
+    if (u < NS) {
+        const R4<R> p = x[i];
+        const int n = ncnt[u];
+        // NL_B entries at a time: all their indices, then all their
+        // positions are in flight together; the sum runs in list order
+        for (int k0 = 0; k0 < n; k0 += NL_B) {
+            int jj[NL_B];
+#pragma unroll
+            for (int q = 0; q < NL_B; ++q) jj[q] = k0 + q < n ? nbr[(k0 + q) * NS + u] : -1;
+            R4<R> o[NL_B];
+#pragma unroll
+            for (int q = 0; q < NL_B; ++q) o[q] = jj[q] >= 0 ? x[jj[q]] : p;
+#pragma unroll
+            for (int q = 0; q < NL_B; ++q) {
+                const R dx = min_image<R>(p.x - o[q].x, box, 0), dy = min_image<R>(p.y - o[q].y, box, 1),
+                        dz = min_image<R>(p.z - o[q].z, box, 2);
+                const R r2 = dx * dx + dy * dy + dz * dz;
+                if (jj[q] >= 0 && r2 < rc2) {
+                    const R fr = lj_fr<R>(r2, sig2, eps24);
+                    fx += fr * dx;
+                    fy += fr * dy;
+                    fz += fr * dz;
+                }
+            }
+        }
+    }
+    for (int o = NL_S / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (u < NS && u % NL_S == 0) f[i] = mk4<R>(fx, fy, fz, R(0));
 }
 
 // Bead chain: bonds kb/2 (r - r0)^2, angles ka/2 (theta - th0)^2, torsions
@@ -410,36 +451,77 @@ __global__ void philox_test_kernel(const uint32_t* __restrict__ in, uint32_t* __
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+template <typename R> static size_t nl_smem_bytes(int ccap, int cap8)
+{
+    return sizeof(R4<R>) * 28 * (size_t)ccap + sizeof(int) * ((size_t)28 * ccap + (size_t)ccap * NL_S * (2 + cap8));
+}
+
 int setup_cells(wtmd_t* h)
 {
     h->ncells = 0;
     if (h->cfg.engine != WTMD_ENGINE_LJ || h->W != 1) return WTMD_OK;
+    // skin 0.3 sigma; cells at least rc + skin wide hold every list partner
+    // in the 27 around an atom's own
+    h->nl_skin = 0.3 * h->cfg.lj_sigma;
+    const double rl = h->cfg.lj_rc + h->nl_skin;
     int nc[3];
     for (int k = 0; k < 3; ++k) {
         if (!(h->cfg.box[k] > 0)) return WTMD_OK;  // open boundaries: all pairs
-        nc[k] = (int)floor(h->cfg.box[k] / h->cfg.lj_rc);
+        nc[k] = (int)floor(h->cfg.box[k] / rl);
         if (nc[k] < 3) return WTMD_OK;             // too small for a 27-cell stencil
     }
     h->nc[0] = nc[0];
     h->nc[1] = nc[1];
     h->nc[2] = nc[2];
     h->ncells = nc[0] * nc[1] * nc[2];
-    // capacity: twice the mean occupancy plus 16 (a liquid cell exceeding it
-    // is a many-sigma event; overflow is reported as WTMD_ECELL)
+    // capacities: twice the mean occupancy plus a margin (a liquid exceeding
+    // them is a many-sigma event; overflow is reported as WTMD_ECELL)
+    const double vol = h->cfg.box[0] * h->cfg.box[1] * h->cfg.box[2];
     const double mean = (double)h->N / h->ncells;
-    int cap = (int)ceil(2.0 * mean + 16.0);
-    h->cell_cap = (cap + 7) / 8 * 8;
-    const size_t sm = h->prec == WTMD_F32 ? lj_tiled_smem<float>(h->cell_cap) : lj_tiled_smem<double>(h->cell_cap);
-    if (sm > 200 * 1024) {
-        h->ncells = 0;  // too dense for the tiled kernel: all pairs
+    h->cell_cap = ((int)ceil(2.0 * mean + 16.0) + 7) / 8 * 8;
+    const double nmean = (double)h->N / vol * 4.0 / 3.0 * 3.14159265358979323846 * rl * rl * rl / NL_S;
+    h->nl_cap8 = ((int)ceil(2.0 * nmean + 12.0) + 3) / 4 * 4;
+    const size_t r4 = h->prec == WTMD_F32 ? sizeof(float4) : sizeof(dbl4);
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_count, sizeof(int) * h->ncells));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_nbr, sizeof(int) * (size_t)h->N * NL_S * h->nl_cap8));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_cnt, sizeof(int) * (size_t)h->N * NL_S));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_xref, r4 * (size_t)h->N));
+    WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_ctl, sizeof(unsigned)));
+    const unsigned one = 1u;  // build before the first use
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->nl_ctl, &one, sizeof(one), cudaMemcpyHostToDevice));
+    // the build kernel's shared memory
+    const size_t sm = h->prec == WTMD_F32 ? nl_smem_bytes<float>(h->cell_cap, h->nl_cap8)
+                                          : nl_smem_bytes<double>(h->cell_cap, h->nl_cap8);
+    h->nl_smem = sm;
+    if (sm > 200 * 1024) {  // too dense for the staged build: all pairs
+        h->ncells = 0;
         return WTMD_OK;
     }
     if (h->prec == WTMD_F32)
-        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(lj_tiled_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(nl_build_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     else
-        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(lj_tiled_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_count, sizeof(int) * h->ncells));
-    WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
+        WTMD_CUDA_TRY(h, cudaFuncSetAttribute(nl_build_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    WTMD_CUDA_TRY(h, cudaMemset(h->cell_count, 0, sizeof(int) * h->ncells));
+    return WTMD_OK;
+}
+
+// The next engine evaluation rebuilds the neighbour lists (the caller may
+// have moved the atoms since the last step).
+int nl_request(wtmd_t* h)
+{
+    if (h->ncells > 0) WTMD_CUDA_TRY(h, cudaMemsetAsync(h->nl_ctl, 0xff, sizeof(unsigned), h->stream));
+    return WTMD_OK;
+}
+
+// Zero cell counts and rebuild flag after an engine evaluation outside a
+// step (a step's closing kick does it there).
+int nl_reset(wtmd_t* h)
+{
+    if (h->ncells > 0) {
+        WTMD_CUDA_TRY(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * h->ncells, h->stream));
+        WTMD_CUDA_TRY(h, cudaMemsetAsync(h->nl_ctl, 0, sizeof(unsigned), h->stream));
+    }
     return WTMD_OK;
 }
 
@@ -466,16 +548,23 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
     case WTMD_ENGINE_LJ: {
         const R rc2 = (R)(c.lj_rc * c.lj_rc), sig2 = (R)(c.lj_sigma * c.lj_sigma), e24 = (R)(24.0 * c.lj_eps);
         if (h->ncells > 0) {
-            WTMD_CUDA_TRY(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * h->ncells, st));
-            cell_bin_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
-                                                   h->cell_count, h->cell_atoms, h->status);
-            mark(h, "lj_cell_bin");
-            cell_sort_kernel<<<(h->ncells + 7) / 8, 256, 8 * 2 * h->cell_cap * sizeof(int), st>>>(
-                h->ncells, h->cell_cap, h->cell_count, h->cell_atoms);
-            mark(h, "lj_cell_sort");
-            lj_tiled_kernel<R><<<h->ncells, LJ_T, lj_tiled_smem<R>(h->cell_cap), st>>>(
-                x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap, h->cell_count, h->cell_atoms, rc2, sig2, e24, f);
-            mark(h, "lj_cell_force");
+            const double rl = c.lj_rc + h->nl_skin;
+            // bin -> build -> forces as programmatic dependents: the first
+            // two return at once unless a rebuild is flagged
+            nl_bin_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
+                                                 h->cell_count, h->cell_atoms, h->nl_ctl, h->status);
+            mark(h, "nl_bin");
+            WTMD_CUDA_TRY(h, launch_pdl(nl_build_kernel<R>, dim3(h->ncells), dim3(NL_T), h->nl_smem, st, (long long)h->N,
+                                        x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
+                                        (const int*)h->cell_count, (const int*)h->cell_atoms, h->nl_nbr, h->nl_cnt,
+                                        (R4<R>*)h->nl_xref, (const unsigned*)h->nl_ctl, h->nl_cap8, (R)(rl * rl),
+                                        h->status));
+            mark(h, "nl_build");
+            const unsigned nbl = (unsigned)((h->N * NL_S + NL_T - 1) / NL_T);
+            WTMD_CUDA_TRY(h, launch_pdl(lj_list_kernel<R>, dim3(nbl), dim3(NL_T), 0, st, (long long)h->N, x, h->box,
+                                        (const int*)h->nl_nbr, (const int*)h->nl_cnt, (const unsigned*)h->nl_ctl,
+                                        rc2, sig2, e24, f));
+            mark(h, "lj_list");
         } else {
             dim3 g((h->max_wn + 127) / 128, h->W);
             lj_allpairs_kernel<R><<<g, 128, 0, st>>>(x, h->woff, h->wn, h->box, rc2, sig2, e24, f);
@@ -509,16 +598,20 @@ int launch_baoab_first(wtmd_t* h, int jmask, int xmask)
     const wtmd_config& c = h->cfg;
     const double c1 = exp(-c.friction * c.dt);
     const double c2 = sqrt((1.0 - c1 * c1) * c.kT / c.mass);
+    // rebuild threshold slightly under (skin / 2)^2 against rounding
+    const double hs2 = 0.249 * h->nl_skin * h->nl_skin;
+    unsigned* nlf = h->ncells > 0 ? h->nl_ctl : nullptr;
     if (h->prec == WTMD_F32)
         WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<float>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
                                     (float4*)h->pos, (float4*)h->vel, (const float4*)h->force,
                                     (const long long*)h->step, c.seed, (float)(0.5 * c.dt), (float)(1.0 / c.mass),
-                                    (float)c1, (float)c2, h->dims, (float4*)h->J, jmask, h->xi, xmask, h->W));
+                                    (float)c1, (float)c2, h->dims, (float4*)h->J, jmask, h->xi, xmask, h->W,
+                                    (const float4*)h->nl_xref, (float)hs2, nlf));
     else
         WTMD_CUDA_TRY(h, launch_pdl(baoab_first_kernel<double>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N,
                                     (dbl4*)h->pos, (dbl4*)h->vel, (const dbl4*)h->force, (const long long*)h->step,
                                     c.seed, 0.5 * c.dt, 1.0 / c.mass, c1, c2, h->dims, (dbl4*)h->J, jmask,
-                                    h->xi, xmask, h->W));
+                                    h->xi, xmask, h->W, (const dbl4*)h->nl_xref, hs2, nlf));
     mark(h, "baoab_first");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;

@@ -81,40 +81,6 @@ struct WkArgs {
     int max_wn;
 };
 
-// Sense-reversing grid barrier for a cooperative launch.  Waits are bounded
-// (~2^31 cycles); on a timeout the status word records it and false is
-// returned, after which the CTA leaves the kernel.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status)
-{
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*vgen == gen) {
-                if (clock64() - t0 > (1ll << 31)) {
-                    atomicOr(status, ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // Targets per pair task of an n-atom walker: the plan's T, or for a smaller
 // walker the least power of two >= n (>= 32), so that its threads split the
 // sources instead of idling.

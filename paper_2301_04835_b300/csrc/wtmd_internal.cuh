@@ -198,6 +198,41 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// Sense-reversing grid barrier for a cooperative launch.  Waits are bounded
+// (~2^31 cycles); on a timeout the status word records it and false is
+// returned, after which the CTA leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == gen) {
+                if (clock64() - t0 > (1ll << 31)) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+
 // ----------------------------------------------------------------------------
 // device-side CV description
 // ----------------------------------------------------------------------------
@@ -299,12 +334,19 @@ struct wtmd_t {
     size_t partial_bytes = 0;
     void* hev_xi = nullptr;    // hills_eval staging
     size_t hev_bytes = 0;
-    // LJ cell list
+    // LJ cell list and Verlet neighbour lists (single periodic walker)
     int nc[3] = {0, 0, 0};
     int ncells = 0;
     int cell_cap = 0;
     int* cell_count = nullptr;
     int* cell_atoms = nullptr;
+    int* nl_nbr = nullptr;          // [nl_cap8][N][NL_S] partners by j mod NL_S, increasing j
+    int* nl_cnt = nullptr;          // [N][NL_S]
+    void* nl_xref = nullptr;        // [N] R4: positions at the last build
+    unsigned* nl_ctl = nullptr;     // [0] rebuild flag
+    int nl_cap8 = 0;
+    size_t nl_smem = 0;             // shared memory of the list build
+    double nl_skin = 0.0;
     // bound arrays
     void* pos = nullptr;
     void* vel = nullptr;
@@ -385,6 +427,8 @@ void surrogate_advanced(wtmd_t* h, int64_t n);
 int surrogate_invalidate(wtmd_t* h);
 void drop_step_graphs(wtmd_t* h);                                // api.cu
 int launch_engine(wtmd_t* h);                                    // engine forces into h->force
+int nl_request(wtmd_t* h);                                       // rebuild the LJ neighbour lists at the next use
+int nl_reset(wtmd_t* h);                                         // cell counts and rebuild flag to 0
 int launch_baoab_first(wtmd_t* h, int jmask, int xmask);         // Jacobian rows / CV values to zero
 bool coord_factored(const wtmd_t* h, int c);  // CV c keeps J as FP32 tile partials (contracted by the kick)
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
