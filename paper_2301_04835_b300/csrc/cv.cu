@@ -962,9 +962,11 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
                                                               int* __restrict__ ccount, int ncells,
                                                               unsigned* __restrict__ nl_ctl)
 {
-    // Launched as a programmatic dependent of the hills sum: the atom's
-    // force, velocity and Jacobian rows (written before the hills sum
-    // started) are loaded first; dV/dxi, V and xi only after the wait.
+    // Launched as a programmatic dependent of the hills sum: the velocity
+    // (written by the previous step) is loaded first; the force and the
+    // Jacobian rows, which come from graph branches that this launch joins
+    // (joined edges are programmatic too), and dV/dxi, V and xi after the
+    // wait.
     // It also resets the engine's cell counts and neighbour-list rebuild
     // flag (the engine branch has joined).
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -975,11 +977,13 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
     R4<R> f = mk4<R>(0, 0, 0, 0), v = f, jr[3] = {f, f, f};
     if (act) {
         w = aw[i];
-        f = force[i];
         v = vel[i];
-        for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
     }
     pdl_wait();
+    if (act) {
+        f = force[i];
+        for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
+    }
     if (blockIdx.x == gridDim.x - 1) deposit_block<R>(dp, xi, V, count, step, dep, ctr, h64, h32, status);
     if (!act) return;
     for (int c = 0; c < d && c < 3; ++c) {

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
                                                         unsigned* status)
 {
     pdl_trigger();
-    if (*ctl == 0u) return;
-    pdl_wait();  // the binning
+    if (*ctl == 0u) return;  // set before the binning launch, a plain one
+    pdl_wait();              // the binning
     extern __shared__ __align__(32) unsigned char nl_smem[];
     const int ls = cap8 + 1;
     R4<R>* cpos = reinterpret_cast<R4<R>*>(nl_smem);
@@ -306,9 +306,10 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
                                                        R4<R>* __restrict__ f)
 {
     const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
-    // the flag was set (or not) before the chain started and is cleared
-    // after it; without a rebuild the lists are those of an earlier step and
-    // nothing is waited for
+    // the flag was set (or not) before the chain started, whose first launch
+    // (the binning) is a plain one, and is cleared after it; without a
+    // rebuild the lists are those of an earlier step and nothing is waited
+    // for
     if (*ctl != 0u) pdl_wait();  // the list build
     const long long NS = N * NL_S;
     const long long i = u / NL_S;
@@ -317,11 +318,19 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
         const R4<R> p = x[i];
         const int n = ncnt[u];
         // NL_B entries at a time: all their indices, then all their
-        // positions are in flight together; the sum runs in list order
-        for (int k0 = 0; k0 < n; k0 += NL_B) {
-            int jj[NL_B];
+        // positions are in flight together; the sum runs in list order.  The
+        // first NL_B slots (NL_B <= cap8) are read with the count.
+        int jj[NL_B];
 #pragma unroll
-            for (int q = 0; q < NL_B; ++q) jj[q] = k0 + q < n ? nbr[(k0 + q) * NS + u] : -1;
+        for (int q = 0; q < NL_B; ++q) jj[q] = nbr[q * NS + u];
+        for (int k0 = 0; k0 < n; k0 += NL_B) {
+            if (k0 > 0) {
+#pragma unroll
+                for (int q = 0; q < NL_B; ++q) jj[q] = k0 + q < n ? nbr[(k0 + q) * NS + u] : -1;
+            } else {
+#pragma unroll
+                for (int q = 0; q < NL_B; ++q) jj[q] = q < n ? jj[q] : -1;
+            }
             R4<R> o[NL_B];
 #pragma unroll
             for (int q = 0; q < NL_B; ++q) o[q] = jj[q] >= 0 ? x[jj[q]] : p;
@@ -480,7 +489,7 @@ int setup_cells(wtmd_t* h)
     const double mean = (double)h->N / h->ncells;
     h->cell_cap = ((int)ceil(2.0 * mean + 16.0) + 7) / 8 * 8;
     const double nmean = (double)h->N / vol * 4.0 / 3.0 * 3.14159265358979323846 * rl * rl * rl / NL_S;
-    h->nl_cap8 = ((int)ceil(2.0 * nmean + 12.0) + 3) / 4 * 4;
+    h->nl_cap8 = std::max(NL_B, ((int)ceil(2.0 * nmean + 12.0) + 3) / 4 * 4);
     const size_t r4 = h->prec == WTMD_F32 ? sizeof(float4) : sizeof(dbl4);
     WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_count, sizeof(int) * h->ncells));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
