@@ -409,17 +409,15 @@ KERNEL_SRC = {"lj_list": "engine.cu", "nl_bin": "engine.cu", "nl_build": "engine
               "deposit": "deposit.cu"}
 
 # Algorithmic work of one launch of each kernel of the 4096-atom step.
-# Pair kernels are bound by FP32 arithmetic ("alu"), counted in FLOP (an FMA
-# is 2): a coordination pair (tagged atom, any other atom) is 39 FLOP --
+# The coordination tile kernel is bound by FP32 arithmetic ("alu"), counted
+# in FLOP (an FMA is 2): a pair (tagged atom, any other atom) is 39 FLOP --
 # difference and minimum image 15, r^2 5, y = r^2/r0^2 1, y^3 2, 1 + y^3 1,
 # reciprocal 1, row sum 1, gradient prefactor 4, its three components 3, row
-# and column accumulation 6; an LJ pair inside the cutoff is 24 FLOP
-# (difference 3, r^2 5, reciprocal 1, (s/r)^6 3, force factor 6, three
-# components 6).  The other kernels move data ("hbm"), counted in compulsory
-# DRAM bytes (each array read or written once).
-FLOP_COORD_PAIR, FLOP_LJ_PAIR = 39, 24
-LJ_RC = 2.5
-LJ_PAIRS = int(N_ATOMS * RHO * 4.0 / 3.0 * np.pi * LJ_RC ** 3)  # ordered pairs inside rc
+# and column accumulation 6.  The other kernels move data ("hbm"), counted in
+# compulsory DRAM bytes (each array read or written once).
+FLOP_COORD_PAIR = 39
+LJ_RC, LJ_SKIN = 2.5, 0.3
+LJ_LIST_PER_ATOM = RHO * 4.0 / 3.0 * np.pi * (LJ_RC + LJ_SKIN) ** 3  # mean Verlet-list length
 
 
 def kernel_work(kernel: str, n_hills: int):
@@ -427,10 +425,13 @@ def kernel_work(kernel: str, n_hills: int):
     r4 = 16
     alu = {
         "coord_tile": N_TAG * (N_ATOMS - 1) * FLOP_COORD_PAIR,
-        "lj_list": LJ_PAIRS * FLOP_LJ_PAIR,
     }
     hbm = {
         "baoab_first": N_ATOMS * r4 * 5,                    # read x, v, f; write x, v
+        # LJ forces from the Verlet lists: the list entries (partners within
+        # rc + skin, 4 B each), the per-sub-list counts, positions in,
+        # forces out; the partner positions are gathered from L2
+        "lj_list": N_ATOMS * (LJ_LIST_PER_ATOM * 4 + 8 * 4 + r4 * 2),
         # J rows of the coordination CV from its partials: 8 column partials
         # per atom, 16 row partials per tagged atom, one J row out
         "coord_jfin": (8 * N_ATOMS + 16 * N_TAG + N_ATOMS) * r4,
