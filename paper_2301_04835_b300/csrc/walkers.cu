@@ -95,45 +95,86 @@ struct PairAcc {
     float fx, fy, fz, gx, gy, gz, sv;
 };
 
-// LJ force and coordination terms of target p against sources [j0, j1).
-// One approximate reciprocal of r^2 serves both: with y = r^2/r0^2 and
-// s = 1/(1 + y^h), ds/dx = -n y^h s^2 dx / r^2 (n = 2h).  H > 0 fixes the
-// exponent h at compile time, H = 0 reads it from the arguments.
+// Staged walker positions, two atoms per pair of float4 records, negated:
+// pair m holds (-x_2m, -x_2m+1, -y_2m, -y_2m+1), (-z_2m, -z_2m+1, w_2m, w_2m+1)
+// with weight w = 1 (a walker of odd size pads its last pair with a far
+// point of weight 0).  Each pair instruction of the loop below then serves
+// two sources (packed f32x2).
+constexpr float WK_FAR = -1.0e4f;  // negated coordinate of the padding point
+
+__device__ __forceinline__ float4 wk_atom(const float4* __restrict__ wpos, int q)
+{
+    const float4 A = wpos[q & ~1], B = wpos[(q & ~1) + 1];
+    return (q & 1) ? make_float4(-A.y, -A.w, -B.y, 0.f) : make_float4(-A.x, -A.z, -B.x, 0.f);
+}
+
+struct PairAcc2 {
+    float2 fx, fy, fz, gx, gy, gz, sv;
+};
+
+// LJ force and coordination terms of target i (position p) against the
+// source pairs [m0, m1), its own pair with itself left out (replaced by the
+// padding point).  One approximate reciprocal of r^2 serves both: with
+// y = r^2/r0^2 and s = 1/(1 + y^h), ds/dx = -n y^h s^2 dx / r^2 (n = 2h).
+// H > 0 fixes the exponent h at compile time, H = 0 reads it from the
+// arguments.
 template <int H>
-__device__ __forceinline__ void pair_range(const float4* __restrict__ wpos, float4 p, int j0, int j1,
-                                           const WkArgs& a, PairAcc& c)
+__device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, float4 p, int i, int m0, int m1,
+                                            const WkArgs& a, PairAcc2& c)
 {
     const bool co = a.cv_coord >= 0;
-    const float nneg = -2.f * (float)a.hpow;
-#pragma unroll 4
-    for (int j = j0; j < j1; ++j) {
-        const float4 s = wpos[j];
-        const float dx = p.x - s.x, dy = p.y - s.y, dz = p.z - s.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float ir2 = rcp_approx(r2);
+    const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y), pz = make_float2(p.z, p.z);
+    const float2 one = make_float2(1.f, 1.f), inv = make_float2(a.inv_r0sq, a.inv_r0sq);
+    const float2 nneg = make_float2(-2.f * (float)a.hpow, -2.f * (float)a.hpow);
+    const float2 sig2 = make_float2(a.sig2, a.sig2), e24 = make_float2(a.eps24, a.eps24);
+    const float2 two = make_float2(2.f, 2.f), mone = make_float2(-1.f, -1.f);
+    const int mi = i >> 1;
+#pragma unroll 2
+    for (int m = m0; m < m1; ++m) {
+        float4 A = wpos[2 * m], B = wpos[2 * m + 1];
+        if (m == mi) {
+            if (i & 1) {
+                A.y = WK_FAR;
+                A.w = WK_FAR;
+                B.y = WK_FAR;
+                B.w = 0.f;
+            } else {
+                A.x = WK_FAR;
+                A.z = WK_FAR;
+                B.x = WK_FAR;
+                B.z = 0.f;
+            }
+        }
+        const float2 dx = __fadd2_rn(px, make_float2(A.x, A.y)), dy = __fadd2_rn(py, make_float2(A.z, A.w)),
+                     dz = __fadd2_rn(pz, make_float2(B.x, B.y));
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
         if (co) {
-            const float y = r2 * a.inv_r0sq;
-            float yh = y;
+            const float2 y = __fmul2_rn(r2, inv);
+            float2 yh = y;
             if constexpr (H > 0) {
 #pragma unroll
-                for (int k = 1; k < H; ++k) yh *= y;
+                for (int k = 1; k < H; ++k) yh = __fmul2_rn(yh, y);
             } else {
-                for (int k = 1; k < a.hpow; ++k) yh *= y;
+                for (int k = 1; k < a.hpow; ++k) yh = __fmul2_rn(yh, y);
             }
-            const float sw = rcp_approx(1.f + yh);
-            c.sv += sw;
-            const float gr = nneg * yh * sw * sw * ir2;
-            c.gx = fmaf(gr, dx, c.gx);
-            c.gy = fmaf(gr, dy, c.gy);
-            c.gz = fmaf(gr, dz, c.gz);
+            const float2 den = __fadd2_rn(one, yh);
+            const float2 sw = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+            const float2 sg = __fmul2_rn(sw, make_float2(B.z, B.w));  // weighted s
+            c.sv = __fadd2_rn(c.sv, sg);
+            const float2 gr = __fmul2_rn(__fmul2_rn(__fmul2_rn(nneg, yh), __fmul2_rn(sg, sw)), ir2);
+            c.gx = __ffma2_rn(gr, dx, c.gx);
+            c.gy = __ffma2_rn(gr, dy, c.gy);
+            c.gz = __ffma2_rn(gr, dz, c.gz);
         }
-        const float sr2 = a.sig2 * ir2;
-        const float sr6 = sr2 * sr2 * sr2;
-        float fr = a.eps24 * fmaf(2.f * sr6, sr6, -sr6) * ir2;
-        fr = r2 < a.rc2 ? fr : 0.f;
-        c.fx = fmaf(fr, dx, c.fx);
-        c.fy = fmaf(fr, dy, c.fy);
-        c.fz = fmaf(fr, dz, c.fz);
+        const float2 sr2 = __fmul2_rn(sig2, ir2);
+        const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+        float2 fr = __fmul2_rn(__fmul2_rn(e24, __fmul2_rn(sr6, __ffma2_rn(sr6, two, mone))), ir2);
+        fr.x = r2.x < a.rc2 ? fr.x : 0.f;
+        fr.y = r2.y < a.rc2 ? fr.y : 0.f;
+        c.fx = __ffma2_rn(fr, dx, c.fx);
+        c.fy = __ffma2_rn(fr, dy, c.fy);
+        c.fz = __ffma2_rn(fr, dz, c.fz);
     }
 }
 
@@ -173,19 +214,30 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
             const long long o = a.woff[w];
             const int T = wk_targets(n, a.T), Gs = WK_T / T;
             const int ti = tid % T, sl = tid / T;
-            for (int q = tid; q < n; q += WK_T) wpos[q] = a.x[o + q];
+            const int np = (n + 1) / 2;
+            for (int q = tid; q < np; q += WK_T) {
+                const float4 u = a.x[o + 2 * q];
+                const bool two = 2 * q + 1 < n;
+                const float4 v = two ? a.x[o + 2 * q + 1] : make_float4(-WK_FAR, -WK_FAR, -WK_FAR, 0.f);
+                wpos[2 * q] = make_float4(-u.x, -v.x, -u.y, -v.y);
+                wpos[2 * q + 1] = make_float4(-u.z, -v.z, 1.f, two ? 1.f : 0.f);
+            }
             __syncthreads();
             const int i = t0 + ti;
             const bool act = i < t1;
             PairAcc acc{};
             if (act) {
-                const float4 p = wpos[i];
-                const int j0 = (int)((long long)n * sl / Gs), j1 = (int)((long long)n * (sl + 1) / Gs);
-                // the self pair is left out by splitting the source range at i
-                const int m0 = i >= j0 && i < j1 ? i : j1;
-                const int m1 = i >= j0 && i < j1 ? i + 1 : j1;
-                pair_range<H>(wpos, p, j0, m0, a, acc);
-                pair_range<H>(wpos, p, m1, j1, a, acc);
+                const float4 p = wk_atom(wpos, i);
+                PairAcc2 c2{};
+                const int m0 = (int)((long long)np * sl / Gs), m1 = (int)((long long)np * (sl + 1) / Gs);
+                pair_range2<H>(wpos, p, i, m0, m1, a, c2);
+                acc.fx = c2.fx.x + c2.fx.y;
+                acc.fy = c2.fy.x + c2.fy.y;
+                acc.fz = c2.fz.x + c2.fz.y;
+                acc.gx = c2.gx.x + c2.gx.y;
+                acc.gy = c2.gy.x + c2.gy.y;
+                acc.gz = c2.gz.x + c2.gz.y;
+                acc.sv = c2.sv.x + c2.sv.y;
             }
             // sum the source slices of each target in slice order
             red[tid][0] = acc.fx;
@@ -212,7 +264,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                     mom[0] = cf{v[6], 0.f};
                 }
                 if (a.cv_rg >= 0) {
-                    const float4 p = wpos[i], p0 = wpos[0];
+                    const float4 p = wk_atom(wpos, i), p0 = wk_atom(wpos, 0);
                     const float ux = p.x - p0.x, uy = p.y - p0.y, uz = p.z - p0.z;
                     mom[1] = cf{ux, 0.f};
                     mom[2] = cf{uy, 0.f};
@@ -255,7 +307,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                         double sc = a.rg_scale != 0.0 ? a.rg_scale : 1.0;
                         if (a.rg_intensive) sc /= cbrt((double)n);
                         a.xi[w * 4 + a.cv_rg] = sc * rg;
-                        const float4 p0 = wpos[0];
+                        const float4 p0 = wk_atom(wpos, 0);
                         a.rgc[w] = make_float4((float)(p0.x + cx), (float)(p0.y + cy), (float)(p0.z + cz),
                                                (float)(sc / (n * rg)));
                     }
@@ -345,7 +397,7 @@ static WkKernel wk_kernel(const wtmd_t* h)
 
 static size_t wk_smem_bytes(const wtmd_t* h)
 {
-    return sizeof(float4) * NST * 2 * CHUNK + 128 + sizeof(float4) * (size_t)h->max_wn;
+    return sizeof(float4) * NST * 2 * CHUNK + 128 + sizeof(float4) * (size_t)(h->max_wn + 1);
 }
 
 static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
