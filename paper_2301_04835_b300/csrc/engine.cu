@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
 template <typename R>
 __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>* __restrict__ x, Box box,
                                                        const int* __restrict__ nbr, const int* __restrict__ ncnt,
-                                                       const unsigned* __restrict__ ctl, R rc2, R sig2, R eps24,
-                                                       R4<R>* __restrict__ f)
+                                                       int cap8, const unsigned* __restrict__ ctl, R rc2, R sig2,
+                                                       R eps24, R4<R>* __restrict__ f)
 {
     const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
     // the flag was set (or not) before the chain started, whose first launch
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
     R fx = 0, fy = 0, fz = 0;
     if (u < NS) {
         const R4<R> p = x[i];
-        const int n = ncnt[u];
+        const int n = min(ncnt[u], cap8);
         // NL_B entries at a time: all their indices, then all their
         // positions are in flight together; the sum runs in list order.  The
         // first NL_B slots (NL_B <= cap8) are read with the count.
@@ -495,6 +495,9 @@ int setup_cells(wtmd_t* h)
     WTMD_CUDA_TRY(h, cudaMalloc(&h->cell_atoms, sizeof(int) * (size_t)h->ncells * h->cell_cap));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_nbr, sizeof(int) * (size_t)h->N * NL_S * h->nl_cap8));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_cnt, sizeof(int) * (size_t)h->N * NL_S));
+    // an atom whose cell overflowed is not given a list: it keeps the last
+    // one it had, or none
+    WTMD_CUDA_TRY(h, cudaMemset(h->nl_cnt, 0, sizeof(int) * (size_t)h->N * NL_S));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_xref, r4 * (size_t)h->N));
     WTMD_CUDA_TRY(h, cudaMalloc(&h->nl_ctl, sizeof(unsigned)));
     const unsigned one = 1u;  // build before the first use
@@ -571,8 +574,8 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
             mark(h, "nl_build");
             const unsigned nbl = (unsigned)((h->N * NL_S + NL_T - 1) / NL_T);
             WTMD_CUDA_TRY(h, launch_pdl(lj_list_kernel<R>, dim3(nbl), dim3(NL_T), 0, st, (long long)h->N, x, h->box,
-                                        (const int*)h->nl_nbr, (const int*)h->nl_cnt, (const unsigned*)h->nl_ctl,
-                                        rc2, sig2, e24, f));
+                                        (const int*)h->nl_nbr, (const int*)h->nl_cnt, h->nl_cap8,
+                                        (const unsigned*)h->nl_ctl, rc2, sig2, e24, f));
             mark(h, "lj_list");
         } else {
             dim3 g((h->max_wn + 127) / 128, h->W);

@@ -11,6 +11,8 @@ of the engine; the oracle evaluates every pair inside the cutoff directly).
   positions the step produced.
 * The FP32 coordination value (exact quantized FP64 atomics) and the forces
   of two evaluations of the same positions are bitwise equal.
+* A cell that overflows its capacity is reported (WTMD_ECELL); atoms left
+  without a list read none (list counts start at 0 and are clamped).
 """
 import numpy as np
 import pytest
@@ -115,4 +117,27 @@ def test_fp32_coordination_is_bitwise_reproducible():
         outs.append((xi.clone(), V.clone(), dV.clone(), F.clone()))
     for o in outs[1:]:
         assert all(torch.equal(p, q) for p, q in zip(outs[0], o))
+    m.close()
+
+
+def test_cell_overflow_is_reported():
+    """A dense block of 64 atoms inside one cell of a dilute box (cell
+    capacity 24) overflows the cell list: the step reports WTMD_ECELL."""
+    wt = _wt()
+    L = 20.0
+    cell = L / 7  # cells at least rc + skin = 2.8 wide
+    g = np.arange(4) * 0.65 + 0.4
+    block = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + 3 * cell
+    r = synth.rng(12)
+    far = 3 * cell + np.array([[7.5, 0.0, 0.0]]) + np.stack(np.meshgrid(np.arange(5), np.arange(5), np.arange(6),
+                                                                        indexing="ij"), -1).reshape(-1, 3) * 1.6
+    x = np.concatenate([block, far[:136] + r.normal(scale=0.02, size=(136, 3))]) % L
+    spec = dict(engine="lj", walker_sizes=[200], box=(L, L, L), dt=0.005, kT=1.0, friction=1.0, sigma=(0.1,),
+                cvs=[dict(kind="component", a=[0], axis=0)])
+    m = gpu_handle(spec, "f32")
+    pos, vel, F = _state(spec, x, np.zeros_like(x), "f32")
+    m.bind(pos, vel, F)
+    with pytest.raises(wt.WtmdError) as e:
+        m.step_n(1)
+    assert e.value.code == -7
     m.close()
