@@ -195,7 +195,7 @@ extern "C" int wtmd_create(const wtmd_config* cfg, wtmd_t** out)
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(WTMD_ECUDA, "streams");
-    for (int c = 1; c < 3; ++c)
+    for (int c = 0; c < 3; ++c)
         if (cudaStreamCreateWithFlags(&h->cv_stream[c], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&h->ev_cv[c], cudaEventDisableTiming) != cudaSuccess)
             return fail(WTMD_ECUDA, "streams");
@@ -433,28 +433,23 @@ static int enqueue_forces(wtmd_t* h)
 }
 
 // Engine force and bias (CVs -> hills sum) both only read the positions, so
-// the engine runs on a side stream forked from and joined back to the main
-// stream (parallel branches of the captured graph).  While profiling, the two
-// run in sequence so that each kernel's event interval is its own.
+// they run as parallel branches of the captured graph: the engine on the
+// main stream, the bias chain forked from it and joined back before the
+// closing kick.  While profiling, the two run in sequence so that each
+// kernel's event interval is its own.
 static int enqueue_engine_and_bias(wtmd_t* h)
 {
     int rc;
     const bool fork = !h->prof;
-    if (fork) {
-        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
-        WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0));
-        cudaStream_t main_stream = h->stream;
-        h->stream = h->side_stream;
-        rc = launch_engine(h);
-        h->stream = main_stream;
-        if (rc) return rc;
-        WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side_stream));
-    } else if ((rc = launch_engine(h))) {
-        return rc;
+    if (!fork) {
+        if ((rc = launch_engine(h)) || (rc = launch_cvs(h, h->pos))) return rc;
+        return launch_bias_sum(h);
     }
-    // CVs 1 and 2 on their own branches, CV 0 on the main stream
+    // the bias chain (CV 0 -> hills sum) on its own branch, CVs 1 and 2 on
+    // theirs, the engine on the main stream; the closing kick joins them
+    WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
     cudaStream_t main_stream = h->stream;
-    for (int c = 1; c < h->ncv && fork; ++c) {
+    for (int c = 1; c < h->ncv; ++c) {
         WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->cv_stream[c], h->ev_fork, 0));
         h->stream = h->cv_stream[c];
         rc = launch_cv(h, h->pos, c);
@@ -462,10 +457,17 @@ static int enqueue_engine_and_bias(wtmd_t* h)
         if (rc) return rc;
         WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_cv[c], h->cv_stream[c]));
     }
-    if ((rc = fork ? launch_cv(h, h->pos, 0) : launch_cvs(h, h->pos))) return rc;
-    for (int c = 1; c < h->ncv && fork; ++c) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0));
-    if ((rc = launch_bias_sum(h))) return rc;
-    if (fork) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->cv_stream[0], h->ev_fork, 0));
+    h->stream = h->cv_stream[0];
+    rc = launch_cv(h, h->pos, 0);
+    for (int c = 1; c < h->ncv && !rc; ++c)
+        if (cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0) != cudaSuccess) rc = WTMD_ECUDA;
+    if (!rc) rc = launch_bias_sum(h);
+    if (!rc && cudaEventRecord(h->ev_join, h->stream) != cudaSuccess) rc = WTMD_ECUDA;
+    h->stream = main_stream;
+    if (rc) return rc;
+    if ((rc = launch_engine(h))) return rc;
+    WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     return WTMD_OK;
 }
 
