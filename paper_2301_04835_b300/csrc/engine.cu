@@ -193,7 +193,9 @@ __global__ void nl_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box,
                               int* __restrict__ ccount, int* __restrict__ catoms, const unsigned* __restrict__ ctl,
                               unsigned* status)
 {
-    pdl_trigger();  // the list build may launch; it waits for the binning only on a rebuild
+    // a programmatic dependent of BAOAB (which sets the flag and moves the
+    // atoms): wait first
+    pdl_wait();
     if (*ctl == 0u) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
                                                         unsigned* status)
 {
     pdl_trigger();
-    if (*ctl == 0u) return;  // set before the binning launch, a plain one
+    if (*ctl == 0u) return;  // final: this is a plain launch after the binning, which waited for BAOAB
     pdl_wait();              // the binning
     extern __shared__ __align__(32) unsigned char nl_smem[];
     const int ls = cap8 + 1;
@@ -306,10 +308,10 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
                                                        R eps24, R4<R>* __restrict__ f)
 {
     const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
-    // the flag was set (or not) before the chain started, whose first launch
-    // (the binning) is a plain one, and is cleared after it; without a
-    // rebuild the lists are those of an earlier step and nothing is waited
-    // for
+    // the flag is final when this launch starts (the list build before it is
+    // a plain launch after the binning, which waited for BAOAB) and is
+    // cleared after the step; without a rebuild the lists are those of an
+    // earlier step and nothing is waited for
     if (*ctl != 0u) pdl_wait();  // the list build
     const long long NS = N * NL_S;
     const long long i = u / NL_S;
@@ -563,14 +565,17 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
             const double rl = c.lj_rc + h->nl_skin;
             // bin -> build -> forces as programmatic dependents: the first
             // two return at once unless a rebuild is flagged
-            nl_bin_kernel<R><<<nb, 256, 0, st>>>(h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
-                                                 h->cell_count, h->cell_atoms, h->nl_ctl, h->status);
+            // binning: a programmatic dependent of BAOAB; the list build: a
+            // plain launch (its large-shared-memory CTAs never wait on an
+            // SM), so the flag it and the force sweep read is final
+            WTMD_CUDA_TRY(h, launch_pdl(nl_bin_kernel<R>, dim3(nb), dim3(256), 0, st, (long long)h->N, x, h->box,
+                                        h->nc[0], h->nc[1], h->nc[2], h->cell_cap, h->cell_count, h->cell_atoms,
+                                        (const unsigned*)h->nl_ctl, h->status));
             mark(h, "nl_bin");
-            WTMD_CUDA_TRY(h, launch_pdl(nl_build_kernel<R>, dim3(h->ncells), dim3(NL_T), h->nl_smem, st, (long long)h->N,
-                                        x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
-                                        (const int*)h->cell_count, (const int*)h->cell_atoms, h->nl_nbr, h->nl_cnt,
-                                        (R4<R>*)h->nl_xref, (const unsigned*)h->nl_ctl, h->nl_cap8, (R)(rl * rl),
-                                        h->status));
+            nl_build_kernel<R><<<h->ncells, NL_T, h->nl_smem, st>>>(
+                (long long)h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap, (const int*)h->cell_count,
+                (const int*)h->cell_atoms, h->nl_nbr, h->nl_cnt, (R4<R>*)h->nl_xref, (const unsigned*)h->nl_ctl,
+                h->nl_cap8, (R)(rl * rl), h->status);
             mark(h, "nl_build");
             const unsigned nbl = (unsigned)((h->N * NL_S + NL_T - 1) / NL_T);
             WTMD_CUDA_TRY(h, launch_pdl(lj_list_kernel<R>, dim3(nbl), dim3(NL_T), 0, st, (long long)h->N, x, h->box,
