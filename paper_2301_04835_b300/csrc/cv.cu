@@ -970,8 +970,6 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
     // It also resets the engine's cell counts and neighbour-list rebuild
     // flag (the engine branch has joined).
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (long long c = i; c < ncells; c += (long long)gridDim.x * blockDim.x) ccount[c] = 0;
-    if (nl_ctl && i == 0) *nl_ctl = 0u;
     const bool act = i < N;
     int w = 0;
     R4<R> f = mk4<R>(0, 0, 0, 0), v = f, jr[3] = {f, f, f};
@@ -980,6 +978,10 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
         v = vel[i];
     }
     pdl_wait();
+    // after the wait: the engine's list build may still be reading the
+    // counts until then (a joined edge lets this launch start early)
+    for (long long c = i; c < ncells; c += (long long)gridDim.x * blockDim.x) ccount[c] = 0;
+    if (nl_ctl && i == 0) *nl_ctl = 0u;
     if (act) {
         f = force[i];
         for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
