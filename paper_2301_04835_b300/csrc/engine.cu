@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
 // increasing j.  Lane s of the atom's NL_S lanes sums the pairs of sub-list
 // s within rc in that order and a fixed xor tree adds the lanes, so the force
 // depends only on the pairs within rc, never on when the list was built.
-// Entry k of sub-list u = NL_S i + s is nbr[k * NL_S N + u], so that the
-// lanes of a warp read consecutive words.
+// Sub-list u = NL_S i + s owns the cap8 contiguous slots from nbr[u * cap8]
+// (written in one run by the list build, read as 16-byte vectors).
 //
 // Three launches per evaluation: binning and the list build return at once
 // unless the rebuild flag is set; the force kernel always runs, and zeroes
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
 constexpr int NL_S = 8;     // sub-lists (lanes) per atom
 constexpr int NL_T = 256;   // threads per CTA of the build and force kernels
 constexpr int NL_B = 12;    // list entries a force lane loads together
+static_assert(NL_B % 4 == 0, "list entries are read as 16-byte vectors");
 
 template <typename R> __device__ __forceinline__ int cell_coord(R q, R invL, int nc)
 {
@@ -261,16 +262,19 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
     }
     for (int k = threadIdx.x; k < nh * NL_S; k += NL_T) hcnt[k] = 0;
     __syncthreads();
-    for (int t = 0; t < nh; ++t) {
-        const int i = hidx[t];
-        const R4<R> p = hpos[t];
-        for (int e = threadIdx.x; e < ncand; e += NL_T) {
-            const int j = cidx[e];
-            const R4<R> o = cpos[e];
+    // each thread holds its candidates and sweeps the home atoms
+    // (broadcast reads), four at a time
+    for (int e = threadIdx.x; e < ncand; e += NL_T) {
+        const int j = cidx[e];
+        const R4<R> o = cpos[e];
+        const int sj = j % NL_S;
+#pragma unroll 4
+        for (int t = 0; t < nh; ++t) {
+            const R4<R> p = hpos[t];
             const R dx = min_image<R>(p.x - o.x, box, 0), dy = min_image<R>(p.y - o.y, box, 1),
                     dz = min_image<R>(p.z - o.z, box, 2);
-            if (j != i && dx * dx + dy * dy + dz * dz < rl2) {
-                const int k = t * NL_S + j % NL_S;
+            if (dx * dx + dy * dy + dz * dz < rl2 && j != hidx[t]) {
+                const int k = t * NL_S + sj;
                 const int slot = atomicAdd(&hcnt[k], 1);
                 if (slot < cap8) hlist[k * ls + slot] = j;
                 else atomicOr(status, ST_CELL);
@@ -278,7 +282,6 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
         }
     }
     __syncthreads();
-    const long long NS = N * NL_S;
     for (int k = threadIdx.x; k < nh * NL_S; k += NL_T) {
         const int n = min(hcnt[k], cap8);
         int* l = hlist + k * ls;
@@ -292,7 +295,8 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
             l[b] = v;
         }
         const long long u = (long long)hidx[k / NL_S] * NL_S + k % NL_S;
-        for (int a = 0; a < n; ++a) nbr[a * NS + u] = l[a];
+        int* out = nbr + u * cap8;  // the sub-list's own contiguous slots
+        for (int a = 0; a < n; ++a) out[a] = l[a];
         ncnt[u] = n;
     }
     for (int t = threadIdx.x; t < nh; t += NL_T) xref[hidx[t]] = hpos[t];
@@ -322,13 +326,20 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
         // NL_B entries at a time: all their indices, then all their
         // positions are in flight together; the sum runs in list order.  The
         // first NL_B slots (NL_B <= cap8) are read with the count.
+        const int* lst = nbr + u * cap8;  // 16-byte aligned (cap8 is a multiple of 4)
         int jj[NL_B];
 #pragma unroll
-        for (int q = 0; q < NL_B; ++q) jj[q] = nbr[q * NS + u];
+        for (int q = 0; q < NL_B; q += 4) {
+            const int4 v = *reinterpret_cast<const int4*>(lst + q);
+            jj[q] = v.x;
+            jj[q + 1] = v.y;
+            jj[q + 2] = v.z;
+            jj[q + 3] = v.w;
+        }
         for (int k0 = 0; k0 < n; k0 += NL_B) {
             if (k0 > 0) {
 #pragma unroll
-                for (int q = 0; q < NL_B; ++q) jj[q] = k0 + q < n ? nbr[(k0 + q) * NS + u] : -1;
+                for (int q = 0; q < NL_B; ++q) jj[q] = k0 + q < n ? lst[k0 + q] : -1;
             } else {
 #pragma unroll
                 for (int q = 0; q < NL_B; ++q) jj[q] = q < n ? jj[q] : -1;
