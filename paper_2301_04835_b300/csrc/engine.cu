@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
 // raises the rebuild flag past skin / 2 (whoever moved the atom); a force
 // evaluation that no BAOAB precedes requests a rebuild.
 //
-// Each atom's partners are stored as NL_S sub-lists by j mod NL_S, each in
-// increasing j.  Lane s of the atom's NL_S lanes sums the pairs of sub-list
+// Each atom's partners are stored as NL_S sub-lists by a hash of j
+// (nl_sub), each in increasing j.  Lane s of the atom's NL_S lanes sums the pairs of sub-list
 // s within rc in that order and a fixed xor tree adds the lanes, so the force
 // depends only on the pairs within rc, never on when the list was built.
 // Sub-list u = NL_S i + s owns the cap8 contiguous slots from nbr[u * cap8]
@@ -169,7 +169,15 @@ __global__ void __launch_bounds__(128) lj_allpairs_kernel(const R4<R>* __restric
 // Three launches per evaluation: binning and the list build return at once
 // unless the rebuild flag is set; the force kernel always runs, and zeroes
 // the cell counts and the flag for the next rebuild.
-constexpr int NL_S = 8;     // sub-lists (lanes) per atom
+constexpr int NL_S = 8;     // sub-lists (lanes) per atom (a power of two)
+constexpr int NL_SHIFT = 29; // 32 - log2(NL_S)
+static_assert((1 << (32 - NL_SHIFT)) == NL_S, "NL_SHIFT matches NL_S");
+
+// Sub-list of partner j: the top bits of a multiplicative (Fibonacci) hash
+// of j, so that the sub-lists stay balanced when atom indices follow
+// positions (a lattice start numbers the atoms row by row: j mod NL_S would
+// put a whole plane of neighbours into one sub-list).
+__host__ __device__ __forceinline__ int nl_sub(int j) { return (int)(((unsigned)j * 2654435761u) >> NL_SHIFT); }
 constexpr int NL_T = 256;   // threads per CTA of the build and force kernels
 constexpr int NL_B = 12;    // list entries a force lane loads together
 static_assert(NL_B % 4 == 0, "list entries are read as 16-byte vectors");
@@ -210,7 +218,7 @@ __global__ void nl_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box,
 
 // List build, one CTA per home cell: the 27 neighbour cells' atoms are
 // staged in shared memory, every (home atom, candidate) pair is tested,
-// partners within rl go to the home atom's sub-list by j mod NL_S, and each
+// partners within rl go to the home atom's sub-list nl_sub(j), and each
 // sub-list is sorted.  Sub-lists in shared memory have an odd stride.
 template <typename R>
 __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>* __restrict__ x, Box box, int ncx,
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
     for (int e = threadIdx.x; e < ncand; e += NL_T) {
         const int j = cidx[e];
         const R4<R> o = cpos[e];
-        const int sj = j % NL_S;
+        const int sj = nl_sub(j);
 #pragma unroll 4
         for (int t = 0; t < nh; ++t) {
             const R4<R> p = hpos[t];
