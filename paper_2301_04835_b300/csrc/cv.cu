@@ -1175,17 +1175,19 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                     }
                     break;
                 }
-                if (!h->jz_pre) WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
-                dim3 gt(cv.ntile * cv.nbchunk, W);
-                // programmatic dependent of the kernel that moved the positions
-                auto kern = cv.nn == 6 ? coord_tile_kernel<R, 3> : coord_tile_kernel<R, 0>;
-                WTMD_CUDA_TRY(h, launch_pdl(kern, gt, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
-                                            (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
-                                            cv.nn / 2, gp, (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col, cv.nB_stride,
-                                            (const double*)cv.scw, (double*)cv.part_row, cv.tile_tk, Jc, xi, c,
-                                            (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b)));
-                mark(h, "coord_tile");
-                break;
+                else {  // FP64: the generic tile kernel, finalized in-launch
+                    if (!h->jz_pre) WTMD_CUDA_TRY(h, cudaMemsetAsync(Jc, 0, sizeof(R4<R>) * (size_t)h->N, st));
+                    dim3 gt(cv.ntile * cv.nbchunk, W);
+                    // programmatic dependent of the kernel that moved the positions
+                    auto kern = cv.nn == 6 ? coord_tile_kernel<R, 3> : coord_tile_kernel<R, 0>;
+                    WTMD_CUDA_TRY(h, launch_pdl(kern, gt, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
+                                                (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
+                                                cv.nn / 2, gp, (R4<R>*)cv.tile_row, (R4<R>*)cv.tile_col,
+                                                cv.nB_stride, (const double*)cv.scw, (double*)cv.part_row,
+                                                cv.tile_tk, Jc, xi, c, (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b)));
+                    mark(h, "coord_tile");
+                    break;
+                }
             }
             const int nt = cv.order ? cv.n_order : h->max_wn;
             // a short list A against many partners: one CTA per member of A
