@@ -257,6 +257,62 @@ def test_bias_eval_each_cv(prec, name):
     _close_F(F, Fr, prec, Fs)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("with_b", [False, True])
+def test_bias_eval_walkers_coordination_tiles(prec, with_b):
+    """Three walkers of uneven size sharing one box: the coordination tile
+    path (an explicit tagged list, partners all atoms of the walker or an
+    explicit list) runs one grid row per walker, each with its own scale and
+    value quantum, and a ragged last tile and chunk."""
+    sizes = [300, 260, 340]
+    L = (300 / 0.8) ** (1 / 3)
+
+    def ties(x, tag):
+        # a pair exactly half a box apart has two minimum images whose
+        # Jacobians differ (the CV has a kink there): keep such draws out
+        off = 0
+        for n in sizes:
+            xw = x[off: off + n].astype(np.float32).astype(np.float64)
+            q = (xw[tag][:, None, :] - xw[None, :, :]) / L
+            if np.any(np.abs(np.abs(q) - 0.5) < 1e-6):
+                return True
+            off += n
+        return False
+
+    for seed in range(21, 121):
+        r = synth.rng(seed)
+        x = np.concatenate([r.uniform(0.0, L, size=(n, 3)) for n in sizes])
+        tag = sorted(r.choice(260, 70, replace=False).tolist())
+        b = sorted(r.choice(260, 200, replace=False).tolist()) if with_b else None
+        if not ties(x, tag):
+            break
+    cvs = [dict(kind="coordination", a=tag, b=b, r0=1.5, nn=6, mm=12), dict(kind="rg", a=list(range(30)))]
+    spec = dict(engine="lj", walker_sizes=sizes, box=(L, L, L), sigma=(0.05, 0.1), cvs=cvs, capacity=2000)
+    wt = _wt()
+    import oracle as o
+
+    dt = torch.float32 if prec == "f32" else torch.float64
+    xin = _f32(x) if prec == "f32" else x
+    sim = o.Sim(oracle_system(spec), x=xin)
+    _, xi0, _, _ = sim.bias(xin, hills=np.zeros((0, 4)))
+    sig = np.asarray(spec["sigma"])
+    # hills around every walker's CVs, so that each walker's bias matters
+    hills = np.concatenate([synth.walk_hills(300, xi0[w, :2] - 3 * sig, xi0[w, :2] + 3 * sig, 0.5 * sig, seed=30 + w)
+                            for w in range(len(sizes))])
+    Fr, xir, Vr, dVr = sim.bias(xin, hills=hills)
+    m = gpu_handle(spec, prec)
+    m.hills_load(hills)
+    pos = wt.particles(xin, dt)
+    F = torch.zeros_like(pos)
+    V, xi, dV = m.bias_eval(pos, F)
+    torch.cuda.synchronize()
+    tol = 1e-12 if prec == "f64" else 1e-6
+    assert np.allclose(to_np(xi), xir[:, :2], rtol=tol, atol=tol)
+    _close_V(to_np(V), Vr, prec)
+    _close_dV(to_np(dV), dVr[:, :2], grad_scale(xir[:, :2], hills, spec["sigma"]), prec)
+    _close_F(to_np(F)[:, :3], Fr, prec, force_scale(sim, xin, hills, [0, 0]))
+
+
 def test_bias_eval_many_walkers_chain_dihedrals():
     """1024 replicas of a 22-bead chain, two dihedral CVs (beads 5-7-9-15 and
     7-9-15-17, 0-based), periodic, sigma 0.35 rad: every replica's forces."""
