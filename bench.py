@@ -571,6 +571,7 @@ def hills_micro(wt, torch, dev, flush):
             pts = torch.tensor(synth.uniform_points(P, lo, hi, seed=P + d), dtype=torch.float32, device=dev)
             V = torch.empty(P, dtype=torch.float32, device=dev)
             dV = torch.empty(P, d, dtype=torch.float32, device=dev)
+            plan = m.hills_tune(P)  # the library's launch-plan autotuner, as the step path uses it
             for _ in range(3):
                 m.hills_eval_into(pts, V, dV)
             reps = 5 if P >= 1024 else 20
@@ -585,7 +586,7 @@ def hills_micro(wt, torch, dev, flush):
             ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
             rate = P * H / (ms * 1e-3)
             peak = min(ex2, fma / ops)
-            out["cases"].append(dict(d=d, P=P, hills=H, ms=ms, hill_evals_per_s=rate,
+            out["cases"].append(dict(d=d, P=P, hills=H, ms=ms, hill_evals_per_s=rate, plan=plan,
                                      bound="mufu" if ex2 <= fma / ops else "fp32",
                                      frac_of_measured_pipe_peak=rate / peak,
                                      hbm_gbs=(H * 16) / (ms * 1e-3) / 1e9))
