@@ -59,7 +59,7 @@ class _Sys(C.Structure):
         ("n_cv", C.c_int64), ("cv", C.POINTER(_CV)), ("sigma", C.c_double * 3),
         ("w0", C.c_double), ("gamma", C.c_double), ("stride", C.c_int64), ("hill_cap", C.c_int64),
         ("grid_bins", C.c_int64 * 3), ("grid_lo", C.c_double * 3), ("grid_hi", C.c_double * 3),
-        ("bias_on", C.c_int64),
+        ("bias_on", C.c_int64), ("bias_grid", C.c_int64),
     ]
 
 
@@ -96,7 +96,10 @@ def lib():
         _lib.orc_wt_height.restype = d
         _lib.orc_grid_add.argtypes = [i64, C.POINTER(i64), dp, dp, dp, dp, dp, d, dp]
         _lib.orc_fes.argtypes = [i64, dp, d, dp]
+        _lib.orc_grid_interp.argtypes = [i64, C.POINTER(i64), dp, dp, dp, dp, i64, dp, dp, dp]
+        _lib.orc_grid_interp.restype = C.c_int
         _lib.orc_bias.argtypes = [C.POINTER(_Sys), dp, dp, i64, dp, dp, dp, dp]
+        _lib.orc_bias_grid.argtypes = [C.POINTER(_Sys), dp, dp, dp, dp, dp, dp]
         _lib.orc_forces.argtypes = [C.POINTER(_Sys), C.POINTER(_State)]
         _lib.orc_run.argtypes = [C.POINTER(_Sys), C.POINTER(_State), i64]
         _lib.orc_num_threads.restype = C.c_int
@@ -233,6 +236,25 @@ def grid_add(grid, bins, lo, hi, sigma, s, w, period=None):
                        _dp(pad(s, 0.0)), w, _dp(grid))
 
 
+def grid_interp(grid, bins, lo, hi, xi, period=None):
+    """Bias V and dV/dxi at points xi [P][d] read from a grid of V (Sec. 2.1.5,
+    bias stored on a pre-defined grid): central-difference node gradients and
+    multilinear interpolation of V and of the gradient (reading stated in
+    wtmd_oracle.c, orc_grid_interp)."""
+    xi = _f64(np.atleast_2d(xi))
+    P, d = xi.shape
+    b = (C.c_int64 * 3)(*(list(bins) + [1] * (3 - d)))
+    pad = lambda v, fill: _f64(list(v) + [fill] * (3 - d))
+    per = pad(period if period is not None else [0.0] * d, 0.0)
+    g = _f64(grid).reshape(-1)
+    V = np.zeros(P)
+    dV = np.zeros((P, d))
+    if lib().orc_grid_interp(d, b, _dp(pad(lo, 0.0)), _dp(pad(hi, 1.0)), _dp(per), _dp(g), P, _dp(xi), _dp(V),
+                             _dp(dV)) != 0:
+        raise ValueError("grid_interp: every axis needs at least 2 cells")
+    return V, dV
+
+
 def fes(grid, gamma):
     g = _f64(grid)
     out = np.zeros_like(g)
@@ -287,6 +309,7 @@ class System:
     grid_lo: tuple = (0.0, 0.0, 0.0)
     grid_hi: tuple = (1.0, 1.0, 1.0)
     bias_on: bool = True
+    bias_grid: bool = False
 
 
 class Sim:
@@ -332,6 +355,7 @@ class Sim:
         s.grid_lo = (C.c_double * 3)(*(list(sys.grid_lo) + [0.0] * (3 - len(sys.grid_lo))))
         s.grid_hi = (C.c_double * 3)(*(list(sys.grid_hi) + [1.0] * (3 - len(sys.grid_hi))))
         s.bias_on = 1 if sys.bias_on else 0
+        s.bias_grid = 1 if sys.bias_grid else 0
         self._sys = s
 
     def _state(self) -> _State:
@@ -370,6 +394,18 @@ class Sim:
         xi, V, dV = np.zeros((W, 3)), np.zeros(W), np.zeros((W, 3))
         if lib().orc_bias(C.byref(self._sys), _dp(x), _dp(h), h.shape[0], _dp(f), _dp(xi), _dp(V), _dp(dV)) != 0:
             raise ValueError("oracle bias failed")
+        return f, xi, V, dV
+
+    def bias_grid(self, x, f=None, grid=None):
+        """One bias evaluation at x with V and dV/dxi read from the grid (the
+        current one, or `grid`): returns (f - J^T dV, xi [W][3], V [W], dV [W][3])."""
+        x = _f64(x).reshape(-1, 3)
+        f = np.zeros_like(x) if f is None else _f64(f).reshape(-1, 3).copy()
+        g = self.grid if grid is None else _f64(grid).reshape(-1)
+        W = len(self._wn)
+        xi, V, dV = np.zeros((W, 3)), np.zeros(W), np.zeros((W, 3))
+        if lib().orc_bias_grid(C.byref(self._sys), _dp(x), _dp(g), _dp(f), _dp(xi), _dp(V), _dp(dV)) != 0:
+            raise ValueError("oracle grid bias failed")
         return f, xi, V, dV
 
     def fes(self):

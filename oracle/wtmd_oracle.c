@@ -489,6 +489,100 @@ void orc_grid_add(int64_t d, const int64_t* bins, const double* lo, const double
     }
 }
 
+/* Bias and its gradient read from the grid (Sec. 2.1.5: the bias potential
+ * kept on a pre-defined grid, trading accuracy for speed).  The paper stores
+ * the potential only and says nothing of how forces are taken from it; the
+ * reading here:
+ *   - nodes are the cell centres c_ik = lo_i + (k + 1/2) dx_i, dx_i =
+ *     (hi_i - lo_i) / n_i, holding V;
+ *   - the gradient at a node along axis i is the central difference
+ *     (V[k+1] - V[k-1]) / (2 dx_i); on a non-periodic axis the end nodes
+ *     take the one-sided difference (V[1] - V[0]) / dx_i and
+ *     (V[n-1] - V[n-2]) / dx_i; periodic axes wrap node indices mod n_i;
+ *   - at a point, u_i = (xi_i - lo_i) / dx_i - 1/2; a periodic axis reduces
+ *     u_i into [0, n_i), a non-periodic one clamps it to [0, n_i - 1]
+ *     (beyond the outermost nodes the edge values hold); the lower corner is
+ *     k_i = floor(u_i) (at most n_i - 2 when non-periodic), t_i = u_i - k_i;
+ *   - V(xi) and each dV/dxi_i are multilinear interpolations of the node
+ *     values over the 2^d corners, corner weight prod_i (t_i or 1 - t_i).
+ * Every axis needs n_i >= 2.  xi and dV are [P][d]. */
+static double orc_grid_node(int64_t d, const int64_t* bins, const double* grid, const int64_t* k)
+{
+    int64_t cell = 0;
+    for (int64_t i = 0; i < d; ++i) cell = cell * bins[i] + k[i];
+    return grid[cell];
+}
+
+static double orc_grid_node_grad(int64_t d, const int64_t* bins, const double* lo, const double* hi,
+                                 const double* period, const double* grid, const int64_t* k, int64_t axis)
+{
+    int64_t n = bins[axis];
+    double dx = (hi[axis] - lo[axis]) / (double)n;
+    int periodic = period && period[axis] > 0.0;
+    int64_t kp[3] = {k[0], k[1], k[2]}, km[3] = {k[0], k[1], k[2]};
+    double span;
+    if (periodic) {
+        kp[axis] = (k[axis] + 1) % n;
+        km[axis] = (k[axis] + n - 1) % n;
+        span = 2.0 * dx;
+    } else if (k[axis] == 0) {
+        kp[axis] = 1;
+        span = dx;
+    } else if (k[axis] == n - 1) {
+        km[axis] = n - 2;
+        span = dx;
+    } else {
+        kp[axis] = k[axis] + 1;
+        km[axis] = k[axis] - 1;
+        span = 2.0 * dx;
+    }
+    return (orc_grid_node(d, bins, grid, kp) - orc_grid_node(d, bins, grid, km)) / span;
+}
+
+int orc_grid_interp(int64_t d, const int64_t* bins, const double* lo, const double* hi, const double* period,
+                    const double* grid, int64_t P, const double* xi, double* V, double* dV)
+{
+    for (int64_t i = 0; i < d; ++i)
+        if (bins[i] < 2) return -1;
+    for (int64_t p = 0; p < P; ++p) {
+        int64_t k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = 0; i < d; ++i) {
+            int64_t n = bins[i];
+            double dx = (hi[i] - lo[i]) / (double)n;
+            double u = (xi[d * p + i] - lo[i]) / dx - 0.5;
+            if (period && period[i] > 0.0) {
+                u -= (double)n * floor(u / (double)n);
+                if (!(u >= 0.0 && u < (double)n)) u = 0.0; /* rounding at n, or a non-finite / huge xi */
+                k0[i] = (int64_t)floor(u);
+                k1[i] = (k0[i] + 1) % n;
+            } else {
+                if (!(u >= 0.0)) u = 0.0; /* below the first node, or not a number */
+                if (u > (double)(n - 1)) u = (double)(n - 1);
+                k0[i] = (int64_t)floor(u);
+                if (k0[i] > n - 2) k0[i] = n - 2;
+                k1[i] = k0[i] + 1;
+            }
+            t[i] = u - (double)k0[i];
+        }
+        double v = 0.0, g[3] = {0.0, 0.0, 0.0};
+        for (int64_t corner = 0; corner < ((int64_t)1 << d); ++corner) {
+            int64_t k[3] = {0, 0, 0};
+            double wgt = 1.0;
+            for (int64_t i = 0; i < d; ++i) {
+                int upper = (int)((corner >> i) & 1);
+                k[i] = upper ? k1[i] : k0[i];
+                wgt *= upper ? t[i] : 1.0 - t[i];
+            }
+            v += wgt * orc_grid_node(d, bins, grid, k);
+            for (int64_t i = 0; i < d; ++i) g[i] += wgt * orc_grid_node_grad(d, bins, lo, hi, period, grid, k, i);
+        }
+        V[p] = v;
+        for (int64_t i = 0; i < d; ++i) dV[d * p + i] = g[i];
+    }
+    return 0;
+}
+
 /* Free-energy estimate from the WT bias: A = -(gamma/(gamma-1)) V + C,
  * (standard metadynamics: A = -V + C); C puts the minimum at zero.
  * Meaning of A: Sec. 2.1, Eq. (free-energy). */
@@ -536,6 +630,7 @@ typedef struct {
     int64_t grid_bins[3];     /* all zero: no grid */
     double grid_lo[3], grid_hi[3];
     int64_t bias_on;
+    int64_t bias_grid;        /* 1: the bias is read from the grid (orc_grid_interp), not summed over hills */
 } orc_sys;
 
 typedef struct {
@@ -593,10 +688,12 @@ static void orc_engine(const orc_sys* s, const double* x, double* f)
     }
 }
 
-/* Bias at x: CVs, hills sum over the first H hills, and f -= J^T dV/dxi
- * for every walker.  xi, V, dV receive the per-walker values. */
-int orc_bias(const orc_sys* s, const double* x, const double* hills, int64_t H, double* f, double* xi, double* V,
-             double* dV)
+/* Bias at x: CVs, then V and dV/dxi from the hills sum over the first H
+ * hills (grid == NULL) or from the grid (orc_grid_interp), and
+ * f -= J^T dV/dxi for every walker.  xi, V, dV receive the per-walker
+ * values. */
+static int orc_bias_from(const orc_sys* s, const double* x, const double* hills, int64_t H, const double* grid,
+                         double* f, double* xi, double* V, double* dV)
 {
     double period[3];
     orc_periods(s, period);
@@ -610,7 +707,15 @@ int orc_bias(const orc_sys* s, const double* x, const double* hills, int64_t H, 
                 free(J);
                 return -1;
             }
-        orc_hills_sum(d, 1, xw, H, hills, s->sigma, period, &vw, gw);
+        if (grid) {
+            int64_t bins[3] = {s->grid_bins[0], s->grid_bins[1], s->grid_bins[2]};
+            if (orc_grid_interp(d, bins, s->grid_lo, s->grid_hi, period, grid, 1, xw, &vw, gw) != 0) {
+                free(J);
+                return -1;
+            }
+        } else {
+            orc_hills_sum(d, 1, xw, H, hills, s->sigma, period, &vw, gw);
+        }
         for (int64_t c = 0; c < d; ++c)
             for (int64_t i = 0; i < 3 * n; ++i) f[3 * o + i] -= gw[c] * J[3 * n * c + i];
         for (int64_t c = 0; c < 3; ++c) {
@@ -623,11 +728,26 @@ int orc_bias(const orc_sys* s, const double* x, const double* hills, int64_t H, 
     return 0;
 }
 
-/* Total force (engine + bias) at the current positions; fills xi, V, dV. */
+int orc_bias(const orc_sys* s, const double* x, const double* hills, int64_t H, double* f, double* xi, double* V,
+             double* dV)
+{
+    return orc_bias_from(s, x, hills, H, NULL, f, xi, V, dV);
+}
+
+/* The same with the bias read from the grid. */
+int orc_bias_grid(const orc_sys* s, const double* x, const double* grid, double* f, double* xi, double* V, double* dV)
+{
+    return orc_bias_from(s, x, NULL, 0, grid, f, xi, V, dV);
+}
+
+/* Total force (engine + bias) at the current positions; fills xi, V, dV.
+ * With bias_grid set the bias comes from the grid, and so does the V that
+ * sets the next hill's height. */
 int orc_forces(const orc_sys* s, orc_state* st)
 {
     orc_engine(s, st->x, st->f);
     if (!s->bias_on) return 0;
+    if (s->bias_grid) return orc_bias_grid(s, st->x, st->grid, st->f, st->xi, st->V, st->dV);
     return orc_bias(s, st->x, st->hills, st->n_hills, st->f, st->xi, st->V, st->dV);
 }
 

@@ -23,6 +23,8 @@ def oracle_system(spec):
               gamma=spec.get("gamma", 10.0), stride=spec.get("stride", 100), hill_cap=spec.get("capacity", 1000))
     if grid:
         kw.update(grid_bins=tuple(grid[0]), grid_lo=tuple(grid[1]), grid_hi=tuple(grid[2]))
+    if spec.get("bias_grid"):
+        kw.update(bias_grid=True)
     return o.System(**kw)
 
 
@@ -38,6 +40,8 @@ def gpu_handle(spec, precision):
         m.cv_define(KIND[c["kind"]], a=c.get("a"), b=c.get("b"), axis=c.get("axis", 0), r0=c.get("r0", 1.5),
                     nn=c.get("nn", 6), mm=c.get("mm", 12), scale=c.get("scale", 0.0), flags=c.get("flags", 0),
                     period=c.get("period", 0.0))
+    if spec.get("bias_grid"):
+        m.bias_source(wt.BIAS_GRID)
     return m
 
 
