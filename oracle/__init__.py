@@ -25,6 +25,10 @@ _SRC = os.path.join(_HERE, "wtmd_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 CV_COMPONENT, CV_DIHEDRAL, CV_COORDINATION, CV_RG, CV_QPAIRS = 1, 2, 3, 4, 5
+CV_DISTANCE, CV_ANGLE, CV_GYRATION = 6, 7, 8
+# CV_GYRATION quantities (axis): principal moments l1 <= l2 <= l3, asphericity,
+# acylindricity, relative shape anisotropy
+GY_L1, GY_L2, GY_L3, GY_ASPHERICITY, GY_ACYLINDRICITY, GY_ANISOTROPY = 0, 1, 2, 3, 4, 5
 CV_INTENSIVE = 1
 ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN, ENGINE_HARMONIC, ENGINE_WELLS3 = 0, 1, 2, 3, 4, 5
 

@@ -276,7 +276,16 @@ double orc_chain(int64_t nb, const double* x, double kb, double r0, double ka, d
 /* Collective variables (Sec. 2.2).  Each evaluates xi for one walker whose  */
 /* atoms are x[0..n-1] and writes the dense Jacobian J[n][3] = d xi / d x.   */
 /* ------------------------------------------------------------------------ */
-enum { ORC_CV_COMPONENT = 1, ORC_CV_DIHEDRAL = 2, ORC_CV_COORDINATION = 3, ORC_CV_RG = 4, ORC_CV_QPAIRS = 5 };
+enum {
+    ORC_CV_COMPONENT = 1,
+    ORC_CV_DIHEDRAL = 2,
+    ORC_CV_COORDINATION = 3,
+    ORC_CV_RG = 4,
+    ORC_CV_QPAIRS = 5,
+    ORC_CV_DISTANCE = 6,
+    ORC_CV_ANGLE = 7,
+    ORC_CV_GYRATION = 8
+};
 enum { ORC_CV_INTENSIVE = 1 };
 
 typedef struct {
@@ -309,6 +318,81 @@ static double orc_switch(double r2, double r0, int64_t nn, double* gr)
 }
 
 static int64_t orc_group(int64_t na, const int32_t* a, int64_t n, int64_t k) { return na < 0 ? k : (int64_t)a[k]; }
+
+/* Members of a group unwrapped by the minimum image relative to its first
+ * member (u [m][3]) and their mean c: the equal-mass centre used by Rg,
+ * Distance and the gyration tensor. */
+static void orc_group_unwrap(int64_t na, const int32_t* a, int64_t n, const double* x, const double* box, double* u,
+                             double c[3])
+{
+    int64_t m = na < 0 ? n : na;
+    int64_t i0 = orc_group(na, a, n, 0);
+    long double cl[3] = {0.0L, 0.0L, 0.0L};
+    for (int64_t p = 0; p < m; ++p) {
+        int64_t i = orc_group(na, a, n, p);
+        double d[3];
+        orc_delta(&x[3 * i], &x[3 * i0], box, d);
+        for (int k = 0; k < 3; ++k) {
+            u[3 * p + k] = x[3 * i0 + k] + d[k];
+            cl[k] += u[3 * p + k];
+        }
+    }
+    for (int k = 0; k < 3; ++k) c[k] = (double)(cl[k] / (long double)m);
+}
+
+/* Eigenvalues (ascending) and unit eigenvectors (columns of V) of a real
+ * symmetric 3x3 matrix by cyclic Jacobi rotations (Golub & Van Loan,
+ * Matrix Computations, Sec. 8.5): each rotation zeroes one off-diagonal
+ * element; sweeps repeat until the off-diagonal norm is negligible. */
+static void orc_eig3(const double S[3][3], double lam[3], double V[3][3])
+{
+    double A[3][3];
+    memcpy(A, S, sizeof(A));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        if (off <= 1e-40 * diag || off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation angle: tan(2 theta) = 2 A_pq / (A_qq - A_pp) */
+                double tau = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+                for (int k = 0; k < 3; ++k) { /* A <- A G (columns p, q) */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 3; ++k) { /* A <- G^T A (rows p, q) */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 3; ++k) { /* V <- V G */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int idx[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i) /* sort ascending */
+        for (int j = i + 1; j < 3; ++j)
+            if (A[idx[j]][idx[j]] < A[idx[i]][idx[i]]) {
+                int t = idx[i];
+                idx[i] = idx[j];
+                idx[j] = t;
+            }
+    double W[3][3];
+    for (int k = 0; k < 3; ++k) {
+        lam[k] = A[idx[k]][idx[k]];
+        for (int i = 0; i < 3; ++i) W[i][k] = V[i][idx[k]];
+    }
+    memcpy(V, W, sizeof(W));
+}
 
 /* Evaluate one CV for one walker.  Returns 0 or -1 on bad input. */
 int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box, double* xi, double* J)
@@ -395,6 +479,125 @@ int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box,
         }
         free(u);
         *xi = sc * rg;
+        return 0;
+    }
+    case ORC_CV_DISTANCE: {
+        /* Sec. 2.2 TwoPointCV "Distance": distance between the equal-mass
+         * centres of groups A and B (each unwrapped relative to its first
+         * member), the centre difference taken by the minimum image.
+         * dxi/dr = -n/|A| for members of A, +n/|B| for members of B, n the
+         * unit vector from c_A to c_B; A and B are disjoint. */
+        int64_t ma = cv->n_a, mb = cv->n_b;
+        double* ua = (double*)malloc(sizeof(double) * 3 * (size_t)ma);
+        double* ub = (double*)malloc(sizeof(double) * 3 * (size_t)mb);
+        double ca[3], cb[3], d[3];
+        orc_group_unwrap(ma, cv->a, n, x, box, ua, ca);
+        orc_group_unwrap(mb, cv->b, n, x, box, ub, cb);
+        orc_delta(cb, ca, box, d);
+        double r = sqrt(dot3(d, d));
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0;
+        for (int64_t p = 0; p < ma; ++p)
+            for (int k = 0; k < 3; ++k) J[3 * cv->a[p] + k] -= sc * d[k] / r / (double)ma;
+        for (int64_t p = 0; p < mb; ++p)
+            for (int k = 0; k < 3; ++k) J[3 * cv->b[p] + k] += sc * d[k] / r / (double)mb;
+        free(ua);
+        free(ub);
+        *xi = sc * r;
+        return 0;
+    }
+    case ORC_CV_ANGLE: {
+        /* Sec. 2.2 ThreePointCV "Angle" at the middle atom: u = p0 - p1,
+         * v = p2 - p1 (minimum image), theta = atan2(|u x v|, u.v) in [0, pi].
+         * With w = u x v, s = |w|, c = u.v, w^ = w / s:
+         * dtheta/du = (c (v x w^) - s v) / (s^2 + c^2),
+         * dtheta/dv = (c (w^ x u) - s u) / (s^2 + c^2),
+         * dtheta/dp1 = -(dtheta/du + dtheta/dv).  At 0 and pi (s = 0) the
+         * gradient is taken as 0. */
+        int64_t i0 = cv->a[0], i1 = cv->a[1], i2 = cv->a[2];
+        double u[3], v[3], w[3], wh[3] = {0.0, 0.0, 0.0}, vw[3], wu[3];
+        orc_delta(&x[3 * i0], &x[3 * i1], box, u);
+        orc_delta(&x[3 * i2], &x[3 * i1], box, v);
+        cross3(u, v, w);
+        double sn = sqrt(dot3(w, w)), cs = dot3(u, v);
+        double th = atan2(sn, cs);
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0;
+        if (sn > 0.0) {
+            for (int k = 0; k < 3; ++k) wh[k] = w[k] / sn;
+            cross3(v, wh, vw);
+            cross3(wh, u, wu);
+            double den = sn * sn + cs * cs;
+            for (int k = 0; k < 3; ++k) {
+                double gu = (cs * vw[k] - sn * v[k]) / den;
+                double gv = (cs * wu[k] - sn * u[k]) / den;
+                J[3 * i0 + k] += sc * gu;
+                J[3 * i2 + k] += sc * gv;
+                J[3 * i1 + k] -= sc * (gu + gv);
+            }
+        }
+        *xi = sc * th;
+        return 0;
+    }
+    case ORC_CV_GYRATION: {
+        /* Sec. 2.2 gyration-tensor CVs (AxisCV PrincipalMoment; Asphericity,
+         * Acylindricity, ShapeAnisotropy), equal masses.  S = 1/m sum_k
+         * (u_k - c)(u_k - c)^T with u, c as for Rg; eigenvalues l1 <= l2 <=
+         * l3, unit eigenvectors e1..e3.  axis selects the quantity:
+         *   0, 1, 2: l1, l2, l3 (principal moments);
+         *   3: asphericity b = l3 - (l1 + l2)/2;
+         *   4: acylindricity c = l2 - l1;
+         *   5: relative shape anisotropy k2 = 3/2 (l1^2+l2^2+l3^2)/(l1+l2+l3)^2 - 1/2.
+         * For a simple eigenvalue dl_j/dr_k = (2/m) (e_j.(u_k - c)) e_j (the
+         * centring term sums to zero), and the quantity's gradient is
+         * sum_j (dq/dl_j) dl_j/dr_k. */
+        int64_t m = cv->n_a < 0 ? n : cv->n_a;
+        double* u = (double*)malloc(sizeof(double) * 3 * (size_t)m);
+        double c[3];
+        orc_group_unwrap(cv->n_a, cv->a, n, x, box, u, c);
+        long double Sl[3][3] = {{0.0L}};
+        for (int64_t p = 0; p < m; ++p)
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) Sl[i][j] += (u[3 * p + i] - c[i]) * (u[3 * p + j] - c[j]);
+        double S[3][3], lam[3], V[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S[i][j] = (double)(Sl[i][j] / (long double)m);
+        orc_eig3(S, lam, V);
+        double q, g[3] = {0.0, 0.0, 0.0};
+        double T = lam[0] + lam[1] + lam[2], Q = lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2];
+        switch (cv->axis) {
+        case 0: case 1: case 2:
+            q = lam[cv->axis];
+            g[cv->axis] = 1.0;
+            break;
+        case 3:
+            q = lam[2] - 0.5 * (lam[0] + lam[1]);
+            g[0] = -0.5;
+            g[1] = -0.5;
+            g[2] = 1.0;
+            break;
+        case 4:
+            q = lam[1] - lam[0];
+            g[0] = -1.0;
+            g[1] = 1.0;
+            break;
+        case 5:
+            q = 1.5 * Q / (T * T) - 0.5;
+            for (int j = 0; j < 3; ++j) g[j] = 3.0 * (lam[j] * T - Q) / (T * T * T);
+            break;
+        default:
+            free(u);
+            return -1;
+        }
+        double sc = cv->scale != 0.0 ? cv->scale : 1.0;
+        for (int64_t p = 0; p < m; ++p) {
+            int64_t i = orc_group(cv->n_a, cv->a, n, p);
+            for (int j = 0; j < 3; ++j) {
+                double proj = 0.0;
+                for (int k = 0; k < 3; ++k) proj += V[k][j] * (u[3 * p + k] - c[k]);
+                for (int k = 0; k < 3; ++k) J[3 * i + k] += sc * g[j] * 2.0 / (double)m * proj * V[k][j];
+            }
+        }
+        free(u);
+        *xi = sc * q;
         return 0;
     }
     case ORC_CV_QPAIRS: {

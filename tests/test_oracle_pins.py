@@ -137,6 +137,14 @@ def _cases():
     yield "rg_subset", o.CV(o.CV_RG, a=[0, 3, 5, 6, 11]), xl, box
     yield "rg_intensive", o.CV(o.CV_RG, a=None, flags=o.CV_INTENSIVE), r.normal(size=(9, 3)), None
     yield "qpairs", o.CV(o.CV_QPAIRS, a=[0, 1, 2, 5, 7, 3], r0=1.5, nn=6, mm=12), xl, box
+    yield "distance_pbc", o.CV(o.CV_DISTANCE, a=[0, 3, 5], b=[9, 11]), xl, box
+    yield "distance_open", o.CV(o.CV_DISTANCE, a=[1], b=[2, 4, 7, 8]), r.normal(size=(10, 3)), None
+    yield "angle", o.CV(o.CV_ANGLE, a=[4, 0, 7]), r.normal(size=(9, 3)), None
+    yield "angle_pbc", o.CV(o.CV_ANGLE, a=[2, 5, 6]), xl, box
+    xg = r.normal(size=(11, 3)) * np.array([1.5, 1.0, 0.6])
+    for q, nm in enumerate(("l1", "l2", "l3", "asphericity", "acylindricity", "anisotropy")):
+        yield "gyration_" + nm, o.CV(o.CV_GYRATION, a=None, axis=q), xg, None
+    yield "gyration_pbc", o.CV(o.CV_GYRATION, a=[0, 3, 5, 6, 11, 12], axis=o.GY_ANISOTROPY), xl, box
 
 
 @pytest.mark.parametrize("name,cv,x,box", list(_cases()), ids=[c[0] for c in _cases()])
@@ -167,6 +175,53 @@ def test_cv_rotation_invariance_zero_net_torque(name, cv, x, box):
         q[:, 0] *= -1
     xi2, _ = o.cv_eval(cv, x @ q.T, box)
     assert xi2 == pytest.approx(xi, abs=1e-11)
+
+
+def test_distance_and_angle_closed_forms():
+    # centres (0,0,0) and (3,4,0): distance 5, whatever the group sizes
+    x = np.array([[1, 0, 0], [-1, 0, 0], [3, 4, 1], [3, 4, -1], [3, 4, 0.0]])
+    xi, J = o.cv_eval(o.CV(o.CV_DISTANCE, a=[0, 1], b=[2, 3, 4]), x)
+    assert xi == pytest.approx(5.0, abs=1e-14)
+    assert np.allclose(J[0], -np.array([0.6, 0.8, 0]) / 2) and np.allclose(J[4], np.array([0.6, 0.8, 0]) / 3)
+    # the centre difference uses the minimum image: groups 9 apart in a box of 10
+    xb = np.array([[0.5, 0, 0], [9.5, 0, 0.0]])
+    assert o.cv_eval(o.CV(o.CV_DISTANCE, a=[0], b=[1]), xb, [10.0, 10.0, 10.0])[0] == pytest.approx(1.0)
+    tri = np.array([[1.0, 0, 0], [0, 0, 0], [0.5, np.sqrt(3) / 2, 0]])
+    for pts, th in ((tri, np.pi / 3), (np.array([[1.0, 0, 0], [0, 0, 0], [0, 2.0, 0]]), np.pi / 2),
+                    (np.array([[1.0, 0, 0], [0, 0, 0], [-3.0, 0, 0]]), np.pi)):
+        assert o.cv_eval(o.CV(o.CV_ANGLE, a=[0, 1, 2]), pts)[0] == pytest.approx(th, abs=1e-14)
+    # unit-length arms at a right angle: moving either end towards the other closes the angle at rate 1
+    xi, J = o.cv_eval(o.CV(o.CV_ANGLE, a=[0, 1, 2]), np.array([[1.0, 0, 0], [0, 0, 0], [0, 1.0, 0]]))
+    assert np.allclose(J[0], [0, -1, 0]) and np.allclose(J[2], [-1, 0, 0]) and np.allclose(J[1], [1, 1, 0])
+
+
+def test_gyration_tensor_closed_forms():
+    """Rod of n atoms spaced a: l3 = a^2 (n^2-1)/12, l1 = l2 = 0, asphericity
+    l3, acylindricity 0, anisotropy 1.  Square of side a: l = (0, a^2/4,
+    a^2/4), asphericity a^2/8, acylindricity a^2/4, anisotropy 1/4.  Cube
+    corners: isotropic, asphericity = acylindricity = anisotropy = 0.  In
+    every case l1 + l2 + l3 = Rg^2."""
+    def q(x, k):
+        return o.cv_eval(o.CV(o.CV_GYRATION, a=None, axis=k), x)[0]
+
+    rot, _ = np.linalg.qr(synth.rng(8).normal(size=(3, 3)))
+    n, a = 7, 0.8
+    rod = (np.arange(n)[:, None] * a * np.array([[1.0, 0, 0]])) @ rot.T + 2.0
+    l3 = a * a * (n * n - 1) / 12
+    assert q(rod, 2) == pytest.approx(l3, rel=1e-12)
+    assert abs(q(rod, 0)) < 1e-13 and abs(q(rod, 1)) < 1e-13
+    assert q(rod, 3) == pytest.approx(l3, rel=1e-12) and abs(q(rod, 4)) < 1e-13
+    assert q(rod, 5) == pytest.approx(1.0, rel=1e-12)
+    sq = (np.array([[1, 1, 0], [1, -1, 0], [-1, 1, 0], [-1, -1, 0.0]]) * a / 2) @ rot.T
+    assert [q(sq, k) for k in range(3)] == pytest.approx([0.0, a * a / 4, a * a / 4], abs=1e-13)
+    assert q(sq, 3) == pytest.approx(a * a / 8, rel=1e-12) and q(sq, 4) == pytest.approx(a * a / 4, rel=1e-12)
+    assert q(sq, 5) == pytest.approx(0.25, rel=1e-12)
+    cube = np.array([[i, j, k] for i in (-1, 1) for j in (-1, 1) for k in (-1, 1)], float) @ rot.T
+    for k in (3, 4, 5):
+        assert abs(q(cube, k)) < 1e-12
+    x = synth.rng(9).normal(size=(13, 3))
+    rg = o.cv_eval(o.CV(o.CV_RG, a=None), x)[0]
+    assert sum(q(x, k) for k in range(3)) == pytest.approx(rg * rg, rel=1e-12)
 
 
 def test_dihedral_conventions():
