@@ -64,6 +64,7 @@ class _Sys(C.Structure):
         ("w0", C.c_double), ("gamma", C.c_double), ("stride", C.c_int64), ("hill_cap", C.c_int64),
         ("grid_bins", C.c_int64 * 3), ("grid_lo", C.c_double * 3), ("grid_hi", C.c_double * 3),
         ("bias_on", C.c_int64), ("bias_grid", C.c_int64),
+        ("bias_harm", C.c_int64), ("harm_kcv", C.c_double * 3), ("harm_centre", C.POINTER(C.c_double)),
     ]
 
 
@@ -72,7 +73,7 @@ class _State(C.Structure):
         ("x", C.POINTER(C.c_double)), ("v", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double)),
         ("hills", C.POINTER(C.c_double)), ("n_hills", C.c_int64), ("grid", C.POINTER(C.c_double)),
         ("step", C.c_int64), ("xi", C.POINTER(C.c_double)), ("V", C.POINTER(C.c_double)),
-        ("dV", C.POINTER(C.c_double)),
+        ("dV", C.POINTER(C.c_double)), ("xi_sum", C.POINTER(C.c_double)), ("n_samples", C.c_int64),
     ]
 
 
@@ -106,6 +107,7 @@ def lib():
         _lib.orc_bias_grid.argtypes = [C.POINTER(_Sys), dp, dp, dp, dp, dp, dp]
         _lib.orc_forces.argtypes = [C.POINTER(_Sys), C.POINTER(_State)]
         _lib.orc_run.argtypes = [C.POINTER(_Sys), C.POINTER(_State), i64]
+        _lib.orc_umbrella_integrate.argtypes = [i64, i64, dp, dp, dp, dp, dp, dp]
         _lib.orc_num_threads.restype = C.c_int
         _lib.orc_set_threads.argtypes = [C.c_int]
     return _lib
@@ -314,6 +316,8 @@ class System:
     grid_hi: tuple = (1.0, 1.0, 1.0)
     bias_on: bool = True
     bias_grid: bool = False
+    umb_k: tuple | None = None         # harmonic bias: spring constant per CV (None: metadynamics)
+    umb_centres: object = None         # [W][d] window centres
 
 
 class Sim:
@@ -360,6 +364,16 @@ class Sim:
         s.grid_hi = (C.c_double * 3)(*(list(sys.grid_hi) + [1.0] * (3 - len(sys.grid_hi))))
         s.bias_on = 1 if sys.bias_on else 0
         s.bias_grid = 1 if sys.bias_grid else 0
+        self.xi_sum = np.zeros((W, 3))
+        self.n_samples = 0
+        if sys.umb_k is not None:
+            d = len(sys.cvs)
+            s.bias_harm = 1
+            s.harm_kcv = (C.c_double * 3)(*(list(sys.umb_k) + [0.0] * (3 - len(sys.umb_k))))
+            cen = np.zeros((W, 3))
+            cen[:, :d] = np.asarray(sys.umb_centres, dtype=np.float64).reshape(W, d)
+            self._centres = np.ascontiguousarray(cen)
+            s.harm_centre = _dp(self._centres)
         self._sys = s
 
     def _state(self) -> _State:
@@ -369,11 +383,25 @@ class Sim:
         st.grid = _dp(self.grid)
         st.step = self.step
         st.xi, st.V, st.dV = _dp(self.xi), _dp(self.V), _dp(self.dV)
+        st.xi_sum, st.n_samples = _dp(self.xi_sum), self.n_samples
         return st
 
     def _pull(self, st: _State):
         self.n_hills = st.n_hills
         self.step = st.step
+        self.n_samples = st.n_samples
+
+    def umbrella(self):
+        """Umbrella integration over the windows' statistics (Sec. 2.1.2):
+        (mean xi [W][d], mean force dA/dxi [W][d], A along the path [W])."""
+        d = len(self.sys.cvs)
+        W = len(self._wn)
+        mean = np.ascontiguousarray(self.xi_sum / max(self.n_samples, 1))
+        per = _f64([c.period for c in self.sys.cvs] + [0.0] * (3 - d))
+        k = _f64(list(self.sys.umb_k) + [0.0] * (3 - d))
+        g, A = np.zeros((W, 3)), np.zeros(W)
+        lib().orc_umbrella_integrate(W, d, _dp(mean), _dp(self._centres), _dp(k), _dp(per), _dp(g), _dp(A))
+        return mean[:, :d], g[:, :d], A
 
     def forces(self):
         st = self._state()

@@ -834,6 +834,9 @@ typedef struct {
     double grid_lo[3], grid_hi[3];
     int64_t bias_on;
     int64_t bias_grid;        /* 1: the bias is read from the grid (orc_grid_interp), not summed over hills */
+    int64_t bias_harm;        /* 1: harmonic bias about per-walker centres (no hills deposited) */
+    double harm_kcv[3];       /* spring constant per CV */
+    const double* harm_centre; /* [W][3] window centres */
 } orc_sys;
 
 typedef struct {
@@ -847,6 +850,8 @@ typedef struct {
     double* xi;     /* [W][3] CVs at x */
     double* V;      /* [W] bias at x (hills before any deposit at this step) */
     double* dV;     /* [W][3] */
+    double* xi_sum; /* [W][3] sum of xi over the steps run (harmonic bias) */
+    int64_t n_samples;
 } orc_state;
 
 static int64_t orc_total_atoms(const orc_sys* s)
@@ -910,7 +915,19 @@ static int orc_bias_from(const orc_sys* s, const double* x, const double* hills,
                 free(J);
                 return -1;
             }
-        if (grid) {
+        if (s->bias_harm) {
+            /* Harmonic biasing (Sec. 2.1.1): V = k/2 (xi - xi0)^2 per CV,
+             * summed; dV/dxi_c = k_c (xi_c - xi0_c), the difference by the
+             * minimum image on periodic CVs.  Each walker has its own centre
+             * (one umbrella window per walker, Sec. 2.1.2). */
+            vw = 0.0;
+            for (int64_t c = 0; c < d; ++c) {
+                double D = xw[c] - s->harm_centre[3 * w + c];
+                if (period[c] > 0.0) D -= period[c] * nearbyint(D / period[c]);
+                vw += 0.5 * s->harm_kcv[c] * D * D;
+                gw[c] = s->harm_kcv[c] * D;
+            }
+        } else if (grid) {
             int64_t bins[3] = {s->grid_bins[0], s->grid_bins[1], s->grid_bins[2]};
             if (orc_grid_interp(d, bins, s->grid_lo, s->grid_hi, period, grid, 1, xw, &vw, gw) != 0) {
                 free(J);
@@ -991,6 +1008,13 @@ int orc_run(const orc_sys* s, orc_state* st, int64_t nsteps)
         for (int64_t i = 0; i < N; ++i)
             for (int64_t k = 0; k < s->dims; ++k) st->v[3 * i + k] += half * st->f[3 * i + k] / s->mass;
         st->step = t + 1;
+        if (s->bias_on && s->bias_harm) {
+            /* window statistics: xi at the end of every step */
+            for (int64_t w = 0; w < s->n_walkers; ++w)
+                for (int c = 0; c < 3; ++c) st->xi_sum[3 * w + c] += st->xi[3 * w + c];
+            st->n_samples += 1;
+            continue; /* harmonic windows deposit no hills */
+        }
         if (s->bias_on && s->stride > 0 && (t + 1) % s->stride == 0) {
             if (st->n_hills + s->n_walkers > s->hill_cap) {
                 rc = -3;
@@ -1009,6 +1033,36 @@ int orc_run(const orc_sys* s, orc_state* st, int64_t nsteps)
         }
     }
     return rc;
+}
+
+/* Umbrella integration along a path of windows (Sec. 2.1.2; Kaestner &
+ * Thiel's estimate in its lowest order): the mean force of window i is
+ * dA/dxi at xi_bar_i = -k (xi_bar_i - xi0_i) (minimum image on periodic
+ * CVs), and A along the path of the xi_bar_i, in window order, is the
+ * trapezoidal integral A_0 = 0, A_{i+1} = A_i + (g_i + g_{i+1})/2 .
+ * (xi_bar_{i+1} - xi_bar_i).  mean_xi, centre and g are [W][3]. */
+void orc_umbrella_integrate(int64_t W, int64_t d, const double* mean_xi, const double* centre, const double* k,
+                            const double* period, double* g, double* A)
+{
+    for (int64_t w = 0; w < W; ++w)
+        for (int64_t c = 0; c < 3; ++c) {
+            double D = 0.0;
+            if (c < d) {
+                D = mean_xi[3 * w + c] - centre[3 * w + c];
+                if (period && period[c] > 0.0) D -= period[c] * nearbyint(D / period[c]);
+            }
+            g[3 * w + c] = c < d ? -k[c] * D : 0.0;
+        }
+    A[0] = 0.0;
+    for (int64_t w = 0; w + 1 < W; ++w) {
+        double dA = 0.0;
+        for (int64_t c = 0; c < d; ++c) {
+            double step = mean_xi[3 * (w + 1) + c] - mean_xi[3 * w + c];
+            if (period && period[c] > 0.0) step -= period[c] * nearbyint(step / period[c]);
+            dA += 0.5 * (g[3 * w + c] + g[3 * (w + 1) + c]) * step;
+        }
+        A[w + 1] = A[w] + dA;
+    }
 }
 
 int orc_num_threads(void)
