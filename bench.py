@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-micro", action="store_true")
     ap.add_argument("--no-walkers", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-grid-bias", action="store_true")
     ap.add_argument("--case", choices=["hills", "walkers", "mlp"], default=None,
                     help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
     return ap.parse_args()
@@ -545,9 +546,111 @@ def run_ours(args, rank, world):
     micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
     walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
     sur = None if args.no_surrogate else surrogate_bench(wt, torch, dev, flush, args.steps)
-    return dict(hills_plan=hills_plan, walkers=walkers, surrogate=sur, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    gridb = None if args.no_grid_bias else grid_bias_bench(wt, torch, dev, flush, args.steps, rank)
+    return dict(hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
+
+
+GRID_BINS = 256  # cells per CV of the grid-read bias figure (dx = 12 sigma / 256)
+
+
+def grid_bias_bench(wt, torch, dev, flush, steps, rank=0):
+    """The headline 4096-atom workload with the bias read from a 256x256 FP64
+    grid (+-6 sigma around the initial CVs) instead of summed over the 1e5
+    hills: steps/s of both sources on one handle (L2 flushed between steps),
+    the read error against the exact sum at the walker and at 4096 sampled
+    points of the hills' range, and the bias alone at those 4096 points."""
+    import synth
+
+    stream = torch.cuda.current_stream()
+    x, v, L, tag, rg = workload_inputs(seed=rank)
+    probe = wt.Wtmd(precision="f32", sigma=SIGMA, walker_sizes=[N_ATOMS], box=(L, L, L), engine="lj")
+    probe.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+    probe.cv_define(wt.CV_RG, a=rg)
+    pos = wt.particles(x, torch.float32)
+    _, xi0, _ = probe.bias_eval(pos)
+    probe.close()
+    xi0 = xi0[0].double().cpu().numpy()
+    sig = np.asarray(SIGMA)
+    lo, hi = list(xi0 - 6 * sig), list(xi0 + 6 * sig)
+    m = wt.Wtmd(precision="f32", sigma=SIGMA, w0=1.0, gamma=8.0, kT=1.0, stride=100, capacity=H_PRE + 100000,
+                seed=rank, engine="lj", walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005, friction=1.0,
+                grid=((GRID_BINS, GRID_BINS), lo, hi))
+    m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+    m.cv_define(wt.CV_RG, a=rg)
+    hills = hills_around(xi0, seed=100 + rank)
+    m.hills_load(hills)
+    m.hills_tune(1)
+    vel = wt.particles(v, torch.float32)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+
+    def timed(K):
+        m.step_n(3, check=True)  # capture for the current source
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for i in range(K):
+            flush.fill_(float(i))
+            torch.cuda._sleep(SLACK_CYCLES)
+            ev[i][0].record(stream)
+            m.step_n(1, check=False)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        return K / (sum(a.elapsed_time(b) for a, b in ev) * 1e-3)
+
+    out = {"workload": "the headline 4096-atom LJ workload and its 1e5 hills; FP64 bias grid "
+                       f"{GRID_BINS}x{GRID_BINS} over +-6 sigma of the initial CVs (cell = {12 / GRID_BINS:.3f} sigma)"}
+    res = {}
+    for name, src in (("hills", wt.BIAS_HILLS), ("grid", wt.BIAS_GRID)):
+        m.bias_source(src)
+        res[name] = timed(steps)
+    out["steps_per_s_hills"], out["steps_per_s_grid"] = res["hills"], res["grid"]
+    out["step_speedup"] = res["grid"] / res["hills"]
+    # read error at the starting configuration (inside the hills; the run
+    # above has since pushed the walker out of the filled region)
+    pos0 = wt.particles(x, torch.float32)
+    m.bias_source(wt.BIAS_HILLS)
+    Vh, _, dVh = m.bias_eval(pos0)
+    m.bias_source(wt.BIAS_GRID)
+    Vg, _, dVg = m.bias_eval(pos0)
+    torch.cuda.synchronize()
+    out["walker_V_kT"] = float(Vh[0])  # kT = 1: 1e5 hills pile up to thousands of kT
+    out["walker_err_kT"] = abs(float(Vg[0]) - float(Vh[0]))
+    out["walker_rel_err"] = out["walker_err_kT"] / abs(float(Vh[0]))
+    out["walker_grad_rel_err"] = float(torch.linalg.norm((dVg - dVh).double()) / torch.linalg.norm(dVh.double()))
+    # 4096 points over the hills' range: error and time of each source
+    P = 4096
+    pts = torch.tensor(synth.uniform_points(P, list(xi0 - 3 * sig), list(xi0 + 3 * sig), seed=77), dtype=torch.float32,
+                       device=dev)
+    Va, dVa = torch.empty(P, device=dev), torch.empty(P, 2, device=dev)
+    Vb, dVb = torch.empty(P, device=dev), torch.empty(P, 2, device=dev)
+    m.hills_tune(P)
+    ms = {}
+    for name, fn, V, dV in (("hills", m.hills_eval_into, Va, dVa), ("grid", m.grid_eval_into, Vb, dVb)):
+        for _ in range(3):
+            fn(pts, V, dV)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for a, b in evs:
+            flush.fill_(1.0)
+            torch.cuda._sleep(SLACK_CYCLES)
+            a.record(stream)
+            fn(pts, V, dV)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms[name] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    err = (Vb.double() - Va.double()).abs()
+    gerr = torch.linalg.norm((dVb - dVa).double(), dim=1) / torch.linalg.norm(dVa.double(), dim=1).clamp_min(1e-30)
+    out["points_4096"] = {"hills_ms": ms["hills"], "grid_ms": ms["grid"],
+                          "hills_bias_evals_per_s": P / (ms["hills"] * 1e-3),
+                          "grid_bias_evals_per_s": P / (ms["grid"] * 1e-3), "speedup": ms["hills"] / ms["grid"],
+                          "rms_err_kT": float(err.pow(2).mean().sqrt()), "max_err_kT": float(err.max()),
+                          "max_rel_err": float((err / Va.double().abs().clamp_min(1e-30)).max()),
+                          "mean_V_kT": float(Va.double().mean()),
+                          "median_grad_rel_err": float(gerr.median())}
+    m.close()
+    return out
 
 
 def hills_micro(wt, torch, dev, flush):
@@ -729,6 +832,7 @@ def main():
         "hills_sum_1e6": r["micro"],
         "walkers_256_clusters": r["walkers"],
         "surrogate_1e6_hills": r["surrogate"],
+        "grid_bias_1e5_hills": r["grid_bias"],
     }
     if not args.no_cpu_baseline and world == 1:
         n, times, cores = cpu_baseline_oracle(seconds=15.0)

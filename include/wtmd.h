@@ -77,6 +77,22 @@ extern "C" {
 #define WTMD_CV_COORDINATION 3 /* sum_{i in A} sum_{j in B, j != i} 1/(1+(r_ij/r0)^n) (rational switch, m = 2n) */
 #define WTMD_CV_RG 4           /* radius of gyration of a group (Sec. 2.2, RadiusofGyration) */
 #define WTMD_CV_QPAIRS 5       /* mean switching function over a fixed list of pairs */
+#define WTMD_CV_DISTANCE 6     /* distance between the equal-mass centres of groups A and B (Sec. 2.2,
+                                * TwoPointCV Distance); each group unwrapped by the minimum image
+                                * relative to its first member, the centre difference by the minimum
+                                * image; A and B non-empty and disjoint */
+#define WTMD_CV_ANGLE 7        /* angle at a[1] between a[0] - a[1] and a[2] - a[1], in [0, pi]
+                                * (Sec. 2.2, ThreePointCV Angle); gradient 0 at 0 and pi */
+#define WTMD_CV_GYRATION 8     /* gyration tensor of group A (all atoms if n_a = -1), equal masses,
+                                * unwrapped as for RG; eigenvalues l1 <= l2 <= l3; `axis` selects
+                                * (Sec. 2.2, PrincipalMoment, Asphericity, Acylindricity,
+                                * ShapeAnisotropy): */
+#define WTMD_GY_L1 0           /*   smallest principal moment */
+#define WTMD_GY_L2 1
+#define WTMD_GY_L3 2           /*   largest */
+#define WTMD_GY_ASPHERICITY 3  /*   l3 - (l1 + l2)/2 */
+#define WTMD_GY_ACYLINDRICITY 4 /*  l2 - l1 */
+#define WTMD_GY_ANISOTROPY 5   /*   3/2 (l1^2 + l2^2 + l3^2)/(l1 + l2 + l3)^2 - 1/2 */
 
 #define WTMD_CV_INTENSIVE 1 /* RG only: divide by (group size)^(1/3) */
 
@@ -107,11 +123,11 @@ typedef struct wtmd_config {
 /* ---- one collective variable; indices are walker-local and host-side ---- */
 typedef struct wtmd_cv_desc {
     int32_t kind;       /* WTMD_CV_* */
-    int32_t axis;       /* COMPONENT: 0, 1 or 2 */
+    int32_t axis;       /* COMPONENT: 0, 1 or 2; GYRATION: WTMD_GY_* */
     int64_t n_a;        /* group A size; -1 = all atoms of the walker (COORDINATION, RG) */
-    const int32_t* a;   /* COMPONENT: 1 index; DIHEDRAL: 4; COORDINATION/RG: group A;
+    const int32_t* a;   /* COMPONENT: 1 index; ANGLE: 3; DIHEDRAL: 4; COORDINATION/RG/GYRATION/DISTANCE: group A;
                            QPAIRS: 2*npairs indices (i0, j0, i1, j1, ...) */
-    int64_t n_b;        /* COORDINATION partner group B size; -1 = all atoms */
+    int64_t n_b;        /* COORDINATION partner group B size (-1 = all atoms); DISTANCE group B */
     const int32_t* b;
     double r0;          /* switching distance */
     int32_t nn, mm;     /* switching exponents; mm must equal 2*nn, nn even, 2..16 */
@@ -139,7 +155,8 @@ int wtmd_set_stream(wtmd_t* h, void* stream);
 
 /* Define the next CV (ids 0..n_cv-1 in call order).  Index lists are copied
  * to the device.  Errors: WTMD_EINVAL (kind, index out of the walker, wrong
- * count, duplicate atoms, mm != 2 nn, more than n_cv CVs). */
+ * count, duplicate atoms, overlapping DISTANCE groups, GYRATION quantity
+ * outside 0..5, mm != 2 nn, more than n_cv CVs). */
 int cv_define(wtmd_t* h, const wtmd_cv_desc* desc, int32_t* cv_id);
 
 /* Bind the engine's particle arrays (device, [n_atoms][4] Real).  n_atoms
@@ -189,6 +206,70 @@ int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out);
  * Errors: WTMD_EINVAL (no grid, n_out too small). */
 int fes_grid(wtmd_t* h, double* out, int64_t n_out);
 
+/* ---- bias read from the grid ----------------------------------------------
+ * The paper offers to keep the bias on a pre-defined grid to trade accuracy
+ * for speed (Sec. 2.1.5); it stores the potential only.  Forces are taken
+ * from it here as follows: the FP64 grid holds V at the cell centres
+ * lo_i + (k + 1/2)(hi_i - lo_i)/bins_i; the gradient at a centre along axis
+ * i is the central difference of its two neighbours (one-sided at the ends
+ * of a non-periodic axis; a periodic axis wraps, and its grid must span
+ * exactly one period); V and dV/dxi at a point are the multilinear
+ * interpolations of the 2^d surrounding centres' values.  A non-periodic
+ * coordinate outside the outermost centres is clamped to them (the edge
+ * values hold).  The cost per point is fixed (2^d (2d + 1) grid reads)
+ * instead of one Gaussian per hill; the error falls with the square of the
+ * cell size relative to sigma. */
+#define WTMD_BIAS_HILLS 0    /* exact sum over the hill list (default) */
+#define WTMD_BIAS_GRID 1     /* read from the grid */
+#define WTMD_BIAS_HARMONIC 2 /* harmonic windows (wtmd_harmonic) */
+
+/* The grid-read bias at P points: xi (device [P][n_cv] Real) ->
+ * V_out [P] Real, dV_out [P][n_cv] Real (device; either may be NULL).
+ * Computed in FP64, rounded to Real.  Errors: WTMD_EINVAL (no grid, an axis
+ * with fewer than 2 cells, bad sizes). */
+int wtmd_grid_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out);
+
+/* Select where step_n and bias_eval take V and dV/dxi from: WTMD_BIAS_HILLS,
+ * WTMD_BIAS_GRID, or WTMD_BIAS_HARMONIC (after wtmd_harmonic).  With the grid, the well-tempered height of each new
+ * hill also uses the grid's V, and hills are still appended to the list and
+ * added to the grid.  Errors: WTMD_EINVAL (unknown source; for the grid: no
+ * grid, an axis with fewer than 2 cells, a periodic CV whose grid does not
+ * span one period, CVs not all defined, the surrogate on, or the persistent
+ * walker step on).  Drops captured step graphs. */
+int wtmd_bias_source(wtmd_t* h, int32_t source);
+
+/* ---- harmonic bias and umbrella windows ------------------------------------
+ * Harmonic biasing adds k/2 (xi - xi0)^2 to the Hamiltonian (Sec. 2.1.1);
+ * umbrella sampling runs one such biased simulation per point of a path and
+ * umbrella integration turns their statistics into a free-energy profile
+ * (Sec. 2.1.2).  Here each walker is one window: V = sum_c k_c/2 (xi_c -
+ * xi0_{w,c})^2, dV/dxi_c = k_c (xi_c - xi0_{w,c}) (minimum image on
+ * periodic CVs), evaluated on the device in FP64 and rounded to Real; no
+ * hills are deposited while it is on.  Every step adds each walker's CVs to
+ * FP64 window sums on the device (bias_eval does not). */
+
+/* Set the spring constants k (host [n_cv], > 0) and the window centres
+ * (host [W][n_cv]), clear the window statistics and make the harmonic bias
+ * the bias source.  Drops captured step graphs.  Errors: WTMD_EINVAL (CVs
+ * not all defined, k <= 0, non-finite centres, surrogate or persistent
+ * walker step on). */
+int wtmd_harmonic(wtmd_t* h, const double* k, const double* centres);
+
+/* Mean CVs of every window over the steps run since the last reset: mean_out
+ * (host [W][n_cv], may be NULL), *n_samples (may be NULL) = steps counted;
+ * reset != 0 clears the sums afterwards.  Synchronizes.  Errors: WTMD_EINVAL
+ * (no windows set). */
+int wtmd_umbrella_stats(wtmd_t* h, double* mean_out, int64_t* n_samples, int32_t reset);
+
+/* Umbrella integration (Sec. 2.1.2) in its lowest order: the mean force of
+ * window w is dA/dxi at its mean CV xi_bar_w, -k (xi_bar_w - xi0_w)
+ * (minimum image on periodic CVs) -> mean_force_out (host [W][n_cv], may be
+ * NULL); A along the path of the xi_bar_w in walker order is the
+ * trapezoidal integral A_0 = 0, A_{w+1} = A_w + (g_w + g_{w+1})/2 .
+ * (xi_bar_{w+1} - xi_bar_w) -> A_out (host [W], may be NULL).  Synchronizes.
+ * Errors: WTMD_EINVAL (no windows, no samples). */
+int wtmd_umbrella_integrate(wtmd_t* h, double* mean_force_out, double* A_out);
+
 /* Replace the hill list by `count` hills from host memory [count][4] double
  * (s0, s1, s2, w); the grid is rebuilt from them.  Errors: WTMD_EINVAL
  * (count > capacity, w <= 0 or non-finite). */
@@ -200,6 +281,32 @@ int wtmd_hills_read(wtmd_t* h, double* hills_host, int64_t capacity_out, int64_t
 
 /* Read the step counter and the hill count (synchronizes the stream). */
 int wtmd_counters(wtmd_t* h, int64_t* step, int64_t* n_hills);
+
+/* ---- checkpoint / restart --------------------------------------------------
+ * The paper lists restarts as a capability still to be added to PySAGES
+ * (Conclusion).  A checkpoint here is a host byte blob holding the
+ * raw state a step reads: hill count, step counter, both hill layouts, the
+ * FP64 grid, and the bound positions, velocities and forces.  The thermostat
+ * noise is keyed by (seed, step, particle), so loading a checkpoint into a
+ * handle made with the same configuration and CVs resumes the run bitwise.
+ * The surrogate's network is not included (refused while it is on; its
+ * weights are saved with wtmd_mlp_params), nor are umbrella-window sums.  The blob is in the byte order of
+ * the machine that wrote it. */
+
+/* Bytes needed by wtmd_checkpoint_save now (depends on the hill count).
+ * Errors: WTMD_EINVAL (particle arrays not bound, surrogate on). */
+int wtmd_checkpoint_size(wtmd_t* h, int64_t* bytes);
+
+/* Write the checkpoint into host memory out[cap_bytes].  Synchronizes.
+ * Errors: WTMD_EINVAL (cap_bytes too small, arrays not bound, surrogate on). */
+int wtmd_checkpoint_save(wtmd_t* h, void* out, int64_t cap_bytes);
+
+/* Restore a checkpoint (host memory in[n_bytes]) into this handle and its
+ * bound arrays; the next step rebuilds the neighbour lists.  Synchronizes.
+ * Errors: WTMD_EINVAL (not a checkpoint, truncated, or written by a handle
+ * with another precision, CV count, walker count, atom count, hill capacity
+ * or grid size; arrays not bound; surrogate on). */
+int wtmd_checkpoint_load(wtmd_t* h, const void* in, int64_t n_bytes);
 
 /* Copy the FP64 bias grid (device) to host memory [n_out] double. */
 int wtmd_grid_read(wtmd_t* h, double* out_host, int64_t n_out);

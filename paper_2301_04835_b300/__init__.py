@@ -28,6 +28,8 @@ OK, EINVAL, ENOMEM, ECAPACITY, ENUMERIC, ETIMEOUT, ECUDA, ECELL = 0, -1, -2, -3,
 F32, F64 = 0, 1
 ENGINE_NONE, ENGINE_MB, ENGINE_LJ, ENGINE_CHAIN = 0, 1, 2, 3
 CV_COMPONENT, CV_DIHEDRAL, CV_COORDINATION, CV_RG, CV_QPAIRS = 1, 2, 3, 4, 5
+CV_DISTANCE, CV_ANGLE, CV_GYRATION = 6, 7, 8
+GY_L1, GY_L2, GY_L3, GY_ASPHERICITY, GY_ACYLINDRICITY, GY_ANISOTROPY = 0, 1, 2, 3, 4, 5
 CV_INTENSIVE = 1
 ENGINE_WELLS3 = 5
 _ENGINES = {"none": ENGINE_NONE, "mb": ENGINE_MB, "lj": ENGINE_LJ, "chain": ENGINE_CHAIN, "wells3": ENGINE_WELLS3}
@@ -67,7 +69,11 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_counters", "wtmd_grid_read", "wtmd_philox", "wtmd_profile_step", "wtmd_probe_peak",
            "wtmd_hills_eval_static", "wtmd_cv_forward", "wtmd_cv_adjoint", "wtmd_walkers_persistent",
            "wtmd_autotune", "wtmd_surrogate", "wtmd_surrogate_config", "wtmd_surrogate_fit", "wtmd_surrogate_status",
-           "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune"]
+           "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune",
+           "wtmd_grid_eval", "wtmd_bias_source", "wtmd_checkpoint_size", "wtmd_checkpoint_save",
+           "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate"]
+
+BIAS_HILLS, BIAS_GRID, BIAS_HARMONIC = 0, 1, 2
 
 MLP_PARAMS = 4481
 
@@ -115,6 +121,14 @@ def lib() -> C.CDLL:
     L.wtmd_mlp_grad.argtypes = [vp, vp, vp, vp, i64, C.c_double, vp]
     L.wtmd_mlp_train.argtypes = [vp, vp, vp, vp, i64, i64, i64, C.c_double, C.c_double, vp]
     L.wtmd_hills_tune.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(C.c_double)]
+    L.wtmd_grid_eval.argtypes = [vp, vp, i64, vp, vp]
+    L.wtmd_bias_source.argtypes = [vp, i32]
+    L.wtmd_checkpoint_size.argtypes = [vp, C.POINTER(i64)]
+    L.wtmd_checkpoint_save.argtypes = [vp, vp, i64]
+    L.wtmd_checkpoint_load.argtypes = [vp, vp, i64]
+    L.wtmd_harmonic.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wtmd_umbrella_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), i32]
+    L.wtmd_umbrella_integrate.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wtmd_cv_forward.argtypes = [vp, vp, vp]
     L.wtmd_cv_adjoint.argtypes = [vp, vp, vp]
     L.wtmd_hills_eval_static.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp, i64, vp, i64, vp,
@@ -405,6 +419,67 @@ class Wtmd:
         self._err(lib().hills_eval(self.h, self._check_tensor(xi, (P, self.d)), P, C.c_void_p(V.data_ptr()),
                                    C.c_void_p(dV.data_ptr())), "hills_eval")
         return V, dV
+
+    def grid_eval(self, xi):
+        """V and dV/dxi at points xi [P][n_cv] read from the FP64 bias grid
+        (central-difference node gradients, multilinear interpolation)."""
+        torch = _torch()
+        self._stream()
+        P = xi.shape[0]
+        V = torch.empty(P, dtype=self.dtype, device=xi.device)
+        dV = torch.empty(P, self.d, dtype=self.dtype, device=xi.device)
+        self._err(lib().wtmd_grid_eval(self.h, self._check_tensor(xi, (P, self.d)), P, C.c_void_p(V.data_ptr()),
+                                       C.c_void_p(dV.data_ptr())), "wtmd_grid_eval")
+        return V, dV
+
+    def grid_eval_into(self, xi, V, dV):
+        """grid_eval into preallocated outputs (no allocation; for timing)."""
+        self._err(lib().wtmd_grid_eval(self.h, C.c_void_p(xi.data_ptr()), xi.shape[0], C.c_void_p(V.data_ptr()),
+                                       C.c_void_p(dV.data_ptr())), "wtmd_grid_eval")
+
+    def bias_source(self, source: int):
+        """Where step_n and bias_eval take the bias from: BIAS_HILLS (exact
+        sum) or BIAS_GRID (read from the grid)."""
+        self._err(lib().wtmd_bias_source(self.h, int(source)), "wtmd_bias_source")
+
+    def harmonic(self, k, centres):
+        """Harmonic windows: spring constants k [n_cv], centres [W][n_cv]."""
+        kk = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(self.d))
+        cc = np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(self.W, self.d))
+        dp = C.POINTER(C.c_double)
+        self._err(lib().wtmd_harmonic(self.h, kk.ctypes.data_as(dp), cc.ctypes.data_as(dp)), "wtmd_harmonic")
+
+    def umbrella_stats(self, reset: bool = False):
+        """(mean CVs [W][n_cv], samples) of the windows."""
+        self._stream()
+        mean = np.zeros((self.W, self.d))
+        n = C.c_int64()
+        self._err(lib().wtmd_umbrella_stats(self.h, mean.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n),
+                                            1 if reset else 0), "wtmd_umbrella_stats")
+        return mean, n.value
+
+    def umbrella_integrate(self):
+        """(mean forces [W][n_cv], A along the window path [W])."""
+        self._stream()
+        g, A = np.zeros((self.W, self.d)), np.zeros(self.W)
+        dp = C.POINTER(C.c_double)
+        self._err(lib().wtmd_umbrella_integrate(self.h, g.ctypes.data_as(dp), A.ctypes.data_as(dp)),
+                  "wtmd_umbrella_integrate")
+        return g, A
+
+    def checkpoint(self) -> bytes:
+        """The run's state as bytes (hills, grid, counters, bound particle
+        arrays); load it with restore() to resume bitwise."""
+        n = C.c_int64()
+        self._err(lib().wtmd_checkpoint_size(self.h, C.byref(n)), "wtmd_checkpoint_size")
+        buf = C.create_string_buffer(n.value)
+        self._err(lib().wtmd_checkpoint_save(self.h, buf, n.value), "wtmd_checkpoint_save")
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Load a checkpoint() of a handle with the same configuration."""
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._err(lib().wtmd_checkpoint_load(self.h, buf, len(blob)), "wtmd_checkpoint_load")
 
     def hills_eval_into(self, xi, V, dV):
         """hills_eval into preallocated outputs (no allocation; for timing)."""

@@ -60,9 +60,12 @@ void drop_step_graphs(wtmd_t* h) { drop_graphs(h); }
 }  // namespace wtmd
 
 // Bias at the walkers' CVs: the exact hills sum, over [k0, count) plus the
-// network's part when the surrogate is active.
+// network's part when the surrogate is active, or the bias read from the grid
+// (WTMD_BIAS_GRID).
 static int launch_bias_sum(wtmd_t* h)
 {
+    if (h->bias_harm) return launch_harmonic(h, h->in_step);
+    if (h->bias_grid) return launch_grid_bias(h, h->xi, true, 4, h->W, h->V, h->dV, 4, true);
     // the preceding kernel on this stream computes CVs (it writes xi only)
     int rc = launch_hills_range(h, h->xi, true, 4, h->W, h->V, h->dV, 4, surrogate_k0(h), h->count,
                                 surrogate_tail_bound(h), true);
@@ -97,6 +100,7 @@ extern "C" int wtmd_destroy(wtmd_t* h)
     for (int i = 0; i < h->ncv; ++i) free_cv(h->cv[i]);
     void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status, h->ticket,
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
+                    h->harm_centre, h->harm_sum,
                     h->cell_atoms, h->nl_nbr, h->nl_cnt, h->nl_xref, h->nl_ctl};
     for (void* p : ptrs) cudaFree(p);
     surrogate_free(h->sur);
@@ -326,13 +330,33 @@ extern "C" int cv_define(wtmd_t* h, const wtmd_cv_desc* d, int32_t* cv_id)
         for (int k = 0; k < 4; ++k) c.hidx[k] = d->a[k];
         c.n_a = 4;
         break;
+    case WTMD_CV_ANGLE:
+        if (d->n_a != 3 || !valid_list(d->a, 3, minw, true)) FAIL(h, WTMD_EINVAL, "ANGLE needs 3 distinct atoms");
+        for (int k = 0; k < 3; ++k) c.hidx[k] = d->a[k];
+        c.n_a = 3;
+        break;
+    case WTMD_CV_DISTANCE: {
+        if (d->n_a < 1 || d->n_b < 1 || !valid_list(d->a, d->n_a, minw, true) || !valid_list(d->b, d->n_b, minw, true))
+            FAIL(h, WTMD_EINVAL, "DISTANCE needs two non-empty groups of distinct atoms");
+        std::vector<char> inA(minw, 0);
+        for (int64_t p = 0; p < d->n_a; ++p) inA[d->a[p]] = 1;
+        for (int64_t p = 0; p < d->n_b; ++p)
+            if (inA[d->b[p]]) FAIL(h, WTMD_EINVAL, "DISTANCE groups must be disjoint");
+        c.n_a = (int)d->n_a;
+        c.n_b = (int)d->n_b;
+        if (upload(d->a, d->n_a, &c.a) || upload(d->b, d->n_b, &c.b)) FAIL(h, WTMD_ENOMEM, "DISTANCE groups");
+        break;
+    }
+    case WTMD_CV_GYRATION:
+        if (d->axis < 0 || d->axis > 5) FAIL(h, WTMD_EINVAL, "GYRATION quantity (axis) must be 0..5");
+        [[fallthrough]];
     case WTMD_CV_RG:
         c.n_a = (int)d->n_a;
         if (d->n_a == -1) {
-            if (minw < 2) FAIL(h, WTMD_EINVAL, "RG needs at least 2 atoms");
+            if (minw < 2) FAIL(h, WTMD_EINVAL, "RG / GYRATION needs at least 2 atoms");
         } else {
-            if (d->n_a < 2 || !valid_list(d->a, d->n_a, minw, true)) FAIL(h, WTMD_EINVAL, "bad RG group");
-            if (upload(d->a, d->n_a, &c.a)) FAIL(h, WTMD_ENOMEM, "RG group");
+            if (d->n_a < 2 || !valid_list(d->a, d->n_a, minw, true)) FAIL(h, WTMD_EINVAL, "bad RG / GYRATION group");
+            if (upload(d->a, d->n_a, &c.a)) FAIL(h, WTMD_ENOMEM, "RG / GYRATION group");
         }
         break;
     case WTMD_CV_COORDINATION:
@@ -487,8 +511,10 @@ static int enqueue_step(wtmd_t* h)
     }
     if ((rc = launch_baoab_first(h, jmask, xmask))) return rc;
     h->jz_pre = true;
+    h->in_step = true;
     rc = enqueue_engine_and_bias(h);
     h->jz_pre = false;
+    h->in_step = false;
     if (rc) return rc;
     return launch_scatter_deposit(h);
 }
@@ -648,6 +674,136 @@ extern "C" int hills_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, voi
     return launch_hills(h, xi, h->prec == WTMD_F64, h->d, P, V_out, dV_out, h->d);
 }
 
+extern "C" int wtmd_grid_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_out)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!h->grid) FAIL(h, WTMD_EINVAL, "the handle has no grid");
+    for (int i = 0; i < h->d; ++i)
+        if (h->cfg.grid_bins[i] < 2) FAIL(h, WTMD_EINVAL, "every grid axis needs at least 2 cells");
+    if (P < 0 || (P > 0 && !xi)) FAIL(h, WTMD_EINVAL, "bad points");
+    if (P > (1ll << 40)) FAIL(h, WTMD_EINVAL, "too many points");
+    if (h->ncv > 0 && h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs (or none) first");
+    return launch_grid_bias(h, xi, h->prec == WTMD_F64, h->d, P, V_out, dV_out, h->d, false);
+}
+
+extern "C" int wtmd_bias_source(wtmd_t* h, int32_t source)
+{
+    if (!h) return WTMD_EINVAL;
+    if (source != WTMD_BIAS_HILLS && source != WTMD_BIAS_GRID && source != WTMD_BIAS_HARMONIC)
+        FAIL(h, WTMD_EINVAL, "unknown bias source");
+    if (source == WTMD_BIAS_HARMONIC) {
+        if (!h->harm_centre) FAIL(h, WTMD_EINVAL, "set the windows with wtmd_harmonic first");
+        if (!h->bias_harm) {
+            h->bias_harm = true;
+            h->bias_grid = false;
+            drop_graphs(h);
+        }
+        return WTMD_OK;
+    }
+    if (h->bias_harm) {
+        h->bias_harm = false;
+        drop_graphs(h);
+    }
+    const bool grid = source == WTMD_BIAS_GRID;
+    if (grid) {
+        if (!h->grid) FAIL(h, WTMD_EINVAL, "the handle has no grid");
+        if (h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
+        for (int i = 0; i < h->d; ++i) {
+            if (h->cfg.grid_bins[i] < 2) FAIL(h, WTMD_EINVAL, "every grid axis needs at least 2 cells");
+            const double per = h->cv[i].period, span = h->cfg.grid_hi[i] - h->cfg.grid_lo[i];
+            if (per > 0.0 && fabs(span - per) > 1e-9 * per)
+                FAIL(h, WTMD_EINVAL, "the grid of a periodic CV must span exactly one period");
+        }
+        if (h->persistent) FAIL(h, WTMD_EINVAL, "not available with the persistent walker step");
+        if (surrogate_k0(h)) FAIL(h, WTMD_EINVAL, "turn the surrogate off first");
+    }
+    if (grid != h->bias_grid) {
+        h->bias_grid = grid;
+        drop_graphs(h);
+    }
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_harmonic(wtmd_t* h, const double* k, const double* centres)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!k || !centres) FAIL(h, WTMD_EINVAL, "null spring constants or centres");
+    if (h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
+    if (h->persistent) FAIL(h, WTMD_EINVAL, "not available with the persistent walker step");
+    if (surrogate_k0(h)) FAIL(h, WTMD_EINVAL, "turn the surrogate off first");
+    for (int c = 0; c < h->d; ++c)
+        if (!(k[c] > 0.0) || !isfinite(k[c])) FAIL(h, WTMD_EINVAL, "spring constants must be finite and > 0");
+    std::vector<double> cen(4 * (size_t)h->W, 0.0);
+    for (int w = 0; w < h->W; ++w)
+        for (int c = 0; c < h->d; ++c) {
+            const double v = centres[(size_t)w * h->d + c];
+            if (!isfinite(v)) FAIL(h, WTMD_EINVAL, "non-finite window centre");
+            cen[4 * (size_t)w + c] = v;
+        }
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (!h->harm_centre) {
+        WTMD_CUDA_TRY(h, cudaMalloc(&h->harm_centre, sizeof(double) * 4 * h->W));
+        WTMD_CUDA_TRY(h, cudaMalloc(&h->harm_sum, sizeof(double) * (4 * h->W + 1)));
+    }
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->harm_centre, cen.data(), sizeof(double) * 4 * h->W, cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemset(h->harm_sum, 0, sizeof(double) * (4 * h->W + 1)));
+    for (int c = 0; c < 3; ++c) h->harm_k[c] = c < h->d ? k[c] : 0.0;
+    h->bias_harm = true;
+    h->bias_grid = false;
+    drop_graphs(h);
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_umbrella_stats(wtmd_t* h, double* mean_out, int64_t* n_samples, int32_t reset)
+{
+    if (!h) return WTMD_EINVAL;
+    if (!h->harm_sum) FAIL(h, WTMD_EINVAL, "no windows (wtmd_harmonic)");
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    std::vector<double> sum(4 * (size_t)h->W + 1);
+    WTMD_CUDA_TRY(h, cudaMemcpy(sum.data(), h->harm_sum, sizeof(double) * sum.size(), cudaMemcpyDeviceToHost));
+    const double n = sum[4 * (size_t)h->W];
+    if (n_samples) *n_samples = (int64_t)n;
+    if (mean_out)
+        for (int w = 0; w < h->W; ++w)
+            for (int c = 0; c < h->d; ++c) mean_out[(size_t)w * h->d + c] = n > 0 ? sum[4 * (size_t)w + c] / n : 0.0;
+    if (reset) WTMD_CUDA_TRY(h, cudaMemset(h->harm_sum, 0, sizeof(double) * sum.size()));
+    return WTMD_OK;
+}
+
+// Umbrella integration (Sec. 2.1.2) on the host from the windows' mean CVs:
+// a few W x d numbers, no device work beyond reading the sums.
+extern "C" int wtmd_umbrella_integrate(wtmd_t* h, double* mean_force_out, double* A_out)
+{
+    if (!h) return WTMD_EINVAL;
+    std::vector<double> mean((size_t)h->W * h->d), cen(4 * (size_t)h->W);
+    int64_t n = 0;
+    int rc = wtmd_umbrella_stats(h, mean.data(), &n, 0);
+    if (rc) return rc;
+    if (n < 1) FAIL(h, WTMD_EINVAL, "no samples yet (run steps with the harmonic bias)");
+    WTMD_CUDA_TRY(h, cudaMemcpy(cen.data(), h->harm_centre, sizeof(double) * cen.size(), cudaMemcpyDeviceToHost));
+    const int d = h->d;
+    std::vector<double> g((size_t)h->W * d);
+    auto wrap = [&](double D, int c) {
+        const double per = h->cv[c].period;
+        return per > 0.0 ? D - per * std::nearbyint(D / per) : D;
+    };
+    for (int w = 0; w < h->W; ++w)
+        for (int c = 0; c < d; ++c)
+            g[(size_t)w * d + c] = -h->harm_k[c] * wrap(mean[(size_t)w * d + c] - cen[4 * (size_t)w + c], c);
+    if (mean_force_out) std::memcpy(mean_force_out, g.data(), sizeof(double) * g.size());
+    if (A_out) {
+        A_out[0] = 0.0;
+        for (int w = 0; w + 1 < h->W; ++w) {
+            double dA = 0.0;
+            for (int c = 0; c < d; ++c)
+                dA += 0.5 * (g[(size_t)w * d + c] + g[(size_t)(w + 1) * d + c]) *
+                      wrap(mean[(size_t)(w + 1) * d + c] - mean[(size_t)w * d + c], c);
+            A_out[w + 1] = A_out[w] + dA;
+        }
+    }
+    return WTMD_OK;
+}
+
 extern "C" int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms)
 {
     if (!h) return WTMD_EINVAL;
@@ -726,6 +882,137 @@ extern "C" int wtmd_counters(wtmd_t* h, int64_t* step, int64_t* n_hills)
     WTMD_CUDA_TRY(h, cudaMemcpy(&c, h->count, sizeof(c), cudaMemcpyDeviceToHost));
     if (step) *step = s;
     if (n_hills) *n_hills = c;
+    return WTMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / restart.  The blob is the raw bytes of everything a step reads
+// that the handle owns -- hill count, step counter, the centre of the scaled
+// FP32 hill layout, both hill layouts, the FP64 grid -- and of the bound
+// particle arrays.  Because the thermostat noise is a counter-based stream
+// keyed by (seed, step, particle), restoring these bytes resumes the run
+// bitwise.  Layout: CkHeader, then hills64 [count][4] double, hills32
+// [cap_pairs][2] float4, grid [ncell] double, positions, velocities, forces
+// [N][4] Real.
+struct CkHeader {
+    uint64_t magic;  // "WTMDCKP1"
+    int32_t version, prec, d, W;
+    int64_t N, cap, cap_pairs, ncell, count, step;
+    double ctr[3];
+    int64_t total;  // bytes of the whole blob
+};
+static const uint64_t kCkMagic = 0x31504b43444d5457ull;  // "WTMDCKP1" little-endian
+
+static int ck_layout(wtmd_t* h, int64_t count, int64_t* total)
+{
+    const int64_t pb = (int64_t)r4sz(h) * h->N;
+    *total = (int64_t)sizeof(CkHeader) + 32 * count + 32 * h->cap_pairs + 8 * h->ncell + 3 * pb;
+    return WTMD_OK;
+}
+
+static int ck_check_handle(wtmd_t* h)
+{
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
+    if (surrogate_k0(h)) FAIL(h, WTMD_EINVAL, "turn the surrogate off first (save its network with wtmd_mlp_params)");
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_checkpoint_size(wtmd_t* h, int64_t* bytes)
+{
+    if (!h || !bytes) return WTMD_EINVAL;
+    int rc;
+    if ((rc = ck_check_handle(h))) return rc;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    long long c = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpy(&c, h->count, sizeof(c), cudaMemcpyDeviceToHost));
+    return ck_layout(h, c, bytes);
+}
+
+extern "C" int wtmd_checkpoint_save(wtmd_t* h, void* out, int64_t cap_bytes)
+{
+    if (!h) return WTMD_EINVAL;
+    int rc;
+    if ((rc = ck_check_handle(h))) return rc;
+    if (!out) FAIL(h, WTMD_EINVAL, "null buffer");
+    if (!h->forces_valid) {  // the forces at the bound positions are part of the state
+        if ((rc = enqueue_forces(h))) return rc;
+        h->forces_valid = true;
+    }
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CkHeader hd{};
+    hd.magic = kCkMagic;
+    hd.version = 1;
+    hd.prec = h->prec;
+    hd.d = h->d;
+    hd.W = h->W;
+    hd.N = h->N;
+    hd.cap = h->cap;
+    hd.cap_pairs = h->cap_pairs;
+    hd.ncell = h->ncell;
+    long long c = 0, st = 0;
+    WTMD_CUDA_TRY(h, cudaMemcpy(&c, h->count, sizeof(c), cudaMemcpyDeviceToHost));
+    WTMD_CUDA_TRY(h, cudaMemcpy(&st, h->step, sizeof(st), cudaMemcpyDeviceToHost));
+    WTMD_CUDA_TRY(h, cudaMemcpy(hd.ctr, h->ctr, sizeof(hd.ctr), cudaMemcpyDeviceToHost));
+    hd.count = c;
+    hd.step = st;
+    ck_layout(h, c, &hd.total);
+    if (cap_bytes < hd.total) FAIL(h, WTMD_EINVAL, "buffer smaller than wtmd_checkpoint_size");
+    char* p = (char*)out;
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    if (c) WTMD_CUDA_TRY(h, cudaMemcpy(p, h->hills64, 32 * (size_t)c, cudaMemcpyDeviceToHost));
+    p += 32 * c;
+    WTMD_CUDA_TRY(h, cudaMemcpy(p, h->hills32, 32 * (size_t)h->cap_pairs, cudaMemcpyDeviceToHost));
+    p += 32 * h->cap_pairs;
+    if (h->ncell) WTMD_CUDA_TRY(h, cudaMemcpy(p, h->grid, 8 * (size_t)h->ncell, cudaMemcpyDeviceToHost));
+    p += 8 * h->ncell;
+    const size_t pb = r4sz(h) * (size_t)h->N;
+    for (void* a : {h->pos, h->vel, h->force}) {
+        WTMD_CUDA_TRY(h, cudaMemcpy(p, a, pb, cudaMemcpyDeviceToHost));
+        p += pb;
+    }
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_checkpoint_load(wtmd_t* h, const void* in, int64_t n_bytes)
+{
+    if (!h) return WTMD_EINVAL;
+    int rc;
+    if ((rc = ck_check_handle(h))) return rc;
+    if (!in || n_bytes < (int64_t)sizeof(CkHeader)) FAIL(h, WTMD_EINVAL, "buffer too small for a checkpoint");
+    CkHeader hd;
+    std::memcpy(&hd, in, sizeof(hd));
+    if (hd.magic != kCkMagic || hd.version != 1) FAIL(h, WTMD_EINVAL, "not a checkpoint of this library");
+    if (hd.prec != h->prec || hd.d != h->d || hd.W != h->W || hd.N != h->N || hd.cap != h->cap ||
+        hd.cap_pairs != h->cap_pairs || hd.ncell != h->ncell)
+        FAIL(h, WTMD_EINVAL, "checkpoint of a handle with another precision, CV count, walkers, atoms, capacity "
+                             "or grid");
+    if (hd.count < 0 || hd.count > h->cap || hd.step < 0) FAIL(h, WTMD_EINVAL, "corrupt checkpoint counters");
+    int64_t total = 0;
+    ck_layout(h, hd.count, &total);
+    if (hd.total != total || n_bytes < total) FAIL(h, WTMD_EINVAL, "truncated or corrupt checkpoint");
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const char* p = (const char*)in + sizeof(hd);
+    if (hd.count) WTMD_CUDA_TRY(h, cudaMemcpy(h->hills64, p, 32 * (size_t)hd.count, cudaMemcpyHostToDevice));
+    p += 32 * hd.count;
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->hills32, p, 32 * (size_t)h->cap_pairs, cudaMemcpyHostToDevice));
+    p += 32 * h->cap_pairs;
+    if (h->ncell) WTMD_CUDA_TRY(h, cudaMemcpy(h->grid, p, 8 * (size_t)h->ncell, cudaMemcpyHostToDevice));
+    p += 8 * h->ncell;
+    const size_t pb = r4sz(h) * (size_t)h->N;
+    for (void* a : {h->pos, h->vel, h->force}) {
+        WTMD_CUDA_TRY(h, cudaMemcpy(a, p, pb, cudaMemcpyHostToDevice));
+        p += pb;
+    }
+    long long c = hd.count, st = hd.step;
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->count, &c, sizeof(c), cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->step, &st, sizeof(st), cudaMemcpyHostToDevice));
+    WTMD_CUDA_TRY(h, cudaMemcpy(h->ctr, hd.ctr, sizeof(hd.ctr), cudaMemcpyHostToDevice));
+    // the restored forces belong to the restored positions; the neighbour
+    // lists were built for other positions and are rebuilt by the next step
+    h->forces_valid = true;
+    if ((rc = nl_request(h))) return rc;
+    WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return WTMD_OK;
 }
 
@@ -816,6 +1103,8 @@ extern "C" int wtmd_walkers_persistent(wtmd_t* h, int32_t enable)
         h->persistent = false;
         return WTMD_OK;
     }
+    if (h->bias_grid || h->bias_harm)
+        FAIL(h, WTMD_EINVAL, "the persistent walker step sums the hills; grid-read and harmonic biases are per-kernel");
     return walkers_enable(h);
 }
 

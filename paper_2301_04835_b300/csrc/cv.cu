@@ -228,6 +228,240 @@ __global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ po
 }
 
 // ---------------------------------------------------------------------------
+// Equal-mass centre of a group (all atoms of the walker when A is null):
+// members unwrapped by the minimum image relative to the first member, as
+// for Rg; compensated FP32 sums on FP32 handles, FP64 sums on FP64 handles.
+// Block-wide; every thread gets the centre.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R4<R> unwrap_member(const R4<R>* pos, long long o, const int* A, int p, const Box& box,
+                                               R rx, R ry, R rz)
+{
+    const int i = A ? A[p] : p;
+    R x, y, z, d[3];
+    load3<R>(pos, o + i, x, y, z);
+    delta<R>(box, x, y, z, rx, ry, rz, d);
+    return mk4<R>(rx + d[0], ry + d[1], rz + d[2], R(0));
+}
+
+template <typename R>
+__device__ void group_centre(const R4<R>* pos, long long o, const int* A, int m, const Box& box, R ref[3], R c[3])
+{
+    load3<R>(pos, o + (A ? A[0] : 0), ref[0], ref[1], ref[2]);
+    cf s[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double sd[3] = {0.0, 0.0, 0.0};
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const R4<R> q = unwrap_member<R>(pos, o, A, p, box, ref[0], ref[1], ref[2]);
+        if constexpr (sizeof(R) == 4) {
+            s[0] = cf_add(s[0], (float)q.x);
+            s[1] = cf_add(s[1], (float)q.y);
+            s[2] = cf_add(s[2], (float)q.z);
+        } else {
+            sd[0] += (double)q.x;
+            sd[1] += (double)q.y;
+            sd[2] += (double)q.z;
+        }
+    }
+    if constexpr (sizeof(R) == 4) {
+        block_sum_cf<3>(s);
+        for (int k = 0; k < 3; ++k) c[k] = (R)(cf_val(s[k]) / m);
+    } else {
+        block_sum<double, 3>(sd);
+        for (int k = 0; k < 3; ++k) c[k] = (R)(sd[k] / m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Distance between the centres of groups A and B (Sec. 2.2, TwoPointCV),
+// the centre difference d = c_B - c_A by the minimum image; xi = scale |d|,
+// dxi/dr = -scale d / (|d| |A|) on A and +scale d / (|d| |B|) on B (A and B
+// disjoint).  One block per walker.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) cv_distance_kernel(const R4<R>* __restrict__ pos,
+                                                          const int64_t* __restrict__ woff, const int* __restrict__ A,
+                                                          int nA, const int* __restrict__ B, int nB, Box box, R scale,
+                                                          double* __restrict__ xi, int col, R4<R>* __restrict__ J)
+{
+    const int w = blockIdx.x;
+    const long long o = woff[w];
+    R ra[3], rb[3], ca[3], cb[3], d[3];
+    group_centre<R>(pos, o, A, nA, box, ra, ca);
+    group_centre<R>(pos, o, B, nB, box, rb, cb);
+    delta<R>(box, cb[0], cb[1], cb[2], ca[0], ca[1], ca[2], d);
+    const R r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const R ga = -scale / (r * (R)nA), gb = scale / (r * (R)nB);
+    for (int p = threadIdx.x; p < nA; p += blockDim.x) J[o + A[p]] = mk4<R>(ga * d[0], ga * d[1], ga * d[2], R(0));
+    for (int p = threadIdx.x; p < nB; p += blockDim.x) J[o + B[p]] = mk4<R>(gb * d[0], gb * d[1], gb * d[2], R(0));
+    if (threadIdx.x == 0) xi[w * 4 + col] = (double)(scale * r);
+}
+
+// ---------------------------------------------------------------------------
+// Angle at the middle of three atoms (Sec. 2.2, ThreePointCV): u = p0 - p1,
+// v = p2 - p1 (minimum image), w = u x v, theta = atan2(|w|, u.v) in [0, pi];
+// with n = w / |w|:  dtheta/du = (u.v (v x n) - |w| v) / (|w|^2 + (u.v)^2),
+// dtheta/dv = (u.v (n x u) - |w| u) / (...), dtheta/dp1 = -(dtheta/du +
+// dtheta/dv); zero where |w| = 0 (theta = 0 or pi).  One thread per walker.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void cv_angle_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff, int W, int3 idx,
+                                Box box, R scale, double* __restrict__ xi, int col, R4<R>* __restrict__ J)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const long long o = woff[w];
+    const long long i0 = o + idx.x, i1 = o + idx.y, i2 = o + idx.z;
+    R p0[3], p1[3], p2[3], u[3], v[3];
+    load3<R>(pos, i0, p0[0], p0[1], p0[2]);
+    load3<R>(pos, i1, p1[0], p1[1], p1[2]);
+    load3<R>(pos, i2, p2[0], p2[1], p2[2]);
+    delta<R>(box, p0[0], p0[1], p0[2], p1[0], p1[1], p1[2], u);
+    delta<R>(box, p2[0], p2[1], p2[2], p1[0], p1[1], p1[2], v);
+    const R wx = u[1] * v[2] - u[2] * v[1], wy = u[2] * v[0] - u[0] * v[2], wz = u[0] * v[1] - u[1] * v[0];
+    const R sn = sqrt(wx * wx + wy * wy + wz * wz);
+    const R cs = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+    R gu[3] = {R(0), R(0), R(0)}, gv[3] = {R(0), R(0), R(0)};
+    if (sn > R(0)) {
+        const R nx = wx / sn, ny = wy / sn, nz = wz / sn;
+        const R inv = scale / (sn * sn + cs * cs);
+        const R vn[3] = {v[1] * nz - v[2] * ny, v[2] * nx - v[0] * nz, v[0] * ny - v[1] * nx};
+        const R nu[3] = {ny * u[2] - nz * u[1], nz * u[0] - nx * u[2], nx * u[1] - ny * u[0]};
+        for (int k = 0; k < 3; ++k) {
+            gu[k] = inv * (cs * vn[k] - sn * v[k]);
+            gv[k] = inv * (cs * nu[k] - sn * u[k]);
+        }
+    }
+    xi[w * 4 + col] = (double)(scale * atan2(sn, cs));
+    J[i0] = mk4<R>(gu[0], gu[1], gu[2], R(0));
+    J[i2] = mk4<R>(gv[0], gv[1], gv[2], R(0));
+    J[i1] = mk4<R>(-(gu[0] + gv[0]), -(gu[1] + gv[1]), -(gu[2] + gv[2]), R(0));
+}
+
+// ---------------------------------------------------------------------------
+// Gyration-tensor CVs (Sec. 2.2: PrincipalMoment, Asphericity,
+// Acylindricity, ShapeAnisotropy), equal masses.  S = (1/m) sum (u-c)(u-c)^T
+// over the unwrapped members; eigenvalues l1 <= l2 <= l3 with unit vectors
+// e1..e3.  quantity 0..2: l1..l3; 3: l3 - (l1+l2)/2; 4: l2 - l1;
+// 5: 3/2 (l1^2+l2^2+l3^2)/(l1+l2+l3)^2 - 1/2.  For simple eigenvalues
+// dl_j/dr_k = (2/m) (e_j . (u_k - c)) e_j; the quantity's gradient is
+// sum_j (dq/dl_j) dl_j/dr_k.  One block per walker; the 3x3 eigenproblem is
+// solved by thread 0 in FP64 with Jacobi rotations, each zeroing one
+// off-diagonal element and updating the others in place.
+// ---------------------------------------------------------------------------
+__device__ void sym3_eigen(double a[3][3], double lam[3], double ev[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) ev[i][j] = i == j ? 1.0 : 0.0;
+    for (int it = 0; it < 64; ++it) {
+        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
+        const double dia = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]);
+        if (off == 0.0 || off <= 1e-18 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = a[p][q];
+                if (apq == 0.0) continue;
+                const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+                const double t = copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = rsqrt(t * t + 1.0), s = t * c;
+                a[p][p] -= t * apq;
+                a[q][q] += t * apq;
+                a[p][q] = a[q][p] = 0.0;
+                const int r = 3 - p - q;  // the remaining index
+                const double arp = a[r][p], arq = a[r][q];
+                a[r][p] = a[p][r] = c * arp - s * arq;
+                a[r][q] = a[q][r] = s * arp + c * arq;
+                for (int k = 0; k < 3; ++k) {
+                    const double vp = ev[k][p], vq = ev[k][q];
+                    ev[k][p] = c * vp - s * vq;
+                    ev[k][q] = s * vp + c * vq;
+                }
+            }
+    }
+    int ord[3] = {0, 1, 2};
+    if (a[ord[1]][ord[1]] < a[ord[0]][ord[0]]) { const int t = ord[0]; ord[0] = ord[1]; ord[1] = t; }
+    if (a[ord[2]][ord[2]] < a[ord[1]][ord[1]]) { const int t = ord[1]; ord[1] = ord[2]; ord[2] = t; }
+    if (a[ord[1]][ord[1]] < a[ord[0]][ord[0]]) { const int t = ord[0]; ord[0] = ord[1]; ord[1] = t; }
+    double e2[3][3];
+    for (int j = 0; j < 3; ++j) {
+        lam[j] = a[ord[j]][ord[j]];
+        for (int k = 0; k < 3; ++k) e2[k][j] = ev[k][ord[j]];
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j) ev[k][j] = e2[k][j];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) cv_gyration_kernel(const R4<R>* __restrict__ pos,
+                                                          const int64_t* __restrict__ woff, const int* __restrict__ wn,
+                                                          const int* __restrict__ A, int nA, Box box, int quantity,
+                                                          double scale, double* __restrict__ xi, int col,
+                                                          R4<R>* __restrict__ J)
+{
+    __shared__ R sh_e[3][3], sh_g[3];  // unit eigenvectors e_j (sh_e[j]) and factors scale dq/dl_j 2/m
+    const int w = blockIdx.x;
+    const long long o = woff[w];
+    const int m = A ? nA : wn[w];
+    R ref[3], c[3];
+    group_centre<R>(pos, o, A, m, box, ref, c);
+    cf t[6] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double td[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const R4<R> q = unwrap_member<R>(pos, o, A, p, box, ref[0], ref[1], ref[2]);
+        const R dx = q.x - c[0], dy = q.y - c[1], dz = q.z - c[2];
+        const R prod[6] = {dx * dx, dy * dy, dz * dz, dx * dy, dx * dz, dy * dz};
+        for (int k = 0; k < 6; ++k) {
+            if constexpr (sizeof(R) == 4) t[k] = cf_add(t[k], (float)prod[k]);
+            else td[k] += (double)prod[k];
+        }
+    }
+    if constexpr (sizeof(R) == 4) {
+        block_sum_cf<6>(t);
+        for (int k = 0; k < 6; ++k) td[k] = cf_val(t[k]);
+    } else {
+        block_sum<double, 6>(td);
+    }
+    if (threadIdx.x == 0) {
+        double S[3][3] = {{td[0] / m, td[3] / m, td[4] / m}, {td[3] / m, td[1] / m, td[5] / m},
+                          {td[4] / m, td[5] / m, td[2] / m}};
+        double l[3], ev[3][3];
+        sym3_eigen(S, l, ev);
+        const double T = l[0] + l[1] + l[2], Q = l[0] * l[0] + l[1] * l[1] + l[2] * l[2];
+        double q = 0.0, g[3] = {0.0, 0.0, 0.0};
+        if (quantity <= 2) {
+            q = l[quantity];
+            g[quantity] = 1.0;
+        } else if (quantity == 3) {
+            q = l[2] - 0.5 * (l[0] + l[1]);
+            g[0] = g[1] = -0.5;
+            g[2] = 1.0;
+        } else if (quantity == 4) {
+            q = l[1] - l[0];
+            g[0] = -1.0;
+            g[1] = 1.0;
+        } else {
+            q = 1.5 * Q / (T * T) - 0.5;
+            for (int j = 0; j < 3; ++j) g[j] = 3.0 * (l[j] * T - Q) / (T * T * T);
+        }
+        for (int j = 0; j < 3; ++j) {
+            sh_g[j] = (R)(scale * g[j] * 2.0 / m);
+            for (int k = 0; k < 3; ++k) sh_e[j][k] = (R)ev[k][j];
+        }
+        xi[w * 4 + col] = scale * q;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < m; p += blockDim.x) {
+        const R4<R> q = unwrap_member<R>(pos, o, A, p, box, ref[0], ref[1], ref[2]);
+        const R d[3] = {q.x - c[0], q.y - c[1], q.z - c[2]};
+        R jr[3] = {R(0), R(0), R(0)};
+        for (int j = 0; j < 3; ++j) {
+            const R f = sh_g[j] * (sh_e[j][0] * d[0] + sh_e[j][1] * d[1] + sh_e[j][2] * d[2]);
+            for (int k = 0; k < 3; ++k) jr[k] += f * sh_e[j][k];
+        }
+        J[o + (A ? A[p] : p)] = mk4<R>(jr[0], jr[1], jr[2], R(0));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Switching-function pair sums.  s(r) = 1/(1 + y^h), y = r^2/r0^2, h = n/2
 // (the rational (1-x^n)/(1-x^m) with m = 2n, which equals this exactly), and
 // ds/dr_t = -(n/r0^2) y^(h-1) s^2 (r_t - r_s).
@@ -1129,6 +1363,20 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
             mark(h, "cv_dihedral");
             break;
         }
+        case WTMD_CV_DISTANCE:
+            cv_distance_kernel<R><<<W, 256, 0, st>>>(pos, h->woff, cv.a, cv.n_a, cv.b, cv.n_b, h->box, sc, xi, c, Jc);
+            mark(h, "cv_distance");
+            break;
+        case WTMD_CV_ANGLE:
+            cv_angle_kernel<R><<<(W + 127) / 128, 128, 0, st>>>(
+                pos, h->woff, W, make_int3(cv.hidx[0], cv.hidx[1], cv.hidx[2]), h->box, sc, xi, c, Jc);
+            mark(h, "cv_angle");
+            break;
+        case WTMD_CV_GYRATION:
+            cv_gyration_kernel<R><<<W, 256, 0, st>>>(pos, h->woff, h->wn, cv.n_a < 0 ? nullptr : cv.a, cv.n_a, h->box,
+                                                     cv.axis, cv.scale != 0.0 ? cv.scale : 1.0, xi, c, Jc);
+            mark(h, "cv_gyration");
+            break;
         case WTMD_CV_RG:
             cv_rg_kernel<R><<<W, 256, 0, st>>>(pos, h->woff, h->wn, cv.n_a < 0 ? nullptr : cv.a, cv.n_a, h->box,
                                                cv.scale, cv.flags & WTMD_CV_INTENSIVE, xi, c, Jc);

@@ -134,6 +134,81 @@ __global__ void fes_kernel(const double* __restrict__ grid, long long n, double 
     out[i] = f * grid[i] - f * vmax[0];
 }
 
+// Bias and gradient read from the grid instead of summed over the hills (the
+// paper's accuracy-for-speed option, Sec. 2.1.5): the grid keeps V at cell
+// centres; the gradient at a node along axis i is the central difference of
+// its neighbours (one-sided at the ends of a non-periodic axis, wrapped on a
+// periodic one), and V and dV/dxi at a point are multilinear interpolations
+// of the node values over the 2^d surrounding nodes.  A non-periodic
+// coordinate is clamped to the outermost nodes.  One thread per point, FP64
+// throughout (the grid is FP64); the result is rounded to R on the store.
+// The point's corner nodes and their neighbours (at most 56 doubles) are
+// L2-resident reads: the kernel is bound by its launch, not by memory.
+template <typename X, typename R>
+__global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double* __restrict__ grid,
+                                                        const X* __restrict__ xi, int xs, long long P,
+                                                        R* __restrict__ V, R* __restrict__ dV, int dvs)
+{
+    // launched as a programmatic dependent of the CV kernel in a step: every
+    // read (xi, grid) comes after the wait; dependents may launch at once, as
+    // their own wait covers this kernel's completion
+    pdl_wait();
+    pdl_trigger();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    long long cstride[3] = {1, 1, 1};
+    for (int i = g.d - 2; i >= 0; --i) cstride[i] = cstride[i + 1] * g.bins[i + 1];
+    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < g.d; ++i) {
+        const int n = g.bins[i];
+        double u = ((double)xi[p * xs + i] - g.lo[i]) / g.dx[i] - 0.5;
+        if (g.per[i] > 0.0) {
+            u -= (double)n * floor(u / (double)n);
+            if (!(u >= 0.0 && u < (double)n)) u = 0.0;  // rounding at n, or a non-finite / huge coordinate
+            k0[i] = (int)floor(u);
+            k1[i] = k0[i] + 1 == n ? 0 : k0[i] + 1;
+        } else {
+            u = fmin(fmax(u, 0.0), (double)(n - 1));
+            k0[i] = min((int)floor(u), n - 2);
+            k1[i] = k0[i] + 1;
+        }
+        t[i] = u - (double)k0[i];
+    }
+    double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
+    for (int c = 0; c < (1 << g.d); ++c) {
+        int k[3];
+        double wgt = 1.0;
+        long long node = 0;
+        for (int i = 0; i < g.d; ++i) {
+            const bool up = (c >> i) & 1;
+            k[i] = up ? k1[i] : k0[i];
+            wgt *= up ? t[i] : 1.0 - t[i];
+            node += k[i] * cstride[i];
+        }
+        v += wgt * grid[node];
+        for (int i = 0; i < g.d; ++i) {
+            const int n = g.bins[i];
+            int kp, km;
+            double span;
+            if (g.per[i] > 0.0) {
+                kp = k[i] + 1 == n ? 0 : k[i] + 1;
+                km = k[i] == 0 ? n - 1 : k[i] - 1;
+                span = 2.0 * g.dx[i];
+            } else {
+                kp = min(k[i] + 1, n - 1);
+                km = max(k[i] - 1, 0);
+                span = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
+            }
+            const double diff = grid[node + (kp - k[i]) * cstride[i]] - grid[node + (km - k[i]) * cstride[i]];
+            gr[i] += wgt * (diff / span);
+        }
+    }
+    if (V) V[p] = (R)v;
+    if (dV)
+        for (int i = 0; i < g.d; ++i) dV[p * dvs + i] = (R)gr[i];
+}
+
 // ---------------------------------------------------------------------------
 static GridPrm grid_prm(const wtmd_t* h)
 {
@@ -161,7 +236,7 @@ static double fes_factor(const wtmd_config& c)
 DepPrm dep_prm(const wtmd_t* h)
 {
     DepPrm p{};
-    p.stride = h->cfg.stride;
+    p.stride = h->bias_harm ? 0 : h->cfg.stride;  // umbrella windows deposit no hills
     p.cap = h->cap;
     p.W = h->W;
     p.d = h->d;
@@ -221,6 +296,85 @@ int launch_fes(wtmd_t* h, double* out)
     fes_kernel<<<(unsigned)((h->ncell + 255) / 256), 256, 0, h->stream>>>(h->grid, h->ncell, fes_factor(h->cfg), vmax,
                                                                           out);
     WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+// Harmonic biasing (Sec. 2.1.1): V = sum_c k_c/2 (xi_c - xi0_c)^2,
+// dV/dxi_c = k_c (xi_c - xi0_c), the difference by the minimum image on a
+// periodic CV; every walker has its own centre xi0 (one umbrella window per
+// walker, Sec. 2.1.2).  In a step the kernel also adds each walker's xi to
+// its window sums (FP64) and counts the sample.  One thread per walker.
+struct HarmPrm {
+    int W, d;
+    double k[3], per[3];
+};
+
+template <typename R>
+__global__ void harmonic_bias_kernel(HarmPrm hp, const double* __restrict__ xi, const double* __restrict__ centre,
+                                     R* __restrict__ V, R* __restrict__ dV, double* __restrict__ sum)
+{
+    pdl_wait();  // xi comes from the CV kernel this launch depends on
+    pdl_trigger();
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= hp.W) return;
+    double v = 0.0;
+    for (int c = 0; c < hp.d; ++c) {
+        const double x = xi[w * 4 + c];
+        double D = x - centre[w * 4 + c];
+        if (hp.per[c] > 0.0) D -= hp.per[c] * rint(D / hp.per[c]);
+        v += 0.5 * hp.k[c] * D * D;
+        dV[w * 4 + c] = (R)(hp.k[c] * D);
+        if (sum) sum[w * 4 + c] += x;
+    }
+    V[w] = (R)v;
+    if (sum && w == 0) sum[hp.W * 4] += 1.0;
+}
+
+int launch_harmonic(wtmd_t* h, bool accumulate)
+{
+    HarmPrm hp{};
+    hp.W = h->W;
+    hp.d = h->d;
+    for (int c = 0; c < 3; ++c) {
+        hp.k[c] = h->harm_k[c];
+        hp.per[c] = c < h->d ? h->cv[c].period : 0.0;
+    }
+    double* sum = accumulate ? h->harm_sum : nullptr;
+    const dim3 blocks((unsigned)((h->W + 127) / 128)), threads(128);
+    cudaError_t e;
+    if (h->prec == WTMD_F32)
+        e = launch_pdl(harmonic_bias_kernel<float>, blocks, threads, 0, h->stream, hp, (const double*)h->xi,
+                       (const double*)h->harm_centre, (float*)h->V, (float*)h->dV, sum);
+    else
+        e = launch_pdl(harmonic_bias_kernel<double>, blocks, threads, 0, h->stream, hp, (const double*)h->xi,
+                       (const double*)h->harm_centre, (double*)h->V, (double*)h->dV, sum);
+    mark(h, "harmonic_bias");
+    WTMD_CUDA_TRY(h, e);
+    return WTMD_OK;
+}
+
+int launch_grid_bias(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs, bool pdl)
+{
+    if (P <= 0) return WTMD_OK;
+    const GridPrm g = grid_prm(h);
+    const dim3 blocks((unsigned)((P + 127) / 128)), threads(128);
+    cudaError_t e;
+    auto go = [&](auto kern, auto xip, auto Vp, auto dVp) {
+        if (pdl) return launch_pdl(kern, blocks, threads, 0, h->stream, g, (const double*)h->grid, xip, xs, (long long)P,
+                                   Vp, dVp, dvs);
+        kern<<<blocks, threads, 0, h->stream>>>(g, h->grid, xip, xs, (long long)P, Vp, dVp, dvs);
+        return cudaGetLastError();
+    };
+    if (h->prec == WTMD_F32) {
+        if (xi_f64)
+            e = go(grid_bias_kernel<double, float>, (const double*)xi, (float*)V, (float*)dV);
+        else
+            e = go(grid_bias_kernel<float, float>, (const float*)xi, (float*)V, (float*)dV);
+    } else {
+        e = go(grid_bias_kernel<double, double>, (const double*)xi, (double*)V, (double*)dV);
+    }
+    mark(h, "grid_bias");
+    WTMD_CUDA_TRY(h, e);
     return WTMD_OK;
 }
 

@@ -921,6 +921,7 @@ extern "C" int wtmd_surrogate(wtmd_t* h, int32_t enable, double tol_kT, int64_t 
     }
     if (!(tol_kT > 0.0) || retrain_every < 0) SFAIL(h, WTMD_EINVAL, "tolerance must be > 0, retrain_every >= 0");
     if (h->persistent) SFAIL(h, WTMD_EINVAL, "the surrogate is not available with the persistent walker step");
+    if (h->bias_grid || h->bias_harm) SFAIL(h, WTMD_EINVAL, "the surrogate replaces the hills sum; another bias source is on");
     Surrogate* s = nullptr;
     int rc = sur_get(h, &s);
     if (rc) return rc;
@@ -981,6 +982,7 @@ extern "C" int wtmd_surrogate_set(wtmd_t* h, int64_t k0, int32_t active)
     if (!h) return WTMD_EINVAL;
     if (k0 < 0 || k0 % 256 || k0 > h->cap) SFAIL(h, WTMD_EINVAL, "k0 must be a multiple of 256 within capacity");
     if (h->persistent) SFAIL(h, WTMD_EINVAL, "the surrogate is not available with the persistent walker step");
+    if (h->bias_grid || h->bias_harm) SFAIL(h, WTMD_EINVAL, "the surrogate replaces the hills sum; another bias source is on");
     Surrogate* s = nullptr;
     int rc = sur_get(h, &s);
     if (rc) return rc;

@@ -366,6 +366,12 @@ struct wtmd_t {
     int graph_steps = 0;
     cudaGraphExec_t graph1 = nullptr;
     bool persistent = false;        // multi-walker step as one persistent launch
+    bool bias_grid = false;         // step/bias_eval read V, dV/dxi from the grid (WTMD_BIAS_GRID)
+    bool bias_harm = false;         // harmonic bias about per-walker centres (WTMD_BIAS_HARMONIC)
+    bool in_step = false;           // the bias being enqueued belongs to a step (window statistics count it)
+    double harm_k[3] = {0.0, 0.0, 0.0};
+    double* harm_centre = nullptr;  // device [W][4] window centres
+    double* harm_sum = nullptr;     // device [W][4] sum of xi over steps, then [W*4] the sample count (as double)
     wtmd::WalkerPlan wk;
     bool no_graph = false;          // capture failed: replay eagerly
     bool jz_pre = false;            // the step zeroed the tile-path coordination J rows before BAOAB
@@ -404,6 +410,11 @@ int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all
 int launch_cv(wtmd_t* h, const void* pos, int c);               // xi, J of CV c
 int launch_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos);  // J^T grad_xi
 int launch_grid_update(wtmd_t* h);                              // FP64 grid += this step's new hills
+// harmonic bias of every walker about its window centre (xi: h->xi)
+int launch_harmonic(wtmd_t* h, bool accumulate);
+// V, dV/dxi at P points read from the FP64 grid (xi: double if xi_f64, else Real)
+int launch_grid_bias(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
+                     int dV_stride, bool pdl);
 int walkers_enable(wtmd_t* h);
 int walkers_retile(wtmd_t* h, int T, int bps, int hsplit_mult);
 int launch_walkers_step(wtmd_t* h, int mode);                   // 0: full step, 1: forces only

@@ -6,7 +6,8 @@ import numpy as np
 
 import synth
 
-KIND = {"component": 1, "dihedral": 2, "coordination": 3, "rg": 4, "qpairs": 5}
+KIND = {"component": 1, "dihedral": 2, "coordination": 3, "rg": 4, "qpairs": 5, "distance": 6, "angle": 7,
+        "gyration": 8}
 
 
 def oracle_system(spec):

@@ -235,6 +235,14 @@ CV_CASES = {
     "coord_ab": [dict(kind="coordination", a=[1, 5, 9, 200], b=list(range(0, 300, 2)), r0=1.5, nn=8, mm=16)],
     "rg_all_intensive": [dict(kind="rg", a=None, flags=1)],
     "qpairs": [dict(kind="qpairs", a=[0, 1, 2, 5, 7, 3, 1, 9, 40, 41], r0=1.5, nn=6, mm=12)],
+    "distance": [dict(kind="distance", a=list(range(0, 40, 3)), b=[100, 101, 250])],
+    "angle": [dict(kind="angle", a=[3, 10, 11])],
+    "gyration_shape": [dict(kind="gyration", a=list(range(100, 164)), axis=5),
+                       dict(kind="gyration", a=list(range(100, 164)), axis=3),
+                       dict(kind="gyration", a=None, axis=2)],
+    "gyration_moments": [dict(kind="gyration", a=list(range(200, 232)), axis=0),
+                         dict(kind="gyration", a=list(range(200, 232)), axis=1),
+                         dict(kind="gyration", a=list(range(200, 232)), axis=4)],
     "three_cvs": [dict(kind="coordination", a=list(range(0, 500, 5)), r0=1.5),
                   dict(kind="rg", a=list(range(100, 164))),
                   dict(kind="qpairs", a=[0, 1, 2, 5, 7, 3, 1, 9], r0=1.5)],
@@ -532,3 +540,16 @@ def test_standard_metadynamics_and_no_deposition(prec):
             assert np.allclose(h[:, :2], sim.hills[:nh, :2], rtol=0, atol=1e-5 if prec == "f32" else 1e-12)
         tol = 1e-4 if prec == "f32" else 1e-12
         assert np.max(np.abs(to_np(pos)[:, :3] - sim.x)) < tol
+
+
+def test_new_cv_definitions_are_validated():
+    wt = _wt()
+    m = wt.Wtmd(precision="f32", sigma=[0.1], walker_sizes=[20])
+    for bad in [dict(kind=wt.CV_DISTANCE, a=[0, 1], b=[1, 2]),  # overlapping groups
+                dict(kind=wt.CV_DISTANCE, a=[0, 1], b=None),  # B must be a list
+                dict(kind=wt.CV_ANGLE, a=[0, 1]), dict(kind=wt.CV_ANGLE, a=[0, 1, 1]),
+                dict(kind=wt.CV_GYRATION, a=[0, 1, 2], axis=6), dict(kind=wt.CV_GYRATION, a=[3], axis=0),
+                dict(kind=wt.CV_GYRATION, a=[0, 25], axis=1)]:
+        with pytest.raises(wt.WtmdError):
+            m.cv_define(**bad)
+    m.cv_define(wt.CV_GYRATION, a=None, axis=wt.GY_ANISOTROPY)
