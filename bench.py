@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-walkers", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-grid-bias", action="store_true")
-    ap.add_argument("--case", choices=["hills", "walkers", "mlp"], default=None,
+    ap.add_argument("--case", choices=["hills", "walkers", "mlp", "grid", "cvs"], default=None,
                     help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
     return ap.parse_args()
 
@@ -728,7 +728,10 @@ def run_case(name: str):
     """One representative launch configuration of a hot kernel, repeated a
     few times: `hills` = FP32 hills sum, 1e6 hills, 4096 points, d = 2;
     `walkers` = the 256-cluster persistent step; `mlp` = network inference at
-    4096 points and training steps on 4096 samples."""
+    4096 points and training steps on 4096 samples; `grid` = the 4096-atom
+    step with the bias read from a 128x128 grid (1e4 hills) and the grid read
+    at 4096 points; `cvs` = Distance, Angle and gyration-tensor CVs of 256
+    walkers of 512 atoms (bias_eval, harmonic windows)."""
     import torch
 
     import paper_2301_04835_b300 as wt
@@ -755,6 +758,42 @@ def run_case(name: str):
         m.bind(pos, vel, F)
         m.walkers_persistent(True)
         m.step_n(8)
+    elif name == "grid":
+        x, v, L, tag, rg = workload_inputs(seed=0)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        probe = wt.Wtmd(precision="f32", sigma=SIGMA, walker_sizes=[N_ATOMS], box=(L, L, L), engine="lj")
+        probe.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+        probe.cv_define(wt.CV_RG, a=rg)
+        xi0 = probe.bias_eval(pos)[1][0].double().cpu().numpy()
+        probe.close()
+        sig = np.asarray(SIGMA)
+        m = wt.Wtmd(precision="f32", sigma=SIGMA, w0=1.0, gamma=8.0, kT=1.0, stride=100, capacity=20000, seed=0,
+                    engine="lj", walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005, friction=1.0,
+                    grid=((128, 128), list(xi0 - 6 * sig), list(xi0 + 6 * sig)))
+        m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+        m.cv_define(wt.CV_RG, a=rg)
+        m.hills_load(synth.walk_hills(10000, xi0 - 3 * sig, xi0 + 3 * sig, 0.5 * sig, seed=100))
+        m.bias_source(wt.BIAS_GRID)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        m.step_n(8)
+        P = 4096
+        pts = torch.tensor(synth.uniform_points(P, list(xi0 - 3 * sig), list(xi0 + 3 * sig), seed=7),
+                           dtype=torch.float32, device=dev)
+        for _ in range(3):
+            m.grid_eval(pts)
+    elif name == "cvs":
+        W, n = 256, 512
+        x = np.concatenate([synth.lattice(n, 0.8, seed=s_, jitter=0.1)[0] for s_ in range(W)])
+        m = wt.Wtmd(precision="f32", sigma=(0.1, 0.1, 0.1), capacity=16, walker_sizes=[n] * W)
+        m.cv_define(wt.CV_GYRATION, a=None, axis=wt.GY_ANISOTROPY)
+        m.cv_define(wt.CV_DISTANCE, a=list(range(0, 64)), b=list(range(256, 320)))
+        m.cv_define(wt.CV_ANGLE, a=[3, 100, 300])
+        m.harmonic((10.0, 10.0, 10.0), np.zeros((W, 3)))
+        pos = wt.particles(x, torch.float32)
+        F = torch.zeros_like(pos)
+        for _ in range(3):
+            m.bias_eval(pos, F)
     else:
         m = wt.Wtmd(precision="f32", sigma=(0.4, 0.4, 0.4), capacity=16, walker_sizes=[1])
         for i in range(3):

@@ -144,7 +144,7 @@ __global__ void fes_kernel(const double* __restrict__ grid, long long n, double 
 // throughout (the grid is FP64); the result is rounded to R on the store.
 // The point's corner nodes and their neighbours (at most 56 doubles) are
 // L2-resident reads: the kernel is bound by its launch, not by memory.
-template <typename X, typename R>
+template <int D, typename X, typename R>
 __global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double* __restrict__ grid,
                                                         const X* __restrict__ xi, int xs, long long P,
                                                         R* __restrict__ V, R* __restrict__ dV, int dvs)
@@ -156,11 +156,16 @@ __global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double*
     pdl_trigger();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
-    long long cstride[3] = {1, 1, 1};
-    for (int i = g.d - 2; i >= 0; --i) cstride[i] = cstride[i + 1] * g.bins[i + 1];
-    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
-    double t[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < g.d; ++i) {
+    constexpr int NC = 1 << D;       // corner nodes
+    constexpr int NV = 1 + 2 * D;    // per corner: the node and its two neighbours on each axis
+    long long cstride[D];
+    cstride[D - 1] = 1;
+#pragma unroll
+    for (int i = D - 2; i >= 0; --i) cstride[i] = cstride[i + 1] * g.bins[i + 1];
+    int k0[D], k1[D];
+    double t[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
         const int n = g.bins[i];
         double u = ((double)xi[p * xs + i] - g.lo[i]) / g.dx[i] - 0.5;
         if (g.per[i] > 0.0) {
@@ -175,38 +180,53 @@ __global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double*
         }
         t[i] = u - (double)k0[i];
     }
-    double v = 0.0, gr[3] = {0.0, 0.0, 0.0};
-    for (int c = 0; c < (1 << g.d); ++c) {
-        int k[3];
-        double wgt = 1.0;
+    // every address first, then every load (unrolled: one round of latency),
+    // then the sums in corner order
+    double val[NC][NV], wgt[NC], span[NC][D];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        int k[D];
+        double w = 1.0;
         long long node = 0;
-        for (int i = 0; i < g.d; ++i) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
             const bool up = (c >> i) & 1;
             k[i] = up ? k1[i] : k0[i];
-            wgt *= up ? t[i] : 1.0 - t[i];
+            w *= up ? t[i] : 1.0 - t[i];
             node += k[i] * cstride[i];
         }
-        v += wgt * grid[node];
-        for (int i = 0; i < g.d; ++i) {
+        wgt[c] = w;
+        val[c][0] = grid[node];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
             const int n = g.bins[i];
             int kp, km;
-            double span;
             if (g.per[i] > 0.0) {
                 kp = k[i] + 1 == n ? 0 : k[i] + 1;
                 km = k[i] == 0 ? n - 1 : k[i] - 1;
-                span = 2.0 * g.dx[i];
+                span[c][i] = 2.0 * g.dx[i];
             } else {
                 kp = min(k[i] + 1, n - 1);
                 km = max(k[i] - 1, 0);
-                span = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
+                span[c][i] = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
             }
-            const double diff = grid[node + (kp - k[i]) * cstride[i]] - grid[node + (km - k[i]) * cstride[i]];
-            gr[i] += wgt * (diff / span);
+            val[c][1 + 2 * i] = grid[node + (kp - k[i]) * cstride[i]];
+            val[c][2 + 2 * i] = grid[node + (km - k[i]) * cstride[i]];
         }
+    }
+    double v = 0.0, gr[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) gr[i] = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        v += wgt[c] * val[c][0];
+#pragma unroll
+        for (int i = 0; i < D; ++i) gr[i] += wgt[c] * ((val[c][1 + 2 * i] - val[c][2 + 2 * i]) / span[c][i]);
     }
     if (V) V[p] = (R)v;
     if (dV)
-        for (int i = 0; i < g.d; ++i) dV[p * dvs + i] = (R)gr[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) dV[p * dvs + i] = (R)gr[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -353,25 +373,29 @@ int launch_harmonic(wtmd_t* h, bool accumulate)
     return WTMD_OK;
 }
 
+template <typename X, typename R>
+static cudaError_t grid_bias_go(wtmd_t* h, const GridPrm& g, const X* xi, int xs, long long P, R* V, R* dV, int dvs,
+                                bool pdl)
+{
+    const dim3 blocks((unsigned)((P + 127) / 128)), threads(128);
+    auto k = g.d == 1 ? grid_bias_kernel<1, X, R> : (g.d == 2 ? grid_bias_kernel<2, X, R> : grid_bias_kernel<3, X, R>);
+    if (pdl) return launch_pdl(k, blocks, threads, 0, h->stream, g, (const double*)h->grid, xi, xs, P, V, dV, dvs);
+    k<<<blocks, threads, 0, h->stream>>>(g, h->grid, xi, xs, P, V, dV, dvs);
+    return cudaGetLastError();
+}
+
 int launch_grid_bias(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P, void* V, void* dV, int dvs, bool pdl)
 {
     if (P <= 0) return WTMD_OK;
     const GridPrm g = grid_prm(h);
-    const dim3 blocks((unsigned)((P + 127) / 128)), threads(128);
     cudaError_t e;
-    auto go = [&](auto kern, auto xip, auto Vp, auto dVp) {
-        if (pdl) return launch_pdl(kern, blocks, threads, 0, h->stream, g, (const double*)h->grid, xip, xs, (long long)P,
-                                   Vp, dVp, dvs);
-        kern<<<blocks, threads, 0, h->stream>>>(g, h->grid, xip, xs, (long long)P, Vp, dVp, dvs);
-        return cudaGetLastError();
-    };
     if (h->prec == WTMD_F32) {
         if (xi_f64)
-            e = go(grid_bias_kernel<double, float>, (const double*)xi, (float*)V, (float*)dV);
+            e = grid_bias_go(h, g, (const double*)xi, xs, (long long)P, (float*)V, (float*)dV, dvs, pdl);
         else
-            e = go(grid_bias_kernel<float, float>, (const float*)xi, (float*)V, (float*)dV);
+            e = grid_bias_go(h, g, (const float*)xi, xs, (long long)P, (float*)V, (float*)dV, dvs, pdl);
     } else {
-        e = go(grid_bias_kernel<double, double>, (const double*)xi, (double*)V, (double*)dV);
+        e = grid_bias_go(h, g, (const double*)xi, xs, (long long)P, (double*)V, (double*)dV, dvs, pdl);
     }
     mark(h, "grid_bias");
     WTMD_CUDA_TRY(h, e);
