@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-walkers", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-grid-bias", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the Mueller-Brown and chain-adjoint figures")
     ap.add_argument("--case", choices=["hills", "walkers", "mlp", "grid", "cvs"], default=None,
                     help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
     return ap.parse_args()
@@ -533,25 +534,24 @@ def run_ours(args, rank, world):
     kernels_per_step = len(prof)
     n_hills = m.counters()[1]
 
-    # end to end through the public API with host buffers: the full state
-    # (positions, velocities, forces) lives in one [3][N][4] buffer bound as
-    # three views, so each step moves it in with one copy from pinned host
-    # memory and out with one copy
+    # end to end through the C ABI with host buffers (wtmd_step_host): the
+    # full state (positions, velocities, forces) lives in one pinned host
+    # buffer [3][N][4] and continues through it step after step; the library
+    # copies it into the bound packed device block, steps, and copies it back
+    # out (one captured graph per call)
     state = torch.stack([pos, vel, F]).contiguous()
     m.bind(state[0], state[1], state[2])
-    m.step_n(3, check=True)  # capture the graphs for the new binding
+    m.step_n(3, check=True)  # forces valid at the bound state
     hst = torch.empty_like(state, device="cpu").pin_memory()
     hst.copy_(state.cpu())
-    ost = torch.empty_like(hst).pin_memory()
+    m.step_host(hst, wait=True)  # captures the host-buffer graph
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
     for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda._sleep(SLACK_CYCLES)
         ee[i][0].record(stream)
-        state.copy_(hst, non_blocking=True)
-        m.step_n(1, check=False)
-        ost.copy_(state, non_blocking=True)
+        m.step_host(hst, wait=False)
         ee[i][1].record(stream)
     torch.cuda.synchronize()
     m.check()
@@ -564,9 +564,151 @@ def run_ours(args, rank, world):
     walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
     sur = None if args.no_surrogate else surrogate_bench(wt, torch, dev, flush, args.steps)
     gridb = None if args.no_grid_bias else grid_bias_bench(wt, torch, dev, flush, args.steps, rank)
-    return dict(hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    mbb = None if args.no_configs else mueller_brown_bench(wt, torch)
+    adj = None if args.no_configs else chain_adjoint_bench(wt, torch, flush)
+    return dict(mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
+
+
+MB_STEPS, MB_BINS, MB_LO, MB_HI = 100_000, (60, 60), (-1.5, -0.5), (1.2, 2.2)
+
+
+def mueller_brown_energy(x, y):
+    """The Mueller-Brown potential (Mueller & Brown, Theor. Chim. Acta 53, 75
+    (1979)), the exact free energy of a particle whose CVs are its own x, y:
+    the reference the recovered free energy is compared with."""
+    A = (-200.0, -100.0, -170.0, 15.0)
+    a = (-1.0, -1.0, -6.5, 0.7)
+    b = (0.0, 0.0, 11.0, 0.6)
+    c = (-10.0, -10.0, -6.5, 0.7)
+    x0 = (1.0, 0.0, -0.5, -1.0)
+    y0 = (0.0, 0.5, 1.5, 1.0)
+    return sum(A[k] * np.exp(a[k] * (x - x0[k]) ** 2 + b[k] * (x - x0[k]) * (y - y0[k]) + c[k] * (y - y0[k]) ** 2)
+               for k in range(4))
+
+
+def _mb_run(wt, torch, steps, dt, friction, w0, stride):
+    kT = 15.0
+    m = wt.Wtmd(precision="f64", sigma=(0.05, 0.05), w0=w0, gamma=10.0, kT=kT, stride=stride,
+                capacity=steps // stride + 16, seed=0, engine="mb", walker_sizes=[1], dims=2, dt=dt, friction=friction,
+                grid=(MB_BINS, MB_LO, MB_HI))
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=1)
+    pos = wt.particles(np.array([[-0.558, 1.442, 0.0]]), torch.float64)
+    vel = wt.particles(np.zeros((1, 3)), torch.float64)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    m.step_n(steps, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    m.check()
+    ms = e0.elapsed_time(e1)
+    hills = m.hills_read()
+    Fg = m.fes_grid().double().cpu().numpy().reshape(MB_BINS)
+    m.close()
+    cx, cy = [MB_LO[i] + (np.arange(MB_BINS[i]) + 0.5) * (MB_HI[i] - MB_LO[i]) / MB_BINS[i] for i in range(2)]
+    U = mueller_brown_energy(*np.meshgrid(cx, cy, indexing="ij"))
+    vis = np.zeros(MB_BINS, bool)
+    for hx, hy in hills[:, :2]:
+        i = int((hx - MB_LO[0]) / (MB_HI[0] - MB_LO[0]) * MB_BINS[0])
+        j = int((hy - MB_LO[1]) / (MB_HI[1] - MB_LO[1]) * MB_BINS[1])
+        if 0 <= i < MB_BINS[0] and 0 <= j < MB_BINS[1]:
+            vis[i, j] = True
+    mask = vis & (U < U.min() + 5 * kT)
+    d = (Fg - U)[mask]
+    d = d - d.mean() if d.size else d
+    return {"steps": steps, "dt": dt, "friction": friction, "w0": w0, "stride": stride, "ms": ms,
+            "steps_per_s": steps / (ms * 1e-3), "hills": int(hills.shape[0]), "visited_cells": int(mask.sum()),
+            "fes_max_err_kT": float(np.abs(d).max() / kT) if d.size else None,
+            "fes_rms_err_kT": float(np.sqrt(np.mean(d ** 2)) / kT) if d.size else None,
+            "fes_span_kT": float((U[mask].max() - U[mask].min()) / kT) if d.size else None}
+
+
+def mueller_brown_bench(wt, torch):
+    """The single-particle Mueller-Brown configuration as specified: BAOAB
+    dt = 1e-4, friction 1, kT = 15, FP64; WTMD on (x, y), sigma 0.05, w0 1,
+    gamma 10, a hill every 100 steps, 1e5 steps (1000 hills), Philox seed 0,
+    started in the deepest minimum.  MD steps/s of the whole run (one step_n
+    call, CUDA graph replays, including the one-time graph capture) and the
+    free energy -(gamma/(gamma-1)) V_grid against U_MB on the visited cells
+    (cells holding a hill centre) up to 5 kT above the minimum, after
+    removing the mean offset.  In 1e5 steps of dt = 1e-4 the particle has
+    not filled the basins; a second run with larger steps, friction and
+    hills (dt = 2e-3, friction 5, w0 = 0.5, a hill every 20 steps, 3e5
+    steps) shows the recovered free energy once it has."""
+    return {"workload": "single particle on Mueller-Brown, kT=15, FP64; WTMD on (x,y), sigma=0.05, gamma=10, "
+                        "Philox seed 0; 60x60 FP64 grid over [-1.5,1.2]x[-0.5,2.2]",
+            "as_specified": _mb_run(wt, torch, MB_STEPS, 1e-4, 1.0, 1.0, 100),
+            "converging": _mb_run(wt, torch, 300_000, 2e-3, 5.0, 0.5, 20)}
+
+
+def chain_adjoint_bench(wt, torch, flush):
+    """1024 replicas of the 22-bead chain, dihedral CVs 5-7-9-15 and
+    7-9-15-17, FP32: CV forward + hand-written adjoint (J^T g) per
+    evaluation, timed with CUDA events (L2 flushed between evaluations), and
+    the adjoint's error against central finite differences of the FP64
+    forward of g . xi on 256 sampled coordinates."""
+    import synth
+
+    W = 1024
+    x = synth.chain_replicas(W, 22, seed=2)
+    spec = dict(sigma=(0.35, 0.35), gamma=6.0, capacity=16, engine="chain", walker_sizes=[22] * W)
+    hs = {}
+    for prec in ("f32", "f64"):
+        hm = wt.Wtmd(precision=prec, **spec)
+        hm.cv_define(wt.CV_DIHEDRAL, a=[5, 7, 9, 15], period=2 * np.pi)
+        hm.cv_define(wt.CV_DIHEDRAL, a=[7, 9, 15, 17], period=2 * np.pi)
+        hs[prec] = hm
+    m = hs["f32"]
+    pos = wt.particles(x.astype(np.float32).astype(np.float64), torch.float32)
+    g = torch.tensor(synth.rng(3).normal(size=(W, 2)), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        m.cv_forward(pos)
+        m.cv_adjoint(g)
+    reps = 50
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        flush.fill_(1.0)
+        torch.cuda._sleep(SLACK_CYCLES)
+        a.record(stream)
+        m.cv_forward(pos)
+        out = m.cv_adjoint(g)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    adj = out[:, :3].double().cpu().numpy()
+    # finite differences of g . xi(x) with the FP64 forward at the FP32-rounded positions
+    x32 = x.astype(np.float32).astype(np.float64)
+    gd = g.double().cpu().numpy()
+    r = synth.rng(17)
+    idx = [(int(r.integers(0, W * 22)), int(r.integers(0, 3))) for _ in range(256)]
+    h = 1e-5
+    xp = x32
+    fd = []
+    m64 = hs["f64"]
+    for (i, k) in idx:
+        xs = []
+        for sgn in (1.0, -1.0):
+            xq = xp.copy()
+            xq[i, k] += sgn * h
+            xi = m64.cv_forward(wt.particles(xq, torch.float64)).double().cpu().numpy()
+            xs.append(float((gd * xi).sum()))
+        fd.append((xs[0] - xs[1]) / (2 * h))
+    fd = np.array(fd)
+    ad = np.array([adj[i, k] for (i, k) in idx])
+    for hm in hs.values():
+        hm.close()
+    return {"workload": "1024 replicas of a 22-bead chain (bond 1.0, angle 109.47 deg, random torsions), dihedral CVs "
+                        "5-7-9-15 and 7-9-15-17, FP32 forward + adjoint",
+            "ms_per_eval": ms, "adjoint_evals_per_s": W / (ms * 1e-3), "launches_per_eval": "forward + adjoint",
+            "fd_samples": len(idx), "fd_max_abs_err": float(np.abs(ad - fd).max()),
+            "fd_rel_err": float(np.linalg.norm(ad - fd) / np.linalg.norm(fd))}
 
 
 GRID_BINS = 256  # cells per CV of the grid-read bias figure (dx = 12 sigma / 256)
@@ -889,6 +1031,8 @@ def main():
         "walkers_256_clusters": r["walkers"],
         "surrogate_1e6_hills": r["surrogate"],
         "grid_bias_1e5_hills": r["grid_bias"],
+        "mueller_brown_1e5_steps": r["mueller_brown"],
+        "chain_1024_adjoint": r["chain_adjoint"],
     }
     if not args.no_cpu_baseline and world == 1:
         n, times, cores = cpu_baseline_oracle(seconds=15.0)

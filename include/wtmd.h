@@ -171,6 +171,22 @@ int wtmd_bind(wtmd_t* h, void* pos, void* vel, void* force, int64_t n_atoms);
  * recorded by kernels surface at wtmd_check(). */
 int step_n(wtmd_t* h, int64_t n_steps);
 
+/* Steps with the state in host memory (the paper keeps particle data on the
+ * device, Sec. 2, Snapshot; this is the call for callers whose state lives
+ * on the host).  in_host and out_host: [3][n_atoms][4] Real = positions,
+ * velocities, forces (the forces must be those at the positions, as a
+ * previous call returned them); out_host may equal in_host.  The state is
+ * copied into the bound arrays, n_steps steps run, and the state is copied
+ * back, all on the handle's stream.  When the bound arrays are one packed
+ * [3][n_atoms][4] block, both buffers are pinned (page-locked) and
+ * n_steps == 1, the copies and the step run as one captured CUDA graph
+ * (captured on the first call with those buffers).  wait != 0 synchronizes
+ * before returning; with wait == 0 the call returns after enqueueing and the
+ * buffers must stay valid (and out_host unread) until the stream reaches
+ * the copies.  Errors: WTMD_EINVAL (n_steps < 1, null buffers, arrays not
+ * bound, CVs not all defined), those of step_n, WTMD_ECUDA. */
+int wtmd_step_host(wtmd_t* h, const void* in_host, void* out_host, int64_t n_steps, int32_t wait);
+
 /* Synchronize the handle's stream and return the first error a kernel
  * recorded since the last check (WTMD_ECAPACITY, WTMD_ENUMERIC, WTMD_ECELL,
  * WTMD_ETIMEOUT), or a CUDA error; clears the recorded status. */

@@ -71,7 +71,8 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_autotune", "wtmd_surrogate", "wtmd_surrogate_config", "wtmd_surrogate_fit", "wtmd_surrogate_status",
            "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune",
            "wtmd_grid_eval", "wtmd_bias_source", "wtmd_checkpoint_size", "wtmd_checkpoint_save",
-           "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate"]
+           "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate",
+           "wtmd_step_host"]
 
 BIAS_HILLS, BIAS_GRID, BIAS_HARMONIC = 0, 1, 2
 
@@ -127,6 +128,7 @@ def lib() -> C.CDLL:
     L.wtmd_checkpoint_save.argtypes = [vp, vp, i64]
     L.wtmd_checkpoint_load.argtypes = [vp, vp, i64]
     L.wtmd_harmonic.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wtmd_step_host.argtypes = [vp, vp, vp, i64, i32]
     L.wtmd_umbrella_stats.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64), i32]
     L.wtmd_umbrella_integrate.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wtmd_cv_forward.argtypes = [vp, vp, vp]
@@ -269,6 +271,19 @@ class Wtmd:
         self._err(lib().step_n(self.h, int(n)), "step_n")
         if check:
             self.check()
+
+    def step_host(self, state_in, state_out=None, n: int = 1, wait: bool = True):
+        """n steps with the state [3][N][4] (positions, velocities, forces) in
+        host memory: a CPU tensor or array, pinned for the single-graph path;
+        state_out defaults to state_in."""
+        self._stream()
+        out = state_in if state_out is None else state_out
+
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        self._err(lib().wtmd_step_host(self.h, C.c_void_p(ptr(state_in)), C.c_void_p(ptr(out)), int(n),
+                                       1 if wait else 0), "wtmd_step_host")
 
     def check(self):
         self._stream()

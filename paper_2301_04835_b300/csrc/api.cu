@@ -51,8 +51,12 @@ static void drop_graphs(wtmd_t* h)
 {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->graph1) cudaGraphExecDestroy(h->graph1);
+    if (h->graph_host) cudaGraphExecDestroy(h->graph_host);
     h->graph = nullptr;
     h->graph1 = nullptr;
+    h->graph_host = nullptr;
+    h->gh_in = nullptr;
+    h->gh_out = nullptr;
 }
 
 namespace wtmd {
@@ -592,6 +596,88 @@ extern "C" int step_n(wtmd_t* h, int64_t n_steps)
         surrogate_advanced(h, seg);
         left -= seg;
     }
+    return WTMD_OK;
+}
+
+// One captured graph: the packed state [3][N][4] in from pinned host memory,
+// one step, the state out to pinned host memory.
+static int capture_host(wtmd_t* h, const void* in, void* out, size_t bytes)
+{
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->stream = user;
+        FAIL(h, WTMD_ECUDA, "begin capture");
+    }
+    int rc = WTMD_OK;
+    if (cudaMemcpyAsync(h->pos, in, bytes, cudaMemcpyHostToDevice, h->cap_stream) != cudaSuccess) rc = WTMD_ECUDA;
+    if (!rc) rc = enqueue_step(h);
+    if (!rc && cudaMemcpyAsync(out, h->pos, bytes, cudaMemcpyDeviceToHost, h->cap_stream) != cudaSuccess)
+        rc = WTMD_ECUDA;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->stream = user;
+    if (rc != WTMD_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        FAIL(h, rc ? rc : WTMD_ECUDA, "capture of the host-buffer step");
+    }
+    e = cudaGraphInstantiate(&h->graph_host, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph_host = nullptr;
+        FAIL(h, WTMD_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    }
+    h->gh_in = in;
+    h->gh_out = out;
+    return WTMD_OK;
+}
+
+static bool pinned(const void* p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+extern "C" int wtmd_step_host(wtmd_t* h, const void* in_host, void* out_host, int64_t n_steps, int32_t wait)
+{
+    if (!h) return WTMD_EINVAL;
+    if (n_steps < 1 || !in_host || !out_host) FAIL(h, WTMD_EINVAL, "need n_steps >= 1 and host buffers");
+    int rc = ready(h);
+    if (rc) return rc;
+    if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
+    const size_t pb = r4sz(h) * (size_t)h->N;
+    const bool packed = (char*)h->vel == (char*)h->pos + pb && (char*)h->force == (char*)h->vel + pb;
+    const bool one_graph = packed && n_steps == 1 && h->forces_valid && !h->persistent && !surrogate_k0(h) &&
+                           !h->no_graph && !h->no_host_graph && !h->prof && pinned(in_host) && pinned(out_host);
+    if (one_graph) {
+        if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+        if (!h->graph_host || h->gh_in != in_host || h->gh_out != out_host) {
+            if (h->graph_host) cudaGraphExecDestroy(h->graph_host);
+            h->graph_host = nullptr;
+            if (capture_host(h, in_host, out_host, 3 * pb) != WTMD_OK) {
+                cudaGetLastError();
+                h->no_host_graph = true;  // this launch sequence cannot be captured here
+            }
+        }
+        if (h->graph_host) {
+            WTMD_CUDA_TRY(h, cudaGraphLaunch(h->graph_host, h->stream));
+            if (wait) WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            return WTMD_OK;
+        }
+    }
+    const char* src = (const char*)in_host;
+    void* dev[3] = {h->pos, h->vel, h->force};
+    for (int k = 0; k < 3; ++k)
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(dev[k], src + k * pb, pb, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = step_n(h, n_steps))) return rc;
+    char* dst = (char*)out_host;
+    for (int k = 0; k < 3; ++k)
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(dst + k * pb, dev[k], pb, cudaMemcpyDeviceToHost, h->stream));
+    if (wait) WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return WTMD_OK;
 }
 

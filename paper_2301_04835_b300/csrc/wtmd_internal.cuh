@@ -365,6 +365,10 @@ struct wtmd_t {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     cudaGraphExec_t graph1 = nullptr;
+    cudaGraphExec_t graph_host = nullptr; // host state in -> one step -> host state out (wtmd_step_host)
+    const void* gh_in = nullptr;          // the host buffers graph_host was captured with
+    void* gh_out = nullptr;
+    bool no_host_graph = false;           // its capture failed: copy around step_n instead
     bool persistent = false;        // multi-walker step as one persistent launch
     bool bias_grid = false;         // step/bias_eval read V, dV/dxi from the grid (WTMD_BIAS_GRID)
     bool bias_harm = false;         // harmonic bias about per-walker centres (WTMD_BIAS_HARMONIC)

@@ -553,3 +553,39 @@ def test_new_cv_definitions_are_validated():
         with pytest.raises(wt.WtmdError):
             m.cv_define(**bad)
     m.cv_define(wt.CV_GYRATION, a=None, axis=wt.GY_ANISOTROPY)
+
+
+def test_mueller_brown_free_energy_recovered_on_gpu():
+    """The whole GPU step (engine, CVs, hills sum, scatter, deposition, FP64
+    grid) recovers the Mueller-Brown free energy: -(gamma/(gamma-1)) V_grid
+    matches U_MB up to a constant within 0.5 kT on visited cells up to 5 kT
+    above the minimum (the CVs are the particle's own x, y, so A = U + C;
+    Sec. 2.1, Eq. (free-energy)).  Same parameters as the oracle's pin."""
+    import oracle as o
+
+    wt = _wt()
+    bins, lo, hi, kT = (60, 60), (-1.5, -0.5), (1.2, 2.2), 15.0
+    m = wt.Wtmd(precision="f64", sigma=(0.05, 0.05), w0=0.5, gamma=10.0, kT=kT, stride=20, capacity=20000, seed=0,
+                engine="mb", walker_sizes=[1], dims=2, dt=2e-3, friction=5.0, grid=(bins, lo, hi))
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=1)
+    pos = wt.particles(np.array([[-0.558, 1.442, 0.0]]), torch.float64)
+    vel = wt.particles(np.zeros((1, 3)), torch.float64)
+    m.bind(pos, vel, torch.zeros_like(pos))
+    m.step_n(300000)
+    hills = m.hills_read()
+    assert hills.shape[0] == 15000
+    F = to_np(m.fes_grid()).reshape(bins)
+    cx, cy = o.grid_centres(bins, lo, hi)
+    U = np.array([[o.mb(a, b)[0] for b in cy] for a in cx])
+    vis = np.zeros(bins, bool)
+    for hx, hy in hills[:, :2]:
+        i, j = int((hx - lo[0]) / (hi[0] - lo[0]) * bins[0]), int((hy - lo[1]) / (hi[1] - lo[1]) * bins[1])
+        if 0 <= i < bins[0] and 0 <= j < bins[1]:
+            vis[i, j] = True
+    mask = vis & (U < U.min() + 5 * kT)
+    assert mask.sum() > 200
+    d = (F - U)[mask]
+    d -= d.mean()
+    assert np.abs(d).max() < 0.5 * kT
+    assert np.sqrt(np.mean(d ** 2)) < 0.25 * kT
