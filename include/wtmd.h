@@ -366,11 +366,15 @@ int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice);
 /* Autotuner of the hills-sum launch plan (Sec. 2.1.5 sum; the plan splits the
  * hill list over CTAs and sets the hill lanes per point) for P evaluation
  * points: times every (lanes per point 1/4/32/256, splits 1 ... 1184)
- * candidate on the handle's current hills at P points placed at the CV
- * centre, and keeps the fastest for later sums with P points (step_n with
- * W = P walkers, bias_eval, hills_eval).  choice (host [2], may be NULL)
- * receives (lanes per point, splits); ms (host, may be NULL) the time of one
- * sum.  Synchronizes; drops captured step graphs. */
+ * candidate of the copy-ring kernel and, on FP32 handles with P <= 8, of
+ * the few-points kernel (lanes per point reported as 0: every thread takes
+ * whole hill pairs from global memory for all P points) on the handle's
+ * current hills at P points placed at the CV centre, and keeps the fastest
+ * for later sums with P points (step_n with W = P walkers, bias_eval,
+ * hills_eval).  choice (host [2], may be NULL) receives (lanes per point,
+ * splits); ms (host, may be NULL) the time of one sum.  Synchronizes; drops
+ * captured step graphs.  Without tuning, FP32 sums of P <= 8 points use the
+ * few-points kernel. */
 int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms);
 
 /* Hills sum for callers that cannot allocate device memory (the paper has no

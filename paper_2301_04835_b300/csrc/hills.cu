@@ -22,6 +22,11 @@
 //     accumulators after every 128-pair chunk (no FP64 in the loop),
 //     and the hill-range splits are reduced in a fixed order by the CTA that
 //     finishes last (one launch, deterministic, no CTA waits for another).
+// Few points (P <= 8, e.g. the CVs of one walker in a step) would leave the
+// copy ring's pipeline mostly filling and draining, so a second FP32 kernel
+// takes whole hill pairs straight from global memory, all P points per
+// thread, with the same arithmetic and the same fixed-order reductions; the
+// plan autotuner times both kinds.
 // FP64 path: the same sum in double with exp(), for parity at 1e-12.
 #include <algorithm>
 #include <cmath>
@@ -81,6 +86,117 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
     // launch starts from a clean ticket (the status word reports the error)
     hills_f32_task<D, TH, PER, PT>(hp, k0p, cnt, xi, xs, P, ctr, prm, partial, out.status, blockIdx.x, blockIdx.y,
                                    gridDim.y, ring, bar, true);
+    finalize_if_last_cf(partial, P, out);
+}
+
+// Few points (P <= SMALL_P, e.g. one walker's CVs in a step): the hill range
+// is split over the CTAs and every thread takes hill pairs q = tid, tid + HB,
+// ... of its CTA's range straight from global memory (32-byte records,
+// coalesced across the warp), its first pairs loaded before the dependency
+// wait since the hills do not depend on the preceding kernel.  Each pair is
+// evaluated against every point with the same packed arithmetic as the
+// copy-ring kernel; per-thread sums are folded into compensated FP32 and
+// reduced over the CTA in a fixed order, and the splits by the last CTA.
+// No copy ring and no mbarrier: the latency of one load round trip, not of
+// a pipeline's fill.
+constexpr int SMALL_P = 8;
+
+template <int D, bool PER, int NP, typename PT>
+__global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __restrict__ hp,
+                                                             const long long* __restrict__ k0p,
+                                                             const long long* __restrict__ cnt,
+                                                             const PT* __restrict__ xi, int xs, int P,
+                                                             const double* __restrict__ ctr, HillPrmF32 prm,
+                                                             dbl4* __restrict__ partial, HillOut<float> out)
+{
+    const int tid = threadIdx.x;
+    const long long k0 = k0p ? *k0p : 0;
+    const long long count = *cnt;
+    const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
+    hp += (size_t)(k0 >> 1) * 2;
+    const long long per = (npairs + gridDim.y - 1) / gridDim.y;
+    const long long q0 = (long long)blockIdx.y * per;
+    const long long q1 = q0 + per < npairs ? q0 + per : npairs;
+    // this thread's pairs in batches of SB, each batch's loads issued before
+    // any is used; the first batch before the wait
+    constexpr int SB = 4;
+    float4 A[SB], B[SB];
+    const long long qa = q0 + tid;
+    auto load_batch = [&](long long qb) {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+            const long long q = qb + (long long)j * HB;
+            if (q < q1) {
+                A[j] = __ldg(hp + 2 * q);
+                B[j] = __ldg(hp + 2 * q + 1);
+            } else {  // no hill: zero weight (height 2^-inf)
+                A[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                B[j] = make_float4(0.f, 0.f, INFINITY, INFINITY);
+            }
+        }
+    };
+    load_batch(qa);
+    pdl_wait();
+    pdl_trigger();
+    float2 X[NP][3];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float v = 0.f;
+            if (p < P && i < D) v = (float)(((double)xi[(size_t)p * xs + i] - ctr[i]) * prm.a[i]);
+            X[p][i] = make_float2(v, v);
+        }
+    float2 v[NP], g0[NP], g1[NP], g2[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
+    for (long long qb = qa; qb < q1; qb += (long long)SB * HB) {
+        if (qb != qa) load_batch(qb);
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                if (p >= P) break;
+                float2 d0 = __fadd2_rn(X[p][0], make_float2(A[j].x, A[j].y));
+                if constexpr (PER) d0 = wrap2(d0, prm.per[0], prm.iper[0]);
+                float2 t = __ffma2_rn(d0, d0, make_float2(B[j].z, B[j].w));
+                float2 d1, d2;
+                if constexpr (D >= 2) {
+                    d1 = __fadd2_rn(X[p][1], make_float2(A[j].z, A[j].w));
+                    if constexpr (PER) d1 = wrap2(d1, prm.per[1], prm.iper[1]);
+                    t = __ffma2_rn(d1, d1, t);
+                }
+                if constexpr (D >= 3) {
+                    d2 = __fadd2_rn(X[p][2], make_float2(B[j].x, B[j].y));
+                    if constexpr (PER) d2 = wrap2(d2, prm.per[2], prm.iper[2]);
+                    t = __ffma2_rn(d2, d2, t);
+                }
+                const float2 e = make_float2(ex2_approx(-t.x), ex2_approx(-t.y));
+                v[p] = __fadd2_rn(v[p], e);
+                g0[p] = __ffma2_rn(e, d0, g0[p]);
+                if constexpr (D >= 2) g1[p] = __ffma2_rn(e, d1, g1[p]);
+                if constexpr (D >= 3) g2[p] = __ffma2_rn(e, d2, g2[p]);
+            }
+        }
+    }
+    __shared__ CF4 red[HB / 32];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (p >= P) break;
+        CF4 a{};
+        a.v[0] = cf_add(cf_add(a.v[0], v[p].x), v[p].y);
+        a.v[1] = cf_add(cf_add(a.v[1], g0[p].x), g0[p].y);
+        a.v[2] = cf_add(cf_add(a.v[2], g1[p].x), g1[p].y);
+        a.v[3] = cf_add(cf_add(a.v[3], g2[p].x), g2[p].y);
+        cf4_lane_sum<32>(a);
+        __syncthreads();  // red[] free from the previous point
+        if (tid % 32 == 0) red[tid / 32] = a;
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < HB / 32; ++w) cf4_add(a, red[w]);
+            store_cf4(partial + (size_t)blockIdx.y * P + p, a);
+        }
+    }
     finalize_if_last_cf(partial, P, out);
 }
 
@@ -177,14 +293,14 @@ static int num_sms()
 
 // Tile heuristic: few points -> many hill lanes per point; many points ->
 // one thread per point.  Splits fill ~4 CTAs per SM over the hill range.
-static Plan plan_for(long long P, long long cap_pairs)
+static Plan plan_for(long long P, long long cap_pairs, bool fp32)
 {
     Plan pl;
     if (P >= 1024) pl.th = 1;
     else if (P >= 64) pl.th = 4;
-    else if (P >= 8) pl.th = 32;
-    else pl.th = 256;
-    const long long tp = HB / pl.th;
+    else if (P > SMALL_P) pl.th = 32;
+    else pl.th = fp32 ? 0 : 256;  // 0: the few-points kernel (FP32 handles)
+    const long long tp = pl.th ? HB / pl.th : P;
     const long long tiles = (P + tp - 1) / tp;
     // few points: ~2 CTAs per SM (each CTA then streams several chunks and
     // the final reduction stays short); many points: ~4 per SM
@@ -212,11 +328,28 @@ static void launch_f32_k(dim3 grid, cudaStream_t st, bool pdl, const float4* hp,
         hills_f32_kernel<D, TH, PER, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
 }
 
+template <int D, bool PER, int NP, typename PT>
+static void launch_f32_small(dim3 grid, cudaStream_t st, bool pdl, const float4* hp, const long long* k0p,
+                             const long long* cnt, const PT* xi, int xs, int P, const double* ctr,
+                             const HillPrmF32& prm, dbl4* part, const HillOut<float>& o)
+{
+    if (pdl)
+        launch_pdl(hills_f32_small_kernel<D, PER, NP, PT>, grid, dim3(HB), 0, st, hp, k0p, cnt, xi, xs, P, ctr, prm,
+                   part, o);
+    else
+        hills_f32_small_kernel<D, PER, NP, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+}
+
 template <int D, bool PER, typename PT>
 static void launch_f32_d(int th, dim3 grid, cudaStream_t st, bool pdl, const float4* hp, const long long* k0p,
                          const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
                          dbl4* part, const HillOut<float>& o)
 {
+    if (th == 0) {  // the few-points kernel (P <= SMALL_P), grid (1, splits)
+        if (P == 1) launch_f32_small<D, PER, 1, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+        else launch_f32_small<D, PER, SMALL_P, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
+        return;
+    }
     switch (th) {
     case 1: launch_f32_k<D, 1, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
     case 4: launch_f32_k<D, 4, PER, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o); break;
@@ -256,7 +389,7 @@ static void launch_f64_t(int th, dim3 grid, cudaStream_t st, const dbl4* hills, 
 // plan launch_hills will pick (call outside graph capture).
 int launch_hills_partial_prealloc(wtmd_t* h, int64_t P)
 {
-    Plan pl = plan_for(P, h->cap_pairs);
+    Plan pl = plan_for(P, h->cap_pairs, h->prec == WTMD_F32);
     for (auto& t : h->tuned)
         if (t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
     const size_t need = (size_t)pl.split * (size_t)P * sizeof(dbl4);
@@ -285,10 +418,11 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         h->err = "hills: too many points";
         return WTMD_EINVAL;
     }
-    Plan pl = plan_for(P, cap_pairs);
+    Plan pl = plan_for(P, cap_pairs, h->prec == WTMD_F32);
     for (auto& t : h->tuned)
         if (max_hills <= 0 && t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
-    const int tp = HB / pl.th;
+    if (pl.th == 0 && (h->prec != WTMD_F32 || P > SMALL_P)) pl.th = 256;  // a tuned plan for another handle kind
+    const int tp = pl.th ? HB / pl.th : (int)P;
     const long long tiles = (P + tp - 1) / tp;
     if (tiles > 0x7fffffff) return WTMD_EINVAL;
     const size_t need = (size_t)pl.split * (size_t)P * sizeof(dbl4);
@@ -395,16 +529,19 @@ int hills_tune(wtmd_t* h, int64_t P, int* th_out, int* split_out, double* ms_out
                    }),
                    h->tuned.end());
     const long long nch = (h->cap_pairs + CHUNK - 1) / CHUNK;
-    const int ths[] = {1, 4, 32, 256};
+    // 0: the few-points kernel, a candidate for FP32 handles with P <= SMALL_P
+    const int ths[] = {0, 1, 4, 32, 256};
     const int splits[] = {1, 2, 4, 8, 16, 32, 64, 96, 128, 148, 192, 296, 444, 592, 888, 1184};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     double best = 1e30;
-    Tuned bt = {plan_for(P, h->cap_pairs).th, plan_for(P, h->cap_pairs).split};
+    const Plan p0 = plan_for(P, h->cap_pairs, h->prec == WTMD_F32);
+    Tuned bt = {p0.th, p0.split};
     int rc = WTMD_OK;
     for (int th : ths) {
-        const long long tiles = (P + HB / th - 1) / (HB / th);
+        if (th == 0 && (h->prec != WTMD_F32 || P > SMALL_P)) continue;
+        const long long tiles = th ? (P + HB / th - 1) / (HB / th) : 1;
         for (int sp : splits) {
             if (sp > nch || tiles * sp > (1ll << 20) || (size_t)sp * P * sizeof(dbl4) > (256ull << 20)) continue;
             h->tuned.push_back({key, Tuned{th, sp}});

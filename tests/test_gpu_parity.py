@@ -127,6 +127,8 @@ HILL_CASES = [
     (3, False, 2100, 513),
     (3, True, 7, 999),
     (1, True, 1100, 4097),
+    (3, False, 1, 200001),   # few-points kernel: hundreds of splits, odd count
+    (2, True, 8, 100003),
 ]
 
 
@@ -476,7 +478,7 @@ def test_hills_tune_keeps_results():
     hills = synth.walk_hills(3000, c - 0.3, c + 0.3, 0.05, seed=4)
     m.hills_load(hills)
     th, sp, ms = m.hills_tune(1)
-    assert th in (1, 4, 32, 256) and sp >= 1 and ms > 0
+    assert th in (0, 1, 4, 32, 256) and sp >= 1 and ms > 0  # 0: the few-points kernel
     V, xi, dV = m.bias_eval(pos)
     Vr, dVr = o.hills_sum(to_np(xi), hills, spec["sigma"])
     _close_V(to_np(V), Vr, "f32")
