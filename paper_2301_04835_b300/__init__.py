@@ -586,6 +586,18 @@ def _cv_function():
     return CVFunction
 
 
+def load_config(name: str | None = None) -> dict:
+    """The five workloads of this library as data (configs.json beside this
+    module): method, engine and CV parameters and the recipe of the seeded
+    synthetic inputs.  name: one of mueller_brown, lj4096, chain1024,
+    walkers256, surrogate32768; None returns all of them."""
+    import json
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs.json")) as f:
+        cfg = json.load(f)
+    return cfg if name is None else cfg[name]
+
+
 def cv_apply(pos, handle):
     """Differentiable CV evaluation: xi = cv_apply(pos, handle)."""
     return _cv_function().apply(pos, handle)
