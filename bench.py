@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-grid-bias", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the Mueller-Brown and chain-adjoint figures")
-    ap.add_argument("--case", choices=["hills", "walkers", "mlp", "grid", "cvs"], default=None,
+    ap.add_argument("--case", choices=["hills", "hills1", "walkers", "mlp", "grid", "cvs"], default=None,
                     help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
     return ap.parse_args()
 
@@ -887,7 +887,8 @@ def run_case(name: str):
     """One representative launch configuration of a hot kernel, repeated a
     few times: `hills` = FP32 hills sum, 1e6 hills, 4096 points, d = 2;
     `walkers` = the 256-cluster persistent step; `mlp` = network inference at
-    4096 points and training steps on 4096 samples; `grid` = the 4096-atom
+    4096 points and training steps on 4096 samples; `hills1` = the FP32 sum of
+    1e5 hills at one point (the few-points kernel); `grid` = the 4096-atom
     step with the bias read from a 128x128 grid (1e4 hills) and the grid read
     at 4096 points; `cvs` = Distance, Angle and gyration-tensor CVs of 256
     walkers of 512 atoms (bias_eval, harmonic windows)."""
@@ -906,6 +907,17 @@ def run_case(name: str):
         pts = torch.tensor(synth.uniform_points(P, [0, 0], [1, 1], seed=P + 2), dtype=torch.float32, device=dev)
         V = torch.empty(P, dtype=torch.float32, device=dev)
         dV = torch.empty(P, 2, dtype=torch.float32, device=dev)
+        for _ in range(5):
+            m.hills_eval_into(pts, V, dV)
+    elif name == "hills1":
+        H = 100_000
+        m = wt.Wtmd(precision="f32", sigma=(0.05, 0.1), capacity=2 * H, walker_sizes=[1])
+        for i in range(2):
+            m.cv_define(wt.CV_COMPONENT, a=[0], axis=i)
+        m.hills_load(synth.uniform_hills(H, [0, 0], [1, 1], seed=13))
+        pts = torch.tensor(synth.uniform_points(1, [0, 0], [1, 1], seed=3), dtype=torch.float32, device=dev)
+        V = torch.empty(1, dtype=torch.float32, device=dev)
+        dV = torch.empty(1, 2, dtype=torch.float32, device=dev)
         for _ in range(5):
             m.hills_eval_into(pts, V, dV)
     elif name == "walkers":
