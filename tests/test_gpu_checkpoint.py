@@ -122,3 +122,22 @@ def test_checkpoint_is_validated():
     m.restore(blob)  # the handle is still usable after the refusals
     m.step_n(5)
     m.check()
+
+
+def test_persistent_walkers_resume_is_bitwise():
+    """The persistent multi-walker step (LJ clusters of uneven size sharing one
+    hill list, a hill per walker every 2 steps, FP64 grid) saved and resumed
+    in a fresh handle reproduces the uninterrupted run bitwise."""
+    from test_gpu_walkers import _setup, cluster_spec, shared_hills
+
+    spec, x, v = cluster_spec(stride=2, grid=((32, 32), (0.0, 0.0), (12.0, 1.0)))
+    hills = shared_hills(spec, x)
+    m, pos, vel, F = _setup(spec, x, v, hills, True)
+    m.step_n(6)
+    blob = m.checkpoint()
+    m.step_n(8)
+    ref = _state(m, pos, vel, F)
+    m2, p2, v2, F2 = _setup(spec, x, v, hills, True)
+    m2.restore(blob)
+    m2.step_n(8)
+    _same(ref, _state(m2, p2, v2, F2))
