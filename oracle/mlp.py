@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (same rule as the rest of `oracle/`): called by
 `tests/` and nothing else; shares no code with the CUDA library.
 
 The paper points to neural-network bias representations (its ANN and FUNN
-methods, Sec. 2.1.6) but prints no network for metadynamics; the surrogate
+methods, Secs. 2.1.7 and 2.1.8) but prints no network for metadynamics; the surrogate
 here is a plain 3 -> 64 -> 64 -> 1 perceptron with SiLU activations,
 z -> z * sigmoid(z), written from those definitions:
 

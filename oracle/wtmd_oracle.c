@@ -397,6 +397,10 @@ static void orc_eig3(const double S[3][3], double lam[3], double V[3][3])
 /* Evaluate one CV for one walker.  Returns 0 or -1 on bad input. */
 int orc_cv_eval(const orc_cv* cv, int64_t n, const double* x, const double* box, double* xi, double* J)
 {
+    /* the switching function is written for m = 2n only (orc_switch): any
+     * other exponent pair is refused, not evaluated as something else */
+    if ((cv->kind == ORC_CV_COORDINATION || cv->kind == ORC_CV_QPAIRS) && (cv->nn < 1 || cv->mm != 2 * cv->nn))
+        return -1;
     for (int64_t i = 0; i < 3 * n; ++i) J[i] = 0.0;
     switch (cv->kind) {
     case ORC_CV_COMPONENT: {

@@ -111,6 +111,80 @@ def test_chain_force_matches_energy_gradient():
     assert np.allclose(f.sum(0), 0.0, atol=1e-9)
 
 
+def test_chain_dimer_closed_form():
+    """A stretched dimer: only the bond term, U = kb/2 (r - r0)^2 and a
+    central force of magnitude kb |r - r0|."""
+    kb, r0 = 100.0, 1.0
+    for r in (0.8, 1.0, 1.3):
+        d = np.array([0.3, -0.4, 1.2])
+        d *= r / np.linalg.norm(d)
+        x = np.array([[0.2, 0.1, -0.3], [0.2, 0.1, -0.3]]) + np.array([[0, 0, 0], d])
+        U, f = o.chain(x, kb=kb, r0=r0, ka=50.0, kt=1.0)
+        assert U == pytest.approx(0.5 * kb * (r - r0) ** 2, rel=1e-13, abs=1e-14)
+        F1 = -kb * (r - r0) * d / r  # on bead 1, along +d when compressed
+        assert np.allclose(f[1], F1, rtol=1e-12, atol=1e-13)
+        assert np.allclose(f[0], -F1, rtol=1e-12, atol=1e-13)
+
+
+def test_chain_trimer_closed_form():
+    """A bent trimer with both bonds at r0: only the angle term,
+    U = ka/2 (theta - theta0)^2 with theta0 in radians; bead 0 on the x axis
+    and bead 2 at angle theta in the xy plane feel tangential forces of size
+    ka |theta - theta0| / r0."""
+    ka, r0, th0 = 50.0, 1.0, np.deg2rad(109.47)
+    for th in (np.deg2rad(90.0), np.deg2rad(109.47), np.deg2rad(150.0)):
+        x = np.array([[r0, 0.0, 0.0], [0.0, 0.0, 0.0], [r0 * np.cos(th), r0 * np.sin(th), 0.0]])
+        U, f = o.chain(x, kb=100.0, r0=r0, ka=ka, th0=th0, kt=1.0)
+        assert U == pytest.approx(0.5 * ka * (th - th0) ** 2, rel=1e-12, abs=1e-14)
+        g = ka * (th - th0) / r0  # dU/dtheta / r0
+        # moving bead 0 by +y closes the angle; moving bead 2 along
+        # (-sin th, cos th) opens it
+        assert np.allclose(f[0], [0.0, g, 0.0], rtol=1e-12, atol=1e-12)
+        assert np.allclose(f[2], -g * np.array([-np.sin(th), np.cos(th), 0.0]), rtol=1e-12, atol=1e-12)
+        assert np.allclose(f[1], -(f[0] + f[2]), rtol=1e-12, atol=1e-12)
+
+
+def _tetramer(r0, th0, phi):
+    """Four beads with bonds r0, both angles th0 and dihedral phi (cis = 0)."""
+    return np.array([
+        [r0 * np.cos(th0), r0 * np.sin(th0), 0.0],
+        [0.0, 0.0, 0.0],
+        [r0, 0.0, 0.0],
+        [r0 - r0 * np.cos(th0), r0 * np.sin(th0) * np.cos(phi), r0 * np.sin(th0) * np.sin(phi)],
+    ])
+
+
+def test_chain_tetramer_torsion_closed_form():
+    """A tetramer with bonds r0 and angles theta0 has only the torsion term
+    kt (1 + cos 3 phi): 2 kt at phi = 0, 0 at pi/3 and pi, kt at pi/2; the end
+    beads feel |dU/dphi| / (r0 sin theta0), normal to their bond plane."""
+    kt, r0, th0 = 1.0, 1.0, np.deg2rad(109.47)
+    for phi, Uc in ((0.0, 2.0), (np.pi / 3, 0.0), (np.pi, 0.0), (np.pi / 2, 1.0), (-np.pi / 2, 1.0)):
+        x = _tetramer(r0, th0, phi)
+        U, f = o.chain(x, kb=100.0, r0=r0, ka=50.0, th0=th0, kt=kt)
+        assert U == pytest.approx(kt * Uc, abs=1e-12)
+        mag = abs(3 * kt * np.sin(3 * phi)) / (r0 * np.sin(th0))
+        assert np.linalg.norm(f[0]) == pytest.approx(mag, rel=1e-10, abs=1e-10)
+        assert np.linalg.norm(f[3]) == pytest.approx(mag, rel=1e-10, abs=1e-10)
+        n012 = np.cross(x[0] - x[1], x[2] - x[1])
+        n123 = np.cross(x[1] - x[2], x[3] - x[2])
+        assert abs(np.dot(f[0], n012)) == pytest.approx(mag * np.linalg.norm(n012), rel=1e-10, abs=1e-10)
+        assert abs(np.dot(f[3], n123)) == pytest.approx(mag * np.linalg.norm(n123), rel=1e-10, abs=1e-10)
+        assert np.allclose(f.sum(0), 0.0, atol=1e-12)
+        assert np.allclose(np.cross(x, f).sum(0), 0.0, atol=1e-12)
+
+
+def test_coordination_refuses_m_not_2n():
+    """The switching function is defined here for m = 2n only; other exponent
+    pairs are refused instead of being evaluated as m = 2n."""
+    x = synth.rng(3).normal(size=(6, 3))
+    with pytest.raises(ValueError):
+        o.cv_eval(o.CV(o.CV_COORDINATION, a=[0, 1], r0=1.5, nn=6, mm=10), x)
+    with pytest.raises(ValueError):
+        o.cv_eval(o.CV(o.CV_QPAIRS, a=[0, 1, 2, 3], r0=1.5, nn=4, mm=12), x)
+    o.cv_eval(o.CV(o.CV_COORDINATION, a=[0, 1], r0=1.5, nn=5, mm=10), x)
+
+
 # --------------------------------------------------------------------------
 # Collective variables (Sec. 2.2)
 # --------------------------------------------------------------------------
