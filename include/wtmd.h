@@ -387,10 +387,12 @@ int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms);
  * [n_cv] double; period NULL or 0 = not periodic).  Calls no cudaMalloc,
  * cudaFree or other allocating routine: its partial sums use a fixed
  * library-owned device array of WTMD_STATIC_MAX_POINTS x 32 bytes (1 MiB)
- * that every GPU loading the library keeps until exit.  The first call on a
- * device looks the array's address up (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array: calls whose
- * kernels overlap on the GPU race, so serialize them.  Work is enqueued on
+ * that every GPU loading the library keeps until exit.  The first call in
+ * each CUDA context (for most callers: the first call on each device, in its
+ * primary context) looks the array's address up (cudaGetSymbolAddress) and
+ * keeps it for that context; make that first call before any stream capture.
+ * All calls share the array: calls whose kernels overlap on the GPU race, so
+ * serialize them.  Work is enqueued on
  * `stream` (cudaStream_t, NULL = default).  Errors: WTMD_EINVAL when
  * P > WTMD_STATIC_MAX_POINTS, for bad sizes, sigma <= 0, negative periods,
  * null or misaligned pointers; WTMD_ECUDA if a CUDA call fails. */
@@ -401,7 +403,7 @@ int wtmd_hills_eval_static(int32_t n_cv, const double* sigma, const double* peri
 
 /* ---- MLP surrogate of the hills sum ----------------------------------------
  * The paper represents biases by neural networks in its ANN and FUNN methods
- * (Sec. 2.1.6); for metadynamics the hills sum (Sec. 2.1.5) is kept and a
+ * (Secs. 2.1.7 and 2.1.8); for metadynamics the hills sum (Sec. 2.1.5) is kept and a
  * network V_nn stands in for its older part only:
  *     V(xi) = V_nn(xi) + sum_{k >= K} w_k exp(-sum_i (xi_i - s_ki)^2 / (2 sigma_i^2)),
  * where V_nn approximates the sum over hills [0, K), K a multiple of 256.

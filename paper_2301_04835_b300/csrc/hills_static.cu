@@ -17,6 +17,7 @@
 // different host threads) race on it, so serialize them.  Each call writes
 // every scratch entry it later reads, so the contents left by the previous
 // call never leak into a result.
+#include <cuda.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -33,24 +34,82 @@ constexpr long long kScratchEntries = WTMD_STATIC_MAX_POINTS;
 
 static __device__ __align__(256) dbl4 g_hills_scratch[kScratchEntries];
 
-// Device address of g_hills_scratch, one per device, looked up on the first
-// call made with that device current.
-constexpr int kMaxDevices = 128;
-static void* g_scratch_addr[kMaxDevices];
+// Device address of g_hills_scratch.  A __device__ array exists once per CUDA
+// context, and host code only holds a stand-in for it, so the address has to
+// be looked up (cudaGetSymbolAddress) with the context current.  Most callers
+// use the primary context of each device, and the lookup happens on their
+// first call on that device; an engine that creates its own contexts gets one
+// lookup per context.  Entries are kept against the context's unique id,
+// which a process never reuses, so a context made after cudaDeviceReset (or a
+// new context that happens to get the old handle value) is looked up afresh.
+// The driver's context queries are reached through the runtime's entry-point
+// lookup, so the library needs no link against libcuda.
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    void* addr;
+};
+constexpr int kMaxContexts = 64;
+static ScratchEntry g_scratch[kMaxContexts];
+static int g_n_scratch = 0;
 static std::mutex g_scratch_mutex;
 
-int scratch_for_current_device(dbl4** out)
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
+static bool g_ctx_fns_tried = false;
+
+// Caller holds g_scratch_mutex.  False if the current context's id cannot be
+// had (then nothing is cached and every call looks the address up).
+static bool current_context_id(unsigned long long* id)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return WTMD_ECUDA;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_hills_scratch) != cudaSuccess || !p) return WTMD_ECUDA;
-        g_scratch_addr[dev] = p;
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
     }
-    *out = static_cast<dbl4*>(g_scratch_addr[dev]);
+    if (!g_ctx_current || !g_ctx_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
+
+int scratch_for_current_context(dbl4** out)
+{
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (have_id)
+        for (int k = 0; k < g_n_scratch; ++k)
+            if (g_scratch[k].ctx_id == id) {
+                *out = static_cast<dbl4*>(g_scratch[k].addr);
+                return WTMD_OK;
+            }
+    // first call in this context (the lookup also makes the device's primary
+    // context current when the caller has none)
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_hills_scratch) != cudaSuccess || !p) return WTMD_ECUDA;
+    if (!have_id) have_id = current_context_id(&id);
+    if (have_id && g_n_scratch < kMaxContexts) g_scratch[g_n_scratch++] = ScratchEntry{id, p};
+    *out = static_cast<dbl4*>(p);
     return WTMD_OK;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 struct Prm {
@@ -162,12 +221,13 @@ extern "C" int wtmd_hills_eval_static(int32_t n_cv, const double* sigma, const d
         prm.gs[i] = -1.0 / (sg * sg);
     }
     dbl4* scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    int rc = scratch_for_current_context(&scratch);
     if (rc) return rc;
 
     int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return WTMD_ECUDA;
     const int th = P >= 1024 ? 1 : (P >= 64 ? 4 : (P >= 8 ? 32 : 256));
     const long long tp = kHB / th;
     const long long tiles = (P + tp - 1) / tp;
@@ -176,14 +236,21 @@ extern "C" int wtmd_hills_eval_static(int32_t n_cv, const double* sigma, const d
     split = std::min<long long>(split, std::max<int64_t>(n_hills, 1));
     split = std::max<long long>(split, 1);
     cudaStream_t st = (cudaStream_t)stream;
-    dim3 grid((unsigned)tiles, (unsigned)split);
+    const dim3 grid((unsigned)tiles, (unsigned)split), block(kHB);
     const int Pi = (int)P;
+    const dbl4* hl = (const dbl4*)hills;
+    const long long H = n_hills;
+    // each launch's own status (the caller's earlier errors are neither
+    // reported here nor cleared)
+    cudaError_t e;
     switch (th) {
-    case 1: static_partial_kernel<1><<<grid, kHB, 0, st>>>((const dbl4*)hills, n_hills, xi, Pi, prm, scratch); break;
-    case 4: static_partial_kernel<4><<<grid, kHB, 0, st>>>((const dbl4*)hills, n_hills, xi, Pi, prm, scratch); break;
-    case 32: static_partial_kernel<32><<<grid, kHB, 0, st>>>((const dbl4*)hills, n_hills, xi, Pi, prm, scratch); break;
-    default: static_partial_kernel<256><<<grid, kHB, 0, st>>>((const dbl4*)hills, n_hills, xi, Pi, prm, scratch); break;
+    case 1: e = launch(static_partial_kernel<1>, grid, block, st, hl, H, xi, Pi, prm, scratch); break;
+    case 4: e = launch(static_partial_kernel<4>, grid, block, st, hl, H, xi, Pi, prm, scratch); break;
+    case 32: e = launch(static_partial_kernel<32>, grid, block, st, hl, H, xi, Pi, prm, scratch); break;
+    default: e = launch(static_partial_kernel<256>, grid, block, st, hl, H, xi, Pi, prm, scratch); break;
     }
-    static_finalize_kernel<<<(Pi + 255) / 256, 256, 0, st>>>(scratch, (int)split, Pi, prm, V_out, dV_out);
-    return cudaGetLastError() == cudaSuccess ? WTMD_OK : WTMD_ECUDA;
+    if (e != cudaSuccess) return WTMD_ECUDA;
+    e = launch(static_finalize_kernel, dim3((unsigned)((Pi + 255) / 256)), dim3(256), st, (const dbl4*)scratch,
+               (int)split, Pi, prm, V_out, dV_out);
+    return e == cudaSuccess ? WTMD_OK : WTMD_ECUDA;
 }

@@ -2,7 +2,7 @@
 //
 // Once the hill list is long, the bias V(xi) = sum_k w_k exp(...) costs one
 // exponential per hill per step.  The paper represents biases by neural
-// networks in its ANN and FUNN methods (Sec. 2.1.6); here a small network
+// networks in its ANN (Sec. 2.1.7) and FUNN (Sec. 2.1.8) methods; here a small network
 // stands in for the older part of the hill list:
 //     V(xi) = V_nn(xi) + sum_{k >= K} w_k exp(...),
 // where V_nn approximates the sum over hills [0, K) and the exact sum covers
