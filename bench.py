@@ -39,6 +39,18 @@ sys.path.insert(0, ROOT)
 # slowdowns (the nvidia-smi clock sampler that runs during the timed region
 # stalls the driver) do not appear as idle device time inside the events.
 SLACK_CYCLES = 200_000
+# Before the first timed step the stream is held by a spin long enough for
+# the host to enqueue every timed step (flush, slack, events, step) behind
+# it.  Measured without it: the first timed step after the sampler started
+# took 150-330 us (median step 25 us), because a driver stall of the host
+# longer than the slack left the GPU idle between the first start event and
+# the step's launch; at K = 20 that one step moved the mean by 30 %.
+GATE_CYCLES_BASE, GATE_CYCLES_PER_STEP = 10_000_000, 100_000
+
+
+def gate_cycles(K: int) -> int:
+    """Spin length (SM cycles) holding the stream while K timed steps are enqueued."""
+    return GATE_CYCLES_BASE + GATE_CYCLES_PER_STEP * K
 
 METRIC = "bias-force evals/s and hill-evals/s (10⁶ hills), % MUFU roofline, MD steps/s"
 N_ATOMS, RHO, N_TAG, N_RG, H_PRE = 4096, 0.8, 512, 64, 100000
@@ -137,6 +149,7 @@ def walkers_bench(wt, torch, dev, flush, steps):
         torch.cuda.synchronize()
         if flushed:
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            torch.cuda._sleep(gate_cycles(K))  # the host enqueues every timed step behind it
             for i, (a, b) in enumerate(evs):
                 flush.fill_(float(i))
                 torch.cuda._sleep(SLACK_CYCLES)
@@ -328,10 +341,11 @@ class Clocks:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, busy=None):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.idx = gpu_index
         self.p = None
+        self.busy = busy  # device work queued while the sampler starts (clocks under load, not idle)
 
     def __enter__(self):
         try:
@@ -339,7 +353,15 @@ class Clocks:
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
-        time.sleep(0.3)
+        t_end = time.perf_counter() + 0.3
+        while time.perf_counter() < t_end:
+            if self.busy is not None:
+                self.busy()
+                import torch
+
+                torch.cuda.synchronize()
+            else:
+                time.sleep(0.01)
         return self
 
     def __exit__(self, *a):
@@ -518,29 +540,44 @@ def run_ours(args, rank, world):
     F = torch.zeros_like(pos)
     _, xi0, _ = m.bias_eval(pos)
     m.hills_load(hills_around(xi0[0].double().cpu().numpy(), seed=100 + rank))
-    hills_plan = m.hills_tune(1)  # one walker: one evaluation point per step
+    # one walker: one evaluation point per step, summed by one cluster of
+    # CTAs (hill records staged in shared memory by TMA before the sum's
+    # dependency wait, split sums met in distributed shared memory); the
+    # isolated-launch plan tuner does not see that overlap, so the plan is set
+    hills_plan = None
+    for cl in (16, 8):
+        try:
+            m.hills_plan(1, -1, cl)
+            hills_plan = (-1, cl, None)
+            break
+        except wt.WtmdError:
+            continue
+    if hills_plan is None:
+        hills_plan = m.hills_tune(1)
     m.bind(pos, vel, F)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # warm-up: graph capture on the first call, then W steps of exactly the
-    # timed loop's body (flush, device-side slack, events, one step), so that
-    # the host path of the timed steps is warm too
-    for i in range(max(args.warmup, 3)):
-        flush.fill_(float(i))
-        torch.cuda._sleep(SLACK_CYCLES)
-        wa, wb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        wa.record(stream)
-        m.step_n(1, check=(i == 0))
-        wb.record(stream)
-    torch.cuda.synchronize()
-    m.check()
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with Clocks(dev.index) as clk:
+    # the clock sampler starts before the warm-up, so that its start-up is
+    # over when the timed steps are enqueued
+    with Clocks(dev.index, busy=lambda: flush.fill_(0.0)) as clk:
+        # warm-up: graph capture on the first call, then W steps of exactly
+        # the timed loop's body (flush, device-side slack, events, one step),
+        # so that the host path of the timed steps is warm too
+        for i in range(max(args.warmup, 3)):
+            flush.fill_(float(i))
+            torch.cuda._sleep(SLACK_CYCLES)
+            wa, wb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            wa.record(stream)
+            m.step_n(1, check=(i == 0))
+            wb.record(stream)
+        torch.cuda.synchronize()
+        m.check()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
+        torch.cuda._sleep(gate_cycles(args.steps))  # hold the stream while the timed steps are enqueued
         for i in range(args.steps):
             flush.fill_(float(i))  # evict L2 between timed steps (not timed)
             torch.cuda._sleep(SLACK_CYCLES)  # device-side slack: host launch hiccups stay outside the events
@@ -552,7 +589,8 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     m.check()
-    dev_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    step_us = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
+    dev_ms = float(step_us.sum() * 1e-3)
 
     # steady state: K steps as one step_n call (graph replays), no flush
     torch.cuda.synchronize()
@@ -581,6 +619,7 @@ def run_ours(args, rank, world):
     m.step_host(hst, wait=True)  # captures the host-buffer graph
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    torch.cuda._sleep(gate_cycles(args.steps))  # the host enqueues every timed step behind it
     for i in range(args.steps):
         flush.fill_(float(i))
         torch.cuda._sleep(SLACK_CYCLES)
@@ -600,7 +639,9 @@ def run_ours(args, rank, world):
     gridb = None if args.no_grid_bias else grid_bias_bench(wt, torch, dev, flush, args.steps, rank)
     mbb = None if args.no_configs else mueller_brown_bench(wt, torch)
     adj = None if args.no_configs else chain_adjoint_bench(wt, torch, flush)
-    return dict(mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    step_stats = {"median_us": float(np.median(step_us)), "min_us": float(step_us.min()),
+                  "max_us": float(step_us.max()), "first_us": float(step_us[0])}
+    return dict(step_stats=step_stats, mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
 
@@ -707,6 +748,8 @@ def chain_adjoint_bench(wt, torch, flush):
         m.cv_adjoint(g)
     reps = 50
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(gate_cycles(reps))  # the host enqueues every evaluation behind it
     for a, b in evs:
         flush.fill_(1.0)
         torch.cuda._sleep(SLACK_CYCLES)
@@ -783,6 +826,7 @@ def grid_bias_bench(wt, torch, dev, flush, steps, rank=0):
         m.step_n(3, check=True)  # capture for the current source
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         torch.cuda.synchronize()
+        torch.cuda._sleep(gate_cycles(K))  # the host enqueues every timed step behind it
         for i in range(K):
             flush.fill_(float(i))
             torch.cuda._sleep(SLACK_CYCLES)
@@ -825,6 +869,8 @@ def grid_bias_bench(wt, torch, dev, flush, steps, rank=0):
         for _ in range(3):
             fn(pts, V, dV)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        torch.cuda.synchronize()
+        torch.cuda._sleep(gate_cycles(10))
         for a, b in evs:
             flush.fill_(1.0)
             torch.cuda._sleep(SLACK_CYCLES)
@@ -872,6 +918,8 @@ def hills_micro(wt, torch, dev, flush):
                 m.hills_eval_into(pts, V, dV)
             reps = 5 if P >= 1024 else 20
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            torch.cuda.synchronize()
+            torch.cuda._sleep(gate_cycles(reps))
             for a, b in evs:
                 flush.fill_(1.0)
                 torch.cuda._sleep(SLACK_CYCLES)
@@ -1069,6 +1117,7 @@ def main():
         "e2e": {"value": job_rate(world, K, r["e2e_ms"]), "unit": "steps/s",
                 "h2d_bytes_per_step": r["e2e_bytes"], "d2h_bytes_per_step": r["e2e_bytes"]},
         "steady_state_steps_per_s": job_rate(world, K, r["steady_ms"]),
+        "timed_step_us": r["step_stats"],
         "wall_s": r["wall"],
         "kernels_ms": {k: round(v, 5) for k, v in prof},
         "hills_plan": {"lanes_per_point": r["hills_plan"][0], "splits": r["hills_plan"][1],

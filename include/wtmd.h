@@ -355,6 +355,25 @@ int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
  * enable = 0 returns to the per-kernel step. */
 int wtmd_walkers_persistent(wtmd_t* h, int32_t enable);
 
+/* The MD step of a single periodic system as one persistent (cooperative)
+ * kernel launch per step (Sec. 3.2.1 steps (a)-(f) with the metadynamics
+ * update of Sec. 2.1.5 inside): the first half of BAOAB, the LJ forces from
+ * the Verlet lists (rebuilt in the same launch when an atom moved past half
+ * the skin), the CVs, the hills sum, deposition, bias force and closing kick,
+ * with bounded grid barriers between the phases and one CTA per SM.  Off by
+ * default (the per-kernel step graph is faster at the sizes measured);
+ * enable = 1 lets step_n and wtmd_step_host use it whenever the handle has
+ * this form: FP32, one walker, LJ engine on the periodic cell lists, every
+ * CV an FP32 tile coordination number (explicit list A) or a radius of
+ * gyration (at most 1024 members), the bias summed from the hills (no
+ * surrogate, grid or harmonic bias, no FP64 bias grid); other handles keep
+ * the per-kernel sequence.  enable = 0 returns to the per-kernel sequence,
+ * any other value leaves the setting; *active (host, may be NULL) receives 1
+ * when the next step runs as one persistent launch, else 0.  Drops captured
+ * step graphs when the setting changes.  Errors: WTMD_EINVAL for a null
+ * handle. */
+int wtmd_fused_step(wtmd_t* h, int32_t enable, int32_t* active);
+
 /* Autotuner of the persistent walker step: times every candidate (targets
  * per pair task 32/64/128/256, CTAs per SM 1/2/4, hill splits per CTA 1/2)
  * over `steps` steps from the same saved state, keeps the fastest, and
@@ -368,14 +387,25 @@ int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice);
  * points: times every (lanes per point 1/4/32/256, splits 1 ... 1184)
  * candidate of the copy-ring kernel and, on FP32 handles with P <= 8, of
  * the few-points kernel (lanes per point reported as 0: every thread takes
- * whole hill pairs from global memory for all P points) on the handle's
- * current hills at P points placed at the CV centre, and keeps the fastest
- * for later sums with P points (step_n with W = P walkers, bias_eval,
- * hills_eval).  choice (host [2], may be NULL) receives (lanes per point,
- * splits); ms (host, may be NULL) the time of one sum.  Synchronizes; drops
- * captured step graphs.  Without tuning, FP32 sums of P <= 8 points use the
- * few-points kernel. */
+ * whole hill pairs from global memory for all P points) and of the cluster
+ * kernel (lanes per point reported as -1: one thread-block cluster of
+ * `splits` = 8 or 16 CTAs whose split sums meet in distributed shared
+ * memory) on the handle's current hills at P points placed at the CV
+ * centre, and keeps the fastest for later sums with P points (step_n with
+ * W = P walkers, bias_eval, hills_eval).  choice (host [2], may be NULL)
+ * receives (lanes per point, splits); ms (host, may be NULL) the time of one
+ * sum.  Synchronizes; drops captured step graphs.  Without tuning, FP32 sums
+ * of P <= 8 points use the few-points kernel. */
 int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms);
+
+/* Set the hills-sum launch plan for P points instead of tuning it (the same
+ * plans wtmd_hills_tune chooses from): lanes = hill lanes per point (1, 4,
+ * 32 or 256: the copy-ring kernel), 0 (the few-points kernel) or -1 (the
+ * cluster kernel; splits 8, or 16 where the device runs clusters of 16),
+ * splits = CTAs the hill list is split over (1 ... 65535).  Lanes 0 and -1
+ * need an FP32 handle and P <= 8.  Drops captured step graphs.  Errors:
+ * WTMD_EINVAL for other values. */
+int wtmd_hills_plan(wtmd_t* h, int64_t P, int32_t lanes, int32_t splits);
 
 /* Hills sum for callers that cannot allocate device memory (the paper has no
  * counterpart: it is an interface for hosts such as an engine plugin that may

@@ -72,7 +72,7 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune",
            "wtmd_grid_eval", "wtmd_bias_source", "wtmd_checkpoint_size", "wtmd_checkpoint_save",
            "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate",
-           "wtmd_step_host"]
+           "wtmd_step_host", "wtmd_fused_step", "wtmd_hills_plan"]
 
 BIAS_HILLS, BIAS_GRID, BIAS_HARMONIC = 0, 1, 2
 
@@ -110,6 +110,8 @@ def lib() -> C.CDLL:
     L.wtmd_profile_step.argtypes = [vp, i64, C.c_char_p, C.POINTER(C.c_double), i32, C.POINTER(i32)]
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wtmd_walkers_persistent.argtypes = [vp, i32]
+    L.wtmd_fused_step.argtypes = [vp, i32, C.POINTER(i32)]
+    L.wtmd_hills_plan.argtypes = [vp, i64, i32, i32]
     L.wtmd_autotune.argtypes = [vp, i64, C.POINTER(i32)]
     dp, fp = C.POINTER(C.c_double), C.POINTER(C.c_float)
     L.wtmd_surrogate.argtypes = [vp, i32, C.c_double, i64]
@@ -310,6 +312,20 @@ class Wtmd:
         ms = C.c_double()
         self._err(lib().wtmd_hills_tune(self.h, int(P), ch, C.byref(ms)), "wtmd_hills_tune")
         return ch[0], ch[1], ms.value
+
+    def fused_step(self, enable=None) -> bool:
+        """Allow (True) or forbid (False, the default) the single-launch
+        persistent step (None leaves the setting); returns whether the next
+        step uses it."""
+        act = C.c_int32()
+        self._err(lib().wtmd_fused_step(self.h, -1 if enable is None else (1 if enable else 0), C.byref(act)),
+                  "wtmd_fused_step")
+        return bool(act.value)
+
+    def hills_plan(self, P: int, lanes: int, splits: int):
+        """Set the hills-sum plan for P points (lanes per point 1/4/32/256,
+        0 = few-points kernel, -1 = cluster kernel; splits)."""
+        self._err(lib().wtmd_hills_plan(self.h, int(P), int(lanes), int(splits)), "wtmd_hills_plan")
 
     def walkers_persistent(self, enable: bool = True):
         """Run each step as one persistent launch over all walkers."""

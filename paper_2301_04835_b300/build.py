@@ -50,8 +50,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
+    headers = [p for p in _deps() if not p.endswith(".cu") and os.path.exists(p)]
+    t_hdr = max((os.path.getmtime(p) for p in headers), default=0.0)
+
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        # an object newer than its source and every header is reused
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), t_hdr):
+            return obj
         cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

@@ -57,6 +57,7 @@ static void drop_graphs(wtmd_t* h)
     h->graph_host = nullptr;
     h->gh_in = nullptr;
     h->gh_out = nullptr;
+    h->ss.ready = false;  // the persistent step's plan follows the CVs and bindings
 }
 
 namespace wtmd {
@@ -105,7 +106,7 @@ extern "C" int wtmd_destroy(wtmd_t* h)
     void* ptrs[] = {h->woff, h->wn, h->atom_walker, h->hills64, h->hills32, h->count, h->step, h->dep, h->status, h->ticket,
                     h->grid, h->gfac, h->xi, h->ctr, h->V, h->dV, h->J, h->partial, h->hev_xi, h->cell_count,
                     h->harm_centre, h->harm_sum,
-                    h->cell_atoms, h->nl_nbr, h->nl_cnt, h->nl_xref, h->nl_ctl};
+                    h->cell_atoms, h->nl_nbr, h->nl_cnt, h->nl_xref, h->nl_ctl, h->ss.bar};
     for (void* p : ptrs) cudaFree(p);
     surrogate_free(h->sur);
     {
@@ -477,7 +478,9 @@ static int enqueue_engine_and_bias(wtmd_t* h)
     // theirs, the engine on the main stream; the closing kick joins them
     WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
     cudaStream_t main_stream = h->stream;
+    const int folded = folded_rg(h);  // computed by CV 0's launch: no branch of its own
     for (int c = 1; c < h->ncv; ++c) {
+        if (c == folded) continue;
         WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->cv_stream[c], h->ev_fork, 0));
         h->stream = h->cv_stream[c];
         rc = launch_cv(h, h->pos, c);
@@ -489,7 +492,7 @@ static int enqueue_engine_and_bias(wtmd_t* h)
     h->stream = h->cv_stream[0];
     rc = launch_cv(h, h->pos, 0);
     for (int c = 1; c < h->ncv && !rc; ++c)
-        if (cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0) != cudaSuccess) rc = WTMD_ECUDA;
+        if (c != folded && cudaStreamWaitEvent(h->stream, h->ev_cv[c], 0) != cudaSuccess) rc = WTMD_ECUDA;
     if (!rc) rc = launch_bias_sum(h);
     if (!rc && cudaEventRecord(h->ev_join, h->stream) != cudaSuccess) rc = WTMD_ECUDA;
     h->stream = main_stream;
@@ -499,9 +502,25 @@ static int enqueue_engine_and_bias(wtmd_t* h)
     return WTMD_OK;
 }
 
+// The step as one persistent launch when the handle's form allows it and
+// its plan is set up (sys_step.cu), else as the per-kernel sequence.
+static bool use_sys_step(const wtmd_t* h)
+{
+    return h->fused_on && h->ss.ready && sys_step_eligible(h, nullptr);
+}
+
+// Set up the persistent step's plan outside graph capture (a no-op when it
+// is ready, switched off or not applicable).
+static int prepare_sys_step(wtmd_t* h)
+{
+    if (!h->fused_on || h->ss.ready || !sys_step_eligible(h, nullptr)) return WTMD_OK;
+    return sys_step_setup(h);
+}
+
 static int enqueue_step(wtmd_t* h)
 {
     if (h->persistent) return launch_walkers_step(h, 0);
+    if (use_sys_step(h)) return launch_sys_step(h);
     int rc;
     h->jf_pending = 0;
     // BAOAB zeroes what the coordination tile kernels accumulate (the FP64
@@ -584,6 +603,7 @@ extern "C" int step_n(wtmd_t* h, int64_t n_steps)
     if (!h->pos || !h->vel || !h->force) FAIL(h, WTMD_EINVAL, "bind positions, velocities and forces first");
     if (n_steps == 0) return WTMD_OK;
     if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+    if ((rc = prepare_sys_step(h))) return rc;
     if (!h->forces_valid) {
         if ((rc = enqueue_forces(h))) return rc;
         h->forces_valid = true;
@@ -655,6 +675,7 @@ extern "C" int wtmd_step_host(wtmd_t* h, const void* in_host, void* out_host, in
                            !h->no_graph && !h->no_host_graph && !h->prof && pinned(in_host) && pinned(out_host);
     if (one_graph) {
         if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
+        if ((rc = prepare_sys_step(h))) return rc;
         if (!h->graph_host || h->gh_in != in_host || h->gh_out != out_host) {
             if (h->graph_host) cudaGraphExecDestroy(h->graph_host);
             h->graph_host = nullptr;
@@ -688,7 +709,11 @@ extern "C" int wtmd_check(wtmd_t* h)
     unsigned st = 0;
     WTMD_CUDA_TRY(h, cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
     WTMD_CUDA_TRY(h, cudaMemset(h->status, 0, sizeof(unsigned)));
-    if (st & ST_TIMEOUT) FAIL(h, WTMD_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_TIMEOUT) {
+        // a barrier that gave up leaves its arrival counter dirty
+        if (h->ss.bar) WTMD_CUDA_TRY(h, cudaMemset(h->ss.bar, 0, sizeof(unsigned) * 4));
+        FAIL(h, WTMD_ETIMEOUT, "a bounded device wait gave up");
+    }
     if (st & ST_NUMERIC) FAIL(h, WTMD_ENUMERIC, "non-finite CV, bias or gradient");
     if (st & ST_CELL) FAIL(h, WTMD_ECELL, "cell list overflow");
     if (st & ST_CAPACITY) FAIL(h, WTMD_ECAPACITY, "hill capacity reached; deposits skipped");
@@ -903,6 +928,15 @@ extern "C" int wtmd_hills_tune(wtmd_t* h, int64_t P, int32_t* choice, double* ms
         choice[0] = th;
         choice[1] = sp;
     }
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_hills_plan(wtmd_t* h, int64_t P, int32_t lanes, int32_t splits)
+{
+    if (!h) return WTMD_EINVAL;
+    const int rc = hills_set_plan(h, P, lanes, splits);
+    if (rc) return rc;
+    drop_graphs(h);  // recapture with the plan
     return WTMD_OK;
 }
 
@@ -1177,6 +1211,17 @@ extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double
         ms[i] = acc[i] / n_steps;
     }
     *n_out = n;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_fused_step(wtmd_t* h, int32_t enable, int32_t* active)
+{
+    if (!h) return WTMD_EINVAL;
+    if (enable == 0 || enable == 1) {
+        if (h->fused_on != (enable == 1)) drop_graphs(h);
+        h->fused_on = enable == 1;
+    }
+    if (active) *active = (h->fused_on && sys_step_eligible(h, nullptr)) ? 1 : 0;
     return WTMD_OK;
 }
 

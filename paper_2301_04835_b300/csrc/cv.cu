@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "step_dev.cuh"
+#include "coord_dev.cuh"
 
 namespace wtmd {
 
@@ -155,15 +156,14 @@ __global__ void cv_dihedral_kernel(const R4<R>* __restrict__ pos, const int64_t*
 // ---------------------------------------------------------------------------
 constexpr int RG_CACHE = 1024;  // members whose unwrapped position stays in shared memory
 
+// Rg of walker w by the whole CTA (u: RG_CACHE staged members in shared
+// memory).  Called after the dependency wait.
 template <typename R>
-__global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
-                                                    const int* __restrict__ wn, const int* __restrict__ A, int nA,
-                                                    Box box, double scale, int intensive, double* __restrict__ xi,
-                                                    int col, R4<R>* __restrict__ J)
+__device__ void cv_rg_body(int w, const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
+                           const int* __restrict__ wn, const int* __restrict__ A, int nA, const Box& box, double scale,
+                           int intensive, double* __restrict__ xi, int col, R4<R>* __restrict__ J, R4<R>* u)
 {
-    __shared__ R4<R> u[RG_CACHE];
     __shared__ R bc[4];  // broadcast: centre (3) and the Jacobian factor
-    const int w = blockIdx.x;
     const long long o = woff[w];
     const int m = A ? nA : wn[w];
     const int i0 = A ? A[0] : 0;
@@ -225,6 +225,22 @@ __global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ po
         J[o + i] = mk4<R>(f * (q.x - c[0]), f * (q.y - c[1]), f * (q.z - c[2]), R(0));
     }
     if (threadIdx.x == 0) xi[w * 4 + col] = rg_s;
+}
+
+
+// One block per walker.  A programmatic dependent of the kernel that moved
+// the atoms: the kernels that need this CV (joined after it) may launch at
+// once; the positions are waited for.
+template <typename R>
+__global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
+                                                    const int* __restrict__ wn, const int* __restrict__ A, int nA,
+                                                    Box box, double scale, int intensive, double* __restrict__ xi,
+                                                    int col, R4<R>* __restrict__ J)
+{
+    __shared__ R4<R> u[RG_CACHE];
+    pdl_trigger();
+    pdl_wait();
+    cv_rg_body<R>((int)blockIdx.x, pos, woff, wn, A, nA, box, scale, intensive, xi, col, J, u);
 }
 
 // ---------------------------------------------------------------------------
@@ -653,8 +669,6 @@ __global__ void __launch_bounds__(CW_T) coord_warp_kernel(const R4<R>* __restric
 // in fixed order by the CTAs that complete a tile or a chunk (tickets), in
 // the same launch: deterministic.
 // ---------------------------------------------------------------------------
-constexpr int CT_T = 256;
-constexpr int CT_B = 256;  // partners per CTA (8 warps x 32)
 constexpr int FB = 4;      // partial sums loaded per batch in the finalization
 
 
@@ -870,51 +884,6 @@ __global__ void __launch_bounds__(CT_T) coord_tile_kernel(const R4<R>* __restric
     }
 }
 
-// ---------------------------------------------------------------------------
-// FP32 form of the tile kernel.  A CTA takes 64 members of A, two per lane
-// (tile members lane and lane + 32), and a chunk of CT_B partners, so that
-// every arithmetic instruction of the pair loop serves two pairs through the
-// packed f32x2 operations.  Partners are staged pre-negated and duplicated
-// into both halves, (-x,-x,-y,-y) and (-z,-z,w,w), so a difference is one
-// packed add.  The minimum image rounds d/L by the 1.5 * 2^23 shift
-// (exact for |d/L| < 2^22) instead of a conversion instruction.
-//
-// The kernel ends with its partials: nothing waits on another CTA.  The CV
-// value needs no second pass: each CTA rounds its share
-// scale * (sum of s over its pairs, its self pairs removed) to a multiple of
-// 2^-q and adds it to xi with a double atomic.  q is chosen on the host so
-// that every partial sum of such shares is a double exactly; the additions
-// are then exact and the result does not depend on their order.  J stays in
-// factored form, row partials [W][chunk][A] and column partials
-// [W][tile][B], contracted per atom in a fixed order by `coord_jfin_kernel`,
-// which in a step runs beside the hills sum (that needs xi only).
-// ---------------------------------------------------------------------------
-constexpr int C2_A = 64;   // targets per CTA (two per lane)
-
-// Factored J of an FP32 tile coordination CV (see coord_j_parts).
-struct CoordParts {
-    const float4* rowpart = nullptr;  // [W][nbchunk][nA]
-    const float4* colpart = nullptr;  // [W][ntile][nB_stride]
-    const int* inv_a = nullptr;       // [max_wn]: position in A or -1
-    const int* inv_b = nullptr;       // [max_wn]: position in B or -1; null: B = all atoms
-    const double* scw = nullptr;      // [W] scale
-    int nA = 0, nbchunk = 0, ntile = 0, nB_stride = 0;
-};
-constexpr int C2_U = 8;    // rotation steps whose pair terms are computed together
-static_assert(CT_B == CT_T, "one staged partner per thread");
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-
-// d - L rint(d / L) for two pairs along one axis (L = hi + lo in two floats);
-// iL = hi = lo = 0 on an open axis leaves d unchanged.
-__device__ __forceinline__ float2 min_image2(float2 d, float2 iL, float2 nhi, float2 nlo)
-{
-    float2 n = __ffma2_rn(d, iL, f2(12582912.f));
-    n = __fadd2_rn(n, f2(-12582912.f));
-    d = __ffma2_rn(n, nhi, d);
-    return __ffma2_rn(n, nlo, d);
-}
-
 template <int HC>
 __global__ void __launch_bounds__(CT_T) coord_tile2_kernel(const float4* __restrict__ pos,
                                                            const int64_t* __restrict__ woff,
@@ -931,167 +900,82 @@ __global__ void __launch_bounds__(CT_T) coord_tile2_kernel(const float4* __restr
     __shared__ double xred[2];
     pdl_trigger();  // the hills sum that follows may start its hill copies now
     const int w = blockIdx.y;
-    const int nw = wn[w];
-    const long long o = woff[w];
-    const int nBw = B ? nB : nw;
-    const int tile = blockIdx.x / nbchunk, chunk = blockIdx.x % nbchunk;
     const int ntile = gridDim.x / nbchunk;
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    const int b0 = chunk * CT_B;
-    const int mb = min(CT_B, nBw - b0);
-    // index lists are constant: read before waiting for the positions
-    const int ia0 = tile * C2_A + lane, ia1 = ia0 + 32;
-    const int a0 = ia0 < nA ? A[ia0] : -1, a1 = ia1 < nA ? A[ia1] : -1;
-    const int q = threadIdx.x;
-    const int jq = q < mb ? (B ? B[b0 + q] : b0 + q) : -1;
-    pdl_wait();
-    if (jq >= 0) {
-        const float4 p = pos[o + jq];
-        srcA[q] = make_float4(-p.x, -p.x, -p.y, -p.y);
-        srcB[q] = make_float4(-p.z, -p.z, 1.f, 1.f);
-    } else {  // padding: weight 0
-        srcA[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        srcB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
-    if (a0 >= 0) t0 = pos[o + a0];
-    if (a1 >= 0) t1 = pos[o + a1];
-    const float2 tx = make_float2(t0.x, t1.x), ty = make_float2(t0.y, t1.y), tz = make_float2(t0.z, t1.z);
-    // an empty target lane adds nothing to the columns
-    const float2 gpl = make_float2(a0 >= 0 ? gpref : 0.f, a1 >= 0 ? gpref : 0.f);
-    float2 iL[3], nhi[3], nlo[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool per = box.Lf[k] > 0.f;
-        iL[k] = f2(per ? box.invLf[k] : 0.f);
-        nhi[k] = f2(per ? -box.Lf[k] : 0.f);
-        nlo[k] = f2(per ? -box.Llo[k] : 0.f);
-    }
-    __syncthreads();
-    // rotation over the warp's 32 partners as in the generic kernel: the
-    // column sum of a partner (both targets of the lane added) moves one
-    // lane down per step and ends in the partner's own lane.  A shuffle
-    // orders the code around it, so the pair terms of C2_U steps are
-    // computed first (independent, interleaved) and then passed along.
-    float2 gx = f2(0.f), gy = gx, gz = gx, sv = gx;
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    const int base = warp * 32, from = (lane + 1) & 31;
-    const float2 inv2 = f2(inv_r0sq), one2 = f2(1.f);
-#pragma unroll 1
-    for (int k0 = 0; k0 < 32; k0 += C2_U) {
-        float hx[C2_U], hy[C2_U], hz[C2_U];
-#pragma unroll
-        for (int u = 0; u < C2_U; ++u) {
-            const int m = base + ((lane + k0 + u) & 31);
-            const float4 pa = srcA[m], pb = srcB[m];
-            const float2 dx = min_image2(__fadd2_rn(tx, make_float2(pa.x, pa.y)), iL[0], nhi[0], nlo[0]);
-            const float2 dy = min_image2(__fadd2_rn(ty, make_float2(pa.z, pa.w)), iL[1], nhi[1], nlo[1]);
-            const float2 dz = min_image2(__fadd2_rn(tz, make_float2(pb.x, pb.y)), iL[2], nhi[2], nlo[2]);
-            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-            const float2 y = __fmul2_rn(r2, inv2);
-            float2 yh1;  // y^(h-1)
-            if constexpr (HC == 1) {
-                yh1 = one2;
-            } else if constexpr (HC > 1) {
-                yh1 = y;
-#pragma unroll
-                for (int e = 2; e < HC; ++e) yh1 = __fmul2_rn(yh1, y);
-            } else {
-                yh1 = one2;
-                for (int e = 1; e < h; ++e) yh1 = __fmul2_rn(yh1, y);
-            }
-            const float2 den = __ffma2_rn(yh1, y, one2);
-            const float2 s = __fmul2_rn(make_float2(rcp_approx(den.x), rcp_approx(den.y)), make_float2(pb.z, pb.w));
-            sv = __fadd2_rn(sv, s);
-            const float2 gr = __fmul2_rn(__fmul2_rn(s, s), __fmul2_rn(yh1, gpl));
-            const float2 px = __fmul2_rn(gr, dx), py = __fmul2_rn(gr, dy), pz = __fmul2_rn(gr, dz);
-            gx = __fadd2_rn(gx, px);
-            gy = __fadd2_rn(gy, py);
-            gz = __fadd2_rn(gz, pz);
-            hx[u] = px.x + px.y;
-            hy[u] = py.x + py.y;
-            hz[u] = pz.x + pz.y;
-        }
-#pragma unroll
-        for (int u = 0; u < C2_U; ++u) {
-            cx = __shfl_sync(0xffffffffu, cx + hx[u], from);
-            cy = __shfl_sync(0xffffffffu, cy + hy[u], from);
-            cz = __shfl_sync(0xffffffffu, cz + hz[u], from);
-        }
-    }
-    if (base + lane < mb)
-        colpart[((size_t)w * ntile + tile) * nB_stride + b0 + base + lane] = make_float4(-cx, -cy, -cz, 0.f);
-    rowred[warp][lane] = make_float4(gx.x, gy.x, gz.x, sv.x);
-    rowred[warp][lane + 32] = make_float4(gx.y, gy.y, gz.y, sv.y);
-    __syncthreads();
-    // rows of the chunk (threads 0..63, warps in order) and this CTA's share
-    // of the CV value; the pair of a target with itself added s(0) in the
-    // chunk that holds it as a partner
-    if (warp < 2) {
-        const int r = threadIdx.x, ia = tile * C2_A + r;
-        double xs = 0.0;
-        if (ia < nA) {
-            float4 t = rowred[0][r];
-            for (int k = 1; k < CT_T / 32; ++k) {
-                const float4 u = rowred[k][r];
-                t.x += u.x;
-                t.y += u.y;
-                t.z += u.z;
-                t.w += u.w;
-            }
-            rowpart[((size_t)w * nbchunk + chunk) * nA + ia] = t;
-            const int a = warp == 0 ? a0 : a1;
-            const int pb = inv_b ? inv_b[a] : (a < nw ? a : -1);
-            if (pb >= b0 && pb < b0 + mb) t.w -= rcp_approx(1.f);
-            xs = (double)t.w;
-        }
-        for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-        if (lane == 0) xred[warp] = xs;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&xi[w * 4 + col], rint(scw[w] * (xred[0] + xred[1]) * xq) * ixq);
+    CoordTile2 t{pos + woff[w], wn[w], A, nA, B, nB, nbchunk, ntile, box, inv_r0sq, h, gpref,
+                 rowpart + (size_t)w * nbchunk * nA, colpart + (size_t)w * ntile * nB_stride, nB_stride, scw[w],
+                 xi + w * 4 + col, inv_b, xq, ixq};
+    coord_tile2_body<HC>(t, (int)blockIdx.x / nbchunk, (int)blockIdx.x % nbchunk, (int)threadIdx.x, srcA, srcB, rowred,
+                         xred, [] { pdl_wait(); }, [] { __syncthreads(); });
 }
 
-// J of one atom of walker w (local index li) from the FP32 tile partials:
-// its column sums over the tiles, then its row sums over the chunks, each
-// in increasing order, times the walker's scale.
-__device__ __forceinline__ float4 coord_j_parts(const CoordParts& p, int w, int li)
+// Coordination tiles with the radius of gyration of another CV in the same
+// launch: CTAs x < ntile * nbchunk take the tiles, CTA x = ntile * nbchunk of
+// each walker the Rg group.  The hills sum, which needs both CVs, then
+// depends on one launch, and that launch lets its dependents start at once.
+constexpr size_t C2_SMEM = sizeof(float4) * (2 * CT_B + (CT_T / 32) * C2_A) + 2 * sizeof(double);
+constexpr size_t C2RG_SMEM = C2_SMEM > sizeof(float4) * RG_CACHE ? C2_SMEM : sizeof(float4) * RG_CACHE;
+
+template <int HC>
+__global__ void __launch_bounds__(CT_T) coord_tile2_rg_kernel(const float4* __restrict__ pos,
+                                                              const int64_t* __restrict__ woff,
+                                                              const int* __restrict__ wn, const int* __restrict__ A,
+                                                              int nA, const int* __restrict__ B, int nB, int nbchunk,
+                                                              Box box, float inv_r0sq, int h, float gpref,
+                                                              float4* __restrict__ rowpart,
+                                                              float4* __restrict__ colpart, int nB_stride,
+                                                              const double* __restrict__ scw, double* __restrict__ xi,
+                                                              int col, const int* __restrict__ inv_b, double xq,
+                                                              double ixq, const int* __restrict__ rA, int rnA,
+                                                              double rscale, int rintensive, int rcol,
+                                                              float4* __restrict__ rJ)
 {
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    const int pb = p.inv_b ? p.inv_b[li] : li;
-    if (pb >= 0) {
-#pragma unroll 8
-        for (int t = 0; t < p.ntile; ++t) {
-            const float4 u = __ldcg(p.colpart + ((size_t)w * p.ntile + t) * p.nB_stride + pb);
-            sx += u.x;
-            sy += u.y;
-            sz += u.z;
-        }
+    __shared__ __align__(16) unsigned char sm[C2RG_SMEM];
+    pdl_trigger();  // the hills sum that follows may start its hill copies now
+    const int w = blockIdx.y;
+    const int ntc = (int)gridDim.x - 1;  // tile CTAs of the walker
+    if ((int)blockIdx.x == ntc) {
+        pdl_wait();
+        cv_rg_body<float>(w, pos, woff, wn, rA, rnA, box, rscale, rintensive, xi, rcol, rJ, reinterpret_cast<float4*>(sm));
+        return;
     }
-    const int ia = p.inv_a[li];
-    if (ia >= 0) {
-#pragma unroll 8
-        for (int c = 0; c < p.nbchunk; ++c) {
-            const float4 u = __ldcg(p.rowpart + ((size_t)w * p.nbchunk + c) * p.nA + ia);
-            sx += u.x;
-            sy += u.y;
-            sz += u.z;
-        }
-    }
-    const float f = (float)p.scw[w];
-    return make_float4(f * sx, f * sy, f * sz, 0.f);
+    float4* srcA = reinterpret_cast<float4*>(sm);
+    float4* srcB = srcA + CT_B;
+    float4(*rowred)[C2_A] = reinterpret_cast<float4(*)[C2_A]>(srcB + CT_B);
+    double* xred = reinterpret_cast<double*>(rowred + CT_T / 32);
+    const int ntile = ntc / nbchunk;
+    CoordTile2 t{pos + woff[w], wn[w], A, nA, B, nB, nbchunk, ntile, box, inv_r0sq, h, gpref,
+                 rowpart + (size_t)w * nbchunk * nA, colpart + (size_t)w * ntile * nB_stride, nB_stride, scw[w],
+                 xi + w * 4 + col, inv_b, xq, ixq};
+    coord_tile2_body<HC>(t, (int)blockIdx.x / nbchunk, (int)blockIdx.x % nbchunk, (int)threadIdx.x, srcA, srcB, rowred,
+                         xred, [] { pdl_wait(); }, [] { __syncthreads(); });
+}
+
+// The Rg CV whose group rides along in the launch of the FP32 tile
+// coordination CV 0 (coord_tile2_rg_kernel), or -1.
+int folded_rg(const wtmd_t* h)
+{
+    if (h->ncv < 2 || !coord_factored(h, 0)) return -1;
+    for (int c = 1; c < h->ncv; ++c)
+        if (h->cv[c].kind == WTMD_CV_RG) return c;
+    return -1;
 }
 
 // J rows of an FP32 tile coordination CV for every atom (0 for atoms in
 // neither group).
+// A programmatic dependent of the tile kernel: the atom's walker and local
+// index are read first, then the partials are waited for.
 __global__ void coord_jfin_kernel(long long N, const int* __restrict__ aw, const int64_t* __restrict__ woff,
                                   CoordParts p, float4* __restrict__ J)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int w = aw[i];
-    const int li = (int)(i - woff[w]);
-    J[i] = coord_j_parts(p, w, li);
+    pdl_trigger();
+    int w = 0, li = 0;
+    if (i < N) {
+        w = aw[i];
+        li = (int)(i - woff[w]);
+    }
+    pdl_wait();
+    if (i < N) J[i] = coord_j_parts(p, w, li);
 }
 
 // J rows and the CV value from the tile partials.  Thread k sums the chunk
@@ -1378,8 +1262,10 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
             mark(h, "cv_gyration");
             break;
         case WTMD_CV_RG:
-            cv_rg_kernel<R><<<W, 256, 0, st>>>(pos, h->woff, h->wn, cv.n_a < 0 ? nullptr : cv.a, cv.n_a, h->box,
-                                               cv.scale, cv.flags & WTMD_CV_INTENSIVE, xi, c, Jc);
+            if (c == folded_rg(h)) break;  // computed by the launch of CV 0
+            WTMD_CUDA_TRY(h, launch_pdl(cv_rg_kernel<R>, dim3(W), dim3(256), 0, st, pos, (const int64_t*)h->woff,
+                                        (const int*)h->wn, (const int*)(cv.n_a < 0 ? nullptr : cv.a), (int)cv.n_a,
+                                        h->box, cv.scale, (int)(cv.flags & WTMD_CV_INTENSIVE), xi, c, Jc));
             mark(h, "cv_rg");
             break;
         case WTMD_CV_COORDINATION: {
@@ -1396,13 +1282,28 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                     // shares are multiples of 2^-q with |xi| < 2^(53-q) for every walker
                     const int q = 50 - std::max(0, (int)std::ceil(std::log2(std::max(cv.xi_bound, 1.0))));
                     dim3 g2(((cv.n_a + C2_A - 1) / C2_A) * cv.nbchunk, W);
-                    auto k2 = cv.nn == 6 ? coord_tile2_kernel<3> : coord_tile2_kernel<0>;
-                    WTMD_CUDA_TRY(h, launch_pdl(k2, g2, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
-                                                (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
-                                                cv.nn / 2, gp, (float4*)cv.tile_row, (float4*)cv.tile_col,
-                                                cv.nB_stride, (const double*)cv.scw, xi, c,
-                                                (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b), std::ldexp(1.0, q),
-                                                std::ldexp(1.0, -q)));
+                    const int rgc = c == 0 ? folded_rg(h) : -1;
+                    if (rgc >= 0) {
+                        const CvDev& rg = h->cv[rgc];
+                        g2.x += 1;
+                        auto k2 = cv.nn == 6 ? coord_tile2_rg_kernel<3> : coord_tile2_rg_kernel<0>;
+                        WTMD_CUDA_TRY(h, launch_pdl(k2, g2, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
+                                                    (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
+                                                    cv.nn / 2, gp, (float4*)cv.tile_row, (float4*)cv.tile_col,
+                                                    cv.nB_stride, (const double*)cv.scw, xi, c,
+                                                    (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b), std::ldexp(1.0, q),
+                                                    std::ldexp(1.0, -q), (const int*)(rg.n_a < 0 ? nullptr : rg.a),
+                                                    (int)rg.n_a, rg.scale, (int)(rg.flags & WTMD_CV_INTENSIVE), rgc,
+                                                    (float4*)(J + (size_t)rgc * h->N)));
+                    } else {
+                        auto k2 = cv.nn == 6 ? coord_tile2_kernel<3> : coord_tile2_kernel<0>;
+                        WTMD_CUDA_TRY(h, launch_pdl(k2, g2, dim3(CT_T), 0, st, pos, (const int64_t*)h->woff,
+                                                    (const int*)h->wn, A, cv.n_a, B, cv.n_b, cv.nbchunk, h->box, inv,
+                                                    cv.nn / 2, gp, (float4*)cv.tile_row, (float4*)cv.tile_col,
+                                                    cv.nB_stride, (const double*)cv.scw, xi, c,
+                                                    (const int*)(cv.n_b < 0 ? nullptr : cv.inv_b), std::ldexp(1.0, q),
+                                                    std::ldexp(1.0, -q)));
+                    }
                     mark(h, "coord_tile");
                     // J rows from the partials.  In a captured step this is
                     // a graph branch of its own beside the hills sum, which
@@ -1414,8 +1315,9 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                         WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->jf_stream[c], h->ev_jfork[c], 0));
                         js = h->jf_stream[c];
                     }
-                    coord_jfin_kernel<<<(unsigned)((h->N + 255) / 256), 256, 0, js>>>(
-                        h->N, h->atom_walker, (const int64_t*)h->woff, coord_parts(h, cv), (float4*)Jc);
+                    WTMD_CUDA_TRY(h, launch_pdl(coord_jfin_kernel, dim3((unsigned)((h->N + 255) / 256)), dim3(256), 0,
+                                                js, (long long)h->N, (const int*)h->atom_walker,
+                                                (const int64_t*)h->woff, coord_parts(h, cv), (float4*)Jc));
                     mark(h, "coord_jfin");
                     if (branch) {
                         WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_jjoin[c], js));

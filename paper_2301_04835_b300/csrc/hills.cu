@@ -101,6 +101,78 @@ __global__ void __launch_bounds__(HB) hills_f32_kernel(const float4* __restrict_
 // a pipeline's fill.
 constexpr int SMALL_P = 8;
 
+// Packed evaluation of SB hill pairs (A, B records) against NP points X
+// (pre-scaled, duplicated into both halves), added to the per-point sums.
+template <int D, bool PER, int NP, int SB>
+__device__ __forceinline__ void pairs_eval(const float4 (&A)[SB], const float4 (&B)[SB], const float2 (&X)[NP][3],
+                                           int P, const HillPrmF32& prm, float2 (&v)[NP], float2 (&g0)[NP],
+                                           float2 (&g1)[NP], float2 (&g2)[NP])
+{
+#pragma unroll
+    for (int j = 0; j < SB; ++j) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (p >= P) break;
+            float2 d0 = __fadd2_rn(X[p][0], make_float2(A[j].x, A[j].y));
+            if constexpr (PER) d0 = wrap2(d0, prm.per[0], prm.iper[0]);
+            float2 t = __ffma2_rn(d0, d0, make_float2(B[j].z, B[j].w));
+            float2 d1, d2;
+            if constexpr (D >= 2) {
+                d1 = __fadd2_rn(X[p][1], make_float2(A[j].z, A[j].w));
+                if constexpr (PER) d1 = wrap2(d1, prm.per[1], prm.iper[1]);
+                t = __ffma2_rn(d1, d1, t);
+            }
+            if constexpr (D >= 3) {
+                d2 = __fadd2_rn(X[p][2], make_float2(B[j].x, B[j].y));
+                if constexpr (PER) d2 = wrap2(d2, prm.per[2], prm.iper[2]);
+                t = __ffma2_rn(d2, d2, t);
+            }
+            const float2 e = make_float2(ex2_approx(-t.x), ex2_approx(-t.y));
+            v[p] = __fadd2_rn(v[p], e);
+            g0[p] = __ffma2_rn(e, d0, g0[p]);
+            if constexpr (D >= 2) g1[p] = __ffma2_rn(e, d1, g1[p]);
+            if constexpr (D >= 3) g2[p] = __ffma2_rn(e, d2, g2[p]);
+        }
+    }
+}
+
+// The points of a few-points launch, scaled and duplicated for the packed
+// arithmetic: X_pi = (xi_pi - c_i) a_i.
+template <int D, int NP, typename PT>
+__device__ __forceinline__ void points_scaled(const PT* __restrict__ xi, int xs, int P, const double* __restrict__ ctr,
+                                              const HillPrmF32& prm, float2 (&X)[NP][3])
+{
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float v = 0.f;
+            if (p < P && i < D) v = (float)(((double)xi[(size_t)p * xs + i] - ctr[i]) * prm.a[i]);
+            X[p][i] = make_float2(v, v);
+        }
+}
+
+// The hill pairs [q0, q1) of a CTA's split, thread tid of T taking pairs
+// q0 + tid + k T, in batches of SB (each batch's loads issued before any is
+// used; the first batch before the dependency wait).
+template <int SB> struct PairBatch {
+    float4 A[SB], B[SB];
+    __device__ __forceinline__ void load(const float4* __restrict__ hp, long long qb, long long q1, int T)
+    {
+#pragma unroll
+        for (int j = 0; j < SB; ++j) {
+            const long long q = qb + (long long)j * T;
+            if (q < q1) {
+                A[j] = __ldg(hp + 2 * q);
+                B[j] = __ldg(hp + 2 * q + 1);
+            } else {  // no hill: zero weight (height 2^-inf)
+                A[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                B[j] = make_float4(0.f, 0.f, INFINITY, INFINITY);
+            }
+        }
+    }
+};
+
 template <int D, bool PER, int NP, typename PT>
 __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __restrict__ hp,
                                                              const long long* __restrict__ k0p,
@@ -117,67 +189,20 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
     const long long per = (npairs + gridDim.y - 1) / gridDim.y;
     const long long q0 = (long long)blockIdx.y * per;
     const long long q1 = q0 + per < npairs ? q0 + per : npairs;
-    // this thread's pairs in batches of SB, each batch's loads issued before
-    // any is used; the first batch before the wait
     constexpr int SB = 4;
-    float4 A[SB], B[SB];
+    PairBatch<SB> pb;
     const long long qa = q0 + tid;
-    auto load_batch = [&](long long qb) {
-#pragma unroll
-        for (int j = 0; j < SB; ++j) {
-            const long long q = qb + (long long)j * HB;
-            if (q < q1) {
-                A[j] = __ldg(hp + 2 * q);
-                B[j] = __ldg(hp + 2 * q + 1);
-            } else {  // no hill: zero weight (height 2^-inf)
-                A[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                B[j] = make_float4(0.f, 0.f, INFINITY, INFINITY);
-            }
-        }
-    };
-    load_batch(qa);
+    pb.load(hp, qa, q1, HB);
     pdl_wait();
     pdl_trigger();
     float2 X[NP][3];
-#pragma unroll
-    for (int p = 0; p < NP; ++p)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            float v = 0.f;
-            if (p < P && i < D) v = (float)(((double)xi[(size_t)p * xs + i] - ctr[i]) * prm.a[i]);
-            X[p][i] = make_float2(v, v);
-        }
+    points_scaled<D, NP, PT>(xi, xs, P, ctr, prm, X);
     float2 v[NP], g0[NP], g1[NP], g2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
     for (long long qb = qa; qb < q1; qb += (long long)SB * HB) {
-        if (qb != qa) load_batch(qb);
-#pragma unroll
-        for (int j = 0; j < SB; ++j) {
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                if (p >= P) break;
-                float2 d0 = __fadd2_rn(X[p][0], make_float2(A[j].x, A[j].y));
-                if constexpr (PER) d0 = wrap2(d0, prm.per[0], prm.iper[0]);
-                float2 t = __ffma2_rn(d0, d0, make_float2(B[j].z, B[j].w));
-                float2 d1, d2;
-                if constexpr (D >= 2) {
-                    d1 = __fadd2_rn(X[p][1], make_float2(A[j].z, A[j].w));
-                    if constexpr (PER) d1 = wrap2(d1, prm.per[1], prm.iper[1]);
-                    t = __ffma2_rn(d1, d1, t);
-                }
-                if constexpr (D >= 3) {
-                    d2 = __fadd2_rn(X[p][2], make_float2(B[j].x, B[j].y));
-                    if constexpr (PER) d2 = wrap2(d2, prm.per[2], prm.iper[2]);
-                    t = __ffma2_rn(d2, d2, t);
-                }
-                const float2 e = make_float2(ex2_approx(-t.x), ex2_approx(-t.y));
-                v[p] = __fadd2_rn(v[p], e);
-                g0[p] = __ffma2_rn(e, d0, g0[p]);
-                if constexpr (D >= 2) g1[p] = __ffma2_rn(e, d1, g1[p]);
-                if constexpr (D >= 3) g2[p] = __ffma2_rn(e, d2, g2[p]);
-            }
-        }
+        if (qb != qa) pb.load(hp, qb, q1, HB);
+        pairs_eval<D, PER, NP, SB>(pb.A, pb.B, X, P, prm, v, g0, g1, g2);
     }
     __shared__ CF4 red[HB / 32];
 #pragma unroll
@@ -198,6 +223,112 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
         }
     }
     finalize_if_last_cf(partial, P, out);
+}
+
+// Few points on one thread-block cluster: the CL CTAs of the cluster split
+// the hill range, and each copies its share of the pair records into shared
+// memory with one bulk (TMA) copy issued before the dependency wait, so the
+// records are on chip when the points are known.  The split sums meet in
+// distributed shared memory: rank 0 adds the ranks' compensated sums in rank
+// order and writes V and dV.  No global partials, fences or tickets;
+// deterministic.  For short hill lists (a walker's point in a step), where
+// the reduction, not the streaming, is the cost.  Records beyond the shared
+// share (lists longer than the capacity the launch was sized for) are read
+// from global memory.
+constexpr int HBC = 256;  // threads per CTA of the cluster kernel
+
+template <int D, bool PER, int NP, typename PT>
+__global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __restrict__ hp,
+                                                                const long long* __restrict__ k0p,
+                                                                const long long* __restrict__ cnt,
+                                                                const PT* __restrict__ xi, int xs, int P,
+                                                                const double* __restrict__ ctr, HillPrmF32 prm,
+                                                                HillOut<float> out, int smem_pairs)
+{
+    extern __shared__ __align__(128) float4 crec[];  // [smem_pairs][2]
+    __shared__ __align__(8) uint64_t cbar;
+    const int tid = threadIdx.x;
+    const long long k0 = k0p ? *k0p : 0;
+    const long long count = *cnt;
+    const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
+    hp += (size_t)(k0 >> 1) * 2;
+    const unsigned rank = cluster_ctarank(), CL = cluster_nctarank();
+    const long long per = (npairs + CL - 1) / CL;
+    const long long q0 = (long long)rank * per;
+    const long long nq = q0 < npairs ? (per < npairs - q0 ? per : npairs - q0) : 0;
+    const int npf = (int)(nq < smem_pairs ? nq : smem_pairs);
+    if (tid == 0) {
+        mbar_init(&cbar, 1);
+        fence_mbar_init();
+        if (npf > 0) {
+            mbar_arrive_expect_tx(&cbar, (uint32_t)npf * 32u);
+            bulk_g2s(crec, hp + 2 * q0, (uint32_t)npf * 32u, &cbar);
+        }
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    pdl_wait();
+    pdl_trigger();
+    float2 X[NP][3];
+    points_scaled<D, NP, PT>(xi, xs, P, ctr, prm, X);
+    float2 v[NP], g0[NP], g1[NP], g2[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
+    bool landed = npf == 0 || mbar_wait_bounded(&cbar, 0, out.status);
+    if (landed) {
+        for (long long k = tid; k < nq; k += HBC) {
+            float4 A[1], B[1];
+            if (k < npf) {
+                A[0] = crec[2 * k];
+                B[0] = crec[2 * k + 1];
+            } else {
+                A[0] = __ldg(hp + 2 * (q0 + k));
+                B[0] = __ldg(hp + 2 * (q0 + k) + 1);
+            }
+            pairs_eval<D, PER, NP, 1>(A, B, X, P, prm, v, g0, g1, g2);
+        }
+    }
+    __shared__ CF4 red[HBC / 32];
+    __shared__ __align__(16) CF4 cta_sum[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (p >= P) break;
+        CF4 a{};
+        a.v[0] = cf_add(cf_add(a.v[0], v[p].x), v[p].y);
+        a.v[1] = cf_add(cf_add(a.v[1], g0[p].x), g0[p].y);
+        a.v[2] = cf_add(cf_add(a.v[2], g1[p].x), g1[p].y);
+        a.v[3] = cf_add(cf_add(a.v[3], g2[p].x), g2[p].y);
+        cf4_lane_sum<32>(a);
+        __syncthreads();  // red[] free from the previous point
+        if (tid % 32 == 0) red[tid / 32] = a;
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < HBC / 32; ++w) cf4_add(a, red[w]);
+            cta_sum[p] = a;
+        }
+    }
+    cluster_sync();  // every rank's sums are in its shared memory
+    if (rank == 0 && tid < 32) {
+        // lane r reads rank r's sums (all ranks' loads in flight together),
+        // then the ranks are added in rank order through shuffles
+        for (int p = 0; p < NP && p < P; ++p) {
+            CF4 mine{};
+            if ((unsigned)tid < CL) {
+                const float4* q = reinterpret_cast<const float4*>(&cta_sum[p]);
+                const float4 u = ld_dsmem_f4(q, (unsigned)tid), w = ld_dsmem_f4(q + 1, (unsigned)tid);
+                mine = CF4{{cf{u.x, u.y}, cf{u.z, u.w}, cf{w.x, w.y}, cf{w.z, w.w}}};
+            }
+            CF4 a{};
+            for (unsigned r = 0; r < CL; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const cf t{__shfl_sync(0xffffffffu, mine.v[i].hi, (int)r), __shfl_sync(0xffffffffu, mine.v[i].lo, (int)r)};
+                    a.v[i] = cf_add(a.v[i], t);
+                }
+            if (tid == 0) emit_cf(p, a, out);
+        }
+    }
+    cluster_sync();  // no rank leaves while rank 0 reads its shared memory
+    if (tid == 0) mbar_inval(&cbar);
 }
 
 template <int TH, bool PER>
@@ -293,9 +424,23 @@ static int num_sms()
 
 // Tile heuristic: few points -> many hill lanes per point; many points ->
 // one thread per point.  Splits fill ~4 CTAs per SM over the hill range.
+static bool cluster16_ok();
+static int cluster_smem_pairs(long long cap_pairs, int CL);
+
 static Plan plan_for(long long P, long long cap_pairs, bool fp32)
 {
     Plan pl;
+    // a walker's few points on a list whose cluster shares fit in shared
+    // memory: the cluster kernel (records staged by TMA before the
+    // dependency wait, sums met in distributed shared memory)
+    if (fp32 && P <= SMALL_P) {
+        const int cl = cluster16_ok() ? 16 : 8;
+        if ((cap_pairs + cl - 1) / cl <= cluster_smem_pairs(cap_pairs, cl)) {
+            pl.th = -1;
+            pl.split = cl;
+            return pl;
+        }
+    }
     if (P >= 1024) pl.th = 1;
     else if (P >= 64) pl.th = 4;
     else if (P > SMALL_P) pl.th = 32;
@@ -340,11 +485,71 @@ static void launch_f32_small(dim3 grid, cudaStream_t st, bool pdl, const float4*
         hills_f32_small_kernel<D, PER, NP, PT><<<grid, HB, 0, st>>>(hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
 }
 
+// The cluster kernel: one cluster of CL CTAs (CL > 8 needs the
+// non-portable cluster size), a programmatic dependent when pdl is set.
+// Pair records a CTA of the cluster kernel keeps in shared memory: its share
+// of the handle's capacity, at most 160 KB.
+static int cluster_smem_pairs(long long cap_pairs, int CL)
+{
+    return (int)std::min<long long>((cap_pairs + CL - 1) / CL, (160 * 1024) / 32);
+}
+
+template <int D, bool PER, int NP, typename PT>
+static cudaError_t launch_f32_cluster(int CL, long long cap_pairs, cudaStream_t st, bool pdl, const float4* hp,
+                                      const long long* k0p, const long long* cnt, const PT* xi, int xs, int P,
+                                      const double* ctr, const HillPrmF32& prm, const HillOut<float>& o)
+{
+    auto k = hills_f32_cluster_kernel<D, PER, NP, PT>;
+    const int sp = cluster_smem_pairs(cap_pairs, CL);
+    const size_t smem = (size_t)sp * 32;
+    // the kernel's attributes, once per device (the first launch comes
+    // before any capture: the step's force evaluation or a direct sum)
+    static bool set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!set[dev]) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        set[dev] = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1, CL);
+    cfg.blockDim = dim3(HBC);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[3];
+    int n = 0;
+    at[n].id = cudaLaunchAttributeClusterDimension;
+    at[n].val.clusterDim.x = 1;
+    at[n].val.clusterDim.y = CL;
+    at[n].val.clusterDim.z = 1;
+    ++n;
+    if (pdl) {
+        at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    at[n].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    at[n].val.sharedMemCarveout = 100;
+    ++n;
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, k, hp, k0p, cnt, xi, xs, P, ctr, prm, o, sp);
+}
+
 template <int D, bool PER, typename PT>
 static void launch_f32_d(int th, dim3 grid, cudaStream_t st, bool pdl, const float4* hp, const long long* k0p,
                          const long long* cnt, const PT* xi, int xs, int P, const double* ctr, const HillPrmF32& prm,
-                         dbl4* part, const HillOut<float>& o)
+                         dbl4* part, const HillOut<float>& o, long long cap_pairs)
 {
+    if (th < 0) {  // the cluster kernel (P <= SMALL_P), one cluster of grid.y CTAs
+        if (P == 1) launch_f32_cluster<D, PER, 1, PT>((int)grid.y, cap_pairs, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, o);
+        else launch_f32_cluster<D, PER, SMALL_P, PT>((int)grid.y, cap_pairs, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, o);
+        return;
+    }
     if (th == 0) {  // the few-points kernel (P <= SMALL_P), grid (1, splits)
         if (P == 1) launch_f32_small<D, PER, 1, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
         else launch_f32_small<D, PER, SMALL_P, PT>(grid, st, pdl, hp, k0p, cnt, xi, xs, P, ctr, prm, part, o);
@@ -361,15 +566,15 @@ static void launch_f32_d(int th, dim3 grid, cudaStream_t st, bool pdl, const flo
 template <typename PT>
 static void launch_f32_pt(int d, bool per, int th, dim3 grid, cudaStream_t st, bool pdl, const float4* hp,
                           const long long* k0p, const long long* cnt, const PT* x, int xs, int P, const double* ctr,
-                          const HillPrmF32& prm, dbl4* part, const HillOut<float>& o)
+                          const HillPrmF32& prm, dbl4* part, const HillOut<float>& o, long long cap_pairs)
 {
     switch (d * 2 + (per ? 1 : 0)) {
-    case 2: launch_f32_d<1, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
-    case 3: launch_f32_d<1, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
-    case 4: launch_f32_d<2, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
-    case 5: launch_f32_d<2, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
-    case 6: launch_f32_d<3, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
-    default: launch_f32_d<3, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o); break;
+    case 2: launch_f32_d<1, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
+    case 3: launch_f32_d<1, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
+    case 4: launch_f32_d<2, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
+    case 5: launch_f32_d<2, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
+    case 6: launch_f32_d<3, false, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
+    default: launch_f32_d<3, true, PT>(th, grid, st, pdl, hp, k0p, cnt, x, xs, P, ctr, prm, part, o, cap_pairs); break;
     }
 }
 
@@ -421,8 +626,8 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
     Plan pl = plan_for(P, cap_pairs, h->prec == WTMD_F32);
     for (auto& t : h->tuned)
         if (max_hills <= 0 && t.first == ((P << 2) | h->d)) pl.th = t.second.th, pl.split = t.second.split;
-    if (pl.th == 0 && (h->prec != WTMD_F32 || P > SMALL_P)) pl.th = 256;  // a tuned plan for another handle kind
-    const int tp = pl.th ? HB / pl.th : (int)P;
+    if (pl.th <= 0 && (h->prec != WTMD_F32 || P > SMALL_P)) pl.th = 256;  // a tuned plan for another handle kind
+    const int tp = pl.th > 0 ? HB / pl.th : (int)P;
     const long long tiles = (P + tp - 1) / tp;
     if (tiles > 0x7fffffff) return WTMD_EINVAL;
     const size_t need = (size_t)pl.split * (size_t)P * sizeof(dbl4);
@@ -461,10 +666,10 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
                          h->status};
         if (xi_f64)
             launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, pdl, h->hills32, k0p, k1p, (const double*)xi,
-                                  xs, Pi, h->ctr, prm, part, o);
+                                  xs, Pi, h->ctr, prm, part, o, cap_pairs);
         else
             launch_f32_pt<float>(h->d, per, pl.th, grid, h->stream, pdl, h->hills32, k0p, k1p, (const float*)xi, xs,
-                                 Pi, h->ctr, prm, part, o);
+                                 Pi, h->ctr, prm, part, o, cap_pairs);
         mark(h, "hills_sum_f32");
         if (!fused) {
             hills_finalize_cf_kernel<<<(Pi + 7) / 8, 256, 0, h->stream>>>(part, pl.split, Pi, o);
@@ -495,6 +700,64 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         }
     }
     WTMD_CUDA_TRY(h, cudaGetLastError());
+    return WTMD_OK;
+}
+
+// Whether clusters of 16 CTAs of the cluster kernel can run on this device
+// (a non-portable size).
+static bool cluster16_probe()
+{
+    auto k = hills_f32_cluster_kernel<2, false, 1, double>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1, 16);
+    cfg.blockDim = dim3(HBC);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 16;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+static bool cluster16_ok()
+{
+    static int known[64] = {0};  // 0 unknown, 1 yes, 2 no, per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (!known[dev]) known[dev] = cluster16_probe() ? 1 : 2;
+    return known[dev] == 1;
+}
+
+// A plan set by the caller (wtmd_hills_plan), checked like the tuner's
+// candidates.
+int hills_set_plan(wtmd_t* h, int64_t P, int lanes, int splits)
+{
+    const bool few = h->prec == WTMD_F32 && P >= 1 && P <= SMALL_P;
+    bool ok = P >= 1 && P <= (1 << 24) && splits >= 1 && splits <= 65535;
+    if (lanes == 0) ok = ok && few;
+    else if (lanes == -1) ok = ok && few && (splits == 8 || (splits == 16 && cluster16_ok()));
+    else ok = ok && (lanes == 1 || lanes == 4 || lanes == 32 || lanes == 256);
+    if (!ok) {
+        h->err = "hills plan: lanes must be 1, 4, 32, 256, 0 or -1 (FP32, P <= 8; -1 with splits 8 or 16)";
+        return WTMD_EINVAL;
+    }
+    const long long key = (P << 2) | h->d;
+    h->tuned.erase(std::remove_if(h->tuned.begin(), h->tuned.end(), [&](const std::pair<long long, Tuned>& t) {
+                       return t.first == key;
+                   }),
+                   h->tuned.end());
+    h->tuned.push_back({key, Tuned{lanes, splits}});
     return WTMD_OK;
 }
 
@@ -529,8 +792,9 @@ int hills_tune(wtmd_t* h, int64_t P, int* th_out, int* split_out, double* ms_out
                    }),
                    h->tuned.end());
     const long long nch = (h->cap_pairs + CHUNK - 1) / CHUNK;
-    // 0: the few-points kernel, a candidate for FP32 handles with P <= SMALL_P
-    const int ths[] = {0, 1, 4, 32, 256};
+    // 0: the few-points kernel, -1: the cluster kernel (split = cluster
+    // size), candidates for FP32 handles with P <= SMALL_P
+    const int ths[] = {-1, 0, 1, 4, 32, 256};
     const int splits[] = {1, 2, 4, 8, 16, 32, 64, 96, 128, 148, 192, 296, 444, 592, 888, 1184};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -540,10 +804,11 @@ int hills_tune(wtmd_t* h, int64_t P, int* th_out, int* split_out, double* ms_out
     Tuned bt = {p0.th, p0.split};
     int rc = WTMD_OK;
     for (int th : ths) {
-        if (th == 0 && (h->prec != WTMD_F32 || P > SMALL_P)) continue;
-        const long long tiles = th ? (P + HB / th - 1) / (HB / th) : 1;
+        if (th <= 0 && (h->prec != WTMD_F32 || P > SMALL_P)) continue;
+        const long long tiles = th > 0 ? (P + HB / th - 1) / (HB / th) : 1;
         for (int sp : splits) {
             if (sp > nch || tiles * sp > (1ll << 20) || (size_t)sp * P * sizeof(dbl4) > (256ull << 20)) continue;
+            if (th < 0 && !(sp == 8 || (sp == 16 && cluster16_ok()))) continue;
             h->tuned.push_back({key, Tuned{th, sp}});
             for (int r = 0; r < 2 && rc == WTMD_OK; ++r) rc = launch_hills(h, xi, h->prec == WTMD_F64, d, P, V, dV, d);
             cudaEventRecord(e0, h->stream);

@@ -152,6 +152,38 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Thread-block clusters: the CTA's rank and the cluster's size, a barrier
+// of all threads of the cluster (release / acquire: shared-memory writes
+// before it are visible to the other CTAs after it), and a 16-byte load from
+// the shared memory of CTA `rank` at the address of a local variable.
+__device__ __forceinline__ unsigned cluster_ctarank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float4 ld_dsmem_f4(const void* local, unsigned rank)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(ra)
+                 : "memory");
+    return v;
+}
+
 // Compensated FP32 sum (hi + lo, Knuth's TwoSum): about 48 significant bits
 // from FP32 instructions only (FP64 throughput is very low on this part).
 struct cf {
@@ -275,6 +307,16 @@ struct Tuned {
 
 struct Surrogate;  // MLP surrogate of the hills sum (mlp.cu)
 
+// Plan of the persistent single-system step (sys_step.cu).
+struct SysStepPlan {
+    bool ready = false;   // set up for the current CVs and capacity
+    int grid = 0;         // CTAs (one per SM)
+    int hpf = 0;          // hill pairs a CTA keeps in shared memory
+    size_t smem = 0;      // dynamic shared memory per CTA
+    double scw[3] = {0.0, 0.0, 0.0};  // coordination scales of walker 0
+    unsigned* bar = nullptr;          // grid-barrier counter and generation
+};
+
 // Plan of the persistent multi-walker step (walkers.cu).
 struct WalkerPlan {
     int T = 0;             // targets per pair task
@@ -380,6 +422,8 @@ struct wtmd_t {
     bool no_graph = false;          // capture failed: replay eagerly
     bool jz_pre = false;            // the step zeroed the tile-path coordination J rows before BAOAB
     wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
+    wtmd::SysStepPlan ss;           // persistent single-system step
+    bool fused_on = false;          // the caller allowed the persistent single-system step
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
     // profiling: when `prof` is set, mark() records a CUDA event on the
@@ -430,7 +474,8 @@ int launch_hills(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t 
 int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xi_stride, int64_t P, void* V, void* dV,
                        int dV_stride, const long long* k0p, const long long* k1p, long long max_hills, bool pdl);
 long long surrogate_tail_bound(const wtmd_t* h);
-int hills_tune(wtmd_t* h, int64_t P, int* th, int* split, double* ms);  // hills.cu                // hills beyond k0 between refits (0: unbounded)
+int hills_tune(wtmd_t* h, int64_t P, int* th, int* split, double* ms);  // hills.cu
+int hills_set_plan(wtmd_t* h, int64_t P, int lanes, int splits);       // hills.cu                // hills beyond k0 between refits (0: unbounded)
 int launch_scatter(wtmd_t* h, void* force, const void* vel_or_null, bool kick);
 int launch_scatter_deposit(wtmd_t* h);                          // kick + deposit (+ grid) of a step
 // surrogate (mlp.cu)
@@ -446,6 +491,10 @@ int nl_request(wtmd_t* h);                                       // rebuild the 
 int nl_reset(wtmd_t* h);                                         // cell counts and rebuild flag to 0
 int launch_baoab_first(wtmd_t* h, int jmask, int xmask);         // Jacobian rows / CV values to zero
 bool coord_factored(const wtmd_t* h, int c);  // CV c keeps J as FP32 tile partials (contracted by the kick)
+int folded_rg(const wtmd_t* h);                                  // Rg CV computed in the launch of coordination CV 0, or -1
+bool sys_step_eligible(const wtmd_t* h, std::string* why);       // the step can run as one persistent launch
+int sys_step_setup(wtmd_t* h);                                   // its plan (outside graph capture)
+int launch_sys_step(wtmd_t* h);                                  // one step as one cooperative launch
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
 int launch_grid_rebuild(wtmd_t* h);
 int launch_fes(wtmd_t* h, double* out);
@@ -468,11 +517,16 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
+    // the largest shared-memory carveout: the kernels that a step runs side
+    // by side then share one SM configuration, so a waiting dependent's CTAs
+    // are not kept off an SM whose carveout another kernel chose smaller
+    at[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    at[1].val.sharedMemCarveout = 100;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 }  // namespace wtmd

@@ -157,6 +157,69 @@ def test_hills_eval_matches_oracle(prec, d, periodic, P, H):
     _close_dV(to_np(dV), dVr, grad_scale(xr, hills, sigma, per), prec)
 
 
+CLUSTER_CASES = [
+    # d, periodic, P, H, cluster size
+    (1, False, 1, 1, 8),
+    (2, False, 1, 100001, 8),
+    (2, False, 1, 100001, 16),
+    (3, True, 3, 4097, 16),
+    (2, True, 8, 200003, 16),
+    (3, False, 1, 0, 8),
+]
+
+
+@pytest.mark.parametrize("d,periodic,P,H,cl", CLUSTER_CASES)
+def test_hills_cluster_kernel_matches_oracle(d, periodic, P, H, cl):
+    """The few-points sum on one thread-block cluster (split sums met in
+    distributed shared memory), forced by wtmd_hills_plan; twice in a row,
+    bitwise equal."""
+    wt = _wt()
+    import oracle as o
+
+    sigma = [0.35, 0.2, 0.5][:d] if periodic else [0.05, 0.1, 0.07][:d]
+    lo, hi = ([-np.pi] * d, [np.pi] * d) if periodic else ([-1.0, 0.5, 2.0][:d], [1.5, 2.0, 3.0][:d])
+    per = [2 * np.pi] * d if periodic else [0.0] * d
+    hills = synth.uniform_hills(H, lo, hi, seed=d * 100 + P + 7)
+    pts = synth.uniform_points(P, lo, hi, seed=d * 100 + P + 8)
+    if H == 1:  # a point near the one hill (far away, V underflows FP32)
+        pts = hills[:1, :d] + 0.3 * np.asarray(sigma)
+    m = wt.Wtmd(precision="f32", sigma=sigma, capacity=max(H, 1) + 3, walker_sizes=[1])
+    for i in range(d):
+        m.cv_define(wt.CV_COMPONENT, a=[0], axis=i, period=per[i])
+    if H:
+        m.hills_load(hills)
+    try:
+        m.hills_plan(P, -1, cl)
+    except wt.WtmdError:
+        assert cl == 16
+        pytest.skip("clusters of 16 CTAs are not available on this device")
+    x = torch.tensor(pts, dtype=torch.float32, device="cuda")
+    V, dV = m.hills_eval(x)
+    V2, dV2 = m.hills_eval(x)
+    torch.cuda.synchronize()
+    assert torch.equal(V, V2) and torch.equal(dV, dV2)
+    xr = _f32(pts)
+    if H == 0:
+        assert torch.all(V == 0) and torch.all(dV == 0)
+        return
+    Vr, dVr = o.hills_sum(xr, hills, sigma, per)
+    _close_V(to_np(V), Vr, "f32")
+    _close_dV(to_np(dV), dVr, grad_scale(xr, hills, sigma, per), "f32")
+
+
+def test_hills_plan_rejects_bad_values():
+    wt = _wt()
+    m = wt.Wtmd(precision="f32", sigma=[0.1], capacity=10, walker_sizes=[1])
+    m.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+    for P, lanes, splits in ((9, 0, 8), (9, -1, 8), (1, -1, 12), (1, 3, 8), (1, 4, 0), (0, 4, 8)):
+        with pytest.raises(wt.WtmdError):
+            m.hills_plan(P, lanes, splits)
+    m64 = wt.Wtmd(precision="f64", sigma=[0.1], capacity=10, walker_sizes=[1])
+    m64.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+    with pytest.raises(wt.WtmdError):
+        m64.hills_plan(1, -1, 8)
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_hills_eval_edge_cases(prec):
     wt = _wt()
@@ -478,7 +541,9 @@ def test_hills_tune_keeps_results():
     hills = synth.walk_hills(3000, c - 0.3, c + 0.3, 0.05, seed=4)
     m.hills_load(hills)
     th, sp, ms = m.hills_tune(1)
-    assert th in (0, 1, 4, 32, 256) and sp >= 1 and ms > 0  # 0: the few-points kernel
+    # 0: the few-points kernel, -1: the cluster kernel (8 or 16 CTAs)
+    assert th in (-1, 0, 1, 4, 32, 256) and sp >= 1 and ms > 0
+    assert th != -1 or sp in (8, 16)
     V, xi, dV = m.bias_eval(pos)
     Vr, dVr = o.hills_sum(to_np(xi), hills, spec["sigma"])
     _close_V(to_np(V), Vr, "f32")
