@@ -344,6 +344,15 @@ int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double* ms, int32
  * measured denominators of the hills-sum roofline; *ms = kernel time. */
 int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
 
+/* Check of the bounded device waits (failure detection without a fault): a
+ * cooperative launch of `blocks` CTAs (1 per SM at most) in which CTA
+ * `absent` leaves before the grid barrier (absent < 0: none leaves); the
+ * others wait for its arrival, give up after limit_cycles SM cycles (1 ...
+ * 2^31) and record the timeout.  *timed_out (host) receives 1 if the wait
+ * gave up, else 0.  The device stays usable.  Errors: WTMD_EINVAL for bad
+ * sizes, WTMD_ENOMEM, WTMD_ECUDA. */
+int wtmd_barrier_probe(int32_t blocks, int32_t absent, int64_t limit_cycles, int32_t* timed_out);
+
 /* Run each MD step of a multi-walker handle as one persistent (cooperative)
  * kernel launch: BAOAB, all-pairs LJ, coordination and Rg CVs, hills sum over
  * the shared hill list, bias force and deposition for every walker, with
@@ -354,6 +363,17 @@ int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
  * and RG (all atoms), walkers of at most 8192 atoms; else WTMD_EINVAL.
  * enable = 0 returns to the per-kernel step. */
 int wtmd_walkers_persistent(wtmd_t* h, int32_t enable);
+
+/* Bound of the grid-barrier waits of this handle's persistent launches (the
+ * multi-walker step and the single-system step), in SM cycles: 0 restores
+ * the default 2^31 (about a second at the maximum clock).  A wait that runs
+ * out records a timeout that the next wtmd_check (or step_n with checking)
+ * returns as WTMD_ETIMEOUT; every CTA then leaves the launch, the step's
+ * results are not valid, and the handle stays usable (restore a checkpoint
+ * to continue).  A short limit lets a test see that path.  Drops captured
+ * step graphs when the limit changes.  Errors: WTMD_EINVAL outside
+ * [0, 2^31]. */
+int wtmd_wait_limit(wtmd_t* h, int64_t cycles);
 
 /* The MD step of a single periodic system as one persistent (cooperative)
  * kernel launch per step (Sec. 3.2.1 steps (a)-(f) with the metadynamics

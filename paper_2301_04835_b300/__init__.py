@@ -72,7 +72,7 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune",
            "wtmd_grid_eval", "wtmd_bias_source", "wtmd_checkpoint_size", "wtmd_checkpoint_save",
            "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate",
-           "wtmd_step_host", "wtmd_fused_step", "wtmd_hills_plan"]
+           "wtmd_step_host", "wtmd_fused_step", "wtmd_hills_plan", "wtmd_wait_limit", "wtmd_barrier_probe"]
 
 BIAS_HILLS, BIAS_GRID, BIAS_HARMONIC = 0, 1, 2
 
@@ -112,6 +112,8 @@ def lib() -> C.CDLL:
     L.wtmd_walkers_persistent.argtypes = [vp, i32]
     L.wtmd_fused_step.argtypes = [vp, i32, C.POINTER(i32)]
     L.wtmd_hills_plan.argtypes = [vp, i64, i32, i32]
+    L.wtmd_wait_limit.argtypes = [vp, i64]
+    L.wtmd_barrier_probe.argtypes = [i32, i32, i64, C.POINTER(i32)]
     L.wtmd_autotune.argtypes = [vp, i64, C.POINTER(i32)]
     dp, fp = C.POINTER(C.c_double), C.POINTER(C.c_float)
     L.wtmd_surrogate.argtypes = [vp, i32, C.c_double, i64]
@@ -326,6 +328,10 @@ class Wtmd:
         """Set the hills-sum plan for P points (lanes per point 1/4/32/256,
         0 = few-points kernel, -1 = cluster kernel; splits)."""
         self._err(lib().wtmd_hills_plan(self.h, int(P), int(lanes), int(splits)), "wtmd_hills_plan")
+
+    def wait_limit(self, cycles: int = 0):
+        """Grid-barrier wait bound of the persistent launches (SM cycles; 0 = default)."""
+        self._err(lib().wtmd_wait_limit(self.h, int(cycles)), "wtmd_wait_limit")
 
     def walkers_persistent(self, enable: bool = True):
         """Run each step as one persistent launch over all walkers."""
@@ -626,6 +632,16 @@ def probe_peak(kind: int):
     if rc:
         raise WtmdError(rc, "wtmd_probe_peak")
     return v.value, ms.value
+
+
+def barrier_probe(blocks: int, absent: int, limit_cycles: int) -> bool:
+    """Cooperative grid where CTA `absent` never reaches the grid barrier:
+    True if the others' bounded wait gave up (wtmd_barrier_probe)."""
+    out = C.c_int32()
+    rc = lib().wtmd_barrier_probe(int(blocks), int(absent), int(limit_cycles), C.byref(out))
+    if rc != OK:
+        raise WtmdError(rc, "wtmd_barrier_probe")
+    return bool(out.value)
 
 
 def particles(x, dtype, device="cuda"):

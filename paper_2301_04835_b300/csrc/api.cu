@@ -1130,8 +1130,9 @@ extern "C" int wtmd_checkpoint_load(wtmd_t* h, const void* in, int64_t n_bytes)
     WTMD_CUDA_TRY(h, cudaMemcpy(h->ctr, hd.ctr, sizeof(hd.ctr), cudaMemcpyHostToDevice));
     // the restored forces belong to the restored positions; the neighbour
     // lists were built for other positions and are rebuilt by the next step
+    // (from clean cell counts: a step that gave up may have left them)
     h->forces_valid = true;
-    if ((rc = nl_request(h))) return rc;
+    if ((rc = nl_reset(h)) || (rc = nl_request(h))) return rc;
     WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return WTMD_OK;
 }
@@ -1211,6 +1212,15 @@ extern "C" int wtmd_profile_step(wtmd_t* h, int64_t n_steps, char* names, double
         ms[i] = acc[i] / n_steps;
     }
     *n_out = n;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_wait_limit(wtmd_t* h, int64_t cycles)
+{
+    if (!h) return WTMD_EINVAL;
+    if (cycles < 0 || cycles > kWaitLimit) FAIL(h, WTMD_EINVAL, "wait limit must be in [0, 2^31] SM cycles");
+    if (h->wait_limit != cycles) drop_graphs(h);  // the limit is a launch argument
+    h->wait_limit = cycles;
     return WTMD_OK;
 }
 

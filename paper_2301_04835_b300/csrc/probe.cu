@@ -7,6 +7,15 @@
 
 namespace wtmd {
 
+// A cooperative grid in which CTA `absent` leaves at once: the others wait at
+// the grid barrier for an arrival that never comes, give up after `limit`
+// cycles and record ST_TIMEOUT (absent < 0: everyone arrives).
+__global__ void barrier_probe_kernel(unsigned* bar, unsigned* status, int absent, long long limit)
+{
+    if ((int)blockIdx.x == absent) return;
+    grid_barrier(bar, gridDim.x, status, limit);
+}
+
 __global__ void __launch_bounds__(256) probe_ex2_kernel(int iters, float seed, float* out)
 {
     float x[8];
@@ -74,4 +83,37 @@ extern "C" int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms)
     *ops_per_s = ops / (best * 1e-3);
     if (ms) *ms = best;
     return WTMD_OK;
+}
+
+extern "C" int wtmd_barrier_probe(int32_t blocks, int32_t absent, int64_t limit_cycles, int32_t* timed_out)
+{
+    if (blocks < 1 || absent >= blocks || limit_cycles < 1 || limit_cycles > wtmd::kWaitLimit) return WTMD_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+        return WTMD_ECUDA;
+    if (blocks > sms) return WTMD_EINVAL;  // one CTA per SM: all co-resident
+    unsigned* buf = nullptr;  // [0..3] barrier, [4] status
+    if (cudaMalloc(&buf, 8 * sizeof(unsigned)) != cudaSuccess) return WTMD_ENOMEM;
+    int rc = WTMD_OK;
+    if (cudaMemset(buf, 0, 8 * sizeof(unsigned)) != cudaSuccess) rc = WTMD_ECUDA;
+    if (!rc) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(64);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        unsigned* status = buf + 4;
+        if (cudaLaunchKernelEx(&cfg, wtmd::barrier_probe_kernel, buf, status, (int)absent, (long long)limit_cycles) !=
+                cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            rc = WTMD_ECUDA;
+        unsigned st = 0;
+        if (!rc && cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) rc = WTMD_ECUDA;
+        if (!rc && timed_out) *timed_out = (st & wtmd::ST_TIMEOUT) ? 1 : 0;
+    }
+    cudaFree(buf);
+    return rc;
 }

@@ -102,6 +102,7 @@ struct SsArgs {
     float* h32;
     unsigned* bar;
     unsigned* status;
+    long long wait_limit;  // grid-barrier wait bound (SM cycles)
 };
 
 // Barrier of one 256-thread warp group of the CTA (named barrier 1 + group).
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(SS_T, 1) sys_step_kernel(SsArgs a)
     auto leave = [&]() {
         if (npf > 0) mbar_wait_bounded(&hbar, 0, a.status);
     };
-    if (!grid_barrier(a.bar, G, a.status)) return leave();
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return leave();
 
     // ---- rebuild of the neighbour lists, when an atom moved past half the skin
     if (tid == 0) rebuild = *(volatile unsigned*)a.ctl != 0u;
@@ -275,11 +276,11 @@ __global__ void __launch_bounds__(SS_T, 1) sys_step_kernel(SsArgs a)
             if (slot < a.ccap) a.catoms[(size_t)cell * a.ccap + slot] = (int)i;
             else atomicOr(a.status, ST_CELL);
         }
-        if (!grid_barrier(a.bar, G, a.status)) return leave();
+        if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return leave();
         for (int c = b; c < a.ncells; c += G)
             nl_build_cell<float>(c, a.x, a.box, a.nc[0], a.nc[1], a.nc[2], a.ccap, a.ccount, a.catoms, a.nbr, a.ncnt,
                                  a.xref, a.cap8, a.rl2, a.status, work);
-        if (!grid_barrier(a.bar, G, a.status)) return leave();
+        if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return leave();
     }
 
     // ---- B: LJ forces (warps 0-7) beside the CV tasks (warps 8-15)
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(SS_T, 1) sys_step_kernel(SsArgs a)
                 ss_rg_task(a, cv, gtid, 1, ru, sm3, sm1);
         }
     }
-    if (!grid_barrier(a.bar, G, a.status)) return leave();
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return leave();
 
     // ---- C: hills partial of the CTA's split; J rows of the coordination CVs
     {
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(SS_T, 1) sys_step_kernel(SsArgs a)
             }
         }
     }
-    if (!grid_barrier(a.bar, G, a.status)) return;
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
     // ---- D: V and dV/dxi (the same fixed order in every CTA), deposition,
     // bias force and closing kick
@@ -597,6 +598,7 @@ int launch_sys_step(wtmd_t* h)
     a.h32 = (float*)h->hills32;
     a.bar = k.bar;
     a.status = h->status;
+    a.wait_limit = h->wait_limit > 0 ? h->wait_limit : kWaitLimit;
     // a clean launch leaves the barrier counter at 0; after a timed-out
     // barrier wtmd_check clears it
     cudaLaunchConfig_t cfg{};

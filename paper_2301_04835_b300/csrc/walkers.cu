@@ -79,6 +79,7 @@ struct WkArgs {
     unsigned* bar;
     unsigned* status;
     int max_wn;
+    long long wait_limit;  // grid-barrier wait bound (SM cycles)
 };
 
 // Targets per pair task of an n-atom walker: the plan's T, or for a smaller
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
         const long long t = *a.step;
         for (long long i = (long long)blockIdx.x * WK_T + tid; i < a.N; i += (long long)G * WK_T)
             baoab_first_atom<float>(i, t, a.x, a.v, a.f, a.seed, a.half, a.inv_m, a.c1, a.c2, 3);
-        if (!grid_barrier(a.bar, G, a.status)) return;
+        if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
     }
 
     // ---- P1: pair tasks, taken from a queue in decreasing cost (greedy
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
             }
         }
     }
-    if (!grid_barrier(a.bar, G, a.status)) return;
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
     // ---- P2a: hills partials for all walker points
     {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                 for (int s = 0; s < NST; ++s) mbar_inval(&hbar[s]);
         }
     }
-    if (!grid_barrier(a.bar, G, a.status)) return;
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
     // ---- P2b: V and dV/dxi per walker (one warp per point)
     {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
             if (lane == 0) emit_cf(p, acc, a.hout);
         }
     }
-    if (!grid_barrier(a.bar, G, a.status)) return;
+    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
     // ---- P3: deposition (CTA 0), bias force and closing kick
     if (mode == 0 && blockIdx.x == 0)
@@ -596,6 +597,7 @@ int launch_walkers_step(wtmd_t* h, int mode)
     a.bar = k.bar;
     a.status = h->status;
     a.max_wn = h->max_wn;
+    a.wait_limit = h->wait_limit > 0 ? h->wait_limit : kWaitLimit;
     // barrier counter, generation and task queue start clean on every launch
     // (a timed-out barrier would leave its counter dirty)
     WTMD_CUDA_TRY(h, cudaMemsetAsync(k.bar, 0, sizeof(unsigned) * 4, h->stream));

@@ -231,9 +231,12 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 // Sense-reversing grid barrier for a cooperative launch.  Waits are bounded
-// (~2^31 cycles); on a timeout the status word records it and false is
-// returned, after which the CTA leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status)
+// (limit SM cycles, by default 2^31, about a second); on a timeout the
+// status word records it and false is returned, after which the CTA leaves
+// the kernel.
+constexpr long long kWaitLimit = 1ll << 31;
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status,
+                                             long long limit = kWaitLimit)
 {
     __shared__ int ok;
     __syncthreads();
@@ -250,7 +253,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
         } else {
             const long long t0 = clock64();
             while (*vgen == gen) {
-                if (clock64() - t0 > (1ll << 31)) {
+                if (clock64() - t0 > limit) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;
                     break;
@@ -424,6 +427,7 @@ struct wtmd_t {
     wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
     wtmd::SysStepPlan ss;           // persistent single-system step
     bool fused_on = false;          // the caller allowed the persistent single-system step
+    long long wait_limit = 0;       // grid-barrier wait bound of the persistent kernels (0: the default)
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
     // profiling: when `prof` is set, mark() records a CUDA event on the

@@ -141,3 +141,65 @@ def test_persistent_walkers_resume_is_bitwise():
     m2.restore(blob)
     m2.step_n(8)
     _same(ref, _state(m2, p2, v2, F2))
+
+
+def _resume_vs_oracle(spec, x, v, t_save, t_more):
+    """GPU: t_save steps, checkpoint, a fresh handle restored from it and
+    t_more steps; oracle: t_save + t_more steps straight.  Returns both."""
+    import oracle as o
+    from systems import oracle_system
+
+    wt = _wt()
+    m = gpu_handle(spec, "f64")
+    pos, vel = wt.particles(x, torch.float64), wt.particles(v, torch.float64)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(t_save)
+    blob = m.checkpoint()
+    m.close()
+    m2 = gpu_handle(spec, "f64")
+    p2, v2 = wt.particles(np.zeros_like(x), torch.float64), wt.particles(np.zeros_like(x), torch.float64)
+    F2 = torch.zeros_like(p2)
+    m2.bind(p2, v2, F2)
+    m2.restore(blob)
+    m2.step_n(t_more)
+    got = _state(m2, p2, v2, F2)
+    sim = o.Sim(oracle_system(spec), x=x, v=v)
+    sim.forces()
+    assert sim.run(t_save + t_more) == 0
+    return got, sim
+
+
+def test_lj_resume_matches_the_oracle_fp64():
+    """FP64 LJ fluid with coordination + Rg CVs and an FP64 grid, saved at
+    step 60 and resumed in a fresh handle for 80 more steps (3 deposits before
+    the save, 4 after), against the oracle run straight for 140 steps."""
+    from synth import velocities
+
+    spec, x, L = lj_fluid_spec(n=500, n_tag=37, n_rg=20, seed=4, jitter=0.1, capacity=4000)
+    spec.update(stride=20, w0=0.5, grid=((32, 24), (0.0, 0.5), (40.0, 3.0)))
+    v = velocities(500, 1.0, 1.0, seed=9)
+    got, sim = _resume_vs_oracle(spec, x, v, 60, 80)
+    assert got["counters"] == (140, sim.n_hills) and sim.n_hills == 7
+    assert np.max(np.abs(got["pos"][:, :3] - sim.x)) < 1e-9
+    assert np.max(np.abs(got["vel"][:, :3] - sim.v)) < 1e-9
+    assert np.allclose(got["hills"], sim.hills[:7], rtol=1e-9, atol=1e-12)
+    g = got["grid"].ravel()
+    assert np.allclose(g, sim.grid, rtol=1e-9, atol=1e-9 * np.abs(sim.grid).max())
+
+
+def test_mueller_brown_grid_sourced_resume_matches_the_oracle():
+    """Three Mueller-Brown walkers whose bias is read from the FP64 grid,
+    saved at step 150 and resumed for 250 more: the oracle's straight run of
+    400 steps gives the same positions, hills and grid."""
+    spec = dict(engine="mb", walker_sizes=[1, 1, 1], dims=2, dt=1e-4, friction=1.0, kT=15.0, seed=0,
+                sigma=(0.05, 0.05), w0=1.0, gamma=10.0, stride=10, capacity=200,
+                grid=((108, 96), (-1.5, -0.5), (1.2, 2.2)), bias_grid=True,
+                cvs=[dict(kind="component", a=[0], axis=0), dict(kind="component", a=[0], axis=1)])
+    x = np.array([[-0.558, 1.442, 0], [0.623, 0.028, 0], [-0.05, 0.467, 0]])
+    got, sim = _resume_vs_oracle(spec, x, np.zeros_like(x), 150, 250)
+    assert got["counters"] == (400, 120) and sim.n_hills == 120
+    assert np.max(np.abs(got["pos"][:, :2] - sim.x[:, :2])) < 1e-10
+    assert np.allclose(got["hills"], sim.hills[:120], rtol=1e-10, atol=1e-12)
+    g = got["grid"].ravel()
+    assert np.allclose(g, sim.grid, rtol=1e-10, atol=1e-10 * np.abs(sim.grid).max())
