@@ -73,8 +73,10 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-grid-bias", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the Mueller-Brown and chain-adjoint figures")
-    ap.add_argument("--case", choices=["hills", "hills1", "walkers", "mlp", "grid", "cvs"], default=None,
-                    help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line)")
+    ap.add_argument("--case", choices=["hills", "hills1", "walkers", "mlp", "grid", "cvs", "mb_long"], default=None,
+                    help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line); "
+                         "mb_long: the Mueller-Brown configuration at its own parameters for 1e6, 3e6 and 1e7 "
+                         "steps, one JSON line each with the free-energy error")
     return ap.parse_args()
 
 
@@ -234,8 +236,8 @@ def surrogate_bench(wt, torch, dev, flush, steps):
     pairs = synth.native_pairs(x, L, sub, 1.5)
     stream = torch.cuda.current_stream()
 
-    def handle(cap):
-        m = wt.Wtmd(precision="f32", sigma=SU_SIGMA, w0=0.05, gamma=3.0, kT=1.0, stride=100, capacity=cap, seed=0,
+    def handle(cap, stride=100):
+        m = wt.Wtmd(precision="f32", sigma=SU_SIGMA, w0=0.05, gamma=3.0, kT=1.0, stride=stride, capacity=cap, seed=0,
                     engine="lj", walker_sizes=[N_SU], box=(L, L, L), dt=0.005, friction=1.0)
         m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
         m.cv_define(wt.CV_RG, a=rg)
@@ -293,6 +295,8 @@ def surrogate_bench(wt, torch, dev, flush, steps):
             r["fit"] = st
         r["bias_force_evals_per_s"] = evals_per_s(m, pos, 200)
         r["steps_per_s"] = steps_per_s(m, steps)
+        # one step's kernels, each timed alone (eager launches behind a hold)
+        r["kernels_ms"] = {k: round(t, 5) for k, t in m.profile_step(10)}
         res[mode] = r
         if mode == "surrogate":
             # batched form: 4096 CV points, exact sum vs network
@@ -327,6 +331,35 @@ def surrogate_bench(wt, torch, dev, flush, steps):
                                    "rms_err_kT_fresh_points": float(np.sqrt(np.mean(e ** 2))),
                                    "max_err_kT_fresh_points": float(np.abs(e).max())}
         m.close()
+    # the run as the configuration states it: hills deposited as it goes (one
+    # every 2 steps here, so that 2e4 are added in 4e4 steps) and, with the
+    # surrogate, refits every 1e4 new hills inside step_n; wall time of the
+    # whole run including the refits
+    RUN, STRIDE, EVERY = 40_000, 2, 10_000
+    run = {}
+    for mode in ("exact", "surrogate"):
+        m = handle(hills.shape[0] + RUN // STRIDE + 4096, stride=STRIDE)
+        m.hills_load(hills)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        if mode == "surrogate":
+            m.surrogate(True, tol_kT=0.05, retrain_every=EVERY)
+        m.step_n(2)  # capture (and the first fit with the surrogate)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.step_n(RUN, check=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        m.check()
+        r = {"steps": RUN, "stride": STRIDE, "wall_s": wall, "steps_per_s": RUN / wall,
+             "hills_at_end": m.counters()[1]}
+        if mode == "surrogate":
+            r["retrain_every"] = EVERY
+            r["status"] = m.surrogate_status()
+        run[mode] = r
+        m.close()
+    out["in_run_refits"] = run
     out.update(res)
     out["bias_force_speedup"] = res["surrogate"]["bias_force_evals_per_s"] / res["exact"]["bias_force_evals_per_s"]
     out["step_speedup"] = res["surrogate"]["steps_per_s"] / res["exact"]["steps_per_s"]
@@ -592,7 +625,9 @@ def run_ours(args, rank, world):
     step_us = np.array([a.elapsed_time(b) * 1e3 for a, b in ev])
     dev_ms = float(step_us.sum() * 1e-3)
 
-    # steady state: K steps as one step_n call (graph replays), no flush
+    # steady state: K steps as one step_n call (graph replays), no flush;
+    # the multi-step graph is replayed once first (its first launch uploads it)
+    m.step_n(8, check=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -633,6 +668,8 @@ def run_ours(args, rank, world):
     # the job is as fast as its slowest replica
     dev_ms_max, steady_ms, e2e_ms = max_over_ranks([dev_ms, steady_ms, e2e_ms], dev)
 
+    arms = None if args.no_configs else lj4096_arms(wt, torch, dev, flush, x, v, L, tag, rg,
+                                                      xi0[0].double().cpu().numpy(), args.steps)
     micro = None if args.no_micro else hills_micro(wt, torch, dev, flush)
     walkers = None if args.no_walkers else walkers_bench(wt, torch, dev, flush, args.steps)
     sur = None if args.no_surrogate else surrogate_bench(wt, torch, dev, flush, args.steps)
@@ -641,9 +678,72 @@ def run_ours(args, rank, world):
     adj = None if args.no_configs else chain_adjoint_bench(wt, torch, flush)
     step_stats = {"median_us": float(np.median(step_us)), "min_us": float(step_us.min()),
                   "max_us": float(step_us.max()), "first_us": float(step_us[0])}
-    return dict(step_stats=step_stats, mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
+    return dict(arms=arms, step_stats=step_stats, mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)
+
+
+def _bias_evals_per_s(wt, torch, m, pos, flush, reps=30):
+    """Bias-force evaluations per second of one handle (CVs and Jacobians,
+    hills sum, -J^T dV/dxi into a force array), L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    F = torch.zeros_like(pos)
+    for _ in range(3):
+        m.bias_eval(pos, F)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(gate_cycles(reps))
+    for a, b in evs:
+        flush.fill_(1.0)
+        torch.cuda._sleep(SLACK_CYCLES)
+        a.record(stream)
+        m.bias_eval(pos, F)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return 1e3 / float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
+def lj4096_arms(wt, torch, dev, flush, x, v, L, tag, rg, xi0, steps):
+    """The 4096-atom workload's bias-force evaluations per second in FP32 and
+    FP64 and its MD steps per second in FP64 (same equilibrated start, CVs
+    and 1e5 hills as the headline; FP64 arithmetic everywhere but the FP32
+    hill layout is not used)."""
+    out = {}
+    hills = hills_around(xi0, seed=100)
+    for prec, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        m = wt.Wtmd(precision=prec, sigma=SIGMA, w0=1.0, gamma=8.0, kT=1.0, stride=100, capacity=H_PRE + 100000,
+                    seed=0, engine="lj", walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005, friction=1.0)
+        m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+        m.cv_define(wt.CV_RG, a=rg)
+        m.hills_load(hills)
+        pos, vel = wt.particles(x, dt), wt.particles(v, dt)
+        r = {"bias_force_evals_per_s": _bias_evals_per_s(wt, torch, m, pos, flush)}
+        if prec == "f64":
+            F = torch.zeros_like(pos)
+            m.bind(pos, vel, F)
+            m.step_n(3, check=True)
+            stream = torch.cuda.current_stream()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize()
+            torch.cuda._sleep(gate_cycles(steps))
+            for i in range(steps):
+                flush.fill_(float(i))
+                torch.cuda._sleep(SLACK_CYCLES)
+                ev[i][0].record(stream)
+                m.step_n(1, check=False)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            m.check()
+            r["steps_per_s"] = steps / (sum(a.elapsed_time(b) for a, b in ev) * 1e-3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.step_n(steps, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r["steady_state_steps_per_s"] = steps / (e0.elapsed_time(e1) * 1e-3)
+        out[prec] = r
+        m.close()
+    return out
 
 
 MB_STEPS, MB_BINS, MB_LO, MB_HI = 100_000, (60, 60), (-1.5, -0.5), (1.2, 2.2)
@@ -899,7 +999,13 @@ def hills_micro(wt, torch, dev, flush):
 
     ex2, _ = wt.probe_peak(0)
     fma, _ = wt.probe_peak(1)
-    out = {"ex2_per_s_measured": ex2, "fp32_lane_ops_per_s_measured": fma, "cases": []}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # derived from unit counts and the maximum clock: SMs x 128 FP32 lanes x
+    # 2032 MHz lane-ops/s (an FMA is one lane-op), 16 MUFU ex2 per SM per clock
+    fma_derived = sms * 128 * 2032e6
+    ex2_derived = sms * 16 * 2032e6
+    out = {"ex2_per_s_measured": ex2, "fp32_lane_ops_per_s_measured": fma,
+           "fp32_lane_ops_per_s_derived": fma_derived, "ex2_per_s_derived": ex2_derived, "cases": []}
     stream = torch.cuda.current_stream()
     H = 1_000_000
     for d, sig in ((2, (0.05, 0.1)), (3, (0.05, 0.1, 0.02))):
@@ -933,6 +1039,7 @@ def hills_micro(wt, torch, dev, flush):
             out["cases"].append(dict(d=d, P=P, hills=H, ms=ms, hill_evals_per_s=rate, plan=plan,
                                      bound="mufu" if ex2 <= fma / ops else "fp32",
                                      frac_of_measured_pipe_peak=rate / peak,
+                                     frac_of_derived_fp32_peak=rate * ops / fma_derived,
                                      hbm_gbs=(H * 16) / (ms * 1e-3) / 1e9))
         m.close()
     return out
@@ -980,6 +1087,10 @@ def run_case(name: str):
     import synth
 
     dev = torch.device("cuda", 0)
+    if name == "mb_long":
+        for n in (1_000_000, 3_000_000, 10_000_000):
+            print(json.dumps(_mb_run(wt, torch, n, 1e-4, 1.0, 1.0, 100)), flush=True)
+        return
     if name == "hills":
         H, P = 1_000_000, 4096
         m = wt.Wtmd(precision="f32", sigma=(0.05, 0.1), capacity=H, walker_sizes=[1])
@@ -1118,6 +1229,7 @@ def main():
                 "h2d_bytes_per_step": r["e2e_bytes"], "d2h_bytes_per_step": r["e2e_bytes"]},
         "steady_state_steps_per_s": job_rate(world, K, r["steady_ms"]),
         "timed_step_us": r["step_stats"],
+        "lj4096_precision_arms": r["arms"],
         "wall_s": r["wall"],
         "kernels_ms": {k: round(v, 5) for k, v in prof},
         "hills_plan": {"lanes_per_point": r["hills_plan"][0], "splits": r["hills_plan"][1],

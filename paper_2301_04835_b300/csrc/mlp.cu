@@ -42,6 +42,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hills_dev.cuh"
 #include "step_dev.cuh"
 
 namespace wtmd {
@@ -70,6 +71,7 @@ struct Surrogate {
     long long* k0 = nullptr;        // device: first hill of the exact tail (0 while inactive)
     long long* kend = nullptr;      // device: end of the fitted hill range
     int* active = nullptr;          // device flag read by the step path
+    float* dom = nullptr;           // device [6]: box of the training inputs (normalised), lo[3] then hi[3]
     long long* ctr = nullptr;       // device [2]: (unused), batch iteration of the training launches
     long long adam_t = 0;           // Adam steps taken (host copy; bias corrections)
     float* partial = nullptr;       // [pblocks][PSTRIDE]
@@ -229,11 +231,60 @@ __device__ __forceinline__ float silu_dd(float z)
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// The exact sum over the fitted hills [0, K) for a point the network was not
+// trained on (the step path's fallback): the FP32 hill layout, lanes over
+// hill pairs, compensated sums, a fixed xor tree over the warp.
+struct HeadSum {
+    const float* dom;         // the training box (normalised inputs); null: no guard
+    const float4* hp;         // FP32 pair records
+    const long long* kend;    // K
+    const double* ctr;        // centre of the scaled layout
+    HillPrmF32 prm;
+    double gs[3];             // dV/dxi_i = gs_i * sum e D_i
+    int* active;              // cleared on a domain exit
+    long long* k0;            // set to 0 on a domain exit: the next steps sum every hill
+};
+
+__device__ __forceinline__ void head_sum_warp(const HeadSum& hs, const double* xip, int d, int lane, CF4& acc)
+{
+    float X[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < d; ++k) X[k] = (float)((xip[k] - hs.ctr[k]) * hs.prm.a[k]);
+    const long long npairs = *hs.kend >> 1;  // K is a multiple of 256
+    float2 v = make_float2(0.f, 0.f), g0 = v, g1 = v, g2 = v;
+    for (long long q = lane; q < npairs; q += 32) {
+        const float4 A = hs.hp[2 * q], B = hs.hp[2 * q + 1];
+        float2 d0 = __fadd2_rn(make_float2(X[0], X[0]), make_float2(A.x, A.y));
+        if (hs.prm.per[0] > 0.f) d0 = wrap2(d0, hs.prm.per[0], hs.prm.iper[0]);
+        float2 t = __ffma2_rn(d0, d0, make_float2(B.z, B.w));
+        float2 d1 = make_float2(0.f, 0.f), d2 = d1;
+        if (d >= 2) {
+            d1 = __fadd2_rn(make_float2(X[1], X[1]), make_float2(A.z, A.w));
+            if (hs.prm.per[1] > 0.f) d1 = wrap2(d1, hs.prm.per[1], hs.prm.iper[1]);
+            t = __ffma2_rn(d1, d1, t);
+        }
+        if (d >= 3) {
+            d2 = __fadd2_rn(make_float2(X[2], X[2]), make_float2(B.x, B.y));
+            if (hs.prm.per[2] > 0.f) d2 = wrap2(d2, hs.prm.per[2], hs.prm.iper[2]);
+            t = __ffma2_rn(d2, d2, t);
+        }
+        const float2 e = make_float2(ex2_approx(-t.x), ex2_approx(-t.y));
+        v = __fadd2_rn(v, e);
+        g0 = __ffma2_rn(e, d0, g0);
+        g1 = __ffma2_rn(e, d1, g1);
+        g2 = __ffma2_rn(e, d2, g2);
+    }
+    acc.v[0] = cf_add(cf_add(cf{0.f, 0.f}, v.x), v.y);
+    acc.v[1] = cf_add(cf_add(cf{0.f, 0.f}, g0.x), g0.y);
+    acc.v[2] = cf_add(cf_add(cf{0.f, 0.f}, g1.x), g1.y);
+    acc.v[3] = cf_add(cf_add(cf{0.f, 0.f}, g2.x), g2.y);
+    cf4_lane_sum<32>(acc);
+}
+
 __global__ void __launch_bounds__(EV_T) mlp_eval_kernel(const MlpW* __restrict__ img,
                                                          const double* __restrict__ norm, const int* __restrict__ active,
                                                          const double* __restrict__ xi, int xs, int d, int P,
                                                          float* __restrict__ V, float* __restrict__ dV, int dvs,
-                                                         int add)
+                                                         int add, HeadSum hs)
 {
     if (active && *active == 0) return;
     __shared__ __align__(16) MlpW s;
@@ -247,6 +298,21 @@ __global__ void __launch_bounds__(EV_T) mlp_eval_kernel(const MlpW* __restrict__
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             if (k < d) x[k] = (float)((xi[(size_t)p * xs + k] - norm[k]) * norm[3 + k]);
+        bool out = false;
+        if (hs.dom)
+            for (int k = 0; k < d; ++k) out = out || !(x[k] >= hs.dom[k] && x[k] <= hs.dom[3 + k]);
+        if (out) {  // outside the inputs the network was trained on: the exact sum
+            CF4 acc{};
+            head_sum_warp(hs, xi + (size_t)p * xs, d, lane, acc);
+            if (lane == 0) {
+                V[p] += (float)cf_val(acc.v[0]);
+                for (int k = 0; k < d; ++k) dV[(size_t)p * dvs + k] += (float)(hs.gs[k] * cf_val(acc.v[1 + k]));
+                *hs.active = 0;
+                *hs.k0 = 0;
+            }
+            __syncwarp();
+            continue;
+        }
         Fwd f;
         warp_forward(s, x, A1[w], G2[w], f);
         if (lane == 0) {
@@ -573,7 +639,7 @@ static uint64_t splitmix(uint64_t& s)
 void surrogate_free(Surrogate* s)
 {
     if (!s) return;
-    void* p[] = {s->master, s->wb, s->img, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->ctr,
+    void* p[] = {s->master, s->wb, s->img, s->m, s->v, s->norm, s->k0, s->kend, s->active, s->dom, s->ctr,
                  s->partial, s->loss, s->grad, s->sx, s->sV, s->sG, s->hV, s->hG};
     for (void* q : p) cudaFree(q);
     delete s;
@@ -602,6 +668,11 @@ static int sur_get(wtmd_t* h, Surrogate** out)
     WTMD_CUDA_TRY(h, cudaMalloc(&s->k0, sizeof(long long)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->kend, sizeof(long long)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->active, sizeof(int)));
+    WTMD_CUDA_TRY(h, cudaMalloc(&s->dom, sizeof(float) * 6));
+    {
+        const float inf_box[6] = {-INFINITY, -INFINITY, -INFINITY, INFINITY, INFINITY, INFINITY};
+        WTMD_CUDA_TRY(h, cudaMemcpy(s->dom, inf_box, sizeof(inf_box), cudaMemcpyHostToDevice));
+    }
     WTMD_CUDA_TRY(h, cudaMalloc(&s->ctr, sizeof(long long) * 2));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->loss, sizeof(float)));
     WTMD_CUDA_TRY(h, cudaMalloc(&s->grad, sizeof(float) * (MP + 1)));
@@ -646,8 +717,22 @@ int launch_mlp_add(wtmd_t* h)
     if (!h->sur || !h->sur->enabled) return WTMD_OK;
     Surrogate& s = *h->sur;
     const int nb = std::max(1, std::min((h->W + EV_W - 1) / EV_W, grad_blocks()));
+    HeadSum hs{};
+    hs.dom = s.dom;
+    hs.hp = h->hills32;
+    hs.kend = s.kend;
+    hs.ctr = h->ctr;
+    for (int i = 0; i < 3; ++i) {
+        hs.prm.a[i] = h->a[i];
+        const double pp = i < h->d ? h->cv[i].period * h->a[i] : 0.0;
+        hs.prm.per[i] = (float)pp;
+        hs.prm.iper[i] = pp > 0.0 ? (float)(1.0 / pp) : 0.f;
+        hs.gs[i] = -2.0 * 0.69314718055994530942 * h->a[i];
+    }
+    hs.active = s.active;
+    hs.k0 = s.k0;
     mlp_eval_kernel<<<nb, EV_T, 0, h->stream>>>(s.img, s.norm, s.active, h->xi, 4, h->d, h->W, (float*)h->V,
-                                                 (float*)h->dV, 4, 1);
+                                                 (float*)h->dV, 4, 1, hs);
     mark(h, "mlp_surrogate");
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
@@ -768,6 +853,25 @@ static int sur_fit(wtmd_t* h)
         WTMD_CUDA_TRY(h, cudaMemcpy(s.norm, nm, sizeof(nm), cudaMemcpyHostToDevice));
         s.have_norm = true;
     }
+    {
+        // the box of the training inputs in the network's units: the step
+        // path uses the network only inside it
+        std::vector<double> hx(3 * S);
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(hx.data(), s.sx, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+        WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        float box[6] = {-INFINITY, -INFINITY, -INFINITY, INFINITY, INFINITY, INFINITY};
+        for (int k = 0; k < h->d; ++k) {
+            double lo = INFINITY, hi = -INFINITY;
+            for (int64_t i = 0; i < S; ++i) {
+                const double u = (hx[3 * i + k] - s.norm_h[k]) * s.norm_h[3 + k];
+                lo = std::min(lo, u);
+                hi = std::max(hi, u);
+            }
+            box[k] = (float)lo;
+            box[3 + k] = (float)hi;
+        }
+        WTMD_CUDA_TRY(h, cudaMemcpyAsync(s.dom, box, sizeof(box), cudaMemcpyHostToDevice, h->stream));
+    }
     // Adam over batches of the training part, in a fixed pseudo-random order
     const int B = (int)std::min<int64_t>(s.batch, Str);
     const long long perm = coprime_step(Str);
@@ -781,7 +885,7 @@ static int sur_fit(wtmd_t* h)
     // held-out error
     const int nbe = (int)std::min<int64_t>((Sho + EV_W - 1) / EV_W, grad_blocks());
     mlp_eval_kernel<<<std::max(nbe, 1), EV_T, 0, h->stream>>>(s.img, s.norm, nullptr, s.sx + 3 * Str, 3, h->d,
-                                                                (int)Sho, s.hV, s.hG, 3, 0);
+                                                                (int)Sho, s.hV, s.hG, 3, 0, HeadSum{});
     WTMD_CUDA_TRY(h, cudaGetLastError());
     std::vector<float> pv(Sho), tv(Sho), pg(3 * Sho), tg(3 * Sho);
     float L = 0.f;
@@ -973,7 +1077,14 @@ extern "C" int wtmd_surrogate_status(wtmd_t* h, double* stats)
         for (int i = 0; i < 8; ++i) stats[i] = 0.0;
         return WTMD_OK;
     }
-    std::memcpy(stats, h->sur->stats, sizeof(h->sur->stats));
+    Surrogate& s = *h->sur;
+    if (s.active) {  // a walker leaving the fitted inputs switches the network off on the device
+        int act = 0;
+        WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        WTMD_CUDA_TRY(h, cudaMemcpy(&act, s.active, sizeof(int), cudaMemcpyDeviceToHost));
+        if (s.stats[5] != 0.0 && act == 0) s.stats[5] = 0.0;
+    }
+    std::memcpy(stats, s.stats, sizeof(s.stats));
     return WTMD_OK;
 }
 
@@ -1034,7 +1145,8 @@ extern "C" int wtmd_mlp_eval(wtmd_t* h, const double* xi, int64_t P, float* V, f
     if (P == 0) return WTMD_OK;
     // each block stages the network once: a few blocks per SM, points by grid stride
     const int nb = (int)std::min<int64_t>((P + EV_W - 1) / EV_W, grad_blocks());
-    mlp_eval_kernel<<<nb, EV_T, 0, h->stream>>>(s->img, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0);
+    mlp_eval_kernel<<<nb, EV_T, 0, h->stream>>>(s->img, s->norm, nullptr, xi, h->d, h->d, (int)P, V, dV, h->d, 0,
+                                                 HeadSum{});
     WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
 }

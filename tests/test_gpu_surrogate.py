@@ -343,7 +343,7 @@ def test_gain_at_1e6_hills():
     Vn, dVn = m.mlp_eval(x64)
     e = to_np(Vn) - to_np(Ve)
     e -= e.mean()
-    assert np.sqrt(np.mean(e ** 2)) <= 0.06  # fresh points, exact GPU sum as reference
+    assert np.sqrt(np.mean(e ** 2)) <= 0.05  # fresh points, exact GPU sum as reference
     assert t_exact / t_nn > 10.0, (t_exact, t_nn)
     # step path: bias of the 2048 walkers, surrogate vs exact
     pos = m._bound[0]
@@ -382,3 +382,42 @@ def test_refits_are_scheduled_inside_step_n():
     d = to_np(V1) - to_np(V0)
     d -= d.mean()
     assert np.sqrt(np.mean(d ** 2)) <= 3 * st["rms_kT"] + 0.05
+
+
+def test_domain_exit_falls_back_to_the_exact_sum():
+    """The network is used only inside the box of the inputs it was trained
+    on.  A walker moved outside it gets, in the same evaluation, the exact sum
+    over the fitted hills (plus the exact tail): its V and dV/dxi equal the
+    exact path's; the network is then switched off on the device (the status
+    reports it) and the exact sum serves every walker until the next fit."""
+    wt = _wt()
+    W = 64
+    spec = dict(engine="wells3", walker_sizes=[1] * W, dims=3, dt=5e-3, kT=1.0, sigma=(0.5, 0.5, 0.5), w0=0.05,
+                gamma=3.0, stride=1, capacity=8192, cvs=[dict(kind="component", a=[0], axis=k) for k in range(3)])
+    m = gpu_handle(spec, "f32")
+    x = synth.rng(2).normal(scale=0.5, size=(W, 3))
+    pos, vel = wt.particles(x, torch.float32), wt.particles(np.zeros_like(x), torch.float32)
+    F = torch.zeros_like(pos)
+    m.bind(pos, vel, F)
+    m.step_n(40)  # 2560 hills, no surrogate yet
+    m.surrogate_config(n_samples=4000, iters=300, batch=512, lr=3e-3, lam=0.1)
+    m.surrogate(True, tol_kT=10.0, retrain_every=0)
+    st = m.surrogate_fit()
+    assert st["active"] == 1.0
+    h = m.hills_read()
+    far = h[:, :3].max(0) + 2.0  # beyond every hill centre and every jittered sample
+    with torch.no_grad():
+        pos[0, :3] = torch.tensor(far, dtype=torch.float32, device="cuda")
+    V1, xi1, dV1 = m.bias_eval(pos)
+    assert m.surrogate_status()["active"] == 0.0
+    V2, _, dV2 = m.bias_eval(pos)  # network off: the exact sum everywhere
+    m.surrogate(False)
+    V0, xi0, dV0 = m.bias_eval(pos)
+    v0, v1, v2 = to_np(V0), to_np(V1), to_np(V2)
+    g0, g1, g2 = to_np(dV0), to_np(dV1), to_np(dV2)
+    scale = np.abs(v0).max() + 1e-30
+    assert v0[0] > 0.0  # the far walker still feels the nearest hills' tails
+    assert abs(v1[0] - v0[0]) <= 1e-5 * v0[0]
+    assert np.abs(g1[0] - g0[0]).max() <= 1e-4 * np.abs(g0[0]).max()
+    assert np.allclose(v2, v0, rtol=1e-5, atol=1e-5 * scale)
+    assert np.allclose(g2, g0, rtol=1e-5, atol=1e-5 * (np.abs(g0).max() + 1e-30))
