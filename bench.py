@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-grid-bias", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the Mueller-Brown and chain-adjoint figures")
-    ap.add_argument("--case", choices=["hills", "hills1", "walkers", "mlp", "grid", "cvs", "mb_long"], default=None,
+    ap.add_argument("--case", choices=["hills", "hills1", "walkers", "mlp", "grid", "cvs", "mb_long", "step"],
+                    default=None,
                     help="run one kernel workload a few times and exit (for ncu captures; prints no JSON line); "
                          "mb_long: the Mueller-Brown configuration at its own parameters for 1e6, 3e6 and 1e7 "
                          "steps, one JSON line each with the free-energy error")
@@ -1087,6 +1088,40 @@ def run_case(name: str):
     import synth
 
     dev = torch.device("cuda", 0)
+    if name == "step":
+        # the 4096-atom step as the headline runs it (cluster plan for the
+        # hills sum, single-step graph, L2 flushed between steps), from a
+        # lattice relaxed for 300 unbiased steps: 30 steps
+        x, v, L, tag, rg = workload_inputs(seed=0)
+        e = wt.Wtmd(precision="f32", sigma=(1.0,), stride=0, capacity=16, seed=1000, engine="lj",
+                    walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005, friction=1.0, kT=1.0)
+        e.cv_define(wt.CV_COMPONENT, a=[0], axis=0)
+        pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+        e.bind(pos, vel, torch.zeros_like(pos))
+        e.step_n(300)
+        e.close()
+        m = wt.Wtmd(precision="f32", sigma=SIGMA, w0=1.0, gamma=8.0, kT=1.0, stride=100, capacity=H_PRE + 100000,
+                    seed=0, engine="lj", walker_sizes=[N_ATOMS], box=(L, L, L), dt=0.005, friction=1.0)
+        m.cv_define(wt.CV_COORDINATION, a=tag, r0=1.5, nn=6, mm=12)
+        m.cv_define(wt.CV_RG, a=rg)
+        _, xi0, _ = m.bias_eval(pos)
+        m.hills_load(hills_around(xi0[0].double().cpu().numpy(), seed=100))
+        for cl in (16, 8):
+            try:
+                m.hills_plan(1, -1, cl)
+                break
+            except wt.WtmdError:
+                continue
+        F = torch.zeros_like(pos)
+        m.bind(pos, vel, F)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for i in range(30):
+            flush.fill_(float(i))
+            m.step_n(1, check=False)
+        torch.cuda.synchronize()
+        m.check()
+        print("case step: ok")
+        return
     if name == "mb_long":
         for n in (1_000_000, 3_000_000, 10_000_000):
             print(json.dumps(_mb_run(wt, torch, n, 1e-4, 1.0, 1.0, 100)), flush=True)
