@@ -188,6 +188,29 @@ def walkers_bench(wt, torch, dev, flush, steps):
         r["steps_per_s_l2_flushed"] = timed(m, max(steps // 4, 10), flushed=True)
         out[mode] = r
         m.close()
+    # the same walkers as umbrella windows (harmonic bias about each walker's
+    # starting CVs, k = (50, 500)) and with the bias read from the grid:
+    # per-kernel launch sequence against the persistent launch (default plan)
+    m0 = cluster_handle(wt, sizes, capacity=16)
+    _, xi0, _ = m0.bias_eval(wt.particles(x, torch.float32))
+    centres = xi0.double().cpu().numpy()[:, :2]
+    m0.close()
+    for src in ("windows", "grid_read"):
+        for mode in ("per_kernel", "persistent"):
+            m = cluster_handle(wt, sizes, grid=grid)
+            m.hills_load(hills)
+            pos, vel = wt.particles(x, torch.float32), wt.particles(v, torch.float32)
+            F = torch.zeros_like(pos)
+            m.bind(pos, vel, F)
+            if src == "windows":
+                m.harmonic((50.0, 500.0), centres)
+            else:
+                m.bias_source(wt.BIAS_GRID)
+            if mode == "persistent":
+                m.walkers_persistent(True)
+            out[f"{src}_{mode}"] = dict(steps_per_s=timed(m, steps, flushed=False),
+                                        steps_per_s_l2_flushed=timed(m, max(steps // 4, 10), flushed=True))
+            m.close()
     return out
 
 

@@ -250,8 +250,8 @@ int wtmd_grid_eval(wtmd_t* h, const void* xi, int64_t P, void* V_out, void* dV_o
  * hill also uses the grid's V, and hills are still appended to the list and
  * added to the grid.  Errors: WTMD_EINVAL (unknown source; for the grid: no
  * grid, an axis with fewer than 2 cells, a periodic CV whose grid does not
- * span one period, CVs not all defined, the surrogate on, or the persistent
- * walker step on).  Drops captured step graphs. */
+ * span one period, CVs not all defined, or the surrogate on).  Drops
+ * captured step graphs; the persistent walker step follows the new source. */
 int wtmd_bias_source(wtmd_t* h, int32_t source);
 
 /* ---- harmonic bias and umbrella windows ------------------------------------
@@ -267,8 +267,7 @@ int wtmd_bias_source(wtmd_t* h, int32_t source);
 /* Set the spring constants k (host [n_cv], > 0) and the window centres
  * (host [W][n_cv]), clear the window statistics and make the harmonic bias
  * the bias source.  Drops captured step graphs.  Errors: WTMD_EINVAL (CVs
- * not all defined, k <= 0, non-finite centres, surrogate or persistent
- * walker step on). */
+ * not all defined, k <= 0, non-finite centres, surrogate on). */
 int wtmd_harmonic(wtmd_t* h, const double* k, const double* centres);
 
 /* Mean CVs of every window over the steps run since the last reset: mean_out
@@ -354,14 +353,21 @@ int wtmd_probe_peak(int32_t kind, double* ops_per_s, double* ms);
 int wtmd_barrier_probe(int32_t blocks, int32_t absent, int64_t limit_cycles, int32_t* timed_out);
 
 /* Run each MD step of a multi-walker handle as one persistent (cooperative)
- * kernel launch: BAOAB, all-pairs LJ, coordination and Rg CVs, hills sum over
- * the shared hill list, bias force and deposition for every walker, with
- * bounded grid barriers between the phases.  The paper runs replicas as
- * separate simulations (Sec. 2, concurrent.futures / MPI); here walkers of
- * uneven size share one GPU launch and one hill list.  Requirements: FP32,
- * LJ engine with open boundaries, 1-2 CVs among COORDINATION (A = B = all)
- * and RG (all atoms), walkers of at most 8192 atoms; else WTMD_EINVAL.
- * enable = 0 returns to the per-kernel step. */
+ * kernel launch: BAOAB, all-pairs LJ, coordination and Rg CVs, the bias at
+ * every walker's CVs, bias force and deposition for every walker, with
+ * bounded grid barriers between the phases.  The bias follows the handle's
+ * source (wtmd_bias_source): the hills sum over the shared hill list, the
+ * FP64 grid read (Sec. 2.1.5), or harmonic windows (wtmd_harmonic, Sec.
+ * 2.1.1; one umbrella window per walker, Sec. 2.1.2, with the window sums
+ * that wtmd_umbrella_stats reads).  The paper runs replicas as separate
+ * simulations (Sec. 2, concurrent.futures / MPI); here walkers of uneven
+ * size share one GPU launch and one hill list.  Each walker is either an
+ * open cluster or, when the configured box has edges > 0, in its own
+ * periodic box of that size (minimum-image pairs; Rg members unwrapped
+ * relative to the walker's first atom).  Requirements: FP32, LJ engine, 1-2
+ * CVs among COORDINATION (A = B = all) and RG (all atoms), walkers of at
+ * most 8192 atoms, surrogate off; else WTMD_EINVAL.  enable = 0 returns to
+ * the per-kernel step. */
 int wtmd_walkers_persistent(wtmd_t* h, int32_t enable);
 
 /* Bound of the grid-barrier waits of this handle's persistent launches (the

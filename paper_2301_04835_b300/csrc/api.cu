@@ -825,7 +825,6 @@ extern "C" int wtmd_bias_source(wtmd_t* h, int32_t source)
             if (per > 0.0 && fabs(span - per) > 1e-9 * per)
                 FAIL(h, WTMD_EINVAL, "the grid of a periodic CV must span exactly one period");
         }
-        if (h->persistent) FAIL(h, WTMD_EINVAL, "not available with the persistent walker step");
         if (surrogate_k0(h)) FAIL(h, WTMD_EINVAL, "turn the surrogate off first");
     }
     if (grid != h->bias_grid) {
@@ -840,7 +839,6 @@ extern "C" int wtmd_harmonic(wtmd_t* h, const double* k, const double* centres)
     if (!h) return WTMD_EINVAL;
     if (!k || !centres) FAIL(h, WTMD_EINVAL, "null spring constants or centres");
     if (h->ncv != h->d) FAIL(h, WTMD_EINVAL, "define all n_cv CVs first");
-    if (h->persistent) FAIL(h, WTMD_EINVAL, "not available with the persistent walker step");
     if (surrogate_k0(h)) FAIL(h, WTMD_EINVAL, "turn the surrogate off first");
     for (int c = 0; c < h->d; ++c)
         if (!(k[c] > 0.0) || !isfinite(k[c])) FAIL(h, WTMD_EINVAL, "spring constants must be finite and > 0");
@@ -1244,8 +1242,6 @@ extern "C" int wtmd_walkers_persistent(wtmd_t* h, int32_t enable)
         h->persistent = false;
         return WTMD_OK;
     }
-    if (h->bias_grid || h->bias_harm)
-        FAIL(h, WTMD_EINVAL, "the persistent walker step sums the hills; grid-read and harmonic biases are per-kernel");
     return walkers_enable(h);
 }
 
@@ -1264,7 +1260,8 @@ extern "C" int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice)
         h->forces_valid = true;
     }
     const size_t pb = sizeof(float4) * (size_t)h->N;
-    void *sx = nullptr, *sv = nullptr, *sf = nullptr, *sg = nullptr;
+    void *sx = nullptr, *sv = nullptr, *sf = nullptr, *sg = nullptr, *sh = nullptr;
+    const size_t hb = sizeof(double) * (4 * (size_t)h->W + 1);  // umbrella window sums and count
     long long counters[2];
     double centre[3];
     WTMD_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1272,7 +1269,9 @@ extern "C" int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice)
     WTMD_CUDA_TRY(h, cudaMalloc(&sv, pb));
     WTMD_CUDA_TRY(h, cudaMalloc(&sf, pb));
     if (h->grid) WTMD_CUDA_TRY(h, cudaMalloc(&sg, sizeof(double) * h->ncell));
+    if (h->harm_sum) WTMD_CUDA_TRY(h, cudaMalloc(&sh, hb));
     auto save = [&]() {
+        if (sh) cudaMemcpy(sh, h->harm_sum, hb, cudaMemcpyDeviceToDevice);
         cudaMemcpy(sx, h->pos, pb, cudaMemcpyDeviceToDevice);
         cudaMemcpy(sv, h->vel, pb, cudaMemcpyDeviceToDevice);
         cudaMemcpy(sf, h->force, pb, cudaMemcpyDeviceToDevice);
@@ -1287,6 +1286,7 @@ extern "C" int wtmd_autotune(wtmd_t* h, int64_t steps, int32_t* choice)
         cudaMemcpy(h->vel, sv, pb, cudaMemcpyDeviceToDevice);
         cudaMemcpy(h->force, sf, pb, cudaMemcpyDeviceToDevice);
         if (sg) cudaMemcpy(h->grid, sg, sizeof(double) * h->ncell, cudaMemcpyDeviceToDevice);
+        if (sh) cudaMemcpy(h->harm_sum, sh, hb, cudaMemcpyDeviceToDevice);
         cudaMemcpy(h->count, &counters[0], sizeof(long long), cudaMemcpyHostToDevice);
         cudaMemcpy(h->step, &counters[1], sizeof(long long), cudaMemcpyHostToDevice);
         cudaMemcpy(h->ctr, centre, sizeof(centre), cudaMemcpyHostToDevice);
@@ -1333,6 +1333,7 @@ done:
     cudaFree(sv);
     cudaFree(sf);
     cudaFree(sg);
+    cudaFree(sh);
     unsigned st = 0;
     cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost);
     st &= ~ST_CAPACITY;  // trial deposits may have hit capacity

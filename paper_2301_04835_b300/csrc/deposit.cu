@@ -28,13 +28,6 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepPrm p, const double* __
     deposit_block<R>(p, xi, V, count, step, dep, ctr, h64, h32, status);
 }
 
-struct GridPrm {
-    int d;
-    int bins[3];
-    int off[3];      // offset of axis i in the factor table
-    double lo[3], dx[3], inv2s2[3], per[3];
-};
-
 // factors f[n][off_i + k] = exp(-D^2/(2 sigma_i^2)) of new hill n on axis i
 __global__ void grid_factor_kernel(GridPrm g, const long long* __restrict__ dep, const dbl4* __restrict__ h64,
                                    int tot, double* __restrict__ fac)
@@ -134,14 +127,8 @@ __global__ void fes_kernel(const double* __restrict__ grid, long long n, double 
     out[i] = f * grid[i] - f * vmax[0];
 }
 
-// Bias and gradient read from the grid instead of summed over the hills (the
-// paper's accuracy-for-speed option, Sec. 2.1.5): the grid keeps V at cell
-// centres; the gradient at a node along axis i is the central difference of
-// its neighbours (one-sided at the ends of a non-periodic axis, wrapped on a
-// periodic one), and V and dV/dxi at a point are multilinear interpolations
-// of the node values over the 2^d surrounding nodes.  A non-periodic
-// coordinate is clamped to the outermost nodes.  One thread per point, FP64
-// throughout (the grid is FP64); the result is rounded to R on the store.
+// Bias and gradient read from the grid at P points (grid_point, one thread
+// per point, FP64 throughout; the result is rounded to R on the store).
 // The point's corner nodes and their neighbours (at most 56 doubles) are
 // L2-resident reads: the kernel is bound by its launch, not by memory.
 template <int D, typename X, typename R>
@@ -156,73 +143,10 @@ __global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double*
     pdl_trigger();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
-    constexpr int NC = 1 << D;       // corner nodes
-    constexpr int NV = 1 + 2 * D;    // per corner: the node and its two neighbours on each axis
-    long long cstride[D];
-    cstride[D - 1] = 1;
+    double x[D], v, gr[D];
 #pragma unroll
-    for (int i = D - 2; i >= 0; --i) cstride[i] = cstride[i + 1] * g.bins[i + 1];
-    int k0[D], k1[D];
-    double t[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        const int n = g.bins[i];
-        double u = ((double)xi[p * xs + i] - g.lo[i]) / g.dx[i] - 0.5;
-        if (g.per[i] > 0.0) {
-            u -= (double)n * floor(u / (double)n);
-            if (!(u >= 0.0 && u < (double)n)) u = 0.0;  // rounding at n, or a non-finite / huge coordinate
-            k0[i] = (int)floor(u);
-            k1[i] = k0[i] + 1 == n ? 0 : k0[i] + 1;
-        } else {
-            u = fmin(fmax(u, 0.0), (double)(n - 1));
-            k0[i] = min((int)floor(u), n - 2);
-            k1[i] = k0[i] + 1;
-        }
-        t[i] = u - (double)k0[i];
-    }
-    // every address first, then every load (unrolled: one round of latency),
-    // then the sums in corner order
-    double val[NC][NV], wgt[NC], span[NC][D];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        int k[D];
-        double w = 1.0;
-        long long node = 0;
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const bool up = (c >> i) & 1;
-            k[i] = up ? k1[i] : k0[i];
-            w *= up ? t[i] : 1.0 - t[i];
-            node += k[i] * cstride[i];
-        }
-        wgt[c] = w;
-        val[c][0] = grid[node];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const int n = g.bins[i];
-            int kp, km;
-            if (g.per[i] > 0.0) {
-                kp = k[i] + 1 == n ? 0 : k[i] + 1;
-                km = k[i] == 0 ? n - 1 : k[i] - 1;
-                span[c][i] = 2.0 * g.dx[i];
-            } else {
-                kp = min(k[i] + 1, n - 1);
-                km = max(k[i] - 1, 0);
-                span[c][i] = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
-            }
-            val[c][1 + 2 * i] = grid[node + (kp - k[i]) * cstride[i]];
-            val[c][2 + 2 * i] = grid[node + (km - k[i]) * cstride[i]];
-        }
-    }
-    double v = 0.0, gr[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) gr[i] = 0.0;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        v += wgt[c] * val[c][0];
-#pragma unroll
-        for (int i = 0; i < D; ++i) gr[i] += wgt[c] * ((val[c][1 + 2 * i] - val[c][2 + 2 * i]) / span[c][i]);
-    }
+    for (int i = 0; i < D; ++i) x[i] = (double)xi[p * xs + i];
+    grid_point<D>(g, grid, x, v, gr);
     if (V) V[p] = (R)v;
     if (dV)
 #pragma unroll
@@ -230,7 +154,7 @@ __global__ void __launch_bounds__(128) grid_bias_kernel(GridPrm g, const double*
 }
 
 // ---------------------------------------------------------------------------
-static GridPrm grid_prm(const wtmd_t* h)
+GridPrm grid_prm(const wtmd_t* h)
 {
     GridPrm g{};
     g.d = h->d;
@@ -319,10 +243,8 @@ int launch_fes(wtmd_t* h, double* out)
     return WTMD_OK;
 }
 
-// Harmonic biasing (Sec. 2.1.1): V = sum_c k_c/2 (xi_c - xi0_c)^2,
-// dV/dxi_c = k_c (xi_c - xi0_c), the difference by the minimum image on a
-// periodic CV; every walker has its own centre xi0 (one umbrella window per
-// walker, Sec. 2.1.2).  In a step the kernel also adds each walker's xi to
+// Harmonic biasing of every walker about its window centre (harmonic_point,
+// Sec. 2.1.1 / 2.1.2).  In a step the kernel also adds each walker's xi to
 // its window sums (FP64) and counts the sample.  One thread per walker.
 struct HarmPrm {
     int W, d;
@@ -337,16 +259,7 @@ __global__ void harmonic_bias_kernel(HarmPrm hp, const double* __restrict__ xi, 
     pdl_trigger();
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= hp.W) return;
-    double v = 0.0;
-    for (int c = 0; c < hp.d; ++c) {
-        const double x = xi[w * 4 + c];
-        double D = x - centre[w * 4 + c];
-        if (hp.per[c] > 0.0) D -= hp.per[c] * rint(D / hp.per[c]);
-        v += 0.5 * hp.k[c] * D * D;
-        dV[w * 4 + c] = (R)(hp.k[c] * D);
-        if (sum) sum[w * 4 + c] += x;
-    }
-    V[w] = (R)v;
+    harmonic_point<R>(hp.d, hp.k, hp.per, xi + w * 4, centre + w * 4, V + w, dV + w * 4, sum ? sum + w * 4 : nullptr);
     if (sum && w == 0) sum[hp.W * 4] += 1.0;
 }
 

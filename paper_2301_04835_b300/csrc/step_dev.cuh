@@ -93,6 +93,168 @@ struct DepPrm {
 
 DepPrm dep_prm(const wtmd_t* h);  // deposit.cu
 
+// FP64 bias grid (Sec. 2.1.5): bins per axis, node spacing dx, the lower
+// edge lo (node k sits at the cell centre lo + (k + 1/2) dx), the hill
+// widths as 1/(2 sigma^2) and the period of a periodic CV (0: none).
+struct GridPrm {
+    int d;
+    int bins[3];
+    int off[3];  // offset of axis i in the per-hill factor table
+    double lo[3], dx[3], inv2s2[3], per[3];
+};
+
+GridPrm grid_prm(const wtmd_t* h);  // deposit.cu
+
+// The staged form of grid_point: every address first, then every load
+// (unrolled: one round of latency), then the sums in corner order.
+template <int D, int NC, int NV>
+__device__ __forceinline__ void grid_point_staged(const GridPrm& g, const double* __restrict__ grid,
+                                                  const long long* cstride, const int* k0, const int* k1,
+                                                  const double* t, double& v, double* gr)
+{
+    double val[NC][NV], wgt[NC], span[NC][D];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        int k[D];
+        double w = 1.0;
+        long long node = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const bool up = (c >> i) & 1;
+            k[i] = up ? k1[i] : k0[i];
+            w *= up ? t[i] : 1.0 - t[i];
+            node += k[i] * cstride[i];
+        }
+        wgt[c] = w;
+        val[c][0] = grid[node];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int n = g.bins[i];
+            int kp, km;
+            if (g.per[i] > 0.0) {
+                kp = k[i] + 1 == n ? 0 : k[i] + 1;
+                km = k[i] == 0 ? n - 1 : k[i] - 1;
+                span[c][i] = 2.0 * g.dx[i];
+            } else {
+                kp = min(k[i] + 1, n - 1);
+                km = max(k[i] - 1, 0);
+                span[c][i] = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
+            }
+            val[c][1 + 2 * i] = grid[node + (kp - k[i]) * cstride[i]];
+            val[c][2 + 2 * i] = grid[node + (km - k[i]) * cstride[i]];
+        }
+    }
+    v = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) gr[i] = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        v += wgt[c] * val[c][0];
+#pragma unroll
+        for (int i = 0; i < D; ++i) gr[i] += wgt[c] * ((val[c][1 + 2 * i] - val[c][2 + 2 * i]) / span[c][i]);
+    }
+}
+
+// Bias and gradient read from the grid instead of summed over the hills (the
+// paper's accuracy-for-speed option, Sec. 2.1.5): the grid keeps V at cell
+// centres; the gradient at a node along axis i is the central difference of
+// its neighbours (one-sided at the ends of a non-periodic axis, wrapped on a
+// periodic one), and V and dV/dxi at the point x are multilinear
+// interpolations of the node values over the 2^d surrounding nodes.  A
+// non-periodic coordinate is clamped to the outermost nodes.  FP64.
+// STAGED: every node address first, then every load (one round of memory
+// latency, 2^d (1 + 2d) values in registers); otherwise corner by corner
+// with few registers, for a caller whose register budget is tight.  Both
+// forms add the same terms in the same order.
+template <int D, bool STAGED = true>
+__device__ __forceinline__ void grid_point(const GridPrm& g, const double* __restrict__ grid, const double* x,
+                                           double& v, double* gr)
+{
+    constexpr int NC = 1 << D;       // corner nodes
+    constexpr int NV = 1 + 2 * D;    // per corner: the node and its two neighbours on each axis
+    long long cstride[D];
+    cstride[D - 1] = 1;
+#pragma unroll
+    for (int i = D - 2; i >= 0; --i) cstride[i] = cstride[i + 1] * g.bins[i + 1];
+    int k0[D], k1[D];
+    double t[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const int n = g.bins[i];
+        double u = (x[i] - g.lo[i]) / g.dx[i] - 0.5;
+        if (g.per[i] > 0.0) {
+            u -= (double)n * floor(u / (double)n);
+            if (!(u >= 0.0 && u < (double)n)) u = 0.0;  // rounding at n, or a non-finite / huge coordinate
+            k0[i] = (int)floor(u);
+            k1[i] = k0[i] + 1 == n ? 0 : k0[i] + 1;
+        } else {
+            u = fmin(fmax(u, 0.0), (double)(n - 1));
+            k0[i] = min((int)floor(u), n - 2);
+            k1[i] = k0[i] + 1;
+        }
+        t[i] = u - (double)k0[i];
+    }
+    if constexpr (!STAGED) {
+        v = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) gr[i] = 0.0;
+#pragma unroll 1
+        for (int c = 0; c < NC; ++c) {
+            double w = 1.0;
+            long long node = 0;
+            int k[D];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const bool up = (c >> i) & 1;
+                k[i] = up ? k1[i] : k0[i];
+                w *= up ? t[i] : 1.0 - t[i];
+                node += k[i] * cstride[i];
+            }
+            v += w * grid[node];
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const int n = g.bins[i];
+                int kp, km;
+                double sp;
+                if (g.per[i] > 0.0) {
+                    kp = k[i] + 1 == n ? 0 : k[i] + 1;
+                    km = k[i] == 0 ? n - 1 : k[i] - 1;
+                    sp = 2.0 * g.dx[i];
+                } else {
+                    kp = min(k[i] + 1, n - 1);
+                    km = max(k[i] - 1, 0);
+                    sp = kp - km == 2 ? 2.0 * g.dx[i] : g.dx[i];
+                }
+                gr[i] += w * ((grid[node + (kp - k[i]) * cstride[i]] - grid[node + (km - k[i]) * cstride[i]]) / sp);
+            }
+        }
+    } else {
+        grid_point_staged<D, NC, NV>(g, grid, cstride, k0, k1, t, v, gr);
+    }
+}
+
+// Harmonic bias of one walker about its window centre (Sec. 2.1.1; one
+// window per walker for umbrella sampling, Sec. 2.1.2):
+// V = sum_c k_c/2 (xi_c - xi0_c)^2, dV/dxi_c = k_c (xi_c - xi0_c), the
+// difference by the minimum image on a periodic CV.  With `sum` the walker's
+// xi is added to its window sums (the caller counts the sample).
+template <typename R>
+__device__ __forceinline__ void harmonic_point(int d, const double* k, const double* per, const double* __restrict__ xi,
+                                               const double* __restrict__ centre, R* V, R* dV,
+                                               double* __restrict__ sum)
+{
+    double v = 0.0;
+    for (int c = 0; c < d; ++c) {
+        const double x = xi[c];
+        double D = x - centre[c];
+        if (per[c] > 0.0) D -= per[c] * rint(D / per[c]);
+        v += 0.5 * k[c] * D * D;
+        dV[c] = (R)(k[c] * D);
+        if (sum) sum[c] += x;
+    }
+    *V = (R)v;
+}
+
 // Deposition by one CTA (all its threads call this): every `stride` steps
 // each walker appends a hill at its CVs with height w0 exp(-V inv_dT) in
 // FP64 (walker order), then the step counter advances.

@@ -1,10 +1,10 @@
 // Many walkers of uneven size in one persistent launch per MD step.
 //
-// Walkers are independent systems (here: Lennard-Jones clusters in open
-// space) that share one hill list; the paper runs replicas as separate
-// simulations (Sec. 2, replicas through concurrent.futures / MPI).  One
-// cooperative kernel does a whole step for all walkers, with bounded grid
-// barriers between the phases:
+// Walkers are independent systems (Lennard-Jones clusters in open space, or
+// each in its own periodic box of the configured size) that share one hill
+// list; the paper runs replicas as separate simulations (Sec. 2, replicas
+// through concurrent.futures / MPI).  One cooperative kernel does a whole
+// step for all walkers, with bounded grid barriers between the phases:
 //   P0  first half of BAOAB for every atom;
 //   P1  (walker, target tile) tasks, handed out by an atomic queue in order
 //       of decreasing cost: the walker's positions are staged in shared
@@ -12,13 +12,22 @@
 //       row sum and its gradient (A = B = all atoms) of each target, plus the
 //       targets' first and second moments for Rg; the walker's last task
 //       finishes its CVs;
-//   P2a hills sum for all walker points over the shared hill list (the FP32
-//       bulk-copy ring task of hills.cu), one partial per hill split;
-//   P2b fixed-order reduction of the splits -> V, dV/dxi per walker;
+//   P2  the bias at every walker's CVs, from the bias source of the handle:
+//       hills: P2a the hills sum for all walker points over the shared hill
+//              list (the FP32 bulk-copy ring task of hills.cu), one partial
+//              per hill split, P2b a fixed-order reduction of the splits;
+//       grid:  the FP64 grid read by interpolation (Sec. 2.1.5), one thread
+//              per walker;
+//       harmonic windows: each walker's harmonic bias about its own centre
+//              (Sec. 2.1.1; umbrella windows, Sec. 2.1.2), with the window
+//              sums of xi accumulated in a step;
 //   P3  deposition (CTA 0) and, for every atom, the bias force -J^T dV/dxi
 //       added to the LJ force and the closing half kick.
 // The FP64 bias grid, when configured, is updated by the two grid kernels
-// that follow (they exit at once on steps without a deposit).
+// that follow (they exit at once on steps without a deposit; harmonic
+// windows deposit nothing).  In a periodic box every pair difference and
+// every Rg member is taken by the minimum image (Rg members relative to the
+// walker's first atom, as in the per-kernel path).
 // Tile sizes, CTAs per SM and the hill split count come from the autotuner
 // (wtmd_autotune).  Every reduction has a fixed order: deterministic.
 #include <algorithm>
@@ -46,7 +55,7 @@ struct WkArgs {
     const int* tcount;  // [W]
     double* tpart;      // [ntasks][2]
     unsigned* ticket;   // [W]
-    float4* rgc;        // [W] Rg centre and Jacobian factor
+    float4* rgc;        // [2W]: Rg centre relative to the first member and Jacobian factor; then the first member
     float4* x;
     float4* v;
     float4* f;
@@ -80,6 +89,15 @@ struct WkArgs {
     unsigned* status;
     int max_wn;
     long long wait_limit;  // grid-barrier wait bound (SM cycles)
+    // periodic box (PER kernels): edge as Lf + Llo, 1/L; 0 on an open axis
+    Box box;
+    // bias source: 0 hills, 1 harmonic windows, 2 grid
+    int bias;
+    const double* hcen;  // [W][4] window centres
+    double* hsum;        // [W][4] window sums of xi, then the sample count
+    double hk[3], hper[3];
+    GridPrm g;
+    const double* grid;
 };
 
 // Targets per pair task of an n-atom walker: the plan's T, or for a smaller
@@ -113,13 +131,28 @@ struct PairAcc2 {
     float2 fx, fy, fz, gx, gy, gz, sv;
 };
 
+// Minimum image of two differences at once: n = rint(d / L) by the
+// 1.5 * 2^23 rounding constant (exact for |d / L| < 2^22), then
+// d - n Lf - n Llo with the box edge as two floats; an open axis has
+// 1/L = L = 0 and keeps d.
+__device__ __forceinline__ float2 wk_wrap2(float2 d, float2 iL, float2 nLf, float2 nLlo)
+{
+    const float2 n = __fadd2_rn(__ffma2_rn(d, iL, make_float2(12582912.f, 12582912.f)),
+                                make_float2(-12582912.f, -12582912.f));
+    return __ffma2_rn(n, nLlo, __ffma2_rn(n, nLf, d));
+}
+
 // LJ force and coordination terms of target i (position p) against the
 // source pairs [m0, m1), its own pair with itself left out (replaced by the
 // padding point).  One approximate reciprocal of r^2 serves both: with
 // y = r^2/r0^2 and s = 1/(1 + y^h), ds/dx = -n y^h s^2 dx / r^2 (n = 2h).
 // H > 0 fixes the exponent h at compile time, H = 0 reads it from the
-// arguments.
-template <int H>
+// arguments and caps y^h at 1e30 (beyond it s and ds/dx are below FP32's
+// range anyway, and the cap keeps y^h s^2 finite for far pairs and the
+// padding point).  PER: minimum-image differences; the padding point and
+// the left-out self pair (weight 0) are then moved to r^2 = rc^2, where the
+// LJ cutoff drops them and the coordination terms are 0.
+template <int H, bool PER>
 __device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, float4 p, int i, int m0, int m1,
                                             const WkArgs& a, PairAcc2& c)
 {
@@ -129,6 +162,15 @@ __device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, flo
     const float2 nneg = make_float2(-2.f * (float)a.hpow, -2.f * (float)a.hpow);
     const float2 sig2 = make_float2(a.sig2, a.sig2), e24 = make_float2(a.eps24, a.eps24);
     const float2 two = make_float2(2.f, 2.f), mone = make_float2(-1.f, -1.f);
+    float2 iL[3], nLf[3], nLlo[3];
+    if constexpr (PER) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            iL[k] = make_float2(a.box.invLf[k], a.box.invLf[k]);
+            nLf[k] = make_float2(-a.box.Lf[k], -a.box.Lf[k]);
+            nLlo[k] = make_float2(-a.box.Llo[k], -a.box.Llo[k]);
+        }
+    }
     const int mi = i >> 1;
 #pragma unroll 2
     for (int m = m0; m < m1; ++m) {
@@ -146,9 +188,18 @@ __device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, flo
                 B.z = 0.f;
             }
         }
-        const float2 dx = __fadd2_rn(px, make_float2(A.x, A.y)), dy = __fadd2_rn(py, make_float2(A.z, A.w)),
-                     dz = __fadd2_rn(pz, make_float2(B.x, B.y));
-        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        float2 dx = __fadd2_rn(px, make_float2(A.x, A.y)), dy = __fadd2_rn(py, make_float2(A.z, A.w)),
+               dz = __fadd2_rn(pz, make_float2(B.x, B.y));
+        if constexpr (PER) {
+            dx = wk_wrap2(dx, iL[0], nLf[0], nLlo[0]);
+            dy = wk_wrap2(dy, iL[1], nLf[1], nLlo[1]);
+            dz = wk_wrap2(dz, iL[2], nLf[2], nLlo[2]);
+        }
+        float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        if constexpr (PER) {
+            r2.x = B.z != 0.f ? r2.x : a.rc2;
+            r2.y = B.w != 0.f ? r2.y : a.rc2;
+        }
         const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
         if (co) {
             const float2 y = __fmul2_rn(r2, inv);
@@ -158,6 +209,8 @@ __device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, flo
                 for (int k = 1; k < H; ++k) yh = __fmul2_rn(yh, y);
             } else {
                 for (int k = 1; k < a.hpow; ++k) yh = __fmul2_rn(yh, y);
+                yh.x = fminf(yh.x, 1e30f);
+                yh.y = fminf(yh.y, 1e30f);
             }
             const float2 den = __fadd2_rn(one, yh);
             const float2 sw = make_float2(rcp_approx(den.x), rcp_approx(den.y));
@@ -179,8 +232,8 @@ __device__ __forceinline__ void pair_range2(const float4* __restrict__ wpos, flo
     }
 }
 
-template <int D, int H>
-__global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mode)
+template <int D, int H, bool PER>
+__global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(const __grid_constant__ WkArgs a, int mode)
 {
     extern __shared__ __align__(128) unsigned char wk_smem[];
     float4 (*ring)[2 * CHUNK] = reinterpret_cast<float4 (*)[2 * CHUNK]>(wk_smem);
@@ -231,7 +284,7 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                 const float4 p = wk_atom(wpos, i);
                 PairAcc2 c2{};
                 const int m0 = (int)((long long)np * sl / Gs), m1 = (int)((long long)np * (sl + 1) / Gs);
-                pair_range2<H>(wpos, p, i, m0, m1, a, c2);
+                pair_range2<H, PER>(wpos, p, i, m0, m1, a, c2);
                 acc.fx = c2.fx.x + c2.fx.y;
                 acc.fy = c2.fy.x + c2.fy.y;
                 acc.fz = c2.fz.x + c2.fz.y;
@@ -266,7 +319,12 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                 }
                 if (a.cv_rg >= 0) {
                     const float4 p = wk_atom(wpos, i), p0 = wk_atom(wpos, 0);
-                    const float ux = p.x - p0.x, uy = p.y - p0.y, uz = p.z - p0.z;
+                    float ux = p.x - p0.x, uy = p.y - p0.y, uz = p.z - p0.z;
+                    if constexpr (PER) {
+                        ux = min_image<float>(ux, a.box, 0);
+                        uy = min_image<float>(uy, a.box, 1);
+                        uz = min_image<float>(uz, a.box, 2);
+                    }
                     mom[1] = cf{ux, 0.f};
                     mom[2] = cf{uy, 0.f};
                     mom[3] = cf{uz, 0.f};
@@ -308,9 +366,8 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
                         double sc = a.rg_scale != 0.0 ? a.rg_scale : 1.0;
                         if (a.rg_intensive) sc /= cbrt((double)n);
                         a.xi[w * 4 + a.cv_rg] = sc * rg;
-                        const float4 p0 = wk_atom(wpos, 0);
-                        a.rgc[w] = make_float4((float)(p0.x + cx), (float)(p0.y + cy), (float)(p0.z + cz),
-                                               (float)(sc / (n * rg)));
+                        a.rgc[w] = make_float4((float)cx, (float)cy, (float)cz, (float)(sc / (n * rg)));
+                        a.rgc[a.W + w] = wk_atom(wpos, 0);
                     }
                     a.ticket[w] = 0u;
                 }
@@ -319,8 +376,8 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
     }
     if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
-    // ---- P2a: hills partials for all walker points
-    {
+    if (a.bias == 0) {
+        // ---- P2a: hills partials for all walker points
         const int tiles = (a.W + WK_T - 1) / WK_T;
         bool fresh = true;
         for (int task = blockIdx.x; task < tiles * a.hsplit; task += G) {
@@ -334,17 +391,33 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
             if (tid == 0)
                 for (int s = 0; s < NST; ++s) mbar_inval(&hbar[s]);
         }
-    }
-    if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
+        if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
-    // ---- P2b: V and dV/dxi per walker (one warp per point)
-    {
+        // ---- P2b: V and dV/dxi per walker (one warp per point)
         const int lane = tid % 32;
         for (int p = blockIdx.x * (WK_T / 32) + tid / 32; p < a.W; p += G * (WK_T / 32)) {
             CF4 acc{};
             for (int s = lane; s < a.hsplit; s += 32) cf4_add(acc, load_cf4(a.hpart + (size_t)s * a.W + p));
             cf4_lane_sum<32>(acc);
             if (lane == 0) emit_cf(p, acc, a.hout);
+        }
+    } else {
+        // ---- P2: harmonic windows or the grid, one thread per walker (the
+        // grid read corner by corner: few registers)
+        for (int p = blockIdx.x * WK_T + tid; p < a.W; p += G * WK_T) {
+            if (a.bias == 1) {
+                harmonic_point<float>(a.d, a.hk, a.hper, a.xi + p * 4, a.hcen + p * 4, a.hout.V + p, a.hout.dV + p * 4,
+                                      mode == 0 ? a.hsum + p * 4 : nullptr);
+                if (mode == 0 && p == 0) a.hsum[a.W * 4] += 1.0;
+            } else {
+                double x[D], v, gr[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) x[q] = a.xi[p * 4 + q];
+                grid_point<D, false>(a.g, a.grid, x, v, gr);
+                a.hout.V[p] = (float)v;
+#pragma unroll
+                for (int q = 0; q < D; ++q) a.hout.dV[p * 4 + q] = (float)gr[q];
+            }
         }
     }
     if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
@@ -364,11 +437,17 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
         }
         if (a.cv_rg >= 0) {
             const float g = a.hout.dV[w * 4 + a.cv_rg];
-            const float4 c = a.rgc[w];
+            const float4 c = a.rgc[w], o = a.rgc[a.W + w];
             const float4 p = a.x[i];
-            F.x -= g * c.w * (p.x - c.x);
-            F.y -= g * c.w * (p.y - c.y);
-            F.z -= g * c.w * (p.z - c.z);
+            float ux = p.x - o.x, uy = p.y - o.y, uz = p.z - o.z;
+            if constexpr (PER) {
+                ux = min_image<float>(ux, a.box, 0);
+                uy = min_image<float>(uy, a.box, 1);
+                uz = min_image<float>(uz, a.box, 2);
+            }
+            F.x -= g * c.w * (ux - c.x);
+            F.y -= g * c.w * (uy - c.y);
+            F.z -= g * c.w * (uz - c.z);
         }
         a.f[i] = F;
         if (mode == 0) {
@@ -387,13 +466,21 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(WkArgs a, int mod
 using WkKernel = void (*)(WkArgs, int);
 
 // n = 6 (h = 3) gets a kernel with the exponent fixed at compile time
+// (and no cap on y^h: with r0 >= 1e-2 the padding point's y^3 stays below
+// FP32's range); a periodic box gets the minimum-image kernels.
+template <bool PER> static WkKernel wk_kernel_t(int d, bool h3)
+{
+    if (d == 1) return h3 ? walkers_step_kernel<1, 3, PER> : walkers_step_kernel<1, 0, PER>;
+    return h3 ? walkers_step_kernel<2, 3, PER> : walkers_step_kernel<2, 0, PER>;
+}
+
 static WkKernel wk_kernel(const wtmd_t* h)
 {
-    int hp = 3;
+    bool h3 = true;
     for (int c = 0; c < h->d; ++c)
-        if (h->cv[c].kind == WTMD_CV_COORDINATION) hp = h->cv[c].nn / 2;
-    if (h->d == 1) return hp == 3 ? walkers_step_kernel<1, 3> : walkers_step_kernel<1, 0>;
-    return hp == 3 ? walkers_step_kernel<2, 3> : walkers_step_kernel<2, 0>;
+        if (h->cv[c].kind == WTMD_CV_COORDINATION) h3 = h->cv[c].nn == 6 && h->cv[c].r0 >= 1e-2;
+    const bool per = h->cfg.box[0] > 0.0 || h->cfg.box[1] > 0.0 || h->cfg.box[2] > 0.0;
+    return per ? wk_kernel_t<true>(h->d, h3) : wk_kernel_t<false>(h->d, h3);
 }
 
 static size_t wk_smem_bytes(const wtmd_t* h)
@@ -449,7 +536,7 @@ static int wk_build(wtmd_t* h, int T, int bps, int hsplit_mult)
     if (!k.ticket) {
         WTMD_CUDA_TRY(h, cudaMalloc(&k.ticket, sizeof(unsigned) * h->W));
         WTMD_CUDA_TRY(h, cudaMemset(k.ticket, 0, sizeof(unsigned) * h->W));
-        WTMD_CUDA_TRY(h, cudaMalloc(&k.rgc, sizeof(float4) * h->W));
+        WTMD_CUDA_TRY(h, cudaMalloc(&k.rgc, sizeof(float4) * 2 * h->W));
         WTMD_CUDA_TRY(h, cudaMalloc(&k.bar, sizeof(unsigned) * 4));  // count, generation, task queue, spare
         WTMD_CUDA_TRY(h, cudaMemset(k.bar, 0, sizeof(unsigned) * 4));
     }
@@ -476,11 +563,6 @@ int walkers_enable(wtmd_t* h)
         h->err = "persistent walkers need an FP32 handle with the LJ engine";
         return WTMD_EINVAL;
     }
-    for (int k = 0; k < 3; ++k)
-        if (h->cfg.box[k] > 0.0) {
-            h->err = "persistent walkers run open (non-periodic) clusters";
-            return WTMD_EINVAL;
-        }
     if (h->ncv != h->d || h->d > 2) {
         h->err = "persistent walkers need 1 or 2 CVs, all defined";
         return WTMD_EINVAL;
@@ -582,13 +664,7 @@ int launch_walkers_step(wtmd_t* h, int mode)
     for (int q = 0; q < 3; ++q) a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
     a.hout.ticket = nullptr;
     a.hout.status = h->status;
-    a.dep.stride = c.stride;
-    a.dep.cap = h->cap;
-    a.dep.W = h->W;
-    a.dep.d = h->d;
-    a.dep.w0 = c.w0;
-    a.dep.inv_dT = (c.gamma == 0.0 || isinf(c.gamma)) ? 0.0 : 1.0 / (c.kT * (c.gamma - 1.0));
-    for (int q = 0; q < 3; ++q) a.dep.a[q] = h->a[q];
+    a.dep = dep_prm(h);  // harmonic windows deposit nothing
     a.count = h->count;
     a.depw = h->dep;
     a.ctrw = h->ctr;
@@ -598,6 +674,16 @@ int launch_walkers_step(wtmd_t* h, int mode)
     a.status = h->status;
     a.max_wn = h->max_wn;
     a.wait_limit = h->wait_limit > 0 ? h->wait_limit : kWaitLimit;
+    a.box = h->box;
+    a.bias = h->bias_harm ? 1 : (h->bias_grid ? 2 : 0);
+    a.hcen = h->harm_centre;
+    a.hsum = h->harm_sum;
+    for (int q = 0; q < 3; ++q) {
+        a.hk[q] = h->harm_k[q];
+        a.hper[q] = q < h->d ? h->cv[q].period : 0.0;
+    }
+    if (h->grid) a.g = grid_prm(h);
+    a.grid = h->grid;
     // barrier counter, generation and task queue start clean on every launch
     // (a timed-out barrier would leave its counter dirty)
     WTMD_CUDA_TRY(h, cudaMemsetAsync(k.bar, 0, sizeof(unsigned) * 4, h->stream));

@@ -47,7 +47,7 @@ def walker_cvs(spec, x):
 
 
 def shared_hills(spec, x, H=1500, seed=5):
-    xi = walker_cvs(spec, x)
+    xi = walker_cvs_box(spec, x)
     return synth.uniform_hills(H, xi.min(0) - 0.3, xi.max(0) + 0.3, seed=seed, w_range=(0.01, 0.3))
 
 
@@ -171,9 +171,6 @@ def test_persistent_rejects_unsupported_handles():
     m = gpu_handle(spec, "f64")
     with pytest.raises(wt.WtmdError):
         m.walkers_persistent(True)
-    m = gpu_handle(dict(spec, box=(20.0, 20.0, 20.0)), "f32")
-    with pytest.raises(wt.WtmdError):
-        m.walkers_persistent(True)
     m = gpu_handle(dict(spec, cvs=[dict(kind="dihedral", a=[0, 1, 2, 3], period=2 * np.pi), dict(kind="rg")]),
                    "f32")
     with pytest.raises(wt.WtmdError):
@@ -240,3 +237,189 @@ def test_full_size_cluster_workload_sampled_against_oracle():
         Fs = force_scale(sim, xw, hills, [0.0, 0.0])
         dF = np.linalg.norm(Fg[off[w]: off[w + 1]] - Fr)
         assert dF <= 1e-5 * (np.linalg.norm(Fr) + np.linalg.norm(Fs)), (w, n, dF / np.linalg.norm(Fr))
+
+
+def periodic_spec(W=6, lo=120, hi=360, L=8.5, seed=0, stride=5, nn=6, capacity=4000):
+    """W walkers, each a Lennard-Jones fluid in its own periodic box of edge
+    L (ragged sizes, log-uniform in [lo, hi]: rho* 0.2-0.6), T* = 1, seeded
+    random positions at least 0.9 sigma apart; CVs as for the clusters."""
+    sizes = synth.log_uniform_sizes(W, lo, hi, seed)
+    x = np.concatenate([synth.random_liquid(int(n), L, seed=300 + w) for w, n in enumerate(sizes)])
+    v = synth.velocities(x.shape[0], 1.0, 1.0, seed=seed + 1)
+    spec = dict(engine="lj", walker_sizes=[int(n) for n in sizes], box=(L, L, L), dt=0.004, kT=1.0, friction=1.0,
+                sigma=(0.2, 0.05), gamma=8.0, w0=0.3, stride=stride, capacity=capacity, seed=seed,
+                cvs=[dict(kind="coordination", r0=1.5, nn=nn, mm=2 * nn), dict(kind="rg")])
+    return spec, x, v
+
+
+def _dpos(X, Y, L):
+    D = X - Y
+    return D - L * np.rint(D / L)
+
+
+@pytest.mark.parametrize("nn", [6, 10])
+def test_persistent_periodic_boxes_match_generic_and_oracle(nn):
+    """Walkers in periodic boxes (minimum-image pairs and Rg members): three
+    steps with a deposit each against the generic FP32 launch sequence, and a
+    20-step trajectory against the FP64 oracle.  n = 10 takes the kernel with
+    the exponent read at run time."""
+    import oracle as o
+
+    spec, x, v = periodic_spec(stride=1, nn=nn)
+    L = spec["box"][0]
+    hills = shared_hills(spec, x)
+    ms = [_setup(spec, x, v, hills, p) for p in (False, True)]
+    for m, *_ in ms:
+        m.step_n(3)
+    torch.cuda.synchronize()
+    (mg, pg, vg, Fg), (mp, pp, vp, Fp) = ms
+    W = len(spec["walker_sizes"])
+    assert mg.counters() == mp.counters() == (3, 1500 + 3 * W)
+    assert np.abs(_dpos(to_np(pp)[:, :3], to_np(pg)[:, :3], L)).max() < 2e-6
+    assert torch.allclose(vp, vg, rtol=0, atol=1e-4)
+    assert torch.isfinite(Fp).all()
+    dF = torch.linalg.norm(Fp - Fg) / torch.linalg.norm(Fg)
+    assert dF < 1e-5, float(dF)
+    hg, hp = mg.hills_read(), mp.hills_read()
+    assert np.allclose(hp[:, :3], hg[:, :3], rtol=1e-5, atol=1e-6)
+    assert np.allclose(hp[:, 3], hg[:, 3], rtol=1e-4)
+
+    spec, x, v = periodic_spec(stride=5, nn=nn)
+    sim = o.Sim(oracle_system(spec), x=_f32(x), v=_f32(v), hills=hills)
+    sim.forces()
+    assert sim.run(20) == 0
+    m, pos, vel, F = _setup(spec, x, v, hills, True)
+    m.step_n(20)
+    torch.cuda.synchronize()
+    D = np.abs(_dpos(to_np(pos)[:, :3], sim.x, L))
+    assert D.max() < 1e-3 and np.median(D) < 1e-5, (D.max(), np.median(D))
+    assert m.counters() == (20, 1500 + 4 * W)
+    h, ref = m.hills_read(), sim.hills[: sim.n_hills]
+    assert np.allclose(h[1500:, :2], ref[1500:, :2], rtol=1e-4, atol=1e-4)
+    assert np.allclose(h[1500:, 3], ref[1500:, 3], rtol=1e-3)
+
+
+def test_persistent_high_exponent_open_clusters():
+    """Open clusters with n = 10, m = 20: the padding point of an odd-sized
+    walker and each target's left-out self pair lie 1e4 away, where y^h
+    exceeds FP32's range; the run-time-exponent kernel caps it, so forces
+    stay finite and match the generic launch sequence."""
+    spec, x, v = cluster_spec(W=9, hi=300, stride=1)
+    spec["cvs"][0] = dict(kind="coordination", r0=1.5, nn=10, mm=20)
+    hills = shared_hills(spec, x)
+    ms = [_setup(spec, x, v, hills, p) for p in (False, True)]
+    for m, *_ in ms:
+        m.step_n(2)
+    torch.cuda.synchronize()
+    (mg, pg, vg, Fg), (mp, pp, vp, Fp) = ms
+    assert torch.isfinite(Fp).all() and torch.isfinite(pp).all()
+    assert torch.allclose(pp, pg, rtol=0, atol=2e-6)
+    dF = torch.linalg.norm(Fp - Fg) / torch.linalg.norm(Fg)
+    assert dF < 1e-5, float(dF)
+
+
+def test_persistent_umbrella_windows_periodic_against_oracle():
+    """Umbrella windows as walkers of the persistent launch (Sec. 2.1.1
+    harmonic bias, Sec. 2.1.2 umbrella sampling): one window per periodic
+    walker on (coordination, Rg), centres offset from the starting CVs.
+    Against the generic launch sequence (forces, window sums) and against
+    the FP64 oracle's run with the same windows (trajectory, window means,
+    sample count, umbrella integration); no hill is deposited."""
+    import oracle as o
+
+    spec, x, v = periodic_spec(stride=5)
+    L = spec["box"][0]
+    W = len(spec["walker_sizes"])
+    xi0 = walker_cvs_box(spec, x)
+    centres = xi0 + np.array([0.4, -0.2])[None, :] * np.sign(np.arange(W) % 2 - 0.5)[:, None]
+    k = (30.0, 8.0)
+
+    def gpu(persistent):
+        m, pos, vel, F = _setup(spec, x, v, None, False)
+        m.harmonic(k, centres)
+        if persistent:
+            m.walkers_persistent(True)
+        return m, pos, vel, F
+
+    ms = [gpu(p) for p in (False, True)]
+    for m, *_ in ms:
+        m.step_n(3)
+    torch.cuda.synchronize()
+    (mg, pg, vg, Fg), (mp, pp, vp, Fp) = ms
+    assert np.abs(_dpos(to_np(pp)[:, :3], to_np(pg)[:, :3], L)).max() < 2e-6
+    dF = torch.linalg.norm(Fp - Fg) / torch.linalg.norm(Fg)
+    assert dF < 1e-5, float(dF)
+    (mean_g, n_g), (mean_p, n_p) = mg.umbrella_stats(), mp.umbrella_stats()
+    assert n_g == n_p == 3
+    np.testing.assert_allclose(mean_p, mean_g, rtol=1e-6)
+
+    osys = oracle_system(spec)
+    osys.umb_k, osys.umb_centres = k, centres
+    sim = o.Sim(osys, x=_f32(x), v=_f32(v))
+    sim.forces()
+    assert sim.run(30) == 0
+    m, pos, vel, F = gpu(True)
+    m.step_n(30)
+    torch.cuda.synchronize()
+    D = np.abs(_dpos(to_np(pos)[:, :3], sim.x, L))
+    assert D.max() < 1e-3 and np.median(D) < 1e-5, (D.max(), np.median(D))
+    assert m.counters()[1] == 0  # windows deposit no hills
+    mean, n = m.umbrella_stats()
+    assert n == sim.n_samples == 30
+    om, og, oA = sim.umbrella()
+    # window means to the trajectories' FP32 agreement (as the deposited CVs
+    # of the metadynamics runs)
+    np.testing.assert_allclose(mean, om, rtol=1e-4, atol=1e-4)
+    g, A = m.umbrella_integrate()
+    kk = np.asarray(k)
+    # mean force k (mean - centre): the means' error times k
+    assert np.all(np.abs(g - og) <= kk[None, :] * 1e-4 * (1 + np.abs(om)) + 1e-6 * np.abs(og))
+    assert np.all(np.isfinite(A))
+
+
+def test_persistent_grid_read_bias_against_generic_and_oracle():
+    """The bias read from the FP64 grid inside the persistent launch (Sec.
+    2.1.5): the grid is updated after each step that deposits and read back
+    at the next step's CVs.  Against the generic launch sequence with the
+    same bias source (forces, hills, grid) and against the FP64 oracle run
+    with the grid-read bias (trajectory and grid)."""
+    import oracle as o
+
+    grid = ((32, 24), (7.0, 1.0), (15.0, 4.0))
+    spec, x, v = cluster_spec(W=9, hi=300, grid=grid, stride=2)
+    spec["bias_grid"] = True
+    ms = [_setup(spec, x, v, None, p) for p in (False, True)]
+    for m, *_ in ms:
+        m.step_n(8)
+    torch.cuda.synchronize()
+    (mg, pg, vg, Fg), (mp, pp, vp, Fp) = ms
+    assert mg.counters() == mp.counters() == (8, 4 * 9)
+    assert torch.allclose(pp, pg, rtol=0, atol=2e-6)
+    dF = torch.linalg.norm(Fp - Fg) / torch.linalg.norm(Fg)
+    assert dF < 1e-5, float(dF)
+    assert np.allclose(mp.grid_read(), mg.grid_read(), rtol=1e-5, atol=1e-7)
+    xi_g, xi_p = mg.hills_read()[:, :2], mp.hills_read()[:, :2]
+    assert np.allclose(xi_p, xi_g, rtol=1e-5, atol=1e-6)
+
+    sim = o.Sim(oracle_system(spec), x=_f32(x), v=_f32(v))
+    sim.forces()
+    assert sim.run(12) == 0
+    m, pos, vel, F = _setup(spec, x, v, None, True)
+    m.step_n(12)
+    torch.cuda.synchronize()
+    X = to_np(pos)[:, :3]
+    assert np.max(np.abs(X - sim.x)) < 1e-3 and np.median(np.abs(X - sim.x)) < 1e-5
+    assert m.counters() == (12, 6 * 9)
+    g = m.grid_read().ravel()
+    assert np.allclose(g, sim.grid, rtol=1e-3, atol=1e-4 * np.abs(sim.grid).max())
+
+
+def walker_cvs_box(spec, x):
+    import oracle as o
+
+    sysd = oracle_system(spec)
+    out, off = [], 0
+    for n in spec["walker_sizes"]:
+        out.append([o.cv_eval(cv, x[off: off + n], list(spec["box"]))[0] for cv in sysd.cvs])
+        off += n
+    return np.asarray(out)
