@@ -105,6 +105,14 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
     const int a0 = ia0 < t.nA ? t.A[ia0] : -1, a1 = ia1 < t.nA ? t.A[ia1] : -1;
     const int q = tid;
     const int jq = q < mb ? (t.B ? t.B[b0 + q] : b0 + q) : -1;
+    // scale times the share quantum 2^q (thread 0 rounds the CTA's share)
+    const double sxq = tid == 0 ? t.scw * t.xq : 0.0;
+    // position in B of this lane's targets (for their self pairs)
+    int pbs = -1;
+    if (warp < 2) {
+        const int a = warp == 0 ? a0 : a1;
+        if (a >= 0) pbs = t.inv_b ? t.inv_b[a] : (a < t.nw ? a : -1);
+    }
     wait();
     if (jq >= 0) {
         const float4 p = t.pos[jq];
@@ -189,7 +197,7 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
     // chunk that holds it as a partner
     if (warp < 2) {
         const int r = tid, ia = tile * C2_A + r;
-        double xs = 0.0;
+        cf xs{0.f, 0.f};
         if (ia < t.nA) {
             float4 u = rowred[0][r];
             for (int k = 1; k < CT_T / 32; ++k) {
@@ -200,16 +208,20 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
                 u.w += v.w;
             }
             t.rowpart[(size_t)chunk * t.nA + ia] = u;
-            const int a = warp == 0 ? a0 : a1;
-            const int pb = t.inv_b ? t.inv_b[a] : (a < t.nw ? a : -1);
-            if (pb >= b0 && pb < b0 + mb) u.w -= rcp_approx(1.f);
-            xs = (double)u.w;
+            if (pbs >= b0 && pbs < b0 + mb) u.w -= rcp_approx(1.f);
+            xs.hi = u.w;
         }
-        for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-        if (lane == 0) xred[warp] = xs;
+        // compensated FP32 (a dependent FP64 operation costs ~64 cycles on
+        // this GPU); the share is rounded to the exact quantum in FP64 once
+        for (int off = 16; off > 0; off >>= 1) xs = cf_add(xs, cf_shfl_xor(xs, off));
+        if (lane == 0) reinterpret_cast<float2*>(xred)[warp] = make_float2(xs.hi, xs.lo);
     }
     sync();
-    if (tid == 0) atomicAdd(t.xi, rint(t.scw * (xred[0] + xred[1]) * t.xq) * t.ixq);
+    if (tid == 0) {
+        const float2 u = reinterpret_cast<const float2*>(xred)[0], v = reinterpret_cast<const float2*>(xred)[1];
+        const cf c = cf_add(cf{u.x, u.y}, cf{v.x, v.y});
+        atomicAdd(t.xi, rint(((double)c.hi + (double)c.lo) * sxq) * t.ixq);
+    }
 }
 
 // J of one atom of walker w (local index li) from the FP32 tile partials:

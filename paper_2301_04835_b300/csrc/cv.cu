@@ -157,31 +157,36 @@ __global__ void cv_dihedral_kernel(const R4<R>* __restrict__ pos, const int64_t*
 constexpr int RG_CACHE = 1024;  // members whose unwrapped position stays in shared memory
 
 // Rg of walker w by the whole CTA (u: RG_CACHE staged members in shared
-// memory).  Called after the dependency wait.
-template <typename R>
+// memory).  The member indices of the first round are read before wait()
+// (the dependency wait of a programmatic launch), the positions after it.
+// FP32 handles finish in FP32 (compensated sums; a dependent FP64 division
+// or square root costs ~700 cycles on this GPU), FP64 handles in FP64.
+template <typename R, class Wait>
 __device__ void cv_rg_body(int w, const R4<R>* __restrict__ pos, const int64_t* __restrict__ woff,
                            const int* __restrict__ wn, const int* __restrict__ A, int nA, const Box& box, double scale,
-                           int intensive, double* __restrict__ xi, int col, R4<R>* __restrict__ J, R4<R>* u)
+                           int intensive, double* __restrict__ xi, int col, R4<R>* __restrict__ J, R4<R>* u, Wait wait)
 {
     __shared__ R bc[4];  // broadcast: centre (3) and the Jacobian factor
     const long long o = woff[w];
     const int m = A ? nA : wn[w];
     const int i0 = A ? A[0] : 0;
+    const int ifirst = (int)threadIdx.x < m ? (A ? A[threadIdx.x] : (int)threadIdx.x) : 0;
+    wait();
     R rx, ry, rz;
     load3<R>(pos, o + i0, rx, ry, rz);
     // unwrapped position of member p (minimum image relative to member 0)
-    auto unwrap = [&](int p) {
-        const int i = A ? A[p] : p;
+    auto unwrap_i = [&](int i) {
         R x, y, z, d[3];
         load3<R>(pos, o + i, x, y, z);
         delta<R>(box, x, y, z, rx, ry, rz, d);
         return mk4<R>(rx + d[0], ry + d[1], rz + d[2], R(0));
     };
+    auto member = [&](int p) { return p == (int)threadIdx.x ? ifirst : (A ? A[p] : p); };
     // FP32 handles sum in compensated FP32, FP64 handles in FP64
     cf s[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     double sd[3] = {0.0, 0.0, 0.0};
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        const R4<R> q = unwrap(p);
+        const R4<R> q = unwrap_i(member(p));
         if (p < RG_CACHE) u[p] = q;
         if constexpr (sizeof(R) == 4) {
             s[0] = cf_add(s[0], (float)q.x);
@@ -195,14 +200,20 @@ __device__ void cv_rg_body(int w, const R4<R>* __restrict__ pos, const int64_t* 
     }
     if constexpr (sizeof(R) == 4) block_sum_cf<3>(s);
     else block_sum<double, 3>(sd);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) bc[k] = (R)((sizeof(R) == 4 ? cf_val(s[k]) : sd[k]) / m);
+    if (threadIdx.x == 0) {
+        if constexpr (sizeof(R) == 4) {
+            const float im = 1.f / (float)m;
+            for (int k = 0; k < 3; ++k) bc[k] = (s[k].hi + s[k].lo) * im;
+        } else {
+            for (int k = 0; k < 3; ++k) bc[k] = (R)(sd[k] / m);
+        }
+    }
     __syncthreads();
     const R c[3] = {bc[0], bc[1], bc[2]};
     cf q2[1] = {{0.f, 0.f}};
     double q2d[1] = {0.0};
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        const R4<R> q = p < RG_CACHE ? u[p] : unwrap(p);
+        const R4<R> q = p < RG_CACHE ? u[p] : unwrap_i(member(p));
         const R ux = q.x - c[0], uy = q.y - c[1], uz = q.z - c[2];
         if constexpr (sizeof(R) == 4) q2[0] = cf_add(q2[0], (float)(ux * ux + uy * uy + uz * uz));
         else q2d[0] += (double)(ux * ux + uy * uy + uz * uz);
@@ -211,22 +222,29 @@ __device__ void cv_rg_body(int w, const R4<R>* __restrict__ pos, const int64_t* 
     else block_sum<double, 1>(q2d);
     __shared__ double rg_s;
     if (threadIdx.x == 0) {
-        const double rg = sqrt((sizeof(R) == 4 ? cf_val(q2[0]) : q2d[0]) / m);
-        double sc = scale != 0.0 ? scale : 1.0;
-        if (intensive) sc /= cbrt((double)m);
-        bc[3] = (R)(sc / (m * rg));
-        rg_s = sc * rg;
+        if constexpr (sizeof(R) == 4) {
+            const float rg = sqrtf((q2[0].hi + q2[0].lo) / (float)m);
+            float sc = scale != 0.0 ? (float)scale : 1.f;
+            if (intensive) sc /= cbrtf((float)m);
+            bc[3] = sc / ((float)m * rg);
+            rg_s = (double)(sc * rg);
+        } else {
+            const double rg = sqrt(q2d[0] / m);
+            double sc = scale != 0.0 ? scale : 1.0;
+            if (intensive) sc /= cbrt((double)m);
+            bc[3] = (R)(sc / (m * rg));
+            rg_s = sc * rg;
+        }
     }
     __syncthreads();
     const R f = bc[3];
     for (int p = threadIdx.x; p < m; p += blockDim.x) {
-        const int i = A ? A[p] : p;
-        const R4<R> q = p < RG_CACHE ? u[p] : unwrap(p);
+        const int i = member(p);
+        const R4<R> q = p < RG_CACHE ? u[p] : unwrap_i(i);
         J[o + i] = mk4<R>(f * (q.x - c[0]), f * (q.y - c[1]), f * (q.z - c[2]), R(0));
     }
     if (threadIdx.x == 0) xi[w * 4 + col] = rg_s;
 }
-
 
 // One block per walker.  A programmatic dependent of the kernel that moved
 // the atoms: the kernels that need this CV (joined after it) may launch at
@@ -239,8 +257,7 @@ __global__ void __launch_bounds__(256) cv_rg_kernel(const R4<R>* __restrict__ po
 {
     __shared__ R4<R> u[RG_CACHE];
     pdl_trigger();
-    pdl_wait();
-    cv_rg_body<R>((int)blockIdx.x, pos, woff, wn, A, nA, box, scale, intensive, xi, col, J, u);
+    cv_rg_body<R>((int)blockIdx.x, pos, woff, wn, A, nA, box, scale, intensive, xi, col, J, u, [] { pdl_wait(); });
 }
 
 // ---------------------------------------------------------------------------
@@ -934,8 +951,8 @@ __global__ void __launch_bounds__(CT_T) coord_tile2_rg_kernel(const float4* __re
     const int w = blockIdx.y;
     const int ntc = (int)gridDim.x - 1;  // tile CTAs of the walker
     if ((int)blockIdx.x == ntc) {
-        pdl_wait();
-        cv_rg_body<float>(w, pos, woff, wn, rA, rnA, box, rscale, rintensive, xi, rcol, rJ, reinterpret_cast<float4*>(sm));
+        cv_rg_body<float>(w, pos, woff, wn, rA, rnA, box, rscale, rintensive, xi, rcol, rJ, reinterpret_cast<float4*>(sm),
+                          [] { pdl_wait(); });
         return;
     }
     float4* srcA = reinterpret_cast<float4*>(sm);

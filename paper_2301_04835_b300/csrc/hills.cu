@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
 // the hill range, and each copies its share of the pair records into shared
 // memory with one bulk (TMA) copy issued before the dependency wait, so the
 // records are on chip when the points are known.  The split sums meet in
-// distributed shared memory: rank 0 adds the ranks' compensated sums in rank
-// order and writes V and dV.  No global partials, fences or tickets;
+// distributed shared memory: rank 0 adds the ranks' compensated sums by a
+// fixed xor tree over 16 lanes (lane r holds rank r) and writes V and dV.  No global partials, fences or tickets;
 // deterministic.  For short hill lists (a walker's point in a step), where
 // the reduction, not the streaming, is the cost.  Records beyond the shared
 // share (lists longer than the capacity the launch was sized for) are read
@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
     cluster_sync();  // every rank's sums are in its shared memory
     if (rank == 0 && tid < 32) {
         // lane r reads rank r's sums (all ranks' loads in flight together),
-        // then the ranks are added in rank order through shuffles
+        // then a fixed xor tree over 16 lanes adds them (lanes >= CL hold 0;
+        // four dependent levels instead of a chain over the ranks)
         for (int p = 0; p < NP && p < P; ++p) {
             CF4 mine{};
             if ((unsigned)tid < CL) {
@@ -317,14 +318,8 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
                 const float4 u = ld_dsmem_f4(q, (unsigned)tid), w = ld_dsmem_f4(q + 1, (unsigned)tid);
                 mine = CF4{{cf{u.x, u.y}, cf{u.z, u.w}, cf{w.x, w.y}, cf{w.z, w.w}}};
             }
-            CF4 a{};
-            for (unsigned r = 0; r < CL; ++r)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const cf t{__shfl_sync(0xffffffffu, mine.v[i].hi, (int)r), __shfl_sync(0xffffffffu, mine.v[i].lo, (int)r)};
-                    a.v[i] = cf_add(a.v[i], t);
-                }
-            if (tid == 0) emit_cf(p, a, out);
+            cf4_lane_sum<16>(mine);
+            if (tid == 0) emit_cf(p, mine, out);
         }
     }
     cluster_sync();  // no rank leaves while rank 0 reads its shared memory
@@ -662,8 +657,8 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         }
         auto part = (dbl4*)h->partial;
         const int Pi = (int)P;
-        HillOut<float> o{(float*)V, (float*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
-                         h->status};
+        HillOut<float> o{(float*)V, (float*)dV, dvs, h->d, {gs[0], gs[1], gs[2]},
+                         {(float)gs[0], (float)gs[1], (float)gs[2]}, fused ? h->ticket : nullptr, h->status};
         if (xi_f64)
             launch_f32_pt<double>(h->d, per, pl.th, grid, h->stream, pdl, h->hills32, k0p, k1p, (const double*)xi,
                                   xs, Pi, h->ctr, prm, part, o, cap_pairs);
@@ -685,8 +680,8 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
         }
         auto part = (dbl4*)h->partial;
         const int Pi = (int)P;
-        HillOut<double> o{(double*)V, (double*)dV, dvs, h->d, {gs[0], gs[1], gs[2]}, fused ? h->ticket : nullptr,
-                          h->status};
+        HillOut<double> o{(double*)V, (double*)dV, dvs, h->d, {gs[0], gs[1], gs[2]},
+                          {(float)gs[0], (float)gs[1], (float)gs[2]}, fused ? h->ticket : nullptr, h->status};
         if (per)
             launch_f64_t<true>(pl.th, grid, h->stream, (const dbl4*)h->hills64, k1p, (const double*)xi, xs, Pi,
                                h->d, prm, part, o);

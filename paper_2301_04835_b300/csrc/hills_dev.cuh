@@ -66,7 +66,8 @@ template <typename R> struct HillOut {
     R* dV;
     int dvs;
     int D;
-    double gs[3];
+    double gs[3];   // dV/dxi_i = gs_i * (sum of the i-th gradient term)
+    float gsf[3];   // gs rounded to FP32 (emit_cf)
     unsigned* ticket;  // null: partials only (a separate finalize kernel reduces them)
     unsigned* status;
 };
@@ -214,12 +215,16 @@ template <int TH> __device__ __forceinline__ void reduce_lanes_cf(CF4& a)
 
 __device__ __forceinline__ void emit_cf(int p, const CF4& a, const HillOut<float>& o)
 {
-    const double v = cf_val(a.v[0]);
-    const double g[3] = {o.gs[0] * cf_val(a.v[1]), o.gs[1] * cf_val(a.v[2]), o.gs[2] * cf_val(a.v[3])};
+    // FP32 throughout: a compensated pair rounds to the nearest float by one
+    // addition, and a dependent FP64 operation costs ~64 cycles on this GPU
+    // (a division or square root ~700), far more than this sum's FP32 work
+    const float v = a.v[0].hi + a.v[0].lo;
+    const float g[3] = {o.gsf[0] * (a.v[1].hi + a.v[1].lo), o.gsf[1] * (a.v[2].hi + a.v[2].lo),
+                        o.gsf[2] * (a.v[3].hi + a.v[3].lo)};
     if (!isfinite(v) || !isfinite(g[0]) || !isfinite(g[1]) || !isfinite(g[2])) atomicOr(o.status, ST_NUMERIC);
-    if (o.V) o.V[p] = (float)v;
+    if (o.V) o.V[p] = v;
     if (o.dV)
-        for (int i = 0; i < o.D; ++i) o.dV[(size_t)p * o.dvs + i] = (float)g[i];
+        for (int i = 0; i < o.D; ++i) o.dV[(size_t)p * o.dvs + i] = g[i];
 }
 
 // Sum of the S splits of point p by the whole CTA (fixed order: thread

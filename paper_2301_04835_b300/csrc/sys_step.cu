@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(SS_T, 1) sys_step_kernel(SsArgs a)
         for (int s = tid; s < (int)G; s += 32) cf4_add(acc, load_cf4(a.hpart + s));
         cf4_lane_sum<32>(acc);
         if (tid == 0) {
-            for (int k = 0; k < 3; ++k) sdv[k] = (float)(a.hout.gs[k] * cf_val(acc.v[1 + k]));
+            for (int k = 0; k < 3; ++k) sdv[k] = a.hout.gsf[k] * (acc.v[1 + k].hi + acc.v[1 + k].lo);  // as emit_cf
             if (b == 0) emit_cf(0, acc, a.hout);
         }
     }
@@ -587,7 +587,10 @@ int launch_sys_step(wtmd_t* h)
     a.hout.dV = (float*)h->dV;
     a.hout.dvs = 4;
     a.hout.D = h->d;
-    for (int q = 0; q < 3; ++q) a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
+    for (int q = 0; q < 3; ++q) {
+        a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
+        a.hout.gsf[q] = (float)a.hout.gs[q];
+    }
     a.hout.ticket = nullptr;
     a.hout.status = h->status;
     a.dep = dep_prm(h);

@@ -661,7 +661,10 @@ int launch_walkers_step(wtmd_t* h, int mode)
     a.hout.dV = (float*)h->dV;
     a.hout.dvs = 4;
     a.hout.D = h->d;
-    for (int q = 0; q < 3; ++q) a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
+    for (int q = 0; q < 3; ++q) {
+        a.hout.gs[q] = -2.0 * 0.69314718055994530942 * h->a[q];
+        a.hout.gsf[q] = (float)a.hout.gs[q];
+    }
     a.hout.ticket = nullptr;
     a.hout.status = h->status;
     a.dep = dep_prm(h);  // harmonic windows deposit nothing
