@@ -145,8 +145,10 @@ __global__ void nl_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box,
                               unsigned* status)
 {
     // a programmatic dependent of BAOAB (which sets the flag and moves the
-    // atoms): wait first
+    // atoms): wait first; the list build may start once every CTA is past
+    // this wait (the flag it reads is then final)
     pdl_wait();
+    pdl_trigger();
     if (*ctl == 0u) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(NL_T) nl_build_kernel(long long N, const R4<R>
                                                         unsigned* status)
 {
     pdl_trigger();
-    if (*ctl == 0u) return;  // final: this is a plain launch after the binning, which waited for BAOAB
+    if (*ctl == 0u) return;  // final: the binning triggers this launch only after its wait for BAOAB
     pdl_wait();              // the binning
     extern __shared__ __align__(32) unsigned char nl_smem[];
     nl_build_cell<R>((int)blockIdx.x, x, box, ncx, ncy, ncz, ccap, ccount, catoms, nbr, ncnt, xref, cap8, rl2, status,
@@ -185,9 +187,9 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
                                                        R eps24, R4<R>* __restrict__ f)
 {
     const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
-    // the flag is final when this launch starts (the list build before it is
-    // a plain launch after the binning, which waited for BAOAB) and is
-    // cleared after the step; without a rebuild the lists are those of an
+    // the flag is final when this launch starts (the list build before it
+    // starts only after the binning's wait for BAOAB) and is cleared after
+    // the step; without a rebuild the lists are those of an
     // earlier step and nothing is waited for
     if (*ctl != 0u) pdl_wait();  // the list build
     R fx = 0, fy = 0, fz = 0;
@@ -399,16 +401,19 @@ template <typename R> static int launch_engine_t(wtmd_t* h)
             // bin -> build -> forces as programmatic dependents: the first
             // two return at once unless a rebuild is flagged
             // binning: a programmatic dependent of BAOAB; the list build: a
-            // plain launch (its large-shared-memory CTAs never wait on an
-            // SM), so the flag it and the force sweep read is final
+            // programmatic dependent of the binning, which triggers it after
+            // its own wait for BAOAB, so the flag that it and the force
+            // sweep read is final (its large-shared-memory CTAs wait on an
+            // SM only in a step with a rebuild)
             WTMD_CUDA_TRY(h, launch_pdl(nl_bin_kernel<R>, dim3(nb), dim3(256), 0, st, (long long)h->N, x, h->box,
                                         h->nc[0], h->nc[1], h->nc[2], h->cell_cap, h->cell_count, h->cell_atoms,
                                         (const unsigned*)h->nl_ctl, h->status));
             mark(h, "nl_bin");
-            nl_build_kernel<R><<<h->ncells, NL_T, h->nl_smem, st>>>(
-                (long long)h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap, (const int*)h->cell_count,
-                (const int*)h->cell_atoms, h->nl_nbr, h->nl_cnt, (R4<R>*)h->nl_xref, (const unsigned*)h->nl_ctl,
-                h->nl_cap8, (R)(rl * rl), h->status);
+            WTMD_CUDA_TRY(h, launch_pdl(nl_build_kernel<R>, dim3(h->ncells), dim3(NL_T), h->nl_smem, st,
+                                        (long long)h->N, x, h->box, h->nc[0], h->nc[1], h->nc[2], h->cell_cap,
+                                        (const int*)h->cell_count, (const int*)h->cell_atoms, h->nl_nbr, h->nl_cnt,
+                                        (R4<R>*)h->nl_xref, (const unsigned*)h->nl_ctl, h->nl_cap8, (R)(rl * rl),
+                                        h->status));
             mark(h, "nl_build");
             const unsigned nbl = (unsigned)((h->N * NL_S + NL_T - 1) / NL_T);
             WTMD_CUDA_TRY(h, launch_pdl(lj_list_kernel<R>, dim3(nbl), dim3(NL_T), 0, st, (long long)h->N, x, h->box,
