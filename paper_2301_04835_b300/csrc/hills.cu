@@ -61,16 +61,30 @@ __global__ void __launch_bounds__(256) hills_finalize_kernel(const dbl4* __restr
     }
 }
 
-__global__ void __launch_bounds__(256) hills_finalize_cf_kernel(const dbl4* __restrict__ partial, int S, int P,
-                                                                HillOut<float> o)
+// Fixed-order sum of the S split partials of the FP32 kernel, 32 points per
+// CTA: lane l takes point 32 b + l, so each split's row of 32 records is one
+// coalesced 1 KB read; warp w takes splits w, w + 32, ... (several loads in
+// flight per thread), and warp 0 adds the 32 warp sums of its point in warp
+// order.
+constexpr int FIN_W = 32;  // warps per finalize CTA
+__global__ void __launch_bounds__(FIN_W * 32) hills_finalize_cf_kernel(const dbl4* __restrict__ partial, int S, int P,
+                                                                      HillOut<float> o)
 {
-    const int lane = threadIdx.x % 32;
-    const int p = blockIdx.x * 8 + threadIdx.x / 32;
-    if (p >= P) return;
+    __shared__ CF4 red[FIN_W][32];
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int p = blockIdx.x * 32 + lane;
     CF4 a{};
-    for (int s = lane; s < S; s += 32) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
-    cf4_lane_sum<32>(a);
-    if (lane == 0) emit_cf(p, a, o);
+    if (p < P) {
+#pragma unroll 4
+        for (int s = w; s < S; s += FIN_W) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
+    }
+    red[w][lane] = a;
+    __syncthreads();
+    if (w == 0 && p < P) {
+        CF4 t = red[0][lane];
+        for (int k = 1; k < FIN_W; ++k) cf4_add(t, red[k][lane]);
+        emit_cf(p, t, o);
+    }
 }
 
 template <int D, int TH, bool PER, typename PT>
@@ -667,7 +681,7 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
                                  Pi, h->ctr, prm, part, o, cap_pairs);
         mark(h, "hills_sum_f32");
         if (!fused) {
-            hills_finalize_cf_kernel<<<(Pi + 7) / 8, 256, 0, h->stream>>>(part, pl.split, Pi, o);
+            hills_finalize_cf_kernel<<<(Pi + 31) / 32, FIN_W * 32, 0, h->stream>>>(part, pl.split, Pi, o);
             mark(h, "hills_finalize");
         }
     } else {

@@ -304,9 +304,9 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
     hp += (size_t)(k0 >> 1) * 2;
     const long long nch = (npairs + CHUNK - 1) / CHUNK;
-    const long long per = (nch + nsplit - 1) / nsplit;
-    const long long c0 = (long long)split * per;
-    const long long c1 = c0 + per < nch ? c0 + per : nch;
+    // balanced: the splits' chunk counts differ by at most one
+    const long long c0 = nch * split / nsplit;
+    const long long c1 = nch * (split + 1) / nsplit;
     const int nmine = c1 > c0 ? (int)(c1 - c0) : 0;
 
     __syncthreads();  // a previous task of this CTA is done with the ring
