@@ -802,6 +802,7 @@ def _mb_run(wt, torch, steps, dt, friction, w0, stride):
     vel = wt.particles(np.zeros((1, 3)), torch.float64)
     F = torch.zeros_like(pos)
     m.bind(pos, vel, F)
+    single_cta = m.small_step()  # the single-CTA many-steps launch (hill capacity <= 2048) or the per-kernel step
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -826,6 +827,7 @@ def _mb_run(wt, torch, steps, dt, friction, w0, stride):
     d = (Fg - U)[mask]
     d = d - d.mean() if d.size else d
     return {"steps": steps, "dt": dt, "friction": friction, "w0": w0, "stride": stride, "ms": ms,
+            "path": "single-CTA launches of up to 65536 steps" if single_cta else "per-kernel step graphs",
             "steps_per_s": steps / (ms * 1e-3), "hills": int(hills.shape[0]), "visited_cells": int(mask.sum()),
             "fes_max_err_kT": float(np.abs(d).max() / kT) if d.size else None,
             "fes_rms_err_kT": float(np.sqrt(np.mean(d ** 2)) / kT) if d.size else None,

@@ -400,6 +400,20 @@ int wtmd_wait_limit(wtmd_t* h, int64_t cycles);
  * handle. */
 int wtmd_fused_step(wtmd_t* h, int32_t enable, int32_t* active);
 
+/* Small FP64 systems in one CTA (Sec. 3.2.1 steps (a)-(f) with the
+ * metadynamics update of Sec. 2.1.5): when the handle is FP64, its engine is
+ * Mueller-Brown or the three wells, every CV is a COMPONENT, it has at most
+ * 512 particles and 256 walkers (with the bias from the hills: at most 16
+ * walkers and a hill capacity of at most 2048)
+ * and the surrogate and the persistent walker step are off, step_n runs up
+ * to 65536 steps per launch of one CTA that loops over the steps (the same
+ * operations and Philox stream as the per-kernel step; the hills sum is
+ * added in another fixed order).  On by default.  enable = 1 allows it,
+ * 0 returns to the per-kernel step, -1 only queries; *active (host, may be
+ * NULL) receives 1 when the next step runs that way.  Drops captured step
+ * graphs when the setting changes.  Errors: WTMD_EINVAL for another enable. */
+int wtmd_small_step(wtmd_t* h, int32_t enable, int32_t* active);
+
 /* Autotuner of the persistent walker step: times every candidate (targets
  * per pair task 32/64/128/256, CTAs per SM 1/2/4, hill splits per CTA 1/2)
  * over `steps` steps from the same saved state, keeps the fastest, and

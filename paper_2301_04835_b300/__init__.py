@@ -72,7 +72,7 @@ EXPORTS = ["wtmd_create", "wtmd_destroy", "wtmd_last_error", "wtmd_set_stream", 
            "wtmd_surrogate_set", "wtmd_mlp_params", "wtmd_mlp_eval", "wtmd_mlp_grad", "wtmd_mlp_train", "wtmd_hills_tune",
            "wtmd_grid_eval", "wtmd_bias_source", "wtmd_checkpoint_size", "wtmd_checkpoint_save",
            "wtmd_checkpoint_load", "wtmd_harmonic", "wtmd_umbrella_stats", "wtmd_umbrella_integrate",
-           "wtmd_step_host", "wtmd_fused_step", "wtmd_hills_plan", "wtmd_wait_limit", "wtmd_barrier_probe"]
+           "wtmd_step_host", "wtmd_fused_step", "wtmd_small_step", "wtmd_hills_plan", "wtmd_wait_limit", "wtmd_barrier_probe"]
 
 BIAS_HILLS, BIAS_GRID, BIAS_HARMONIC = 0, 1, 2
 
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
     L.wtmd_probe_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wtmd_walkers_persistent.argtypes = [vp, i32]
     L.wtmd_fused_step.argtypes = [vp, i32, C.POINTER(i32)]
+    L.wtmd_small_step.argtypes = [vp, i32, C.POINTER(i32)]
     L.wtmd_hills_plan.argtypes = [vp, i64, i32, i32]
     L.wtmd_wait_limit.argtypes = [vp, i64]
     L.wtmd_barrier_probe.argtypes = [i32, i32, i64, C.POINTER(i32)]
@@ -322,6 +323,15 @@ class Wtmd:
         act = C.c_int32()
         self._err(lib().wtmd_fused_step(self.h, -1 if enable is None else (1 if enable else 0), C.byref(act)),
                   "wtmd_fused_step")
+        return bool(act.value)
+
+    def small_step(self, enable=None) -> bool:
+        """Allow (True, the default) or forbid (False) the single-CTA
+        many-steps launch for small FP64 analytic systems (None leaves the
+        setting); returns whether the next step uses it."""
+        act = C.c_int32()
+        self._err(lib().wtmd_small_step(self.h, -1 if enable is None else (1 if enable else 0), C.byref(act)),
+                  "wtmd_small_step")
         return bool(act.value)
 
     def hills_plan(self, P: int, lanes: int, splits: int):

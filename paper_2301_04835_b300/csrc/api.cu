@@ -520,6 +520,7 @@ static int prepare_sys_step(wtmd_t* h)
 static int enqueue_step(wtmd_t* h)
 {
     if (h->persistent) return launch_walkers_step(h, 0);
+    if (small_step_eligible(h)) return launch_small_steps(h, 1);
     if (use_sys_step(h)) return launch_sys_step(h);
     int rc;
     h->jf_pending = 0;
@@ -575,6 +576,7 @@ static int ready(wtmd_t* h)
 static int run_steps(wtmd_t* h, int64_t n_steps)
 {
     int rc;
+    if (small_step_eligible(h)) return launch_small_steps(h, n_steps);  // many steps per launch, no graph
     if (!h->graph && !h->no_graph) {
         if (capture(h, kGraphSteps, &h->graph) != WTMD_OK || capture(h, 1, &h->graph1) != WTMD_OK) {
             // this launch sequence cannot be captured here: replay eagerly
@@ -1230,6 +1232,19 @@ extern "C" int wtmd_fused_step(wtmd_t* h, int32_t enable, int32_t* active)
         h->fused_on = enable == 1;
     }
     if (active) *active = (h->fused_on && sys_step_eligible(h, nullptr)) ? 1 : 0;
+    return WTMD_OK;
+}
+
+extern "C" int wtmd_small_step(wtmd_t* h, int32_t enable, int32_t* active)
+{
+    if (!h) return WTMD_EINVAL;
+    if (enable == 0 || enable == 1) {
+        if (h->small_on != (enable == 1)) drop_graphs(h);
+        h->small_on = enable == 1;
+    } else if (enable != -1) {
+        FAIL(h, WTMD_EINVAL, "enable must be 0, 1 or -1 (query)");
+    }
+    if (active) *active = small_step_eligible(h) ? 1 : 0;
     return WTMD_OK;
 }
 

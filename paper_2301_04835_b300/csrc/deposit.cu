@@ -28,49 +28,18 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepPrm p, const double* __
     deposit_block<R>(p, xi, V, count, step, dep, ctr, h64, h32, status);
 }
 
-// factors f[n][off_i + k] = exp(-D^2/(2 sigma_i^2)) of new hill n on axis i
 __global__ void grid_factor_kernel(GridPrm g, const long long* __restrict__ dep, const dbl4* __restrict__ h64,
                                    int tot, double* __restrict__ fac)
 {
-    const long long nnew = dep[1];
-    const long long first = dep[0];
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nnew * tot;
-         q += (long long)gridDim.x * blockDim.x) {
-        const long long n = q / tot;
-        const int j = (int)(q % tot);
-        int i = 0;
-        while (i + 1 < g.d && j >= g.off[i + 1]) ++i;
-        const int k = j - g.off[i];
-        const dbl4 h = h64[first + n];
-        const double s = i == 0 ? h.x : (i == 1 ? h.y : h.z);
-        double D = g.lo[i] + (k + 0.5) * g.dx[i] - s;
-        if (g.per[i] > 0.0) D -= g.per[i] * rint(D / g.per[i]);
-        fac[q] = exp(-D * D * g.inv2s2[i]);
-    }
+    grid_factors(g, dep, h64, tot, fac, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                 (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void grid_add_kernel(GridPrm g, const long long* __restrict__ dep, const dbl4* __restrict__ h64, int tot,
                                 const double* __restrict__ fac, long long ncell, double* __restrict__ grid)
 {
-    const long long nnew = dep[1];
-    if (nnew == 0) return;
-    const long long first = dep[0];
-    for (long long cidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; cidx < ncell;
-         cidx += (long long)gridDim.x * blockDim.x) {
-        int k[3] = {0, 0, 0};
-        long long rem = cidx;
-        for (int i = g.d - 1; i >= 0; --i) {
-            k[i] = (int)(rem % g.bins[i]);
-            rem /= g.bins[i];
-        }
-        double v = grid[cidx];
-        for (long long n = 0; n < nnew; ++n) {
-            double e = h64[first + n].w;
-            for (int i = 0; i < g.d; ++i) e *= fac[n * tot + g.off[i] + k[i]];
-            v += e;
-        }
-        grid[cidx] = v;
-    }
+    grid_add(g, dep, h64, tot, fac, ncell, grid, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+             (long long)gridDim.x * blockDim.x);
 }
 
 // Rebuild the grid from all hills (after a hill-list load).

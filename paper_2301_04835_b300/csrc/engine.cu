@@ -12,6 +12,7 @@
 // used).  Positions are never wrapped; distances use the minimum image.
 #include "step_dev.cuh"
 #include "lj_dev.cuh"
+#include "analytic_dev.cuh"
 
 namespace wtmd {
 
@@ -44,43 +45,12 @@ __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __
     }
 }
 
-// Mueller-Brown (Mueller & Brown 1979): sum of four anisotropic Gaussians.
-__constant__ double kMB[6][4] = {
-    {-200.0, -100.0, -170.0, 15.0},  // A
-    {-1.0, -1.0, -6.5, 0.7},         // a
-    {0.0, 0.0, 11.0, 0.6},           // b
-    {-10.0, -10.0, -6.5, 0.7},       // c
-    {1.0, 0.0, -0.5, -1.0},          // x0
-    {0.0, 0.5, 1.5, 1.0},            // y0
-};
-
-// Three Gaussian wells in a harmonic confinement (3-D test landscape):
-// U = -sum_m A_m exp(-|r - c_m|^2 / (2 s_m^2)) + (k/2) |r|^2, F = -grad U.
-__constant__ double kW3[3][5] = {
-    // A, s, c_x, c_y, c_z
-    {8.0, 0.45, -1.0, 0.0, 0.0},
-    {6.0, 0.40, 1.0, 0.2, -0.3},
-    {7.0, 0.50, 0.1, 1.3, 0.6},
-};
-constexpr double kW3Conf = 1.5;
-
 template <typename R>
 __global__ void wells3_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __restrict__ f)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const R4<R> p = x[i];
-    R fx = -(R)kW3Conf * p.x, fy = -(R)kW3Conf * p.y, fz = -(R)kW3Conf * p.z;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const R dx = p.x - (R)kW3[m][2], dy = p.y - (R)kW3[m][3], dz = p.z - (R)kW3[m][4];
-        const R is2 = (R)(1.0 / (kW3[m][1] * kW3[m][1]));
-        const R e = (R)kW3[m][0] * exp(-(R)0.5 * (dx * dx + dy * dy + dz * dz) * is2);
-        fx -= e * dx * is2;
-        fy -= e * dy * is2;
-        fz -= e * dz * is2;
-    }
-    f[i] = mk4<R>(fx, fy, fz, R(0));
+    f[i] = wells3_force<R>(x[i]);
 }
 
 template <typename R>
@@ -88,17 +58,7 @@ __global__ void mb_kernel(long long N, const R4<R>* __restrict__ x, R4<R>* __res
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const R4<R> p = x[i];
-    R gx = 0, gy = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const R dx = p.x - (R)kMB[4][k], dy = p.y - (R)kMB[5][k];
-        const R a = (R)kMB[1][k], b = (R)kMB[2][k], c = (R)kMB[3][k];
-        const R e = (R)kMB[0][k] * exp(a * dx * dx + b * dx * dy + c * dy * dy);
-        gx += e * (R(2) * a * dx + b * dy);
-        gy += e * (b * dx + R(2) * c * dy);
-    }
-    f[i] = mk4<R>(-gx, -gy, R(0), R(0));
+    f[i] = mb_force<R>(x[i]);
 }
 
 template <typename R>

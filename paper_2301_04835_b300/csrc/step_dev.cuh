@@ -60,6 +60,23 @@ template <> __device__ __forceinline__ Normal3<float> noise3<float>(uint64_t see
     return n;
 }
 
+// B-A-O-A half of a BAOAB step of one particle (x, v, f in registers) with
+// the normal deviates g of its step.
+template <typename R>
+__device__ __forceinline__ void baoa_update(R4<R>& xi, R4<R>& vi, const R4<R>& fi, const R* g, R half, R inv_m, R c1,
+                                            R c2, int dims)
+{
+    auto baoa = [&](R& xx, R& vv, R ff, R gg) {
+        vv += half * ff * inv_m;
+        xx += half * vv;
+        vv = c1 * vv + c2 * gg;
+        xx += half * vv;
+    };
+    baoa(xi.x, vi.x, fi.x, g[0]);
+    baoa(xi.y, vi.y, fi.y, g[1]);
+    if (dims > 2) baoa(xi.z, vi.z, fi.z, g[2]);
+}
+
 // B-A-O-A half of a BAOAB step for atom i at step t (the closing B follows
 // the force evaluation).
 template <typename R>
@@ -70,15 +87,7 @@ __device__ __forceinline__ void baoab_first_atom(long long i, long long t, R4<R>
     const Normal3<R> n = noise3<R>(seed, t, (uint32_t)i);
     R4<R> xi = x[i], vi = v[i];
     const R4<R> fi = f[i];
-    auto baoa = [&](R& xx, R& vv, R ff, R g) {
-        vv += half * ff * inv_m;
-        xx += half * vv;
-        vv = c1 * vv + c2 * g;
-        xx += half * vv;
-    };
-    baoa(xi.x, vi.x, fi.x, n.g[0]);
-    baoa(xi.y, vi.y, fi.y, n.g[1]);
-    if (dims > 2) baoa(xi.z, vi.z, fi.z, n.g[2]);
+    baoa_update<R>(xi, vi, fi, n.g, half, inv_m, c1, c2, dims);
     x[i] = xi;
     v[i] = vi;
 }
@@ -104,6 +113,55 @@ struct GridPrm {
 };
 
 GridPrm grid_prm(const wtmd_t* h);  // deposit.cu
+
+// Grid update after a deposit (dep = {first new hill, count}): the factors
+// f[n][off_i + k] = exp(-D^2/(2 sigma_i^2)) of new hill n on axis i at cell
+// centre k (minimum image on a periodic axis), then every cell adds
+// w_n prod_i f[n][off_i + k_i] over the new hills in order.  Items q0,
+// q0 + qs, ... of each loop are this thread's.
+__device__ __forceinline__ void grid_factors(const GridPrm& g, const long long* __restrict__ dep,
+                                             const dbl4* __restrict__ h64, int tot, double* __restrict__ fac,
+                                             long long q0, long long qs)
+{
+    const long long nnew = dep[1];
+    const long long first = dep[0];
+    for (long long q = q0; q < nnew * tot; q += qs) {
+        const long long n = q / tot;
+        const int j = (int)(q % tot);
+        int i = 0;
+        while (i + 1 < g.d && j >= g.off[i + 1]) ++i;
+        const int k = j - g.off[i];
+        const dbl4 h = h64[first + n];
+        const double s = i == 0 ? h.x : (i == 1 ? h.y : h.z);
+        double D = g.lo[i] + (k + 0.5) * g.dx[i] - s;
+        if (g.per[i] > 0.0) D -= g.per[i] * rint(D / g.per[i]);
+        fac[q] = exp(-D * D * g.inv2s2[i]);
+    }
+}
+
+__device__ __forceinline__ void grid_add(const GridPrm& g, const long long* __restrict__ dep,
+                                         const dbl4* __restrict__ h64, int tot, const double* __restrict__ fac,
+                                         long long ncell, double* __restrict__ grid, long long c0, long long cs)
+{
+    const long long nnew = dep[1];
+    if (nnew == 0) return;
+    const long long first = dep[0];
+    for (long long cidx = c0; cidx < ncell; cidx += cs) {
+        int k[3] = {0, 0, 0};
+        long long rem = cidx;
+        for (int i = g.d - 1; i >= 0; --i) {
+            k[i] = (int)(rem % g.bins[i]);
+            rem /= g.bins[i];
+        }
+        double v = grid[cidx];
+        for (long long n = 0; n < nnew; ++n) {
+            double e = h64[first + n].w;
+            for (int i = 0; i < g.d; ++i) e *= fac[n * tot + g.off[i] + k[i]];
+            v += e;
+        }
+        grid[cidx] = v;
+    }
+}
 
 // The staged form of grid_point: every address first, then every load
 // (unrolled: one round of latency), then the sums in corner order.

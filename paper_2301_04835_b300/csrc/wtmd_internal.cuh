@@ -427,6 +427,7 @@ struct wtmd_t {
     wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
     wtmd::SysStepPlan ss;           // persistent single-system step
     bool fused_on = false;          // the caller allowed the persistent single-system step
+    bool small_on = true;           // small FP64 analytic systems run many steps per single-CTA launch
     long long wait_limit = 0;       // grid-barrier wait bound of the persistent kernels (0: the default)
     // autotune cache: key = (P bucket, d) -> tile
     std::vector<std::pair<long long, wtmd::Tuned>> tuned;
@@ -499,6 +500,8 @@ int folded_rg(const wtmd_t* h);                                  // Rg CV comput
 bool sys_step_eligible(const wtmd_t* h, std::string* why);       // the step can run as one persistent launch
 int sys_step_setup(wtmd_t* h);                                   // its plan (outside graph capture)
 int launch_sys_step(wtmd_t* h);                                  // one step as one cooperative launch
+bool small_step_eligible(const wtmd_t* h);                       // small_step.cu: the handle's steps run in one CTA
+int launch_small_steps(wtmd_t* h, int64_t n_steps);              // n steps, SMS_CHUNK per launch
 int launch_deposit(wtmd_t* h);                                   // deposit + grid + step++
 int launch_grid_rebuild(wtmd_t* h);
 int launch_fes(wtmd_t* h, double* out);
