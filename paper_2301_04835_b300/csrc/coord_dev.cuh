@@ -107,10 +107,11 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
     const int jq = q < mb ? (t.B ? t.B[b0 + q] : b0 + q) : -1;
     // scale times the share quantum 2^q (thread 0 rounds the CTA's share)
     const double sxq = tid == 0 ? t.scw * t.xq : 0.0;
-    // position in B of this lane's targets (for their self pairs)
+    // position in B of this lane's targets (for their self pairs), in the
+    // warps that sum the rows
     int pbs = -1;
-    if (warp < 2) {
-        const int a = warp == 0 ? a0 : a1;
+    if (warp == 2 || warp == 3) {
+        const int a = warp == 2 ? a0 : a1;
         if (a >= 0) pbs = t.inv_b ? t.inv_b[a] : (a < t.nw ? a : -1);
     }
     wait();
@@ -192,11 +193,12 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
     rowred[warp][lane] = make_float4(gx.x, gy.x, gz.x, sv.x);
     rowred[warp][lane + 32] = make_float4(gx.y, gy.y, gz.y, sv.y);
     sync();
-    // rows of the chunk (threads 0..63, warps in order) and this CTA's share
-    // of the CV value; the pair of a target with itself added s(0) in the
-    // chunk that holds it as a partner
-    if (warp < 2) {
-        const int r = tid, ia = tile * C2_A + r;
+    // rows of the chunk (warps 2 and 3 -- warp 0 was measured ~1.2 us slower
+    // here -- summing the warps' partials in order) and this CTA's share of
+    // the CV value; the pair of a target with itself added s(0) in the chunk
+    // that holds it as a partner
+    if (warp == 2 || warp == 3) {
+        const int r = tid - 64, ia = tile * C2_A + r;
         cf xs{0.f, 0.f};
         if (ia < t.nA) {
             float4 u = rowred[0][r];
@@ -214,7 +216,7 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
         // compensated FP32 (a dependent FP64 operation costs ~64 cycles on
         // this GPU); the share is rounded to the exact quantum in FP64 once
         for (int off = 16; off > 0; off >>= 1) xs = cf_add(xs, cf_shfl_xor(xs, off));
-        if (lane == 0) reinterpret_cast<float2*>(xred)[warp] = make_float2(xs.hi, xs.lo);
+        if (lane == 0) reinterpret_cast<float2*>(xred)[warp - 2] = make_float2(xs.hi, xs.lo);
     }
     sync();
     if (tid == 0) {
