@@ -315,25 +315,29 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
         __syncthreads();  // red[] free from the previous point
         if (tid % 32 == 0) red[tid / 32] = a;
         __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < HBC / 32; ++w) cf4_add(a, red[w]);
-            cta_sum[p] = a;
+        // the warps' sums in order, by warp 1 (warp 0, which issued the bulk
+        // copy, is kept out of the tail)
+        if (tid == 32) {
+            CF4 t = red[0];
+            for (int w = 1; w < HBC / 32; ++w) cf4_add(t, red[w]);
+            cta_sum[p] = t;
         }
     }
     cluster_sync();  // every rank's sums are in its shared memory
-    if (rank == 0 && tid < 32) {
-        // lane r reads rank r's sums (all ranks' loads in flight together),
-        // then a fixed xor tree over 16 lanes adds them (lanes >= CL hold 0;
-        // four dependent levels instead of a chain over the ranks)
+    if (rank == 0 && tid >= 32 && tid < 64) {
+        // lane r of warp 1 reads rank r's sums (all ranks' loads in flight
+        // together), then a fixed xor tree over 16 lanes adds them (lanes >= CL
+        // hold 0; four dependent levels instead of a chain over the ranks)
+        const unsigned r = (unsigned)(tid - 32);
         for (int p = 0; p < NP && p < P; ++p) {
             CF4 mine{};
-            if ((unsigned)tid < CL) {
+            if (r < CL) {
                 const float4* q = reinterpret_cast<const float4*>(&cta_sum[p]);
-                const float4 u = ld_dsmem_f4(q, (unsigned)tid), w = ld_dsmem_f4(q + 1, (unsigned)tid);
+                const float4 u = ld_dsmem_f4(q, r), w = ld_dsmem_f4(q + 1, r);
                 mine = CF4{{cf{u.x, u.y}, cf{u.z, u.w}, cf{w.x, w.y}, cf{w.z, w.w}}};
             }
             cf4_lane_sum<16>(mine);
-            if (tid == 0) emit_cf(p, mine, out);
+            if (r == 0) emit_cf(p, mine, out);
         }
     }
     cluster_sync();  // no rank leaves while rank 0 reads its shared memory
