@@ -1112,6 +1112,17 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
         w = aw[i];
         v = vel[i];
     }
+    // the deposit's step counter, hill count and layout centre change only
+    // in this kernel (the previous step's launch has completed): read them
+    // before the wait
+    __shared__ long long dpre[2];
+    __shared__ double dcpre[3];
+    const bool dep_block = blockIdx.x == gridDim.x - 1;
+    if (dep_block && threadIdx.x == 0) {
+        dpre[0] = *step;
+        dpre[1] = *count;
+        for (int k = 0; k < 3; ++k) dcpre[k] = ctr[k];
+    }
     pdl_wait();
     // after the wait: the engine's list build may still be reading the
     // counts until then (a joined edge lets this launch start early)
@@ -1121,7 +1132,7 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
         f = force[i];
         for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
     }
-    if (blockIdx.x == gridDim.x - 1) deposit_block<R>(dp, xi, V, count, step, dep, ctr, h64, h32, status);
+    if (dep_block) deposit_block_at<R>(dp, dpre, dcpre, xi, V, count, step, dep, ctr, h64, h32, status);
     if (!act) return;
     for (int c = 0; c < d && c < 3; ++c) {
         const R g = dV[w * 4 + c];

@@ -315,20 +315,24 @@ __device__ __forceinline__ void harmonic_point(int d, const double* k, const dou
 
 // Deposition by one CTA (all its threads call this): every `stride` steps
 // each walker appends a hill at its CVs with height w0 exp(-V inv_dT) in
-// FP64 (walker order), then the step counter advances.
+// FP64 (walker order), then the step counter advances.  deposit_block_at
+// takes the step counter and the hill count (pre[0], pre[1]) and the layout
+// centre (cpre) as thread 0 read them earlier (they change only here, so a
+// kernel can read them before its dependency wait); deposit_block reads
+// them itself.
 template <typename R>
-__device__ void deposit_block(const DepPrm& p, const double* __restrict__ xi, const R* __restrict__ V,
-                              long long* __restrict__ count, long long* __restrict__ step, long long* __restrict__ dep,
-                              double* __restrict__ ctr, dbl4* __restrict__ h64, float* __restrict__ h32,
-                              unsigned* status)
+__device__ void deposit_block_at(const DepPrm& p, const long long* pre, const double* cpre,
+                                 const double* __restrict__ xi, const R* __restrict__ V, long long* __restrict__ count,
+                                 long long* __restrict__ step, long long* __restrict__ dep, double* __restrict__ ctr,
+                                 dbl4* __restrict__ h64, float* __restrict__ h32, unsigned* status)
 {
     __shared__ long long base;
     __shared__ int doit;
     __shared__ double c[3];
     if (threadIdx.x == 0) {
-        const long long t = *step;
+        const long long t = pre[0];
         doit = p.stride > 0 && (t + 1) % p.stride == 0;
-        base = *count;
+        base = pre[1];
         if (doit && base + p.W > p.cap) {
             atomicOr(status, ST_CAPACITY);
             doit = 0;
@@ -337,9 +341,10 @@ __device__ void deposit_block(const DepPrm& p, const double* __restrict__ xi, co
         dep[1] = doit ? p.W : 0;
         // the centre of the scaled FP32 layout is fixed by the first hill
         // when no grid defined it
-        if (doit && isnan(ctr[0]))
-            for (int i = 0; i < 3; ++i) ctr[i] = i < p.d ? xi[i] : 0.0;
-        for (int i = 0; i < 3; ++i) c[i] = ctr[i];
+        double cc[3] = {cpre[0], cpre[1], cpre[2]};
+        if (doit && isnan(cc[0]))
+            for (int i = 0; i < 3; ++i) ctr[i] = cc[i] = i < p.d ? xi[i] : 0.0;
+        for (int i = 0; i < 3; ++i) c[i] = cc[i];
     }
     __syncthreads();
     if (doit) {
@@ -359,8 +364,24 @@ __device__ void deposit_block(const DepPrm& p, const double* __restrict__ xi, co
     __syncthreads();
     if (threadIdx.x == 0) {
         if (doit) *count = base + p.W;
-        *step = *step + 1;
+        *step = pre[0] + 1;
     }
+}
+
+template <typename R>
+__device__ void deposit_block(const DepPrm& p, const double* __restrict__ xi, const R* __restrict__ V,
+                              long long* __restrict__ count, long long* __restrict__ step, long long* __restrict__ dep,
+                              double* __restrict__ ctr, dbl4* __restrict__ h64, float* __restrict__ h32,
+                              unsigned* status)
+{
+    __shared__ long long pre[2];
+    __shared__ double cpre[3];
+    if (threadIdx.x == 0) {
+        pre[0] = *step;
+        pre[1] = *count;
+        for (int i = 0; i < 3; ++i) cpre[i] = ctr[i];
+    }
+    deposit_block_at<R>(p, pre, cpre, xi, V, count, step, dep, ctr, h64, h32, status);
 }
 
 }  // namespace wtmd
