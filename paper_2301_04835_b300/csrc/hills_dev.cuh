@@ -297,17 +297,18 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     const int hl = tid % TH;
     const int p = tile * TP + tid / TH;
 
-    // hills [k0, count): k0 is a multiple of 2 * CHUNK, so the range starts
-    // on a chunk boundary of the pair layout
+    // hills [k0, count) as pair records (k0 even); the split's pairs
+    // [q0, q1) are balanced to within one pair over the splits, and go
+    // through the ring in chunks of up to CHUNK pairs (any pair starts on a
+    // 32-byte boundary, so a chunk may start anywhere)
     const long long k0 = k0p ? *k0p : 0;
     const long long count = *cnt;
     const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
     hp += (size_t)(k0 >> 1) * 2;
-    const long long nch = (npairs + CHUNK - 1) / CHUNK;
-    // balanced: the splits' chunk counts differ by at most one
-    const long long c0 = nch * split / nsplit;
-    const long long c1 = nch * (split + 1) / nsplit;
-    const int nmine = c1 > c0 ? (int)(c1 - c0) : 0;
+    const long long q0 = npairs * split / nsplit;
+    const long long nq = npairs * (split + 1) / nsplit - q0;
+    const int nmine = (int)((nq + CHUNK - 1) / CHUNK);
+    auto chunk_pairs = [&](int k) { return (int)(nq - (long long)k * CHUNK < CHUNK ? nq - (long long)k * CHUNK : CHUNK); };
 
     __syncthreads();  // a previous task of this CTA is done with the ring
     if (tid == 0) {
@@ -320,8 +321,8 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < NST && s < nmine; ++s) {
-            mbar_arrive_expect_tx(&bar[s], CHUNK * 32);
-            bulk_g2s(ring[s], hp + (size_t)(c0 + s) * CHUNK * 2, CHUNK * 32, &bar[s]);
+            mbar_arrive_expect_tx(&bar[s], (uint32_t)chunk_pairs(s) * 32u);
+            bulk_g2s(ring[s], hp + (size_t)(q0 + (long long)s * CHUNK) * 2, (uint32_t)chunk_pairs(s) * 32u, &bar[s]);
         }
     }
     // The hill records and counts were written before the preceding kernel
@@ -353,9 +354,10 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
         const bool ok = mbar_wait_bounded(&bar[s], parity, status);
         if (!__syncthreads_and(ok)) break;
         const float4* sh = ring[s];
+        const int ncp = chunk_pairs(c);
         float2 v = make_float2(0.f, 0.f), g0 = v, g1 = v, g2 = v;
 #pragma unroll 4
-        for (int q = hl; q < CHUNK; q += TH) {
+        for (int q = hl; q < ncp; q += TH) {
             const float4 A = sh[2 * q];
             const float4 B = sh[2 * q + 1];
             float2 d0 = __fadd2_rn(X0, make_float2(A.x, A.y));
@@ -392,8 +394,9 @@ __device__ bool hills_f32_task(const float4* __restrict__ hp, const long long* _
         }
         __syncthreads();  // stage s consumed by every thread
         if (tid == 0 && c + NST < nmine) {
-            mbar_arrive_expect_tx(&bar[s], CHUNK * 32);
-            bulk_g2s(ring[s], hp + (size_t)(c0 + c + NST) * CHUNK * 2, CHUNK * 32, &bar[s]);
+            const int n = chunk_pairs(c + NST);
+            mbar_arrive_expect_tx(&bar[s], (uint32_t)n * 32u);
+            bulk_g2s(ring[s], hp + (size_t)(q0 + (long long)(c + NST) * CHUNK) * 2, (uint32_t)n * 32u, &bar[s]);
         }
     }
     if (c < nmine) {
