@@ -393,13 +393,11 @@ __global__ void __launch_bounds__(WK_T, 4) walkers_step_kernel(const __grid_cons
         }
         if (!grid_barrier(a.bar, G, a.status, a.wait_limit)) return;
 
-        // ---- P2b: V and dV/dxi per walker (one warp per point)
-        const int lane = tid % 32;
-        for (int p = blockIdx.x * (WK_T / 32) + tid / 32; p < a.W; p += G * (WK_T / 32)) {
-            CF4 acc{};
-            for (int s = lane; s < a.hsplit; s += 32) cf4_add(acc, load_cf4(a.hpart + (size_t)s * a.W + p));
-            cf4_lane_sum<32>(acc);
-            if (lane == 0) emit_cf(p, acc, a.hout);
+        // ---- P2b: V and dV/dxi per walker, one CTA per walker (thread
+        // strides over the splits, xor tree, warps in order)
+        for (int p = blockIdx.x; p < a.W; p += G) {
+            const CF4 acc = cta_split_sum(a.hpart, a.hsplit, a.W, p);
+            if (tid == 0) emit_cf(p, acc, a.hout);
         }
     } else {
         // ---- P2: harmonic windows or the grid, one thread per walker (the
