@@ -744,6 +744,22 @@ static int copy_cols(wtmd_t* h, void* dst, const void* src, bool src_f64, int co
     return WTMD_OK;
 }
 
+// bias_eval's outputs in one launch: V [W] and the [W][4] CV values (double)
+// and gradients (Real) as [W][d] Real, any of them optional
+template <typename R>
+__global__ static void bias_out_kernel(const R* __restrict__ V, const double* __restrict__ xi,
+                                       const R* __restrict__ dV, R* __restrict__ V_out, R* __restrict__ xi_out,
+                                       R* __restrict__ dV_out, int W, int d)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    if (V_out) V_out[w] = V[w];
+    for (int c = 0; c < d; ++c) {
+        if (xi_out) xi_out[w * d + c] = (R)xi[w * 4 + c];
+        if (dV_out) dV_out[w * d + c] = dV[w * 4 + c];
+    }
+}
+
 extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_out, void* xi_out, void* dV_out)
 {
     if (!h) return WTMD_EINVAL;
@@ -751,12 +767,26 @@ extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_
     if (rc) return rc;
     if (!pos) FAIL(h, WTMD_EINVAL, "null positions");
     if ((rc = launch_hills_partial_prealloc(h, h->W))) return rc;
-    if ((rc = launch_cvs(h, pos))) return rc;
+    // the J rows of a tile coordination CV go on a branch beside the hills
+    // sum (which needs only xi); the scatter joins it
+    h->jbranch = true;
+    rc = launch_cvs(h, pos);
+    h->jbranch = false;
+    if (rc) return rc;
     if ((rc = launch_bias_sum(h))) return rc;
+    if ((rc = join_jbranches(h))) return rc;
     if (force_inout && (rc = launch_scatter(h, force_inout, nullptr, false))) return rc;
-    if (V_out) WTMD_CUDA_TRY(h, cudaMemcpyAsync(V_out, h->V, realsz(h) * h->W, cudaMemcpyDeviceToDevice, h->stream));
-    if (xi_out && (rc = copy_cols(h, xi_out, h->xi, true, h->d))) return rc;
-    if (dV_out && (rc = copy_cols(h, dV_out, h->dV, false, h->d))) return rc;
+    if (V_out || xi_out || dV_out) {
+        const int nb = (h->W + 127) / 128;
+        if (h->prec == WTMD_F32)
+            bias_out_kernel<float><<<nb, 128, 0, h->stream>>>((const float*)h->V, h->xi, (const float*)h->dV,
+                                                             (float*)V_out, (float*)xi_out, (float*)dV_out, h->W, h->d);
+        else
+            bias_out_kernel<double><<<nb, 128, 0, h->stream>>>((const double*)h->V, h->xi, (const double*)h->dV,
+                                                              (double*)V_out, (double*)xi_out, (double*)dV_out, h->W,
+                                                              h->d);
+        WTMD_CUDA_TRY(h, cudaGetLastError());
+    }
     return WTMD_OK;
 }
 

@@ -1337,7 +1337,7 @@ template <typename R> static int launch_cvs_t(wtmd_t* h, const void* pos_, int c
                     // a graph branch of its own beside the hills sum, which
                     // needs only xi; the closing kick joins it.
                     cudaStream_t js = st;
-                    const bool branch = h->jz_pre && !h->prof;
+                    const bool branch = (h->jz_pre || h->jbranch) && !h->prof;
                     if (branch) {
                         WTMD_CUDA_TRY(h, cudaEventRecord(h->ev_jfork[c], st));
                         WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->jf_stream[c], h->ev_jfork[c], 0));
@@ -1417,13 +1417,20 @@ int launch_cvs(wtmd_t* h, const void* pos)
     return h->prec == WTMD_F32 ? launch_cvs_t<float>(h, pos, 0, h->ncv) : launch_cvs_t<double>(h, pos, 0, h->ncv);
 }
 
+int join_jbranches(wtmd_t* h)
+{
+    for (int c = 0; c < 3; ++c)
+        if (h->jf_pending >> c & 1) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_jjoin[c], 0));
+    h->jf_pending = 0;
+    return WTMD_OK;
+}
+
 int launch_scatter_deposit(wtmd_t* h)
 {
     const int nb = (int)((h->N + 255) / 256);
     // join the J branches of the FP32 coordination CVs
-    for (int c = 0; c < 3; ++c)
-        if (h->jf_pending >> c & 1) WTMD_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_jjoin[c], 0));
-    h->jf_pending = 0;
+    int rc = join_jbranches(h);
+    if (rc) return rc;
     const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
     const DepPrm dp = dep_prm(h);
     // programmatic dependent of the hills sum (or of the network's part)

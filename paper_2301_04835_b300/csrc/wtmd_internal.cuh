@@ -427,6 +427,7 @@ struct wtmd_t {
     wtmd::Surrogate* sur = nullptr; // MLP surrogate state (null until used)
     wtmd::SysStepPlan ss;           // persistent single-system step
     bool fused_on = false;          // the caller allowed the persistent single-system step
+    bool jbranch = false;           // bias_eval: the J rows of a tile CV on a branch beside the hills sum
     bool small_on = true;           // small FP64 analytic systems run many steps per single-CTA launch
     long long wait_limit = 0;       // grid-barrier wait bound of the persistent kernels (0: the default)
     // autotune cache: key = (P bucket, d) -> tile
@@ -459,7 +460,8 @@ inline void mark(wtmd_t* h, const char* name)
 namespace wtmd {
 
 // launchers (defined in the .cu files); all enqueue on h->stream
-int launch_cvs(wtmd_t* h, const void* pos);                     // xi, J for all CVs
+int launch_cvs(wtmd_t* h, const void* pos);                       // xi, J for all CVs
+int join_jbranches(wtmd_t* h);                                    // the main stream waits for the J-row branches
 int launch_cv(wtmd_t* h, const void* pos, int c);               // xi, J of CV c
 int launch_adjoint(wtmd_t* h, const void* grad_xi, void* grad_pos);  // J^T grad_xi
 int launch_grid_update(wtmd_t* h);                              // FP64 grid += this step's new hills
