@@ -751,6 +751,8 @@ __global__ static void bias_out_kernel(const R* __restrict__ V, const double* __
                                        const R* __restrict__ dV, R* __restrict__ V_out, R* __restrict__ xi_out,
                                        R* __restrict__ dV_out, int W, int d)
 {
+    pdl_wait();  // a programmatic dependent of the bias force kernel
+    pdl_trigger();
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= W) return;
     if (V_out) V_out[w] = V[w];
@@ -779,13 +781,13 @@ extern "C" int bias_eval(wtmd_t* h, const void* pos, void* force_inout, void* V_
     if (V_out || xi_out || dV_out) {
         const int nb = (h->W + 127) / 128;
         if (h->prec == WTMD_F32)
-            bias_out_kernel<float><<<nb, 128, 0, h->stream>>>((const float*)h->V, h->xi, (const float*)h->dV,
-                                                             (float*)V_out, (float*)xi_out, (float*)dV_out, h->W, h->d);
+            WTMD_CUDA_TRY(h, launch_pdl(bias_out_kernel<float>, dim3(nb), dim3(128), 0, h->stream, (const float*)h->V,
+                                        (const double*)h->xi, (const float*)h->dV, (float*)V_out, (float*)xi_out,
+                                        (float*)dV_out, h->W, h->d));
         else
-            bias_out_kernel<double><<<nb, 128, 0, h->stream>>>((const double*)h->V, h->xi, (const double*)h->dV,
-                                                              (double*)V_out, (double*)xi_out, (double*)dV_out, h->W,
-                                                              h->d);
-        WTMD_CUDA_TRY(h, cudaGetLastError());
+            WTMD_CUDA_TRY(h, launch_pdl(bias_out_kernel<double>, dim3(nb), dim3(128), 0, h->stream,
+                                        (const double*)h->V, (const double*)h->xi, (const double*)h->dV,
+                                        (double*)V_out, (double*)xi_out, (double*)dV_out, h->W, h->d));
     }
     return WTMD_OK;
 }

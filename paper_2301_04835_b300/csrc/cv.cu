@@ -1152,6 +1152,8 @@ __global__ void scatter_kernel(long long N, int d, const int* __restrict__ aw, c
                                const R4<R>* __restrict__ J, R4<R>* __restrict__ force, R4<R>* __restrict__ vel,
                                R half_dt_over_m, int dims)
 {
+    pdl_wait();  // a programmatic dependent of the bias sum: everything it reads comes after the wait
+    pdl_trigger();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) scatter_atom<R>(i, d, aw, dV, J, N, force, vel, half_dt_over_m, dims);
 }
@@ -1456,15 +1458,14 @@ int launch_scatter(wtmd_t* h, void* force, const void* vel, bool kick)
     const int nb = (int)((h->N + 255) / 256);
     const double hdm = 0.5 * h->cfg.dt / h->cfg.mass;
     if (h->prec == WTMD_F32)
-        scatter_kernel<float><<<nb, 256, 0, h->stream>>>(h->N, h->d, h->atom_walker, (const float*)h->dV,
-                                                         (const float4*)h->J, (float4*)force,
-                                                         kick ? (float4*)vel : nullptr, (float)hdm, h->dims);
+        WTMD_CUDA_TRY(h, launch_pdl(scatter_kernel<float>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N, h->d,
+                                    (const int*)h->atom_walker, (const float*)h->dV, (const float4*)h->J,
+                                    (float4*)force, kick ? (float4*)vel : (float4*)nullptr, (float)hdm, h->dims));
     else
-        scatter_kernel<double><<<nb, 256, 0, h->stream>>>(h->N, h->d, h->atom_walker, (const double*)h->dV,
-                                                          (const dbl4*)h->J, (dbl4*)force,
-                                                          kick ? (dbl4*)vel : nullptr, hdm, h->dims);
+        WTMD_CUDA_TRY(h, launch_pdl(scatter_kernel<double>, dim3(nb), dim3(256), 0, h->stream, (long long)h->N, h->d,
+                                    (const int*)h->atom_walker, (const double*)h->dV, (const dbl4*)h->J,
+                                    (dbl4*)force, kick ? (dbl4*)vel : (dbl4*)nullptr, hdm, h->dims));
     mark(h, "scatter_kick");
-    WTMD_CUDA_TRY(h, cudaGetLastError());
     return WTMD_OK;
 }
 
