@@ -243,9 +243,12 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
 // the hill range, and each copies its share of the pair records into shared
 // memory with one bulk (TMA) copy issued before the dependency wait, so the
 // records are on chip when the points are known.  The split sums meet in
-// distributed shared memory: rank 0 adds the ranks' compensated sums by a
-// fixed xor tree over 16 lanes (lane r holds rank r) and writes V and dV.  No global partials, fences or tickets;
-// deterministic.  For short hill lists (a walker's point in a step), where
+// rank 0's shared memory: each rank pushes its compensated sums there with
+// asynchronous stores counted on a barrier of rank 0 and leaves; rank 0 adds
+// them by a fixed xor tree over 16 lanes (lane r holds rank r) and writes V
+// and dV.  One cluster barrier, arrived at on entry and passed before the
+// first push (rank 0's barrier is initialised by then); no global partials,
+// fences or tickets; deterministic.  For short hill lists (a walker's point in a step), where
 // the reduction, not the streaming, is the cost.  Records beyond the shared
 // share (lists longer than the capacity the launch was sized for) are read
 // from global memory.
@@ -260,28 +263,35 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
                                                                 HillOut<float> out, int smem_pairs)
 {
     extern __shared__ __align__(128) float4 crec[];  // [smem_pairs][2]
-    __shared__ __align__(8) uint64_t cbar;
+    __shared__ __align__(8) uint64_t cbar, rbar;
+    __shared__ __align__(16) CF4 rsum[16][NP];  // rank 0: rank r's sums, pushed by rank r
     const int tid = threadIdx.x;
     const long long k0 = k0p ? *k0p : 0;
     const long long count = *cnt;
     const long long npairs = count > k0 ? ((count + 1) >> 1) - (k0 >> 1) : 0;
     hp += (size_t)(k0 >> 1) * 2;
     const unsigned rank = cluster_ctarank(), CL = cluster_nctarank();
+    const int Pn = P < NP ? P : NP;
     const long long per = (npairs + CL - 1) / CL;
     const long long q0 = (long long)rank * per;
     const long long nq = q0 < npairs ? (per < npairs - q0 ? per : npairs - q0) : 0;
     const int npf = (int)(nq < smem_pairs ? nq : smem_pairs);
     if (tid == 0) {
         mbar_init(&cbar, 1);
+        mbar_init(&rbar, 1);
         fence_mbar_init();
+        // rank 0 expects 32 bytes per point from every other rank
+        if (rank == 0) mbar_arrive_expect_tx(&rbar, (CL - 1) * (unsigned)Pn * 32u);
         if (npf > 0) {
             mbar_arrive_expect_tx(&cbar, (uint32_t)npf * 32u);
             bulk_g2s(crec, hp + 2 * q0, (uint32_t)npf * 32u, &cbar);
         }
     }
-    __syncthreads();  // the barrier is initialised before anyone waits on it
+    __syncthreads();  // the barriers are initialised before anyone waits on them
+    cluster_arrive();
     pdl_wait();
     pdl_trigger();
+    cluster_wait();  // every rank's barriers are initialised (long since, by now)
     float2 X[NP][3];
     points_scaled<D, NP, PT>(xi, xs, P, ctr, prm, X);
     float2 v[NP], g0[NP], g1[NP], g2[NP];
@@ -302,10 +312,9 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
         }
     }
     __shared__ CF4 red[HBC / 32];
-    __shared__ __align__(16) CF4 cta_sum[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        if (p >= P) break;
+        if (p >= Pn) break;
         CF4 a{};
         a.v[0] = cf_add(cf_add(a.v[0], v[p].x), v[p].y);
         a.v[1] = cf_add(cf_add(a.v[1], g0[p].x), g0[p].y);
@@ -316,32 +325,43 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
         if (tid % 32 == 0) red[tid / 32] = a;
         __syncthreads();
         // the warps' sums in order, by warp 1 (warp 0, which issued the bulk
-        // copy, is kept out of the tail)
+        // copy, is kept out of the tail), pushed to rank 0 (every rank pushes
+        // every point, whatever its copy did, so rank 0's count completes);
+        // rank 0 keeps its own
         if (tid == 32) {
             CF4 t = red[0];
             for (int w = 1; w < HBC / 32; ++w) cf4_add(t, red[w]);
-            cta_sum[p] = t;
-        }
-    }
-    cluster_sync();  // every rank's sums are in its shared memory
-    if (rank == 0 && tid >= 32 && tid < 64) {
-        // lane r of warp 1 reads rank r's sums (all ranks' loads in flight
-        // together), then a fixed xor tree over 16 lanes adds them (lanes >= CL
-        // hold 0; four dependent levels instead of a chain over the ranks)
-        const unsigned r = (unsigned)(tid - 32);
-        for (int p = 0; p < NP && p < P; ++p) {
-            CF4 mine{};
-            if (r < CL) {
-                const float4* q = reinterpret_cast<const float4*>(&cta_sum[p]);
-                const float4 u = ld_dsmem_f4(q, r), w = ld_dsmem_f4(q + 1, r);
-                mine = CF4{{cf{u.x, u.y}, cf{u.z, u.w}, cf{w.x, w.y}, cf{w.z, w.w}}};
+            if (rank == 0) {
+                rsum[0][p] = t;
+            } else {
+                float4* q = reinterpret_cast<float4*>(&rsum[rank][p]);
+                st_async_f4(q, 0, make_float4(t.v[0].hi, t.v[0].lo, t.v[1].hi, t.v[1].lo), &rbar);
+                st_async_f4(q + 1, 0, make_float4(t.v[2].hi, t.v[2].lo, t.v[3].hi, t.v[3].lo), &rbar);
             }
-            cf4_lane_sum<16>(mine);
-            if (r == 0) emit_cf(p, mine, out);
         }
     }
-    cluster_sync();  // no rank leaves while rank 0 reads its shared memory
     if (tid == 0) mbar_inval(&cbar);
+    if (rank != 0 || tid < 32 || tid >= 64) return;
+    // rank 0, warp 1: wait for the other ranks' pushes (longer than any
+    // rank's own bounded copy wait, after which that rank still pushes;
+    // rank 0's own sums were written by lane 0 of this warp), then lane r
+    // takes rank r's sums and a fixed xor tree over 16 lanes adds them (lanes
+    // >= CL hold 0; four dependent levels instead of a chain over the ranks)
+    bool got = mbar_try_wait_cluster(&rbar, 0);
+    if (!got) {
+        const long long t0 = clock64();
+        while (!(got = mbar_try_wait_cluster(&rbar, 0)) && clock64() - t0 <= (1ll << 33)) {
+        }
+        if (!got && tid == 32) atomicOr(out.status, ST_TIMEOUT);
+    }
+    if (!got) return;
+    const unsigned r = (unsigned)(tid - 32);
+    for (int p = 0; p < Pn; ++p) {
+        CF4 mine{};
+        if (r < CL) mine = rsum[r][p];
+        cf4_lane_sum<16>(mine);
+        if (r == 0) emit_cf(p, mine, out);
+    }
 }
 
 template <int TH, bool PER>

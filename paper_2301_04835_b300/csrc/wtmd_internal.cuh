@@ -137,6 +137,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// The same test with acquire ordering at cluster scope: for a barrier whose
+// transactions are stores of other CTAs of the cluster (st_async_f4).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: gives up after ~2^31 SM cycles (about a second), records
 // ST_TIMEOUT and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status)
@@ -171,6 +185,31 @@ __device__ __forceinline__ unsigned cluster_nctarank()
 __device__ __forceinline__ void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The two halves of cluster_sync, for a barrier whose wait comes long after
+// the arrival (every thread of the CTA calls both, in this order).
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Asynchronous 16-byte store into the shared memory of CTA `rank` of the
+// cluster, at the address of the local variable `local` (16-byte aligned);
+// its bytes complete transactions of the mbarrier at the address of `bar`
+// in that CTA, which the receiver waits on (mbar_try_wait_cluster).  The
+// value travels from registers: the storing CTA may exit before it lands.
+__device__ __forceinline__ void st_async_f4(void* local, unsigned rank, float4 v, uint64_t* bar)
+{
+    uint32_t ra, rb;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rb) : "r"(smem_addr(bar)), "r"(rank));
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     ra),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rb)
+                 : "memory");
 }
 __device__ __forceinline__ float4 ld_dsmem_f4(const void* local, unsigned rank)
 {
