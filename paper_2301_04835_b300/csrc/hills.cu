@@ -252,10 +252,17 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
 // the reduction, not the streaming, is the cost.  Records beyond the shared
 // share (lists longer than the capacity the launch was sized for) are read
 // from global memory.
-constexpr int HBC = 256;  // threads per CTA of the cluster kernel
+// Threads per CTA of the cluster kernel and pairs a thread takes per
+// batch (its shared-memory loads issued together): for one or two points a
+// CTA's share is a few thousand pairs, and 16 warps with four independent
+// pairs in flight each hide the shared-memory and MUFU latencies that 8
+// warps with one pair left exposed; more points keep 8 warps and one pair
+// (their per-point registers).
+__host__ __device__ constexpr int cluster_threads(int NP) { return NP <= 2 ? 512 : 256; }
+__host__ __device__ constexpr int cluster_batch(int NP) { return NP <= 2 ? 4 : 1; }
 
 template <int D, bool PER, int NP, typename PT>
-__global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __restrict__ hp,
+__global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(const float4* __restrict__ hp,
                                                                 const long long* __restrict__ k0p,
                                                                 const long long* __restrict__ cnt,
                                                                 const PT* __restrict__ xi, int xs, int P,
@@ -297,9 +304,20 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
     float2 v[NP], g0[NP], g1[NP], g2[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
+    constexpr int T = cluster_threads(NP), SB = cluster_batch(NP), NW = T / 32;
     bool landed = npf == 0 || mbar_wait_bounded(&cbar, 0, out.status);
     if (landed) {
-        for (long long k = tid; k < nq; k += HBC) {
+        long long k = tid;
+        for (; k + (SB - 1) * T < npf; k += SB * T) {
+            float4 A[SB], B[SB];
+#pragma unroll
+            for (int j = 0; j < SB; ++j) {
+                A[j] = crec[2 * (k + j * T)];
+                B[j] = crec[2 * (k + j * T) + 1];
+            }
+            pairs_eval<D, PER, NP, SB>(A, B, X, P, prm, v, g0, g1, g2);
+        }
+        for (; k < nq; k += T) {  // the rest of the shared share, then records beyond it
             float4 A[1], B[1];
             if (k < npf) {
                 A[0] = crec[2 * k];
@@ -311,7 +329,7 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
             pairs_eval<D, PER, NP, 1>(A, B, X, P, prm, v, g0, g1, g2);
         }
     }
-    __shared__ CF4 red[HBC / 32];
+    __shared__ CF4 red[NW];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         if (p >= Pn) break;
@@ -324,13 +342,15 @@ __global__ void __launch_bounds__(HBC) hills_f32_cluster_kernel(const float4* __
         __syncthreads();  // red[] free from the previous point
         if (tid % 32 == 0) red[tid / 32] = a;
         __syncthreads();
-        // the warps' sums in order, by warp 1 (warp 0, which issued the bulk
-        // copy, is kept out of the tail), pushed to rank 0 (every rank pushes
-        // every point, whatever its copy did, so rank 0's count completes);
-        // rank 0 keeps its own
-        if (tid == 32) {
-            CF4 t = red[0];
-            for (int w = 1; w < HBC / 32; ++w) cf4_add(t, red[w]);
+        // the warps' sums by a fixed xor tree on warp 1 (warp 0, which issued
+        // the bulk copy, is kept out of the tail; lane w holds warp w), pushed
+        // to rank 0 by its lane 0 (every rank pushes every point, whatever its
+        // copy did, so rank 0's count completes); rank 0 keeps its own
+        if (tid >= 32 && tid < 64) {
+            CF4 t{};
+            if (tid - 32 < NW) t = red[tid - 32];
+            cf4_lane_sum<NW>(t);
+            if (tid != 32) continue;
             if (rank == 0) {
                 rsum[0][p] = t;
             } else {
@@ -550,7 +570,7 @@ static cudaError_t launch_f32_cluster(int CL, long long cap_pairs, cudaStream_t 
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(1, CL);
-    cfg.blockDim = dim3(HBC);
+    cfg.blockDim = dim3(cluster_threads(NP));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[3];
@@ -747,7 +767,7 @@ static bool cluster16_probe()
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(1, 16);
-    cfg.blockDim = dim3(HBC);
+    cfg.blockDim = dim3(cluster_threads(1));
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 1;
