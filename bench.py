@@ -576,6 +576,39 @@ def equilibrate(wt, torch, x, v, L, seed):
     return out
 
 
+def graph_floor(torch, dev, flush, stream, reps=30):
+    """Context for the step's event interval: CUDA graphs of one and of
+    eight dependent trivial kernels (a 4 KB tensor add), timed exactly like
+    a step (L2 flushed, device-side slack, events around the replay).  Their
+    medians are the launch, dependency and drain cost a graph of that many
+    kernels pays whatever the kernels do."""
+    y = torch.zeros(1024, device=dev)
+    out = {}
+    for name, n in (("one_kernel", 1), ("eight_serial_kernels", 8)):
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            y.add_(1.0)
+        stream.wait_stream(side)
+        with torch.cuda.graph(g):
+            for _ in range(n):
+                y.add_(1.0)
+        g.replay()
+        us = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            torch.cuda._sleep(SLACK_CYCLES)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            us.append(a.elapsed_time(b) * 1e3)
+        out[name] = float(np.median(us))
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -705,7 +738,8 @@ def run_ours(args, rank, world):
     mbb = None if args.no_configs else mueller_brown_bench(wt, torch)
     adj = None if args.no_configs else chain_adjoint_bench(wt, torch, flush)
     step_stats = {"median_us": float(np.median(step_us)), "min_us": float(step_us.min()),
-                  "max_us": float(step_us.max()), "first_us": float(step_us[0])}
+                  "max_us": float(step_us.max()), "first_us": float(step_us[0]),
+                  "graph_floor_us": graph_floor(torch, dev, flush, stream)}
     return dict(arms=arms, step_stats=step_stats, mueller_brown=mbb, chain_adjoint=adj, hills_plan=hills_plan, walkers=walkers, surrogate=sur, grid_bias=gridb, dev_ms=dev_ms_max, wall=wall, clocks=clk.summary(), steady_ms=steady_ms, prof=prof,
                 kernels_per_step=kernels_per_step, n_hills=n_hills, e2e_ms=e2e_ms, e2e_bytes=bytes_step,
                 micro=micro)

@@ -147,6 +147,11 @@ __global__ void __launch_bounds__(NL_T) lj_list_kernel(long long N, const R4<R>*
                                                        R eps24, R4<R>* __restrict__ f)
 {
     const long long u = (long long)blockIdx.x * NL_T + threadIdx.x;
+    // what follows may launch now: every kernel launched after this one
+    // waits for it before reading the forces, and BAOAB, whose positions and
+    // velocities they read before that wait, has completed (the binning
+    // waited for it before the list build and this launch could start)
+    pdl_trigger();
     // the flag is final when this launch starts (the list build before it
     // starts only after the binning's wait for BAOAB) and is cleared after
     // the step; without a rebuild the lists are those of an
