@@ -166,10 +166,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
-// Thread-block clusters: the CTA's rank and the cluster's size, a barrier
-// of all threads of the cluster (release / acquire: shared-memory writes
-// before it are visible to the other CTAs after it), and a 16-byte load from
-// the shared memory of CTA `rank` at the address of a local variable.
+// Thread-block clusters: the CTA's rank and the cluster's size, a split
+// barrier of all threads of the cluster, and an asynchronous store into the
+// shared memory of another CTA of the cluster.
 __device__ __forceinline__ unsigned cluster_ctarank()
 {
     unsigned r;
@@ -182,15 +181,14 @@ __device__ __forceinline__ unsigned cluster_nctarank()
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
     return r;
 }
-__device__ __forceinline__ void cluster_sync()
+// The two halves of a cluster barrier, for one whose wait comes long after
+// the arrival (every thread of the CTA calls both, in this order).  The
+// arrival is relaxed: it orders nothing but the mbarrier initialisations
+// that fence_mbar_init released before it, so no thread pays a memory
+// barrier for it.
+__device__ __forceinline__ void cluster_arrive_relaxed()
 {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// The two halves of cluster_sync, for a barrier whose wait comes long after
-// the arrival (every thread of the CTA calls both, in this order).
-__device__ __forceinline__ void cluster_arrive()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait()
 {
@@ -210,17 +208,6 @@ __device__ __forceinline__ void st_async_f4(void* local, unsigned rank, float4 v
                      ra),
                  "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rb)
                  : "memory");
-}
-__device__ __forceinline__ float4 ld_dsmem_f4(const void* local, unsigned rank)
-{
-    uint32_t ra;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(ra)
-                 : "memory");
-    return v;
 }
 
 // Compensated FP32 sum (hi + lo, Knuth's TwoSum): about 48 significant bits
