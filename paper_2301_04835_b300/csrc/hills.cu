@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
         }
     }
     __syncthreads();  // the barriers are initialised before anyone waits on them
-    cluster_arrive();
+    cluster_arrive_relaxed();
     pdl_wait();
     pdl_trigger();
     cluster_wait();  // every rank's barriers are initialised (long since, by now)
