@@ -261,6 +261,24 @@ __global__ void __launch_bounds__(HB) hills_f32_small_kernel(const float4* __res
 __host__ __device__ constexpr int cluster_threads(int NP) { return NP <= 2 ? 512 : 256; }
 __host__ __device__ constexpr int cluster_batch(int NP) { return NP <= 2 ? 4 : 1; }
 
+// Rank 0's last step (warp 1): lane r takes rank r's sums and a fixed xor
+// tree over 16 lanes adds them (lanes >= CL hold 0; four dependent levels
+// instead of a chain over the ranks); lane 0 writes V and dV.  Not inlined:
+// the kernel also runs it once on zeros with no outputs before its
+// dependency wait, so that these instructions are in the SM's instruction
+// cache when the real sums arrive (run cold, the tree and the writes took
+// ~1-2 us, nearly all of it instruction fetch).
+template <int NP>
+__device__ __noinline__ void cluster_tail(const CF4 (*rsum)[NP], int Pn, unsigned CL, unsigned r, HillOut<float> out)
+{
+    for (int p = 0; p < Pn; ++p) {
+        CF4 mine{};
+        if (r < CL) mine = rsum[r][p];
+        cf4_lane_sum<16>(mine);
+        if (r == 0) emit_cf(p, mine, out);
+    }
+}
+
 template <int D, bool PER, int NP, typename PT>
 __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(const float4* __restrict__ hp,
                                                                 const long long* __restrict__ k0p,
@@ -296,6 +314,14 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
     }
     __syncthreads();  // the barriers are initialised before anyone waits on them
     cluster_arrive_relaxed();
+    if (rank == 0 && tid >= 32 && tid < 64) {
+        // the tail once on zeros (no ranks read, no outputs): instruction
+        // cache warm-up while the CV launch runs
+        HillOut<float> none = out;
+        none.V = nullptr;
+        none.dV = nullptr;
+        cluster_tail<NP>(rsum, 1, 0u, (unsigned)(tid - 32), none);
+    }
     pdl_wait();
     pdl_trigger();
     cluster_wait();  // every rank's barriers are initialised (long since, by now)
@@ -375,13 +401,7 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
         if (!got && tid == 32) atomicOr(out.status, ST_TIMEOUT);
     }
     if (!got) return;
-    const unsigned r = (unsigned)(tid - 32);
-    for (int p = 0; p < Pn; ++p) {
-        CF4 mine{};
-        if (r < CL) mine = rsum[r][p];
-        cf4_lane_sum<16>(mine);
-        if (r == 0) emit_cf(p, mine, out);
-    }
+    cluster_tail<NP>(rsum, Pn, CL, (unsigned)(tid - 32), out);
 }
 
 template <int TH, bool PER>
