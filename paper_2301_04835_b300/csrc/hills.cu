@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
     extern __shared__ __align__(128) float4 crec[];  // [smem_pairs][2]
     __shared__ __align__(8) uint64_t cbar, rbar;
     __shared__ __align__(16) CF4 rsum[16][NP];  // rank 0: rank r's sums, pushed by rank r
+    __shared__ __align__(16) float4 dryrec[10];  // five zero pair records for the dry pass
     const int tid = threadIdx.x;
     const long long k0 = k0p ? *k0p : 0;
     const long long count = *cnt;
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
             bulk_g2s(crec, hp + 2 * q0, (uint32_t)npf * 32u, &cbar);
         }
     }
+    if (tid < 10) dryrec[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();  // the barriers are initialised before anyone waits on them
     cluster_arrive_relaxed();
     if (rank == 0 && tid >= 32 && tid < 64) {
@@ -322,67 +324,84 @@ __global__ void __launch_bounds__(cluster_threads(NP)) hills_f32_cluster_kernel(
         none.dV = nullptr;
         cluster_tail<NP>(rsum, 1, 0u, (unsigned)(tid - 32), none);
     }
-    pdl_wait();
-    pdl_trigger();
-    cluster_wait();  // every rank's barriers are initialised (long since, by now)
-    float2 X[NP][3];
-    points_scaled<D, NP, PT>(xi, xs, P, ctr, prm, X);
-    float2 v[NP], g0[NP], g1[NP], g2[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
     constexpr int T = cluster_threads(NP), SB = cluster_batch(NP), NW = T / 32;
-    bool landed = npf == 0 || mbar_wait_bounded(&cbar, 0, out.status);
-    if (landed) {
-        long long k = tid;
-        for (; k + (SB - 1) * T < npf; k += SB * T) {
-            float4 A[SB], B[SB];
-#pragma unroll
-            for (int j = 0; j < SB; ++j) {
-                A[j] = crec[2 * (k + j * T)];
-                B[j] = crec[2 * (k + j * T) + 1];
-            }
-            pairs_eval<D, PER, NP, SB>(A, B, X, P, prm, v, g0, g1, g2);
-        }
-        for (; k < nq; k += T) {  // the rest of the shared share, then records beyond it
-            float4 A[1], B[1];
-            if (k < npf) {
-                A[0] = crec[2 * k];
-                B[0] = crec[2 * k + 1];
-            } else {
-                A[0] = __ldg(hp + 2 * (q0 + k));
-                B[0] = __ldg(hp + 2 * (q0 + k) + 1);
-            }
-            pairs_eval<D, PER, NP, 1>(A, B, X, P, prm, v, g0, g1, g2);
-        }
-    }
     __shared__ CF4 red[NW];
+    // Two passes over one copy of the code: a dry pass before the dependency
+    // wait (zero points, five zero pair records taken by every thread, sums
+    // reduced but not pushed) brings the instructions into the SM's caches
+    // while the CV launch runs; the real pass follows the wait.
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool dry = pass == 0;
+        float2 X[NP][3];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        if (p >= Pn) break;
-        CF4 a{};
-        a.v[0] = cf_add(cf_add(a.v[0], v[p].x), v[p].y);
-        a.v[1] = cf_add(cf_add(a.v[1], g0[p].x), g0[p].y);
-        a.v[2] = cf_add(cf_add(a.v[2], g1[p].x), g1[p].y);
-        a.v[3] = cf_add(cf_add(a.v[3], g2[p].x), g2[p].y);
-        cf4_lane_sum<32>(a);
-        __syncthreads();  // red[] free from the previous point
-        if (tid % 32 == 0) red[tid / 32] = a;
-        __syncthreads();
-        // the warps' sums by a fixed xor tree on warp 1 (warp 0, which issued
-        // the bulk copy, is kept out of the tail; lane w holds warp w), pushed
-        // to rank 0 by its lane 0 (every rank pushes every point, whatever its
-        // copy did, so rank 0's count completes); rank 0 keeps its own
-        if (tid >= 32 && tid < 64) {
-            CF4 t{};
-            if (tid - 32 < NW) t = red[tid - 32];
-            cf4_lane_sum<NW>(t);
-            if (tid != 32) continue;
-            if (rank == 0) {
-                rsum[0][p] = t;
-            } else {
-                float4* q = reinterpret_cast<float4*>(&rsum[rank][p]);
-                st_async_f4(q, 0, make_float4(t.v[0].hi, t.v[0].lo, t.v[1].hi, t.v[1].lo), &rbar);
-                st_async_f4(q + 1, 0, make_float4(t.v[2].hi, t.v[2].lo, t.v[3].hi, t.v[3].lo), &rbar);
+        for (int p = 0; p < NP; ++p) X[p][0] = X[p][1] = X[p][2] = make_float2(0.f, 0.f);
+        if (!dry) {
+            pdl_wait();
+            pdl_trigger();
+            cluster_wait();  // every rank's barriers are initialised (long since, by now)
+            points_scaled<D, NP, PT>(xi, xs, P, ctr, prm, X);
+        }
+        float2 v[NP], g0[NP], g1[NP], g2[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) v[p] = g0[p] = g1[p] = g2[p] = make_float2(0.f, 0.f);
+        const float4* src = dry ? dryrec : crec;
+        const long long nqp = dry ? 5 : nq;
+        const long long npfp = dry ? 5 : npf;
+        const int st = dry ? 1 : T;
+        const bool landed = dry || npf == 0 || mbar_wait_bounded(&cbar, 0, out.status);
+        if (landed) {
+            long long k = dry ? 0 : tid;
+            for (; k + (SB - 1) * st < npfp; k += SB * st) {
+                float4 A[SB], B[SB];
+#pragma unroll
+                for (int j = 0; j < SB; ++j) {
+                    A[j] = src[2 * (k + j * st)];
+                    B[j] = src[2 * (k + j * st) + 1];
+                }
+                pairs_eval<D, PER, NP, SB>(A, B, X, P, prm, v, g0, g1, g2);
+            }
+            for (; k < nqp; k += st) {  // the rest of the shared share, then records beyond it
+                float4 A[1], B[1];
+                if (k < npfp) {
+                    A[0] = src[2 * k];
+                    B[0] = src[2 * k + 1];
+                } else {
+                    A[0] = __ldg(hp + 2 * (q0 + k));
+                    B[0] = __ldg(hp + 2 * (q0 + k) + 1);
+                }
+                pairs_eval<D, PER, NP, 1>(A, B, X, P, prm, v, g0, g1, g2);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (p >= Pn) break;
+            CF4 a{};
+            a.v[0] = cf_add(cf_add(a.v[0], v[p].x), v[p].y);
+            a.v[1] = cf_add(cf_add(a.v[1], g0[p].x), g0[p].y);
+            a.v[2] = cf_add(cf_add(a.v[2], g1[p].x), g1[p].y);
+            a.v[3] = cf_add(cf_add(a.v[3], g2[p].x), g2[p].y);
+            cf4_lane_sum<32>(a);
+            __syncthreads();  // red[] free from the previous point (or pass)
+            if (tid % 32 == 0) red[tid / 32] = a;
+            __syncthreads();
+            // the warps' sums by a fixed xor tree on warp 1 (warp 0, which
+            // issued the bulk copy, is kept out of the tail; lane w holds warp
+            // w), pushed to rank 0 by its lane 0 (every rank pushes every
+            // point, whatever its copy did, so rank 0's count completes);
+            // rank 0 keeps its own
+            if (tid >= 32 && tid < 64) {
+                CF4 t{};
+                if (tid - 32 < NW) t = red[tid - 32];
+                cf4_lane_sum<NW>(t);
+                if (tid != 32 || dry) continue;
+                if (rank == 0) {
+                    rsum[0][p] = t;
+                } else {
+                    float4* q = reinterpret_cast<float4*>(&rsum[rank][p]);
+                    st_async_f4(q, 0, make_float4(t.v[0].hi, t.v[0].lo, t.v[1].hi, t.v[1].lo), &rbar);
+                    st_async_f4(q + 1, 0, make_float4(t.v[2].hi, t.v[2].lo, t.v[3].hi, t.v[3].lo), &rbar);
+                }
             }
         }
     }
