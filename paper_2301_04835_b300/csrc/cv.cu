@@ -1124,21 +1124,25 @@ __global__ void __launch_bounds__(256) scatter_deposit_kernel(long long N, int d
         for (int k = 0; k < 3; ++k) dcpre[k] = ctr[k];
     }
     pdl_wait();
+    // every load of the update first (one round trip to L2 for all of them)
+    R g[3] = {R(0), R(0), R(0)};
+    if (act) {
+        f = force[i];
+        for (int c = 0; c < d && c < 3; ++c) {
+            jr[c] = J[(size_t)c * N + i];
+            g[c] = dV[w * 4 + c];
+        }
+    }
     // after the wait: the engine's list build may still be reading the
     // counts until then (a joined edge lets this launch start early)
     for (long long c = i; c < ncells; c += (long long)gridDim.x * blockDim.x) ccount[c] = 0;
     if (nl_ctl && i == 0) *nl_ctl = 0u;
-    if (act) {
-        f = force[i];
-        for (int c = 0; c < d && c < 3; ++c) jr[c] = J[(size_t)c * N + i];
-    }
     if (dep_block) deposit_block_at<R>(dp, dpre, dcpre, xi, V, count, step, dep, ctr, h64, h32, status);
     if (!act) return;
     for (int c = 0; c < d && c < 3; ++c) {
-        const R g = dV[w * 4 + c];
-        f.x -= g * jr[c].x;
-        f.y -= g * jr[c].y;
-        f.z -= g * jr[c].z;
+        f.x -= g[c] * jr[c].x;
+        f.y -= g[c] * jr[c].y;
+        f.z -= g[c] * jr[c].z;
     }
     force[i] = f;
     v.x += half_dt_over_m * f.x;
