@@ -115,17 +115,19 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
         if (a >= 0) pbs = t.inv_b ? t.inv_b[a] : (a < t.nw ? a : -1);
     }
     wait();
+    // the partner's and both targets' positions in one round trip, before
+    // the shared-memory stores (which the compiler will not move loads past)
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), t0 = p, t1 = p;
+    if (jq >= 0) p = t.pos[jq];
+    if (a0 >= 0) t0 = t.pos[a0];
+    if (a1 >= 0) t1 = t.pos[a1];
     if (jq >= 0) {
-        const float4 p = t.pos[jq];
         srcA[q] = make_float4(-p.x, -p.x, -p.y, -p.y);
         srcB[q] = make_float4(-p.z, -p.z, 1.f, 1.f);
     } else {  // padding: weight 0
         srcA[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         srcB[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float4 t0 = make_float4(0.f, 0.f, 0.f, 0.f), t1 = t0;
-    if (a0 >= 0) t0 = t.pos[a0];
-    if (a1 >= 0) t1 = t.pos[a1];
     const float2 tx = make_float2(t0.x, t1.x), ty = make_float2(t0.y, t1.y), tz = make_float2(t0.z, t1.z);
     // an empty target lane adds nothing to the columns
     const float2 gpl = make_float2(a0 >= 0 ? t.gpref : 0.f, a1 >= 0 ? t.gpref : 0.f);

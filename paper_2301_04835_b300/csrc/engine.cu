@@ -31,16 +31,28 @@ __global__ void baoab_first_kernel(long long N, R4<R>* __restrict__ x, R4<R>* __
     pdl_wait();
     pdl_trigger();  // the CV kernels that follow may launch; they wait for these positions
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // every load first (one round trip), then the zeroing stores and the update
+    const bool act = i < N;
+    R4<R> xa = mk4<R>(R(0), R(0), R(0), R(0)), va = xa, fa = xa, ra = xa;
+    if (act) {
+        xa = x[i];
+        va = v[i];
+        fa = f[i];
+        if (nl_flag) ra = xref[i];
+    }
+    const long long t = *step;
     if (i < W)
         for (int c = 0; c < 3; ++c)
             if (xmask >> c & 1) xi[i * 4 + c] = 0.0;
-    if (i >= N) return;
+    if (!act) return;
     for (int c = 0; c < 3; ++c)
         if (jmask >> c & 1) J[(size_t)c * N + i] = mk4<R>(R(0), R(0), R(0), R(0));
-    baoab_first_atom<R>(i, *step, x, v, f, seed, half, inv_m, c1, c2, dims);
+    const Normal3<R> n = noise3<R>(seed, t, (uint32_t)i);
+    baoa_update<R>(xa, va, fa, n.g, half, inv_m, c1, c2, dims);
+    x[i] = xa;
+    v[i] = va;
     if (nl_flag) {  // moved more than half the skin since the neighbour lists were built
-        const R4<R> p = x[i], q = xref[i];
-        const R dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        const R dx = xa.x - ra.x, dy = xa.y - ra.y, dz = xa.z - ra.z;
         if (dx * dx + dy * dy + dz * dz > half_skin2) atomicOr(nl_flag, 1u);
     }
 }
