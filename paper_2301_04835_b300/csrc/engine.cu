@@ -121,10 +121,11 @@ __global__ void nl_bin_kernel(long long N, const R4<R>* __restrict__ x, Box box,
     // this wait (the flag it reads is then final)
     pdl_wait();
     pdl_trigger();
-    if (*ctl == 0u) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // the position is loaded with the flag (one round trip in a rebuild step)
+    const R4<R> p = i < N ? x[i] : mk4<R>(R(0), R(0), R(0), R(0));
+    if (*ctl == 0u) return;
     if (i >= N) return;
-    const R4<R> p = x[i];
     const int cell = (cell_coord<R>(p.x, box_inv<R>(box, 0), ncx) * ncy + cell_coord<R>(p.y, box_inv<R>(box, 1), ncy)) *
                          ncz + cell_coord<R>(p.z, box_inv<R>(box, 2), ncz);
     const int slot = atomicAdd(&ccount[cell], 1);
