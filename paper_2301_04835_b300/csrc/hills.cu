@@ -61,26 +61,34 @@ __global__ void __launch_bounds__(256) hills_finalize_kernel(const dbl4* __restr
     }
 }
 
-// Fixed-order sum of the S split partials of the FP32 kernel, 32 points per
-// CTA: lane l takes point 32 b + l, so each split's row of 32 records is one
-// coalesced 1 KB read; warp w takes splits w, w + 32, ... (several loads in
-// flight per thread), and warp 0 adds the 32 warp sums of its point in warp
-// order.
+// Fixed-order sum of the S split partials of the FP32 kernel, FIN_P points
+// per CTA (more CTAs than one per 32 points: at a few hundred points the
+// partials are several MB, and the read needs more SMs than P / 32): lane l
+// of warp w takes point FIN_P b + l % FIN_P and splits g, g + 128, ...
+// with g = 4 w + l / FIN_P (each split's FIN_P records are one 256-byte
+// read); the four groups of a warp meet by a fixed xor tree, and one thread
+// per point adds the 32 warp sums in warp order.
 constexpr int FIN_W = 32;  // warps per finalize CTA
+constexpr int FIN_P = 8;   // points per finalize CTA
 __global__ void __launch_bounds__(FIN_W * 32) hills_finalize_cf_kernel(const dbl4* __restrict__ partial, int S, int P,
                                                                       HillOut<float> o)
 {
-    __shared__ CF4 red[FIN_W][32];
+    __shared__ CF4 red[FIN_W][FIN_P];
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
-    const int p = blockIdx.x * 32 + lane;
+    const int p = blockIdx.x * FIN_P + lane % FIN_P;
+    constexpr int G = FIN_W * 32 / FIN_P;  // split groups
     CF4 a{};
     if (p < P) {
 #pragma unroll 4
-        for (int s = w; s < S; s += FIN_W) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
+        for (int s = 4 * w + lane / FIN_P; s < S; s += G) cf4_add(a, load_cf4(partial + (size_t)s * P + p));
     }
-    red[w][lane] = a;
+#pragma unroll
+    for (int off = FIN_P; off < 32; off <<= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.v[i] = cf_add(a.v[i], cf_shfl_xor(a.v[i], off));
+    if (lane < FIN_P) red[w][lane] = a;
     __syncthreads();
-    if (w == 0 && p < P) {
+    if (w == 0 && lane < FIN_P && p < P) {
         CF4 t = red[0][lane];
         for (int k = 1; k < FIN_W; ++k) cf4_add(t, red[k][lane]);
         emit_cf(p, t, o);
@@ -764,7 +772,7 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
                                  Pi, h->ctr, prm, part, o, cap_pairs);
         mark(h, "hills_sum_f32");
         if (!fused) {
-            hills_finalize_cf_kernel<<<(Pi + 31) / 32, FIN_W * 32, 0, h->stream>>>(part, pl.split, Pi, o);
+            hills_finalize_cf_kernel<<<(Pi + FIN_P - 1) / FIN_P, FIN_W * 32, 0, h->stream>>>(part, pl.split, Pi, o);
             mark(h, "hills_finalize");
         }
     } else {
