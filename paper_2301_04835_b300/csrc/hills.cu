@@ -74,6 +74,10 @@ __global__ void __launch_bounds__(FIN_W * 32) hills_finalize_cf_kernel(const dbl
                                                                       HillOut<float> o)
 {
     __shared__ CF4 red[FIN_W][FIN_P];
+    // a programmatic dependent of the split kernel (its launch overlaps that
+    // kernel's run): the partials are read after the wait
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
     const int p = blockIdx.x * FIN_P + lane % FIN_P;
     constexpr int G = FIN_W * 32 / FIN_P;  // split groups
@@ -772,7 +776,8 @@ int launch_hills_range(wtmd_t* h, const void* xi, bool xi_f64, int xs, int64_t P
                                  Pi, h->ctr, prm, part, o, cap_pairs);
         mark(h, "hills_sum_f32");
         if (!fused) {
-            hills_finalize_cf_kernel<<<(Pi + FIN_P - 1) / FIN_P, FIN_W * 32, 0, h->stream>>>(part, pl.split, Pi, o);
+            WTMD_CUDA_TRY(h, launch_pdl(hills_finalize_cf_kernel, dim3((Pi + FIN_P - 1) / FIN_P), dim3(FIN_W * 32), 0,
+                                        h->stream, (const dbl4*)part, pl.split, Pi, o));
             mark(h, "hills_finalize");
         }
     } else {
