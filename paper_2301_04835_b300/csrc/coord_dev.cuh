@@ -228,34 +228,58 @@ __device__ __forceinline__ void coord_tile2_body(const CoordTile2& t, int tile, 
     }
 }
 
-// J of one atom of walker w (local index li) from the FP32 tile partials:
-// its column sums over the tiles, then its row sums over the chunks, each
-// in increasing order, times the walker's scale.
+// J of one atom of walker w from the FP32 tile partials, given its position
+// pb in B and ia in A (-1: not a member) and the walker's scale f: its
+// column sums over the tiles, then its row sums over the chunks, each in
+// increasing order, times the scale.  coord_j_parts takes the atom's local
+// index li instead and reads the three itself.
+__device__ __forceinline__ float4 coord_j_parts_at(const CoordParts& p, int w, int pb, int ia, float f)
+{
+    // the first JB column and JB row partials are in flight together; the
+    // sums run columns then rows, each in increasing order
+    constexpr int JB = 8;
+    const int nt = pb >= 0 ? p.ntile : 0, nc = ia >= 0 ? p.nbchunk : 0;
+    const float4* cb = p.colpart + (size_t)w * p.ntile * p.nB_stride + (pb >= 0 ? pb : 0);
+    const float4* rb = p.rowpart + (size_t)w * p.nbchunk * p.nA + (ia >= 0 ? ia : 0);
+    float4 cu[JB], ru[JB];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) {
+        cu[q] = q < nt ? __ldcg(cb + (size_t)q * p.nB_stride) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ru[q] = q < nc ? __ldcg(rb + (size_t)q * p.nA) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+        if (q < nt) {
+            sx += cu[q].x;
+            sy += cu[q].y;
+            sz += cu[q].z;
+        }
+    for (int t = JB; t < nt; ++t) {
+        const float4 u = __ldcg(cb + (size_t)t * p.nB_stride);
+        sx += u.x;
+        sy += u.y;
+        sz += u.z;
+    }
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+        if (q < nc) {
+            sx += ru[q].x;
+            sy += ru[q].y;
+            sz += ru[q].z;
+        }
+    for (int c = JB; c < nc; ++c) {
+        const float4 u = __ldcg(rb + (size_t)c * p.nA);
+        sx += u.x;
+        sy += u.y;
+        sz += u.z;
+    }
+    return make_float4(f * sx, f * sy, f * sz, 0.f);
+}
+
 __device__ __forceinline__ float4 coord_j_parts(const CoordParts& p, int w, int li)
 {
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    const int pb = p.inv_b ? p.inv_b[li] : li;
-    if (pb >= 0) {
-#pragma unroll 8
-        for (int t = 0; t < p.ntile; ++t) {
-            const float4 u = __ldcg(p.colpart + ((size_t)w * p.ntile + t) * p.nB_stride + pb);
-            sx += u.x;
-            sy += u.y;
-            sz += u.z;
-        }
-    }
-    const int ia = p.inv_a[li];
-    if (ia >= 0) {
-#pragma unroll 8
-        for (int c = 0; c < p.nbchunk; ++c) {
-            const float4 u = __ldcg(p.rowpart + ((size_t)w * p.nbchunk + c) * p.nA + ia);
-            sx += u.x;
-            sy += u.y;
-            sz += u.z;
-        }
-    }
-    const float f = (float)p.scw[w];
-    return make_float4(f * sx, f * sy, f * sz, 0.f);
+    return coord_j_parts_at(p, w, p.inv_b ? p.inv_b[li] : li, p.inv_a[li], (float)p.scw[w]);
 }
 
 }  // namespace wtmd

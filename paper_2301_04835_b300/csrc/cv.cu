@@ -986,13 +986,19 @@ __global__ void coord_jfin_kernel(long long N, const int* __restrict__ aw, const
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     pdl_trigger();
-    int w = 0, li = 0;
+    // the atom's walker, its positions in the two groups and the walker's
+    // scale are constant: read before the wait
+    int w = 0, pb = -1, ia = -1;
+    float f = 0.f;
     if (i < N) {
         w = aw[i];
-        li = (int)(i - woff[w]);
+        const int li = (int)(i - woff[w]);
+        pb = p.inv_b ? p.inv_b[li] : li;
+        ia = p.inv_a[li];
+        f = (float)p.scw[w];
     }
     pdl_wait();
-    if (i < N) J[i] = coord_j_parts(p, w, li);
+    if (i < N) J[i] = coord_j_parts_at(p, w, pb, ia, f);
 }
 
 // J rows and the CV value from the tile partials.  Thread k sums the chunk
